@@ -1,0 +1,148 @@
+"""Pins for the merge-step oracle (Sec. 4.2.1) and the numpy model of Alg. 2."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import check, merge
+from paper_2508_11467_gb300 import inputs
+
+EPS = np.finfo(np.float64).eps
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _random_M(N, seed, gap=1e-3):
+    rng = np.random.default_rng(seed)
+    d = np.concatenate(([0.0], np.sort(rng.uniform(gap, 1.0, N - 1))))
+    # keep poles separated by at least gap
+    for i in range(1, N):
+        d[i] = max(d[i], d[i - 1] + gap)
+    z = rng.uniform(0.05, 0.5, N) * rng.choice([-1.0, 1.0], N)
+    return d, z
+
+
+def _dense_M(d, z):
+    N = d.shape[0]
+    M = np.zeros((N, N))
+    M[0, :] = z
+    M[np.arange(1, N), np.arange(1, N)] = d[1:]
+    return M
+
+
+@pytest.mark.parametrize("N,seed", [(1, 0), (2, 1), (5, 2), (40, 3), (200, 4)])
+def test_secular_roots_are_singular_values_of_M(N, seed):
+    d, z = _random_M(N, seed)
+    org, tau, omega = merge.secular_roots(d, z)
+    # library pin: singular values of the dense M (Eq. diag-one-side-M)
+    ref = np.sort(np.linalg.svd(_dense_M(d, z), compute_uv=False))
+    assert np.max(np.abs(omega - ref)) <= 8 * N * EPS * ref[-1]
+    # interlacing d_i < w_i < d_{i+1}
+    assert np.all(omega > d) and np.all(omega[:-1] < d[1:])
+    # the origin is the nearer pole
+    assert np.all(np.abs(tau) <= 0.5 * np.concatenate((np.diff(d), [np.inf])) * (1 + 1e-12))
+    f, scale = merge.secular_f(d, z, org, tau)
+    assert np.all(np.abs(f) <= 64 * N * EPS * scale)
+
+
+def test_lowner_reproduces_z_when_separated():
+    d, z = _random_M(60, 9, gap=1e-2)
+    org, tau, _ = merge.secular_roots(d, z)
+    zt = merge.lowner_ztilde(d, z, org, tau)
+    assert np.all(np.sign(zt) == np.sign(z))
+    normM = np.linalg.norm(_dense_M(d, z), 2)
+    assert np.max(np.abs(zt - z)) <= 1e3 * 60 * EPS * normM
+
+
+def test_lowner_roots_are_exact_for_ztilde():
+    # omega are (to rounding) the exact roots of the secular equation of z~
+    d, z = _random_M(80, 10, gap=1e-3)
+    org, tau, _ = merge.secular_roots(d, z)
+    zt = merge.lowner_ztilde(d, z, org, tau)
+    f, scale = merge.secular_f(d, zt, org, tau)
+    assert np.all(np.abs(f) <= 64 * 80 * EPS * scale)
+
+
+@pytest.mark.parametrize("N,seed", [(1, 1), (3, 2), (64, 5), (300, 6)])
+def test_m_vectors_orthonormal_and_exact(N, seed):
+    d, z = _random_M(N, seed, gap=1e-4)
+    org, tau, omega = merge.secular_roots(d, z)
+    zt = merge.lowner_ztilde(d, z, org, tau)
+    UM, VM = merge.m_vectors(d, zt, org, tau)
+    assert check.orth_err(UM) <= 16 * N * EPS
+    assert check.orth_err(VM) <= 16 * N * EPS
+    Mt = _dense_M(d, zt)
+    # M~ v_i = w_i u_i (Eq. M-svd-vec)
+    R = Mt @ VM - UM * omega[None, :]
+    assert np.linalg.norm(R) <= 16 * N * EPS * np.linalg.norm(Mt)
+
+
+def test_deflation_cases_n3_golden():
+    with open(os.path.join(GOLDEN, "deflation_n3.json")) as fh:
+        g = json.load(fh)
+    for case in g["cases"]:
+        d = np.array(case["d"])
+        z = np.array(case["z"])
+        tol = merge.deflation_tol(d, 0.5, 0.5)
+        assert tol == 8 * EPS * max(np.max(np.abs(d)), 0.5)
+        out = merge.deflate(d, z, tol)
+        assert out["keep"].tolist() == case["keep"], case["name"]
+        assert out["defl"].tolist() == case["defl"], case["name"]
+        assert np.allclose(out["dval"], case["dval"], rtol=0, atol=0), case["name"]
+        if case["z0_is_tol"]:
+            assert out["zkeep"][0] == tol
+            assert np.allclose(out["zkeep"][1:], case["zkeep_tail"], rtol=0, atol=0)
+        else:
+            assert np.allclose(out["zkeep"], case["zkeep"], rtol=1e-15, atol=0), case["name"]
+        if "rot" in case:
+            kind, p, q, c, s = out["rots"][0]
+            r = case["rot"]
+            assert (kind, p, q) == (r["kind"], r["p"], r["q"])
+            assert abs(c - r["c"]) <= 2 * EPS and abs(s - r["s"]) <= 2 * EPS
+
+
+def test_deflation_is_backward_stable():
+    # P M Q = [[M1, 0], [0, D]] + O(tol): rebuild from the deflated pieces
+    rng = np.random.default_rng(12)
+    N = 30
+    d = np.concatenate(([0.0], np.sort(rng.uniform(0, 1, N - 1))))
+    d[5] = d[4] + 1e-17          # close pair
+    d[1] = 3e-17                 # close to d_0 = 0
+    z = rng.uniform(-0.5, 0.5, N)
+    z[9] = 1e-18                 # small z
+    tol = merge.deflation_tol(d, 0.5, 0.5)
+    out = merge.deflate(d, z, tol)
+    I = np.eye(N)
+    Wr, Vr = merge.apply_rotations(out["rots"], I, I)
+    M = _dense_M(d, z)
+    # rotated basis: M = Wr Mdef Vr^T with Mdef block diagonal after reordering
+    Mdef = Wr.T @ M @ Vr
+    keep, defl = out["keep"], out["defl"]
+    target = np.zeros((N, N))
+    target[np.ix_(keep, keep)] = _dense_M(d[keep], out["zkeep"])
+    target[defl, defl] = out["dval"]
+    assert np.linalg.norm(Mdef - target) <= 8 * tol
+    assert set(keep.tolist()) | set(defl.tolist()) == set(range(N))
+    assert 9 in defl.tolist() and 1 in defl.tolist() and 4 in defl.tolist()
+
+
+@pytest.mark.parametrize("kind,n,leaf", [("uniform", 33, 16), ("uniform", 256, 16), ("graded", 256, 16),
+                                         ("clustered", 256, 16), ("ones", 100, 8), ("uniform", 257, 32)])
+def test_numpy_bdc_model_matches_qr(kind, n, leaf):
+    d, e = inputs.make(kind, n, {"uniform": 0, "graded": 1, "clustered": 2, "ones": 0}[kind])
+    s, U, VT = merge.bdc_svd(d, e, leaf)
+    ref = oracle.sigma_only(d, e)
+    assert check.sigma_rel_err(s, ref) <= 1e-13 * n
+    assert oracle.residual(d, e, s, U, VT) <= 1e-13 * n
+    assert check.orth_err(U) <= 1e-13 * n
+    assert check.orth_err(VT.T) <= 1e-13 * n
+
+
+def test_numpy_bdc_full_deflation():
+    d, _ = inputs.uniform(64, 5)
+    e = np.zeros(63)
+    s, U, VT = merge.bdc_svd(d, e, 8)
+    # every merge deflates fully; only the scaling by max|d| rounds
+    assert np.max(np.abs(s - np.sort(d)[::-1])) <= 2 * EPS * np.max(d)
+    assert oracle.residual(d, e, s, U, VT) <= 4 * EPS
