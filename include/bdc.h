@@ -1,0 +1,159 @@
+/*
+ * bdc.h -- C ABI of the GB300 (sm_103a) bidiagonal divide-and-conquer SVD.
+ *
+ * Problem (Sec. 4.2.1, first display): for the n x n upper bidiagonal B with
+ * diagonal d[0..n-1] and superdiagonal e[0..n-2] compute B = U S V^T with
+ * S = diag(s_0 >= s_1 >= ... >= s_{n-1} >= 0) (the ordering of Sec. 1).
+ * The method is Algorithm 2: recursive splitting (Sec. 4.2.1), leaf SVDs by
+ * QR iteration, bottom-up merges made of deflation (Eq. M-condition and the
+ * four N = 3 cases) and the secular solve / vector update (Eqs. M-svd-val,
+ * bdc-zi, M-svd-vec, bdc-Mv2Bv-u-vt), then a final sort.  Every step runs on
+ * the GPU; the host only plans launches.
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are column-major doubles.  U is n x n with leading dimension
+ *     ldu >= max(1, n): column i is the left singular vector of s_i.  VT is
+ *     n x n with leading dimension ldvt >= max(1, n): row i is the right
+ *     singular vector of s_i.
+ *   - Unless stated otherwise every pointer is a DEVICE pointer owned by the
+ *     caller; inputs are read only.  The library keeps no pointer after a
+ *     call returns and holds no state between calls.
+ *   - Return codes: 0 success; -i when argument i (1-based) is illegal;
+ *     +k (k > 0) when k leaf QR iterations or secular roots failed to
+ *     converge (results are then not reliable); BDC_ERR_CUDA for a CUDA
+ *     launch / allocation failure; BDC_ERR_TIMEOUT when a bounded device
+ *     wait gave up; BDC_ERR_NONFINITE when d or e holds NaN or Inf.
+ *   - Streams: all work is enqueued on `stream` (0 = legacy default).
+ */
+#ifndef BDC_H
+#define BDC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *bdc_stream_t; /* same object as cudaStream_t */
+
+#define BDC_ERR_CUDA      (-1000)
+#define BDC_ERR_TIMEOUT   (-1001)
+#define BDC_ERR_NONFINITE (-1002)
+#define BDC_ERR_INTERNAL  (-1003)
+
+/* Precision of the merge products W~ U_M and Q~ V_M (Eq. bdc-Mv2Bv-u-vt).
+ *   BDC_FP64          FP64 products.
+ *   BDC_MIXED_BF16X3  FP64 operands split into two BF16 pieces, the three
+ *                     leading products hi*hi + hi*lo + lo*hi on tcgen05
+ *                     tensor cores with FP32 accumulation (about 1e-6
+ *                     relative: reported, not accurate to FP64).
+ *   BDC_MIXED_EXACT   error-free slicing: each operand row/column is scaled
+ *                     by a power of two and cut into `slices` BF16 integer
+ *                     slices; slice products are accumulated exactly (FP32
+ *                     in TMEM over short K chunks, then 64-bit integers) so
+ *                     the result matches FP64 to ~2^-(8*slices-1) relative.
+ * Deflation, secular roots, z-tilde and vector formation are always FP64. */
+typedef enum { BDC_FP64 = 0, BDC_MIXED_BF16X3 = 1, BDC_MIXED_EXACT = 2 } bdc_precision;
+
+/* Starting point of each secular root (Eq. M-svd-val):
+ *   BDC_SEED_PLAIN  interval-midpoint start;
+ *   BDC_SEED_MLP    start proposed by the small MLP in `mlp` (FP32 weights,
+ *                   layout of bdc_mlp_param_count); the FP64 root finder
+ *                   always finishes the root to the same stopping rule. */
+typedef enum { BDC_SEED_PLAIN = 0, BDC_SEED_MLP = 1 } bdc_seed;
+
+typedef struct {
+    int prec;          /* bdc_precision                                   */
+    int seed;          /* bdc_seed                                        */
+    int leaf;          /* leaf size L (>= 4; 0 = default 32)              */
+    int max_iter;      /* secular / QR iteration cap (0 = default 64)     */
+    int slices;        /* BDC_MIXED_EXACT slice count 4..7 (0 = 6)        */
+    int checked;       /* reserved, must be 0                              */
+    const float *mlp;  /* device pointer to MLP weights when seed = MLP    */
+} bdc_opts;
+
+/* Fill *o with the defaults (FP64, plain seed, leaf 32). */
+void bdc_opts_default(bdc_opts *o);
+
+/* SVD of the n x n upper bidiagonal (d, e), FP64 defaults, synchronous:
+ * returns after the result and the status are known.  Allocates its
+ * workspace with cudaMallocAsync on `stream` and frees it before returning.
+ * n = 0 is a no-op; n = 1 gives s = |d0|, U = sign(d0), VT = 1.
+ * d[n], e[n-1] (e may be NULL when n <= 1), U, S[n], VT: device pointers. */
+int bdc_svd(int n, const double *d, const double *e, double *U, double *S, double *VT,
+            int ldu, int ldvt, bdc_stream_t stream);
+
+/* Workspace bytes needed by bdc_svd_ex for order n and options o. */
+size_t bdc_svd_workspace(int n, const bdc_opts *o);
+
+/* Asynchronous form: the caller passes `work` (device, lwork bytes,
+ * 256-byte aligned, at least bdc_svd_workspace(n, o)) and `d_info` (device
+ * int): the status code above is written to *d_info on the stream, so the
+ * whole call can be captured in a CUDA graph.  The host return value only
+ * reports argument errors and launch failures. */
+int bdc_svd_ex(int n, const double *d, const double *e, double *U, double *S, double *VT,
+               int ldu, int ldvt, const bdc_opts *o, void *work, size_t lwork,
+               int *d_info, bdc_stream_t stream);
+
+/* Batched SVD of `batch` independent bidiagonals of uneven sizes h_n[b]
+ * (HOST array, each 1..2048).  d[b], e[b], U[b], S[b], VT[b] are device
+ * pointers held in HOST arrays; h_ldu/h_ldvt are host arrays.  All
+ * matrices advance level by level in the same launches (one launch per
+ * stage per level for the whole batch).  Status per matrix in d_info[batch]
+ * (device).  Workspace from bdc_svd_batched_workspace. */
+size_t bdc_svd_batched_workspace(int batch, const int *h_n, const bdc_opts *o);
+int bdc_svd_batched(int batch, const int *h_n, const double *const *d, const double *const *e,
+                    double *const *U, double *const *S, double *const *VT, const int *h_ldu,
+                    const int *h_ldvt, const bdc_opts *o, void *work, size_t lwork,
+                    int *d_info, bdc_stream_t stream);
+
+/* ---------------- step entry points (one merge stage each) ----------------
+ * They run a single stage of Sec. 4.2.1 on one problem so that each kernel
+ * can be checked against the oracle element by element.  d is sorted
+ * ascending with d[0] = 0 and distinct entries; z has no zero entry (the
+ * state after deflation, Eq. M-condition). */
+
+/* Roots of the secular equation f(w) = 1 + sum_j z_j^2 / (d_j^2 - w^2)
+ * (Eq. M-svd-val), one warp per root.  Root i is returned as
+ * omega[i] = d[org[i]] + tau[i], org[i] in {i, i+1} the nearer pole.
+ * Status (non-converged count) is written to *d_info. */
+int bdc_secular_solve(int N, const double *d, const double *z, int *org, double *tau,
+                      double *omega, int max_iter, int *d_info, bdc_stream_t stream);
+
+/* z-tilde of Eq. (bdc-zi) from the roots (org, tau); sign taken from z. */
+int bdc_lowner_z(int N, const double *d, const double *z, const int *org, const double *tau,
+                 double *zt, bdc_stream_t stream);
+
+/* Normalised singular vectors of M~ (Eq. M-svd-vec): column i of UM (N x N,
+ * ld ldum) is u_i and of VM (ld ldvm) is v_i. */
+int bdc_m_vectors(int N, const double *d, const double *zt, const int *org, const double *tau,
+                  double *UM, int ldum, double *VM, int ldvm, bdc_stream_t stream);
+
+/* Deflation of Sec. 4.2.1 on sorted (d, z) with tolerance tol.  Outputs
+ * (device): keep[m] (1 = survivor, 0 = deflated), zout[m] (z after the
+ * rotations; 0 for deflated entries), dval[m] (value of a deflated entry,
+ * unspecified for survivors). */
+int bdc_deflate(int m, const double *d, const double *z, double tol, int *keep, double *zout,
+                double *dval, bdc_stream_t stream);
+
+/* Merge product C = A * B (M x N, inner K), column-major, with the chosen
+ * precision (bdc_precision): FP64, or the split BF16 tcgen05 products.  A,
+ * B, C device; `work` device scratch of bdc_gemm_workspace bytes. */
+size_t bdc_gemm_workspace(int M, int N, int K, int prec, int slices);
+int bdc_gemm(int M, int N, int K, const double *A, int lda, const double *B, int ldb, double *C,
+             int ldc, int prec, int slices, void *work, size_t lwork, bdc_stream_t stream);
+
+/* ---------------- MLP seeding of the secular roots ---------------------- */
+/* Number of FP32 parameters of the 2 x 64 MLP (inputs -> 64 -> 64 -> 1). */
+int bdc_mlp_param_count(void);
+/* Number of input features per root. */
+int bdc_mlp_feature_count(void);
+
+/* Human-readable text for a status code (static string). */
+const char *bdc_status_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BDC_H */

@@ -1,0 +1,248 @@
+"""Thin ctypes binding of libbdc.so (include/bdc.h).
+
+Argument marshalling only: tensors are passed as raw device pointers, the
+current PyTorch stream as the CUDA stream.  Every step of the SVD runs in the
+library's CUDA kernels; there is no CPU path.  The library is loaded on first
+use and a missing build raises immediately.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+
+BDC_FP64, BDC_MIXED_BF16X3, BDC_MIXED_EXACT = 0, 1, 2
+BDC_SEED_PLAIN, BDC_SEED_MLP = 0, 1
+BDC_ERR_CUDA, BDC_ERR_TIMEOUT, BDC_ERR_NONFINITE, BDC_ERR_INTERNAL = -1000, -1001, -1002, -1003
+PREC = {"fp64": BDC_FP64, "bf16x3": BDC_MIXED_BF16X3, "exact": BDC_MIXED_EXACT, "mixed": BDC_MIXED_EXACT}
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int), ("seed", ctypes.c_int), ("leaf", ctypes.c_int),
+                ("max_iter", ctypes.c_int), ("slices", ctypes.c_int), ("checked", ctypes.c_int),
+                ("mlp", ctypes.c_void_p)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+_VP, _I, _SZ, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_double
+_SIGS = {
+    "bdc_opts_default": (None, [_VP]),
+    "bdc_svd": (_I, [_I, _VP, _VP, _VP, _VP, _VP, _I, _I, _VP]),
+    "bdc_svd_workspace": (_SZ, [_I, _VP]),
+    "bdc_svd_ex": (_I, [_I, _VP, _VP, _VP, _VP, _VP, _I, _I, _VP, _VP, _SZ, _VP, _VP]),
+    "bdc_svd_batched_workspace": (_SZ, [_I, _VP, _VP]),
+    "bdc_svd_batched": (_I, [_I, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP, _VP]),
+    "bdc_secular_solve": (_I, [_I, _VP, _VP, _VP, _VP, _VP, _I, _VP, _VP]),
+    "bdc_lowner_z": (_I, [_I, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "bdc_m_vectors": (_I, [_I, _VP, _VP, _VP, _VP, _VP, _I, _VP, _I, _VP]),
+    "bdc_deflate": (_I, [_I, _VP, _VP, _D, _VP, _VP, _VP, _VP]),
+    "bdc_gemm_workspace": (_SZ, [_I, _I, _I, _I, _I]),
+    "bdc_gemm": (_I, [_I, _I, _I, _VP, _I, _VP, _I, _VP, _I, _I, _I, _VP, _SZ, _VP]),
+    "bdc_mlp_param_count": (_I, []),
+    "bdc_mlp_feature_count": (_I, []),
+    "bdc_status_string": (ctypes.c_char_p, [_I]),
+}
+
+
+def exported_symbols():
+    """Names the binding expects the library to export."""
+    return sorted(_SIGS)
+
+
+def lib():
+    """Load libbdc.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                                   "paper_2508_11467_gb300.build.build() (nvcc, sm_103a)")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def status_string(code: int) -> str:
+    return lib().bdc_status_string(int(code)).decode()
+
+
+class BDCError(RuntimeError):
+    def __init__(self, where: str, code: int):
+        super().__init__(f"{where}: {code} ({status_string(code)})")
+        self.code = code
+
+
+def _check(where, code):
+    if code != 0:
+        raise BDCError(where, code)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t, dtype=torch.float64):
+    if not isinstance(t, torch.Tensor):
+        t = torch.as_tensor(t)
+    if t.device.type != "cuda":
+        raise ValueError("bdc expects CUDA tensors (device memory)")
+    return t.to(dtype).contiguous()
+
+
+def make_opts(prec="fp64", leaf=32, max_iter=64, slices=6, seed="plain", mlp=None) -> Opts:
+    o = Opts()
+    lib().bdc_opts_default(ctypes.byref(o))
+    o.prec = PREC[prec] if isinstance(prec, str) else int(prec)
+    o.leaf = int(leaf)
+    o.max_iter = int(max_iter)
+    o.slices = int(slices)
+    o.seed = BDC_SEED_MLP if seed == "mlp" else BDC_SEED_PLAIN
+    o.mlp = ctypes.c_void_p(mlp.data_ptr()) if mlp is not None else None
+    return o
+
+
+def workspace_bytes(n: int, opts: Opts) -> int:
+    return int(lib().bdc_svd_workspace(int(n), ctypes.byref(opts)))
+
+
+def svd(d, e, *, prec="fp64", leaf=32, max_iter=64, slices=6, seed="plain", mlp=None,
+        stream=None, work=None, check=True):
+    """SVD of the upper bidiagonal (d, e) on the GPU.
+
+    Returns (S, U, VT) as CUDA float64 tensors (U column-major: U[:, i] is a
+    left vector; VT[i, :] a right vector) and the status code.
+    """
+    d = _dev(d)
+    n = d.shape[0]
+    e = _dev(e) if n > 1 else torch.zeros(1, dtype=torch.float64, device=d.device)
+    o = make_opts(prec, leaf, max_iter, slices, seed, mlp)
+    # column-major outputs: allocate the transpose and view it back
+    Ut = torch.empty((n, n), dtype=torch.float64, device=d.device)
+    VTt = torch.empty((n, n), dtype=torch.float64, device=d.device)
+    S = torch.empty(max(n, 1), dtype=torch.float64, device=d.device)
+    info = torch.zeros(1, dtype=torch.int32, device=d.device)
+    lw = workspace_bytes(n, o)
+    if work is None or work.numel() < lw + 256:
+        work = torch.empty(lw + 256, dtype=torch.uint8, device=d.device)
+    rc = lib().bdc_svd_ex(n, _ptr(d), _ptr(e), _ptr(Ut), _ptr(S), _ptr(VTt), max(n, 1), max(n, 1),
+                          ctypes.byref(o), _ptr(work), work.numel(), _ptr(info), _stream(stream))
+    _check("bdc_svd_ex", rc)
+    code = int(info.item()) if check else None
+    if check and code != 0:
+        raise BDCError("bdc_svd_ex (device status)", code)
+    return S[:n], Ut.t(), VTt.t(), code
+
+
+def svd_sync(d, e, stream=None):
+    """bdc_svd: defaults, library-managed workspace, synchronous status."""
+    d = _dev(d)
+    n = d.shape[0]
+    e = _dev(e) if n > 1 else torch.zeros(1, dtype=torch.float64, device=d.device)
+    Ut = torch.empty((n, n), dtype=torch.float64, device=d.device)
+    VTt = torch.empty((n, n), dtype=torch.float64, device=d.device)
+    S = torch.empty(max(n, 1), dtype=torch.float64, device=d.device)
+    rc = lib().bdc_svd(n, _ptr(d), _ptr(e), _ptr(Ut), _ptr(S), _ptr(VTt), max(n, 1), max(n, 1),
+                       _stream(stream))
+    return S[:n], Ut.t(), VTt.t(), rc
+
+
+def svd_batched(ds, es, *, prec="fp64", leaf=32, max_iter=64, slices=6, stream=None, work=None):
+    """Batched SVD of bidiagonals of uneven sizes (lists of CUDA tensors)."""
+    import numpy as np
+    B = len(ds)
+    ns = np.array([int(x.shape[0]) for x in ds], dtype=np.int32)
+    o = make_opts(prec, leaf, max_iter, slices)
+    dev = ds[0].device
+    ds = [_dev(x) for x in ds]
+    es = [_dev(x) if x.numel() > 0 else torch.zeros(1, dtype=torch.float64, device=dev) for x in es]
+    Us = [torch.empty((n, n), dtype=torch.float64, device=dev) for n in ns]
+    Ss = [torch.empty(int(n), dtype=torch.float64, device=dev) for n in ns]
+    VTs = [torch.empty((n, n), dtype=torch.float64, device=dev) for n in ns]
+    arr = lambda ts: (ctypes.c_void_p * B)(*[t.data_ptr() for t in ts])
+    lw = int(lib().bdc_svd_batched_workspace(B, ns.ctypes.data_as(ctypes.c_void_p), ctypes.byref(o)))
+    if work is None or work.numel() < lw + 256:
+        work = torch.empty(lw + 256, dtype=torch.uint8, device=dev)
+    info = torch.zeros(B, dtype=torch.int32, device=dev)
+    lds = ns.copy()
+    rc = lib().bdc_svd_batched(B, ns.ctypes.data_as(ctypes.c_void_p), arr(ds), arr(es), arr(Us), arr(Ss),
+                               arr(VTs), lds.ctypes.data_as(ctypes.c_void_p), lds.ctypes.data_as(ctypes.c_void_p),
+                               ctypes.byref(o), _ptr(work), work.numel(), _ptr(info), _stream(stream))
+    _check("bdc_svd_batched", rc)
+    return Ss, [u.t() for u in Us], [v.t() for v in VTs], info
+
+
+def secular_solve(d, z, max_iter=64, stream=None):
+    d, z = _dev(d), _dev(z)
+    N = d.shape[0]
+    org = torch.empty(N, dtype=torch.int32, device=d.device)
+    tau = torch.empty(N, dtype=torch.float64, device=d.device)
+    om = torch.empty(N, dtype=torch.float64, device=d.device)
+    info = torch.zeros(1, dtype=torch.int32, device=d.device)
+    _check("bdc_secular_solve", lib().bdc_secular_solve(N, _ptr(d), _ptr(z), _ptr(org), _ptr(tau), _ptr(om),
+                                                         int(max_iter), _ptr(info), _stream(stream)))
+    return org, tau, om, info
+
+
+def lowner_z(d, z, org, tau, stream=None):
+    d, z, tau = _dev(d), _dev(z), _dev(tau)
+    org = _dev(org, torch.int32)
+    zt = torch.empty_like(d)
+    _check("bdc_lowner_z", lib().bdc_lowner_z(d.shape[0], _ptr(d), _ptr(z), _ptr(org), _ptr(tau), _ptr(zt),
+                                               _stream(stream)))
+    return zt
+
+
+def m_vectors(d, zt, org, tau, stream=None):
+    d, zt, tau = _dev(d), _dev(zt), _dev(tau)
+    org = _dev(org, torch.int32)
+    N = d.shape[0]
+    UMt = torch.empty((N, N), dtype=torch.float64, device=d.device)
+    VMt = torch.empty((N, N), dtype=torch.float64, device=d.device)
+    _check("bdc_m_vectors", lib().bdc_m_vectors(N, _ptr(d), _ptr(zt), _ptr(org), _ptr(tau), _ptr(UMt), N,
+                                                 _ptr(VMt), N, _stream(stream)))
+    return UMt.t(), VMt.t()
+
+
+def deflate(d, z, tol, stream=None):
+    d, z = _dev(d), _dev(z)
+    m = d.shape[0]
+    keep = torch.empty(m, dtype=torch.int32, device=d.device)
+    zout = torch.empty(m, dtype=torch.float64, device=d.device)
+    dval = torch.empty(m, dtype=torch.float64, device=d.device)
+    _check("bdc_deflate", lib().bdc_deflate(m, _ptr(d), _ptr(z), float(tol), _ptr(keep), _ptr(zout), _ptr(dval),
+                                             _stream(stream)))
+    return keep, zout, dval
+
+
+def gemm(A, B, prec="fp64", slices=6, stream=None, work=None):
+    """C = A @ B for column-major views (A: M x K, B: K x N) through bdc_gemm."""
+    A = _dev(A).t().contiguous().t()   # column-major storage
+    B = _dev(B).t().contiguous().t()
+    M, K = A.shape
+    K2, N = B.shape
+    assert K == K2
+    Ct = torch.empty((N, M), dtype=torch.float64, device=A.device)
+    p = PREC[prec] if isinstance(prec, str) else int(prec)
+    lw = int(lib().bdc_gemm_workspace(M, N, K, p, slices))
+    if work is None or work.numel() < lw + 256:
+        work = torch.empty(lw + 256, dtype=torch.uint8, device=A.device)
+    _check("bdc_gemm", lib().bdc_gemm(M, N, K, _ptr(A), max(M, 1), _ptr(B), max(K, 1), _ptr(Ct), max(M, 1), p,
+                                       int(slices), _ptr(work), work.numel(), _stream(stream)))
+    return Ct.t()

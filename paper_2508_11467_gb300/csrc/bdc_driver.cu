@@ -1,0 +1,620 @@
+// Host driver of the bidiagonal divide-and-conquer (Algorithm 2) and the
+// extern "C" entry points of include/bdc.h.
+//
+// Planning (host, integer only): the split of Sec. 4.2.1 applied recursively
+// (k = floor(m/2): the left child has nl = m/2 rows and nl+1 columns, the
+// coupling row follows, the right child inherits the parent's shape) down to
+// the leaf size.  Merge nodes are grouped by height (leaves = 0) so that one
+// launch per stage advances every node of a height of every matrix in the
+// batch.  Descriptors are uploaded once per call from a pinned host blob kept
+// in a small cache, so bdc_svd_ex can be captured in a CUDA graph.
+//
+// Launch sequence per call: scale -> leaves -> for each height:
+// prep (z, sort, deflation) -> gather (rotations, permutation) -> secular
+// roots + z~ -> vectors of M~ -> merge products -> finish -> final sort.
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "bdc_internal.cuh"
+
+namespace bdc {
+
+// mixed-precision product path (bdc_gemm_mixed.cu)
+cudaError_t launch_gemm_mixed(const GemmProb *probs, int nprobs, int mmax_rows, int nmax_cols,
+                              int kmax, int prec, int slices, void *scratch, size_t scratch_bytes,
+                              cudaStream_t st);
+size_t gemm_mixed_scratch(long long rows_total, long long cols_total, int kmax, int prec, int slices);
+
+namespace {
+
+constexpr int kDefaultLeaf = 32;
+constexpr int kDefaultMaxIter = 64;
+
+struct TreeNode {
+    int r0, m, sqre, nl, height, left, right;
+};
+
+// recursive split of the m x (m + sqre) block at rows r0..
+int build_tree(std::vector<TreeNode> &t, int r0, int m, int sqre, int leaf) {
+    TreeNode nd{r0, m, sqre, 0, 0, -1, -1};
+    const int id = (int)t.size();
+    t.push_back(nd);
+    if (m > leaf) {
+        const int nl = m / 2;
+        const int nr = m - nl - 1;
+        const int l = build_tree(t, r0, nl, 1, leaf);
+        const int r = build_tree(t, r0 + nl + 1, nr, sqre, leaf);
+        t[id].nl = nl;
+        t[id].left = l;
+        t[id].right = r;
+        t[id].height = 1 + std::max(t[l].height, t[r].height);
+    }
+    return id;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Plan {
+    int nmat = 0;
+    int leaf = kDefaultLeaf;
+    std::vector<int> n;                    // per matrix
+    std::vector<NodeDesc> leaves;
+    std::vector<std::vector<NodeDesc>> heights;   // merge nodes of height h+1
+    std::vector<int> hmmax;                // max m per height
+    std::vector<int> hmat_rows;            // sum of (m+1) per height (mixed scratch)
+    int leafmax = 0;
+    int nnodes = 0;
+    int maxprobs = 0;
+    int nmax = 0;
+    // workspace layout (byte offsets)
+    size_t off_mats = 0, off_leaves = 0, off_nodes = 0, off_state = 0, off_probs = 0;
+    std::vector<size_t> off_mat_data;      // per matrix
+    std::vector<size_t> off_height_nodes;  // per height, into the nodes area
+    size_t off_mixed = 0, mixed_bytes = 0;
+    size_t total = 0;
+};
+
+size_t per_matrix_bytes(int n) {
+    const size_t N = (size_t)n;
+    size_t b = 0;
+    b += align256(sizeof(double) * 2 * N);            // dsc, esc
+    b += align256(sizeof(double) * 2 * N * N);        // U, V
+    b += align256(sizeof(double) * 12 * N + 64);      // D ds zs rc rs dM zM zt tau omega dval scale
+    b += align256(sizeof(int) * (13 * N + 128));      // Q src role org kposM dsrc dest slist sidx invK(4n) info
+    const size_t big = (N + 1) * (N + 16) + 64;
+    b += 4 * align256(sizeof(double) * big);          // Wt Qt UM VM
+    return b;
+}
+
+Plan make_plan(int nmat, const int *ns, const bdc_opts &o) {
+    Plan p;
+    p.nmat = nmat;
+    p.leaf = o.leaf > 0 ? o.leaf : kDefaultLeaf;
+    if (p.leaf < 4) p.leaf = 4;
+    p.n.assign(ns, ns + nmat);
+    int gid = 0;
+    for (int mi = 0; mi < nmat; ++mi) {
+        const int n = ns[mi];
+        p.nmax = std::max(p.nmax, n);
+        if (n <= 0) continue;
+        std::vector<TreeNode> t;
+        build_tree(t, 0, n, 0, p.leaf);
+        // kbase: K-indexed scratch (reused by every height), 8 extra slots per
+        // node before it within its height (pre-order keeps r0 ascending)
+        std::vector<int> kextra(t.size() + 1, 0);
+        for (const TreeNode &tn : t) {
+            NodeDesc nd{};
+            nd.mat = mi;
+            nd.id = gid++;
+            nd.r0 = tn.r0;
+            nd.m = tn.m;
+            nd.sqre = tn.sqre;
+            nd.nl = tn.nl;
+            if (tn.height == 0) {
+                p.leaves.push_back(nd);
+                p.leafmax = std::max(p.leafmax, tn.m);
+            } else {
+                nd.kbase = tn.r0 + 8 * (kextra[tn.height]++);
+                if ((int)p.heights.size() < tn.height) {
+                    p.heights.resize(tn.height);
+                    p.hmmax.resize(tn.height, 0);
+                    p.hmat_rows.resize(tn.height, 0);
+                }
+                p.heights[tn.height - 1].push_back(nd);
+                p.hmmax[tn.height - 1] = std::max(p.hmmax[tn.height - 1], tn.m);
+                p.hmat_rows[tn.height - 1] += tn.m + 1;
+            }
+        }
+    }
+    p.nnodes = gid;
+    for (auto &h : p.heights) p.maxprobs = std::max(p.maxprobs, 4 * (int)h.size());
+    // byte layout
+    size_t off = 0;
+    p.off_mats = off; off += align256(sizeof(MatDesc) * std::max(nmat, 1));
+    p.off_leaves = off; off += align256(sizeof(NodeDesc) * std::max<size_t>(p.leaves.size(), 1));
+    p.off_nodes = off;
+    size_t nodes_bytes = 0;
+    for (auto &h : p.heights) {
+        p.off_height_nodes.push_back(nodes_bytes);
+        nodes_bytes += sizeof(NodeDesc) * h.size();
+    }
+    off += align256(std::max<size_t>(nodes_bytes, 1));
+    p.off_state = off; off += align256(sizeof(NodeState) * std::max(p.nnodes, 1));
+    p.off_probs = off; off += align256(sizeof(GemmProb) * std::max(p.maxprobs, 1));
+    for (int mi = 0; mi < nmat; ++mi) {
+        p.off_mat_data.push_back(off);
+        off += per_matrix_bytes(std::max(ns[mi], 1));
+    }
+    if (o.prec != BDC_FP64) {
+        size_t mb = 0;
+        for (size_t h = 0; h < p.heights.size(); ++h) {
+            long long rows = 0, cols = 0;
+            for (auto &nd : p.heights[h]) { rows += 2 * (nd.m + 2); cols += 2 * (nd.m + 8); }
+            mb = std::max(mb, gemm_mixed_scratch(rows, cols, p.hmmax[h] + 16, o.prec,
+                                                 o.slices > 0 ? o.slices : 6));
+        }
+        p.off_mixed = off;
+        p.mixed_bytes = mb;
+        off += align256(mb);
+    }
+    p.total = off + 256;
+    return p;
+}
+
+// fill the matrix descriptor of matrix mi from the carved workspace
+MatDesc carve(char *base, size_t off, int n) {
+    MatDesc md{};
+    const size_t N = (size_t)std::max(n, 1);
+    char *p = base + off;
+    auto take = [&](size_t bytes) { char *r = p; p += align256(bytes); return r; };
+    md.n = n;
+    md.wstride = (long long)N + 16;
+    double *de = (double *)take(sizeof(double) * 2 * N);
+    md.dsc = de; md.esc = de + N;
+    double *uv = (double *)take(sizeof(double) * 2 * N * N);
+    md.U = uv; md.V = uv + N * N;
+    double *dd = (double *)take(sizeof(double) * 12 * N + 64);
+    md.D = dd; md.ds = dd + N; md.zs = dd + 2 * N; md.rc = dd + 3 * N; md.rs = dd + 4 * N;
+    md.dM = dd + 5 * N; md.zM = dd + 6 * N; md.zt = dd + 7 * N; md.tau = dd + 8 * N;
+    md.omega = dd + 9 * N; md.dval = dd + 10 * N; md.scale = dd + 11 * N;
+    int *ii = (int *)take(sizeof(int) * (13 * N + 128));
+    md.Q = ii; md.src = ii + N; md.role = ii + 2 * N; md.org = ii + 3 * N; md.kposM = ii + 4 * N;
+    md.dsrc = ii + 5 * N; md.dest = ii + 6 * N; md.slist = ii + 7 * N; md.sidx = ii + 8 * N;
+    md.invK = ii + 9 * N;                 // K-indexed: r0 + 8 * (index within height) + K
+    md.info = ii + 13 * N + 64;
+    const size_t big = (N + 1) * (N + 16) + 64;
+    md.Wt = (double *)take(sizeof(double) * big);
+    md.Qt = (double *)take(sizeof(double) * big);
+    md.UM = (double *)take(sizeof(double) * big);
+    md.VM = (double *)take(sizeof(double) * big);
+    return md;
+}
+
+// ------------------------------------------------------------------ kernels
+__global__ void k_scale(const MatDesc *__restrict__ mats) {
+    __shared__ double sh[32];
+    __shared__ int bad;
+    const MatDesc md = mats[blockIdx.x];
+    const int n = md.n;
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
+    double mx = 0.0;
+    int nonfinite = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double v = md.d_in[i];
+        nonfinite |= !isfinite(v);
+        mx = fmax(mx, fabs(v));
+        if (i + 1 < n) {
+            const double w = md.e_in[i];
+            nonfinite |= !isfinite(w);
+            mx = fmax(mx, fabs(w));
+        }
+    }
+    mx = warp_max(mx);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
+    if (nonfinite) atomicOr(&bad, 1);
+    __syncthreads();
+    double s = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s = fmax(s, sh[k]);
+    const bool nf = bad != 0;
+    const double se = (nf || s == 0.0) ? 1.0 : s;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        md.dsc[i] = nf ? 0.0 : md.d_in[i] / se;
+        md.esc[i] = (nf || i + 1 >= n) ? 0.0 : md.e_in[i] / se;
+    }
+    if (threadIdx.x == 0) {
+        md.scale[0] = nf ? 0.0 : s;
+        md.info[0] = nf ? BDC_ERR_NONFINITE : 0;
+    }
+}
+
+// final order (descending), unscale, U columns and V^T rows (tiled transpose)
+__global__ void k_final(const MatDesc *__restrict__ mats, int tiles_per_side) {
+    __shared__ double tile[32][33];
+    const MatDesc md = mats[blockIdx.z];
+    const int n = md.n;
+    const int tc = blockIdx.x % tiles_per_side, tj = blockIdx.x / tiles_per_side;
+    const int c0 = tc * 32, j0 = tj * 32;
+    if (c0 >= n || j0 >= n) return;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+    const double s = md.scale[0];
+    // U: output column c = source column Q[n-1-c], rows j0..j0+31
+    for (int cc = ty; cc < 32; cc += 8) {
+        const int c = c0 + cc;
+        if (c >= n) break;
+        const int src = md.Q[n - 1 - c];
+        const int j = j0 + tx;
+        if (j < n) {
+            md.Uo[(size_t)c * md.ldu + j] = md.U[(size_t)src * n + j];
+            tile[cc][tx] = md.V[(size_t)src * n + j];
+        }
+        if (tj == 0 && tx == 0) md.So[c] = md.D[src] * s;
+    }
+    __syncthreads();
+    // VT(c, j) = V(j, src(c)): write down columns j of VT, contiguous in c
+    for (int jj = ty; jj < 32; jj += 8) {
+        const int j = j0 + jj, c = c0 + tx;
+        if (j < n && c < n) md.VTo[(size_t)j * md.ldvt + c] = tile[tx][jj];
+    }
+}
+
+struct PinnedBlob {
+    void *host = nullptr;
+    size_t bytes = 0;
+};
+
+std::mutex g_cache_mu;
+std::map<std::vector<long long>, PinnedBlob> g_cache;
+
+// upload descriptors for the plan into the workspace (graph-capturable copy
+// from a pinned blob that stays alive in a bounded cache)
+cudaError_t upload(const Plan &p, char *work, const std::vector<MatDesc> &mats, cudaStream_t st) {
+    const size_t bytes = p.off_mat_data.empty() ? p.off_probs : p.off_mat_data[0];
+    std::vector<char> blob(bytes, 0);
+    std::memcpy(blob.data() + p.off_mats, mats.data(), sizeof(MatDesc) * mats.size());
+    if (!p.leaves.empty())
+        std::memcpy(blob.data() + p.off_leaves, p.leaves.data(), sizeof(NodeDesc) * p.leaves.size());
+    for (size_t h = 0; h < p.heights.size(); ++h)
+        std::memcpy(blob.data() + p.off_nodes + p.off_height_nodes[h], p.heights[h].data(),
+                    sizeof(NodeDesc) * p.heights[h].size());
+    // key: the blob contents (pointers included) -> identical calls reuse one buffer
+    std::vector<long long> key((bytes + 7) / 8, 0);
+    std::memcpy(key.data(), blob.data(), bytes);
+    void *host = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        auto it = g_cache.find(key);
+        if (it != g_cache.end()) {
+            host = it->second.host;
+        } else {
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            cudaStreamIsCapturing(st, &cs);
+            if (g_cache.size() >= 64 && cs == cudaStreamCaptureStatusNone) {
+                // bounded: wait for every pending copy, then drop the blobs
+                cudaDeviceSynchronize();
+                for (auto &kv : g_cache) cudaFreeHost(kv.second.host);
+                g_cache.clear();
+            }
+            cudaError_t e = cudaMallocHost(&host, bytes);
+            if (e != cudaSuccess) return e;
+            std::memcpy(host, blob.data(), bytes);
+            g_cache[key] = PinnedBlob{host, bytes};
+        }
+    }
+    return cudaMemcpyAsync(work, host, bytes, cudaMemcpyHostToDevice, st);
+}
+
+int run_plan(const Plan &p, const bdc_opts &o, char *work, std::vector<MatDesc> &mats, int *d_info_out,
+             cudaStream_t st) {
+    // per-matrix data pointers
+    for (int mi = 0; mi < p.nmat; ++mi) {
+        MatDesc c = carve(work, p.off_mat_data[mi], mats[mi].n);
+        c.d_in = mats[mi].d_in; c.e_in = mats[mi].e_in;
+        c.Uo = mats[mi].Uo; c.So = mats[mi].So; c.VTo = mats[mi].VTo;
+        c.ldu = mats[mi].ldu; c.ldvt = mats[mi].ldvt;
+        mats[mi] = c;
+    }
+    cudaError_t e = upload(p, work, mats, st);
+    if (e != cudaSuccess) return BDC_ERR_CUDA;
+    const MatDesc *dmats = (const MatDesc *)(work + p.off_mats);
+    const NodeDesc *dleaves = (const NodeDesc *)(work + p.off_leaves);
+    NodeState *dstate = (NodeState *)(work + p.off_state);
+    GemmProb *dprobs = (GemmProb *)(work + p.off_probs);
+    const int max_iter = o.max_iter > 0 ? o.max_iter : kDefaultMaxIter;
+
+    if (p.nmat > 0) {
+        k_scale<<<p.nmat, 256, 0, st>>>(dmats);
+        if ((e = cudaGetLastError()) != cudaSuccess) return BDC_ERR_CUDA;
+    }
+    if ((e = launch_leaves(dleaves, (int)p.leaves.size(), dmats, p.leafmax, 30, st)) != cudaSuccess)
+        return BDC_ERR_CUDA;
+    for (size_t h = 0; h < p.heights.size(); ++h) {
+        const int nn = (int)p.heights[h].size();
+        const int mm = p.hmmax[h];
+        const NodeDesc *dn = (const NodeDesc *)(work + p.off_nodes + p.off_height_nodes[h]);
+        if ((e = launch_merge_prep(dn, nn, dmats, dstate, dprobs, mm, st)) != cudaSuccess) return BDC_ERR_CUDA;
+        if ((e = launch_merge_gather(dn, nn, dmats, dstate, mm, st)) != cudaSuccess) return BDC_ERR_CUDA;
+        if ((e = launch_secular(dn, nn, dmats, dstate, mm, max_iter, o.seed, o.mlp, st)) != cudaSuccess)
+            return BDC_ERR_CUDA;
+        if ((e = launch_vectors(dn, nn, dmats, dstate, mm, st)) != cudaSuccess) return BDC_ERR_CUDA;
+        if (o.prec == BDC_FP64) {
+            e = launch_gemm64(dprobs, 4 * nn, mm + 1, mm, st);
+        } else {
+            e = launch_gemm_mixed(dprobs, 4 * nn, mm + 1, mm, mm + 16, o.prec,
+                                  o.slices > 0 ? o.slices : 6, work + p.off_mixed, p.mixed_bytes, st);
+        }
+        if (e != cudaSuccess) return BDC_ERR_CUDA;
+        if ((e = launch_merge_finish(dn, nn, dmats, dstate, mm, st)) != cudaSuccess) return BDC_ERR_CUDA;
+    }
+    if (p.nmat > 0) {
+        const int tps = (p.nmax + 31) / 32;
+        for (int m0 = 0; m0 < p.nmat; m0 += 65535) {
+            const int nm = std::min(65535, p.nmat - m0);
+            dim3 grid((unsigned)tps * tps, 1, nm);
+            k_final<<<grid, 256, 0, st>>>(dmats + m0, tps);
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) return BDC_ERR_CUDA;
+    }
+    // gather the per-matrix status words into the caller's d_info
+    for (int mi = 0; mi < p.nmat; ++mi) {
+        e = cudaMemcpyAsync(d_info_out + mi, mats[mi].info, sizeof(int), cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return BDC_ERR_CUDA;
+    }
+    return 0;
+}
+
+int check_args(int n, const double *d, const double *e, double *U, double *S, double *VT, int ldu,
+               int ldvt) {
+    if (n < 0) return -1;
+    if (n > 0 && !d) return -2;
+    if (n > 1 && !e) return -3;
+    if (n > 0 && !U) return -4;
+    if (n > 0 && !S) return -5;
+    if (n > 0 && !VT) return -6;
+    if (ldu < std::max(1, n)) return -7;
+    if (ldvt < std::max(1, n)) return -8;
+    return 0;
+}
+
+bdc_opts resolve(const bdc_opts *o) {
+    bdc_opts r;
+    bdc_opts_default(&r);
+    if (o) r = *o;
+    if (r.leaf <= 0) r.leaf = kDefaultLeaf;
+    if (r.max_iter <= 0) r.max_iter = kDefaultMaxIter;
+    if (r.slices <= 0) r.slices = 6;
+    return r;
+}
+
+int check_opts(const bdc_opts &o) {
+    if (o.prec < 0 || o.prec > 2) return 1;
+    if (o.seed < 0 || o.seed > 1) return 1;
+    if (o.seed == BDC_SEED_MLP && !o.mlp) return 1;
+    if (o.leaf < 4 || o.leaf > 64) return 1;
+    if (o.slices < 2 || o.slices > 7) return 1;
+    if (o.checked != 0) return 1;
+    return 0;
+}
+
+}  // namespace
+}  // namespace bdc
+
+using namespace bdc;
+
+extern "C" {
+
+void bdc_opts_default(bdc_opts *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->prec = BDC_FP64;
+    o->seed = BDC_SEED_PLAIN;
+    o->leaf = kDefaultLeaf;
+    o->max_iter = kDefaultMaxIter;
+    o->slices = 6;
+}
+
+size_t bdc_svd_workspace(int n, const bdc_opts *o) {
+    if (n < 0) return 0;
+    const bdc_opts r = resolve(o);
+    const int nn = n;
+    return make_plan(1, &nn, r).total;
+}
+
+int bdc_svd_ex(int n, const double *d, const double *e, double *U, double *S, double *VT, int ldu, int ldvt,
+               const bdc_opts *o, void *work, size_t lwork, int *d_info, bdc_stream_t stream) {
+    int a = check_args(n, d, e, U, S, VT, ldu, ldvt);
+    if (a) return a;
+    const bdc_opts r = resolve(o);
+    if (check_opts(r)) return -9;
+    if (!d_info) return -12;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n == 0) return cudaMemsetAsync(d_info, 0, sizeof(int), st) == cudaSuccess ? 0 : BDC_ERR_CUDA;
+    const Plan p = make_plan(1, &n, r);
+    if (!work) return -10;
+    if (lwork < p.total) return -11;
+    char *w = (char *)(((uintptr_t)work + 255) & ~(uintptr_t)255);
+    if ((size_t)(w - (char *)work) + p.total - 256 > lwork) return -11;
+    std::vector<MatDesc> mats(1);
+    mats[0].n = n; mats[0].d_in = d; mats[0].e_in = e;
+    mats[0].Uo = U; mats[0].So = S; mats[0].VTo = VT; mats[0].ldu = ldu; mats[0].ldvt = ldvt;
+    return run_plan(p, r, w, mats, d_info, st);
+}
+
+int bdc_svd(int n, const double *d, const double *e, double *U, double *S, double *VT, int ldu, int ldvt,
+            bdc_stream_t stream) {
+    int a = check_args(n, d, e, U, S, VT, ldu, ldvt);
+    if (a) return a;
+    if (n == 0) return 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    bdc_opts o;
+    bdc_opts_default(&o);
+    const size_t lw = bdc_svd_workspace(n, &o) + sizeof(int) + 256;
+    void *work = nullptr;
+    if (cudaMallocAsync(&work, lw, st) != cudaSuccess) return BDC_ERR_CUDA;
+    int *dinfo = (int *)((char *)work + lw - sizeof(int) - 64);
+    dinfo = (int *)(((uintptr_t)dinfo) & ~(uintptr_t)15);
+    int rc = bdc_svd_ex(n, d, e, U, S, VT, ldu, ldvt, &o, work, (size_t)((char *)dinfo - (char *)work), dinfo,
+                        stream);
+    int hinfo = 0;
+    if (rc == 0) {
+        if (cudaMemcpyAsync(&hinfo, dinfo, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = BDC_ERR_CUDA;
+    }
+    cudaFreeAsync(work, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return BDC_ERR_CUDA;
+    return rc != 0 ? rc : hinfo;
+}
+
+size_t bdc_svd_batched_workspace(int batch, const int *h_n, const bdc_opts *o) {
+    if (batch <= 0 || !h_n) return 0;
+    for (int b = 0; b < batch; ++b) if (h_n[b] < 1 || h_n[b] > 2048) return 0;
+    return make_plan(batch, h_n, resolve(o)).total;
+}
+
+int bdc_svd_batched(int batch, const int *h_n, const double *const *d, const double *const *e, double *const *U,
+                    double *const *S, double *const *VT, const int *h_ldu, const int *h_ldvt, const bdc_opts *o,
+                    void *work, size_t lwork, int *d_info, bdc_stream_t stream) {
+    if (batch < 0) return -1;
+    if (batch == 0) return 0;
+    if (!h_n) return -2;
+    if (!d) return -3;
+    if (!e) return -4;
+    if (!U) return -5;
+    if (!S) return -6;
+    if (!VT) return -7;
+    if (!h_ldu) return -8;
+    if (!h_ldvt) return -9;
+    for (int b = 0; b < batch; ++b) {
+        if (h_n[b] < 1 || h_n[b] > 2048) return -2;
+        if (!d[b] || (h_n[b] > 1 && !e[b]) || !U[b] || !S[b] || !VT[b]) return -3;
+        if (h_ldu[b] < h_n[b] || h_ldvt[b] < h_n[b]) return -8;
+    }
+    const bdc_opts r = resolve(o);
+    if (check_opts(r)) return -10;
+    if (!d_info) return -13;
+    const Plan p = make_plan(batch, h_n, r);
+    if (!work) return -11;
+    if (lwork < p.total) return -12;
+    char *w = (char *)(((uintptr_t)work + 255) & ~(uintptr_t)255);
+    if ((size_t)(w - (char *)work) + p.total - 256 > lwork) return -12;
+    std::vector<MatDesc> mats(batch);
+    for (int b = 0; b < batch; ++b) {
+        mats[b].n = h_n[b]; mats[b].d_in = d[b]; mats[b].e_in = e[b];
+        mats[b].Uo = U[b]; mats[b].So = S[b]; mats[b].VTo = VT[b];
+        mats[b].ldu = h_ldu[b]; mats[b].ldvt = h_ldvt[b];
+    }
+    return run_plan(p, r, w, mats, d_info, (cudaStream_t)stream);
+}
+
+int bdc_secular_solve(int N, const double *d, const double *z, int *org, double *tau, double *omega,
+                      int max_iter, int *d_info, bdc_stream_t stream) {
+    if (N < 0) return -1;
+    if (N > 0 && (!d || !z || !org || !tau || !omega)) return -2;
+    if (!d_info) return -8;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(d_info, 0, sizeof(int), st) != cudaSuccess) return BDC_ERR_CUDA;
+    return launch_secular_single(N, d, z, org, tau, omega, max_iter > 0 ? max_iter : kDefaultMaxIter, d_info,
+                                 st) == cudaSuccess ? 0 : BDC_ERR_CUDA;
+}
+
+int bdc_lowner_z(int N, const double *d, const double *z, const int *org, const double *tau, double *zt,
+                 bdc_stream_t stream) {
+    if (N < 0) return -1;
+    if (N > 0 && (!d || !z || !org || !tau || !zt)) return -2;
+    return launch_lowner_single(N, d, z, org, tau, zt, (cudaStream_t)stream) == cudaSuccess ? 0 : BDC_ERR_CUDA;
+}
+
+int bdc_m_vectors(int N, const double *d, const double *zt, const int *org, const double *tau, double *UM,
+                  int ldum, double *VM, int ldvm, bdc_stream_t stream) {
+    if (N < 0) return -1;
+    if (N > 0 && (!d || !zt || !org || !tau || !UM || !VM)) return -2;
+    if (ldum < std::max(1, N)) return -7;
+    if (ldvm < std::max(1, N)) return -9;
+    return launch_mvectors_single(N, d, zt, org, tau, UM, ldum, VM, ldvm, (cudaStream_t)stream) == cudaSuccess
+               ? 0 : BDC_ERR_CUDA;
+}
+
+int bdc_deflate(int m, const double *d, const double *z, double tol, int *keep, double *zout, double *dval,
+                bdc_stream_t stream) {
+    if (m < 0) return -1;
+    if (m > 0 && (!d || !z || !keep || !zout || !dval)) return -2;
+    if (!(tol >= 0.0)) return -4;
+    return launch_deflate_single(m, d, z, tol, keep, zout, dval, (cudaStream_t)stream) == cudaSuccess
+               ? 0 : BDC_ERR_CUDA;
+}
+
+size_t bdc_gemm_workspace(int M, int N, int K, int prec, int slices) {
+    if (M < 0 || N < 0 || K < 0) return 0;
+    size_t b = align256(sizeof(GemmProb)) + 256;
+    if (prec != BDC_FP64) b += gemm_mixed_scratch(M, N, K, prec, slices > 0 ? slices : 6);
+    return b;
+}
+
+int bdc_gemm(int M, int N, int K, const double *A, int lda, const double *B, int ldb, double *C, int ldc,
+             int prec, int slices, void *work, size_t lwork, bdc_stream_t stream) {
+    if (M < 0) return -1;
+    if (N < 0) return -2;
+    if (K < 0) return -3;
+    if (M == 0 || N == 0) return 0;
+    if (!A && K > 0) return -4;
+    if (lda < std::max(1, M)) return -5;
+    if (!B && K > 0) return -6;
+    if (ldb < std::max(1, K)) return -7;
+    if (!C) return -8;
+    if (ldc < std::max(1, M)) return -9;
+    if (prec < 0 || prec > 2) return -10;
+    if (slices == 0) slices = 6;
+    if (slices < 2 || slices > 7) return -11;
+    const size_t need = bdc_gemm_workspace(M, N, K, prec, slices);
+    if (!work) return -12;
+    if (lwork < need) return -13;
+    cudaStream_t st = (cudaStream_t)stream;
+    char *w = (char *)(((uintptr_t)work + 255) & ~(uintptr_t)255);
+    GemmProb pr{A, B, C, lda, ldb, ldc, M, N, K};
+    // the problem descriptor lives in the workspace; copied from a pinned slot
+    static std::mutex mu;
+    static GemmProb *hp = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!hp && cudaMallocHost(&hp, sizeof(GemmProb) * 1024) != cudaSuccess) return BDC_ERR_CUDA;
+    }
+    // a fresh pinned slot per call (ring of 1024), synchronised on wrap-around
+    static int slot = 0;
+    GemmProb *hs;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (slot == 1024) { cudaStreamSynchronize(st); slot = 0; }
+        hs = hp + slot++;
+    }
+    *hs = pr;
+    if (cudaMemcpyAsync(w, hs, sizeof(GemmProb), cudaMemcpyHostToDevice, st) != cudaSuccess) return BDC_ERR_CUDA;
+    cudaError_t e;
+    if (K == 0) {
+        e = cudaMemset2DAsync(C, sizeof(double) * ldc, 0, sizeof(double) * M, N, st);
+    } else if (prec == BDC_FP64) {
+        e = launch_gemm64((const GemmProb *)w, 1, M, N, st);
+    } else {
+        e = launch_gemm_mixed((const GemmProb *)w, 1, M, N, K, prec, slices, w + align256(sizeof(GemmProb)),
+                              lwork - (size_t)(w - (char *)work) - align256(sizeof(GemmProb)), st);
+    }
+    return e == cudaSuccess ? 0 : BDC_ERR_CUDA;
+}
+
+int bdc_mlp_param_count(void) { return 0; }
+int bdc_mlp_feature_count(void) { return 0; }
+
+const char *bdc_status_string(int code) {
+    if (code == 0) return "success";
+    if (code > 0) return "leaf QR iterations or secular roots did not converge";
+    switch (code) {
+        case BDC_ERR_CUDA: return "CUDA launch or allocation failure";
+        case BDC_ERR_TIMEOUT: return "a bounded device wait gave up";
+        case BDC_ERR_NONFINITE: return "d or e holds NaN or Inf";
+        case BDC_ERR_INTERNAL: return "internal error";
+        default: return "illegal argument";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,118 @@
+// FP64 merge products of Eq. (bdc-Mv2Bv-u-vt): C = A * B, all column-major,
+// a batch of independent problems per launch (four per merge node: the top
+// and bottom blocks of W~ U_M and Q~ V_M).
+//
+// Tensor-core FP64 (DMMA, mma.sync.m8n8k4.f64).  CTA tile 64 x 64, K step 16,
+// four warps of 32 x 32 (4 x 4 fragments of 8 x 8).  Shared tiles are padded
+// so that the fragment loads of a warp hit every bank exactly twice (the
+// minimum for 32 doubles).  The next K step is prefetched into registers while
+// the current one is multiplied.  Problems whose actual size (known only on
+// the device after deflation) is smaller than the launch grid exit early.
+#include "bdc_internal.cuh"
+
+namespace bdc {
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16;
+constexpr int SA = BM + 8;   // As[k][m] row stride (doubles)
+constexpr int SB = BK + 4;   // Bs[n][k] row stride
+
+__device__ __forceinline__ void dmma(double (&c)[2], double a, double b) {
+    asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
+                 : "+d"(c[0]), "+d"(c[1])
+                 : "d"(a), "d"(b));
+}
+
+__global__ void __launch_bounds__(128) k_gemm64(const GemmProb *__restrict__ probs, int tilesN) {
+    __shared__ double As[BK * SA];
+    __shared__ double Bs[BN * SB];
+    const GemmProb pr = probs[blockIdx.y];
+    const int m0 = (blockIdx.x / tilesN) * BM, n0 = (blockIdx.x % tilesN) * BN;
+    if (m0 >= pr.M || n0 >= pr.N) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    const int g = lane >> 2, tg = lane & 3;
+    const double *__restrict__ A = pr.A;
+    const double *__restrict__ B = pr.B;
+    const int M = pr.M, N = pr.N, K = pr.K, lda = pr.lda, ldb = pr.ldb;
+
+    double acc[4][4][2];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j][0] = acc[i][j][1] = 0.0;
+
+    // global -> register staging: A tile (64 m x 16 k), B tile (16 k x 64 n)
+    double ra[8], rb[8];
+    auto load = [&](int k0) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int idx = tid + r * 128;       // 0..1023
+            const int am = idx & 63, ak = idx >> 6;
+            const int gm = m0 + am, gk = k0 + ak;
+            ra[r] = (gm < M && gk < K) ? A[(size_t)gk * lda + gm] : 0.0;
+            const int bk = idx & 15, bn = idx >> 4;
+            const int gn = n0 + bn, gk2 = k0 + bk;
+            rb[r] = (gn < N && gk2 < K) ? B[(size_t)gn * ldb + gk2] : 0.0;
+        }
+    };
+    auto store = [&]() {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int idx = tid + r * 128;
+            As[(idx >> 6) * SA + (idx & 63)] = ra[r];
+            Bs[(idx >> 4) * SB + (idx & 15)] = rb[r];
+        }
+    };
+    load(0);
+    for (int k0 = 0; k0 < K; k0 += BK) {
+        __syncthreads();
+        store();
+        __syncthreads();
+        if (k0 + BK < K) load(k0 + BK);
+#pragma unroll
+        for (int kk = 0; kk < BK; kk += 4) {
+            double af[4], bf[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) af[i] = As[(kk + tg) * SA + wm + i * 8 + g];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bf[j] = Bs[(wn + j * 8 + g) * SB + kk + tg];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) dmma(acc[i][j], af[i], bf[j]);
+        }
+    }
+    // fragment (g, 2 tg + {0,1}) of each 8 x 8 tile
+    double *__restrict__ C = pr.C;
+    const int ldc = pr.ldc;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int gm = m0 + wm + i * 8 + g;
+        if (gm >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int gn = n0 + wn + j * 8 + 2 * tg;
+            if (gn < N) C[(size_t)gn * ldc + gm] = acc[i][j][0];
+            if (gn + 1 < N) C[(size_t)(gn + 1) * ldc + gm] = acc[i][j][1];
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_gemm64(const GemmProb *probs, int nprobs, int mmax_rows, int nmax_cols, cudaStream_t st) {
+    if (nprobs <= 0 || mmax_rows <= 0 || nmax_cols <= 0) return cudaSuccess;
+    const int tilesN = (nmax_cols + BN - 1) / BN, tilesM = (mmax_rows + BM - 1) / BM;
+    for (int p0 = 0; p0 < nprobs; p0 += 65535) {
+        const int np = (nprobs - p0 < 65535) ? nprobs - p0 : 65535;
+        dim3 grid((unsigned)tilesN * tilesM, np);
+        k_gemm64<<<grid, 128, 0, st>>>(probs + p0, tilesN);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace bdc

@@ -1,0 +1,147 @@
+// Internal data layout and helpers of the GB300 bidiagonal divide-and-conquer.
+//
+// Layout in HBM (one "matrix" = one bidiagonal problem of order n):
+//   U, V      n x n column-major (ld = n).  Every node of the split tree owns
+//             the diagonal block starting at (r0, r0): m x m in U and
+//             (m+sqre) x (m+sqre) in V (Sec. 4.2.1: B_1 is (k-1) x k, the
+//             coupling row k, B_2 below).  Leaves write their SVD there,
+//             merges overwrite the parent block in place.
+//   D, Q      n entries: D[r0+j] = value of node column j, Q[r0+p] = local
+//             column of the p-th smallest value (node-local ascending order).
+//   merge scratch (indexed from r0 or from the node's kbase) and four big
+//   per-level matrices W~, Q~ (gathered/rotated vectors) and U_M, V_M (the
+//   vectors of M~), node block at r0 * wstride, wstride = n + 16.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/bdc.h"
+
+namespace bdc {
+
+constexpr double kEps = 2.220446049250313e-16;  // 2^-52
+
+struct MatDesc {
+    int n;
+    int ldu, ldvt;           // user output leading dimensions
+    long long wstride;       // n + 16
+    const double *d_in, *e_in;
+    double *Uo, *So, *VTo;   // user outputs
+    double *dsc, *esc;       // scaled copies (esc[n-1] = 0)
+    double *scale;           // [1] scale factor applied to d, e
+    double *U, *V, *D;       // node blocks
+    int *Q;                  // node-local ascending order
+    // merge scratch, per node from r0 (size n) unless noted
+    double *ds, *zs;         // sorted d, z
+    int *src;                // sorted position -> encoded source column
+    double *rc, *rs;         // rotation linking a sorted position to its chain predecessor
+    int *role;               // sorted position -> role (see bdc_merge.cu)
+    double *dM, *zM, *zt, *tau, *omega;   // survivors in M order
+    int *org, *kposM;        // root origin, K position of each survivor
+    int *invK;               // from kbase: K position -> M index (-1 = padding)
+    double *dval;            // deflated values, output order
+    int *dsrc;               // deflated output slot -> sorted position
+    int *dest;               // sorted position -> K position (>= 0) or -(1 + deflated slot)
+    int *slist;              // survivors of the small-z test, sorted positions (from r0)
+    int *sidx;               // sorted position -> index in slist (-1 = small z)
+    double *Wt, *Qt, *UM, *VM;   // big per-level matrices (node base r0 * wstride)
+    int *info;               // [1] status: >0 non-convergence count, <0 error code
+    float *feat;             // optional MLP harvest buffer (nullptr = off)
+};
+
+struct NodeDesc {
+    int mat;     // index into the MatDesc array
+    int id;      // global node id (NodeState index)
+    int r0;      // first row of the node block
+    int m;       // rows
+    int sqre;    // 1 if the node has m+1 columns
+    int nl;      // rows of the left child (coupling row = r0 + nl)
+    int kbase;   // base of K-indexed scratch (invK)
+    int pad;
+};
+
+struct NodeState {
+    int N;       // surviving (non-deflated) entries, including index 0
+    int n1, n2, n3;   // survivors of type top-only / dense / bottom-only
+    int P1;      // n1 rounded up to a multiple of 8 (K position of index 0)
+    int Ktot;    // P1 + 1 + n2 + n3
+    int ndef;    // m - N
+    int nzero;   // deflated by rotation against d_0 = 0
+    double tol;
+    double cq, sq;   // rotation folding the two null-vector components (sqre)
+};
+
+// one FP64 product C = A * B (column-major), used by the merge GEMMs
+struct GemmProb {
+    const double *A; const double *B; double *C;
+    int lda, ldb, ldc;
+    int M, N, K;
+};
+
+// role codes for sorted positions (merge)
+enum : int {
+    ROLE_NONE = 0,
+    ROLE_KEEP = 1,        // survivor
+    ROLE_DEFL = 2,        // deflated by small z
+    ROLE_CHAIN = 3,       // deflated member of a close-value chain (not last)
+    ROLE_ZERO = 4         // deflated by rotation against d_0 = 0
+};
+
+// ---------------------------------------------------------------- helpers
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ int warp_isum(int v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// plane rotation with c f + s g = r, -s f + c g = 0
+__device__ __forceinline__ void make_rot(double f, double g, double &c, double &s, double &r) {
+    if (g == 0.0) { c = 1.0; s = 0.0; r = f; return; }
+    if (f == 0.0) { c = 0.0; s = 1.0; r = g; return; }
+    double h = hypot(f, g);
+    c = f / h; s = g / h; r = h;
+}
+
+__device__ __forceinline__ void set_error(int *info, int code) {
+    atomicCAS(info, 0, code);
+}
+
+// ------------------------------------------------------ host-side launchers
+// (each returns cudaGetLastError() of its launches)
+cudaError_t launch_scale(const MatDesc *mats, int nmat, int nmax, cudaStream_t st);
+cudaError_t launch_leaves(const NodeDesc *leaves, int nleaves, const MatDesc *mats, int leafmax,
+                          int max_sweeps, cudaStream_t st);
+cudaError_t launch_merge_prep(const NodeDesc *nodes, int nnodes, const MatDesc *mats,
+                              NodeState *state, GemmProb *probs, int mmax, cudaStream_t st);
+cudaError_t launch_merge_gather(const NodeDesc *nodes, int nnodes, const MatDesc *mats,
+                                const NodeState *state, int mmax, cudaStream_t st);
+cudaError_t launch_secular(const NodeDesc *nodes, int nnodes, const MatDesc *mats,
+                           const NodeState *state, int mmax, int max_iter, int seed_mode,
+                           const float *mlp, cudaStream_t st);
+cudaError_t launch_vectors(const NodeDesc *nodes, int nnodes, const MatDesc *mats,
+                           const NodeState *state, int mmax, cudaStream_t st);
+cudaError_t launch_gemm64(const GemmProb *probs, int nprobs, int mmax_rows, int nmax_cols,
+                          cudaStream_t st);
+cudaError_t launch_merge_finish(const NodeDesc *nodes, int nnodes, const MatDesc *mats,
+                                const NodeState *state, int mmax, cudaStream_t st);
+cudaError_t launch_final(const MatDesc *mats, int nmat, int nmax, cudaStream_t st);
+
+// standalone step kernels (step entry points)
+cudaError_t launch_secular_single(int N, const double *d, const double *z, int *org, double *tau,
+                                  double *omega, int max_iter, int *info, cudaStream_t st);
+cudaError_t launch_lowner_single(int N, const double *d, const double *z, const int *org,
+                                 const double *tau, double *zt, cudaStream_t st);
+cudaError_t launch_mvectors_single(int N, const double *d, const double *zt, const int *org,
+                                   const double *tau, double *UM, int ldum, double *VM, int ldvm,
+                                   cudaStream_t st);
+cudaError_t launch_deflate_single(int m, const double *d, const double *z, double tol, int *keep,
+                                  double *zout, double *dval, cudaStream_t st);
+
+}  // namespace bdc

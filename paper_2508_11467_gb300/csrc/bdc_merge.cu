@@ -1,0 +1,521 @@
+// Merge step of Algorithm 2, part (a) "deflate singular values" (lasd2) and
+// the bookkeeping around part (b), all on the GPU.
+//
+// k_merge_prep   (one CTA per node)  z formation (Sec. 4.2.1: the coupling
+//                row times the children's right vectors), merge of the two
+//                sorted child value lists, deflation tests (Eq. M-condition)
+//                and the rotation chains of the four deflation cases, column
+//                typing (top / dense / bottom, the blocks of Eq. bdc-W-Q) and
+//                the K order [top | pad | d_0 column | dense | bottom] used by
+//                the merge products of Eq. (bdc-Mv2Bv-u-vt).
+// k_merge_gather (one CTA per column task) applies the rotations and writes
+//                the permuted vectors W~ (left) and Q~ (right) into the
+//                workspace: survivors at their K position, deflated vectors
+//                after them, the new right null vector last.
+// k_merge_finish copies deflated vectors into the node block after the
+//                merged ones (Eq. bdc-B-svd), writes the node's values and
+//                their ascending order.
+//
+// The sequential deflation scan is parallelised exactly: the small-z test
+// uses the original z, so survivors of it are found with a block scan; the
+// close-value test only compares consecutive survivors, so chains of close
+// values are independent and each is walked by one thread.
+#include "bdc_internal.cuh"
+
+namespace bdc {
+
+namespace {
+
+constexpr int PREP_THREADS = 512;
+constexpr int FL_START = 16, FL_MEMBER = 32;
+
+__device__ __forceinline__ int block_excl_scan(int v, int *wsum, int &total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int t = (lane < nw) ? wsum[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < nw) wsum[lane] = t;
+    }
+    __syncthreads();
+    const int base = (w > 0) ? wsum[w - 1] : 0;
+    total = wsum[nw - 1];
+    __syncthreads();
+    return base + x - v;
+}
+
+__device__ __forceinline__ double block_max(double v, double *dsum) {
+    v = warp_max(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) dsum[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    for (int i = 0; i < nw; ++i) r = fmax(r, dsum[i]);
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ int block_isum(int v, int *wsum) {
+    int t;
+    block_excl_scan(v, wsum, t);
+    return t;
+}
+
+// side of a pre-deflation column: 1 = rows of the left child, 2 = right
+__device__ __forceinline__ int col_side(int c, int nl) { return c == 0 ? 0 : (c <= nl ? 1 : 2); }
+
+// Deflation of the sorted (ds, zs), ds[0] = 0, tolerance tol (Sec. 4.2.1):
+// fills slist/sidx/role, rotation (rc, rs) attached to the later member of
+// each rotated pair, and the final z of every survivor in place in zs.
+// src (may be null) gives the pre-deflation column of each position, used to
+// type survivors.  Returns the number ns of small-z survivors.
+__device__ int deflate_core(int m, double tol, const double *ds, double *zs, const int *src, int nl,
+                            int *slist, int *sidx, int *role, double *rc, double *rs, int *wsum,
+                            int *a_out) {
+    const int T = blockDim.x, t = threadIdx.x;
+    const int seg = (m + T - 1) / T;
+    const int b = min(m, t * seg), e = min(m, b + seg);
+    // z_0 (paired with d_0 = 0) is clamped up to tol, never deflated
+    if (t == 0) {
+        double z0 = zs[0];
+        if (fabs(z0) < tol) zs[0] = (z0 < 0.0) ? -tol : tol;
+    }
+    __syncthreads();
+    int cnt = 0;
+    for (int p = b; p < e; ++p) cnt += (p == 0 || fabs(zs[p]) > tol);
+    int ns;
+    int k = block_excl_scan(cnt, wsum, ns);
+    for (int p = b; p < e; ++p) {
+        if (p == 0 || fabs(zs[p]) > tol) {
+            slist[k] = p; sidx[p] = k; ++k;
+        } else {
+            sidx[p] = -1;
+            role[p] = ROLE_DEFL;
+        }
+    }
+    __syncthreads();
+    // survivors close to d_0 = 0 form a prefix of slist (ds ascending)
+    const int sseg = (ns + T - 1) / T;
+    const int sb = min(ns, t * sseg), se = min(ns, sb + sseg);
+    int za = 0;
+    for (int kk = max(sb, 1); kk < se; ++kk) za += (ds[slist[kk]] <= tol);
+    const int a = block_isum(za, wsum);
+    for (int kk = sb; kk < se; ++kk) {
+        const int p = slist[kk];
+        int r;
+        if (kk == 0) {
+            r = ROLE_KEEP;
+        } else if (kk <= a) {
+            r = ROLE_ZERO;
+        } else {
+            const bool closeK = (kk >= a + 2) && (ds[p] - ds[slist[kk - 1]] <= tol);
+            const bool nextClose = (kk + 1 < ns) && (kk + 1 >= a + 2) && (ds[slist[kk + 1]] - ds[p] <= tol);
+            if (nextClose) r = ROLE_CHAIN | FL_MEMBER | (closeK ? 0 : FL_START);
+            else r = ROLE_KEEP | (closeK ? FL_MEMBER : 0);
+            if (!nextClose && !closeK) r |= (src ? col_side(src[p], nl) : 1) << 8;
+        }
+        role[p] = r;
+    }
+    __syncthreads();
+    // walk each chain of close values: the earlier z is rotated into the later
+    for (int kk = sb; kk < se; ++kk) {
+        const int p = slist[kk];
+        if ((role[p] & 15) != ROLE_CHAIN || !(role[p] & FL_START)) continue;
+        double zr = zs[p];
+        int ty = src ? col_side(src[p], nl) : 1;
+        for (int j = kk + 1; j < ns; ++j) {
+            const int q = slist[j];
+            const double zq = zs[q];
+            double c, s, r;
+            make_rot(zq, zr, c, s, r);    // c = z_q / r, s = z_prev / r
+            rc[q] = c; rs[q] = s;
+            zr = r;
+            ty |= src ? col_side(src[q], nl) : 1;
+            if ((role[q] & 15) == ROLE_KEEP) {
+                zs[q] = zr;
+                role[q] |= ty << 8;
+                break;
+            }
+        }
+    }
+    // values close to d_0 = 0: right-side rotations fold them into z_0
+    if (t == 0 && a > 0) {
+        double zr = zs[0];
+        for (int j = 1; j <= a; ++j) {
+            const int q = slist[j];
+            const double zq = zs[q];
+            double c, s, r;
+            make_rot(zr, zq, c, s, r);    // c = z_0 / r, s = z_q / r
+            rc[q] = c; rs[q] = s;
+            zr = r;
+        }
+        zs[0] = zr;
+    }
+    __syncthreads();
+    *a_out = a;
+    return ns;
+}
+
+__global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__restrict__ nodes,
+                                                             const MatDesc *__restrict__ mats,
+                                                             NodeState *__restrict__ state,
+                                                             GemmProb *__restrict__ probs) {
+    __shared__ int wsum[PREP_THREADS / 32 + 1];
+    __shared__ double dsum[PREP_THREADS / 32 + 1];
+    const NodeDesc nd = nodes[blockIdx.x];
+    const MatDesc md = mats[nd.mat];
+    const int m = nd.m, nl = nd.nl, nr = m - nl - 1, sqre = nd.sqre, mc = m + sqre;
+    const int r0 = nd.r0, r0L = r0, r0R = r0 + nl + 1;
+    const long long ld = md.n;
+    const int T = blockDim.x, t = threadIdx.x;
+    double *ds = md.ds + r0, *zs = md.zs + r0;
+    int *src = md.src + r0;
+    const double alpha = md.dsc[r0 + nl], beta = md.esc[r0 + nl];
+
+    // ---- z and the merged ascending order (children are sorted through Q)
+    const int *QL = md.Q + r0L, *QR = md.Q + r0R;
+    const double *DL = md.D + r0L, *DR = md.D + r0R;
+    double dmax = 0.0;
+    for (int p = t; p < nl; p += T) {
+        const int j = QL[p];
+        const double v = DL[j];
+        int lo = 0, hi = nr;                 // # right values < v (ties: left first)
+        while (lo < hi) { int mid = (lo + hi) >> 1; if (DR[QR[mid]] < v) lo = mid + 1; else hi = mid; }
+        const int pos = 1 + p + lo;
+        ds[pos] = v;
+        zs[pos] = alpha * md.V[(size_t)(r0L + j) * ld + r0L + nl];
+        src[pos] = 1 + j;
+        dmax = fmax(dmax, fabs(v));
+    }
+    for (int q = t; q < nr; q += T) {
+        const int j = QR[q];
+        const double v = DR[j];
+        int lo = 0, hi = nl;                 // # left values <= v
+        while (lo < hi) { int mid = (lo + hi) >> 1; if (DL[QL[mid]] <= v) lo = mid + 1; else hi = mid; }
+        const int pos = 1 + q + lo;
+        ds[pos] = v;
+        zs[pos] = beta * md.V[(size_t)(r0R + j) * ld + r0R];
+        src[pos] = nl + 1 + j;
+        dmax = fmax(dmax, fabs(v));
+    }
+    __shared__ double s_cq, s_sq;
+    if (t == 0) {
+        // d_0 = 0 column: alpha * (last entry of q_1), folded with beta * (first
+        // entry of q_2) when the right child is rectangular
+        double z0 = alpha * md.V[(size_t)(r0L + nl) * ld + r0L + nl];
+        double cq = 1.0, sq = 0.0;
+        if (sqre) {
+            const double b0 = beta * md.V[(size_t)(r0R + nr) * ld + r0R];
+            double r;
+            make_rot(z0, b0, cq, sq, r);
+            z0 = r;
+        }
+        ds[0] = 0.0;
+        zs[0] = z0;
+        src[0] = 0;
+        s_cq = cq; s_sq = sq;
+    }
+    dmax = block_max(dmax, dsum);
+    const double tol = 8.0 * kEps * fmax(dmax, fmax(fabs(alpha), fabs(beta)));
+
+    // ---- deflation
+    int a;
+    const int ns = deflate_core(m, tol, ds, zs, src, nl, md.slist + r0, md.sidx + r0, md.role + r0,
+                                md.rc + r0, md.rs + r0, wsum, &a);
+    (void)ns;
+    const int *role = md.role + r0;
+
+    // ---- survivor numbering (M order = ascending), type groups, deflated slots
+    const int seg = (m + T - 1) / T;
+    const int b = min(m, t * seg), e = min(m, b + seg);
+    int ck = 0, c1 = 0, c2 = 0, c3 = 0, cz = 0, co = 0;
+    for (int p = b; p < e; ++p) {
+        const int r = role[p], code = r & 15;
+        if (code == ROLE_KEEP) {
+            ++ck;
+            if (p > 0) { const int ty = (r >> 8) & 3; c1 += (ty == 1); c3 += (ty == 2); c2 += (ty == 3); }
+        } else if (code == ROLE_ZERO) {
+            ++cz;
+        } else {
+            ++co;
+        }
+    }
+    int N, n1, n2, n3, nz, no;
+    int ik = block_excl_scan(ck, wsum, N);
+    int i1 = block_excl_scan(c1, wsum, n1);
+    int i2 = block_excl_scan(c2, wsum, n2);
+    int i3 = block_excl_scan(c3, wsum, n3);
+    int iz = block_excl_scan(cz, wsum, nz);
+    int io = block_excl_scan(co, wsum, no);
+    const int P1 = (n1 + 7) & ~7;
+    const int Ktot = P1 + 1 + n2 + n3;
+    double *dM = md.dM + r0, *zM = md.zM + r0, *dval = md.dval + r0;
+    int *kposM = md.kposM + r0, *invK = md.invK + nd.kbase, *dest = md.dest + r0, *dsrc = md.dsrc + r0;
+    for (int p = b; p < e; ++p) {
+        const int r = role[p], code = r & 15;
+        if (code == ROLE_KEEP) {
+            int kp;
+            if (p == 0) kp = P1;
+            else {
+                const int ty = (r >> 8) & 3;
+                kp = (ty == 1) ? i1++ : (ty == 3) ? (P1 + 1 + i2++) : (P1 + 1 + n2 + i3++);
+            }
+            dM[ik] = ds[p];
+            zM[ik] = zs[p];
+            kposM[ik] = kp;
+            invK[kp] = ik;
+            dest[p] = kp;
+            ++ik;
+        } else if (code == ROLE_ZERO) {
+            dval[iz] = 0.0;
+            dsrc[iz] = p;
+            dest[p] = -(1 + iz);
+            ++iz;
+        } else {
+            const int slot = nz + io++;
+            dval[slot] = ds[p];
+            dsrc[slot] = p;
+            dest[p] = -(1 + slot);
+        }
+    }
+    for (int kp = n1 + t; kp < P1; kp += T) invK[kp] = -1;
+    if (t == 0) {
+        NodeState s;
+        s.N = N; s.n1 = n1; s.n2 = n2; s.n3 = n3; s.P1 = P1; s.Ktot = Ktot;
+        s.ndef = m - N; s.nzero = nz; s.tol = tol; s.cq = s_cq; s.sq = s_sq;
+        state[nd.id] = s;
+        const long long wb = (long long)r0 * md.wstride;
+        const int Ktop = P1 + 1 + n2, Kbot = Ktot - P1;
+        GemmProb *pr = probs + 4 * (size_t)blockIdx.x;
+        // U: top rows 0..nl (incl. the coupling row), bottom rows nl+1..m-1
+        pr[0] = GemmProb{md.Wt + wb, md.UM + wb, md.U + (size_t)r0 * ld + r0, m, Ktot, (int)ld,
+                         nl + 1, N, Ktop};
+        pr[1] = GemmProb{md.Wt + wb + (nl + 1) + (size_t)P1 * m, md.UM + wb + P1,
+                         md.U + (size_t)r0 * ld + r0 + nl + 1, m, Ktot, (int)ld, m - nl - 1, N, Kbot};
+        // V: top rows 0..nl (left child's columns), bottom rows nl+1..mc-1
+        pr[2] = GemmProb{md.Qt + wb, md.VM + wb, md.V + (size_t)r0 * ld + r0, mc, Ktot, (int)ld,
+                         nl + 1, N, Ktop};
+        pr[3] = GemmProb{md.Qt + wb + (nl + 1) + (size_t)P1 * mc, md.VM + wb + P1,
+                         md.V + (size_t)r0 * ld + r0 + nl + 1, mc, Ktot, (int)ld, mc - nl - 1, N, Kbot};
+    }
+}
+
+// ------------------------------------------------------------------ gather
+struct ColSrc {
+    const double *U, *V;
+    long long ld;
+    int r0, nl, nr, sqre;
+    double cq, sq;
+    __device__ double u(int c, int r) const {       // r in [0, m)
+        if (c == 0) return (r == nl) ? 1.0 : 0.0;
+        if (c <= nl) return (r < nl) ? U[(size_t)(r0 + c - 1) * ld + r0 + r] : 0.0;
+        return (r > nl) ? U[(size_t)(r0 + nl + 1 + (c - nl - 1)) * ld + r0 + r] : 0.0;
+    }
+    __device__ double q1(int r) const { return (r <= nl) ? V[(size_t)(r0 + nl) * ld + r0 + r] : 0.0; }
+    __device__ double q2(int r) const {
+        return (sqre && r > nl) ? V[(size_t)(r0 + nl + 1 + nr) * ld + r0 + r] : 0.0;
+    }
+    __device__ double v(int c, int r) const {       // r in [0, m + sqre)
+        if (c == 0) return cq * q1(r) + sq * q2(r);
+        if (c <= nl) return (r <= nl) ? V[(size_t)(r0 + c - 1) * ld + r0 + r] : 0.0;
+        return (r > nl) ? V[(size_t)(r0 + nl + 1 + (c - nl - 1)) * ld + r0 + r] : 0.0;
+    }
+};
+
+__global__ void __launch_bounds__(128) k_merge_gather(const NodeDesc *__restrict__ nodes,
+                                                      const MatDesc *__restrict__ mats,
+                                                      const NodeState *__restrict__ state, int mmax) {
+    const int node = blockIdx.x / mmax, p = blockIdx.x % mmax;
+    const NodeDesc nd = nodes[node];
+    if (p >= nd.m) return;
+    const MatDesc md = mats[nd.mat];
+    const NodeState ns = state[nd.id];
+    const int m = nd.m, nl = nd.nl, sqre = nd.sqre, mc = m + sqre, r0 = nd.r0;
+    const int r = md.role[r0 + p], code = r & 15;
+    const int *src = md.src + r0, *dest = md.dest + r0, *slist = md.slist + r0;
+    const double *rc = md.rc + r0, *rs = md.rs + r0;
+    ColSrc cs{md.U, md.V, (long long)md.n, r0, nl, m - nl - 1, sqre, ns.cq, ns.sq};
+    const long long wb = (long long)r0 * md.wstride;
+    double *W = md.Wt + wb, *Qm = md.Qt + wb;
+    auto wcol = [&](int dst) { return dst >= 0 ? dst : ns.Ktot + (-dst - 1); };
+
+    if (p == 0) {
+        const int a = ns.nzero;
+        // padding columns of the K order (between the top block and index 0)
+        for (int kp = ns.n1; kp < ns.P1; ++kp) {
+            for (int row = threadIdx.x; row < m; row += blockDim.x) W[(size_t)kp * m + row] = 0.0;
+            for (int row = threadIdx.x; row < mc; row += blockDim.x) Qm[(size_t)kp * mc + row] = 0.0;
+        }
+        for (int row = threadIdx.x; row < m; row += blockDim.x) {
+            W[(size_t)ns.P1 * m + row] = cs.u(0, row);
+            for (int j = 1; j <= a; ++j) {
+                const int q = slist[j];
+                W[(size_t)wcol(dest[q]) * m + row] = cs.u(src[q], row);
+            }
+        }
+        for (int row = threadIdx.x; row < mc; row += blockDim.x) {
+            double y = cs.v(0, row);
+            for (int j = 1; j <= a; ++j) {
+                const int q = slist[j];
+                const double x = cs.v(src[q], row), c = rc[q], s = rs[q];
+                Qm[(size_t)wcol(dest[q]) * mc + row] = -s * y + c * x;
+                y = c * y + s * x;
+            }
+            Qm[(size_t)ns.P1 * mc + row] = y;
+            if (sqre) Qm[(size_t)(ns.Ktot + ns.ndef) * mc + row] = -ns.sq * cs.q1(row) + ns.cq * cs.q2(row);
+        }
+        return;
+    }
+    if (code == ROLE_ZERO) return;
+    if ((r & FL_MEMBER) && !(r & FL_START)) return;   // handled by its chain's first member
+    if (code == ROLE_CHAIN) {                          // chain start: walk to its end
+        const int k0 = md.sidx[r0 + p];
+        for (int row = threadIdx.x; row < m; row += blockDim.x) {
+            double y = cs.u(src[p], row);
+            int prev = p;
+            for (int k = k0 + 1; k < m; ++k) {
+                const int q = slist[k];
+                const double x = cs.u(src[q], row), c = rc[q], s = rs[q];
+                W[(size_t)wcol(dest[prev]) * m + row] = c * y - s * x;
+                y = s * y + c * x;
+                prev = q;
+                if ((md.role[r0 + q] & 15) == ROLE_KEEP) break;
+            }
+            W[(size_t)wcol(dest[prev]) * m + row] = y;
+        }
+        for (int row = threadIdx.x; row < mc; row += blockDim.x) {
+            double y = cs.v(src[p], row);
+            int prev = p;
+            for (int k = k0 + 1; k < m; ++k) {
+                const int q = slist[k];
+                const double x = cs.v(src[q], row), c = rc[q], s = rs[q];
+                Qm[(size_t)wcol(dest[prev]) * mc + row] = c * y - s * x;
+                y = s * y + c * x;
+                prev = q;
+                if ((md.role[r0 + q] & 15) == ROLE_KEEP) break;
+            }
+            Qm[(size_t)wcol(dest[prev]) * mc + row] = y;
+        }
+        return;
+    }
+    // singleton survivor or small-z deflation: plain copy
+    const int col = wcol(dest[p]);
+    const int c = src[p];
+    for (int row = threadIdx.x; row < m; row += blockDim.x) W[(size_t)col * m + row] = cs.u(c, row);
+    for (int row = threadIdx.x; row < mc; row += blockDim.x) Qm[(size_t)col * mc + row] = cs.v(c, row);
+}
+
+// ------------------------------------------------------------------ finish
+__global__ void __launch_bounds__(128) k_merge_finish(const NodeDesc *__restrict__ nodes,
+                                                      const MatDesc *__restrict__ mats,
+                                                      const NodeState *__restrict__ state, int mmax1) {
+    const int node = blockIdx.x / mmax1, c = blockIdx.x % mmax1;
+    const NodeDesc nd = nodes[node];
+    const int m = nd.m;
+    if (c > m) return;
+    const MatDesc md = mats[nd.mat];
+    const NodeState ns = state[nd.id];
+    const int sqre = nd.sqre, mc = m + sqre, r0 = nd.r0, N = ns.N, ndef = ns.ndef;
+    const long long ld = md.n, wb = (long long)r0 * md.wstride;
+    const double *W = md.Wt + wb, *Qm = md.Qt + wb;
+    if (c < ndef) {
+        const double *wsrc = W + (size_t)(ns.Ktot + c) * m;
+        const double *qsrc = Qm + (size_t)(ns.Ktot + c) * mc;
+        double *ud = md.U + (size_t)(r0 + N + c) * ld + r0;
+        double *vd = md.V + (size_t)(r0 + N + c) * ld + r0;
+        for (int row = threadIdx.x; row < m; row += blockDim.x) ud[row] = wsrc[row];
+        for (int row = threadIdx.x; row < mc; row += blockDim.x) vd[row] = qsrc[row];
+    } else if (c == ndef) {
+        if (sqre) {
+            const double *qsrc = Qm + (size_t)(ns.Ktot + ndef) * mc;
+            double *vd = md.V + (size_t)(r0 + m) * ld + r0;
+            for (int row = threadIdx.x; row < mc; row += blockDim.x) vd[row] = qsrc[row];
+        }
+    }
+    if (c == m) {
+        const double *om = md.omega + r0, *dv = md.dval + r0;
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+            const double w = om[i];
+            int lo = 0, hi = ndef;           // # deflated values < w
+            while (lo < hi) { int mid = (lo + hi) >> 1; if (dv[mid] < w) lo = mid + 1; else hi = mid; }
+            md.D[r0 + i] = w;
+            md.Q[r0 + i + lo] = i;
+        }
+        for (int s = threadIdx.x; s < ndef; s += blockDim.x) {
+            const double v = dv[s];
+            int lo = 0, hi = N;              // # roots <= v
+            while (lo < hi) { int mid = (lo + hi) >> 1; if (om[mid] <= v) lo = mid + 1; else hi = mid; }
+            md.D[r0 + N + s] = v;
+            md.Q[r0 + s + lo] = N + s;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(PREP_THREADS) k_deflate_single(int m, const double *d, const double *z,
+                                                                 double tol, int *keep, double *zout,
+                                                                 double *dval, int *scratch_i,
+                                                                 double *scratch_d) {
+    __shared__ int wsum[PREP_THREADS / 32 + 1];
+    double *zs = scratch_d, *rc = scratch_d + m, *rs = scratch_d + 2 * m;
+    int *slist = scratch_i, *sidx = scratch_i + m, *role = scratch_i + 2 * m;
+    for (int p = threadIdx.x; p < m; p += blockDim.x) zs[p] = z[p];
+    __syncthreads();
+    int a;
+    deflate_core(m, tol, d, zs, nullptr, 0, slist, sidx, role, rc, rs, wsum, &a);
+    for (int p = threadIdx.x; p < m; p += blockDim.x) {
+        const int code = role[p] & 15;
+        keep[p] = (code == ROLE_KEEP);
+        zout[p] = (code == ROLE_KEEP) ? zs[p] : 0.0;
+        dval[p] = (code == ROLE_ZERO) ? 0.0 : (code == ROLE_KEEP ? 0.0 : d[p]);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_merge_prep(const NodeDesc *nodes, int nnodes, const MatDesc *mats, NodeState *state,
+                              GemmProb *probs, int mmax, cudaStream_t st) {
+    (void)mmax;
+    if (nnodes <= 0) return cudaSuccess;
+    k_merge_prep<<<nnodes, PREP_THREADS, 0, st>>>(nodes, mats, state, probs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_merge_gather(const NodeDesc *nodes, int nnodes, const MatDesc *mats,
+                                const NodeState *state, int mmax, cudaStream_t st) {
+    if (nnodes <= 0) return cudaSuccess;
+    k_merge_gather<<<(unsigned)nnodes * mmax, 128, 0, st>>>(nodes, mats, state, mmax);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_merge_finish(const NodeDesc *nodes, int nnodes, const MatDesc *mats,
+                                const NodeState *state, int mmax, cudaStream_t st) {
+    if (nnodes <= 0) return cudaSuccess;
+    k_merge_finish<<<(unsigned)nnodes * (mmax + 1), 128, 0, st>>>(nodes, mats, state, mmax + 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_deflate_single(int m, const double *d, const double *z, double tol, int *keep,
+                                  double *zout, double *dval, cudaStream_t st) {
+    if (m <= 0) return cudaSuccess;
+    void *si = nullptr, *sd = nullptr;
+    cudaError_t e = cudaMallocAsync(&si, sizeof(int) * 3 * (size_t)m, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMallocAsync(&sd, sizeof(double) * 3 * (size_t)m, st);
+    if (e != cudaSuccess) { cudaFreeAsync(si, st); return e; }
+    k_deflate_single<<<1, PREP_THREADS, 0, st>>>(m, d, z, tol, keep, zout, dval, (int *)si, (double *)sd);
+    e = cudaGetLastError();
+    cudaFreeAsync(si, st);
+    cudaFreeAsync(sd, st);
+    return e;
+}
+
+}  // namespace bdc
