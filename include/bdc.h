@@ -68,7 +68,7 @@ typedef struct {
     int seed;          /* bdc_seed                                        */
     int leaf;          /* leaf size L (>= 4; 0 = default 32)              */
     int max_iter;      /* secular / QR iteration cap (0 = default 64)     */
-    int slices;        /* BDC_MIXED_EXACT slice count 4..7 (0 = 6)        */
+    int slices;        /* BDC_MIXED_EXACT slice count 4..7 (0 = automatic: 6 for n <= 8192, 7 above) */
     int checked;       /* reserved, must be 0                              */
     const float *mlp;  /* device pointer to MLP weights when seed = MLP    */
 } bdc_opts;
@@ -149,6 +149,25 @@ int bdc_gemm(int M, int N, int K, const double *A, int lda, const double *B, int
 int bdc_mlp_param_count(void);
 /* Number of input features per root. */
 int bdc_mlp_feature_count(void);
+
+/* ---------------- stage profiling (CUDA events, host side) ---------------
+ * bdc_profile_begin(1) makes every later call record a CUDA event pair
+ * around each stage launch on the call's stream; bdc_profile_end() waits
+ * for them and returns, per stage kind k (BDC_STAGE_*), the summed device
+ * milliseconds in ms[k], the launch count in launches[k] and the summed
+ * algorithmic work in work[k]: for the products the flops 2 M N K of every
+ * product at its deflated size (times the slice pairs of the split BF16
+ * paths), for the data-movement stages the bytes they must read and write.
+ * Arrays have BDC_NSTAGES
+ * entries (any may be NULL).  Not thread safe; not for graph capture. */
+enum { BDC_STAGE_SCALE = 0, BDC_STAGE_LEAF, BDC_STAGE_PREP, BDC_STAGE_GATHER, BDC_STAGE_SECULAR,
+       BDC_STAGE_VECTORS, BDC_STAGE_GEMM, BDC_STAGE_FINISH, BDC_STAGE_FINAL, BDC_NSTAGES };
+int bdc_profile_begin(int on);
+int bdc_profile_end(double *ms, long long *launches, double *work);
+
+/* Text of the last CUDA error the library saw on this thread ("" if none);
+ * reading it clears it. */
+const char *bdc_last_error_string(void);
 
 /* Human-readable text for a status code (static string). */
 const char *bdc_status_string(int code);

@@ -150,6 +150,16 @@ int oracle_bdsqr(int n, const double *d_in, const double *e_in, double *s,
         for (int i = 0; i < n; ++i) { Uw[(size_t)i * n + i] = 1.0; Vw[(size_t)i * n + i] = 1.0; }
     }
 
+    /* The SVD is homogeneous (sigma(cB) = c sigma(B), same vectors): work on
+     * B / max|d, e| so that the squares in the shift cannot overflow, and
+     * scale the singular values back at the end. */
+    double bscale = 0.0;
+    for (int i = 0; i < n; ++i) bscale = fmax(bscale, fabs(d[i]));
+    for (int i = 0; i + 1 < n; ++i) bscale = fmax(bscale, fabs(e[i]));
+    if (bscale > 0.0) {
+        for (int i = 0; i < n; ++i) d[i] /= bscale;
+        for (int i = 0; i + 1 < n; ++i) e[i] /= bscale;
+    }
     double bnorm = 0.0;
     for (int i = 0; i < n; ++i) bnorm = fmax(bnorm, fabs(d[i]));
     for (int i = 0; i + 1 < n; ++i) bnorm = fmax(bnorm, fabs(e[i]));
@@ -217,6 +227,8 @@ int oracle_bdsqr(int n, const double *d_in, const double *e_in, double *s,
             }
         }
     }
+    if (bscale > 0.0)
+        for (int i = 0; i < n; ++i) d[i] *= bscale;
     memcpy(s, d, sizeof(double) * n);
     if (want) {
         for (int j = 0; j < n; ++j)

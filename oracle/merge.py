@@ -154,8 +154,9 @@ def m_vectors(d, zt, org, tau):
 # --------------------------------------------------------------------------
 def deflation_tol(d, alpha, beta):
     """Reading of 'eps ||M||_2, eps a small multiple of machine precision':
-    tol = 8 eps max(max|d|, |alpha|, |beta|)."""
-    return 8.0 * EPS * max(float(np.max(np.abs(d))) if len(d) else 0.0, abs(alpha), abs(beta))
+    tol = 8 eps max(max|d|, |alpha|, |beta|, 2^-400).  The floor only matters
+    for an all-zero node, where it keeps tol^2 a normal number."""
+    return 8.0 * EPS * max(float(np.max(np.abs(d))) if len(d) else 0.0, abs(alpha), abs(beta), 2.0 ** -400)
 
 
 def deflate(d, z, tol):

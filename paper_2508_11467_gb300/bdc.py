@@ -49,7 +49,29 @@ _SIGS = {
     "bdc_mlp_param_count": (_I, []),
     "bdc_mlp_feature_count": (_I, []),
     "bdc_status_string": (ctypes.c_char_p, [_I]),
+    "bdc_profile_begin": (_I, [_I]),
+    "bdc_profile_end": (_I, [_VP, _VP, _VP]),
+    "bdc_last_error_string": (ctypes.c_char_p, []),
 }
+
+STAGES = ["scale", "leaf", "prep", "gather", "secular", "vectors", "gemm", "finish", "final"]
+
+
+def profile_begin():
+    _check("bdc_profile_begin", lib().bdc_profile_begin(1))
+
+
+def profile_end():
+    """Per-stage device ms, launch counts and algorithmic work since profile_begin()."""
+    import numpy as np
+    k = len(STAGES)
+    ms = np.zeros(k)
+    ln = np.zeros(k, dtype=np.int64)
+    wk = np.zeros(k)
+    _check("bdc_profile_end", lib().bdc_profile_end(ms.ctypes.data_as(ctypes.c_void_p),
+                                                     ln.ctypes.data_as(ctypes.c_void_p),
+                                                     wk.ctypes.data_as(ctypes.c_void_p)))
+    return {s: {"ms": float(ms[i]), "launches": int(ln[i]), "work": float(wk[i])} for i, s in enumerate(STAGES)}
 
 
 def exported_symbols():
@@ -80,7 +102,8 @@ def status_string(code: int) -> str:
 
 class BDCError(RuntimeError):
     def __init__(self, where: str, code: int):
-        super().__init__(f"{where}: {code} ({status_string(code)})")
+        detail = lib().bdc_last_error_string().decode() if code == BDC_ERR_CUDA else ""
+        super().__init__(f"{where}: {code} ({status_string(code)}{': ' + detail if detail else ''})")
         self.code = code
 
 
@@ -106,7 +129,7 @@ def _dev(t, dtype=torch.float64):
     return t.to(dtype).contiguous()
 
 
-def make_opts(prec="fp64", leaf=32, max_iter=64, slices=6, seed="plain", mlp=None) -> Opts:
+def make_opts(prec="fp64", leaf=32, max_iter=64, slices=0, seed="plain", mlp=None) -> Opts:
     o = Opts()
     lib().bdc_opts_default(ctypes.byref(o))
     o.prec = PREC[prec] if isinstance(prec, str) else int(prec)
@@ -122,7 +145,7 @@ def workspace_bytes(n: int, opts: Opts) -> int:
     return int(lib().bdc_svd_workspace(int(n), ctypes.byref(opts)))
 
 
-def svd(d, e, *, prec="fp64", leaf=32, max_iter=64, slices=6, seed="plain", mlp=None,
+def svd(d, e, *, prec="fp64", leaf=32, max_iter=64, slices=0, seed="plain", mlp=None,
         stream=None, work=None, check=True):
     """SVD of the upper bidiagonal (d, e) on the GPU.
 
@@ -144,7 +167,7 @@ def svd(d, e, *, prec="fp64", leaf=32, max_iter=64, slices=6, seed="plain", mlp=
     rc = lib().bdc_svd_ex(n, _ptr(d), _ptr(e), _ptr(Ut), _ptr(S), _ptr(VTt), max(n, 1), max(n, 1),
                           ctypes.byref(o), _ptr(work), work.numel(), _ptr(info), _stream(stream))
     _check("bdc_svd_ex", rc)
-    code = int(info.item()) if check else None
+    code = int(info.item())
     if check and code != 0:
         raise BDCError("bdc_svd_ex (device status)", code)
     return S[:n], Ut.t(), VTt.t(), code
@@ -163,7 +186,7 @@ def svd_sync(d, e, stream=None):
     return S[:n], Ut.t(), VTt.t(), rc
 
 
-def svd_batched(ds, es, *, prec="fp64", leaf=32, max_iter=64, slices=6, stream=None, work=None):
+def svd_batched(ds, es, *, prec="fp64", leaf=32, max_iter=64, slices=0, stream=None, work=None):
     """Batched SVD of bidiagonals of uneven sizes (lists of CUDA tensors)."""
     import numpy as np
     B = len(ds)

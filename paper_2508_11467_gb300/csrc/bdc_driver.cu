@@ -22,10 +22,10 @@
 
 namespace bdc {
 
-// mixed-precision product path (bdc_gemm_mixed.cu)
-cudaError_t launch_gemm_mixed(const GemmProb *probs, int nprobs, int mmax_rows, int nmax_cols,
-                              int kmax, int prec, int slices, void *scratch, size_t scratch_bytes,
-                              cudaStream_t st);
+// mixed-precision product path (bdc_gemm_mixed.cu): products packed one after
+// another in the sliced operand arrays, rows bounded by Mmax[p], columns by Nmax[p]
+cudaError_t launch_gemm_mixed(const GemmProb *probs, int nprobs, const int *Mmax, const int *Nmax, int kmax,
+                              int prec, int slices, void *scratch, size_t scratch_bytes, cudaStream_t st);
 size_t gemm_mixed_scratch(long long rows_total, long long cols_total, int kmax, int prec, int slices);
 
 namespace {
@@ -56,6 +56,16 @@ int build_tree(std::vector<TreeNode> &t, int r0, int m, int sqre, int leaf) {
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+thread_local char g_last_err[256] = "";
+
+int note(cudaError_t e) {
+    if (e != cudaSuccess) {
+        std::snprintf(g_last_err, sizeof(g_last_err), "%s (%d)", cudaGetErrorString(e), (int)e);
+        return note(e);
+    }
+    return 0;
+}
 
 struct Plan {
     int nmat = 0;
@@ -152,8 +162,8 @@ Plan make_plan(int nmat, const int *ns, const bdc_opts &o) {
         size_t mb = 0;
         for (size_t h = 0; h < p.heights.size(); ++h) {
             long long rows = 0, cols = 0;
-            for (auto &nd : p.heights[h]) { rows += 2 * (nd.m + 2); cols += 2 * (nd.m + 8); }
-            mb = std::max(mb, gemm_mixed_scratch(rows, cols, p.hmmax[h] + 16, o.prec,
+            for (auto &nd : p.heights[h]) { rows += 2 * (nd.m + 1); cols += 4 * nd.m; }
+            mb = std::max(mb, gemm_mixed_scratch(rows, cols, p.hmmax[h] + 9, o.prec,
                                                  o.slices > 0 ? o.slices : 6));
         }
         p.off_mixed = off;
@@ -269,6 +279,49 @@ struct PinnedBlob {
 std::mutex g_cache_mu;
 std::map<std::vector<long long>, PinnedBlob> g_cache;
 
+// --------------------------------------------------------------- profiling
+struct ProfEvent {
+    int stage;
+    cudaEvent_t a, b;
+    long long launches;
+    double work;
+};
+// executed work of a recorded call, computed from the device-side deflation
+// results (NodeState) once the call has finished
+struct ProfCall {
+    const NodeState *dstate;
+    int nnodes;
+    std::vector<NodeDesc> merges;
+    int pairs;
+};
+struct Profiler {
+    bool on = false;
+    std::vector<ProfEvent> ev;
+    std::vector<ProfCall> calls;
+};
+Profiler g_prof;
+
+struct StageScope {
+    cudaStream_t st;
+    int stage;
+    long long launches;
+    double work;
+    cudaEvent_t a = nullptr, b = nullptr;
+    StageScope(cudaStream_t s, int k, long long l, double w) : st(s), stage(k), launches(l), work(w) {
+        if (g_prof.on) {
+            cudaEventCreate(&a);
+            cudaEventCreate(&b);
+            cudaEventRecord(a, st);
+        }
+    }
+    ~StageScope() {
+        if (g_prof.on && a) {
+            cudaEventRecord(b, st);
+            g_prof.ev.push_back(ProfEvent{stage, a, b, launches, work});
+        }
+    }
+};
+
 // upload descriptors for the plan into the workspace (graph-capturable copy
 // from a pinned blob that stays alive in a bounded cache)
 cudaError_t upload(const Plan &p, char *work, const std::vector<MatDesc> &mats, cudaStream_t st) {
@@ -318,50 +371,97 @@ int run_plan(const Plan &p, const bdc_opts &o, char *work, std::vector<MatDesc> 
         mats[mi] = c;
     }
     cudaError_t e = upload(p, work, mats, st);
-    if (e != cudaSuccess) return BDC_ERR_CUDA;
+    if (e != cudaSuccess) return note(e);
     const MatDesc *dmats = (const MatDesc *)(work + p.off_mats);
     const NodeDesc *dleaves = (const NodeDesc *)(work + p.off_leaves);
     NodeState *dstate = (NodeState *)(work + p.off_state);
     GemmProb *dprobs = (GemmProb *)(work + p.off_probs);
     const int max_iter = o.max_iter > 0 ? o.max_iter : kDefaultMaxIter;
 
+    double nsq = 0.0;
+    for (int mi = 0; mi < p.nmat; ++mi) nsq += (double)mats[mi].n * mats[mi].n;
     if (p.nmat > 0) {
+        StageScope sc(st, BDC_STAGE_SCALE, 1, 0.0);
         k_scale<<<p.nmat, 256, 0, st>>>(dmats);
-        if ((e = cudaGetLastError()) != cudaSuccess) return BDC_ERR_CUDA;
+        if ((e = cudaGetLastError()) != cudaSuccess) return note(e);
     }
-    if ((e = launch_leaves(dleaves, (int)p.leaves.size(), dmats, p.leafmax, 30, st)) != cudaSuccess)
-        return BDC_ERR_CUDA;
+    {
+        StageScope sc(st, BDC_STAGE_LEAF, p.leaves.empty() ? 0 : 1, 0.0);
+        if ((e = launch_leaves(dleaves, (int)p.leaves.size(), dmats, p.leafmax, 30, st)) != cudaSuccess)
+            return note(e);
+    }
+    const int pairs = (o.prec == BDC_MIXED_EXACT) ? (o.slices * (o.slices + 1)) / 2
+                      : (o.prec == BDC_MIXED_BF16X3) ? 3 : 1;
+    if (g_prof.on) {
+        ProfCall pc{dstate, p.nnodes, {}, pairs};
+        for (auto &h : p.heights) pc.merges.insert(pc.merges.end(), h.begin(), h.end());
+        g_prof.calls.push_back(std::move(pc));
+    }
     for (size_t h = 0; h < p.heights.size(); ++h) {
         const int nn = (int)p.heights[h].size();
         const int mm = p.hmmax[h];
         const NodeDesc *dn = (const NodeDesc *)(work + p.off_nodes + p.off_height_nodes[h]);
-        if ((e = launch_merge_prep(dn, nn, dmats, dstate, dprobs, mm, st)) != cudaSuccess) return BDC_ERR_CUDA;
-        if ((e = launch_merge_gather(dn, nn, dmats, dstate, mm, st)) != cudaSuccess) return BDC_ERR_CUDA;
-        if ((e = launch_secular(dn, nn, dmats, dstate, mm, max_iter, o.seed, o.mlp, st)) != cudaSuccess)
-            return BDC_ERR_CUDA;
-        if ((e = launch_vectors(dn, nn, dmats, dstate, mm, st)) != cudaSuccess) return BDC_ERR_CUDA;
-        if (o.prec == BDC_FP64) {
-            e = launch_gemm64(dprobs, 4 * nn, mm + 1, mm, st);
-        } else {
-            e = launch_gemm_mixed(dprobs, 4 * nn, mm + 1, mm, mm + 16, o.prec,
-                                  o.slices > 0 ? o.slices : 6, work + p.off_mixed, p.mixed_bytes, st);
+        double m2 = 0.0;
+        for (const NodeDesc &nd : p.heights[h]) m2 += (double)nd.m * nd.m;
+        {
+            StageScope sc(st, BDC_STAGE_PREP, 1, 0.0);
+            if ((e = launch_merge_prep(dn, nn, dmats, dstate, dprobs, mm, st)) != cudaSuccess) return note(e);
         }
-        if (e != cudaSuccess) return BDC_ERR_CUDA;
-        if ((e = launch_merge_finish(dn, nn, dmats, dstate, mm, st)) != cudaSuccess) return BDC_ERR_CUDA;
+        {   // reads the children's U, V halves (8 m^2 B), writes W~ and Q~ (16 m^2 B)
+            StageScope sc(st, BDC_STAGE_GATHER, 1, 24.0 * m2);
+            if ((e = launch_merge_gather(dn, nn, dmats, dstate, mm, st)) != cudaSuccess) return note(e);
+        }
+        {
+            StageScope sc(st, BDC_STAGE_SECULAR, 2, 0.0);
+            if ((e = launch_secular(dn, nn, dmats, dstate, mm, max_iter, o.seed, o.mlp, st)) != cudaSuccess)
+                return note(e);
+        }
+        {   // writes U_M and V_M: 16 N Ktot B (added from the node states)
+            StageScope sc(st, BDC_STAGE_VECTORS, 1, 0.0);
+            if ((e = launch_vectors(dn, nn, dmats, dstate, mm, st)) != cudaSuccess) return note(e);
+        }
+        {   // 2 M N K per product as deflated, x slice pairs (added from the node states)
+            // FP64: one launch; split BF16: two slicing kernels + the exact-group
+            // and (for more than 4 slices) the low-group product kernels
+            const int gl = (o.prec == BDC_FP64) ? 1 : (o.prec == BDC_MIXED_EXACT && o.slices > 4) ? 4 : 3;
+            StageScope sc(st, BDC_STAGE_GEMM, gl, 0.0);
+            if (o.prec == BDC_FP64) {
+                e = launch_gemm64(dprobs, 4 * nn, mm + 1, mm, st);
+            } else {
+                std::vector<int> Mx(4 * nn), Nx(4 * nn);
+                for (int k = 0; k < nn; ++k) {
+                    const NodeDesc &nd = p.heights[h][k];
+                    Mx[4 * k + 0] = nd.nl + 1;
+                    Mx[4 * k + 1] = nd.m - nd.nl - 1;
+                    Mx[4 * k + 2] = nd.nl + 1;
+                    Mx[4 * k + 3] = nd.m + nd.sqre - nd.nl - 1;
+                    for (int j = 0; j < 4; ++j) Nx[4 * k + j] = nd.m;
+                }
+                e = launch_gemm_mixed(dprobs, 4 * nn, Mx.data(), Nx.data(), mm + 9, o.prec,
+                                      o.slices > 0 ? o.slices : 6, work + p.off_mixed, p.mixed_bytes, st);
+            }
+            if (e != cudaSuccess) return note(e);
+        }
+        {
+            StageScope sc(st, BDC_STAGE_FINISH, 1, 0.0);
+            if ((e = launch_merge_finish(dn, nn, dmats, dstate, mm, st)) != cudaSuccess) return note(e);
+        }
     }
     if (p.nmat > 0) {
+        // reads U, V (16 n^2 B), writes U, V^T (16 n^2 B)
+        StageScope sc(st, BDC_STAGE_FINAL, (p.nmat + 65534) / 65535, 32.0 * nsq);
         const int tps = (p.nmax + 31) / 32;
         for (int m0 = 0; m0 < p.nmat; m0 += 65535) {
             const int nm = std::min(65535, p.nmat - m0);
             dim3 grid((unsigned)tps * tps, 1, nm);
             k_final<<<grid, 256, 0, st>>>(dmats + m0, tps);
         }
-        if ((e = cudaGetLastError()) != cudaSuccess) return BDC_ERR_CUDA;
+        if ((e = cudaGetLastError()) != cudaSuccess) return note(e);
     }
     // gather the per-matrix status words into the caller's d_info
     for (int mi = 0; mi < p.nmat; ++mi) {
         e = cudaMemcpyAsync(d_info_out + mi, mats[mi].info, sizeof(int), cudaMemcpyDeviceToDevice, st);
-        if (e != cudaSuccess) return BDC_ERR_CUDA;
+        if (e != cudaSuccess) return note(e);
     }
     return 0;
 }
@@ -379,13 +479,18 @@ int check_args(int n, const double *d, const double *e, double *U, double *S, do
     return 0;
 }
 
-bdc_opts resolve(const bdc_opts *o) {
+// slices = 0 picks the count from the order: each merge level adds the
+// product error (~2^-(8S-2) relative) to U and V, so larger trees get one
+// more slice (6 up to n = 8192, 7 above) to keep the residual below 1e-12
+int auto_slices(int nmax) { return nmax <= 8192 ? 6 : 7; }
+
+bdc_opts resolve(const bdc_opts *o, int nmax) {
     bdc_opts r;
     bdc_opts_default(&r);
     if (o) r = *o;
     if (r.leaf <= 0) r.leaf = kDefaultLeaf;
     if (r.max_iter <= 0) r.max_iter = kDefaultMaxIter;
-    if (r.slices <= 0) r.slices = 6;
+    if (r.slices <= 0) r.slices = auto_slices(nmax);
     return r;
 }
 
@@ -413,12 +518,12 @@ void bdc_opts_default(bdc_opts *o) {
     o->seed = BDC_SEED_PLAIN;
     o->leaf = kDefaultLeaf;
     o->max_iter = kDefaultMaxIter;
-    o->slices = 6;
+    o->slices = 0;   // automatic: 6 for n <= 8192, 7 above
 }
 
 size_t bdc_svd_workspace(int n, const bdc_opts *o) {
     if (n < 0) return 0;
-    const bdc_opts r = resolve(o);
+    const bdc_opts r = resolve(o, n);
     const int nn = n;
     return make_plan(1, &nn, r).total;
 }
@@ -427,11 +532,11 @@ int bdc_svd_ex(int n, const double *d, const double *e, double *U, double *S, do
                const bdc_opts *o, void *work, size_t lwork, int *d_info, bdc_stream_t stream) {
     int a = check_args(n, d, e, U, S, VT, ldu, ldvt);
     if (a) return a;
-    const bdc_opts r = resolve(o);
+    const bdc_opts r = resolve(o, n);
     if (check_opts(r)) return -9;
     if (!d_info) return -12;
     cudaStream_t st = (cudaStream_t)stream;
-    if (n == 0) return cudaMemsetAsync(d_info, 0, sizeof(int), st) == cudaSuccess ? 0 : BDC_ERR_CUDA;
+    if (n == 0) return note(cudaMemsetAsync(d_info, 0, sizeof(int), st));
     const Plan p = make_plan(1, &n, r);
     if (!work) return -10;
     if (lwork < p.total) return -11;
@@ -453,7 +558,7 @@ int bdc_svd(int n, const double *d, const double *e, double *U, double *S, doubl
     bdc_opts_default(&o);
     const size_t lw = bdc_svd_workspace(n, &o) + sizeof(int) + 256;
     void *work = nullptr;
-    if (cudaMallocAsync(&work, lw, st) != cudaSuccess) return BDC_ERR_CUDA;
+    if (int r = note(cudaMallocAsync(&work, lw, st))) return r;
     int *dinfo = (int *)((char *)work + lw - sizeof(int) - 64);
     dinfo = (int *)(((uintptr_t)dinfo) & ~(uintptr_t)15);
     int rc = bdc_svd_ex(n, d, e, U, S, VT, ldu, ldvt, &o, work, (size_t)((char *)dinfo - (char *)work), dinfo,
@@ -463,14 +568,16 @@ int bdc_svd(int n, const double *d, const double *e, double *U, double *S, doubl
         if (cudaMemcpyAsync(&hinfo, dinfo, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = BDC_ERR_CUDA;
     }
     cudaFreeAsync(work, st);
-    if (cudaStreamSynchronize(st) != cudaSuccess) return BDC_ERR_CUDA;
+    if (int r = note(cudaStreamSynchronize(st))) return r;
     return rc != 0 ? rc : hinfo;
 }
 
 size_t bdc_svd_batched_workspace(int batch, const int *h_n, const bdc_opts *o) {
     if (batch <= 0 || !h_n) return 0;
     for (int b = 0; b < batch; ++b) if (h_n[b] < 1 || h_n[b] > 2048) return 0;
-    return make_plan(batch, h_n, resolve(o)).total;
+    int nmax = 0;
+    for (int b = 0; b < batch; ++b) nmax = std::max(nmax, h_n[b]);
+    return make_plan(batch, h_n, resolve(o, nmax)).total;
 }
 
 int bdc_svd_batched(int batch, const int *h_n, const double *const *d, const double *const *e, double *const *U,
@@ -491,7 +598,9 @@ int bdc_svd_batched(int batch, const int *h_n, const double *const *d, const dou
         if (!d[b] || (h_n[b] > 1 && !e[b]) || !U[b] || !S[b] || !VT[b]) return -3;
         if (h_ldu[b] < h_n[b] || h_ldvt[b] < h_n[b]) return -8;
     }
-    const bdc_opts r = resolve(o);
+    int nmax = 0;
+    for (int b = 0; b < batch; ++b) nmax = std::max(nmax, h_n[b]);
+    const bdc_opts r = resolve(o, nmax);
     if (check_opts(r)) return -10;
     if (!d_info) return -13;
     const Plan p = make_plan(batch, h_n, r);
@@ -514,16 +623,16 @@ int bdc_secular_solve(int N, const double *d, const double *z, int *org, double 
     if (N > 0 && (!d || !z || !org || !tau || !omega)) return -2;
     if (!d_info) return -8;
     cudaStream_t st = (cudaStream_t)stream;
-    if (cudaMemsetAsync(d_info, 0, sizeof(int), st) != cudaSuccess) return BDC_ERR_CUDA;
-    return launch_secular_single(N, d, z, org, tau, omega, max_iter > 0 ? max_iter : kDefaultMaxIter, d_info,
-                                 st) == cudaSuccess ? 0 : BDC_ERR_CUDA;
+    if (int r = note(cudaMemsetAsync(d_info, 0, sizeof(int), st))) return r;
+    return note(launch_secular_single(N, d, z, org, tau, omega, max_iter > 0 ? max_iter : kDefaultMaxIter, d_info,
+                                      st));
 }
 
 int bdc_lowner_z(int N, const double *d, const double *z, const int *org, const double *tau, double *zt,
                  bdc_stream_t stream) {
     if (N < 0) return -1;
     if (N > 0 && (!d || !z || !org || !tau || !zt)) return -2;
-    return launch_lowner_single(N, d, z, org, tau, zt, (cudaStream_t)stream) == cudaSuccess ? 0 : BDC_ERR_CUDA;
+    return note(launch_lowner_single(N, d, z, org, tau, zt, (cudaStream_t)stream));
 }
 
 int bdc_m_vectors(int N, const double *d, const double *zt, const int *org, const double *tau, double *UM,
@@ -532,8 +641,7 @@ int bdc_m_vectors(int N, const double *d, const double *zt, const int *org, cons
     if (N > 0 && (!d || !zt || !org || !tau || !UM || !VM)) return -2;
     if (ldum < std::max(1, N)) return -7;
     if (ldvm < std::max(1, N)) return -9;
-    return launch_mvectors_single(N, d, zt, org, tau, UM, ldum, VM, ldvm, (cudaStream_t)stream) == cudaSuccess
-               ? 0 : BDC_ERR_CUDA;
+    return note(launch_mvectors_single(N, d, zt, org, tau, UM, ldum, VM, ldvm, (cudaStream_t)stream));
 }
 
 int bdc_deflate(int m, const double *d, const double *z, double tol, int *keep, double *zout, double *dval,
@@ -541,8 +649,7 @@ int bdc_deflate(int m, const double *d, const double *z, double tol, int *keep, 
     if (m < 0) return -1;
     if (m > 0 && (!d || !z || !keep || !zout || !dval)) return -2;
     if (!(tol >= 0.0)) return -4;
-    return launch_deflate_single(m, d, z, tol, keep, zout, dval, (cudaStream_t)stream) == cudaSuccess
-               ? 0 : BDC_ERR_CUDA;
+    return note(launch_deflate_single(m, d, z, tol, keep, zout, dval, (cudaStream_t)stream));
 }
 
 size_t bdc_gemm_workspace(int M, int N, int K, int prec, int slices) {
@@ -578,7 +685,7 @@ int bdc_gemm(int M, int N, int K, const double *A, int lda, const double *B, int
     static GemmProb *hp = nullptr;
     {
         std::lock_guard<std::mutex> lk(mu);
-        if (!hp && cudaMallocHost(&hp, sizeof(GemmProb) * 1024) != cudaSuccess) return BDC_ERR_CUDA;
+        if (!hp) { if (int r = note(cudaMallocHost(&hp, sizeof(GemmProb) * 1024))) return r; }
     }
     // a fresh pinned slot per call (ring of 1024), synchronised on wrap-around
     static int slot = 0;
@@ -589,21 +696,76 @@ int bdc_gemm(int M, int N, int K, const double *A, int lda, const double *B, int
         hs = hp + slot++;
     }
     *hs = pr;
-    if (cudaMemcpyAsync(w, hs, sizeof(GemmProb), cudaMemcpyHostToDevice, st) != cudaSuccess) return BDC_ERR_CUDA;
+    if (int r = note(cudaMemcpyAsync(w, hs, sizeof(GemmProb), cudaMemcpyHostToDevice, st))) return r;
     cudaError_t e;
     if (K == 0) {
         e = cudaMemset2DAsync(C, sizeof(double) * ldc, 0, sizeof(double) * M, N, st);
     } else if (prec == BDC_FP64) {
         e = launch_gemm64((const GemmProb *)w, 1, M, N, st);
     } else {
-        e = launch_gemm_mixed((const GemmProb *)w, 1, M, N, K, prec, slices, w + align256(sizeof(GemmProb)),
+        e = launch_gemm_mixed((const GemmProb *)w, 1, &M, &N, K, prec, slices, w + align256(sizeof(GemmProb)),
                               lwork - (size_t)(w - (char *)work) - align256(sizeof(GemmProb)), st);
     }
-    return e == cudaSuccess ? 0 : BDC_ERR_CUDA;
+    return note(e);
+}
+
+int bdc_profile_begin(int on) {
+    for (auto &ev : g_prof.ev) { cudaEventDestroy(ev.a); cudaEventDestroy(ev.b); }
+    g_prof.ev.clear();
+    g_prof.calls.clear();
+    g_prof.on = on != 0;
+    return 0;
+}
+
+int bdc_profile_end(double *ms, long long *launches, double *work) {
+    double t[BDC_NSTAGES] = {0}, w[BDC_NSTAGES] = {0};
+    long long l[BDC_NSTAGES] = {0};
+    int rc = 0;
+    for (auto &ev : g_prof.ev) {
+        float x = 0.f;
+        if (cudaEventSynchronize(ev.b) != cudaSuccess || cudaEventElapsedTime(&x, ev.a, ev.b) != cudaSuccess)
+            rc = BDC_ERR_CUDA;
+        t[ev.stage] += x;
+        l[ev.stage] += ev.launches;
+        w[ev.stage] += ev.work;
+        cudaEventDestroy(ev.a);
+        cudaEventDestroy(ev.b);
+    }
+    g_prof.ev.clear();
+    for (auto &pc : g_prof.calls) {
+        std::vector<NodeState> hs(pc.nnodes);
+        if (cudaMemcpy(hs.data(), pc.dstate, sizeof(NodeState) * pc.nnodes, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            rc = BDC_ERR_CUDA;
+            continue;
+        }
+        for (const NodeDesc &nd : pc.merges) {
+            const NodeState &ns = hs[nd.id];
+            const double N = ns.N, Ktop = ns.P1 + 1 + ns.n2, Kbot = ns.Ktot - ns.P1;
+            const double top = nd.nl + 1, botU = nd.m - nd.nl - 1, botV = nd.m + nd.sqre - nd.nl - 1;
+            w[BDC_STAGE_GEMM] += 2.0 * N * (2.0 * top * Ktop + (botU + botV) * Kbot) * pc.pairs;
+            w[BDC_STAGE_VECTORS] += 16.0 * N * ns.Ktot;
+            w[BDC_STAGE_FINISH] += 16.0 * (double)ns.ndef * (2.0 * nd.m + nd.sqre);
+        }
+    }
+    g_prof.calls.clear();
+    g_prof.on = false;
+    for (int k = 0; k < BDC_NSTAGES; ++k) {
+        if (ms) ms[k] = t[k];
+        if (launches) launches[k] = l[k];
+        if (work) work[k] = w[k];
+    }
+    return rc;
 }
 
 int bdc_mlp_param_count(void) { return 0; }
 int bdc_mlp_feature_count(void) { return 0; }
+
+const char *bdc_last_error_string(void) {
+    static thread_local char out[256];
+    std::memcpy(out, g_last_err, sizeof(out));
+    g_last_err[0] = 0;
+    return out;
+}
 
 const char *bdc_status_string(int code) {
     if (code == 0) return "success";

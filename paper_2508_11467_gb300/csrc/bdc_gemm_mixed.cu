@@ -1,18 +1,790 @@
-// Mixed-precision merge products (BF16 slices on tcgen05 tensor cores).
+// Mixed-precision merge products of Eq. (bdc-Mv2Bv-u-vt) on tcgen05 tensor
+// cores (sm_103a): C = A B with FP64 A (M x K), B (K x N), C, column-major.
+//
+// BDC_MIXED_EXACT (error-free slicing, after Ozaki, Ogita, Oishi and Rump):
+//   every row r of A is scaled by 2^-E_r (|A_rk| 2^-E_r <= 1/2) and written as
+//   S balanced base-256 digits n_1..n_S (|n_s| <= 128, value sum n_s 2^-8s),
+//   every column c of B likewise with 2^-F_c.  Slice s is stored in BF16 as
+//   n_s 2^-8(s-1) (exact: 8 significant bits).  The products of slice pairs
+//   (i, j) with i + j <= S + 1 (1-based) are summed on the tensor cores in
+//   FP32.  The tensor core truncates when it aligns the addends of an
+//   accumulation, so an FP32 accumulator is only trusted where every partial
+//   sum is an integer multiple of its group's unit 2^-8g below 2^22 (then
+//   nothing is cut): groups g = i + j - 2 <= 4 accumulate in such short K
+//   chunks and are drained into integer registers; the groups g >= 5 (weight
+//   <= 2^-40 of the result) are restarted every 32 of K and summed in FP32
+//   registers.  Relative error about 2^-(8S-2) of |A_r| |B_c| (S = 6:
+//   ~1.4e-14); see MODE_E / MODE_L below.
+// BDC_MIXED_BF16X3: A = hi + lo, B = hi + lo elementwise in BF16 and
+//   hi*hi + hi*lo + lo*hi accumulated in FP32 (~1e-5 relative; reported).
+//
+// Data path per product (several products per launch):
+//   k_slice_a : 32 rows per CTA, two passes over K through shared memory
+//               (row maxima, then integer digit extraction), row-major
+//               K-contiguous BF16 slices [slice][row][Kld] + exponents E.
+//   k_slice_b : one warp per column (B is K-contiguous), same digits + F.
+//   k_mma     : 128 x 128 tile per CTA, K staged 32 at a time by TMA (3-D box
+//               32 x 128 x S, 64-byte swizzle) into a 2-stage ring; warp 0
+//               issues TMA, warp 1 allocates TMEM (512 columns) and one lane
+//               issues tcgen05.mma kind::f16 (BF16 x BF16 -> FP32), warps 2-9
+//               drain and store.  Every mbarrier wait is bounded (2 s of
+//               %globaltimer); a timeout sets an error word and unwinds.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <cstring>
+#include <mutex>
+#include <vector>
+
 #include "bdc_internal.cuh"
 
 namespace bdc {
 
-size_t gemm_mixed_scratch(long long rows_total, long long cols_total, int kmax, int prec, int slices) {
-    (void)rows_total; (void)cols_total; (void)kmax; (void)prec; (void)slices;
-    return 256;
+struct MixProb {
+    int a_row0;   // first row of the product in the A slice array
+    int b_col0;   // first column in the B slice array
+    int tile0;    // first tile of the product in the launch grid
+    int tilesN;   // tiles along N (for the host-known bound Nmax)
+    int Mmax, Nmax;
+    int pad0, pad1;
+};
+
+namespace {
+
+constexpr int TM = 128, TK = 32, TN_MAX = 128;
+constexpr int NSTAGE = 2;
+constexpr int EPI_WARPS = 8;
+constexpr int THREADS = 32 * (2 + EPI_WARPS);
+constexpr unsigned long long kWaitNs = 2000000000ull;   // bounded waits: 2 s
+
+// ------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait; returns false (and flags err) after kWaitNs
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err, volatile int *abort_flag) {
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = gtimer();
+    for (;;) {
+        if (mbar_try(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (gtimer() - t0 > kWaitNs) {
+            atomicCAS(err, 0, 1);
+            *abort_flag = 1;
+            return false;
+        }
+    }
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// K-major operand in shared memory, 64-byte swizzle: rows of 64 B, 8-row
+// groups 512 B apart (SBO), start address advanced by 32 B per K step of 16.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | (1ull << 16) | ((uint64_t)(512 >> 4) << 32) | (1ull << 46) |
+           (4ull << 61);
+}
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// exact integer of an FP32 value v = I 2^-sh with |I| < 2^22
+__device__ __forceinline__ int exact_int(float v, float scale) {
+    return __float_as_int(fmaf(v, scale, 12582912.0f)) - 0x4B400000;
 }
 
-cudaError_t launch_gemm_mixed(const GemmProb *probs, int nprobs, int mmax_rows, int nmax_cols, int kmax,
-                              int prec, int slices, void *scratch, size_t scratch_bytes, cudaStream_t st) {
-    (void)probs; (void)nprobs; (void)mmax_rows; (void)nmax_cols; (void)kmax; (void)prec; (void)slices;
-    (void)scratch; (void)scratch_bytes; (void)st;
-    return cudaErrorNotSupported;
+__device__ __forceinline__ double pow2(int e) {   // 2^e for -1022 <= e <= 1023
+    return __longlong_as_double((long long)(e + 1023) << 52);
+}
+__device__ __forceinline__ double ldexp_safe(double x, int e) {
+    if (e > 1000) return x * pow2(1000) * pow2(e - 1000);
+    if (e < -1000) return x * pow2(-1000) * pow2(e + 1000);
+    return x * pow2(e);
+}
+
+// --------------------------------------------------------------- slicing
+// exponent E with 2^E >= 2 max|x| > 2^(E-1)  (0 for an all-zero set)
+__device__ __forceinline__ int scale_exp(unsigned long long maxbits) {
+    if (maxbits == 0) return 0;
+    const int ef = (int)(maxbits >> 52);
+    if (ef == 0) return -1022 + 2;               // subnormal maximum
+    return ef - 1023 + 2;
+}
+
+// balanced base-256 digits of round(x 2^(8S - E)): slices n_1..n_S, |n_s| <= 128
+template <int S>
+__device__ __forceinline__ void digits(double x, int E, int (&n)[S]) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int ef = (int)((b >> 52) & 0x7FF);
+    long long X = 0;
+    if (ef != 0) {
+        const long long mant = (long long)((b & 0xFFFFFFFFFFFFFull) | (1ull << 52));
+        const int shift = ef - 1075 - E + 8 * S;   // X = mant * 2^shift
+        if (shift >= 0) X = mant << shift;
+        else if (shift > -63) X = (mant + (1ll << (-shift - 1))) >> (-shift);
+        if (b >> 63) X = -X;
+    }
+#pragma unroll
+    for (int s = S - 1; s >= 0; --s) {
+        const long long dgt = ((X + 128) & 255) - 128;
+        n[s] = (int)dgt;
+        X = (X - dgt) >> 8;
+    }
+    n[0] += (int)(X << 8);   // carry out of the top digit (only when |x| 2^-E = 1/2)
+}
+
+__device__ __forceinline__ __nv_bfloat16 slice_bf16(int n, int s) {   // n 2^-8s (s = 0-based slice)
+    return __float2bfloat16_rn(__int2float_rn(n) * __uint_as_float((uint32_t)(127 - 8 * s) << 23));
+}
+
+// A operand: 32 rows per CTA (256 threads), A column-major
+template <int S, bool EXACT>
+__global__ void __launch_bounds__(256) k_slice_a(const GemmProb *__restrict__ probs, const MixProb *__restrict__ mix,
+                                                int nprobs, int row_blocks_total, const int *__restrict__ rb_start,
+                                                __nv_bfloat16 *__restrict__ As, int *__restrict__ Ea, int rowsA,
+                                                int Kld) {
+    __shared__ unsigned long long smax[8][33];
+    __shared__ __nv_bfloat16 tile[S][32][72];
+    // locate the product of this row block
+    int lo = 0, hi = nprobs - 1;
+    while (lo < hi) { int mid = (lo + hi + 1) >> 1; if (rb_start[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1; }
+    const int p = lo;
+    const GemmProb pr = probs[p];
+    const MixProb mx = mix[p];
+    const int r0 = (blockIdx.x - rb_start[p]) * 32;
+    if (r0 >= mx.Mmax) return;
+    const int tr = threadIdx.x & 31, tc = threadIdx.x >> 5;   // row within block, column lane
+    const int row = r0 + tr;
+    const bool rowok = row < pr.M;
+    const int K = pr.K;
+    int E = 0;
+    if (EXACT) {
+        unsigned long long mx2 = 0;
+        if (rowok)
+            for (int k = tc; k < K; k += 8) {
+                const unsigned long long b = (unsigned long long)__double_as_longlong(pr.A[(size_t)k * pr.lda + row]) &
+                                             0x7FFFFFFFFFFFFFFFull;
+                mx2 = b > mx2 ? b : mx2;
+            }
+        smax[tc][tr] = mx2;
+        __syncthreads();
+        unsigned long long m = 0;
+        for (int q = 0; q < 8; ++q) m = smax[q][tr] > m ? smax[q][tr] : m;
+        E = scale_exp(m);
+        if (tc == 0 && row < mx.Mmax) Ea[mx.a_row0 + row] = rowok ? E : 0;
+    }
+    // second pass: digits, staged through shared memory so rows are written
+    // K-contiguous; only up to the last 32-wide stage the MMA reads
+    const int Kend = min(Kld, (K + TK - 1) / TK * TK);
+    for (int k0 = 0; k0 < Kend; k0 += 64) {
+        for (int kk = tc; kk < 64; kk += 8) {
+            const int k = k0 + kk;
+            const double x = (rowok && k < K) ? pr.A[(size_t)k * pr.lda + row] : 0.0;
+            if (EXACT) {
+                int n[S];
+                digits<S>(x, E, n);
+#pragma unroll
+                for (int s = 0; s < S; ++s) tile[s][tr][kk] = slice_bf16(n[s], s);
+            } else {
+                const float xf = (float)x;
+                const __nv_bfloat16 h = __float2bfloat16_rn(xf);
+                tile[0][tr][kk] = h;
+                tile[1][tr][kk] = __float2bfloat16_rn(xf - __bfloat162float(h));
+            }
+        }
+        __syncthreads();
+        // 32 rows x 64 columns x S slices out, 8 columns (16 B) per thread-store
+        for (int idx = threadIdx.x; idx < S * 32 * 8; idx += 256) {
+            const int s = idx / 256, rem = idx % 256, rr = rem >> 3, seg = rem & 7;
+            const int grow = r0 + rr;
+            if (grow < mx.Mmax && k0 + seg * 8 < Kend) {
+                const uint4 v = *reinterpret_cast<const uint4 *>(&tile[s][rr][seg * 8]);
+                *reinterpret_cast<uint4 *>(As + ((size_t)s * rowsA + mx.a_row0 + grow) * Kld + k0 + seg * 8) = v;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// B operand: one warp per column (column-major B is K-contiguous)
+template <int S, bool EXACT>
+__global__ void __launch_bounds__(256) k_slice_b(const GemmProb *__restrict__ probs, const MixProb *__restrict__ mix,
+                                                int nprobs, const int *__restrict__ cb_start, int cols_total,
+                                                __nv_bfloat16 *__restrict__ Bs, int *__restrict__ Fb, int colsB, int Kld) {
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (gw >= cols_total) return;
+    int lo = 0, hi = nprobs - 1;
+    while (lo < hi) { int mid = (lo + hi + 1) >> 1; if (cb_start[mid] <= gw) lo = mid; else hi = mid - 1; }
+    const int p = lo;
+    const GemmProb pr = probs[p];
+    const MixProb mx = mix[p];
+    const int c = gw - cb_start[p];
+    if (c >= mx.Nmax) return;
+    const bool colok = c < pr.N;
+    const int K = pr.K;
+    const double *col = pr.B + (size_t)c * pr.ldb;
+    int F = 0;
+    if (EXACT) {
+        unsigned long long m = 0;
+        if (colok)
+            for (int k = lane; k < K; k += 32) {
+                const unsigned long long b = (unsigned long long)__double_as_longlong(col[k]) & 0x7FFFFFFFFFFFFFFFull;
+                m = b > m ? b : m;
+            }
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long y = __shfl_xor_sync(0xffffffffu, m, o);
+            m = y > m ? y : m;
+        }
+        F = scale_exp(m);
+        if (lane == 0) Fb[mx.b_col0 + c] = colok ? F : 0;
+    }
+    __nv_bfloat16 *dst = Bs + (size_t)(mx.b_col0 + c) * Kld;
+    const int Kend = min(Kld, (K + TK - 1) / TK * TK);
+    for (int k = lane; k < Kend; k += 32) {
+        const double x = (colok && k < K) ? col[k] : 0.0;
+        if (EXACT) {
+            int n[S];
+            digits<S>(x, F, n);
+#pragma unroll
+            for (int s = 0; s < S; ++s) dst[(size_t)s * colsB * Kld + k] = slice_bf16(n[s], s);
+        } else {
+            const float xf = (float)x;
+            const __nv_bfloat16 h = __float2bfloat16_rn(xf);
+            dst[k] = h;
+            dst[(size_t)colsB * Kld + k] = __float2bfloat16_rn(xf - __bfloat162float(h));
+        }
+    }
+}
+
+// ------------------------------------------------------------- MMA kernels
+// Three kernel modes share the TMA producer, the 128 x 128 tile and four
+// 128-column TMEM accumulators at columns 0, 128, 256, 384:
+//   MODE_E   exact groups g = 0..3 (10 slice pairs), K chunks of 64 split in
+//            two staggered sets, set A = {g0, g3} over stages {0,1},{2,3},...
+//            and set B = {g1, g2} over {0},{1,2},{3,4},...; each set drains
+//            into the 64-bit integers L (unit 2^-24) while the other set's
+//            MMAs run.  Writes C = 2^(E+F-40) L.
+//   MODE_L   the remaining groups g >= 4: group 4 in its own accumulator,
+//            exact per 32-wide stage (|I_4| <= 5 * 2^14 * 32 < 2^22), the rest
+//            (weight <= 2^-40) in a second one, both restarted every stage and
+//            summed over the stages in FP32 registers (round to nearest); two
+//            accumulator buffers alternate per stage.  Adds 2^(E+F-16) SL to C.
+//   MODE_X3  BF16x3: (hi, lo) pairs (0,0), (0,1), (1,0) in one accumulator
+//            over the whole K.  Writes C.
+enum { MODE_E = 0, MODE_L = 1, MODE_X3 = 2 };
+constexpr int TNX = 128;
+
+template <int S, int MODE>
+__global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUtensorMap tmA,
+                                                     const __grid_constant__ CUtensorMap tmB,
+                                                     const GemmProb *__restrict__ probs,
+                                                     const MixProb *__restrict__ mix, int nprobs,
+                                                     const int *__restrict__ Ea, const int *__restrict__ Fb,
+                                                     int *__restrict__ err) {
+    constexpr int TILE = TM * TK * 2;                 // one 128 x 32 BF16 slice tile (A or B)
+    constexpr int STAGE_BYTES = 2 * S * TILE;
+    // kind::f16 instruction descriptor: D = F32, A = B = BF16, K-major,
+    // N/8 in bits 17-22, M/16 in bits 24-28
+    constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TNX >> 3) << 17) |
+                               ((uint32_t)(TM >> 4) << 24);
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = (uint64_t *)(smem + NSTAGE * STAGE_BYTES);
+    uint64_t *empty = full + NSTAGE;
+    uint64_t *accfull = empty + NSTAGE;      // [2]: set A / set B (MODE_E) or buffer 0 / 1 (MODE_L)
+    uint64_t *accempty = accfull + 2;        // [2]
+    uint32_t *tmem_slot = (uint32_t *)(accempty + 2);
+    volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+
+    int lo = 0, hi = nprobs - 1;
+    while (lo < hi) { int mid = (lo + hi + 1) >> 1; if (mix[mid].tile0 <= (int)blockIdx.x) lo = mid; else hi = mid - 1; }
+    const int p = lo;
+    const GemmProb pr = probs[p];
+    const MixProb mx = mix[p];
+    const int t = blockIdx.x - mx.tile0;
+    const int m0 = (t / mx.tilesN) * TM, n0 = (t % mx.tilesN) * TNX;
+    if (m0 >= pr.M || n0 >= pr.N || pr.K <= 0) return;
+    const int nk = (pr.K + TK - 1) / TK;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < NSTAGE; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
+        for (int i = 0; i < 2; ++i) { mbar_init(&accfull[i], 1); mbar_init(&accempty[i], 32 * EPI_WARPS); }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            for (int s = 0; s < nk; ++s) {
+                const int buf = s & 1;
+                if (s >= NSTAGE && !mbar_wait(&empty[buf], ((s >> 1) - 1) & 1, err, abort_flag)) break;
+                mbar_expect_tx(&full[buf], STAGE_BYTES);
+                const uint32_t dstA = smem_u32(smem + buf * STAGE_BYTES);
+                tma_load_3d(dstA, &tmA, s * TK, mx.a_row0 + m0, 0, &full[buf]);
+                tma_load_3d(dstA + S * TILE, &tmB, s * TK, mx.b_col0 + n0, 0, &full[buf]);
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer (one lane)
+        if (lane == 0) {
+            auto mma = [&](uint32_t col, uint32_t a, uint32_t b, uint32_t acc) {
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, "
+                    "p;\n}\n" ::"r"(tmem + col),
+                    "l"(sdesc(a)), "l"(sdesc(b)), "r"(idesc), "r"(acc)
+                    : "memory");
+            };
+            bool ok = true;
+            for (int s = 0; s < nk && ok; ++s) {
+                const int buf = s & 1;
+                if (!mbar_wait(&full[buf], (s >> 1) & 1, err, abort_flag)) { ok = false; break; }
+                fence_after();
+                const uint32_t bA = smem_u32(smem + buf * STAGE_BYTES);
+                const uint32_t bB = bA + S * TILE;
+                if constexpr (MODE == MODE_X3) {
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk) {
+                        mma(0, bA + kk * 32, bB + kk * 32, (s == 0 && kk == 0) ? 0u : 1u);
+                        mma(0, bA + kk * 32, bB + TILE + kk * 32, 1u);
+                        mma(0, bA + TILE + kk * 32, bB + kk * 32, 1u);
+                    }
+                    umma_commit(&empty[buf]);
+                    if (s == nk - 1) umma_commit(&accfull[0]);
+                } else if constexpr (MODE == MODE_L) {
+                    const int b = s & 1;                       // accumulator buffer of this stage
+                    if (s >= 2) {
+                        if (!mbar_wait(&accempty[b], ((s >> 1) - 1) & 1, err, abort_flag)) { ok = false; break; }
+                        fence_after();
+                    }
+                    const uint32_t c4 = 256 * b, cl = 256 * b + 128;
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk) {
+#pragma unroll
+                        for (int i = 0; i <= 4; ++i)
+                            if (i < S && 4 - i < S)
+                                mma(c4, bA + i * TILE + kk * 32, bB + (4 - i) * TILE + kk * 32,
+                                    (kk == 0 && i == 0) ? 0u : 1u);
+                        bool first = true;
+#pragma unroll
+                        for (int g = 5; g <= S - 1; ++g)
+#pragma unroll
+                            for (int i = 0; i <= g; ++i) {
+                                const int j = g - i;
+                                if (i >= S || j >= S) continue;
+                                mma(cl, bA + i * TILE + kk * 32, bB + j * TILE + kk * 32,
+                                    (kk == 0 && first) ? 0u : 1u);
+                                first = false;
+                            }
+                    }
+                    umma_commit(&empty[buf]);
+                    umma_commit(&accfull[b]);
+                } else {
+                    // MODE_E: set A = {g0 @0, g3 @384}, set B = {g1 @128, g2 @256}
+                    auto issueA = [&](bool fresh) {
+#pragma unroll
+                        for (int kk = 0; kk < 2; ++kk) {
+                            mma(0, bA + kk * 32, bB + kk * 32, (fresh && kk == 0) ? 0u : 1u);
+#pragma unroll
+                            for (int i = 0; i <= 3; ++i)
+                                mma(384, bA + i * TILE + kk * 32, bB + (3 - i) * TILE + kk * 32,
+                                    (fresh && kk == 0 && i == 0) ? 0u : 1u);
+                        }
+                    };
+                    auto issueB = [&](bool fresh) {
+#pragma unroll
+                        for (int kk = 0; kk < 2; ++kk) {
+#pragma unroll
+                            for (int i = 0; i <= 1; ++i)
+                                mma(128, bA + i * TILE + kk * 32, bB + (1 - i) * TILE + kk * 32,
+                                    (fresh && kk == 0 && i == 0) ? 0u : 1u);
+#pragma unroll
+                            for (int i = 0; i <= 2; ++i)
+                                mma(256, bA + i * TILE + kk * 32, bB + (2 - i) * TILE + kk * 32,
+                                    (fresh && kk == 0 && i == 0) ? 0u : 1u);
+                        }
+                    };
+                    if ((s & 1) == 0) {
+                        issueB(s == 0);                    // set B continues (starts at s = 0)
+                        if (s >= 2) {                      // set A starts a chunk: its drain must be done
+                            if (!mbar_wait(&accempty[0], ((s >> 1) - 1) & 1, err, abort_flag)) { ok = false; }
+                            fence_after();
+                        }
+                        if (ok) issueA(true);
+                    } else {
+                        issueA(false);
+                        if (!mbar_wait(&accempty[1], ((s - 1) >> 1) & 1, err, abort_flag)) { ok = false; }
+                        fence_after();
+                        if (ok) issueB(true);
+                    }
+                    umma_commit(&empty[buf]);
+                    if (((s & 1) == 0) || s == nk - 1) umma_commit(&accfull[1]);   // set B chunk ends
+                    if (((s & 1) == 1) || s == nk - 1) umma_commit(&accfull[0]);   // set A chunk ends
+                }
+            }
+        }
+    } else {
+        // ------------------------------------------------ epilogue (warps 2..9)
+        const int q = warp & 3;                    // TMEM lane quarter this warp may access
+        const int half = (warp - 2) >> 2;          // column half
+        const int row = m0 + 32 * q + lane;
+        const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16) + 64 * half;
+        bool ok = true;
+        if constexpr (MODE == MODE_E) {
+            long long L[64];
+#pragma unroll
+            for (int i = 0; i < 64; ++i) L[i] = 0;
+            int cA = 0, cB = 0;
+            for (int s = 0; s < nk && ok; ++s) {
+                if (((s & 1) == 0) || s == nk - 1) {                // set B: g1, g2
+                    if (!mbar_wait(&accfull[1], cB & 1, err, abort_flag)) { ok = false; break; }
+                    fence_after();
+#pragma unroll
+                    for (int cb = 0; cb < 4; ++cb) {
+                        float v1[16], v2[16];
+                        tmem_ld16(tl + 128 + 16 * cb, v1);
+                        tmem_ld16(tl + 256 + 16 * cb, v2);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            const int tt = exact_int(v1[i], 256.0f) * 256 + exact_int(v2[i], 65536.0f);
+                            L[16 * cb + i] += (long long)tt * 256;     // I_1 2^16 + I_2 2^8
+                        }
+                    }
+                    fence_before();
+                    mbar_arrive(&accempty[1]);
+                    ++cB;
+                }
+                if (((s & 1) == 1) || s == nk - 1) {                // set A: g0, g3
+                    if (!mbar_wait(&accfull[0], cA & 1, err, abort_flag)) { ok = false; break; }
+                    fence_after();
+#pragma unroll
+                    for (int cb = 0; cb < 4; ++cb) {
+                        float v0[16], v3[16];
+                        tmem_ld16(tl + 16 * cb, v0);
+                        tmem_ld16(tl + 384 + 16 * cb, v3);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int i = 0; i < 16; ++i)
+                            L[16 * cb + i] += ((long long)exact_int(v0[i], 1.0f) << 24) +
+                                              exact_int(v3[i], 16777216.0f);   // I_0 2^24 + I_3
+                    }
+                    fence_before();
+                    mbar_arrive(&accempty[0]);
+                    ++cA;
+                }
+            }
+            if (ok) {
+                const int Er = (row < pr.M) ? Ea[mx.a_row0 + row] : 0;
+#pragma unroll
+                for (int i = 0; i < 64; ++i) {
+                    const int col = n0 + 64 * half + i;
+                    if (row < pr.M && col < pr.N)
+                        pr.C[(size_t)col * pr.ldc + row] = ldexp_safe((double)L[i], Er + Fb[mx.b_col0 + col] - 40);
+                }
+            }
+        } else if constexpr (MODE == MODE_L) {
+            // group 4 is exact per stage (and weighs <= 2^-32), groups >= 5 weigh
+            // <= 2^-40: both are summed over the stages in FP32 registers
+            float SL[64];
+#pragma unroll
+            for (int i = 0; i < 64; ++i) SL[i] = 0.f;
+            for (int s = 0; s < nk; ++s) {
+                const int b = s & 1;
+                if (!mbar_wait(&accfull[b], (s >> 1) & 1, err, abort_flag)) { ok = false; break; }
+                fence_after();
+#pragma unroll
+                for (int cb = 0; cb < 4; ++cb) {
+                    float v4[16], vl[16];
+                    tmem_ld16(tl + 256 * b + 16 * cb, v4);
+                    if (S > 5) tmem_ld16(tl + 256 * b + 128 + 16 * cb, vl);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        SL[16 * cb + i] += v4[i];
+                        if (S > 5) SL[16 * cb + i] += vl[i];
+                    }
+                }
+                fence_before();
+                mbar_arrive(&accempty[b]);
+            }
+            if (ok) {
+                const int Er = (row < pr.M) ? Ea[mx.a_row0 + row] : 0;
+#pragma unroll
+                for (int i = 0; i < 64; ++i) {
+                    const int col = n0 + 64 * half + i;
+                    if (row < pr.M && col < pr.N) {
+                        const int e = Er + Fb[mx.b_col0 + col];
+                        double *c = pr.C + (size_t)col * pr.ldc + row;
+                        *c += ldexp_safe((double)SL[i], e - 16);
+                    }
+                }
+            }
+        } else {
+            if (!mbar_wait(&accfull[0], 0, err, abort_flag)) ok = false;
+            fence_after();
+            if (ok) {
+#pragma unroll
+                for (int cb = 0; cb < 4; ++cb) {
+                    float v[16];
+                    tmem_ld16(tl + 16 * cb, v);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const int col = n0 + 64 * half + 16 * cb + i;
+                        if (row < pr.M && col < pr.N) pr.C[(size_t)col * pr.ldc + row] = (double)v[i];
+                    }
+                }
+            }
+        }
+        fence_before();
+    }
+    __syncthreads();
+    if (warp == 1) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+    }
+}
+
+// ------------------------------------------------------------- host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    });
+    return fn;
+}
+
+// 3-D map over [slice][row][Kld] BF16 with a 32 x box_rows x S box and 64 B swizzle
+bool make_map(CUtensorMap *m, void *base, int rows, int Kld, int S, int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)Kld, (cuuint64_t)rows, (cuuint64_t)S};
+    cuuint64_t strides[2] = {(cuuint64_t)Kld * 2, (cuuint64_t)rows * Kld * 2};
+    cuuint32_t box[3] = {TK, (cuuint32_t)box_rows, (cuuint32_t)S};
+    cuuint32_t estr[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+    size_t offA, offB, offE, offF, offErr, offMix, offRb, offCb, total;
+};
+
+Layout layout(long long rowsA, long long colsB, int Kld, int S, int nprobs) {
+    Layout L{};
+    size_t o = 0;
+    L.offA = o; o += align256((size_t)S * rowsA * Kld * 2);
+    L.offB = o; o += align256((size_t)S * colsB * Kld * 2);
+    L.offE = o; o += align256(sizeof(int) * (size_t)rowsA);
+    L.offF = o; o += align256(sizeof(int) * (size_t)colsB);
+    L.offErr = o; o += 256;
+    L.offMix = o; o += align256(sizeof(MixProb) * (size_t)nprobs);
+    L.offRb = o; o += align256(sizeof(int) * (size_t)nprobs);
+    L.offCb = o; o += align256(sizeof(int) * (size_t)nprobs);
+    L.total = o;
+    return L;
+}
+
+template <int S, bool EXACT>
+cudaError_t run_mixed(const GemmProb *probs, int nprobs, const std::vector<MixProb> &hm, int rowsA, int colsB,
+                      int Kld, char *scratch, const Layout &L, cudaStream_t st) {
+    __nv_bfloat16 *As = (__nv_bfloat16 *)(scratch + L.offA);
+    __nv_bfloat16 *Bs = (__nv_bfloat16 *)(scratch + L.offB);
+    int *E = (int *)(scratch + L.offE), *F = (int *)(scratch + L.offF), *err = (int *)(scratch + L.offErr);
+    MixProb *dmix = (MixProb *)(scratch + L.offMix);
+    int *rb = (int *)(scratch + L.offRb), *cb = (int *)(scratch + L.offCb);
+    // row-block and column starts
+    std::vector<int> hrb(nprobs), hcb(nprobs);
+    int rbt = 0, cbt = 0, tiles = 0;
+    for (int p = 0; p < nprobs; ++p) {
+        hrb[p] = rbt; rbt += (hm[p].Mmax + 31) / 32;
+        hcb[p] = cbt; cbt += hm[p].Nmax;
+        tiles = hm[p].tile0 + ((hm[p].Mmax + TM - 1) / TM) * hm[p].tilesN;
+    }
+    if (hm.size() && hm[0].tilesN != (hm[0].Nmax + TNX - 1) / TNX) return cudaErrorInvalidValue;
+    // small tables through a pinned ring (graph-capturable copies)
+    static std::mutex mu;
+    static char *ring = nullptr;
+    static size_t ring_off = 0;
+    constexpr size_t kRing = 64ull << 20;
+    const size_t need = sizeof(MixProb) * nprobs + 2 * sizeof(int) * nprobs + 3 * 256;
+    if (need > kRing) return cudaErrorInvalidValue;
+    char *h;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!ring && cudaMallocHost((void **)&ring, kRing) != cudaSuccess) return cudaErrorMemoryAllocation;
+        if (ring_off + need > kRing) {
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            cudaStreamIsCapturing(st, &cs);
+            if (cs == cudaStreamCaptureStatusNone) cudaDeviceSynchronize();
+            ring_off = 0;
+        }
+        h = ring + ring_off;
+        ring_off += (need + 255) & ~(size_t)255;
+    }
+    char *hp = h;
+    std::memcpy(hp, hm.data(), sizeof(MixProb) * nprobs);
+    cudaError_t e = cudaMemcpyAsync(dmix, hp, sizeof(MixProb) * nprobs, cudaMemcpyHostToDevice, st);
+    hp += align256(sizeof(MixProb) * nprobs);
+    std::memcpy(hp, hrb.data(), sizeof(int) * nprobs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(rb, hp, sizeof(int) * nprobs, cudaMemcpyHostToDevice, st);
+    hp += align256(sizeof(int) * nprobs);
+    std::memcpy(hp, hcb.data(), sizeof(int) * nprobs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cb, hp, sizeof(int) * nprobs, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+
+    k_slice_a<S, EXACT><<<rbt, 256, 0, st>>>(probs, dmix, nprobs, rbt, rb, As, E, rowsA, Kld);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_slice_b<S, EXACT><<<(cbt + 7) / 8, 256, 0, st>>>(probs, dmix, nprobs, cb, cbt, Bs, F, colsB, Kld);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, As, rowsA, Kld, S, TM) || !make_map(&mb, Bs, colsB, Kld, S, TNX)) return cudaErrorInvalidValue;
+    const size_t smem = NSTAGE * (size_t)(2 * S * TM * TK * 2) + 1024 + 256;
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [&] {
+        if constexpr (EXACT) {
+            attr_err = cudaFuncSetAttribute(k_mma<S, MODE_E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (attr_err == cudaSuccess)
+                attr_err =
+                    cudaFuncSetAttribute(k_mma<S, MODE_L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        } else {
+            attr_err = cudaFuncSetAttribute(k_mma<S, MODE_X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        }
+    });
+    if (attr_err != cudaSuccess) return attr_err;
+    if (tiles <= 0) return cudaSuccess;
+    if constexpr (EXACT) {
+        k_mma<S, MODE_E><<<tiles, THREADS, smem, st>>>(ma, mb, probs, dmix, nprobs, E, F, err);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if constexpr (S > 4) k_mma<S, MODE_L><<<tiles, THREADS, smem, st>>>(ma, mb, probs, dmix, nprobs, E, F, err);
+    } else {
+        k_mma<S, MODE_X3><<<tiles, THREADS, smem, st>>>(ma, mb, probs, dmix, nprobs, E, F, err);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t gemm_mixed_scratch(long long rows_total, long long cols_total, int kmax, int prec, int slices) {
+    const int S = (prec == BDC_MIXED_BF16X3) ? 2 : slices;
+    const int Kld = (kmax + TK - 1) / TK * TK;
+    const int nprobs = 1 << 16;
+    return layout(rows_total + TM, cols_total + TN_MAX, Kld, S, nprobs).total + 1024;
+}
+
+// probs: device problem table (M, N, K known on the device); hm: host layout
+cudaError_t launch_gemm_mixed_tab(const GemmProb *probs, int nprobs, const std::vector<MixProb> &hm, int rowsA,
+                                  int colsB, int kmax, int prec, int slices, void *scratch, size_t scratch_bytes,
+                                  cudaStream_t st) {
+    if (nprobs <= 0) return cudaSuccess;
+    const int S = (prec == BDC_MIXED_BF16X3) ? 2 : slices;
+    const int Kld = (kmax + TK - 1) / TK * TK;
+    const Layout L = layout(rowsA + TM, colsB + TN_MAX, Kld, S, nprobs);
+    if (L.total > scratch_bytes) return cudaErrorInvalidValue;
+    char *sc = (char *)scratch;
+    const int ra = rowsA + TM, cbn = colsB + TN_MAX;
+    if (prec == BDC_MIXED_BF16X3) return run_mixed<2, false>(probs, nprobs, hm, ra, cbn, Kld, sc, L, st);
+    switch (S) {
+        case 4: return run_mixed<4, true>(probs, nprobs, hm, ra, cbn, Kld, sc, L, st);
+        case 5: return run_mixed<5, true>(probs, nprobs, hm, ra, cbn, Kld, sc, L, st);
+        case 6: return run_mixed<6, true>(probs, nprobs, hm, ra, cbn, Kld, sc, L, st);
+        case 7: return run_mixed<7, true>(probs, nprobs, hm, ra, cbn, Kld, sc, L, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// simple layout: products packed one after another (rows by M bound, columns by N bound)
+cudaError_t launch_gemm_mixed(const GemmProb *probs, int nprobs, const int *Mmax, const int *Nmax, int kmax, int prec,
+                              int slices, void *scratch, size_t scratch_bytes, cudaStream_t st) {
+    std::vector<MixProb> hm(nprobs);
+    int rows = 0, cols = 0, tiles = 0;
+    const int tn = TNX;
+    for (int p = 0; p < nprobs; ++p) {
+        MixProb m{};
+        m.a_row0 = rows; m.b_col0 = cols; m.tile0 = tiles;
+        m.Mmax = Mmax[p]; m.Nmax = Nmax[p];
+        m.tilesN = (m.Nmax + tn - 1) / tn;
+        tiles += ((m.Mmax + TM - 1) / TM) * m.tilesN;
+        rows += m.Mmax; cols += m.Nmax;
+        hm[p] = m;
+    }
+    return launch_gemm_mixed_tab(probs, nprobs, hm, rows, cols, kmax, prec, slices, scratch, scratch_bytes, st);
+}
+
+int gemm_mixed_error(void *scratch, long long rows_total, long long cols_total, int kmax, int prec, int slices) {
+    (void)scratch; (void)rows_total; (void)cols_total; (void)kmax; (void)prec; (void)slices;
+    return 0;
 }
 
 }  // namespace bdc

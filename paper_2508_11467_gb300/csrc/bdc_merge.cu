@@ -225,7 +225,9 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
         s_cq = cq; s_sq = sq;
     }
     dmax = block_max(dmax, dsum);
-    const double tol = 8.0 * kEps * fmax(dmax, fmax(fabs(alpha), fabs(beta)));
+    // 8 eps ||M|| with ||M|| ~ max(|d|, |alpha|, |beta|); the floor 2^-400
+    // keeps an all-zero node well defined (tol^2 stays a normal number)
+    const double tol = 8.0 * kEps * fmax(fmax(dmax, 0x1p-400), fmax(fabs(alpha), fabs(beta)));
 
     // ---- deflation
     int a;

@@ -152,3 +152,37 @@ def test_negative_and_scaled_entries(bdc):
     d = d * sgn * 1e150
     e = e * sgn[:299] * 1e150
     _check_full(bdc, d, e, leaf=16)
+
+
+# ---------------------------------------------------------------- mixed precision
+@pytest.mark.parametrize("kind,seed", [("uniform", 0), ("graded", 1), ("clustered", 2)])
+def test_mixed_exact_n4096(bdc, kind, seed):
+    """Split-BF16 merge products (6 slices): same FP64 tolerances as the
+    FP64 path, residual well inside 1e-12."""
+    d, e = inputs.make(kind, 4096, seed)
+    err, res, ou, ov = _check_full(bdc, d, e, leaf=32, prec="exact", slices=6)
+    assert res <= 1e-12 and ou <= 1e-12 * 4096 and ov <= 1e-12 * 4096
+
+
+@pytest.mark.parametrize("n,leaf", [(33, 16), (300, 16), (1000, 32)])
+def test_mixed_exact_small(bdc, n, leaf):
+    d, e = inputs.uniform(n, 40 + n)
+    _check_full(bdc, d, e, leaf=leaf, prec="exact", slices=6)
+
+
+def test_mixed_exact_closed_form(bdc):
+    n = 2048
+    d, e = inputs.ones(n)
+    k = np.arange(1, n + 1)
+    _check_full(bdc, d, e, ref=2.0 * np.cos(k * np.pi / (2 * n + 1)), leaf=32, prec="exact", slices=6)
+
+
+def test_bf16x3_literal_split_error_is_reported(bdc):
+    # the literal 3-term BF16 split with FP32 accumulation is ~1e-5 accurate:
+    # it runs end to end and its (larger) error is what bench/DESIGN report
+    d, e = inputs.make("clustered", 1024, 2)
+    S, U, VT, info = _run(bdc, d, e, leaf=32, prec="bf16x3")
+    s = S.cpu().numpy()
+    res = oracle.residual(d, e, s, U.cpu().numpy(), VT.cpu().numpy())
+    assert info == 0 and np.all(np.isfinite(s))
+    assert 1e-9 < res < 1e-2
