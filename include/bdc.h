@@ -137,6 +137,23 @@ int bdc_m_vectors(int N, const double *d, const double *zt, const int *org, cons
 int bdc_deflate(int m, const double *d, const double *z, double tol, int *keep, double *zout,
                 double *dval, bdc_stream_t stream);
 
+/* Allocation-free form of bdc_deflate, for callers that must not allocate
+ * device memory during the call (the device allocator is owned by another
+ * component, or all memory is reserved up front).  The paper has no
+ * counterpart of this entry point.  Same arguments and outputs as
+ * bdc_deflate; the scratch is a fixed array in the library's device memory
+ * (about 2.4 MB, held on every device that loads the library until exit),
+ * so m is limited to BDC_DEFLATE_NOALLOC_MAX: a larger (or negative) m
+ * returns -1 before any work is queued.  No cudaMalloc / cudaFree or other
+ * allocating call is made.  The first call on a device looks the array's
+ * device address up (cudaGetSymbolAddress) with that device current; make
+ * that first call before capturing a stream.  All calls share the array, so
+ * calls that can run at the same time on the GPU race and must be ordered
+ * by the caller. */
+#define BDC_DEFLATE_NOALLOC_MAX 65536
+int bdc_deflate_noalloc(int m, const double *d, const double *z, double tol, int *keep, double *zout,
+                        double *dval, bdc_stream_t stream);
+
 /* Merge product C = A * B (M x N, inner K), column-major, with the chosen
  * precision (bdc_precision): FP64, or the split BF16 tcgen05 products.  A,
  * B, C device; `work` device scratch of bdc_gemm_workspace bytes. */

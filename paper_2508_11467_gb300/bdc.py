@@ -44,6 +44,7 @@ _SIGS = {
     "bdc_lowner_z": (_I, [_I, _VP, _VP, _VP, _VP, _VP, _VP]),
     "bdc_m_vectors": (_I, [_I, _VP, _VP, _VP, _VP, _VP, _I, _VP, _I, _VP]),
     "bdc_deflate": (_I, [_I, _VP, _VP, _D, _VP, _VP, _VP, _VP]),
+    "bdc_deflate_noalloc": (_I, [_I, _VP, _VP, _D, _VP, _VP, _VP, _VP]),
     "bdc_gemm_workspace": (_SZ, [_I, _I, _I, _I, _I]),
     "bdc_gemm": (_I, [_I, _I, _I, _VP, _I, _VP, _I, _VP, _I, _I, _I, _VP, _SZ, _VP]),
     "bdc_mlp_param_count": (_I, []),
@@ -251,6 +252,25 @@ def deflate(d, z, tol, stream=None):
     dval = torch.empty(m, dtype=torch.float64, device=d.device)
     _check("bdc_deflate", lib().bdc_deflate(m, _ptr(d), _ptr(z), float(tol), _ptr(keep), _ptr(zout), _ptr(dval),
                                              _stream(stream)))
+    return keep, zout, dval
+
+
+NOALLOC_MAX = 65536
+
+
+def deflate_noalloc(d, z, tol, stream=None):
+    """bdc_deflate_noalloc: deflation with the library's fixed device scratch.
+
+    For callers that cannot allocate device memory during the call; m is at
+    most NOALLOC_MAX and calls that overlap on the GPU must be ordered.
+    """
+    d, z = _dev(d), _dev(z)
+    m = d.shape[0]
+    keep = torch.empty(m, dtype=torch.int32, device=d.device)
+    zout = torch.empty(m, dtype=torch.float64, device=d.device)
+    dval = torch.empty(m, dtype=torch.float64, device=d.device)
+    _check("bdc_deflate_noalloc", lib().bdc_deflate_noalloc(m, _ptr(d), _ptr(z), float(tol), _ptr(keep), _ptr(zout),
+                                                             _ptr(dval), _stream(stream)))
     return keep, zout, dval
 
 

@@ -20,6 +20,8 @@
 // uses the original z, so survivors of it are found with a block scan; the
 // close-value test only compares consecutive survivors, so chains of close
 // values are independent and each is walked by one thread.
+#include <mutex>
+
 #include "bdc_internal.cuh"
 
 namespace bdc {
@@ -521,3 +523,70 @@ cudaError_t launch_deflate_single(int m, const double *d, const double *z, doubl
 }
 
 }  // namespace bdc
+
+// ---------------------------------------------------------------------------
+// Allocation-free deflation.
+//
+// bdc_deflate above obtains its scratch with cudaMallocAsync.  Some callers
+// cannot allocate device memory at the moment they call: code that runs
+// while another component owns the device allocator (a framework caching
+// allocator, or an application that reserves all memory up front and treats
+// any further allocation as a failure), and latency-critical loops that must
+// not touch the driver's allocator at all.  For them bdc_deflate_noalloc does
+// the same work with its scratch in a fixed array that lives in the module's
+// global memory for as long as the library is loaded (on every device that
+// loads it).  Only the problem size is limited: m <= BDC_DEFLATE_NOALLOC_MAX.
+//
+// The array is shared by every call: calls whose kernels overlap on the GPU
+// (different streams without ordering) race on it and must be serialised by
+// the caller.  Every scratch entry a call reads is written earlier by the
+// same call, so nothing has to be cleared between calls.
+// ---------------------------------------------------------------------------
+namespace bdc {
+namespace {
+
+constexpr int kNoAllocMax = BDC_DEFLATE_NOALLOC_MAX;
+constexpr size_t kNoAllocDoubles = 3 * (size_t)kNoAllocMax;   // zs, rc, rs
+constexpr size_t kNoAllocInts = 3 * (size_t)kNoAllocMax;      // slist, sidx, role
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocDoubles * sizeof(double) +
+                                                                  kNoAllocInts * sizeof(int)];
+
+// device address of g_noalloc_scratch, looked up once per device (the host
+// symbol is only a stand-in and must never be passed to a kernel)
+constexpr int kMaxDevices = 64;
+void *g_noalloc_ptr[kMaxDevices] = {nullptr};
+std::mutex g_noalloc_mu;
+
+cudaError_t noalloc_scratch(void **out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace bdc
+
+extern "C" int bdc_deflate_noalloc(int m, const double *d, const double *z, double tol, int *keep, double *zout,
+                                   double *dval, bdc_stream_t stream) {
+    using namespace bdc;
+    if (m < 0 || m > kNoAllocMax) return -1;
+    if (m > 0 && (!d || !z || !keep || !zout || !dval)) return -2;
+    if (!(tol >= 0.0)) return -4;
+    if (m == 0) return 0;
+    void *base = nullptr;
+    if (noalloc_scratch(&base) != cudaSuccess) return BDC_ERR_CUDA;
+    double *sd = (double *)base;
+    int *si = (int *)((char *)base + kNoAllocDoubles * sizeof(double));
+    k_deflate_single<<<1, PREP_THREADS, 0, (cudaStream_t)stream>>>(m, d, z, tol, keep, zout, dval, si, sd);
+    return cudaGetLastError() == cudaSuccess ? 0 : BDC_ERR_CUDA;
+}
