@@ -345,8 +345,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
     const int p = lo;
     const GemmProb pr = probs[p];
     const MixProb mx = mix[p];
+    // grouped rasterization: bands of 8 row blocks walk the column blocks
+    // together, so the CTAs resident at one time share A and B tiles in L2
     const int t = blockIdx.x - mx.tile0;
-    const int m0 = (t / mx.tilesN) * TM, n0 = (t % mx.tilesN) * TNX;
+    const int tilesM = (mx.Mmax + TM - 1) / TM;
+    constexpr int G = 8;
+    const int band = t / (G * mx.tilesN), in_band = t % (G * mx.tilesN);
+    const int bm0 = band * G, bsz = min(G, tilesM - bm0);
+    const int m0 = (bm0 + in_band % bsz) * TM, n0 = (in_band / bsz) * TNX;
     if (m0 >= pr.M || n0 >= pr.N || pr.K <= 0) return;
     const int nk = (pr.K + TK - 1) / TK;
 
@@ -382,26 +388,38 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer (one lane)
         if (lane == 0) {
-            auto mma = [&](uint32_t col, uint32_t a, uint32_t b, uint32_t acc) {
-                asm volatile(
-                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, "
-                    "p;\n}\n" ::"r"(tmem + col),
-                    "l"(sdesc(a)), "l"(sdesc(b)), "r"(idesc), "r"(acc)
-                    : "memory");
-            };
+            // descriptors of every slice tile of both ring buffers, computed once;
+            // the K step of 16 (32 B) adds 2 to the 16-byte address field
+            uint64_t dA[NSTAGE][S], dB[NSTAGE][S];
+#pragma unroll
+            for (int b = 0; b < NSTAGE; ++b)
+#pragma unroll
+                for (int i = 0; i < S; ++i) {
+                    const uint32_t a = smem_u32(smem + b * STAGE_BYTES + i * TILE);
+                    dA[b][i] = sdesc(a);
+                    dB[b][i] = sdesc(a + S * TILE);
+                }
             bool ok = true;
             for (int s = 0; s < nk && ok; ++s) {
                 const int buf = s & 1;
                 if (!mbar_wait(&full[buf], (s >> 1) & 1, err, abort_flag)) { ok = false; break; }
                 fence_after();
-                const uint32_t bA = smem_u32(smem + buf * STAGE_BYTES);
-                const uint32_t bB = bA + S * TILE;
+                // operand "addresses" below are (buffer, tile index, K step) handles
+                auto mma = [&](uint32_t col, int ia, int ib, int kk, uint32_t acc) {
+                    const uint64_t a = (buf ? dA[1][ia] : dA[0][ia]) + 2 * kk;
+                    const uint64_t b = (buf ? dB[1][ib] : dB[0][ib]) + 2 * kk;
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, "
+                        "p;\n}\n" ::"r"(tmem + col),
+                        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+                        : "memory");
+                };
                 if constexpr (MODE == MODE_X3) {
 #pragma unroll
                     for (int kk = 0; kk < 2; ++kk) {
-                        mma(0, bA + kk * 32, bB + kk * 32, (s == 0 && kk == 0) ? 0u : 1u);
-                        mma(0, bA + kk * 32, bB + TILE + kk * 32, 1u);
-                        mma(0, bA + TILE + kk * 32, bB + kk * 32, 1u);
+                        mma(0, 0, 0, kk, (s == 0 && kk == 0) ? 0u : 1u);
+                        mma(0, 0, 1, kk, 1u);
+                        mma(0, 1, 0, kk, 1u);
                     }
                     umma_commit(&empty[buf]);
                     if (s == nk - 1) umma_commit(&accfull[0]);
@@ -417,8 +435,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
 #pragma unroll
                         for (int i = 0; i <= 4; ++i)
                             if (i < S && 4 - i < S)
-                                mma(c4, bA + i * TILE + kk * 32, bB + (4 - i) * TILE + kk * 32,
-                                    (kk == 0 && i == 0) ? 0u : 1u);
+                                mma(c4, i, 4 - i, kk, (kk == 0 && i == 0) ? 0u : 1u);
                         bool first = true;
 #pragma unroll
                         for (int g = 5; g <= S - 1; ++g)
@@ -426,8 +443,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
                             for (int i = 0; i <= g; ++i) {
                                 const int j = g - i;
                                 if (i >= S || j >= S) continue;
-                                mma(cl, bA + i * TILE + kk * 32, bB + j * TILE + kk * 32,
-                                    (kk == 0 && first) ? 0u : 1u);
+                                mma(cl, i, j, kk, (kk == 0 && first) ? 0u : 1u);
                                 first = false;
                             }
                     }
@@ -438,24 +454,18 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
                     auto issueA = [&](bool fresh) {
 #pragma unroll
                         for (int kk = 0; kk < 2; ++kk) {
-                            mma(0, bA + kk * 32, bB + kk * 32, (fresh && kk == 0) ? 0u : 1u);
+                            mma(0, 0, 0, kk, (fresh && kk == 0) ? 0u : 1u);
 #pragma unroll
-                            for (int i = 0; i <= 3; ++i)
-                                mma(384, bA + i * TILE + kk * 32, bB + (3 - i) * TILE + kk * 32,
-                                    (fresh && kk == 0 && i == 0) ? 0u : 1u);
+                            for (int i = 0; i <= 3; ++i) mma(384, i, 3 - i, kk, (fresh && kk == 0 && i == 0) ? 0u : 1u);
                         }
                     };
                     auto issueB = [&](bool fresh) {
 #pragma unroll
                         for (int kk = 0; kk < 2; ++kk) {
 #pragma unroll
-                            for (int i = 0; i <= 1; ++i)
-                                mma(128, bA + i * TILE + kk * 32, bB + (1 - i) * TILE + kk * 32,
-                                    (fresh && kk == 0 && i == 0) ? 0u : 1u);
+                            for (int i = 0; i <= 1; ++i) mma(128, i, 1 - i, kk, (fresh && kk == 0 && i == 0) ? 0u : 1u);
 #pragma unroll
-                            for (int i = 0; i <= 2; ++i)
-                                mma(256, bA + i * TILE + kk * 32, bB + (2 - i) * TILE + kk * 32,
-                                    (fresh && kk == 0 && i == 0) ? 0u : 1u);
+                            for (int i = 0; i <= 2; ++i) mma(256, i, 2 - i, kk, (fresh && kk == 0 && i == 0) ? 0u : 1u);
                         }
                     };
                     if ((s & 1) == 0) {
@@ -485,7 +495,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
         const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16) + 64 * half;
         bool ok = true;
         if constexpr (MODE == MODE_E) {
-            long long L[64];
+            // unsigned: the magic offsets wrap modulo 2^64 and cancel exactly at the end
+            unsigned long long L[64];
 #pragma unroll
             for (int i = 0; i < 64; ++i) L[i] = 0;
             int cA = 0, cB = 0;
@@ -501,8 +512,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
                         tmem_wait_ld();
 #pragma unroll
                         for (int i = 0; i < 16; ++i) {
-                            const int tt = exact_int(v1[i], 256.0f) * 256 + exact_int(v2[i], 65536.0f);
-                            L[16 * cb + i] += (long long)tt * 256;     // I_1 2^16 + I_2 2^8
+                            // raw magic bits b = I + 0x4B400000; the offsets are removed once at the end
+                            const unsigned b1 = __float_as_uint(fmaf(v1[i], 256.0f, 12582912.0f));
+                            const unsigned b2 = __float_as_uint(fmaf(v2[i], 65536.0f, 12582912.0f));
+                            L[16 * cb + i] += ((unsigned long long)b1 << 16) + ((unsigned long long)b2 << 8);
                         }
                     }
                     fence_before();
@@ -519,9 +532,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
                         tmem_ld16(tl + 384 + 16 * cb, v3);
                         tmem_wait_ld();
 #pragma unroll
-                        for (int i = 0; i < 16; ++i)
-                            L[16 * cb + i] += ((long long)exact_int(v0[i], 1.0f) << 24) +
-                                              exact_int(v3[i], 16777216.0f);   // I_0 2^24 + I_3
+                        for (int i = 0; i < 16; ++i) {
+                            const unsigned b0 = __float_as_uint(fmaf(v0[i], 1.0f, 12582912.0f));
+                            const unsigned b3 = __float_as_uint(fmaf(v3[i], 16777216.0f, 12582912.0f));
+                            L[16 * cb + i] += ((unsigned long long)b0 << 24) + (unsigned long long)b3;
+                        }
                     }
                     fence_before();
                     mbar_arrive(&accempty[0]);
@@ -529,12 +544,18 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
                 }
             }
             if (ok) {
+                // remove the magic offsets: every set-A drain added M (2^24 + 1),
+                // every set-B drain M (2^16 + 2^8), M = 0x4B400000
+                const unsigned long long M = 0x4B400000ull;
+                const unsigned long long corr =
+                    (unsigned long long)cA * M * ((1ull << 24) + 1) + (unsigned long long)cB * M * ((1ull << 16) + (1ull << 8));
                 const int Er = (row < pr.M) ? Ea[mx.a_row0 + row] : 0;
 #pragma unroll
                 for (int i = 0; i < 64; ++i) {
                     const int col = n0 + 64 * half + i;
                     if (row < pr.M && col < pr.N)
-                        pr.C[(size_t)col * pr.ldc + row] = ldexp_safe((double)L[i], Er + Fb[mx.b_col0 + col] - 40);
+                        pr.C[(size_t)col * pr.ldc + row] =
+                            ldexp_safe((double)(long long)(L[i] - corr), Er + Fb[mx.b_col0 + col] - 40);
                 }
             }
         } else if constexpr (MODE == MODE_L) {
