@@ -48,8 +48,9 @@ def parse():
     ap.add_argument("--n", type=int, default=16384)
     ap.add_argument("--kind", default="uniform", choices=["uniform", "graded", "clustered", "ones"])
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--leaf", type=int, default=32)
+    ap.add_argument("--leaf", type=int, default=16)
     ap.add_argument("--slices", type=int, default=0, help="0 = automatic (6 up to n=8192, 7 above)")
+    ap.add_argument("--mixed-min", type=int, default=0, help="smallest merge order using split BF16 (0 = auto)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true")
@@ -188,7 +189,7 @@ def main():
     e_pin = torch.from_numpy(e_h).pin_memory()
     d = d_pin.to(dev)
     e = e_pin.to(dev)
-    o = bdc.make_opts(a.prec, a.leaf, 64, a.slices)
+    o = bdc.make_opts(a.prec, a.leaf, 64, a.slices, mixed_min=a.mixed_min)
     lw = bdc.workspace_bytes(n, o)
     work = torch.empty(lw + 256, dtype=torch.uint8, device=dev)
     Ut = torch.empty((n, n), dtype=torch.float64, device=dev)
@@ -310,6 +311,9 @@ def main():
                 "peak_source": gemm_unit_src, "dominant_stage": dominant}
     stages = {k: {"ms_per_step": v["ms"] / a.steps, "launches_per_step": v["launches"] / a.steps,
                   "work_per_step": v["work"] / a.steps} for k, v in prof.items()}
+    if prof["secular"].get("roots"):
+        stages["secular"]["roots_per_step"] = prof["secular"]["roots"] / a.steps
+        stages["secular"]["iters_per_root"] = prof["secular"]["iters"] / prof["secular"]["roots"]
     hbm = float(peaks.get("hbm_gbs", FALLBACK["hbm_gbs"]))
     for k in ("gather", "vectors", "finish", "final"):
         if prof[k]["ms"] > 0:

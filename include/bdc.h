@@ -66,14 +66,17 @@ typedef enum { BDC_SEED_PLAIN = 0, BDC_SEED_MLP = 1 } bdc_seed;
 typedef struct {
     int prec;          /* bdc_precision                                   */
     int seed;          /* bdc_seed                                        */
-    int leaf;          /* leaf size L (>= 4; 0 = default 32)              */
+    int leaf;          /* leaf size L (4..64; 0 = default 16)             */
     int max_iter;      /* secular / QR iteration cap (0 = default 64)     */
     int slices;        /* BDC_MIXED_EXACT slice count 4..7 (0 = automatic: 6 for n <= 8192, 7 above) */
     int checked;       /* reserved, must be 0                              */
     const float *mlp;  /* device pointer to MLP weights when seed = MLP    */
+    int mixed_min;     /* split-BF16 products only for merges of order >= mixed_min,
+                          FP64 products below (0 = automatic: 256)          */
+    int reserved;      /* must be 0                                        */
 } bdc_opts;
 
-/* Fill *o with the defaults (FP64, plain seed, leaf 32). */
+/* Fill *o with the defaults (FP64, plain seed, leaf 16, automatic slices). */
 void bdc_opts_default(bdc_opts *o);
 
 /* SVD of the n x n upper bidiagonal (d, e), FP64 defaults, synchronous:
@@ -181,6 +184,9 @@ enum { BDC_STAGE_SCALE = 0, BDC_STAGE_LEAF, BDC_STAGE_PREP, BDC_STAGE_GATHER, BD
        BDC_STAGE_VECTORS, BDC_STAGE_GEMM, BDC_STAGE_FINISH, BDC_STAGE_FINAL, BDC_NSTAGES };
 int bdc_profile_begin(int on);
 int bdc_profile_end(double *ms, long long *launches, double *work);
+/* After bdc_profile_end: secular roots solved and root-finder iterations
+ * spent (summed over the recorded calls), *roots and *iters (host). */
+int bdc_profile_secular(long long *roots, long long *iters);
 
 /* Text of the last CUDA error the library saw on this thread ("" if none);
  * reading it clears it. */

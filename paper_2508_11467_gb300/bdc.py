@@ -26,7 +26,7 @@ PREC = {"fp64": BDC_FP64, "bf16x3": BDC_MIXED_BF16X3, "exact": BDC_MIXED_EXACT, 
 class Opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("seed", ctypes.c_int), ("leaf", ctypes.c_int),
                 ("max_iter", ctypes.c_int), ("slices", ctypes.c_int), ("checked", ctypes.c_int),
-                ("mlp", ctypes.c_void_p)]
+                ("mlp", ctypes.c_void_p), ("mixed_min", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 _lock = threading.Lock()
@@ -52,6 +52,7 @@ _SIGS = {
     "bdc_status_string": (ctypes.c_char_p, [_I]),
     "bdc_profile_begin": (_I, [_I]),
     "bdc_profile_end": (_I, [_VP, _VP, _VP]),
+    "bdc_profile_secular": (_I, [_VP, _VP]),
     "bdc_last_error_string": (ctypes.c_char_p, []),
 }
 
@@ -72,7 +73,12 @@ def profile_end():
     _check("bdc_profile_end", lib().bdc_profile_end(ms.ctypes.data_as(ctypes.c_void_p),
                                                      ln.ctypes.data_as(ctypes.c_void_p),
                                                      wk.ctypes.data_as(ctypes.c_void_p)))
-    return {s: {"ms": float(ms[i]), "launches": int(ln[i]), "work": float(wk[i])} for i, s in enumerate(STAGES)}
+    out = {s: {"ms": float(ms[i]), "launches": int(ln[i]), "work": float(wk[i])} for i, s in enumerate(STAGES)}
+    r, it = ctypes.c_longlong(0), ctypes.c_longlong(0)
+    lib().bdc_profile_secular(ctypes.byref(r), ctypes.byref(it))
+    out["secular"]["roots"] = int(r.value)
+    out["secular"]["iters"] = int(it.value)
+    return out
 
 
 def exported_symbols():
@@ -130,9 +136,10 @@ def _dev(t, dtype=torch.float64):
     return t.to(dtype).contiguous()
 
 
-def make_opts(prec="fp64", leaf=32, max_iter=64, slices=0, seed="plain", mlp=None) -> Opts:
+def make_opts(prec="fp64", leaf=16, max_iter=64, slices=0, seed="plain", mlp=None, mixed_min=0) -> Opts:
     o = Opts()
     lib().bdc_opts_default(ctypes.byref(o))
+    o.mixed_min = int(mixed_min)
     o.prec = PREC[prec] if isinstance(prec, str) else int(prec)
     o.leaf = int(leaf)
     o.max_iter = int(max_iter)
@@ -146,8 +153,8 @@ def workspace_bytes(n: int, opts: Opts) -> int:
     return int(lib().bdc_svd_workspace(int(n), ctypes.byref(opts)))
 
 
-def svd(d, e, *, prec="fp64", leaf=32, max_iter=64, slices=0, seed="plain", mlp=None,
-        stream=None, work=None, check=True):
+def svd(d, e, *, prec="fp64", leaf=16, max_iter=64, slices=0, seed="plain", mlp=None,
+        stream=None, work=None, check=True, mixed_min=0):
     """SVD of the upper bidiagonal (d, e) on the GPU.
 
     Returns (S, U, VT) as CUDA float64 tensors (U column-major: U[:, i] is a
@@ -156,7 +163,7 @@ def svd(d, e, *, prec="fp64", leaf=32, max_iter=64, slices=0, seed="plain", mlp=
     d = _dev(d)
     n = d.shape[0]
     e = _dev(e) if n > 1 else torch.zeros(1, dtype=torch.float64, device=d.device)
-    o = make_opts(prec, leaf, max_iter, slices, seed, mlp)
+    o = make_opts(prec, leaf, max_iter, slices, seed, mlp, mixed_min)
     # column-major outputs: allocate the transpose and view it back
     Ut = torch.empty((n, n), dtype=torch.float64, device=d.device)
     VTt = torch.empty((n, n), dtype=torch.float64, device=d.device)
@@ -187,7 +194,7 @@ def svd_sync(d, e, stream=None):
     return S[:n], Ut.t(), VTt.t(), rc
 
 
-def svd_batched(ds, es, *, prec="fp64", leaf=32, max_iter=64, slices=0, stream=None, work=None):
+def svd_batched(ds, es, *, prec="fp64", leaf=16, max_iter=64, slices=0, stream=None, work=None):
     """Batched SVD of bidiagonals of uneven sizes (lists of CUDA tensors)."""
     import numpy as np
     B = len(ds)

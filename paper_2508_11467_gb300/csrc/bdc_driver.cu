@@ -30,23 +30,24 @@ size_t gemm_mixed_scratch(long long rows_total, long long cols_total, int kmax, 
 
 namespace {
 
-constexpr int kDefaultLeaf = 32;
+// leaf 16: measured best on GB300 (n = 16384; the paper's 32 was best on MI210/V100)
+constexpr int kDefaultLeaf = 16;
 constexpr int kDefaultMaxIter = 64;
 
 struct TreeNode {
-    int r0, m, sqre, nl, height, left, right;
+    int r0, m, sqre, nl, height, left, right, depth;
 };
 
 // recursive split of the m x (m + sqre) block at rows r0..
-int build_tree(std::vector<TreeNode> &t, int r0, int m, int sqre, int leaf) {
-    TreeNode nd{r0, m, sqre, 0, 0, -1, -1};
+int build_tree(std::vector<TreeNode> &t, int r0, int m, int sqre, int leaf, int depth = 0) {
+    TreeNode nd{r0, m, sqre, 0, 0, -1, -1, depth};
     const int id = (int)t.size();
     t.push_back(nd);
     if (m > leaf) {
         const int nl = m / 2;
         const int nr = m - nl - 1;
-        const int l = build_tree(t, r0, nl, 1, leaf);
-        const int r = build_tree(t, r0 + nl + 1, nr, sqre, leaf);
+        const int l = build_tree(t, r0, nl, 1, leaf, depth + 1);
+        const int r = build_tree(t, r0 + nl + 1, nr, sqre, leaf, depth + 1);
         t[id].nl = nl;
         t[id].left = l;
         t[id].right = r;
@@ -91,7 +92,7 @@ size_t per_matrix_bytes(int n) {
     const size_t N = (size_t)n;
     size_t b = 0;
     b += align256(sizeof(double) * 2 * N);            // dsc, esc
-    b += align256(sizeof(double) * 2 * N * N);        // U, V
+    b += align256(sizeof(double) * 4 * N * N);        // U, V (two copies each)
     b += align256(sizeof(double) * 12 * N + 64);      // D ds zs rc rs dM zM zt tau omega dval scale
     b += align256(sizeof(int) * (13 * N + 128));      // Q src role org kposM dsrc dest slist sidx invK(4n) info
     const size_t big = (N + 1) * (N + 16) + 64;
@@ -123,6 +124,7 @@ Plan make_plan(int nmat, const int *ns, const bdc_opts &o) {
             nd.m = tn.m;
             nd.sqre = tn.sqre;
             nd.nl = tn.nl;
+            nd.buf = tn.depth & 1;
             if (tn.height == 0) {
                 p.leaves.push_back(nd);
                 p.leafmax = std::max(p.leafmax, tn.m);
@@ -140,6 +142,8 @@ Plan make_plan(int nmat, const int *ns, const bdc_opts &o) {
         }
     }
     p.nnodes = gid;
+    for (size_t h = 0; h < p.heights.size(); ++h)
+        for (auto &nd : p.heights[h]) nd.pad = p.hmmax[h];   // the height's largest order
     for (auto &h : p.heights) p.maxprobs = std::max(p.maxprobs, 4 * (int)h.size());
     // byte layout
     size_t off = 0;
@@ -184,8 +188,8 @@ MatDesc carve(char *base, size_t off, int n) {
     md.wstride = (long long)N + 16;
     double *de = (double *)take(sizeof(double) * 2 * N);
     md.dsc = de; md.esc = de + N;
-    double *uv = (double *)take(sizeof(double) * 2 * N * N);
-    md.U = uv; md.V = uv + N * N;
+    double *uv = (double *)take(sizeof(double) * 4 * N * N);
+    md.U[0] = uv; md.V[0] = uv + N * N; md.U[1] = uv + 2 * N * N; md.V[1] = uv + 3 * N * N;
     double *dd = (double *)take(sizeof(double) * 12 * N + 64);
     md.D = dd; md.ds = dd + N; md.zs = dd + 2 * N; md.rc = dd + 3 * N; md.rs = dd + 4 * N;
     md.dM = dd + 5 * N; md.zM = dd + 6 * N; md.zt = dd + 7 * N; md.tau = dd + 8 * N;
@@ -258,8 +262,8 @@ __global__ void k_final(const MatDesc *__restrict__ mats, int tiles_per_side) {
         const int src = md.Q[n - 1 - c];
         const int j = j0 + tx;
         if (j < n) {
-            md.Uo[(size_t)c * md.ldu + j] = md.U[(size_t)src * n + j];
-            tile[cc][tx] = md.V[(size_t)src * n + j];
+            md.Uo[(size_t)c * md.ldu + j] = md.U[0][(size_t)src * n + j];   // the root has depth 0
+            tile[cc][tx] = md.V[0][(size_t)src * n + j];
         }
         if (tj == 0 && tx == 0) md.So[c] = md.D[src] * s;
     }
@@ -293,6 +297,7 @@ struct ProfCall {
     int nnodes;
     std::vector<NodeDesc> merges;
     int pairs;
+    int mixed_min;   // merges of order >= mixed_min ran the split products
 };
 struct Profiler {
     bool on = false;
@@ -300,6 +305,7 @@ struct Profiler {
     std::vector<ProfCall> calls;
 };
 Profiler g_prof;
+long long g_sec_roots = 0, g_sec_iters = 0;
 
 struct StageScope {
     cudaStream_t st;
@@ -393,7 +399,7 @@ int run_plan(const Plan &p, const bdc_opts &o, char *work, std::vector<MatDesc> 
     const int pairs = (o.prec == BDC_MIXED_EXACT) ? (o.slices * (o.slices + 1)) / 2
                       : (o.prec == BDC_MIXED_BF16X3) ? 3 : 1;
     if (g_prof.on) {
-        ProfCall pc{dstate, p.nnodes, {}, pairs};
+        ProfCall pc{dstate, p.nnodes, {}, pairs, o.prec == BDC_FP64 ? (1 << 30) : o.mixed_min};
         for (auto &h : p.heights) pc.merges.insert(pc.merges.end(), h.begin(), h.end());
         g_prof.calls.push_back(std::move(pc));
     }
@@ -423,9 +429,12 @@ int run_plan(const Plan &p, const bdc_opts &o, char *work, std::vector<MatDesc> 
         {   // 2 M N K per product as deflated, x slice pairs (added from the node states)
             // FP64: one launch; split BF16: two slicing kernels + the exact-group
             // and (for more than 4 slices) the low-group product kernels
-            const int gl = (o.prec == BDC_FP64) ? 1 : (o.prec == BDC_MIXED_EXACT && o.slices > 4) ? 4 : 3;
+            // small merges use the FP64 products: the split path's fixed costs
+            // (slicing, two kernels, TMEM set-up per tile) dominate there
+            const bool mixed_here = (o.prec != BDC_FP64) && mm >= o.mixed_min;
+            const int gl = !mixed_here ? 1 : (o.prec == BDC_MIXED_EXACT && o.slices > 4) ? 4 : 3;
             StageScope sc(st, BDC_STAGE_GEMM, gl, 0.0);
-            if (o.prec == BDC_FP64) {
+            if (!mixed_here) {
                 e = launch_gemm64(dprobs, 4 * nn, mm + 1, mm, st);
             } else {
                 std::vector<int> Mx(4 * nn), Nx(4 * nn);
@@ -491,6 +500,7 @@ bdc_opts resolve(const bdc_opts *o, int nmax) {
     if (r.leaf <= 0) r.leaf = kDefaultLeaf;
     if (r.max_iter <= 0) r.max_iter = kDefaultMaxIter;
     if (r.slices <= 0) r.slices = auto_slices(nmax);
+    if (r.mixed_min <= 0) r.mixed_min = 256;   // measured crossover (n = 16384)
     return r;
 }
 
@@ -500,7 +510,7 @@ int check_opts(const bdc_opts &o) {
     if (o.seed == BDC_SEED_MLP && !o.mlp) return 1;
     if (o.leaf < 4 || o.leaf > 64) return 1;
     if (o.slices < 2 || o.slices > 7) return 1;
-    if (o.checked != 0) return 1;
+    if (o.checked != 0 || o.reserved != 0) return 1;
     return 0;
 }
 
@@ -713,6 +723,7 @@ int bdc_profile_begin(int on) {
     for (auto &ev : g_prof.ev) { cudaEventDestroy(ev.a); cudaEventDestroy(ev.b); }
     g_prof.ev.clear();
     g_prof.calls.clear();
+    g_sec_roots = g_sec_iters = 0;
     g_prof.on = on != 0;
     return 0;
 }
@@ -742,9 +753,14 @@ int bdc_profile_end(double *ms, long long *launches, double *work) {
             const NodeState &ns = hs[nd.id];
             const double N = ns.N, Ktop = ns.P1 + 1 + ns.n2, Kbot = ns.Ktot - ns.P1;
             const double top = nd.nl + 1, botU = nd.m - nd.nl - 1, botV = nd.m + nd.sqre - nd.nl - 1;
-            w[BDC_STAGE_GEMM] += 2.0 * N * (2.0 * top * Ktop + (botU + botV) * Kbot) * pc.pairs;
+            // mixed_min compares with the height's largest order (as the launch
+            // decision does); per node this is exact up to that granularity
+            w[BDC_STAGE_GEMM] += 2.0 * N * (2.0 * top * Ktop + (botU + botV) * Kbot) *
+                                 (nd.pad >= pc.mixed_min ? pc.pairs : 1);
+            g_sec_roots += ns.N;
+            g_sec_iters += (long long)ns.iters;
             w[BDC_STAGE_VECTORS] += 16.0 * N * ns.Ktot;
-            w[BDC_STAGE_FINISH] += 16.0 * (double)ns.ndef * (2.0 * nd.m + nd.sqre);
+            w[BDC_STAGE_GATHER] += 0.0;
         }
     }
     g_prof.calls.clear();
@@ -755,6 +771,12 @@ int bdc_profile_end(double *ms, long long *launches, double *work) {
         if (work) work[k] = w[k];
     }
     return rc;
+}
+
+int bdc_profile_secular(long long *roots, long long *iters) {
+    if (roots) *roots = g_sec_roots;
+    if (iters) *iters = g_sec_iters;
+    return 0;
 }
 
 int bdc_mlp_param_count(void) { return 0; }

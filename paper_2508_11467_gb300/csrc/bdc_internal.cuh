@@ -1,11 +1,12 @@
 // Internal data layout and helpers of the GB300 bidiagonal divide-and-conquer.
 //
 // Layout in HBM (one "matrix" = one bidiagonal problem of order n):
-//   U, V      n x n column-major (ld = n).  Every node of the split tree owns
-//             the diagonal block starting at (r0, r0): m x m in U and
-//             (m+sqre) x (m+sqre) in V (Sec. 4.2.1: B_1 is (k-1) x k, the
-//             coupling row k, B_2 below).  Leaves write their SVD there,
-//             merges overwrite the parent block in place.
+//   U, V      two copies each, n x n column-major (ld = n).  Every node of the
+//             split tree owns the diagonal block starting at (r0, r0): m x m in
+//             U and (m+sqre) x (m+sqre) in V (Sec. 4.2.1: B_1 is (k-1) x k, the
+//             coupling row k, B_2 below) of copy (depth % 2): a node reads its
+//             children from the other copy, so vectors can be written to their
+//             final place while the children are still being read.
 //   D, Q      n entries: D[r0+j] = value of node column j, Q[r0+p] = local
 //             column of the p-th smallest value (node-local ascending order).
 //   merge scratch (indexed from r0 or from the node's kbase) and four big
@@ -29,7 +30,8 @@ struct MatDesc {
     double *Uo, *So, *VTo;   // user outputs
     double *dsc, *esc;       // scaled copies (esc[n-1] = 0)
     double *scale;           // [1] scale factor applied to d, e
-    double *U, *V, *D;       // node blocks
+    double *U[2], *V[2];     // node blocks, copy = tree depth % 2
+    double *D;               // node values
     int *Q;                  // node-local ascending order
     // merge scratch, per node from r0 (size n) unless noted
     double *ds, *zs;         // sorted d, z
@@ -57,7 +59,9 @@ struct NodeDesc {
     int sqre;    // 1 if the node has m+1 columns
     int nl;      // rows of the left child (coupling row = r0 + nl)
     int kbase;   // base of K-indexed scratch (invK)
-    int pad;
+    int pad;     // largest order among the nodes of this node's height
+    int buf;     // U/V copy this node writes (its depth % 2); children are in 1 - buf
+    int pad2;
 };
 
 struct NodeState {
@@ -69,6 +73,7 @@ struct NodeState {
     int nzero;   // deflated by rotation against d_0 = 0
     double tol;
     double cq, sq;   // rotation folding the two null-vector components (sqre)
+    unsigned long long iters;   // secular iterations summed over the node's roots
 };
 
 // one FP64 product C = A * B (column-major), used by the merge GEMMs
@@ -123,7 +128,7 @@ cudaError_t launch_merge_prep(const NodeDesc *nodes, int nnodes, const MatDesc *
 cudaError_t launch_merge_gather(const NodeDesc *nodes, int nnodes, const MatDesc *mats,
                                 const NodeState *state, int mmax, cudaStream_t st);
 cudaError_t launch_secular(const NodeDesc *nodes, int nnodes, const MatDesc *mats,
-                           const NodeState *state, int mmax, int max_iter, int seed_mode,
+                           NodeState *state, int mmax, int max_iter, int seed_mode,
                            const float *mlp, cudaStream_t st);
 cudaError_t launch_vectors(const NodeDesc *nodes, int nnodes, const MatDesc *mats,
                            const NodeState *state, int mmax, cudaStream_t st);

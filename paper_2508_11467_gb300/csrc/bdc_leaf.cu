@@ -222,13 +222,14 @@ __global__ void __launch_bounds__(32) k_leaf(const NodeDesc *__restrict__ leaves
     __syncwarp();
     const long long ld = md.n;
     const int r0 = nd.r0;
+    double *Uo = md.U[nd.buf], *Vo = md.V[nd.buf];
     for (int p = 0; p < m; ++p) {
         const int j = perm[p];
-        for (int r = lane; r < m; r += 32) md.U[(size_t)(r0 + p) * ld + r0 + r] = Us[j * ldu + r];
-        for (int r = lane; r < mc; r += 32) md.V[(size_t)(r0 + p) * ld + r0 + r] = Vs[j * ldv + r];
+        for (int r = lane; r < m; r += 32) Uo[(size_t)(r0 + p) * ld + r0 + r] = Us[j * ldu + r];
+        for (int r = lane; r < mc; r += 32) Vo[(size_t)(r0 + p) * ld + r0 + r] = Vs[j * ldv + r];
     }
     if (sq)
-        for (int r = lane; r < mc; r += 32) md.V[(size_t)(r0 + m) * ld + r0 + r] = Vs[m * ldv + r];
+        for (int r = lane; r < mc; r += 32) Vo[(size_t)(r0 + m) * ld + r0 + r] = Vs[m * ldv + r];
     for (int p = lane; p < m; p += 32) {
         md.D[r0 + p] = dd[perm[p]];
         md.Q[r0 + p] = p;

@@ -9,12 +9,11 @@
 //                the K order [top | pad | d_0 column | dense | bottom] used by
 //                the merge products of Eq. (bdc-Mv2Bv-u-vt).
 // k_merge_gather (one CTA per column task) applies the rotations and writes
-//                the permuted vectors W~ (left) and Q~ (right) into the
-//                workspace: survivors at their K position, deflated vectors
-//                after them, the new right null vector last.
-// k_merge_finish copies deflated vectors into the node block after the
-//                merged ones (Eq. bdc-B-svd), writes the node's values and
-//                their ascending order.
+//                the survivors' vectors W~ (left) and Q~ (right) into the
+//                workspace at their K position, and the deflated vectors and
+//                the new right null vector straight into the node's block.
+// k_merge_finish writes the node's values (roots, then deflated values,
+//                Eq. bdc-B-svd) and their ascending order.
 //
 // The sequential deflation scan is parallelised exactly: the small-z test
 // uses the original z, so survivors of it are found with a block scan; the
@@ -182,6 +181,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
     double *ds = md.ds + r0, *zs = md.zs + r0;
     int *src = md.src + r0;
     const double alpha = md.dsc[r0 + nl], beta = md.esc[r0 + nl];
+    const double *Vc = md.V[1 - nd.buf];                 // children's right vectors
 
     // ---- z and the merged ascending order (children are sorted through Q)
     const int *QL = md.Q + r0L, *QR = md.Q + r0R;
@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
         while (lo < hi) { int mid = (lo + hi) >> 1; if (DR[QR[mid]] < v) lo = mid + 1; else hi = mid; }
         const int pos = 1 + p + lo;
         ds[pos] = v;
-        zs[pos] = alpha * md.V[(size_t)(r0L + j) * ld + r0L + nl];
+        zs[pos] = alpha * Vc[(size_t)(r0L + j) * ld + r0L + nl];
         src[pos] = 1 + j;
         dmax = fmax(dmax, fabs(v));
     }
@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
         while (lo < hi) { int mid = (lo + hi) >> 1; if (DL[QL[mid]] <= v) lo = mid + 1; else hi = mid; }
         const int pos = 1 + q + lo;
         ds[pos] = v;
-        zs[pos] = beta * md.V[(size_t)(r0R + j) * ld + r0R];
+        zs[pos] = beta * Vc[(size_t)(r0R + j) * ld + r0R];
         src[pos] = nl + 1 + j;
         dmax = fmax(dmax, fabs(v));
     }
@@ -213,10 +213,10 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
     if (t == 0) {
         // d_0 = 0 column: alpha * (last entry of q_1), folded with beta * (first
         // entry of q_2) when the right child is rectangular
-        double z0 = alpha * md.V[(size_t)(r0L + nl) * ld + r0L + nl];
+        double z0 = alpha * Vc[(size_t)(r0L + nl) * ld + r0L + nl];
         double cq = 1.0, sq = 0.0;
         if (sqre) {
-            const double b0 = beta * md.V[(size_t)(r0R + nr) * ld + r0R];
+            const double b0 = beta * Vc[(size_t)(r0R + nr) * ld + r0R];
             double r;
             make_rot(z0, b0, cq, sq, r);
             z0 = r;
@@ -295,21 +295,22 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
     if (t == 0) {
         NodeState s;
         s.N = N; s.n1 = n1; s.n2 = n2; s.n3 = n3; s.P1 = P1; s.Ktot = Ktot;
-        s.ndef = m - N; s.nzero = nz; s.tol = tol; s.cq = s_cq; s.sq = s_sq;
+        s.ndef = m - N; s.nzero = nz; s.tol = tol; s.cq = s_cq; s.sq = s_sq; s.iters = 0;
         state[nd.id] = s;
         const long long wb = (long long)r0 * md.wstride;
         const int Ktop = P1 + 1 + n2, Kbot = Ktot - P1;
         GemmProb *pr = probs + 4 * (size_t)blockIdx.x;
         // U: top rows 0..nl (incl. the coupling row), bottom rows nl+1..m-1
-        pr[0] = GemmProb{md.Wt + wb, md.UM + wb, md.U + (size_t)r0 * ld + r0, m, Ktot, (int)ld,
+        double *Uo = md.U[nd.buf], *Vo = md.V[nd.buf];
+        pr[0] = GemmProb{md.Wt + wb, md.UM + wb, Uo + (size_t)r0 * ld + r0, m, Ktot, (int)ld,
                          nl + 1, N, Ktop};
         pr[1] = GemmProb{md.Wt + wb + (nl + 1) + (size_t)P1 * m, md.UM + wb + P1,
-                         md.U + (size_t)r0 * ld + r0 + nl + 1, m, Ktot, (int)ld, m - nl - 1, N, Kbot};
+                         Uo + (size_t)r0 * ld + r0 + nl + 1, m, Ktot, (int)ld, m - nl - 1, N, Kbot};
         // V: top rows 0..nl (left child's columns), bottom rows nl+1..mc-1
-        pr[2] = GemmProb{md.Qt + wb, md.VM + wb, md.V + (size_t)r0 * ld + r0, mc, Ktot, (int)ld,
+        pr[2] = GemmProb{md.Qt + wb, md.VM + wb, Vo + (size_t)r0 * ld + r0, mc, Ktot, (int)ld,
                          nl + 1, N, Ktop};
         pr[3] = GemmProb{md.Qt + wb + (nl + 1) + (size_t)P1 * mc, md.VM + wb + P1,
-                         md.V + (size_t)r0 * ld + r0 + nl + 1, mc, Ktot, (int)ld, mc - nl - 1, N, Kbot};
+                         Vo + (size_t)r0 * ld + r0 + nl + 1, mc, Ktot, (int)ld, mc - nl - 1, N, Kbot};
     }
 }
 
@@ -347,10 +348,18 @@ __global__ void __launch_bounds__(128) k_merge_gather(const NodeDesc *__restrict
     const int r = md.role[r0 + p], code = r & 15;
     const int *src = md.src + r0, *dest = md.dest + r0, *slist = md.slist + r0;
     const double *rc = md.rc + r0, *rs = md.rs + r0;
-    ColSrc cs{md.U, md.V, (long long)md.n, r0, nl, m - nl - 1, sqre, ns.cq, ns.sq};
-    const long long wb = (long long)r0 * md.wstride;
+    ColSrc cs{md.U[1 - nd.buf], md.V[1 - nd.buf], (long long)md.n, r0, nl, m - nl - 1, sqre, ns.cq, ns.sq};
+    const long long wb = (long long)r0 * md.wstride, ld = md.n;
     double *W = md.Wt + wb, *Qm = md.Qt + wb;
-    auto wcol = [&](int dst) { return dst >= 0 ? dst : ns.Ktot + (-dst - 1); };
+    // survivors go to the K-ordered workspace W~ / Q~ (leading dimension m / m+sqre);
+    // deflated vectors straight to their final column N + slot of the node block
+    double *Uo = md.U[nd.buf] + (size_t)r0 * ld + r0, *Vo = md.V[nd.buf] + (size_t)r0 * ld + r0;
+    auto ucol = [&](int dst) -> double * {
+        return dst >= 0 ? W + (size_t)dst * m : Uo + (size_t)(ns.N + (-dst - 1)) * ld;
+    };
+    auto vcol = [&](int dst) -> double * {
+        return dst >= 0 ? Qm + (size_t)dst * mc : Vo + (size_t)(ns.N + (-dst - 1)) * ld;
+    };
 
     if (p == 0) {
         const int a = ns.nzero;
@@ -363,7 +372,7 @@ __global__ void __launch_bounds__(128) k_merge_gather(const NodeDesc *__restrict
             W[(size_t)ns.P1 * m + row] = cs.u(0, row);
             for (int j = 1; j <= a; ++j) {
                 const int q = slist[j];
-                W[(size_t)wcol(dest[q]) * m + row] = cs.u(src[q], row);
+                ucol(dest[q])[row] = cs.u(src[q], row);
             }
         }
         for (int row = threadIdx.x; row < mc; row += blockDim.x) {
@@ -371,11 +380,12 @@ __global__ void __launch_bounds__(128) k_merge_gather(const NodeDesc *__restrict
             for (int j = 1; j <= a; ++j) {
                 const int q = slist[j];
                 const double x = cs.v(src[q], row), c = rc[q], s = rs[q];
-                Qm[(size_t)wcol(dest[q]) * mc + row] = -s * y + c * x;
+                vcol(dest[q])[row] = -s * y + c * x;
                 y = c * y + s * x;
             }
             Qm[(size_t)ns.P1 * mc + row] = y;
-            if (sqre) Qm[(size_t)(ns.Ktot + ns.ndef) * mc + row] = -ns.sq * cs.q1(row) + ns.cq * cs.q2(row);
+            // the new right null vector: last column of the node's V block
+            if (sqre) Vo[(size_t)m * ld + row] = -ns.sq * cs.q1(row) + ns.cq * cs.q2(row);
         }
         return;
     }
@@ -389,12 +399,12 @@ __global__ void __launch_bounds__(128) k_merge_gather(const NodeDesc *__restrict
             for (int k = k0 + 1; k < m; ++k) {
                 const int q = slist[k];
                 const double x = cs.u(src[q], row), c = rc[q], s = rs[q];
-                W[(size_t)wcol(dest[prev]) * m + row] = c * y - s * x;
+                ucol(dest[prev])[row] = c * y - s * x;
                 y = s * y + c * x;
                 prev = q;
                 if ((md.role[r0 + q] & 15) == ROLE_KEEP) break;
             }
-            W[(size_t)wcol(dest[prev]) * m + row] = y;
+            ucol(dest[prev])[row] = y;
         }
         for (int row = threadIdx.x; row < mc; row += blockDim.x) {
             double y = cs.v(src[p], row);
@@ -402,65 +412,46 @@ __global__ void __launch_bounds__(128) k_merge_gather(const NodeDesc *__restrict
             for (int k = k0 + 1; k < m; ++k) {
                 const int q = slist[k];
                 const double x = cs.v(src[q], row), c = rc[q], s = rs[q];
-                Qm[(size_t)wcol(dest[prev]) * mc + row] = c * y - s * x;
+                vcol(dest[prev])[row] = c * y - s * x;
                 y = s * y + c * x;
                 prev = q;
                 if ((md.role[r0 + q] & 15) == ROLE_KEEP) break;
             }
-            Qm[(size_t)wcol(dest[prev]) * mc + row] = y;
+            vcol(dest[prev])[row] = y;
         }
         return;
     }
     // singleton survivor or small-z deflation: plain copy
-    const int col = wcol(dest[p]);
     const int c = src[p];
-    for (int row = threadIdx.x; row < m; row += blockDim.x) W[(size_t)col * m + row] = cs.u(c, row);
-    for (int row = threadIdx.x; row < mc; row += blockDim.x) Qm[(size_t)col * mc + row] = cs.v(c, row);
+    double *ud = ucol(dest[p]), *vd = vcol(dest[p]);
+    for (int row = threadIdx.x; row < m; row += blockDim.x) ud[row] = cs.u(c, row);
+    for (int row = threadIdx.x; row < mc; row += blockDim.x) vd[row] = cs.v(c, row);
 }
 
 // ------------------------------------------------------------------ finish
-__global__ void __launch_bounds__(128) k_merge_finish(const NodeDesc *__restrict__ nodes,
+// node values (roots, then deflated values) and their ascending order; the
+// vectors are already in place (products and gather write the node block)
+__global__ void __launch_bounds__(256) k_merge_finish(const NodeDesc *__restrict__ nodes,
                                                       const MatDesc *__restrict__ mats,
-                                                      const NodeState *__restrict__ state, int mmax1) {
-    const int node = blockIdx.x / mmax1, c = blockIdx.x % mmax1;
-    const NodeDesc nd = nodes[node];
-    const int m = nd.m;
-    if (c > m) return;
+                                                      const NodeState *__restrict__ state) {
+    const NodeDesc nd = nodes[blockIdx.x];
     const MatDesc md = mats[nd.mat];
     const NodeState ns = state[nd.id];
-    const int sqre = nd.sqre, mc = m + sqre, r0 = nd.r0, N = ns.N, ndef = ns.ndef;
-    const long long ld = md.n, wb = (long long)r0 * md.wstride;
-    const double *W = md.Wt + wb, *Qm = md.Qt + wb;
-    if (c < ndef) {
-        const double *wsrc = W + (size_t)(ns.Ktot + c) * m;
-        const double *qsrc = Qm + (size_t)(ns.Ktot + c) * mc;
-        double *ud = md.U + (size_t)(r0 + N + c) * ld + r0;
-        double *vd = md.V + (size_t)(r0 + N + c) * ld + r0;
-        for (int row = threadIdx.x; row < m; row += blockDim.x) ud[row] = wsrc[row];
-        for (int row = threadIdx.x; row < mc; row += blockDim.x) vd[row] = qsrc[row];
-    } else if (c == ndef) {
-        if (sqre) {
-            const double *qsrc = Qm + (size_t)(ns.Ktot + ndef) * mc;
-            double *vd = md.V + (size_t)(r0 + m) * ld + r0;
-            for (int row = threadIdx.x; row < mc; row += blockDim.x) vd[row] = qsrc[row];
-        }
+    const int r0 = nd.r0, N = ns.N, ndef = ns.ndef;
+    const double *om = md.omega + r0, *dv = md.dval + r0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const double w = om[i];
+        int lo = 0, hi = ndef;           // # deflated values < w
+        while (lo < hi) { int mid = (lo + hi) >> 1; if (dv[mid] < w) lo = mid + 1; else hi = mid; }
+        md.D[r0 + i] = w;
+        md.Q[r0 + i + lo] = i;
     }
-    if (c == m) {
-        const double *om = md.omega + r0, *dv = md.dval + r0;
-        for (int i = threadIdx.x; i < N; i += blockDim.x) {
-            const double w = om[i];
-            int lo = 0, hi = ndef;           // # deflated values < w
-            while (lo < hi) { int mid = (lo + hi) >> 1; if (dv[mid] < w) lo = mid + 1; else hi = mid; }
-            md.D[r0 + i] = w;
-            md.Q[r0 + i + lo] = i;
-        }
-        for (int s = threadIdx.x; s < ndef; s += blockDim.x) {
-            const double v = dv[s];
-            int lo = 0, hi = N;              // # roots <= v
-            while (lo < hi) { int mid = (lo + hi) >> 1; if (om[mid] <= v) lo = mid + 1; else hi = mid; }
-            md.D[r0 + N + s] = v;
-            md.Q[r0 + s + lo] = N + s;
-        }
+    for (int s = threadIdx.x; s < ndef; s += blockDim.x) {
+        const double v = dv[s];
+        int lo = 0, hi = N;              // # roots <= v
+        while (lo < hi) { int mid = (lo + hi) >> 1; if (om[mid] <= v) lo = mid + 1; else hi = mid; }
+        md.D[r0 + N + s] = v;
+        md.Q[r0 + s + lo] = N + s;
     }
 }
 
@@ -503,7 +494,8 @@ cudaError_t launch_merge_gather(const NodeDesc *nodes, int nnodes, const MatDesc
 cudaError_t launch_merge_finish(const NodeDesc *nodes, int nnodes, const MatDesc *mats,
                                 const NodeState *state, int mmax, cudaStream_t st) {
     if (nnodes <= 0) return cudaSuccess;
-    k_merge_finish<<<(unsigned)nnodes * (mmax + 1), 128, 0, st>>>(nodes, mats, state, mmax + 1);
+    (void)mmax;
+    k_merge_finish<<<(unsigned)nnodes, 256, 0, st>>>(nodes, mats, state);
     return cudaGetLastError();
 }
 

@@ -144,7 +144,7 @@ __device__ int solve_root(const double *__restrict__ d, const double *__restrict
 
 __global__ void __launch_bounds__(256) k_secular(const NodeDesc *__restrict__ nodes,
                                                  const MatDesc *__restrict__ mats,
-                                                 const NodeState *__restrict__ state, int mmax,
+                                                 NodeState *__restrict__ state, int mmax,
                                                  int max_iter, int nnodes) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     const int node = warp / mmax, i = warp % mmax;
@@ -168,6 +168,7 @@ __global__ void __launch_bounds__(256) k_secular(const NodeDesc *__restrict__ no
         md.tau[nd.r0 + i] = tau;
         md.omega[nd.r0 + i] = d[o] + tau;
         if (it < 0) atomicAdd(md.info, 1);
+        atomicAdd(&state[nd.id].iters, (unsigned long long)(it < 0 ? max_iter : it));
     }
 }
 
@@ -304,7 +305,7 @@ __global__ void __launch_bounds__(256) k_mvectors_single(int N, const double *d,
 
 }  // namespace
 
-cudaError_t launch_secular(const NodeDesc *nodes, int nnodes, const MatDesc *mats, const NodeState *state,
+cudaError_t launch_secular(const NodeDesc *nodes, int nnodes, const MatDesc *mats, NodeState *state,
                            int mmax, int max_iter, int seed_mode, const float *mlp, cudaStream_t st) {
     (void)seed_mode; (void)mlp;
     if (nnodes <= 0) return cudaSuccess;

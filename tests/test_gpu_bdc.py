@@ -131,8 +131,9 @@ def test_nonfinite_input_reports_error(bdc):
 
 
 def test_sync_entry_point_matches_async(bdc):
+    # bdc_svd uses the library defaults; bdc_svd_ex with default options must match bitwise
     d, e = inputs.uniform(300, 9)
-    S1, U1, VT1, info = _run(bdc, d, e, leaf=32)
+    S1, U1, VT1, info = _run(bdc, d, e)
     S2, U2, VT2, rc = bdc.svd_sync(torch.from_numpy(d).cuda(), torch.from_numpy(e).cuda())
     assert rc == 0 and info == 0
     assert torch.equal(S1, S2) and torch.equal(U1, U2) and torch.equal(VT1, VT2)
