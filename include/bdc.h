@@ -57,11 +57,13 @@ typedef struct CUstream_st *bdc_stream_t; /* same object as cudaStream_t */
 typedef enum { BDC_FP64 = 0, BDC_MIXED_BF16X3 = 1, BDC_MIXED_EXACT = 2 } bdc_precision;
 
 /* Starting point of each secular root (Eq. M-svd-val):
- *   BDC_SEED_PLAIN  interval-midpoint start;
- *   BDC_SEED_MLP    start proposed by the small MLP in `mlp` (FP32 weights,
- *                   layout of bdc_mlp_param_count); the FP64 root finder
- *                   always finishes the root to the same stopping rule. */
-typedef enum { BDC_SEED_PLAIN = 0, BDC_SEED_MLP = 1 } bdc_seed;
+ *   BDC_SEED_PLAIN     interval-midpoint start;
+ *   BDC_SEED_MLP       analytic estimate corrected by the small MLP in `mlp`
+ *                      (FP32 weights, layout of bdc_mlp_param_count);
+ *   BDC_SEED_ANALYTIC  the analytic estimate alone (no network).
+ * The FP64 root finder always finishes every root to the same stopping
+ * rule, so the start changes the iteration count, not the accuracy. */
+typedef enum { BDC_SEED_PLAIN = 0, BDC_SEED_MLP = 1, BDC_SEED_ANALYTIC = 2 } bdc_seed;
 
 typedef struct {
     int prec;          /* bdc_precision                                   */
@@ -164,11 +166,91 @@ size_t bdc_gemm_workspace(int M, int N, int K, int prec, int slices);
 int bdc_gemm(int M, int N, int K, const double *A, int lda, const double *B, int ldb, double *C,
              int ldc, int prec, int slices, void *work, size_t lwork, bdc_stream_t stream);
 
-/* ---------------- MLP seeding of the secular roots ---------------------- */
-/* Number of FP32 parameters of the 2 x 64 MLP (inputs -> 64 -> 64 -> 1). */
+/* ---------------- MLP seeding of the secular roots ----------------------
+ * The paper solves every root of the secular equation (Eq. M-svd-val) from
+ * a fixed start; it has no learned component.  These entry points add one.
+ * Root i (0 <= i < N-1) lies in (d_i, d_{i+1}); with D2 = d_{i+1}^2 - d_i^2
+ * its position t = (w_i^2 - d_i^2) / D2 is held as the logit y =
+ * ln(t / (1 - t)).  The start is yhat = y_q + g(f):
+ *   y_q  an analytic estimate: the two interval poles exactly, the rest of
+ *        the secular function frozen at the interval midpoint (the 8
+ *        nearest other poles on each side summed exactly, the farther ones
+ *        through the first two moments of their z^2 weights in d^2), which
+ *        leaves a quadratic in t;
+ *   g    a 2 x 64 tanh MLP (FP32) trained on the gap y - y_q of roots that
+ *        FP64 runs produced.
+ * The solver starts at yhat instead of the interval midpoint (one pole-sum
+ * evaluation fewer, and a closer start), and polishes from the nearer pole
+ * if yhat lands on the wrong half.  The last root always starts plainly.
+ *
+ * Features (FP32, each clamped to [-40, 40]), a = z_i^2/D2, b =
+ * z_{i+1}^2/D2, gap_k = d_{k+1} - d_k, rho = sum z^2:
+ *   f0 = ln a   f1 = ln b   f2 = ln(rho/D2)
+ *   f3 = ln(gap_{i-1}/gap_i) (0 at i = 0)   f4 = ln(gap_{i+1}/gap_i) (0 at i = N-2)
+ *   f5 = ln(z_{i-1}^2/D2) (-40 at i = 0)    f6 = ln(z_{i+2}^2/D2) (-40 at i = N-2)
+ *   f7 = asinh(near-pole sum)   f8 = asinh(far-pole estimate)   f9 = y_q
+ *   f10 = d_i/d_{i+1}
+ * Parameters (FP32, bdc_mlp_param_count entries): [0,11) feature means,
+ * [11,22) inverse standard deviations, W1 (64 x 11, row per hidden unit),
+ * b1[64], W2 (64 x 64), b2[64], W3[64], b3;
+ * g = W3.tanh(W2 tanh(W1 xn + b1) + b2) + b3, xn = (f - mean) * istd.
+ * All pointers below are device pointers; calls are asynchronous on
+ * `stream`; non-zero returns: negative = argument error, BDC_ERR_CUDA. */
+/* Number of FP32 parameters (5015). */
 int bdc_mlp_param_count(void);
-/* Number of input features per root. */
+/* Number of input features per root (11). */
 int bdc_mlp_feature_count(void);
+
+/* Features of roots 0..N-2 of one sorted secular problem (d[0] = 0 <
+ * d[1] < ... , z non-zero) into feat[(N-1) x 11], row-major, and the
+ * analytic estimates y_q into yq[N-1] (yq may be NULL). */
+int bdc_mlp_features(int N, const double *d, const double *z, float *feat, double *yq, bdc_stream_t stream);
+
+/* bdc_secular_solve with a start rule `seed` (bdc_seed; `mlp` is needed
+ * for BDC_SEED_MLP only) and the iterations each root used in iters[N]
+ * (NULL = not wanted; -1 = did not converge). */
+int bdc_secular_solve_ex(int N, const double *d, const double *z, int seed, const float *mlp, int *org,
+                         double *tau, double *omega, int *iters, int max_iter, int *d_info, bdc_stream_t stream);
+
+/* bdc_svd_ex that also appends, for every secular root the merges solve
+ * (except each merge's last root), its features to feat[cap x 11] and its
+ * training target r = y - y_q (clamped to [-40, 40]) to targ[cap].
+ * *d_count (device) is the running number of samples: the caller zeroes it
+ * once, later calls append; slots at or past `cap` are counted but not
+ * written.  The sample order is not deterministic (roots append in
+ * completion order). */
+int bdc_svd_harvest(int n, const double *d, const double *e, double *U, double *S, double *VT, int ldu, int ldvt,
+                    const bdc_opts *o, void *work, size_t lwork, int *d_info, float *feat, float *targ, int cap,
+                    int *d_count, bdc_stream_t stream);
+
+/* Initialise params from `count` harvested feature rows: feature means and
+ * inverse standard deviations (floor 1e-3 on the deviation), Glorot-uniform
+ * hidden weights from a counter-based generator keyed by `seed`, zero
+ * biases and a zero output layer (g = 0: the start is y_q until trained).
+ * `targ` is not read and may be NULL. */
+int bdc_mlp_init(float *params, const float *feat, const float *targ, int count, unsigned long long seed,
+                 bdc_stream_t stream);
+
+/* Gradient of loss = mean over samples of h(g - r), h the Huber function
+ * with threshold `huber` (h(u) = u^2/2 for |u| <= huber, huber (|u| -
+ * huber/2) beyond; huber <= 0: u^2/2 everywhere), with respect to params
+ * into grad[param_count] (the normalisation entries are 0: not trained);
+ * *loss (may be NULL) gets the loss.  `work` is device scratch of
+ * bdc_mlp_grad_workspace(count) bytes.  For a given sample order the
+ * result is deterministic. */
+size_t bdc_mlp_grad_workspace(int count);
+int bdc_mlp_grad(const float *params, const float *feat, const float *targ, int count, float huber, float *grad,
+                 float *loss, void *work, size_t lwork, bdc_stream_t stream);
+
+/* One Adam step (step >= 1 is the bias-correction count) on the trained
+ * entries (from index 22) of params; m and v (param_count entries, zeroed
+ * before step 1) are the moment estimates. */
+int bdc_mlp_adam(float *params, const float *grad, float *m, float *v, int step, float lr, float beta1,
+                 float beta2, float eps, bdc_stream_t stream);
+
+/* g for `count` feature rows into out[count], with the same inference code
+ * the root solver runs. */
+int bdc_mlp_predict(const float *params, const float *feat, int count, float *out, bdc_stream_t stream);
 
 /* ---------------- stage profiling (CUDA events, host side) ---------------
  * bdc_profile_begin(1) makes every later call record a CUDA event pair

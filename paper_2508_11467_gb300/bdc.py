@@ -18,7 +18,8 @@ from . import build as _build
 LIB_PATH = _build.LIB
 
 BDC_FP64, BDC_MIXED_BF16X3, BDC_MIXED_EXACT = 0, 1, 2
-BDC_SEED_PLAIN, BDC_SEED_MLP = 0, 1
+BDC_SEED_PLAIN, BDC_SEED_MLP, BDC_SEED_ANALYTIC = 0, 1, 2
+SEED = {"plain": BDC_SEED_PLAIN, "mlp": BDC_SEED_MLP, "analytic": BDC_SEED_ANALYTIC}
 BDC_ERR_CUDA, BDC_ERR_TIMEOUT, BDC_ERR_NONFINITE, BDC_ERR_INTERNAL = -1000, -1001, -1002, -1003
 PREC = {"fp64": BDC_FP64, "bf16x3": BDC_MIXED_BF16X3, "exact": BDC_MIXED_EXACT, "mixed": BDC_MIXED_EXACT}
 
@@ -49,6 +50,16 @@ _SIGS = {
     "bdc_gemm": (_I, [_I, _I, _I, _VP, _I, _VP, _I, _VP, _I, _I, _I, _VP, _SZ, _VP]),
     "bdc_mlp_param_count": (_I, []),
     "bdc_mlp_feature_count": (_I, []),
+    "bdc_mlp_features": (_I, [_I, _VP, _VP, _VP, _VP, _VP]),
+    "bdc_secular_solve_ex": (_I, [_I, _VP, _VP, _I, _VP, _VP, _VP, _VP, _VP, _I, _VP, _VP]),
+    "bdc_svd_harvest": (_I, [_I, _VP, _VP, _VP, _VP, _VP, _I, _I, _VP, _VP, _SZ, _VP, _VP, _VP, _I, _VP,
+                             _VP]),
+    "bdc_mlp_init": (_I, [_VP, _VP, _VP, _I, ctypes.c_ulonglong, _VP]),
+    "bdc_mlp_grad_workspace": (_SZ, [_I]),
+    "bdc_mlp_grad": (_I, [_VP, _VP, _VP, _I, ctypes.c_float, _VP, _VP, _VP, _SZ, _VP]),
+    "bdc_mlp_adam": (_I, [_VP, _VP, _VP, _VP, _I, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                          ctypes.c_float, _VP]),
+    "bdc_mlp_predict": (_I, [_VP, _VP, _I, _VP, _VP]),
     "bdc_status_string": (ctypes.c_char_p, [_I]),
     "bdc_profile_begin": (_I, [_I]),
     "bdc_profile_end": (_I, [_VP, _VP, _VP]),
@@ -144,7 +155,7 @@ def make_opts(prec="fp64", leaf=16, max_iter=64, slices=0, seed="plain", mlp=Non
     o.leaf = int(leaf)
     o.max_iter = int(max_iter)
     o.slices = int(slices)
-    o.seed = BDC_SEED_MLP if seed == "mlp" else BDC_SEED_PLAIN
+    o.seed = SEED[seed] if isinstance(seed, str) else int(seed)
     o.mlp = ctypes.c_void_p(mlp.data_ptr()) if mlp is not None else None
     return o
 
@@ -296,3 +307,149 @@ def gemm(A, B, prec="fp64", slices=6, stream=None, work=None):
     _check("bdc_gemm", lib().bdc_gemm(M, N, K, _ptr(A), max(M, 1), _ptr(B), max(K, 1), _ptr(Ct), max(M, 1), p,
                                        int(slices), _ptr(work), work.numel(), _stream(stream)))
     return Ct.t()
+
+
+# ---------------------------------------------------------------- MLP start points
+def mlp_param_count() -> int:
+    return int(lib().bdc_mlp_param_count())
+
+
+def mlp_feature_count() -> int:
+    return int(lib().bdc_mlp_feature_count())
+
+
+def mlp_features(d, z, stream=None):
+    """Features ((N-1) x 11 float32) and analytic estimates y_q ((N-1)
+    float64) of roots 0..N-2 of one sorted secular problem."""
+    d, z = _dev(d), _dev(z)
+    N = d.shape[0]
+    f = torch.empty((max(N - 1, 0), mlp_feature_count()), dtype=torch.float32, device=d.device)
+    yq = torch.empty(max(N - 1, 0), dtype=torch.float64, device=d.device)
+    _check("bdc_mlp_features", lib().bdc_mlp_features(N, _ptr(d), _ptr(z), _ptr(f), _ptr(yq), _stream(stream)))
+    return f, yq
+
+
+def secular_solve_ex(d, z, seed="plain", mlp=None, max_iter=64, stream=None):
+    """Secular roots with a chosen start rule; also the iterations per root."""
+    d, z = _dev(d), _dev(z)
+    N = d.shape[0]
+    org = torch.empty(N, dtype=torch.int32, device=d.device)
+    tau = torch.empty(N, dtype=torch.float64, device=d.device)
+    om = torch.empty(N, dtype=torch.float64, device=d.device)
+    it = torch.empty(N, dtype=torch.int32, device=d.device)
+    info = torch.zeros(1, dtype=torch.int32, device=d.device)
+    _check("bdc_secular_solve_ex",
+           lib().bdc_secular_solve_ex(N, _ptr(d), _ptr(z), SEED[seed] if isinstance(seed, str) else int(seed),
+                                      _ptr(mlp), _ptr(org), _ptr(tau), _ptr(om), _ptr(it), int(max_iter),
+                                      _ptr(info), _stream(stream)))
+    return org, tau, om, it, info
+
+
+class Harvest:
+    """Device buffers that collect (features, target) pairs from SVD runs."""
+
+    def __init__(self, cap: int, device="cuda"):
+        self.cap = int(cap)
+        self.feat = torch.empty((self.cap, mlp_feature_count()), dtype=torch.float32, device=device)
+        self.targ = torch.empty(self.cap, dtype=torch.float32, device=device)
+        self.count = torch.zeros(1, dtype=torch.int32, device=device)
+
+    def size(self) -> int:
+        return min(int(self.count.item()), self.cap)
+
+    def data(self):
+        k = self.size()
+        return self.feat[:k], self.targ[:k]
+
+
+def svd_harvest(d, e, harvest: Harvest, *, prec="fp64", leaf=16, max_iter=64, slices=0, stream=None,
+                check=True, mixed_min=0):
+    """svd() that appends every merge root's (features, target) to `harvest`."""
+    d = _dev(d)
+    n = d.shape[0]
+    e = _dev(e) if n > 1 else torch.zeros(1, dtype=torch.float64, device=d.device)
+    o = make_opts(prec, leaf, max_iter, slices, "plain", None, mixed_min)
+    Ut = torch.empty((n, n), dtype=torch.float64, device=d.device)
+    VTt = torch.empty((n, n), dtype=torch.float64, device=d.device)
+    S = torch.empty(max(n, 1), dtype=torch.float64, device=d.device)
+    info = torch.zeros(1, dtype=torch.int32, device=d.device)
+    lw = workspace_bytes(n, o)
+    work = torch.empty(lw + 256, dtype=torch.uint8, device=d.device)
+    rc = lib().bdc_svd_harvest(n, _ptr(d), _ptr(e), _ptr(Ut), _ptr(S), _ptr(VTt), max(n, 1), max(n, 1),
+                               ctypes.byref(o), _ptr(work), work.numel(), _ptr(info), _ptr(harvest.feat),
+                               _ptr(harvest.targ), harvest.cap, _ptr(harvest.count), _stream(stream))
+    _check("bdc_svd_harvest", rc)
+    code = int(info.item())
+    if check and code != 0:
+        raise BDCError("bdc_svd_harvest (device status)", code)
+    return S[:n], Ut.t(), VTt.t(), code
+
+
+def mlp_init(feat, targ=None, seed=0, stream=None):
+    """Fresh parameters (normalisation from the data, Glorot hidden weights,
+    zero output layer)."""
+    P = torch.empty(mlp_param_count(), dtype=torch.float32, device=feat.device)
+    _check("bdc_mlp_init", lib().bdc_mlp_init(_ptr(P), _ptr(feat), _ptr(targ), int(feat.shape[0]),
+                                               int(seed), _stream(stream)))
+    return P
+
+
+def mlp_grad(P, feat, targ, huber=0.25, stream=None, work=None):
+    """(gradient, loss) of the mean Huber loss (threshold `huber`; <= 0:
+    squares), both on the device."""
+    count = int(feat.shape[0])
+    g = torch.empty_like(P)
+    loss = torch.empty(1, dtype=torch.float32, device=P.device)
+    lw = int(lib().bdc_mlp_grad_workspace(count))
+    if work is None or work.numel() < lw:
+        work = torch.empty(max(lw, 1), dtype=torch.uint8, device=P.device)
+    _check("bdc_mlp_grad", lib().bdc_mlp_grad(_ptr(P), _ptr(feat), _ptr(targ), count, float(huber), _ptr(g),
+                                               _ptr(loss), _ptr(work), work.numel(), _stream(stream)))
+    return g, loss
+
+
+def mlp_adam(P, g, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check("bdc_mlp_adam", lib().bdc_mlp_adam(_ptr(P), _ptr(g), _ptr(m), _ptr(v), int(step), float(lr),
+                                               float(beta1), float(beta2), float(eps), _stream(stream)))
+
+
+def mlp_predict(P, feat, stream=None):
+    out = torch.empty(int(feat.shape[0]), dtype=torch.float32, device=P.device)
+    _check("bdc_mlp_predict", lib().bdc_mlp_predict(_ptr(P), _ptr(feat), int(feat.shape[0]), _ptr(out),
+                                                     _stream(stream)))
+    return out
+
+
+def mlp_train(feat, targ, steps=1500, lr=3e-3, seed=0, huber=0.25, stream=None):
+    """Full-batch Adam on the harvested pairs with the library's kernels
+    (Huber loss, threshold `huber`); the learning rate decays linearly to
+    lr/10.  Returns (params, losses)."""
+    P = mlp_init(feat, targ, seed, stream)
+    m = torch.zeros_like(P)
+    v = torch.zeros_like(P)
+    count = int(feat.shape[0])
+    lw = int(lib().bdc_mlp_grad_workspace(count))
+    work = torch.empty(max(lw, 1), dtype=torch.uint8, device=P.device)
+    losses = torch.empty(steps, dtype=torch.float32, device=P.device)
+    g = torch.empty_like(P)
+    for k in range(1, steps + 1):
+        lr_k = lr * (1.0 - 0.9 * (k - 1) / max(steps - 1, 1))
+        _check("bdc_mlp_grad", lib().bdc_mlp_grad(_ptr(P), _ptr(feat), _ptr(targ), count, float(huber), _ptr(g),
+                                                   _ptr(losses[k - 1:k]), _ptr(work), work.numel(),
+                                                   _stream(stream)))
+        mlp_adam(P, g, m, v, k, lr_k, stream=stream)
+    return P, losses
+
+
+def mlp_save(P, path):
+    """Write the parameters as raw little-endian float32."""
+    import numpy as np
+    np.asarray(P.detach().cpu().numpy(), dtype="<f4").tofile(path)
+
+
+def mlp_load(path, device="cuda"):
+    import numpy as np
+    a = np.fromfile(path, dtype="<f4")
+    if a.size != mlp_param_count():
+        raise ValueError(f"{path}: {a.size} floats, expected {mlp_param_count()}")
+    return torch.from_numpy(a).to(device)

@@ -93,7 +93,8 @@ size_t per_matrix_bytes(int n) {
     size_t b = 0;
     b += align256(sizeof(double) * 2 * N);            // dsc, esc
     b += align256(sizeof(double) * 4 * N * N);        // U, V (two copies each)
-    b += align256(sizeof(double) * 12 * N + 64);      // D ds zs rc rs dM zM zt tau omega dval scale
+    b += align256(sizeof(double) * 20 * N + 64);      // D ds zs rc rs dM zM zt tau omega dval scale pz(6n) ystart yq
+    b += align256(sizeof(float) * 11 * N);            // fs (root features)
     b += align256(sizeof(int) * (13 * N + 128));      // Q src role org kposM dsrc dest slist sidx invK(4n) info
     const size_t big = (N + 1) * (N + 16) + 64;
     b += 4 * align256(sizeof(double) * big);          // Wt Qt UM VM
@@ -190,10 +191,12 @@ MatDesc carve(char *base, size_t off, int n) {
     md.dsc = de; md.esc = de + N;
     double *uv = (double *)take(sizeof(double) * 4 * N * N);
     md.U[0] = uv; md.V[0] = uv + N * N; md.U[1] = uv + 2 * N * N; md.V[1] = uv + 3 * N * N;
-    double *dd = (double *)take(sizeof(double) * 12 * N + 64);
+    double *dd = (double *)take(sizeof(double) * 20 * N + 64);
     md.D = dd; md.ds = dd + N; md.zs = dd + 2 * N; md.rc = dd + 3 * N; md.rs = dd + 4 * N;
     md.dM = dd + 5 * N; md.zM = dd + 6 * N; md.zt = dd + 7 * N; md.tau = dd + 8 * N;
-    md.omega = dd + 9 * N; md.dval = dd + 10 * N; md.scale = dd + 11 * N;
+    md.omega = dd + 9 * N; md.dval = dd + 10 * N; md.scale = dd + 11 * N; md.pz = dd + 12 * N;
+    md.ystart = dd + 18 * N; md.yq = dd + 19 * N;
+    md.fs = (float *)take(sizeof(float) * 11 * N);
     int *ii = (int *)take(sizeof(int) * (13 * N + 128));
     md.Q = ii; md.src = ii + N; md.role = ii + 2 * N; md.org = ii + 3 * N; md.kposM = ii + 4 * N;
     md.dsrc = ii + 5 * N; md.dest = ii + 6 * N; md.slist = ii + 7 * N; md.sidx = ii + 8 * N;
@@ -374,6 +377,7 @@ int run_plan(const Plan &p, const bdc_opts &o, char *work, std::vector<MatDesc> 
         c.d_in = mats[mi].d_in; c.e_in = mats[mi].e_in;
         c.Uo = mats[mi].Uo; c.So = mats[mi].So; c.VTo = mats[mi].VTo;
         c.ldu = mats[mi].ldu; c.ldvt = mats[mi].ldvt;
+        c.feat = mats[mi].feat; c.targ = mats[mi].targ; c.hcount = mats[mi].hcount; c.hcap = mats[mi].hcap;
         mats[mi] = c;
     }
     cudaError_t e = upload(p, work, mats, st);
@@ -383,6 +387,10 @@ int run_plan(const Plan &p, const bdc_opts &o, char *work, std::vector<MatDesc> 
     NodeState *dstate = (NodeState *)(work + p.off_state);
     GemmProb *dprobs = (GemmProb *)(work + p.off_probs);
     const int max_iter = o.max_iter > 0 ? o.max_iter : kDefaultMaxIter;
+    // the root start estimates need the per-merge moment scans
+    int harvest = 0;
+    for (int mi = 0; mi < p.nmat; ++mi) harvest |= (mats[mi].feat != nullptr);
+    const int scans = (o.seed != BDC_SEED_PLAIN) || harvest;
 
     double nsq = 0.0;
     for (int mi = 0; mi < p.nmat; ++mi) nsq += (double)mats[mi].n * mats[mi].n;
@@ -411,15 +419,15 @@ int run_plan(const Plan &p, const bdc_opts &o, char *work, std::vector<MatDesc> 
         for (const NodeDesc &nd : p.heights[h]) m2 += (double)nd.m * nd.m;
         {
             StageScope sc(st, BDC_STAGE_PREP, 1, 0.0);
-            if ((e = launch_merge_prep(dn, nn, dmats, dstate, dprobs, mm, st)) != cudaSuccess) return note(e);
+            if ((e = launch_merge_prep(dn, nn, dmats, dstate, dprobs, mm, scans, st)) != cudaSuccess) return note(e);
         }
         {   // reads the children's U, V halves (8 m^2 B), writes W~ and Q~ (16 m^2 B)
             StageScope sc(st, BDC_STAGE_GATHER, 1, 24.0 * m2);
             if ((e = launch_merge_gather(dn, nn, dmats, dstate, mm, st)) != cudaSuccess) return note(e);
         }
         {
-            StageScope sc(st, BDC_STAGE_SECULAR, 2, 0.0);
-            if ((e = launch_secular(dn, nn, dmats, dstate, mm, max_iter, o.seed, o.mlp, st)) != cudaSuccess)
+            StageScope sc(st, BDC_STAGE_SECULAR, (o.seed != BDC_SEED_PLAIN || harvest) ? 3 : 2, 0.0);
+            if ((e = launch_secular(dn, nn, dmats, dstate, mm, max_iter, o.seed, o.mlp, harvest, st)) != cudaSuccess)
                 return note(e);
         }
         {   // writes U_M and V_M: 16 N Ktot B (added from the node states)
@@ -506,7 +514,7 @@ bdc_opts resolve(const bdc_opts *o, int nmax) {
 
 int check_opts(const bdc_opts &o) {
     if (o.prec < 0 || o.prec > 2) return 1;
-    if (o.seed < 0 || o.seed > 1) return 1;
+    if (o.seed < 0 || o.seed > 2) return 1;
     if (o.seed == BDC_SEED_MLP && !o.mlp) return 1;
     if (o.leaf < 4 || o.leaf > 64) return 1;
     if (o.slices < 2 || o.slices > 7) return 1;
@@ -555,6 +563,29 @@ int bdc_svd_ex(int n, const double *d, const double *e, double *U, double *S, do
     std::vector<MatDesc> mats(1);
     mats[0].n = n; mats[0].d_in = d; mats[0].e_in = e;
     mats[0].Uo = U; mats[0].So = S; mats[0].VTo = VT; mats[0].ldu = ldu; mats[0].ldvt = ldvt;
+    return run_plan(p, r, w, mats, d_info, st);
+}
+
+int bdc_svd_harvest(int n, const double *d, const double *e, double *U, double *S, double *VT, int ldu, int ldvt,
+                    const bdc_opts *o, void *work, size_t lwork, int *d_info, float *feat, float *targ, int cap,
+                    int *d_count, bdc_stream_t stream) {
+    int a = check_args(n, d, e, U, S, VT, ldu, ldvt);
+    if (a) return a;
+    const bdc_opts r = resolve(o, n);
+    if (check_opts(r)) return -9;
+    if (!d_info) return -12;
+    if (cap < 0 || !d_count || (cap > 0 && (!feat || !targ))) return -13;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n == 0) return note(cudaMemsetAsync(d_info, 0, sizeof(int), st));
+    const Plan p = make_plan(1, &n, r);
+    if (!work) return -10;
+    if (lwork < p.total) return -11;
+    char *w = (char *)(((uintptr_t)work + 255) & ~(uintptr_t)255);
+    if ((size_t)(w - (char *)work) + p.total - 256 > lwork) return -11;
+    std::vector<MatDesc> mats(1);
+    mats[0].n = n; mats[0].d_in = d; mats[0].e_in = e;
+    mats[0].Uo = U; mats[0].So = S; mats[0].VTo = VT; mats[0].ldu = ldu; mats[0].ldvt = ldvt;
+    mats[0].feat = feat; mats[0].targ = targ; mats[0].hcount = d_count; mats[0].hcap = cap;
     return run_plan(p, r, w, mats, d_info, st);
 }
 
@@ -635,7 +666,19 @@ int bdc_secular_solve(int N, const double *d, const double *z, int *org, double 
     cudaStream_t st = (cudaStream_t)stream;
     if (int r = note(cudaMemsetAsync(d_info, 0, sizeof(int), st))) return r;
     return note(launch_secular_single(N, d, z, org, tau, omega, max_iter > 0 ? max_iter : kDefaultMaxIter, d_info,
-                                      st));
+                                      BDC_SEED_PLAIN, nullptr, nullptr, st));
+}
+
+int bdc_secular_solve_ex(int N, const double *d, const double *z, int seed, const float *mlp, int *org,
+                         double *tau, double *omega, int *iters, int max_iter, int *d_info, bdc_stream_t stream) {
+    if (N < 0) return -1;
+    if (N > 0 && (!d || !z || !org || !tau || !omega)) return -2;
+    if (seed < 0 || seed > 2 || (seed == BDC_SEED_MLP && !mlp)) return -4;
+    if (!d_info) return -11;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (int r = note(cudaMemsetAsync(d_info, 0, sizeof(int), st))) return r;
+    return note(launch_secular_single(N, d, z, org, tau, omega, max_iter > 0 ? max_iter : kDefaultMaxIter, d_info,
+                                      seed, mlp, iters, st));
 }
 
 int bdc_lowner_z(int N, const double *d, const double *z, const int *org, const double *tau, double *zt,
@@ -779,8 +822,48 @@ int bdc_profile_secular(long long *roots, long long *iters) {
     return 0;
 }
 
-int bdc_mlp_param_count(void) { return 0; }
-int bdc_mlp_feature_count(void) { return 0; }
+int bdc_mlp_param_count(void) { return mlp_param_count(); }
+int bdc_mlp_feature_count(void) { return mlp_feature_count(); }
+
+int bdc_mlp_features(int N, const double *d, const double *z, float *feat, double *yq, bdc_stream_t stream) {
+    if (N < 0) return -1;
+    if (N > 1 && (!d || !z || !feat)) return -2;
+    return note(launch_mlp_features_single(N, d, z, feat, yq, (cudaStream_t)stream));
+}
+
+int bdc_mlp_init(float *params, const float *feat, const float *targ, int count, unsigned long long seed,
+                 bdc_stream_t stream) {
+    if (!params) return -1;
+    if (count < 0 || (count > 0 && !feat)) return -2;
+    (void)targ;
+    return note(launch_mlp_init(params, feat, count, seed, (cudaStream_t)stream));
+}
+
+size_t bdc_mlp_grad_workspace(int count) { return count < 0 ? 0 : mlp_grad_workspace(count); }
+
+int bdc_mlp_grad(const float *params, const float *feat, const float *targ, int count, float huber, float *grad,
+                 float *loss, void *work, size_t lwork, bdc_stream_t stream) {
+    if (!params || !grad) return -1;
+    if (count < 0 || (count > 0 && (!feat || !targ))) return -2;
+    if (count > 0 && (!work || lwork < mlp_grad_workspace(count))) return -3;
+    if (!(huber == huber)) return -4;
+    return note(launch_mlp_grad(params, feat, targ, count, huber, grad, loss, (float *)work,
+                                (cudaStream_t)stream));
+}
+
+int bdc_mlp_adam(float *params, const float *grad, float *m, float *v, int step, float lr, float beta1,
+                 float beta2, float eps, bdc_stream_t stream) {
+    if (!params || !grad || !m || !v) return -1;
+    if (step < 1) return -2;
+    if (!(lr > 0.f) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f)) return -3;
+    return note(launch_mlp_adam(params, grad, m, v, step, lr, beta1, beta2, eps, (cudaStream_t)stream));
+}
+
+int bdc_mlp_predict(const float *params, const float *feat, int count, float *out, bdc_stream_t stream) {
+    if (!params) return -1;
+    if (count < 0 || (count > 0 && (!feat || !out))) return -2;
+    return note(launch_mlp_predict(params, feat, count, out, (cudaStream_t)stream));
+}
 
 const char *bdc_last_error_string(void) {
     static thread_local char out[256];

@@ -48,7 +48,15 @@ struct MatDesc {
     int *sidx;               // sorted position -> index in slist (-1 = small z)
     double *Wt, *Qt, *UM, *VM;   // big per-level matrices (node base r0 * wstride)
     int *info;               // [1] status: >0 non-convergence count, <0 error code
-    float *feat;             // optional MLP harvest buffer (nullptr = off)
+    double *pz;              // per-merge z^2 moment scans [6][n]: prefix sums of z^2, z^2 d^2,
+                             // z^2 d^4 (rows 0-2), suffix sums (rows 3-5); root start features
+    double *ystart;          // per-root start fractions (seeded starts), indexed r0 + i
+    double *yq;              // per-root analytic estimates (harvest)
+    float *fs;               // per-root features [n][kMlpIn] (harvest)
+    float *feat;             // optional MLP harvest: features [hcap][kMlpIn] (nullptr = off)
+    float *targ;             // harvest targets [hcap]
+    int *hcount;             // harvest counter (device)
+    int hcap;                // harvest capacity
 };
 
 struct NodeDesc {
@@ -74,6 +82,7 @@ struct NodeState {
     double tol;
     double cq, sq;   // rotation folding the two null-vector components (sqre)
     unsigned long long iters;   // secular iterations summed over the node's roots
+    double rho;                 // sum of z^2 over the survivors (after deflation)
 };
 
 // one FP64 product C = A * B (column-major), used by the merge GEMMs
@@ -124,12 +133,12 @@ cudaError_t launch_scale(const MatDesc *mats, int nmat, int nmax, cudaStream_t s
 cudaError_t launch_leaves(const NodeDesc *leaves, int nleaves, const MatDesc *mats, int leafmax,
                           int max_sweeps, cudaStream_t st);
 cudaError_t launch_merge_prep(const NodeDesc *nodes, int nnodes, const MatDesc *mats,
-                              NodeState *state, GemmProb *probs, int mmax, cudaStream_t st);
+                              NodeState *state, GemmProb *probs, int mmax, int scans, cudaStream_t st);
 cudaError_t launch_merge_gather(const NodeDesc *nodes, int nnodes, const MatDesc *mats,
                                 const NodeState *state, int mmax, cudaStream_t st);
 cudaError_t launch_secular(const NodeDesc *nodes, int nnodes, const MatDesc *mats,
                            NodeState *state, int mmax, int max_iter, int seed_mode,
-                           const float *mlp, cudaStream_t st);
+                           const float *mlp, int harvest, cudaStream_t st);
 cudaError_t launch_vectors(const NodeDesc *nodes, int nnodes, const MatDesc *mats,
                            const NodeState *state, int mmax, cudaStream_t st);
 cudaError_t launch_gemm64(const GemmProb *probs, int nprobs, int mmax_rows, int nmax_cols,
@@ -140,7 +149,21 @@ cudaError_t launch_final(const MatDesc *mats, int nmat, int nmax, cudaStream_t s
 
 // standalone step kernels (step entry points)
 cudaError_t launch_secular_single(int N, const double *d, const double *z, int *org, double *tau,
-                                  double *omega, int max_iter, int *info, cudaStream_t st);
+                                  double *omega, int max_iter, int *info, int seed_mode, const float *mlp,
+                                  int *iters, cudaStream_t st);
+// MLP training (bdc_mlp.cu)
+size_t mlp_grad_workspace(int count);
+cudaError_t launch_mlp_init(float *P, const float *feat, int count, unsigned long long seed,
+                            cudaStream_t st);
+cudaError_t launch_mlp_grad(const float *P, const float *feat, const float *targ, int count, float huber,
+                            float *grad, float *loss, float *work, cudaStream_t st);
+cudaError_t launch_mlp_adam(float *P, const float *grad, float *m, float *v, int step, float lr, float b1,
+                            float b2, float eps, cudaStream_t st);
+cudaError_t launch_mlp_predict(const float *P, const float *feat, int count, float *out, cudaStream_t st);
+int mlp_param_count();
+int mlp_feature_count();
+cudaError_t launch_mlp_features_single(int N, const double *d, const double *z, float *feat, double *yq,
+                                       cudaStream_t st);
 cudaError_t launch_lowner_single(int N, const double *d, const double *z, const int *org,
                                  const double *tau, double *zt, cudaStream_t st);
 cudaError_t launch_mvectors_single(int N, const double *d, const double *zt, const int *org,

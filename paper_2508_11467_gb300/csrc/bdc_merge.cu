@@ -71,6 +71,53 @@ __device__ __forceinline__ int block_isum(int v, int *wsum) {
     return t;
 }
 
+// exclusive block scan of doubles in thread order (reverse = false: sum over
+// threads before t; true: over threads after t); no subtraction, so small
+// partial sums keep their relative accuracy
+__device__ __forceinline__ double block_excl_scan_d(double v, double *buf, bool reverse) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double x = v;
+    if (!reverse) {
+        for (int o = 1; o < 32; o <<= 1) {
+            const double y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+    } else {
+        for (int o = 1; o < 32; o <<= 1) {
+            const double y = __shfl_down_sync(0xffffffffu, x, o);
+            if (lane + o < 32) x += y;
+        }
+    }
+    double ex = reverse ? __shfl_down_sync(0xffffffffu, x, 1) : __shfl_up_sync(0xffffffffu, x, 1);
+    if (reverse ? lane == 31 : lane == 0) ex = 0.0;
+    if (reverse ? lane == 0 : lane == 31) buf[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        double t = (lane < nw) ? buf[lane] : 0.0;
+        double tx = t;
+        if (!reverse) {
+            for (int o = 1; o < 32; o <<= 1) {
+                const double y = __shfl_up_sync(0xffffffffu, tx, o);
+                if (lane >= o) tx += y;
+            }
+        } else {
+            for (int o = 1; o < 32; o <<= 1) {
+                const double y = __shfl_down_sync(0xffffffffu, tx, o);
+                if (lane + o < 32) tx += y;
+            }
+        }
+        // exclusive over warps
+        double e = reverse ? __shfl_down_sync(0xffffffffu, tx, 1) : __shfl_up_sync(0xffffffffu, tx, 1);
+        if (reverse ? lane == 31 : lane == 0) e = 0.0;
+        __syncwarp();
+        if (lane < nw) buf[lane] = e;
+    }
+    __syncthreads();
+    const double r = buf[w] + ex;
+    __syncthreads();
+    return r;
+}
+
 // side of a pre-deflation column: 1 = rows of the left child, 2 = right
 __device__ __forceinline__ int col_side(int c, int nl) { return c == 0 ? 0 : (c <= nl ? 1 : 2); }
 
@@ -169,7 +216,7 @@ __device__ int deflate_core(int m, double tol, const double *ds, double *zs, con
 __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__restrict__ nodes,
                                                              const MatDesc *__restrict__ mats,
                                                              NodeState *__restrict__ state,
-                                                             GemmProb *__restrict__ probs) {
+                                                             GemmProb *__restrict__ probs, int scans) {
     __shared__ int wsum[PREP_THREADS / 32 + 1];
     __shared__ double dsum[PREP_THREADS / 32 + 1];
     const NodeDesc nd = nodes[blockIdx.x];
@@ -255,6 +302,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
     }
     int N, n1, n2, n3, nz, no;
     int ik = block_excl_scan(ck, wsum, N);
+    const int ik0 = ik;                       // this thread's survivors: [ik0, ik0 + ck)
     int i1 = block_excl_scan(c1, wsum, n1);
     int i2 = block_excl_scan(c2, wsum, n2);
     int i3 = block_excl_scan(c3, wsum, n3);
@@ -292,10 +340,45 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
         }
     }
     for (int kp = n1 + t; kp < P1; kp += T) invK[kp] = -1;
+    if (scans) {
+        // moment scans of the survivors for the root start estimates: prefix
+        // sums (inclusive) of z^2, z^2 d^2, z^2 d^4 and the same suffix sums
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+        for (int k = ik0; k < ik0 + ck; ++k) {
+            const double z2 = zM[k] * zM[k], d2 = dM[k] * dM[k];
+            a0 += z2; a1 += z2 * d2; a2 += z2 * d2 * d2;
+        }
+        double *pz = md.pz + r0;
+        const long long sn = md.n;
+        double c0 = block_excl_scan_d(a0, dsum, false), c1 = block_excl_scan_d(a1, dsum, false),
+               c2 = block_excl_scan_d(a2, dsum, false);
+        for (int k = ik0; k < ik0 + ck; ++k) {
+            const double z2 = zM[k] * zM[k], d2 = dM[k] * dM[k];
+            c0 += z2; c1 += z2 * d2; c2 += z2 * d2 * d2;
+            pz[k] = c0; pz[sn + k] = c1; pz[2 * sn + k] = c2;
+        }
+        c0 = block_excl_scan_d(a0, dsum, true); c1 = block_excl_scan_d(a1, dsum, true);
+        c2 = block_excl_scan_d(a2, dsum, true);
+        for (int k = ik0 + ck - 1; k >= ik0; --k) {
+            const double z2 = zM[k] * zM[k], d2 = dM[k] * dM[k];
+            c0 += z2; c1 += z2 * d2; c2 += z2 * d2 * d2;
+            pz[3 * sn + k] = c0; pz[4 * sn + k] = c1; pz[5 * sn + k] = c2;
+        }
+    }
+    __syncthreads();
+    // rho = sum of the survivors' z^2 (the secular solver's upper bound for
+    // the last root and one of the MLP features)
+    double zz = 0.0;
+    for (int k = t; k < N; k += T) zz = fma(zM[k], zM[k], zz);
+    zz = warp_sum(zz);
+    if ((t & 31) == 0) dsum[t >> 5] = zz;
+    __syncthreads();
     if (t == 0) {
+        double rho = 0.0;
+        for (int w = 0; w < (T >> 5); ++w) rho += dsum[w];
         NodeState s;
         s.N = N; s.n1 = n1; s.n2 = n2; s.n3 = n3; s.P1 = P1; s.Ktot = Ktot;
-        s.ndef = m - N; s.nzero = nz; s.tol = tol; s.cq = s_cq; s.sq = s_sq; s.iters = 0;
+        s.ndef = m - N; s.nzero = nz; s.tol = tol; s.cq = s_cq; s.sq = s_sq; s.iters = 0; s.rho = rho;
         state[nd.id] = s;
         const long long wb = (long long)r0 * md.wstride;
         const int Ktop = P1 + 1 + n2, Kbot = Ktot - P1;
@@ -477,10 +560,10 @@ __global__ void __launch_bounds__(PREP_THREADS) k_deflate_single(int m, const do
 }  // namespace
 
 cudaError_t launch_merge_prep(const NodeDesc *nodes, int nnodes, const MatDesc *mats, NodeState *state,
-                              GemmProb *probs, int mmax, cudaStream_t st) {
+                              GemmProb *probs, int mmax, int scans, cudaStream_t st) {
     (void)mmax;
     if (nnodes <= 0) return cudaSuccess;
-    k_merge_prep<<<nnodes, PREP_THREADS, 0, st>>>(nodes, mats, state, probs);
+    k_merge_prep<<<nnodes, PREP_THREADS, 0, st>>>(nodes, mats, state, probs, scans);
     return cudaGetLastError();
 }
 

@@ -9,7 +9,9 @@
 //            (a "middle way" step in the sense of R.-C. Li), safeguarded by a
 //            bracket; lanes split the pole sums and reduce with shuffles.
 //            Stopping rule: |f| <= 16 eps (1 + sum |terms|), or a step below
-//            4 eps |x|.
+//            4 eps |x|.  Optionally the start comes from a small MLP
+//            (bdc_mlp.cuh) instead of the interval midpoint; the stopping
+//            rule is the same, so the MLP only changes the iteration count.
 // k_lowner   one warp per i: |z~_i| of Eq. (bdc-zi) as a product over k of
 //            (w_k^2 - d_i^2) / (d_{k'}^2 - d_i^2) (every factor lies in (0, 1]
 //            by interlacing), lane partial products, then a shuffle product
@@ -20,6 +22,7 @@
 //
 // All arithmetic is FP64.
 #include "bdc_internal.cuh"
+#include "bdc_mlp.cuh"
 
 namespace bdc {
 
@@ -54,67 +57,36 @@ __device__ __forceinline__ Sums pole_sums(const double *__restrict__ d, const do
     return s;
 }
 
-// Solve root i of (d, z) (N entries, d[0] = 0 < d[1] < ...).  Returns the
-// number of iterations used, or -1 if not converged.  All lanes return the
-// same result.  x0 (optional, NaN = none) is a proposed start w^2 - d_o^2
-// relative to the origin chosen here.
-__device__ int solve_root(const double *__restrict__ d, const double *__restrict__ z, int N, int i,
-                          int max_iter, double zz, int &org_out, double &tau_out, double start_frac) {
-    const int lane = threadIdx.x & 31;
-    if (N == 1) {
-        org_out = 0;
-        tau_out = fabs(z[0]);
-        return 0;
-    }
-    const bool last = (i == N - 1);
-    const double dl = d[i];
-    const double du = last ? sqrt(dl * dl + zz) : d[i + 1];
-    const double h = 0.5 * (du - dl);
-    int o;
-    double dor, lo, hi, lamL, lamR, x;
+struct RootState {
+    int o;                       // origin pole index
+    double dor;                  // d_o
+    double lo, hi;               // bracket for x = w^2 - d_o^2
+    double lamL, lamR;           // the two interval poles relative to d_o^2
+    double x;
+    double dl, du;               // the interval poles d_i, d_{i+1}
     Sums s;
-    if (!last) {
-        // sign of f at the interval midpoint picks the nearer pole as origin
-        const double xmid = h * (2.0 * dl + h);
-        s = pole_sums(d, z, N, i, dl, xmid, lane);
-        const double fmid = 1.0 + s.psi + s.phi;
-        if (fmid >= 0.0) {
-            o = i; dor = dl; lo = 0.0; hi = xmid;
-            lamL = 0.0; lamR = (du - dl) * (du + dl);
-            x = xmid;
-        } else {
-            o = i + 1; dor = du; lo = -h * (2.0 * du - h); hi = 0.0;
-            lamL = -(du - dl) * (du + dl); lamR = 0.0;
-            x = lo;                        // the same point, measured from d_{i+1}
-        }
-    } else {
-        o = i; dor = dl; lo = 0.0; hi = zz;
-        lamL = 0.0; lamR = 0.0;
-        x = 0.5 * zz;
-        s = pole_sums(d, z, N, i, dor, x, lane);
-    }
-    if (!(start_frac != start_frac)) {     // proposed start inside the bracket
-        const double xs = lo + start_frac * (hi - lo);
-        if (xs > lo && xs < hi) {
-            x = xs;
-            s = pole_sums(d, z, N, i, dor, x, lane);
-        }
-    }
+};
+
+// Safeguarded rational iteration from r.x; returns the iterations used or
+// -1 when max_iter did not suffice.  All lanes return the same result.
+__device__ __forceinline__ int root_iterate(const double *__restrict__ d, const double *__restrict__ z, int N, int i, bool last,
+                            int max_iter, RootState &r) {
+    const int lane = threadIdx.x & 31;
     int it = 0;
     for (;;) {
-        const double f = 1.0 + s.psi + s.phi;
-        const double scale = 1.0 + s.phi - s.psi;
+        const double f = 1.0 + r.s.psi + r.s.phi;
+        const double scale = 1.0 + r.s.phi - r.s.psi;
         if (fabs(f) <= 16.0 * kEps * scale) break;
-        if (f > 0.0) hi = x; else lo = x;
-        if (it >= max_iter) { it = -1; break; }
+        if (f > 0.0) r.hi = r.x; else r.lo = r.x;
+        if (it >= max_iter) return -1;
         // rational model through the two nearest poles (value and slope)
-        const double DL = lamL - x;
+        const double DL = r.lamL - r.x;
         double eta;
         bool ok = true;
         if (!last) {
-            const double DR = lamR - x;
-            const double sL = DL * DL * s.dpsi, sR = DR * DR * s.dphi;
-            const double C = f - DL * s.dpsi - DR * s.dphi;
+            const double DR = r.lamR - r.x;
+            const double sL = DL * DL * r.s.dpsi, sR = DR * DR * r.s.dphi;
+            const double C = f - DL * r.s.dpsi - DR * r.s.dphi;
             const double a = C * (DL + DR) + sL + sR;
             const double b = C * DL * DR + sL * DR + sR * DL;
             if (C == 0.0) {
@@ -124,28 +96,197 @@ __device__ int solve_root(const double *__restrict__ d, const double *__restrict
                 eta = (a > 0.0) ? (2.0 * b / (a + disc)) : ((a - disc) / (2.0 * C));
             }
         } else {
-            const double sL = DL * DL * s.dpsi;
-            const double C = f - DL * s.dpsi;
+            const double sL = DL * DL * r.s.dpsi;
+            const double C = f - DL * r.s.dpsi;
             if (C > 0.0) eta = DL + sL / C; else { eta = 0.0; ok = false; }
         }
-        double xn = x + eta;
-        if (!ok || !(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
-        const double step = xn - x;
-        x = xn;
+        double xn = r.x + eta;
+        if (!ok || !(xn > r.lo && xn < r.hi)) xn = 0.5 * (r.lo + r.hi);
+        const double step = xn - r.x;
+        r.x = xn;
         ++it;
-        s = pole_sums(d, z, N, i, dor, x, lane);
-        if (fabs(step) <= 4.0 * kEps * fabs(x)) break;
+        if (!last) {
+            // keep the origin at the nearer pole: an iterate past the interval
+            // midpoint is re-expressed from the other pole (x and D2 are
+            // within a factor 2, so x -+ D2 is exact); from the midpoint start
+            // the bracket never crosses, from a predicted start it may
+            const double D2 = r.lamR - r.lamL;
+            if (r.o == i && r.x > 0.5 * D2) {
+                r.o = i + 1; r.dor = r.du; r.x -= D2; r.lo -= D2; r.hi -= D2; r.lamL = -D2; r.lamR = 0.0;
+            } else if (r.o == i + 1 && r.x < -0.5 * D2) {
+                r.o = i; r.dor = r.dl; r.x += D2; r.lo += D2; r.hi += D2; r.lamL = 0.0; r.lamR = D2;
+            }
+        }
+        r.s = pole_sums(d, z, N, i, r.dor, r.x, lane);
+        if (fabs(step) <= 4.0 * kEps * fabs(r.x)) break;
     }
-    org_out = o;
-    // tau = w - d_o from x = (w - d_o)(w + d_o)
-    tau_out = x / (dor + sqrt(dor * dor + x));
     return it;
 }
 
-__global__ void __launch_bounds__(256) k_secular(const NodeDesc *__restrict__ nodes,
+// Solve root i of (d, z) (N entries, d[0] = 0 < d[1] < ...).  Returns the
+// number of iterations used, or -1 if not converged.  All lanes return the
+// same result.  vstart (NaN = none) is a predicted start (start_fraction of
+// a predicted logit, see bdc_mlp.cuh); with it the solver starts there
+// instead of evaluating the interval midpoint, and polishes from the nearer
+// pole if the prediction chose the farther one.
+__device__ __forceinline__ int solve_root(const double *__restrict__ d, const double *__restrict__ z, int N, int i,
+                          int max_iter, double zz, int &org_out, double &tau_out, double &x_out, double vstart) {
+    const int lane = threadIdx.x & 31;
+    if (N == 1) {
+        org_out = 0;
+        tau_out = fabs(z[0]);
+        x_out = tau_out * tau_out;
+        return 0;
+    }
+    const bool last = (i == N - 1);
+    const double dl = d[i];
+    const double du = last ? sqrt(dl * dl + zz) : d[i + 1];
+    const double h = 0.5 * (du - dl);
+    const bool use_mlp = !last && (vstart == vstart);
+    RootState r;
+    r.dl = dl;
+    r.du = du;
+    if (use_mlp) {
+        const double D2 = (du - dl) * (du + dl);
+        if (vstart > 0.0) {
+            r.o = i; r.dor = dl; r.lo = 0.0; r.hi = D2; r.lamL = 0.0; r.lamR = D2; r.x = vstart * D2;
+        } else {
+            r.o = i + 1; r.dor = du; r.lo = -D2; r.hi = 0.0; r.lamL = -D2; r.lamR = 0.0; r.x = vstart * D2;
+        }
+        if (!(r.x > r.lo && r.x < r.hi)) r.x = 0.5 * (r.lo + r.hi);
+        r.s = pole_sums(d, z, N, i, r.dor, r.x, lane);
+    } else if (!last) {
+        // sign of f at the interval midpoint picks the nearer pole as origin
+        const double xmid = h * (2.0 * dl + h);
+        r.s = pole_sums(d, z, N, i, dl, xmid, lane);
+        const double fmid = 1.0 + r.s.psi + r.s.phi;
+        if (fmid >= 0.0) {
+            r.o = i; r.dor = dl; r.lo = 0.0; r.hi = xmid;
+            r.lamL = 0.0; r.lamR = (du - dl) * (du + dl);
+            r.x = xmid;
+        } else {
+            r.o = i + 1; r.dor = du; r.lo = -h * (2.0 * du - h); r.hi = 0.0;
+            r.lamL = -(du - dl) * (du + dl); r.lamR = 0.0;
+            r.x = r.lo;                    // the same point, measured from d_{i+1}
+        }
+    } else {
+        r.o = i; r.dor = dl; r.lo = 0.0; r.hi = zz;
+        r.lamL = 0.0; r.lamR = 0.0;
+        r.x = 0.5 * zz;
+        r.s = pole_sums(d, z, N, i, r.dor, r.x, lane);
+    }
+    int it = root_iterate(d, z, N, i, last, max_iter, r);
+    if (use_mlp && it >= 0) {
+        // the origin must be the nearer pole (no cancellation in d_j - w)
+        const double D2 = (du - dl) * (du + dl);
+        bool sw = false;
+        if (r.o == i && r.x > 0.5 * D2) {
+            r.o = i + 1; r.dor = du; r.x -= D2; r.lo = -D2; r.hi = 0.0; r.lamL = -D2; r.lamR = 0.0; sw = true;
+        } else if (r.o == i + 1 && r.x < -0.5 * D2) {
+            r.o = i; r.dor = dl; r.x += D2; r.lo = 0.0; r.hi = D2; r.lamL = 0.0; r.lamR = D2; sw = true;
+        }
+        if (sw) {
+            if (!(r.x > r.lo && r.x < r.hi)) r.x = 0.5 * (r.lo + r.hi);
+            r.s = pole_sums(d, z, N, i, r.dor, r.x, lane);
+            const int it2 = root_iterate(d, z, N, i, last, max_iter, r);
+            it = (it2 < 0) ? -1 : it + 1 + it2;
+        }
+    }
+    org_out = r.o;
+    x_out = r.x;
+    // tau = w - d_o from x = (w - d_o)(w + d_o)
+    tau_out = r.x / (r.dor + sqrt(r.dor * r.dor + r.x));
+    return it;
+}
+
+// far-pole moment sums of root i from the merge's prefix (poles j <= i-9)
+// and suffix (poles j >= i+10) sums
+__device__ __forceinline__ void far_from_scans(const double *__restrict__ pz, long long stride, int N, int i,
+                                               FarSums &L, FarSums &R) {
+    const int jl = i - kMlpNear - 1, jr = i + kMlpNear + 2;
+    L = (jl >= 0) ? FarSums{pz[jl], pz[stride + jl], pz[2 * stride + jl]} : FarSums{0.0, 0.0, 0.0};
+    R = (jr <= N - 1) ? FarSums{pz[3 * stride + jr], pz[4 * stride + jr], pz[5 * stride + jr]}
+                      : FarSums{0.0, 0.0, 0.0};
+}
+
+// the same sums formed directly by one warp (standalone entry points)
+__device__ __forceinline__ void far_direct(const double *__restrict__ d, const double *__restrict__ z, int N,
+                                           int i, int lane, FarSums &L, FarSums &R) {
+    double l0 = 0.0, l1 = 0.0, l2 = 0.0, r0 = 0.0, r1 = 0.0, r2 = 0.0;
+    for (int j = lane; j < N; j += 32) {
+        const double z2 = z[j] * z[j], d2 = d[j] * d[j];
+        if (j <= i - kMlpNear - 1) { l0 += z2; l1 += z2 * d2; l2 += z2 * d2 * d2; }
+        if (j >= i + kMlpNear + 2) { r0 += z2; r1 += z2 * d2; r2 += z2 * d2 * d2; }
+    }
+    L = FarSums{warp_sum(l0), warp_sum(l1), warp_sum(l2)};
+    R = FarSums{warp_sum(r0), warp_sum(r1), warp_sum(r2)};
+}
+
+// natural log of a positive FP64 value to FP32 accuracy without a call:
+// exponent from the bits, FP32 log of the mantissa in [1, 2)
+__device__ __forceinline__ double log_approx(double v) {
+    const long long b = __double_as_longlong(v);
+    const int ex = (int)((b >> 52) & 0x7ff);
+    if (ex == 0 || ex == 0x7ff) return (v > 0.0 && ex == 0x7ff) ? 1e300 : -1e300;   // 0, subnormal, inf
+    const double mant = __longlong_as_double((b & 0x000fffffffffffffll) | 0x3ff0000000000000ll);
+    return (double)(ex - 1023) * 0.6931471805599453 + (double)__logf((float)mant);
+}
+
+// logit of the converged root's position, from x relative to its origin
+__device__ __forceinline__ double root_logit(int o, int i, double x, double D2) {
+    return (o == i) ? log_approx(x) - log_approx(D2 - x) : log_approx(D2 + x) - log_approx(-x);
+}
+
+// start fraction of a predicted logit y: +t for t = sigmoid(y) <= 1/2
+// (origin d_i, x = t D2), -(1 - t) otherwise (origin d_{i+1}, x = -(1-t) D2)
+// The logit is limited to +-36 (t >= 2e-16): a start closer to a pole than
+// that gains nothing and can leave the root finder crawling back.
+__device__ __forceinline__ double start_fraction(double y) {
+    const double ey = exp(-fmin(fabs(y), 36.0));
+    const double small = ey / (1.0 + ey);
+    return (y <= 0.0) ? small : -small;
+}
+
+// Start of every root but each merge's last: one thread per root computes
+// the features and the analytic estimate y_q, and with an MLP the corrected
+// start y_q + g (weights staged in shared memory).  Writes ystart (and,
+// when harvesting, the features and y_q for k_secular to append).
+__global__ void __launch_bounds__(128) k_root_start(const NodeDesc *__restrict__ nodes,
+                                                    const MatDesc *__restrict__ mats,
+                                                    const NodeState *__restrict__ state, int mmax, int nnodes,
+                                                    int seed_mode, const float *__restrict__ mlp) {
+    extern __shared__ float Ps[];
+    const bool use_net = (seed_mode == BDC_SEED_MLP);
+    if (use_net) {
+        for (int p = threadIdx.x; p < kMlpParams; p += blockDim.x) Ps[p] = mlp[p];
+        __syncthreads();
+    }
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int node = (int)(idx / mmax), i = (int)(idx % mmax);
+    if (node >= nnodes) return;
+    const NodeDesc nd = nodes[node];
+    const int N = state[nd.id].N;
+    if (i >= N - 1) return;
+    const MatDesc md = mats[nd.mat];
+    const double *d = md.dM + nd.r0, *z = md.zM + nd.r0;
+    FarSums L, R;
+    far_from_scans(md.pz + nd.r0, md.n, N, i, L, R);
+    float f[kMlpIn];
+    const double yq = mlp_features(d, z, N, i, state[nd.id].rho, L, R, f);
+    double ys = yq;
+    if (use_net) ys += (double)mlp_predict_thread(Ps, f);
+    md.ystart[nd.r0 + i] = start_fraction(ys);
+    if (md.feat != nullptr) {
+        md.yq[nd.r0 + i] = yq;
+#pragma unroll
+        for (int k = 0; k < kMlpIn; ++k) md.fs[(size_t)(nd.r0 + i) * kMlpIn + k] = f[k];
+    }
+}
+
+__global__ void __launch_bounds__(256, 2) k_secular(const NodeDesc *__restrict__ nodes,
                                                  const MatDesc *__restrict__ mats,
                                                  NodeState *__restrict__ state, int mmax,
-                                                 int max_iter, int nnodes) {
+                                                 int max_iter, int nnodes, int seed_mode) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     const int node = warp / mmax, i = warp % mmax;
     if (node >= nnodes) return;
@@ -155,42 +296,83 @@ __global__ void __launch_bounds__(256) k_secular(const NodeDesc *__restrict__ no
     const MatDesc md = mats[nd.mat];
     const double *d = md.dM + nd.r0, *z = md.zM + nd.r0;
     const int N = ns.N;
-    double zz = 0.0;
-    if (i == N - 1) {
-        for (int j = lane; j < N; j += 32) zz = fma(z[j], z[j], zz);
-        zz = warp_sum(zz);
-    }
+    const double zz = ns.rho;                       // sum z^2 (computed by the merge prep)
+    double vstart = __longlong_as_double(0x7ff8000000000000ll);   // NaN: plain start
+    if (seed_mode != BDC_SEED_PLAIN && i < N - 1) vstart = md.ystart[nd.r0 + i];
     int o;
-    double tau;
-    const int it = solve_root(d, z, N, i, max_iter, zz, o, tau, __longlong_as_double(0x7ff8000000000000ll));
+    double tau, x;
+    const int it = solve_root(d, z, N, i, max_iter, zz, o, tau, x, vstart);
     if (lane == 0) {
         md.org[nd.r0 + i] = o;
         md.tau[nd.r0 + i] = tau;
         md.omega[nd.r0 + i] = d[o] + tau;
         if (it < 0) atomicAdd(md.info, 1);
         atomicAdd(&state[nd.id].iters, (unsigned long long)(it < 0 ? max_iter : it));
+        if (md.feat != nullptr && i < N - 1 && it >= 0) {
+            // harvest (features, y - y_q): the network learns the correction
+            const double D2 = (d[i + 1] - d[i]) * (d[i + 1] + d[i]);
+            const int slot = atomicAdd(md.hcount, 1);
+            if (slot < md.hcap) {
+                const float *fr = md.fs + (size_t)(nd.r0 + i) * kMlpIn;
+#pragma unroll
+                for (int k = 0; k < kMlpIn; ++k) md.feat[(size_t)slot * kMlpIn + k] = fr[k];
+                md.targ[slot] = clamp40(root_logit(o, i, x, D2) - md.yq[nd.r0 + i]);
+            }
+        }
     }
 }
 
-__global__ void __launch_bounds__(256) k_secular_single(int N, const double *d, const double *z, int *org,
+__device__ __forceinline__ double warp_sumsq(const double *__restrict__ z, int N, int lane) {
+    double zz = 0.0;
+    for (int j = lane; j < N; j += 32) zz = fma(z[j], z[j], zz);
+    return warp_sum(zz);
+}
+
+__global__ void __launch_bounds__(256, 2) k_secular_single(int N, const double *d, const double *z, int *org,
                                                         double *tau, double *omega, int max_iter,
-                                                        int *info) {
+                                                        int *info, int seed_mode, const float *__restrict__ mlp,
+                                                        int *iters) {
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (i >= N) return;
-    double zz = 0.0;
-    if (i == N - 1) {
-        for (int j = lane; j < N; j += 32) zz = fma(z[j], z[j], zz);
-        zz = warp_sum(zz);
+    const bool need_rho = (i == N - 1) || seed_mode != BDC_SEED_PLAIN;
+    const double zz = need_rho ? warp_sumsq(z, N, lane) : 0.0;
+    double ystart = __longlong_as_double(0x7ff8000000000000ll);
+    if (seed_mode != BDC_SEED_PLAIN && i < N - 1) {
+        float f[kMlpIn];
+        FarSums L, R;
+        far_direct(d, z, N, i, lane, L, R);
+        const double yq = mlp_features(d, z, N, i, zz, L, R, f);
+        ystart = start_fraction((seed_mode == BDC_SEED_MLP) ? yq + (double)mlp_predict_thread(mlp, f) : yq);
     }
     int o;
-    double t;
-    const int it = solve_root(d, z, N, i, max_iter, zz, o, t, __longlong_as_double(0x7ff8000000000000ll));
+    double t, x;
+    const int it = solve_root(d, z, N, i, max_iter, zz, o, t, x, ystart);
     if (lane == 0) {
         org[i] = o;
         tau[i] = t;
         omega[i] = d[o] + t;
+        if (iters) iters[i] = it;
         if (it < 0) atomicAdd(info, 1);
     }
+}
+
+// features and analytic estimates of roots 0..N-2 of one secular problem
+__global__ void __launch_bounds__(256) k_mlp_features_single(int N, const double *d, const double *z,
+                                                             float *feat, double *yq_out) {
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (i >= N - 1) return;
+    const double zz = warp_sumsq(z, N, lane);
+    FarSums L, R;
+    far_direct(d, z, N, i, lane, L, R);
+    float f[kMlpIn];
+    const double yq = mlp_features(d, z, N, i, zz, L, R, f);
+    if (lane < kMlpIn) {
+        float v = f[0];
+#pragma unroll
+        for (int k = 1; k < kMlpIn; ++k) if (lane == k) v = f[k];
+        feat[(size_t)i * kMlpIn + lane] = v;
+    }
+    if (lane == 0 && yq_out) yq_out[i] = yq;
 }
 
 // |z~_i|^2 of Eq. (bdc-zi), 0-based: (w_{N-1}^2 - d_i^2) *
@@ -306,14 +488,23 @@ __global__ void __launch_bounds__(256) k_mvectors_single(int N, const double *d,
 }  // namespace
 
 cudaError_t launch_secular(const NodeDesc *nodes, int nnodes, const MatDesc *mats, NodeState *state,
-                           int mmax, int max_iter, int seed_mode, const float *mlp, cudaStream_t st) {
-    (void)seed_mode; (void)mlp;
+                           int mmax, int max_iter, int seed_mode, const float *mlp, int harvest,
+                           cudaStream_t st) {
     if (nnodes <= 0) return cudaSuccess;
-    const long long warps = (long long)nnodes * mmax;
-    k_secular<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(nodes, mats, state, mmax, max_iter, nnodes);
+    const long long roots = (long long)nnodes * mmax;
+    if (seed_mode != BDC_SEED_PLAIN || harvest) {
+        const size_t smem = (seed_mode == BDC_SEED_MLP) ? sizeof(float) * kMlpParams : 0;
+        if (smem > 48 * 1024) return cudaErrorInvalidValue;
+        k_root_start<<<(unsigned)((roots + 127) / 128), 128, smem, st>>>(nodes, mats, state, mmax, nnodes,
+                                                                          seed_mode, mlp);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    k_secular<<<(unsigned)((roots + 7) / 8), 256, 0, st>>>(nodes, mats, state, mmax, max_iter, nnodes,
+                                                           seed_mode);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_lowner<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(nodes, mats, state, mmax, nnodes);
+    k_lowner<<<(unsigned)((roots + 7) / 8), 256, 0, st>>>(nodes, mats, state, mmax, nnodes);
     return cudaGetLastError();
 }
 
@@ -325,9 +516,18 @@ cudaError_t launch_vectors(const NodeDesc *nodes, int nnodes, const MatDesc *mat
 }
 
 cudaError_t launch_secular_single(int N, const double *d, const double *z, int *org, double *tau,
-                                  double *omega, int max_iter, int *info, cudaStream_t st) {
+                                  double *omega, int max_iter, int *info, int seed_mode, const float *mlp,
+                                  int *iters, cudaStream_t st) {
     if (N <= 0) return cudaSuccess;
-    k_secular_single<<<(N + 7) / 8, 256, 0, st>>>(N, d, z, org, tau, omega, max_iter, info);
+    k_secular_single<<<(N + 7) / 8, 256, 0, st>>>(N, d, z, org, tau, omega, max_iter, info, seed_mode, mlp,
+                                                   iters);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_features_single(int N, const double *d, const double *z, float *feat, double *yq,
+                                       cudaStream_t st) {
+    if (N <= 1) return cudaSuccess;
+    k_mlp_features_single<<<(N - 1 + 7) / 8, 256, 0, st>>>(N, d, z, feat, yq);
     return cudaGetLastError();
 }
 
