@@ -7,6 +7,7 @@ seed 0), singular values and both vector sets, through the C ABI
 The metric is time per SVD (lower is better).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--prec exact|fp64|bf16x3]
+                  [--start mlp|analytic|plain]
   python bench.py --impl reference ...   # the FP64 CPU oracle on host cores
 
 Multi-GPU runs (torchrun) are independent replicas (weak scaling): every rank
@@ -51,6 +52,8 @@ def parse():
     ap.add_argument("--leaf", type=int, default=16)
     ap.add_argument("--slices", type=int, default=0, help="0 = automatic (6 up to n=8192, 7 above)")
     ap.add_argument("--mixed-min", type=int, default=0, help="smallest merge order using split BF16 (0 = auto)")
+    ap.add_argument("--start", default="mlp", choices=["plain", "analytic", "mlp"],
+                    help="secular root start: interval midpoint, analytic estimate, or analytic + trained MLP")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true")
@@ -189,7 +192,28 @@ def main():
     e_pin = torch.from_numpy(e_h).pin_memory()
     d = d_pin.to(dev)
     e = e_pin.to(dev)
-    o = bdc.make_opts(a.prec, a.leaf, 64, a.slices, mixed_min=a.mixed_min)
+    # root starts: the MLP is trained here, before any timing, with the
+    # library's own kernels on roots harvested from FP64 runs of n = 8192
+    # uniform (seed 4) and graded (seed 5) bidiagonals
+    P = None
+    train_info = None
+    if a.start == "mlp":
+        t0 = time.perf_counter()
+        H = bdc.Harvest(1 << 21, device=dev)
+        for kind, sd in (("uniform", 4), ("graded", 5)):
+            dh, eh = inputs.make(kind, 8192, sd)
+            bdc.svd_harvest(torch.from_numpy(dh).to(dev), torch.from_numpy(eh).to(dev), H)
+        F, R = H.data()
+        P, losses = bdc.mlp_train(F, R, steps=1500, lr=3e-3, seed=0, huber=0.25)
+        torch.cuda.synchronize()
+        g = bdc.mlp_predict(P, F)
+        train_info = {"samples": int(F.shape[0]), "steps": 1500, "loss": [float(losses[0]), float(losses[-1])],
+                      "median_abs_err_analytic": float(R.abs().median()),
+                      "median_abs_err_mlp": float((g - R).abs().median()),
+                      "seconds": time.perf_counter() - t0,
+                      "data": "harvest of n=8192 uniform seed 4 + graded seed 5 (FP64 runs)"}
+        del H
+    o = bdc.make_opts(a.prec, a.leaf, 64, a.slices, seed=a.start, mlp=P, mixed_min=a.mixed_min)
     lw = bdc.workspace_bytes(n, o)
     work = torch.empty(lw + 256, dtype=torch.uint8, device=dev)
     Ut = torch.empty((n, n), dtype=torch.float64, device=dev)
@@ -321,6 +345,25 @@ def main():
             stages[k]["hbm_frac"] = stages[k]["GBps"] / hbm
     launches = int(sum(v["launches"] for v in prof.values()) / a.steps) * a.steps
 
+    # the root-start comparison: one untimed run with the plain midpoint start
+    root_start = {"mode": a.start, "iters_per_root": stages["secular"].get("iters_per_root"),
+                  "secular_ms_per_step": stages["secular"]["ms_per_step"], "mlp_training": train_info}
+    if a.start != "plain":
+        o_plain = bdc.make_opts(a.prec, a.leaf, 64, a.slices, seed="plain", mixed_min=a.mixed_min)
+        bdc.profile_begin()
+        q0 = torch.cuda.Event(enable_timing=True)
+        q1 = torch.cuda.Event(enable_timing=True)
+        q0.record(st)
+        rc = L.bdc_svd_ex(n, bdc._ptr(d), bdc._ptr(e), bdc._ptr(Ut), bdc._ptr(S), bdc._ptr(VTt), n, n,
+                          ctypes.byref(o_plain), bdc._ptr(work), work.numel(), bdc._ptr(info),
+                          ctypes.c_void_p(st.cuda_stream))
+        q1.record(st)
+        torch.cuda.synchronize()
+        pp = bdc.profile_end()
+        if rc == 0 and pp["secular"].get("roots"):
+            root_start["plain"] = {"iters_per_root": pp["secular"]["iters"] / pp["secular"]["roots"],
+                                   "secular_ms": pp["secular"]["ms"], "svd_ms": q0.elapsed_time(q1)}
+
     cpu = None
     if not a.no_cpu_baseline and world == 1:
         cpu = cpu_baseline_oracle(n, a.kind, a.seed)
@@ -342,12 +385,13 @@ def main():
         "config": {"workload": workload_name(a), "n": n, "prec": a.prec, "leaf": a.leaf,
                    "slices": (a.slices or (6 if n <= 8192 else 7)) if a.prec == "exact" else None,
                    "l2": "inputs larger than L2 (U, V and workspace > 10 GB per step)",
-                   "parallelism": f"replicas x{world}"},
+                   "start": a.start, "parallelism": f"replicas x{world}"},
         "gflops_paper_model": flops_model / (ms * 1e-3) / 1e9,
         "status": status,
         "accuracy": acc,
         "roofline": roofline,
         "stages": stages,
+        "root_start": root_start,
         "gpu_launches": launches,
         "e2e": e2e,
         "cpu_baseline": cpu,
