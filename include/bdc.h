@@ -113,6 +113,35 @@ int bdc_svd_batched(int batch, const int *h_n, const double *const *d, const dou
                     const int *h_ldvt, const bdc_opts *o, void *work, size_t lwork,
                     int *d_info, bdc_stream_t stream);
 
+/* ---------------- plans: a fixed batch as one CUDA graph -----------------
+ * bdc_plan_create records the whole launch sequence of bdc_svd_batched for
+ * fixed sizes, pointers and options into a CUDA graph (nothing runs at
+ * creation); bdc_plan_launch replays it on `stream` with one graph launch:
+ * every stage of every level of every matrix, no host work per call.
+ * Arguments as for bdc_svd_batched (batch >= 1; a single matrix is a batch
+ * of one); `work`, the matrices and d_info must stay valid while the plan
+ * is used, and launches of one plan must not overlap on the GPU (they share
+ * the workspace).  The descriptors are copied from host memory that the
+ * plan owns, so the plan is independent of later calls.  Returns 0 or a
+ * negative argument code / BDC_ERR_CUDA; *plan is NULL on failure. */
+typedef struct bdc_plan_s *bdc_plan;
+int bdc_plan_create(bdc_plan *plan, int batch, const int *h_n, const double *const *d, const double *const *e,
+                    double *const *U, double *const *S, double *const *VT, const int *h_ldu, const int *h_ldvt,
+                    const bdc_opts *o, void *work, size_t lwork, int *d_info);
+int bdc_plan_launch(bdc_plan plan, bdc_stream_t stream);
+void bdc_plan_destroy(bdc_plan plan);
+
+/* Autotuner for batches: times candidate plans on synthetic bidiagonals of
+ * the given orders (d, e ~ U(0.5, 1.5), counter-based generator) and writes
+ * the fastest leaf size into o->leaf, and for split-BF16 products the
+ * fastest o->mixed_min (the merge order from which products use them).
+ * Other fields of *o are kept.  `reps` timed graph launches per candidate
+ * (0 = 3).  Allocates and frees its own device memory on `stream` and
+ * synchronises it.  Results are cached per (order histogram in powers of
+ * two, precision, start rule): a repeated call returns the cached choice
+ * without timing.  *ms (may be NULL) gets the best time per batch. */
+int bdc_autotune(int batch, const int *h_n, bdc_opts *o, int reps, double *ms, bdc_stream_t stream);
+
 /* ---------------- step entry points (one merge stage each) ----------------
  * They run a single stage of Sec. 4.2.1 on one problem so that each kernel
  * can be checked against the oracle element by element.  d is sorted

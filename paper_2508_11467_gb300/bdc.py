@@ -60,6 +60,10 @@ _SIGS = {
     "bdc_mlp_adam": (_I, [_VP, _VP, _VP, _VP, _I, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                           ctypes.c_float, _VP]),
     "bdc_mlp_predict": (_I, [_VP, _VP, _I, _VP, _VP]),
+    "bdc_plan_create": (_I, [_VP, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
+    "bdc_plan_launch": (_I, [_VP, _VP]),
+    "bdc_plan_destroy": (None, [_VP]),
+    "bdc_autotune": (_I, [_I, _VP, _VP, _I, _VP, _VP]),
     "bdc_status_string": (ctypes.c_char_p, [_I]),
     "bdc_profile_begin": (_I, [_I]),
     "bdc_profile_end": (_I, [_VP, _VP, _VP]),
@@ -453,3 +457,77 @@ def mlp_load(path, device="cuda"):
     if a.size != mlp_param_count():
         raise ValueError(f"{path}: {a.size} floats, expected {mlp_param_count()}")
     return torch.from_numpy(a).to(device)
+
+
+# ---------------------------------------------------------------- batched plans
+class BatchPlan:
+    """A fixed batch of bidiagonals solved by one CUDA-graph launch.
+
+    d_flat, e_flat: CUDA float64 tensors holding the matrices back to back
+    (matrix b at offset sum(ns[:b]); e has n-1 entries there).  Outputs live in
+    flat buffers: S at the same offsets, U and V^T (column-major, n x n) at
+    offsets sum(ns[:b]**2).  Built by bdc_plan_create; launch() enqueues the
+    whole solve on the stream."""
+
+    def __init__(self, d_flat, e_flat, ns, *, prec="fp64", leaf=16, max_iter=64, slices=0, seed="plain",
+                 mlp=None, mixed_min=0):
+        import numpy as np
+        self.ns = np.asarray(ns, dtype=np.int32)
+        B = len(self.ns)
+        dev = d_flat.device
+        self.d, self.e = _dev(d_flat), _dev(e_flat)
+        self.off = np.concatenate([[0], np.cumsum(self.ns, dtype=np.int64)])
+        self.off2 = np.concatenate([[0], np.cumsum(self.ns.astype(np.int64) ** 2)])
+        self.S = torch.empty(int(self.off[-1]), dtype=torch.float64, device=dev)
+        self.U = torch.empty(int(self.off2[-1]), dtype=torch.float64, device=dev)
+        self.VT = torch.empty(int(self.off2[-1]), dtype=torch.float64, device=dev)
+        self.info = torch.zeros(B, dtype=torch.int32, device=dev)
+        self.opts = make_opts(prec, leaf, max_iter, slices, seed, mlp, mixed_min)
+        self._mlp = mlp
+        lw = int(lib().bdc_svd_batched_workspace(B, self.ns.ctypes.data_as(ctypes.c_void_p), ctypes.byref(self.opts)))
+        self.work = torch.empty(lw + 256, dtype=torch.uint8, device=dev)
+        ptrs = lambda base, offs, esz: (ctypes.c_void_p * B)(*[base.data_ptr() + int(o) * esz for o in offs[:B]])
+        self._pd = ptrs(self.d, self.off, 8)
+        self._pe = ptrs(self.e, self.off, 8)
+        self._pu = ptrs(self.U, self.off2, 8)
+        self._ps = ptrs(self.S, self.off, 8)
+        self._pv = ptrs(self.VT, self.off2, 8)
+        self._ld = self.ns.copy()
+        self._plan = ctypes.c_void_p()
+        _check("bdc_plan_create", lib().bdc_plan_create(
+            ctypes.byref(self._plan), B, self.ns.ctypes.data_as(ctypes.c_void_p), self._pd, self._pe, self._pu,
+            self._ps, self._pv, self._ld.ctypes.data_as(ctypes.c_void_p), self._ld.ctypes.data_as(ctypes.c_void_p),
+            ctypes.byref(self.opts), _ptr(self.work), self.work.numel(), _ptr(self.info)))
+
+    def launch(self, stream=None):
+        _check("bdc_plan_launch", lib().bdc_plan_launch(self._plan, _stream(stream)))
+
+    def result(self, b):
+        """(S, U, VT) of matrix b as CUDA views (U[:, i] left vectors)."""
+        n = int(self.ns[b])
+        o, o2 = int(self.off[b]), int(self.off2[b])
+        U = self.U[o2:o2 + n * n].view(n, n).t()
+        VT = self.VT[o2:o2 + n * n].view(n, n).t()
+        return self.S[o:o + n], U, VT
+
+    def close(self):
+        if getattr(self, "_plan", None) is not None and self._plan.value:
+            lib().bdc_plan_destroy(self._plan)
+            self._plan = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def autotune(ns, prec="fp64", seed="plain", slices=0, reps=3, stream=None):
+    """bdc_autotune: (leaf, mixed_min, ms per batch) for a batch of orders ns."""
+    import numpy as np
+    ns = np.asarray(ns, dtype=np.int32)
+    o = make_opts(prec, 16, 64, slices, seed)
+    ms = ctypes.c_double(0.0)
+    _check("bdc_autotune", lib().bdc_autotune(len(ns), ns.ctypes.data_as(ctypes.c_void_p), ctypes.byref(o),
+                                               int(reps), ctypes.byref(ms), _stream(stream)))
+    return int(o.leaf), int(o.mixed_min), float(ms.value)

@@ -249,6 +249,11 @@ __global__ void k_scale(const MatDesc *__restrict__ mats) {
 }
 
 // final order (descending), unscale, U columns and V^T rows (tiled transpose)
+__global__ void k_info(const MatDesc *__restrict__ mats, int nmat, int *__restrict__ out) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m < nmat) out[m] = *mats[m].info;
+}
+
 __global__ void k_final(const MatDesc *__restrict__ mats, int tiles_per_side) {
     __shared__ double tile[32][33];
     const MatDesc md = mats[blockIdx.z];
@@ -277,6 +282,30 @@ __global__ void k_final(const MatDesc *__restrict__ mats, int tiles_per_side) {
         if (j < n && c < n) md.VTo[(size_t)j * md.ldvt + c] = tile[tx][jj];
     }
 }
+
+// Pinned host memory owned by a plan: while a plan captures its launch
+// sequence into a CUDA graph, every host->device copy of descriptors and
+// tables reads from blocks that live as long as the plan (the graph replays
+// those copies), instead of the shared cache and ring of one-shot calls.
+struct PinnedArena {
+    std::vector<void *> blocks;
+    void *alloc(size_t bytes) {
+        void *q = nullptr;
+        if (cudaMallocHost(&q, bytes) != cudaSuccess) return nullptr;
+        blocks.push_back(q);
+        return q;
+    }
+    ~PinnedArena() {
+        for (void *q : blocks) cudaFreeHost(q);
+    }
+};
+thread_local PinnedArena *g_arena = nullptr;
+
+}  // namespace
+
+void *plan_pinned_alloc(size_t bytes) { return g_arena ? g_arena->alloc(bytes) : nullptr; }
+
+namespace {
 
 struct PinnedBlob {
     void *host = nullptr;
@@ -346,6 +375,12 @@ cudaError_t upload(const Plan &p, char *work, const std::vector<MatDesc> &mats, 
     std::vector<long long> key((bytes + 7) / 8, 0);
     std::memcpy(key.data(), blob.data(), bytes);
     void *host = nullptr;
+    if (g_arena) {
+        host = g_arena->alloc(bytes);
+        if (!host) return cudaErrorMemoryAllocation;
+        std::memcpy(host, blob.data(), bytes);
+        return cudaMemcpyAsync(work, host, bytes, cudaMemcpyHostToDevice, st);
+    }
     {
         std::lock_guard<std::mutex> lk(g_cache_mu);
         auto it = g_cache.find(key);
@@ -476,9 +511,9 @@ int run_plan(const Plan &p, const bdc_opts &o, char *work, std::vector<MatDesc> 
         if ((e = cudaGetLastError()) != cudaSuccess) return note(e);
     }
     // gather the per-matrix status words into the caller's d_info
-    for (int mi = 0; mi < p.nmat; ++mi) {
-        e = cudaMemcpyAsync(d_info_out + mi, mats[mi].info, sizeof(int), cudaMemcpyDeviceToDevice, st);
-        if (e != cudaSuccess) return note(e);
+    if (p.nmat > 0) {
+        k_info<<<(p.nmat + 255) / 256, 256, 0, st>>>(dmats, p.nmat, d_info_out);
+        if ((e = cudaGetLastError()) != cudaSuccess) return note(e);
     }
     return 0;
 }
@@ -621,11 +656,36 @@ size_t bdc_svd_batched_workspace(int batch, const int *h_n, const bdc_opts *o) {
     return make_plan(batch, h_n, resolve(o, nmax)).total;
 }
 
-int bdc_svd_batched(int batch, const int *h_n, const double *const *d, const double *const *e, double *const *U,
-                    double *const *S, double *const *VT, const int *h_ldu, const int *h_ldvt, const bdc_opts *o,
-                    void *work, size_t lwork, int *d_info, bdc_stream_t stream) {
+}  // extern "C"
+
+namespace bdc {
+namespace {
+
+// synthetic autotuning input: x[k] = 0.5 + u_k, u_k in [0, 1) from splitmix64 of
+// (seed, k) (53 random bits)
+__global__ void k_fill_uniform(double *__restrict__ x, long long count, unsigned long long seed) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    unsigned long long z = seed * 0x9E3779B97F4A7C15ull + (unsigned long long)k + 1;
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    x[k] = 0.5 + (double)(z >> 11) * 0x1.0p-53;
+}
+
+struct TuneResult {
+    int leaf, mixed_min;
+    double ms;
+};
+std::mutex g_tune_mu;
+std::map<std::vector<int>, TuneResult> g_tune;
+
+// argument checks and plan set-up shared by bdc_svd_batched and bdc_plan_create
+int batched_setup(int batch, const int *h_n, const double *const *d, const double *const *e, double *const *U,
+                  double *const *S, double *const *VT, const int *h_ldu, const int *h_ldvt, const bdc_opts *o,
+                  void *work, size_t lwork, int *d_info, Plan &p, bdc_opts &r, char *&w, std::vector<MatDesc> &mats) {
     if (batch < 0) return -1;
-    if (batch == 0) return 0;
     if (!h_n) return -2;
     if (!d) return -3;
     if (!e) return -4;
@@ -641,21 +701,224 @@ int bdc_svd_batched(int batch, const int *h_n, const double *const *d, const dou
     }
     int nmax = 0;
     for (int b = 0; b < batch; ++b) nmax = std::max(nmax, h_n[b]);
-    const bdc_opts r = resolve(o, nmax);
+    r = resolve(o, nmax);
     if (check_opts(r)) return -10;
     if (!d_info) return -13;
-    const Plan p = make_plan(batch, h_n, r);
+    p = make_plan(batch, h_n, r);
     if (!work) return -11;
     if (lwork < p.total) return -12;
-    char *w = (char *)(((uintptr_t)work + 255) & ~(uintptr_t)255);
+    w = (char *)(((uintptr_t)work + 255) & ~(uintptr_t)255);
     if ((size_t)(w - (char *)work) + p.total - 256 > lwork) return -12;
-    std::vector<MatDesc> mats(batch);
+    mats.assign(batch, MatDesc{});
     for (int b = 0; b < batch; ++b) {
         mats[b].n = h_n[b]; mats[b].d_in = d[b]; mats[b].e_in = e[b];
         mats[b].Uo = U[b]; mats[b].So = S[b]; mats[b].VTo = VT[b];
         mats[b].ldu = h_ldu[b]; mats[b].ldvt = h_ldvt[b];
     }
+    return 0;
+}
+
+}  // namespace
+}  // namespace bdc
+
+// a captured launch sequence: the whole solve of a fixed batch as one graph
+struct bdc_plan_s {
+    bdc::PinnedArena arena;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int batch = 0;
+};
+
+extern "C" {
+
+int bdc_svd_batched(int batch, const int *h_n, const double *const *d, const double *const *e, double *const *U,
+                    double *const *S, double *const *VT, const int *h_ldu, const int *h_ldvt, const bdc_opts *o,
+                    void *work, size_t lwork, int *d_info, bdc_stream_t stream) {
+    if (batch == 0) return 0;
+    Plan p;
+    bdc_opts r;
+    char *w = nullptr;
+    std::vector<MatDesc> mats;
+    if (int a = batched_setup(batch, h_n, d, e, U, S, VT, h_ldu, h_ldvt, o, work, lwork, d_info, p, r, w, mats))
+        return a;
     return run_plan(p, r, w, mats, d_info, (cudaStream_t)stream);
+}
+
+int bdc_plan_create(bdc_plan *plan, int batch, const int *h_n, const double *const *d, const double *const *e,
+                    double *const *U, double *const *S, double *const *VT, const int *h_ldu, const int *h_ldvt,
+                    const bdc_opts *o, void *work, size_t lwork, int *d_info) {
+    if (!plan) return -14;
+    *plan = nullptr;
+    if (batch <= 0) return -1;
+    Plan p;
+    bdc_opts r;
+    char *w = nullptr;
+    std::vector<MatDesc> mats;
+    if (int a = batched_setup(batch, h_n, d, e, U, S, VT, h_ldu, h_ldvt, o, work, lwork, d_info, p, r, w, mats))
+        return a;
+    bdc_plan_s *pl = new bdc_plan_s();
+    pl->batch = batch;
+    cudaStream_t cs = nullptr;
+    cudaError_t ce = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (ce != cudaSuccess) { delete pl; return note(ce); }
+    // capture (nothing runs now): descriptor and table copies read the plan's
+    // own pinned blocks; stage profiling is off while capturing
+    const bool prof = g_prof.on;
+    g_prof.on = false;
+    g_arena = &pl->arena;
+    int rc = note(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+    if (rc == 0) {
+        rc = run_plan(p, r, w, mats, d_info, cs);
+        cudaGraph_t g = nullptr;
+        const int rc2 = note(cudaStreamEndCapture(cs, &g));
+        if (rc == 0) rc = rc2;
+        pl->graph = g;
+    }
+    g_arena = nullptr;
+    g_prof.on = prof;
+    cudaStreamDestroy(cs);
+    if (rc == 0) rc = note(cudaGraphInstantiate(&pl->exec, pl->graph, 0));
+    if (rc != 0) {
+        if (pl->graph) cudaGraphDestroy(pl->graph);
+        delete pl;
+        return rc;
+    }
+    *plan = pl;
+    return 0;
+}
+
+int bdc_plan_launch(bdc_plan plan, bdc_stream_t stream) {
+    if (!plan || !plan->exec) return -1;
+    return note(cudaGraphLaunch(plan->exec, (cudaStream_t)stream));
+}
+
+void bdc_plan_destroy(bdc_plan plan) {
+    if (!plan) return;
+    if (plan->exec) cudaGraphExecDestroy(plan->exec);
+    if (plan->graph) cudaGraphDestroy(plan->graph);
+    delete plan;
+}
+
+int bdc_autotune(int batch, const int *h_n, bdc_opts *o, int reps, double *ms_out, bdc_stream_t stream) {
+    if (batch <= 0) return -1;
+    if (!h_n) return -2;
+    if (!o) return -3;
+    for (int b = 0; b < batch; ++b) if (h_n[b] < 1 || h_n[b] > 2048) return -2;
+    if (reps <= 0) reps = 3;
+    int nmax = 0;
+    for (int b = 0; b < batch; ++b) nmax = std::max(nmax, h_n[b]);
+    const bdc_opts base = resolve(o, nmax);
+    if (check_opts(base)) return -3;
+    cudaStream_t st = (cudaStream_t)stream;
+    // cache key: precision, start rule, slices, and the order histogram in powers of two
+    std::vector<int> key = {base.prec, base.seed, base.slices};
+    key.resize(3 + 12, 0);
+    for (int b = 0; b < batch; ++b) {
+        int k = 0;
+        while ((2 << k) <= h_n[b]) ++k;
+        key[3 + k]++;
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            o->leaf = it->second.leaf;
+            o->mixed_min = it->second.mixed_min;
+            if (ms_out) *ms_out = it->second.ms;
+            return 0;
+        }
+    }
+    // synthetic matrices, outputs, status words
+    long long sn = 0, sn2 = 0;
+    std::vector<long long> off(batch), off2(batch);
+    for (int b = 0; b < batch; ++b) {
+        off[b] = sn; off2[b] = sn2;
+        sn += h_n[b]; sn2 += (long long)h_n[b] * h_n[b];
+    }
+    const std::vector<int> leaves = {8, 12, 16, 24, 32};
+    const std::vector<int> mins = {128, 256, 512, 1024, 4096};   // 4096: FP64 products everywhere
+    size_t lw = 0;
+    for (int L : leaves) {
+        bdc_opts c = base;
+        c.leaf = L;
+        lw = std::max(lw, make_plan(batch, h_n, c).total);
+    }
+    double *dbuf = nullptr, *ebuf = nullptr, *Ub = nullptr, *VTb = nullptr, *Sb = nullptr;
+    int *info = nullptr;
+    void *work = nullptr;
+    auto release = [&] {
+        for (void *q : {(void *)dbuf, (void *)ebuf, (void *)Ub, (void *)VTb, (void *)Sb, (void *)info, work})
+            if (q) cudaFreeAsync(q, st);
+        cudaStreamSynchronize(st);
+    };
+    int rc = note(cudaMallocAsync(&dbuf, sizeof(double) * sn, st));
+    if (!rc) rc = note(cudaMallocAsync(&ebuf, sizeof(double) * sn, st));
+    if (!rc) rc = note(cudaMallocAsync(&Ub, sizeof(double) * sn2, st));
+    if (!rc) rc = note(cudaMallocAsync(&VTb, sizeof(double) * sn2, st));
+    if (!rc) rc = note(cudaMallocAsync(&Sb, sizeof(double) * sn, st));
+    if (!rc) rc = note(cudaMallocAsync(&info, sizeof(int) * batch, st));
+    if (!rc) rc = note(cudaMallocAsync(&work, lw + 256, st));
+    if (rc) { release(); return rc; }
+    k_fill_uniform<<<(unsigned)((sn + 255) / 256), 256, 0, st>>>(dbuf, sn, 0x5eedull);
+    k_fill_uniform<<<(unsigned)((sn + 255) / 256), 256, 0, st>>>(ebuf, sn, 0x5eefull);
+    if ((rc = note(cudaGetLastError()))) { release(); return rc; }
+    std::vector<const double *> pd(batch), pe(batch);
+    std::vector<double *> pu(batch), ps(batch), pv(batch);
+    for (int b = 0; b < batch; ++b) {
+        pd[b] = dbuf + off[b]; pe[b] = ebuf + off[b]; ps[b] = Sb + off[b];
+        pu[b] = Ub + off2[b]; pv[b] = VTb + off2[b];
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    auto time_one = [&](const bdc_opts &c, double &t) -> int {
+        bdc_plan pl = nullptr;
+        int r = bdc_plan_create(&pl, batch, h_n, pd.data(), pe.data(), pu.data(), ps.data(), pv.data(), h_n, h_n,
+                                &c, work, lw + 256, info);
+        if (r) return r;
+        r = bdc_plan_launch(pl, st);                          // warm-up
+        if (!r) r = note(cudaEventRecord(e0, st));
+        for (int k = 0; k < reps && !r; ++k) r = bdc_plan_launch(pl, st);
+        if (!r) r = note(cudaEventRecord(e1, st));
+        if (!r) r = note(cudaEventSynchronize(e1));
+        float fms = 0.f;
+        if (!r) r = note(cudaEventElapsedTime(&fms, e0, e1));
+        bdc_plan_destroy(pl);
+        t = fms / reps;
+        return r;
+    };
+    TuneResult best{base.leaf, base.mixed_min, 1e300};
+    // leaf first (products as given), then the split-BF16 threshold
+    for (int L : leaves) {
+        if (L > std::max(nmax, 8)) continue;
+        bdc_opts c = base;
+        c.leaf = L;
+        double t = 0.0;
+        if ((rc = time_one(c, t))) break;
+        if (t < best.ms) best = TuneResult{L, base.mixed_min, t};
+    }
+    if (!rc && base.prec != BDC_FP64) {
+        for (int mm : mins) {
+            bdc_opts c = base;
+            c.leaf = best.leaf;
+            c.mixed_min = mm;
+            double t = 0.0;
+            if ((rc = time_one(c, t))) break;
+            if (t < best.ms) best = TuneResult{best.leaf, mm, t};
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    release();
+    if (rc) return rc;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[key] = best;
+    }
+    o->leaf = best.leaf;
+    o->mixed_min = best.mixed_min;
+    if (ms_out) *ms_out = best.ms;
+    return 0;
 }
 
 int bdc_secular_solve(int N, const double *d, const double *z, int *org, double *tau, double *omega,

@@ -691,15 +691,16 @@ cudaError_t run_mixed(const GemmProb *probs, int nprobs, const std::vector<MixPr
         tiles = hm[p].tile0 + ((hm[p].Mmax + TM - 1) / TM) * hm[p].tilesN;
     }
     if (hm.size() && hm[0].tilesN != (hm[0].Nmax + TNX - 1) / TNX) return cudaErrorInvalidValue;
-    // small tables through a pinned ring (graph-capturable copies)
+    // small tables through pinned host memory: the capturing plan's own
+    // blocks, else a shared ring (copies stay valid until the ring wraps)
     static std::mutex mu;
     static char *ring = nullptr;
     static size_t ring_off = 0;
     constexpr size_t kRing = 64ull << 20;
     const size_t need = sizeof(MixProb) * nprobs + 2 * sizeof(int) * nprobs + 3 * 256;
     if (need > kRing) return cudaErrorInvalidValue;
-    char *h;
-    {
+    char *h = (char *)plan_pinned_alloc(need);
+    if (!h) {
         std::lock_guard<std::mutex> lk(mu);
         if (!ring && cudaMallocHost((void **)&ring, kRing) != cudaSuccess) return cudaErrorMemoryAllocation;
         if (ring_off + need > kRing) {

@@ -151,6 +151,10 @@ cudaError_t launch_final(const MatDesc *mats, int nmat, int nmax, cudaStream_t s
 cudaError_t launch_secular_single(int N, const double *d, const double *z, int *org, double *tau,
                                   double *omega, int max_iter, int *info, int seed_mode, const float *mlp,
                                   int *iters, cudaStream_t st);
+// pinned host memory owned by the plan being captured (nullptr when no plan
+// capture is active on this thread; callers then use their own buffers)
+void *plan_pinned_alloc(size_t bytes);
+
 // MLP training (bdc_mlp.cu)
 size_t mlp_grad_workspace(int count);
 cudaError_t launch_mlp_init(float *P, const float *feat, int count, unsigned long long seed,

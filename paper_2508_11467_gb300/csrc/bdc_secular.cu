@@ -18,7 +18,8 @@
 //            reduction; sign from z_i.
 // k_vectors  one CTA per column i: v_i, u_i of Eq. (M-svd-vec), normalised,
 //            written in the K order of the merge product (coalesced down the
-//            column).
+//            column); k_vectors_warp does the same with a warp per column
+//            for merges of order <= 1024.
 //
 // All arithmetic is FP64.
 #include "bdc_internal.cuh"
@@ -477,6 +478,50 @@ __global__ void __launch_bounds__(256) k_vectors(const NodeDesc *__restrict__ no
                 ns.Ktot, md.UM + wb + (size_t)i * ns.Ktot, md.VM + wb + (size_t)i * ns.Ktot, sh);
 }
 
+// the same with one warp per column (8 columns per CTA), for heights whose
+// merges are small: a whole CTA per short column is mostly idle threads
+__global__ void __launch_bounds__(256) k_vectors_warp(const NodeDesc *__restrict__ nodes,
+                                                      const MatDesc *__restrict__ mats,
+                                                      const NodeState *__restrict__ state, int mmax,
+                                                      int nnodes) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int node = warp / mmax, i = warp % mmax;
+    if (node >= nnodes) return;
+    const NodeDesc nd = nodes[node];
+    const NodeState ns = state[nd.id];
+    if (i >= ns.N) return;
+    const MatDesc md = mats[nd.mat];
+    const int r0 = nd.r0, N = ns.N, Ktot = ns.Ktot;
+    const long long wb = (long long)r0 * md.wstride;
+    const double *d = md.dM + r0, *zt = md.zt + r0;
+    const int *invK = md.invK + nd.kbase;
+    const double dor = d[md.org[r0 + i]], tau = md.tau[r0 + i];
+    double sv = 0.0, su = 0.0;
+    for (int j = lane; j < N; j += 32) {
+        const double dj = d[j];
+        const double v = zt[j] / (((dj - dor) - tau) * (dj + dor + tau));
+        const double u = (j == 0) ? -1.0 : dj * v;
+        sv = fma(v, v, sv);
+        su = fma(u, u, su);
+    }
+    sv = warp_sum(sv);
+    su = warp_sum(su);
+    const double iv = 1.0 / sqrt(sv), iu = 1.0 / sqrt(su);
+    double *UMcol = md.UM + wb + (size_t)i * Ktot, *VMcol = md.VM + wb + (size_t)i * Ktot;
+    for (int p = lane; p < Ktot; p += 32) {
+        const int j = invK[p];
+        double uo = 0.0, vo = 0.0;
+        if (j >= 0) {
+            const double dj = d[j];
+            const double v = zt[j] / (((dj - dor) - tau) * (dj + dor + tau));
+            vo = v * iv;
+            uo = ((j == 0) ? -1.0 : dj * v) * iu;
+        }
+        UMcol[p] = uo;
+        VMcol[p] = vo;
+    }
+}
+
 __global__ void __launch_bounds__(256) k_mvectors_single(int N, const double *d, const double *zt,
                                                          const int *org, const double *tau, double *UM,
                                                          int ldum, double *VM, int ldvm) {
@@ -511,7 +556,12 @@ cudaError_t launch_secular(const NodeDesc *nodes, int nnodes, const MatDesc *mat
 cudaError_t launch_vectors(const NodeDesc *nodes, int nnodes, const MatDesc *mats, const NodeState *state,
                            int mmax, cudaStream_t st) {
     if (nnodes <= 0) return cudaSuccess;
-    k_vectors<<<(unsigned)nnodes * mmax, 256, 0, st>>>(nodes, mats, state, mmax);
+    if (mmax <= 1024) {
+        const long long warps = (long long)nnodes * mmax;
+        k_vectors_warp<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(nodes, mats, state, mmax, nnodes);
+    } else {
+        k_vectors<<<(unsigned)nnodes * mmax, 256, 0, st>>>(nodes, mats, state, mmax);
+    }
     return cudaGetLastError();
 }
 

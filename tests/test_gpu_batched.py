@@ -1,0 +1,155 @@
+"""Batched SVD (bdc_svd_batched, plans replayed as CUDA graphs, autotuner)
+against the FP64 oracle.
+
+Every checked matrix meets the FP64 bar of the single-matrix path
+(relative singular-value error, residual and orthogonality <= 1e-13 n).
+The 2048-matrix batch has orders floor(exp(U(ln 32, ln 1024))) (seed 3),
+d, e ~ U(0.5, 1.5); a spread of its matrices is checked one by one.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import check
+from paper_2508_11467_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bdc():
+    from paper_2508_11467_gb300 import bdc as b
+    from paper_2508_11467_gb300 import build
+    build.build()
+    b.lib()
+    return b
+
+
+def _flat(mats):
+    ns = np.array([len(d) for d, _ in mats], dtype=np.int32)
+    off = np.concatenate([[0], np.cumsum(ns)])
+    D = np.zeros(int(off[-1]))
+    E = np.zeros(int(off[-1]))
+    for b, (d, e) in enumerate(mats):
+        D[off[b]:off[b] + len(d)] = d
+        E[off[b]:off[b] + len(e)] = e
+    return ns, torch.from_numpy(D).cuda(), torch.from_numpy(E).cuda()
+
+
+def _orth(X):
+    G = X.t() @ X
+    G.diagonal().sub_(1.0)
+    return float(torch.linalg.norm(G))
+
+
+def _check(d, e, S, U, VT, tol_scale=1e-13, res_tol=None):
+    n = len(d)
+    s = S.cpu().numpy()
+    tol = tol_scale * n
+    assert np.all(np.diff(s) <= 0) and np.all(s >= 0)
+    assert check.sigma_rel_err(s, oracle.sigma_only(d, e)) <= tol
+    res = oracle.residual(d, e, s, U.cpu().numpy(), VT.cpu().numpy())
+    assert res <= (res_tol if res_tol is not None else tol), res
+    assert _orth(U) <= tol and _orth(VT.t()) <= tol
+
+
+def test_batched_list_api_matches_oracle(bdc):
+    mats = inputs.batch(64, seed=3, lo=32, hi=300)
+    ds = [torch.from_numpy(d).cuda() for d, _ in mats]
+    es = [torch.from_numpy(e).cuda() for _, e in mats]
+    Ss, Us, VTs, info = bdc.svd_batched(ds, es)
+    torch.cuda.synchronize()
+    assert int(info.abs().max()) == 0
+    for b, (d, e) in enumerate(mats):
+        _check(d, e, Ss[b], Us[b], VTs[b])
+
+
+def test_batched_matches_single_matrix_bitwise(bdc):
+    mats = inputs.batch(20, seed=7, lo=32, hi=400)
+    ds = [torch.from_numpy(d).cuda() for d, _ in mats]
+    es = [torch.from_numpy(e).cuda() for _, e in mats]
+    Ss, Us, VTs, info = bdc.svd_batched(ds, es)
+    for b in (0, 7, 19):
+        S1, U1, VT1, _ = bdc.svd(ds[b], es[b])
+        assert torch.equal(Ss[b], S1) and torch.equal(Us[b], U1) and torch.equal(VTs[b], VT1)
+
+
+def test_plan_graph_equals_direct_call_and_replays(bdc):
+    mats = inputs.batch(48, seed=5, lo=32, hi=512)
+    ns, D, E = _flat(mats)
+    plan = bdc.BatchPlan(D, E, ns)
+    plan.launch()
+    torch.cuda.synchronize()
+    assert int(plan.info.abs().max()) == 0
+    ds = [torch.from_numpy(d).cuda() for d, _ in mats]
+    es = [torch.from_numpy(e).cuda() for _, e in mats]
+    Ss, Us, VTs, _ = bdc.svd_batched(ds, es)
+    for b in range(len(mats)):
+        S, U, VT = plan.result(b)
+        assert torch.equal(S, Ss[b]) and torch.equal(U, Us[b]) and torch.equal(VT, VTs[b])
+    # the graph reads the inputs at launch time: new values, same plan
+    mats2 = [inputs.uniform(int(n), 1000 + b) for b, n in enumerate(ns)]
+    _, D2, E2 = _flat(mats2)
+    plan.d.copy_(D2)
+    plan.e.copy_(E2)
+    plan.launch()
+    plan.launch()
+    torch.cuda.synchronize()
+    for b in (0, 11, 47):
+        S, U, VT = plan.result(b)
+        _check(*mats2[b], S, U, VT)
+    plan.close()
+
+
+def test_config4_2048_matrices(bdc):
+    """2048 bidiagonals, n log-uniform in [32, 1024], one graph launch."""
+    mats = inputs.batch(2048, seed=3)
+    ns, D, E = _flat(mats)
+    assert ns.min() >= 32 and ns.max() <= 1024
+    plan = bdc.BatchPlan(D, E, ns)
+    plan.launch()
+    torch.cuda.synchronize()
+    assert int(plan.info.abs().max()) == 0
+    order = np.argsort(ns)
+    pick = sorted(set(order[np.linspace(0, len(ns) - 1, 16).astype(int)].tolist() + [int(order[-1])]))
+    for b in pick:
+        S, U, VT = plan.result(b)
+        _check(*mats[b], S, U, VT)
+    plan.close()
+
+
+def test_batched_mixed_products(bdc):
+    mats = inputs.batch(32, seed=9, lo=300, hi=1024)
+    ns, D, E = _flat(mats)
+    plan = bdc.BatchPlan(D, E, ns, prec="exact")
+    plan.launch()
+    torch.cuda.synchronize()
+    assert int(plan.info.abs().max()) == 0
+    for b in (0, 13, 31):
+        S, U, VT = plan.result(b)
+        _check(*mats[b], S, U, VT, res_tol=1e-12)
+    plan.close()
+
+
+def test_autotune_picks_a_candidate_and_caches(bdc):
+    import time
+    ns = inputs.batch_sizes(256, seed=3)
+    leaf, mm, ms = bdc.autotune(ns, "fp64", reps=2)
+    assert leaf in (8, 12, 16, 24, 32) and ms > 0
+    t0 = time.perf_counter()
+    leaf2, mm2, ms2 = bdc.autotune(ns, "fp64", reps=2)
+    assert (leaf2, mm2, ms2) == (leaf, mm, ms)
+    assert time.perf_counter() - t0 < 0.5
+    leaf3, mm3, _ = bdc.autotune(ns, "exact", reps=1)
+    assert leaf3 in (8, 12, 16, 24, 32) and mm3 in (128, 256, 512, 1024, 4096)
+    # the chosen configuration solves the batch correctly
+    mats = inputs.batch(256, seed=3)
+    _, D, E = _flat(mats)
+    plan = bdc.BatchPlan(D, E, ns, leaf=leaf)
+    plan.launch()
+    torch.cuda.synchronize()
+    assert int(plan.info.abs().max()) == 0
+    S, U, VT = plan.result(5)
+    _check(*mats[5], S, U, VT)
+    plan.close()
