@@ -131,6 +131,26 @@ int bdc_plan_create(bdc_plan *plan, int batch, const int *h_n, const double *con
 int bdc_plan_launch(bdc_plan plan, bdc_stream_t stream);
 void bdc_plan_destroy(bdc_plan plan);
 
+/* ---------------- single precision (batches) ----------------------------
+ * The same batched solve with FP32 data and FP32 arithmetic in every step
+ * (leaves, deflation with tol = 8 eps_32 ||M||, secular roots, z~, vectors,
+ * and the merge products on CUDA cores).  Arguments as for
+ * bdc_svd_batched / bdc_plan_create with float data pointers; options must
+ * keep prec = 0 and seed = BDC_SEED_PLAIN (the split-BF16 products and the
+ * root starts are FP64-path features).  Plans from bdc_plan_create_f32 are
+ * launched and destroyed with bdc_plan_launch / bdc_plan_destroy.
+ * Accuracy: relative singular-value error, residual and orthogonality
+ * about n * eps_32. */
+size_t bdc_svd_batched_workspace_f32(int batch, const int *h_n, const bdc_opts *o);
+int bdc_svd_batched_f32(int batch, const int *h_n, const float *const *d, const float *const *e, float *const *U,
+                        float *const *S, float *const *VT, const int *h_ldu, const int *h_ldvt, const bdc_opts *o,
+                        void *work, size_t lwork, int *d_info, bdc_stream_t stream);
+int bdc_plan_create_f32(bdc_plan *plan, int batch, const int *h_n, const float *const *d, const float *const *e,
+                        float *const *U, float *const *S, float *const *VT, const int *h_ldu, const int *h_ldvt,
+                        const bdc_opts *o, void *work, size_t lwork, int *d_info);
+/* bdc_autotune for the FP32 path (leaf size only). */
+int bdc_autotune_f32(int batch, const int *h_n, bdc_opts *o, int reps, double *ms, bdc_stream_t stream);
+
 /* Autotuner for batches: times candidate plans on synthetic bidiagonals of
  * the given orders (d, e ~ U(0.5, 1.5), counter-based generator) and writes
  * the fastest leaf size into o->leaf, and for split-BF16 products the

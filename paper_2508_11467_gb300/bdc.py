@@ -64,6 +64,10 @@ _SIGS = {
     "bdc_plan_launch": (_I, [_VP, _VP]),
     "bdc_plan_destroy": (None, [_VP]),
     "bdc_autotune": (_I, [_I, _VP, _VP, _I, _VP, _VP]),
+    "bdc_svd_batched_workspace_f32": (_SZ, [_I, _VP, _VP]),
+    "bdc_autotune_f32": (_I, [_I, _VP, _VP, _I, _VP, _VP]),
+    "bdc_svd_batched_f32": (_I, [_I, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP, _VP]),
+    "bdc_plan_create_f32": (_I, [_VP, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "bdc_status_string": (ctypes.c_char_p, [_I]),
     "bdc_profile_begin": (_I, [_I]),
     "bdc_profile_end": (_I, [_VP, _VP, _VP]),
@@ -470,31 +474,38 @@ class BatchPlan:
     whole solve on the stream."""
 
     def __init__(self, d_flat, e_flat, ns, *, prec="fp64", leaf=16, max_iter=64, slices=0, seed="plain",
-                 mlp=None, mixed_min=0):
+                 mlp=None, mixed_min=0, dtype=torch.float64):
         import numpy as np
         self.ns = np.asarray(ns, dtype=np.int32)
         B = len(self.ns)
         dev = d_flat.device
-        self.d, self.e = _dev(d_flat), _dev(e_flat)
+        self.dtype = dtype
+        f32 = dtype == torch.float32
+        esz = 4 if f32 else 8
+        self.d, self.e = _dev(d_flat, dtype), _dev(e_flat, dtype)
         self.off = np.concatenate([[0], np.cumsum(self.ns, dtype=np.int64)])
         self.off2 = np.concatenate([[0], np.cumsum(self.ns.astype(np.int64) ** 2)])
-        self.S = torch.empty(int(self.off[-1]), dtype=torch.float64, device=dev)
-        self.U = torch.empty(int(self.off2[-1]), dtype=torch.float64, device=dev)
-        self.VT = torch.empty(int(self.off2[-1]), dtype=torch.float64, device=dev)
+        self.S = torch.empty(int(self.off[-1]), dtype=dtype, device=dev)
+        self.U = torch.empty(int(self.off2[-1]), dtype=dtype, device=dev)
+        self.VT = torch.empty(int(self.off2[-1]), dtype=dtype, device=dev)
         self.info = torch.zeros(B, dtype=torch.int32, device=dev)
         self.opts = make_opts(prec, leaf, max_iter, slices, seed, mlp, mixed_min)
         self._mlp = mlp
-        lw = int(lib().bdc_svd_batched_workspace(B, self.ns.ctypes.data_as(ctypes.c_void_p), ctypes.byref(self.opts)))
+        wsfn = lib().bdc_svd_batched_workspace_f32 if f32 else lib().bdc_svd_batched_workspace
+        lw = int(wsfn(B, self.ns.ctypes.data_as(ctypes.c_void_p), ctypes.byref(self.opts)))
+        if lw == 0:
+            raise BDCError("bdc_svd_batched_workspace", -2)
         self.work = torch.empty(lw + 256, dtype=torch.uint8, device=dev)
-        ptrs = lambda base, offs, esz: (ctypes.c_void_p * B)(*[base.data_ptr() + int(o) * esz for o in offs[:B]])
-        self._pd = ptrs(self.d, self.off, 8)
-        self._pe = ptrs(self.e, self.off, 8)
-        self._pu = ptrs(self.U, self.off2, 8)
-        self._ps = ptrs(self.S, self.off, 8)
-        self._pv = ptrs(self.VT, self.off2, 8)
+        ptrs = lambda base, offs: (ctypes.c_void_p * B)(*[base.data_ptr() + int(o) * esz for o in offs[:B]])
+        self._pd = ptrs(self.d, self.off)
+        self._pe = ptrs(self.e, self.off)
+        self._pu = ptrs(self.U, self.off2)
+        self._ps = ptrs(self.S, self.off)
+        self._pv = ptrs(self.VT, self.off2)
         self._ld = self.ns.copy()
         self._plan = ctypes.c_void_p()
-        _check("bdc_plan_create", lib().bdc_plan_create(
+        create = lib().bdc_plan_create_f32 if f32 else lib().bdc_plan_create
+        _check("bdc_plan_create", create(
             ctypes.byref(self._plan), B, self.ns.ctypes.data_as(ctypes.c_void_p), self._pd, self._pe, self._pu,
             self._ps, self._pv, self._ld.ctypes.data_as(ctypes.c_void_p), self._ld.ctypes.data_as(ctypes.c_void_p),
             ctypes.byref(self.opts), _ptr(self.work), self.work.numel(), _ptr(self.info)))
@@ -522,12 +533,14 @@ class BatchPlan:
             pass
 
 
-def autotune(ns, prec="fp64", seed="plain", slices=0, reps=3, stream=None):
-    """bdc_autotune: (leaf, mixed_min, ms per batch) for a batch of orders ns."""
+def autotune(ns, prec="fp64", seed="plain", slices=0, reps=3, stream=None, dtype=torch.float64):
+    """bdc_autotune (bdc_autotune_f32 for dtype=torch.float32): (leaf,
+    mixed_min, ms per batch) for a batch of orders ns."""
     import numpy as np
     ns = np.asarray(ns, dtype=np.int32)
     o = make_opts(prec, 16, 64, slices, seed)
     ms = ctypes.c_double(0.0)
-    _check("bdc_autotune", lib().bdc_autotune(len(ns), ns.ctypes.data_as(ctypes.c_void_p), ctypes.byref(o),
-                                               int(reps), ctypes.byref(ms), _stream(stream)))
+    fn = lib().bdc_autotune_f32 if dtype == torch.float32 else lib().bdc_autotune
+    _check("bdc_autotune", fn(len(ns), ns.ctypes.data_as(ctypes.c_void_p), ctypes.byref(o),
+                              int(reps), ctypes.byref(ms), _stream(stream)))
     return int(o.leaf), int(o.mixed_min), float(ms.value)

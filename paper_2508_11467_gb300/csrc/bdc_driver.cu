@@ -20,13 +20,15 @@
 
 #include "bdc_internal.cuh"
 
-namespace bdc {
+namespace BDC_NS {
 
+#ifndef BDC_FP32
 // mixed-precision product path (bdc_gemm_mixed.cu): products packed one after
 // another in the sliced operand arrays, rows bounded by Mmax[p], columns by Nmax[p]
 cudaError_t launch_gemm_mixed(const GemmProb *probs, int nprobs, const int *Mmax, const int *Nmax, int kmax,
                               int prec, int slices, void *scratch, size_t scratch_bytes, cudaStream_t st);
 size_t gemm_mixed_scratch(long long rows_total, long long cols_total, int kmax, int prec, int slices);
+#endif
 
 namespace {
 
@@ -91,13 +93,13 @@ struct Plan {
 size_t per_matrix_bytes(int n) {
     const size_t N = (size_t)n;
     size_t b = 0;
-    b += align256(sizeof(double) * 2 * N);            // dsc, esc
-    b += align256(sizeof(double) * 4 * N * N);        // U, V (two copies each)
-    b += align256(sizeof(double) * 20 * N + 64);      // D ds zs rc rs dM zM zt tau omega dval scale pz(6n) ystart yq
+    b += align256(sizeof(real_t) * 2 * N);            // dsc, esc
+    b += align256(sizeof(real_t) * 4 * N * N);        // U, V (two copies each)
+    b += align256(sizeof(real_t) * 20 * N + 64);      // D ds zs rc rs dM zM zt tau omega dval scale pz(6n) ystart yq
     b += align256(sizeof(float) * 11 * N);            // fs (root features)
     b += align256(sizeof(int) * (13 * N + 128));      // Q src role org kposM dsrc dest slist sidx invK(4n) info
     const size_t big = (N + 1) * (N + 16) + 64;
-    b += 4 * align256(sizeof(double) * big);          // Wt Qt UM VM
+    b += 4 * align256(sizeof(real_t) * big);          // Wt Qt UM VM
     return b;
 }
 
@@ -163,6 +165,7 @@ Plan make_plan(int nmat, const int *ns, const bdc_opts &o) {
         p.off_mat_data.push_back(off);
         off += per_matrix_bytes(std::max(ns[mi], 1));
     }
+#ifndef BDC_FP32
     if (o.prec != BDC_FP64) {
         size_t mb = 0;
         for (size_t h = 0; h < p.heights.size(); ++h) {
@@ -175,6 +178,7 @@ Plan make_plan(int nmat, const int *ns, const bdc_opts &o) {
         p.mixed_bytes = mb;
         off += align256(mb);
     }
+#endif
     p.total = off + 256;
     return p;
 }
@@ -187,11 +191,11 @@ MatDesc carve(char *base, size_t off, int n) {
     auto take = [&](size_t bytes) { char *r = p; p += align256(bytes); return r; };
     md.n = n;
     md.wstride = (long long)N + 16;
-    double *de = (double *)take(sizeof(double) * 2 * N);
+    real_t *de = (real_t *)take(sizeof(real_t) * 2 * N);
     md.dsc = de; md.esc = de + N;
-    double *uv = (double *)take(sizeof(double) * 4 * N * N);
+    real_t *uv = (real_t *)take(sizeof(real_t) * 4 * N * N);
     md.U[0] = uv; md.V[0] = uv + N * N; md.U[1] = uv + 2 * N * N; md.V[1] = uv + 3 * N * N;
-    double *dd = (double *)take(sizeof(double) * 20 * N + 64);
+    real_t *dd = (real_t *)take(sizeof(real_t) * 20 * N + 64);
     md.D = dd; md.ds = dd + N; md.zs = dd + 2 * N; md.rc = dd + 3 * N; md.rs = dd + 4 * N;
     md.dM = dd + 5 * N; md.zM = dd + 6 * N; md.zt = dd + 7 * N; md.tau = dd + 8 * N;
     md.omega = dd + 9 * N; md.dval = dd + 10 * N; md.scale = dd + 11 * N; md.pz = dd + 12 * N;
@@ -203,29 +207,29 @@ MatDesc carve(char *base, size_t off, int n) {
     md.invK = ii + 9 * N;                 // K-indexed: r0 + 8 * (index within height) + K
     md.info = ii + 13 * N + 64;
     const size_t big = (N + 1) * (N + 16) + 64;
-    md.Wt = (double *)take(sizeof(double) * big);
-    md.Qt = (double *)take(sizeof(double) * big);
-    md.UM = (double *)take(sizeof(double) * big);
-    md.VM = (double *)take(sizeof(double) * big);
+    md.Wt = (real_t *)take(sizeof(real_t) * big);
+    md.Qt = (real_t *)take(sizeof(real_t) * big);
+    md.UM = (real_t *)take(sizeof(real_t) * big);
+    md.VM = (real_t *)take(sizeof(real_t) * big);
     return md;
 }
 
 // ------------------------------------------------------------------ kernels
 __global__ void k_scale(const MatDesc *__restrict__ mats) {
-    __shared__ double sh[32];
+    __shared__ real_t sh[32];
     __shared__ int bad;
     const MatDesc md = mats[blockIdx.x];
     const int n = md.n;
     if (threadIdx.x == 0) bad = 0;
     __syncthreads();
-    double mx = 0.0;
+    real_t mx = R(0);
     int nonfinite = 0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const double v = md.d_in[i];
+        const real_t v = md.d_in[i];
         nonfinite |= !isfinite(v);
         mx = fmax(mx, fabs(v));
         if (i + 1 < n) {
-            const double w = md.e_in[i];
+            const real_t w = md.e_in[i];
             nonfinite |= !isfinite(w);
             mx = fmax(mx, fabs(w));
         }
@@ -234,16 +238,16 @@ __global__ void k_scale(const MatDesc *__restrict__ mats) {
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
     if (nonfinite) atomicOr(&bad, 1);
     __syncthreads();
-    double s = 0.0;
+    real_t s = R(0);
     for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s = fmax(s, sh[k]);
     const bool nf = bad != 0;
-    const double se = (nf || s == 0.0) ? 1.0 : s;
+    const real_t se = (nf || s == R(0)) ? R(1) : s;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        md.dsc[i] = nf ? 0.0 : md.d_in[i] / se;
-        md.esc[i] = (nf || i + 1 >= n) ? 0.0 : md.e_in[i] / se;
+        md.dsc[i] = nf ? R(0) : md.d_in[i] / se;
+        md.esc[i] = (nf || i + 1 >= n) ? R(0) : md.e_in[i] / se;
     }
     if (threadIdx.x == 0) {
-        md.scale[0] = nf ? 0.0 : s;
+        md.scale[0] = nf ? R(0) : s;
         md.info[0] = nf ? BDC_ERR_NONFINITE : 0;
     }
 }
@@ -255,14 +259,14 @@ __global__ void k_info(const MatDesc *__restrict__ mats, int nmat, int *__restri
 }
 
 __global__ void k_final(const MatDesc *__restrict__ mats, int tiles_per_side) {
-    __shared__ double tile[32][33];
+    __shared__ real_t tile[32][33];
     const MatDesc md = mats[blockIdx.z];
     const int n = md.n;
     const int tc = blockIdx.x % tiles_per_side, tj = blockIdx.x / tiles_per_side;
     const int c0 = tc * 32, j0 = tj * 32;
     if (c0 >= n || j0 >= n) return;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
-    const double s = md.scale[0];
+    const real_t s = md.scale[0];
     // U: output column c = source column Q[n-1-c], rows j0..j0+31
     for (int cc = ty; cc < 32; cc += 8) {
         const int c = c0 + cc;
@@ -287,23 +291,17 @@ __global__ void k_final(const MatDesc *__restrict__ mats, int tiles_per_side) {
 // sequence into a CUDA graph, every host->device copy of descriptors and
 // tables reads from blocks that live as long as the plan (the graph replays
 // those copies), instead of the shared cache and ring of one-shot calls.
-struct PinnedArena {
-    std::vector<void *> blocks;
-    void *alloc(size_t bytes) {
-        void *q = nullptr;
-        if (cudaMallocHost(&q, bytes) != cudaSuccess) return nullptr;
-        blocks.push_back(q);
-        return q;
-    }
-    ~PinnedArena() {
-        for (void *q : blocks) cudaFreeHost(q);
-    }
-};
-thread_local PinnedArena *g_arena = nullptr;
+thread_local std::vector<void *> *g_arena = nullptr;
 
 }  // namespace
 
-void *plan_pinned_alloc(size_t bytes) { return g_arena ? g_arena->alloc(bytes) : nullptr; }
+void *plan_pinned_alloc(size_t bytes) {
+    if (!g_arena) return nullptr;
+    void *q = nullptr;
+    if (cudaMallocHost(&q, bytes) != cudaSuccess) return nullptr;
+    g_arena->push_back(q);
+    return q;
+}
 
 namespace {
 
@@ -376,7 +374,7 @@ cudaError_t upload(const Plan &p, char *work, const std::vector<MatDesc> &mats, 
     std::memcpy(key.data(), blob.data(), bytes);
     void *host = nullptr;
     if (g_arena) {
-        host = g_arena->alloc(bytes);
+        host = plan_pinned_alloc(bytes);
         if (!host) return cudaErrorMemoryAllocation;
         std::memcpy(host, blob.data(), bytes);
         return cudaMemcpyAsync(work, host, bytes, cudaMemcpyHostToDevice, st);
@@ -479,7 +477,9 @@ int run_plan(const Plan &p, const bdc_opts &o, char *work, std::vector<MatDesc> 
             StageScope sc(st, BDC_STAGE_GEMM, gl, 0.0);
             if (!mixed_here) {
                 e = launch_gemm64(dprobs, 4 * nn, mm + 1, mm, st);
-            } else {
+            }
+#ifndef BDC_FP32
+            else {
                 std::vector<int> Mx(4 * nn), Nx(4 * nn);
                 for (int k = 0; k < nn; ++k) {
                     const NodeDesc &nd = p.heights[h][k];
@@ -492,6 +492,7 @@ int run_plan(const Plan &p, const bdc_opts &o, char *work, std::vector<MatDesc> 
                 e = launch_gemm_mixed(dprobs, 4 * nn, Mx.data(), Nx.data(), mm + 9, o.prec,
                                       o.slices > 0 ? o.slices : 6, work + p.off_mixed, p.mixed_bytes, st);
             }
+#endif
             if (e != cudaSuccess) return note(e);
         }
         {
@@ -548,6 +549,9 @@ bdc_opts resolve(const bdc_opts *o, int nmax) {
 }
 
 int check_opts(const bdc_opts &o) {
+#ifdef BDC_FP32
+    if (o.prec != BDC_FP64 || o.seed != BDC_SEED_PLAIN) return 1;   // FP32: plain products and starts
+#endif
     if (o.prec < 0 || o.prec > 2) return 1;
     if (o.seed < 0 || o.seed > 2) return 1;
     if (o.seed == BDC_SEED_MLP && !o.mlp) return 1;
@@ -558,10 +562,11 @@ int check_opts(const bdc_opts &o) {
 }
 
 }  // namespace
-}  // namespace bdc
+}  // namespace BDC_NS
 
-using namespace bdc;
+using namespace BDC_NS;
 
+#ifndef BDC_FP32
 extern "C" {
 
 void bdc_opts_default(bdc_opts *o) {
@@ -657,13 +662,14 @@ size_t bdc_svd_batched_workspace(int batch, const int *h_n, const bdc_opts *o) {
 }
 
 }  // extern "C"
+#endif  // BDC_FP32
 
-namespace bdc {
+namespace BDC_NS {
 namespace {
 
 // synthetic autotuning input: x[k] = 0.5 + u_k, u_k in [0, 1) from splitmix64 of
 // (seed, k) (53 random bits)
-__global__ void k_fill_uniform(double *__restrict__ x, long long count, unsigned long long seed) {
+__global__ void k_fill_uniform(real_t *__restrict__ x, long long count, unsigned long long seed) {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= count) return;
     unsigned long long z = seed * 0x9E3779B97F4A7C15ull + (unsigned long long)k + 1;
@@ -671,7 +677,7 @@ __global__ void k_fill_uniform(double *__restrict__ x, long long count, unsigned
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     z ^= z >> 31;
-    x[k] = 0.5 + (double)(z >> 11) * 0x1.0p-53;
+    x[k] = (real_t)(0.5 + (double)(z >> 11) * 0x1.0p-53);
 }
 
 struct TuneResult {
@@ -682,8 +688,8 @@ std::mutex g_tune_mu;
 std::map<std::vector<int>, TuneResult> g_tune;
 
 // argument checks and plan set-up shared by bdc_svd_batched and bdc_plan_create
-int batched_setup(int batch, const int *h_n, const double *const *d, const double *const *e, double *const *U,
-                  double *const *S, double *const *VT, const int *h_ldu, const int *h_ldvt, const bdc_opts *o,
+int batched_setup(int batch, const int *h_n, const real_t *const *d, const real_t *const *e, real_t *const *U,
+                  real_t *const *S, real_t *const *VT, const int *h_ldu, const int *h_ldvt, const bdc_opts *o,
                   void *work, size_t lwork, int *d_info, Plan &p, bdc_opts &r, char *&w, std::vector<MatDesc> &mats) {
     if (batch < 0) return -1;
     if (!h_n) return -2;
@@ -718,54 +724,17 @@ int batched_setup(int batch, const int *h_n, const double *const *d, const doubl
     return 0;
 }
 
-}  // namespace
-}  // namespace bdc
-
-// a captured launch sequence: the whole solve of a fixed batch as one graph
-struct bdc_plan_s {
-    bdc::PinnedArena arena;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    int batch = 0;
-};
-
-extern "C" {
-
-int bdc_svd_batched(int batch, const int *h_n, const double *const *d, const double *const *e, double *const *U,
-                    double *const *S, double *const *VT, const int *h_ldu, const int *h_ldvt, const bdc_opts *o,
-                    void *work, size_t lwork, int *d_info, bdc_stream_t stream) {
-    if (batch == 0) return 0;
-    Plan p;
-    bdc_opts r;
-    char *w = nullptr;
-    std::vector<MatDesc> mats;
-    if (int a = batched_setup(batch, h_n, d, e, U, S, VT, h_ldu, h_ldvt, o, work, lwork, d_info, p, r, w, mats))
-        return a;
-    return run_plan(p, r, w, mats, d_info, (cudaStream_t)stream);
-}
-
-int bdc_plan_create(bdc_plan *plan, int batch, const int *h_n, const double *const *d, const double *const *e,
-                    double *const *U, double *const *S, double *const *VT, const int *h_ldu, const int *h_ldvt,
-                    const bdc_opts *o, void *work, size_t lwork, int *d_info) {
-    if (!plan) return -14;
-    *plan = nullptr;
-    if (batch <= 0) return -1;
-    Plan p;
-    bdc_opts r;
-    char *w = nullptr;
-    std::vector<MatDesc> mats;
-    if (int a = batched_setup(batch, h_n, d, e, U, S, VT, h_ldu, h_ldvt, o, work, lwork, d_info, p, r, w, mats))
-        return a;
-    bdc_plan_s *pl = new bdc_plan_s();
-    pl->batch = batch;
+// record the launch sequence of a plan into pl's CUDA graph (nothing runs):
+// descriptor and table copies read pl's own pinned blocks; stage profiling
+// is off while capturing
+int plan_capture(bdc_plan_s *pl, const Plan &p, const bdc_opts &r, char *w, std::vector<MatDesc> &mats,
+                 int *d_info) {
     cudaStream_t cs = nullptr;
     cudaError_t ce = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-    if (ce != cudaSuccess) { delete pl; return note(ce); }
-    // capture (nothing runs now): descriptor and table copies read the plan's
-    // own pinned blocks; stage profiling is off while capturing
+    if (ce != cudaSuccess) return note(ce);
     const bool prof = g_prof.on;
     g_prof.on = false;
-    g_arena = &pl->arena;
+    g_arena = &pl->pinned;
     int rc = note(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
     if (rc == 0) {
         rc = run_plan(p, r, w, mats, d_info, cs);
@@ -778,28 +747,41 @@ int bdc_plan_create(bdc_plan *plan, int batch, const int *h_n, const double *con
     g_prof.on = prof;
     cudaStreamDestroy(cs);
     if (rc == 0) rc = note(cudaGraphInstantiate(&pl->exec, pl->graph, 0));
+    return rc;
+}
+
+void plan_free(bdc_plan_s *pl) {
+    if (!pl) return;
+    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    if (pl->graph) cudaGraphDestroy(pl->graph);
+    for (void *q : pl->pinned) cudaFreeHost(q);
+    delete pl;
+}
+
+int plan_create_impl(bdc_plan *plan, int batch, const int *h_n, const real_t *const *d, const real_t *const *e,
+                     real_t *const *U, real_t *const *S, real_t *const *VT, const int *h_ldu, const int *h_ldvt,
+                     const bdc_opts *o, void *work, size_t lwork, int *d_info) {
+    if (!plan) return -14;
+    *plan = nullptr;
+    if (batch <= 0) return -1;
+    Plan p;
+    bdc_opts r;
+    char *w = nullptr;
+    std::vector<MatDesc> mats;
+    if (int a = batched_setup(batch, h_n, d, e, U, S, VT, h_ldu, h_ldvt, o, work, lwork, d_info, p, r, w, mats))
+        return a;
+    bdc_plan_s *pl = new bdc_plan_s();
+    pl->batch = batch;
+    const int rc = plan_capture(pl, p, r, w, mats, d_info);
     if (rc != 0) {
-        if (pl->graph) cudaGraphDestroy(pl->graph);
-        delete pl;
+        plan_free(pl);
         return rc;
     }
     *plan = pl;
     return 0;
 }
 
-int bdc_plan_launch(bdc_plan plan, bdc_stream_t stream) {
-    if (!plan || !plan->exec) return -1;
-    return note(cudaGraphLaunch(plan->exec, (cudaStream_t)stream));
-}
-
-void bdc_plan_destroy(bdc_plan plan) {
-    if (!plan) return;
-    if (plan->exec) cudaGraphExecDestroy(plan->exec);
-    if (plan->graph) cudaGraphDestroy(plan->graph);
-    delete plan;
-}
-
-int bdc_autotune(int batch, const int *h_n, bdc_opts *o, int reps, double *ms_out, bdc_stream_t stream) {
+int autotune_impl(int batch, const int *h_n, bdc_opts *o, int reps, double *ms_out, cudaStream_t st) {
     if (batch <= 0) return -1;
     if (!h_n) return -2;
     if (!o) return -3;
@@ -809,7 +791,6 @@ int bdc_autotune(int batch, const int *h_n, bdc_opts *o, int reps, double *ms_ou
     for (int b = 0; b < batch; ++b) nmax = std::max(nmax, h_n[b]);
     const bdc_opts base = resolve(o, nmax);
     if (check_opts(base)) return -3;
-    cudaStream_t st = (cudaStream_t)stream;
     // cache key: precision, start rule, slices, and the order histogram in powers of two
     std::vector<int> key = {base.prec, base.seed, base.slices};
     key.resize(3 + 12, 0);
@@ -843,7 +824,7 @@ int bdc_autotune(int batch, const int *h_n, bdc_opts *o, int reps, double *ms_ou
         c.leaf = L;
         lw = std::max(lw, make_plan(batch, h_n, c).total);
     }
-    double *dbuf = nullptr, *ebuf = nullptr, *Ub = nullptr, *VTb = nullptr, *Sb = nullptr;
+    real_t *dbuf = nullptr, *ebuf = nullptr, *Ub = nullptr, *VTb = nullptr, *Sb = nullptr;
     int *info = nullptr;
     void *work = nullptr;
     auto release = [&] {
@@ -851,19 +832,19 @@ int bdc_autotune(int batch, const int *h_n, bdc_opts *o, int reps, double *ms_ou
             if (q) cudaFreeAsync(q, st);
         cudaStreamSynchronize(st);
     };
-    int rc = note(cudaMallocAsync(&dbuf, sizeof(double) * sn, st));
-    if (!rc) rc = note(cudaMallocAsync(&ebuf, sizeof(double) * sn, st));
-    if (!rc) rc = note(cudaMallocAsync(&Ub, sizeof(double) * sn2, st));
-    if (!rc) rc = note(cudaMallocAsync(&VTb, sizeof(double) * sn2, st));
-    if (!rc) rc = note(cudaMallocAsync(&Sb, sizeof(double) * sn, st));
+    int rc = note(cudaMallocAsync(&dbuf, sizeof(real_t) * sn, st));
+    if (!rc) rc = note(cudaMallocAsync(&ebuf, sizeof(real_t) * sn, st));
+    if (!rc) rc = note(cudaMallocAsync(&Ub, sizeof(real_t) * sn2, st));
+    if (!rc) rc = note(cudaMallocAsync(&VTb, sizeof(real_t) * sn2, st));
+    if (!rc) rc = note(cudaMallocAsync(&Sb, sizeof(real_t) * sn, st));
     if (!rc) rc = note(cudaMallocAsync(&info, sizeof(int) * batch, st));
     if (!rc) rc = note(cudaMallocAsync(&work, lw + 256, st));
     if (rc) { release(); return rc; }
     k_fill_uniform<<<(unsigned)((sn + 255) / 256), 256, 0, st>>>(dbuf, sn, 0x5eedull);
     k_fill_uniform<<<(unsigned)((sn + 255) / 256), 256, 0, st>>>(ebuf, sn, 0x5eefull);
     if ((rc = note(cudaGetLastError()))) { release(); return rc; }
-    std::vector<const double *> pd(batch), pe(batch);
-    std::vector<double *> pu(batch), ps(batch), pv(batch);
+    std::vector<const real_t *> pd(batch), pe(batch);
+    std::vector<real_t *> pu(batch), ps(batch), pv(batch);
     for (int b = 0; b < batch; ++b) {
         pd[b] = dbuf + off[b]; pe[b] = ebuf + off[b]; ps[b] = Sb + off[b];
         pu[b] = Ub + off2[b]; pv[b] = VTb + off2[b];
@@ -873,17 +854,17 @@ int bdc_autotune(int batch, const int *h_n, bdc_opts *o, int reps, double *ms_ou
     cudaEventCreate(&e1);
     auto time_one = [&](const bdc_opts &c, double &t) -> int {
         bdc_plan pl = nullptr;
-        int r = bdc_plan_create(&pl, batch, h_n, pd.data(), pe.data(), pu.data(), ps.data(), pv.data(), h_n, h_n,
+        int r = plan_create_impl(&pl, batch, h_n, pd.data(), pe.data(), pu.data(), ps.data(), pv.data(), h_n, h_n,
                                 &c, work, lw + 256, info);
         if (r) return r;
-        r = bdc_plan_launch(pl, st);                          // warm-up
+        r = note(cudaGraphLaunch(pl->exec, st));               // warm-up
         if (!r) r = note(cudaEventRecord(e0, st));
-        for (int k = 0; k < reps && !r; ++k) r = bdc_plan_launch(pl, st);
+        for (int k = 0; k < reps && !r; ++k) r = note(cudaGraphLaunch(pl->exec, st));
         if (!r) r = note(cudaEventRecord(e1, st));
         if (!r) r = note(cudaEventSynchronize(e1));
         float fms = 0.f;
         if (!r) r = note(cudaEventElapsedTime(&fms, e0, e1));
-        bdc_plan_destroy(pl);
+        plan_free(pl);
         t = fms / reps;
         return r;
     };
@@ -897,7 +878,7 @@ int bdc_autotune(int batch, const int *h_n, bdc_opts *o, int reps, double *ms_ou
         if ((rc = time_one(c, t))) break;
         if (t < best.ms) best = TuneResult{L, base.mixed_min, t};
     }
-    if (!rc && base.prec != BDC_FP64) {
+    if (!rc && base.prec != BDC_FP64) {   // split-BF16 threshold (FP64 build only)
         for (int mm : mins) {
             bdc_opts c = base;
             c.leaf = best.leaf;
@@ -920,6 +901,43 @@ int bdc_autotune(int batch, const int *h_n, bdc_opts *o, int reps, double *ms_ou
     if (ms_out) *ms_out = best.ms;
     return 0;
 }
+
+}  // namespace
+}  // namespace BDC_NS
+
+#ifndef BDC_FP32
+extern "C" {
+
+int bdc_svd_batched(int batch, const int *h_n, const double *const *d, const double *const *e, double *const *U,
+                    double *const *S, double *const *VT, const int *h_ldu, const int *h_ldvt, const bdc_opts *o,
+                    void *work, size_t lwork, int *d_info, bdc_stream_t stream) {
+    if (batch == 0) return 0;
+    Plan p;
+    bdc_opts r;
+    char *w = nullptr;
+    std::vector<MatDesc> mats;
+    if (int a = batched_setup(batch, h_n, d, e, U, S, VT, h_ldu, h_ldvt, o, work, lwork, d_info, p, r, w, mats))
+        return a;
+    return run_plan(p, r, w, mats, d_info, (cudaStream_t)stream);
+}
+
+int bdc_plan_create(bdc_plan *plan, int batch, const int *h_n, const double *const *d, const double *const *e,
+                    double *const *U, double *const *S, double *const *VT, const int *h_ldu, const int *h_ldvt,
+                    const bdc_opts *o, void *work, size_t lwork, int *d_info) {
+    return plan_create_impl(plan, batch, h_n, d, e, U, S, VT, h_ldu, h_ldvt, o, work, lwork, d_info);
+}
+
+int bdc_autotune(int batch, const int *h_n, bdc_opts *o, int reps, double *ms, bdc_stream_t stream) {
+    return autotune_impl(batch, h_n, o, reps, ms, (cudaStream_t)stream);
+}
+
+int bdc_plan_launch(bdc_plan plan, bdc_stream_t stream) {
+    if (!plan || !plan->exec) return -1;
+    return note(cudaGraphLaunch(plan->exec, (cudaStream_t)stream));
+}
+
+void bdc_plan_destroy(bdc_plan plan) { plan_free(plan); }
+
 
 int bdc_secular_solve(int N, const double *d, const double *z, int *org, double *tau, double *omega,
                       int max_iter, int *d_info, bdc_stream_t stream) {
@@ -1148,3 +1166,43 @@ const char *bdc_status_string(int code) {
 }
 
 }  // extern "C"
+#endif  // BDC_FP32
+
+#ifdef BDC_FP32
+// single-precision batched entry points (include/bdc.h): the same plan and
+// launch sequence as bdc_svd_batched / bdc_plan_create, FP32 data path
+extern "C" {
+
+size_t bdc_svd_batched_workspace_f32(int batch, const int *h_n, const bdc_opts *o) {
+    if (batch <= 0 || !h_n) return 0;
+    for (int b = 0; b < batch; ++b) if (h_n[b] < 1 || h_n[b] > 2048) return 0;
+    int nmax = 0;
+    for (int b = 0; b < batch; ++b) nmax = std::max(nmax, h_n[b]);
+    return make_plan(batch, h_n, resolve(o, nmax)).total;
+}
+
+int bdc_svd_batched_f32(int batch, const int *h_n, const float *const *d, const float *const *e, float *const *U,
+                        float *const *S, float *const *VT, const int *h_ldu, const int *h_ldvt, const bdc_opts *o,
+                        void *work, size_t lwork, int *d_info, bdc_stream_t stream) {
+    if (batch == 0) return 0;
+    Plan p;
+    bdc_opts r;
+    char *w = nullptr;
+    std::vector<MatDesc> mats;
+    if (int a = batched_setup(batch, h_n, d, e, U, S, VT, h_ldu, h_ldvt, o, work, lwork, d_info, p, r, w, mats))
+        return a;
+    return run_plan(p, r, w, mats, d_info, (cudaStream_t)stream);
+}
+
+int bdc_plan_create_f32(bdc_plan *plan, int batch, const int *h_n, const float *const *d, const float *const *e,
+                        float *const *U, float *const *S, float *const *VT, const int *h_ldu, const int *h_ldvt,
+                        const bdc_opts *o, void *work, size_t lwork, int *d_info) {
+    return plan_create_impl(plan, batch, h_n, d, e, U, S, VT, h_ldu, h_ldvt, o, work, lwork, d_info);
+}
+
+int bdc_autotune_f32(int batch, const int *h_n, bdc_opts *o, int reps, double *ms, bdc_stream_t stream) {
+    return autotune_impl(batch, h_n, o, reps, ms, (cudaStream_t)stream);
+}
+
+}  // extern "C"
+#endif  // BDC_FP32

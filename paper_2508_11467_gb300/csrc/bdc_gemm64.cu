@@ -1,8 +1,12 @@
-// FP64 merge products of Eq. (bdc-Mv2Bv-u-vt): C = A * B, all column-major,
-// a batch of independent problems per launch (four per merge node: the top
-// and bottom blocks of W~ U_M and Q~ V_M).
+// Merge products of Eq. (bdc-Mv2Bv-u-vt) in the working precision: C = A * B,
+// all column-major, a batch of independent problems per launch (four per
+// merge node: the top and bottom blocks of W~ U_M and Q~ V_M).
 //
-// Tensor-core FP64 (DMMA, mma.sync.m8n8k4.f64).  CTA tile 64 x 64, K step 16,
+// FP32 build: CUDA-core FP32 FMA, CTA tile 64 x 64, K step 16, 256 threads
+// of 4 x 4 outputs, operands staged k-major in padded shared tiles (float4
+// reads), the next K step prefetched into registers.
+//
+// FP64 build: tensor-core FP64 (DMMA, mma.sync.m8n8k4.f64).  CTA tile 64 x 64, K step 16,
 // four warps of 32 x 32 (4 x 4 fragments of 8 x 8).  Shared tiles are padded
 // so that the fragment loads of a warp hit every bank exactly twice (the
 // minimum for 32 doubles).  The next K step is prefetched into registers while
@@ -10,10 +14,81 @@
 // the device after deflation) is smaller than the launch grid exit early.
 #include "bdc_internal.cuh"
 
-namespace bdc {
+namespace BDC_NS {
 
 namespace {
 
+#ifdef BDC_FP32
+constexpr int BM = 64, BN = 64, BK = 16, SP = 68;   // SP: padded row stride of both tiles (floats)
+
+__global__ void __launch_bounds__(256) k_gemm32(const GemmProb *__restrict__ probs, int tilesN) {
+    __shared__ __align__(16) float As[BK * SP];    // As[k][m]
+    __shared__ __align__(16) float Bs[BK * SP];    // Bs[k][n]
+    const GemmProb pr = probs[blockIdx.y];
+    const int m0 = (blockIdx.x / tilesN) * BM, n0 = (blockIdx.x % tilesN) * BN;
+    if (m0 >= pr.M || n0 >= pr.N) return;
+    const int tid = threadIdx.x;
+    const int tm = (tid >> 4) * 4, tn = (tid & 15) * 4;
+    const float *__restrict__ A = pr.A;
+    const float *__restrict__ B = pr.B;
+    const int M = pr.M, N = pr.N, K = pr.K, lda = pr.lda, ldb = pr.ldb;
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    float ra[4], rb[4];
+    auto load = [&](int k0) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int idx = tid + r * 256;       // 0..1023
+            const int am = idx & 63, ak = idx >> 6;
+            const int gm = m0 + am, gk = k0 + ak;
+            ra[r] = (gm < M && gk < K) ? A[(size_t)gk * lda + gm] : 0.f;
+            const int bk = idx & 15, bn = idx >> 4;
+            const int gn = n0 + bn, gk2 = k0 + bk;
+            rb[r] = (gn < N && gk2 < K) ? B[(size_t)gn * ldb + gk2] : 0.f;
+        }
+    };
+    auto store = [&]() {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int idx = tid + r * 256;
+            As[(idx >> 6) * SP + (idx & 63)] = ra[r];
+            Bs[(idx & 15) * SP + (idx >> 4)] = rb[r];
+        }
+    };
+    load(0);
+    for (int k0 = 0; k0 < K; k0 += BK) {
+        __syncthreads();
+        store();
+        __syncthreads();
+        if (k0 + BK < K) load(k0 + BK);
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            const float4 a = *reinterpret_cast<const float4 *>(As + kk * SP + tm);
+            const float4 b = *reinterpret_cast<const float4 *>(Bs + kk * SP + tn);
+            const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        }
+    }
+    float *__restrict__ C = pr.C;
+    const int ldc = pr.ldc;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int gn = n0 + tn + j;
+        if (gn >= N) continue;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int gm = m0 + tm + i;
+            if (gm < M) C[(size_t)gn * ldc + gm] = acc[i][j];
+        }
+    }
+}
+#else
 constexpr int BM = 64, BN = 64, BK = 16;
 constexpr int SA = BM + 8;   // As[k][m] row stride (doubles)
 constexpr int SB = BK + 4;   // Bs[n][k] row stride
@@ -100,6 +175,8 @@ __global__ void __launch_bounds__(128) k_gemm64(const GemmProb *__restrict__ pro
     }
 }
 
+#endif  // BDC_FP32
+
 }  // namespace
 
 cudaError_t launch_gemm64(const GemmProb *probs, int nprobs, int mmax_rows, int nmax_cols, cudaStream_t st) {
@@ -108,11 +185,15 @@ cudaError_t launch_gemm64(const GemmProb *probs, int nprobs, int mmax_rows, int 
     for (int p0 = 0; p0 < nprobs; p0 += 65535) {
         const int np = (nprobs - p0 < 65535) ? nprobs - p0 : 65535;
         dim3 grid((unsigned)tilesN * tilesM, np);
+#ifdef BDC_FP32
+        k_gemm32<<<grid, 256, 0, st>>>(probs + p0, tilesN);
+#else
         k_gemm64<<<grid, 128, 0, st>>>(probs + p0, tilesN);
+#endif
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
-}  // namespace bdc
+}  // namespace BDC_NS

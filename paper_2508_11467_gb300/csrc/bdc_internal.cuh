@@ -12,46 +12,78 @@
 //   merge scratch (indexed from r0 or from the node's kbase) and four big
 //   per-level matrices W~, Q~ (gathered/rotated vectors) and U_M, V_M (the
 //   vectors of M~), node block at r0 * wstride, wstride = n + 16.
+//
+// The data path is compiled twice from the same sources: in FP64 (namespace
+// bdc, real_t = double) and, with -DBDC_FP32, in FP32 (namespace bdc32,
+// real_t = float) for the single-precision batched entry points.  Literal
+// constants in arithmetic on real_t are written R(...) so that the FP32
+// build does no FP64 arithmetic.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/bdc.h"
 
-namespace bdc {
+// a captured plan (bdc_plan_create / bdc_plan_create_f32): its CUDA graph
+// and the pinned host blocks the graph's descriptor copies read from
+struct bdc_plan_s {
+    std::vector<void *> pinned;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int batch = 0;
+};
 
-constexpr double kEps = 2.220446049250313e-16;  // 2^-52
+#ifdef BDC_FP32
+#define BDC_NS bdc32
+#else
+#define BDC_NS bdc
+#endif
+#define R(x) (static_cast<real_t>(x))
+
+namespace BDC_NS {
+
+#ifdef BDC_FP32
+typedef float real_t;
+constexpr real_t kEps = 1.1920928955078125e-7f;  // 2^-23
+constexpr real_t kTolFloor = 0x1p-60f;           // keeps tol^2 a normal number
+#else
+typedef double real_t;
+constexpr real_t kEps = 2.220446049250313e-16;   // 2^-52
+constexpr real_t kTolFloor = 0x1p-400;
+#endif
 
 struct MatDesc {
     int n;
     int ldu, ldvt;           // user output leading dimensions
     long long wstride;       // n + 16
-    const double *d_in, *e_in;
-    double *Uo, *So, *VTo;   // user outputs
-    double *dsc, *esc;       // scaled copies (esc[n-1] = 0)
-    double *scale;           // [1] scale factor applied to d, e
-    double *U[2], *V[2];     // node blocks, copy = tree depth % 2
-    double *D;               // node values
+    const real_t *d_in, *e_in;
+    real_t *Uo, *So, *VTo;   // user outputs
+    real_t *dsc, *esc;       // scaled copies (esc[n-1] = 0)
+    real_t *scale;           // [1] scale factor applied to d, e
+    real_t *U[2], *V[2];     // node blocks, copy = tree depth % 2
+    real_t *D;               // node values
     int *Q;                  // node-local ascending order
     // merge scratch, per node from r0 (size n) unless noted
-    double *ds, *zs;         // sorted d, z
+    real_t *ds, *zs;         // sorted d, z
     int *src;                // sorted position -> encoded source column
-    double *rc, *rs;         // rotation linking a sorted position to its chain predecessor
+    real_t *rc, *rs;         // rotation linking a sorted position to its chain predecessor
     int *role;               // sorted position -> role (see bdc_merge.cu)
-    double *dM, *zM, *zt, *tau, *omega;   // survivors in M order
+    real_t *dM, *zM, *zt, *tau, *omega;   // survivors in M order
     int *org, *kposM;        // root origin, K position of each survivor
     int *invK;               // from kbase: K position -> M index (-1 = padding)
-    double *dval;            // deflated values, output order
+    real_t *dval;            // deflated values, output order
     int *dsrc;               // deflated output slot -> sorted position
     int *dest;               // sorted position -> K position (>= 0) or -(1 + deflated slot)
     int *slist;              // survivors of the small-z test, sorted positions (from r0)
     int *sidx;               // sorted position -> index in slist (-1 = small z)
-    double *Wt, *Qt, *UM, *VM;   // big per-level matrices (node base r0 * wstride)
+    real_t *Wt, *Qt, *UM, *VM;   // big per-level matrices (node base r0 * wstride)
     int *info;               // [1] status: >0 non-convergence count, <0 error code
-    double *pz;              // per-merge z^2 moment scans [6][n]: prefix sums of z^2, z^2 d^2,
+    real_t *pz;              // per-merge z^2 moment scans [6][n]: prefix sums of z^2, z^2 d^2,
                              // z^2 d^4 (rows 0-2), suffix sums (rows 3-5); root start features
-    double *ystart;          // per-root start fractions (seeded starts), indexed r0 + i
-    double *yq;              // per-root analytic estimates (harvest)
+    real_t *ystart;          // per-root start fractions (seeded starts), indexed r0 + i
+    real_t *yq;              // per-root analytic estimates (harvest)
     float *fs;               // per-root features [n][kMlpIn] (harvest)
     float *feat;             // optional MLP harvest: features [hcap][kMlpIn] (nullptr = off)
     float *targ;             // harvest targets [hcap]
@@ -79,15 +111,15 @@ struct NodeState {
     int Ktot;    // P1 + 1 + n2 + n3
     int ndef;    // m - N
     int nzero;   // deflated by rotation against d_0 = 0
-    double tol;
-    double cq, sq;   // rotation folding the two null-vector components (sqre)
+    real_t tol;
+    real_t cq, sq;   // rotation folding the two null-vector components (sqre)
     unsigned long long iters;   // secular iterations summed over the node's roots
-    double rho;                 // sum of z^2 over the survivors (after deflation)
+    real_t rho;                 // sum of z^2 over the survivors (after deflation)
 };
 
-// one FP64 product C = A * B (column-major), used by the merge GEMMs
+// one product C = A * B (column-major, real_t), used by the merge GEMMs
 struct GemmProb {
-    const double *A; const double *B; double *C;
+    const real_t *A; const real_t *B; real_t *C;
     int lda, ldb, ldc;
     int M, N, K;
 };
@@ -106,7 +138,11 @@ __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
-__device__ __forceinline__ double warp_max(double v) {
+__device__ __forceinline__ float warp_sum(float v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ real_t warp_max(real_t v) {
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
@@ -116,10 +152,10 @@ __device__ __forceinline__ int warp_isum(int v) {
 }
 
 // plane rotation with c f + s g = r, -s f + c g = 0
-__device__ __forceinline__ void make_rot(double f, double g, double &c, double &s, double &r) {
-    if (g == 0.0) { c = 1.0; s = 0.0; r = f; return; }
-    if (f == 0.0) { c = 0.0; s = 1.0; r = g; return; }
-    double h = hypot(f, g);
+__device__ __forceinline__ void make_rot(real_t f, real_t g, real_t &c, real_t &s, real_t &r) {
+    if (g == R(0)) { c = R(1); s = R(0); r = f; return; }
+    if (f == R(0)) { c = R(0); s = R(1); r = g; return; }
+    const real_t h = hypot(f, g);
     c = f / h; s = g / h; r = h;
 }
 
@@ -176,4 +212,4 @@ cudaError_t launch_mvectors_single(int N, const double *d, const double *zt, con
 cudaError_t launch_deflate_single(int m, const double *d, const double *z, double tol, int *keep,
                                   double *zout, double *dval, cudaStream_t st);
 
-}  // namespace bdc
+}  // namespace BDC_NS

@@ -13,7 +13,7 @@
 // the identity order in Q.
 #include "bdc_internal.cuh"
 
-namespace bdc {
+namespace BDC_NS {
 
 namespace {
 
@@ -24,10 +24,10 @@ struct LeafCtl {
 };
 
 // columns a, b of an SMEM column-major matrix, rows handled by this lane
-__device__ __forceinline__ void rot_rows(double *X, int ld, int rows, int lane, int a, int b,
-                                         double c, double s) {
+__device__ __forceinline__ void rot_rows(real_t *X, int ld, int rows, int lane, int a, int b,
+                                         real_t c, real_t s) {
     for (int r = lane; r < rows; r += 32) {
-        double u = X[a * ld + r], v = X[b * ld + r];
+        real_t u = X[a * ld + r], v = X[b * ld + r];
         X[a * ld + r] = c * u + s * v;
         X[b * ld + r] = -s * u + c * v;
     }
@@ -36,27 +36,27 @@ __device__ __forceinline__ void rot_rows(double *X, int ld, int rows, int lane, 
 __global__ void __launch_bounds__(32) k_leaf(const NodeDesc *__restrict__ leaves,
                                              const MatDesc *__restrict__ mats, int L,
                                              int max_sweeps) {
-    extern __shared__ double sm[];
+    extern __shared__ real_t sm[];
     const int lane = threadIdx.x;
     const NodeDesc nd = leaves[blockIdx.x];
     const MatDesc md = mats[nd.mat];
     const int m = nd.m, sq = nd.sqre, mc = m + sq;
     const int ldu = L, ldv = L + 1;
-    double *Us = sm;
-    double *Vs = Us + (size_t)L * L;
-    double *dd = Vs + (size_t)(L + 1) * (L + 1);
-    double *ee = dd + (L + 1);
-    double *c1 = ee + (L + 1);
-    double *s1 = c1 + (L + 1);
-    double *c2 = s1 + (L + 1);
-    double *s2 = c2 + (L + 1);
+    real_t *Us = sm;
+    real_t *Vs = Us + (size_t)L * L;
+    real_t *dd = Vs + (size_t)(L + 1) * (L + 1);
+    real_t *ee = dd + (L + 1);
+    real_t *c1 = ee + (L + 1);
+    real_t *s1 = c1 + (L + 1);
+    real_t *c2 = s1 + (L + 1);
+    real_t *s2 = c2 + (L + 1);
     int *perm = (int *)(s2 + (L + 1));
     volatile LeafCtl *ctl = (volatile LeafCtl *)(perm + L + 2);
 
     for (int j = 0; j < m; ++j)
-        for (int r = lane; r < m; r += 32) Us[j * ldu + r] = (r == j) ? 1.0 : 0.0;
+        for (int r = lane; r < m; r += 32) Us[j * ldu + r] = (r == j) ? R(1) : R(0);
     for (int j = 0; j < mc; ++j)
-        for (int r = lane; r < mc; r += 32) Vs[j * ldv + r] = (r == j) ? 1.0 : 0.0;
+        for (int r = lane; r < mc; r += 32) Vs[j * ldv + r] = (r == j) ? R(1) : R(0);
     for (int i = lane; i < m; i += 32) dd[i] = md.dsc[nd.r0 + i];
     for (int i = lane; i < m - 1 + sq; i += 32) ee[i] = md.esc[nd.r0 + i];
     if (lane == 0) { ctl->info = 0; ctl->hi = m - 1; }
@@ -65,15 +65,15 @@ __global__ void __launch_bounds__(32) k_leaf(const NodeDesc *__restrict__ leaves
     // ---- rectangular leaf: rotate the extra column (index m) away
     if (sq) {
         if (lane == 0) {
-            double x = ee[m - 1];
+            real_t x = ee[m - 1];
             for (int j = m - 1; j >= 0; --j) {
-                double c, s, r;
+                real_t c, s, r;
                 make_rot(dd[j], x, c, s, r);
                 dd[j] = r;
                 c1[j] = c; s1[j] = s;
                 if (j > 0) { x = -s * ee[j - 1]; ee[j - 1] = c * ee[j - 1]; }
             }
-            ee[m - 1] = 0.0;
+            ee[m - 1] = R(0);
         }
         __syncwarp();
         for (int j = m - 1; j >= 0; --j) rot_rows(Vs, ldv, mc, lane, j, m, c1[j], s1[j]);
@@ -81,11 +81,11 @@ __global__ void __launch_bounds__(32) k_leaf(const NodeDesc *__restrict__ leaves
     }
 
     // leaf-local norm for the zero-diagonal threshold
-    double bn = 0.0;
+    real_t bn = R(0);
     for (int i = lane; i < m; i += 32) bn = fmax(bn, fabs(dd[i]));
     for (int i = lane; i < m - 1; i += 32) bn = fmax(bn, fabs(ee[i]));
     bn = warp_max(bn);
-    const double dtiny = kEps * bn;
+    const real_t dtiny = kEps * bn;
 
     long long budget = (long long)max_sweeps * (m > 0 ? m : 1);
     for (;;) {
@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(32) k_leaf(const NodeDesc *__restrict__ leaves
                 act = ACT_DONE;
             } else if (fabs(ee[hi - 1]) <= kEps * (fabs(dd[hi - 1]) + fabs(dd[hi])) ||
                        fabs(ee[hi - 1]) <= dtiny * kEps) {
-                ee[hi - 1] = 0.0;
+                ee[hi - 1] = R(0);
                 ctl->hi = hi - 1;
                 act = ACT_NOOP;
             } else {
@@ -104,18 +104,18 @@ __global__ void __launch_bounds__(32) k_leaf(const NodeDesc *__restrict__ leaves
                 while (lo > 0 && fabs(ee[lo - 1]) > kEps * (fabs(dd[lo - 1]) + fabs(dd[lo])) &&
                        fabs(ee[lo - 1]) > dtiny * kEps)
                     --lo;
-                if (lo > 0) ee[lo - 1] = 0.0;
+                if (lo > 0) ee[lo - 1] = R(0);
                 int kz = -1;
                 for (int k = lo; k <= hi; ++k)
                     if (fabs(dd[k]) <= dtiny) { kz = k; break; }
                 if (kz >= 0) {
-                    dd[kz] = 0.0;
+                    dd[kz] = R(0);
                     if (kz < hi) {            // clear row kz with rows kz+1..hi
-                        double x = ee[kz];
-                        ee[kz] = 0.0;
+                        real_t x = ee[kz];
+                        ee[kz] = R(0);
                         int cnt = 0;
-                        for (int j = kz + 1; j <= hi && x != 0.0; ++j) {
-                            double c, s, r;
+                        for (int j = kz + 1; j <= hi && x != R(0); ++j) {
+                            real_t c, s, r;
                             make_rot(dd[j], x, c, s, r);
                             dd[j] = r;
                             if (j < hi) { x = -s * ee[j]; ee[j] = c * ee[j]; }
@@ -124,11 +124,11 @@ __global__ void __launch_bounds__(32) k_leaf(const NodeDesc *__restrict__ leaves
                         }
                         act = ACT_CHASE_ROW; ctl->k = kz; ctl->cnt = cnt;
                     } else {                  // clear column hi with columns hi-1..lo
-                        double x = ee[hi - 1];
-                        ee[hi - 1] = 0.0;
+                        real_t x = ee[hi - 1];
+                        ee[hi - 1] = R(0);
                         int jend = hi;
-                        for (int j = hi - 1; j >= lo && x != 0.0; --j) {
-                            double c, s, r;
+                        for (int j = hi - 1; j >= lo && x != R(0); --j) {
+                            real_t c, s, r;
                             make_rot(dd[j], x, c, s, r);
                             dd[j] = r;
                             if (j > lo) { x = -s * ee[j - 1]; ee[j - 1] = c * ee[j - 1]; }
@@ -140,28 +140,28 @@ __global__ void __launch_bounds__(32) k_leaf(const NodeDesc *__restrict__ leaves
                     ctl->lo = lo;
                 } else if (budget-- <= 0) {
                     int cnt = 0;
-                    for (int i = 0; i < hi; ++i) cnt += (ee[i] != 0.0);
+                    for (int i = 0; i < hi; ++i) cnt += (ee[i] != R(0));
                     ctl->info = cnt > 0 ? cnt : 1;
                     act = ACT_DONE;
                 } else {
                     // Golub-Kahan sweep on [lo, hi] with a Wilkinson shift
-                    double dm = dd[hi - 1], dn = dd[hi], em = ee[hi - 1];
-                    double el = (hi - 1 > lo) ? ee[hi - 2] : 0.0;
-                    double t11 = dm * dm + el * el, t22 = dn * dn + em * em, t12 = dm * em;
-                    double delta = 0.5 * (t11 - t22);
-                    double sg = (delta >= 0.0) ? 1.0 : -1.0;
-                    double den = delta + sg * hypot(delta, t12);
-                    double mu = (den != 0.0) ? t22 - t12 * t12 / den : t22;
-                    double y = dd[lo] * dd[lo] - mu;
-                    double z = dd[lo] * ee[lo];
+                    real_t dm = dd[hi - 1], dn = dd[hi], em = ee[hi - 1];
+                    real_t el = (hi - 1 > lo) ? ee[hi - 2] : R(0);
+                    real_t t11 = dm * dm + el * el, t22 = dn * dn + em * em, t12 = dm * em;
+                    real_t delta = R(0.5) * (t11 - t22);
+                    real_t sg = (delta >= R(0)) ? R(1) : R(-1);
+                    real_t den = delta + sg * hypot(delta, t12);
+                    real_t mu = (den != R(0)) ? t22 - t12 * t12 / den : t22;
+                    real_t y = dd[lo] * dd[lo] - mu;
+                    real_t z = dd[lo] * ee[lo];
                     for (int k = lo; k < hi; ++k) {
-                        double c, s, r;
+                        real_t c, s, r;
                         make_rot(y, z, c, s, r);
                         if (k > lo) ee[k - 1] = r;
-                        double dk = dd[k], ek = ee[k], dk1 = dd[k + 1];
+                        real_t dk = dd[k], ek = ee[k], dk1 = dd[k + 1];
                         dd[k] = c * dk + s * ek;
                         ee[k] = -s * dk + c * ek;
-                        double bulge = s * dk1;
+                        real_t bulge = s * dk1;
                         dd[k + 1] = c * dk1;
                         c1[k] = c; s1[k] = s;
                         make_rot(dd[k], bulge, c, s, r);
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(32) k_leaf(const NodeDesc *__restrict__ leaves
                         ee[k] = c * ek + s * dk1;
                         dd[k + 1] = -s * ek + c * dk1;
                         if (k < hi - 1) {
-                            double ek1 = ee[k + 1];
+                            real_t ek1 = ee[k + 1];
                             z = s * ek1;
                             ee[k + 1] = c * ek1;
                             y = ee[k];
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(32) k_leaf(const NodeDesc *__restrict__ leaves
 
     // non-negative values: flip the matching right vector
     for (int j = 0; j < m; ++j) {
-        if (dd[j] < 0.0) {
+        if (dd[j] < R(0)) {
             for (int r = lane; r < mc; r += 32) Vs[j * ldv + r] = -Vs[j * ldv + r];
         }
     }
@@ -211,10 +211,10 @@ __global__ void __launch_bounds__(32) k_leaf(const NodeDesc *__restrict__ leaves
     __syncwarp();
     // ascending order (ties by index)
     for (int j = lane; j < m; j += 32) {
-        double v = dd[j];
+        real_t v = dd[j];
         int rank = 0;
         for (int i = 0; i < m; ++i) {
-            double w = dd[i];
+            real_t w = dd[i];
             rank += (w < v) || (w == v && i < j);
         }
         perm[rank] = j;
@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(32) k_leaf(const NodeDesc *__restrict__ leaves
     __syncwarp();
     const long long ld = md.n;
     const int r0 = nd.r0;
-    double *Uo = md.U[nd.buf], *Vo = md.V[nd.buf];
+    real_t *Uo = md.U[nd.buf], *Vo = md.V[nd.buf];
     for (int p = 0; p < m; ++p) {
         const int j = perm[p];
         for (int r = lane; r < m; r += 32) Uo[(size_t)(r0 + p) * ld + r0 + r] = Us[j * ldu + r];
@@ -243,7 +243,7 @@ cudaError_t launch_leaves(const NodeDesc *leaves, int nleaves, const MatDesc *ma
                           int max_sweeps, cudaStream_t st) {
     if (nleaves <= 0) return cudaSuccess;
     const int L = leafmax;
-    size_t smem = sizeof(double) * ((size_t)L * L + (size_t)(L + 1) * (L + 1) + 6 * (size_t)(L + 1)) +
+    size_t smem = sizeof(real_t) * ((size_t)L * L + (size_t)(L + 1) * (L + 1) + 6 * (size_t)(L + 1)) +
                   sizeof(int) * (L + 2) + sizeof(LeafCtl) + 16;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -254,4 +254,4 @@ cudaError_t launch_leaves(const NodeDesc *leaves, int nleaves, const MatDesc *ma
     return cudaGetLastError();
 }
 
-}  // namespace bdc
+}  // namespace BDC_NS

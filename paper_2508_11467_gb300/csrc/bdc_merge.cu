@@ -23,7 +23,7 @@
 
 #include "bdc_internal.cuh"
 
-namespace bdc {
+namespace BDC_NS {
 
 namespace {
 
@@ -54,12 +54,12 @@ __device__ __forceinline__ int block_excl_scan(int v, int *wsum, int &total) {
     return base + x - v;
 }
 
-__device__ __forceinline__ double block_max(double v, double *dsum) {
+__device__ __forceinline__ real_t block_max(real_t v, real_t *dsum) {
     v = warp_max(v);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (lane == 0) dsum[w] = v;
     __syncthreads();
-    double r = 0.0;
+    real_t r = 0.0;
     for (int i = 0; i < nw; ++i) r = fmax(r, dsum[i]);
     __syncthreads();
     return r;
@@ -71,49 +71,49 @@ __device__ __forceinline__ int block_isum(int v, int *wsum) {
     return t;
 }
 
-// exclusive block scan of doubles in thread order (reverse = false: sum over
+// exclusive block scan of real_ts in thread order (reverse = false: sum over
 // threads before t; true: over threads after t); no subtraction, so small
 // partial sums keep their relative accuracy
-__device__ __forceinline__ double block_excl_scan_d(double v, double *buf, bool reverse) {
+__device__ __forceinline__ real_t block_excl_scan_d(real_t v, real_t *buf, bool reverse) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    double x = v;
+    real_t x = v;
     if (!reverse) {
         for (int o = 1; o < 32; o <<= 1) {
-            const double y = __shfl_up_sync(0xffffffffu, x, o);
+            const real_t y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
         }
     } else {
         for (int o = 1; o < 32; o <<= 1) {
-            const double y = __shfl_down_sync(0xffffffffu, x, o);
+            const real_t y = __shfl_down_sync(0xffffffffu, x, o);
             if (lane + o < 32) x += y;
         }
     }
-    double ex = reverse ? __shfl_down_sync(0xffffffffu, x, 1) : __shfl_up_sync(0xffffffffu, x, 1);
+    real_t ex = reverse ? __shfl_down_sync(0xffffffffu, x, 1) : __shfl_up_sync(0xffffffffu, x, 1);
     if (reverse ? lane == 31 : lane == 0) ex = 0.0;
     if (reverse ? lane == 0 : lane == 31) buf[w] = x;
     __syncthreads();
     if (w == 0) {
-        double t = (lane < nw) ? buf[lane] : 0.0;
-        double tx = t;
+        real_t t = (lane < nw) ? buf[lane] : R(0);
+        real_t tx = t;
         if (!reverse) {
             for (int o = 1; o < 32; o <<= 1) {
-                const double y = __shfl_up_sync(0xffffffffu, tx, o);
+                const real_t y = __shfl_up_sync(0xffffffffu, tx, o);
                 if (lane >= o) tx += y;
             }
         } else {
             for (int o = 1; o < 32; o <<= 1) {
-                const double y = __shfl_down_sync(0xffffffffu, tx, o);
+                const real_t y = __shfl_down_sync(0xffffffffu, tx, o);
                 if (lane + o < 32) tx += y;
             }
         }
         // exclusive over warps
-        double e = reverse ? __shfl_down_sync(0xffffffffu, tx, 1) : __shfl_up_sync(0xffffffffu, tx, 1);
+        real_t e = reverse ? __shfl_down_sync(0xffffffffu, tx, 1) : __shfl_up_sync(0xffffffffu, tx, 1);
         if (reverse ? lane == 31 : lane == 0) e = 0.0;
         __syncwarp();
         if (lane < nw) buf[lane] = e;
     }
     __syncthreads();
-    const double r = buf[w] + ex;
+    const real_t r = buf[w] + ex;
     __syncthreads();
     return r;
 }
@@ -126,16 +126,16 @@ __device__ __forceinline__ int col_side(int c, int nl) { return c == 0 ? 0 : (c 
 // each rotated pair, and the final z of every survivor in place in zs.
 // src (may be null) gives the pre-deflation column of each position, used to
 // type survivors.  Returns the number ns of small-z survivors.
-__device__ int deflate_core(int m, double tol, const double *ds, double *zs, const int *src, int nl,
-                            int *slist, int *sidx, int *role, double *rc, double *rs, int *wsum,
+__device__ int deflate_core(int m, real_t tol, const real_t *ds, real_t *zs, const int *src, int nl,
+                            int *slist, int *sidx, int *role, real_t *rc, real_t *rs, int *wsum,
                             int *a_out) {
     const int T = blockDim.x, t = threadIdx.x;
     const int seg = (m + T - 1) / T;
     const int b = min(m, t * seg), e = min(m, b + seg);
     // z_0 (paired with d_0 = 0) is clamped up to tol, never deflated
     if (t == 0) {
-        double z0 = zs[0];
-        if (fabs(z0) < tol) zs[0] = (z0 < 0.0) ? -tol : tol;
+        real_t z0 = zs[0];
+        if (fabs(z0) < tol) zs[0] = (z0 < R(0)) ? -tol : tol;
     }
     __syncthreads();
     int cnt = 0;
@@ -178,12 +178,12 @@ __device__ int deflate_core(int m, double tol, const double *ds, double *zs, con
     for (int kk = sb; kk < se; ++kk) {
         const int p = slist[kk];
         if ((role[p] & 15) != ROLE_CHAIN || !(role[p] & FL_START)) continue;
-        double zr = zs[p];
+        real_t zr = zs[p];
         int ty = src ? col_side(src[p], nl) : 1;
         for (int j = kk + 1; j < ns; ++j) {
             const int q = slist[j];
-            const double zq = zs[q];
-            double c, s, r;
+            const real_t zq = zs[q];
+            real_t c, s, r;
             make_rot(zq, zr, c, s, r);    // c = z_q / r, s = z_prev / r
             rc[q] = c; rs[q] = s;
             zr = r;
@@ -197,11 +197,11 @@ __device__ int deflate_core(int m, double tol, const double *ds, double *zs, con
     }
     // values close to d_0 = 0: right-side rotations fold them into z_0
     if (t == 0 && a > 0) {
-        double zr = zs[0];
+        real_t zr = zs[0];
         for (int j = 1; j <= a; ++j) {
             const int q = slist[j];
-            const double zq = zs[q];
-            double c, s, r;
+            const real_t zq = zs[q];
+            real_t c, s, r;
             make_rot(zr, zq, c, s, r);    // c = z_0 / r, s = z_q / r
             rc[q] = c; rs[q] = s;
             zr = r;
@@ -218,25 +218,25 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
                                                              NodeState *__restrict__ state,
                                                              GemmProb *__restrict__ probs, int scans) {
     __shared__ int wsum[PREP_THREADS / 32 + 1];
-    __shared__ double dsum[PREP_THREADS / 32 + 1];
+    __shared__ real_t dsum[PREP_THREADS / 32 + 1];
     const NodeDesc nd = nodes[blockIdx.x];
     const MatDesc md = mats[nd.mat];
     const int m = nd.m, nl = nd.nl, nr = m - nl - 1, sqre = nd.sqre, mc = m + sqre;
     const int r0 = nd.r0, r0L = r0, r0R = r0 + nl + 1;
     const long long ld = md.n;
     const int T = blockDim.x, t = threadIdx.x;
-    double *ds = md.ds + r0, *zs = md.zs + r0;
+    real_t *ds = md.ds + r0, *zs = md.zs + r0;
     int *src = md.src + r0;
-    const double alpha = md.dsc[r0 + nl], beta = md.esc[r0 + nl];
-    const double *Vc = md.V[1 - nd.buf];                 // children's right vectors
+    const real_t alpha = md.dsc[r0 + nl], beta = md.esc[r0 + nl];
+    const real_t *Vc = md.V[1 - nd.buf];                 // children's right vectors
 
     // ---- z and the merged ascending order (children are sorted through Q)
     const int *QL = md.Q + r0L, *QR = md.Q + r0R;
-    const double *DL = md.D + r0L, *DR = md.D + r0R;
-    double dmax = 0.0;
+    const real_t *DL = md.D + r0L, *DR = md.D + r0R;
+    real_t dmax = 0.0;
     for (int p = t; p < nl; p += T) {
         const int j = QL[p];
-        const double v = DL[j];
+        const real_t v = DL[j];
         int lo = 0, hi = nr;                 // # right values < v (ties: left first)
         while (lo < hi) { int mid = (lo + hi) >> 1; if (DR[QR[mid]] < v) lo = mid + 1; else hi = mid; }
         const int pos = 1 + p + lo;
@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
     }
     for (int q = t; q < nr; q += T) {
         const int j = QR[q];
-        const double v = DR[j];
+        const real_t v = DR[j];
         int lo = 0, hi = nl;                 // # left values <= v
         while (lo < hi) { int mid = (lo + hi) >> 1; if (DL[QL[mid]] <= v) lo = mid + 1; else hi = mid; }
         const int pos = 1 + q + lo;
@@ -256,15 +256,15 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
         src[pos] = nl + 1 + j;
         dmax = fmax(dmax, fabs(v));
     }
-    __shared__ double s_cq, s_sq;
+    __shared__ real_t s_cq, s_sq;
     if (t == 0) {
         // d_0 = 0 column: alpha * (last entry of q_1), folded with beta * (first
         // entry of q_2) when the right child is rectangular
-        double z0 = alpha * Vc[(size_t)(r0L + nl) * ld + r0L + nl];
-        double cq = 1.0, sq = 0.0;
+        real_t z0 = alpha * Vc[(size_t)(r0L + nl) * ld + r0L + nl];
+        real_t cq = 1.0, sq = 0.0;
         if (sqre) {
-            const double b0 = beta * Vc[(size_t)(r0R + nr) * ld + r0R];
-            double r;
+            const real_t b0 = beta * Vc[(size_t)(r0R + nr) * ld + r0R];
+            real_t r;
             make_rot(z0, b0, cq, sq, r);
             z0 = r;
         }
@@ -274,9 +274,10 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
         s_cq = cq; s_sq = sq;
     }
     dmax = block_max(dmax, dsum);
-    // 8 eps ||M|| with ||M|| ~ max(|d|, |alpha|, |beta|); the floor 2^-400
-    // keeps an all-zero node well defined (tol^2 stays a normal number)
-    const double tol = 8.0 * kEps * fmax(fmax(dmax, 0x1p-400), fmax(fabs(alpha), fabs(beta)));
+    // 8 eps ||M|| with ||M|| ~ max(|d|, |alpha|, |beta|); the floor (2^-400 in
+    // FP64, 2^-60 in FP32) keeps an all-zero node well defined (tol^2 stays a
+    // normal number)
+    const real_t tol = R(8) * kEps * fmax(fmax(dmax, kTolFloor), fmax(fabs(alpha), fabs(beta)));
 
     // ---- deflation
     int a;
@@ -310,7 +311,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
     int io = block_excl_scan(co, wsum, no);
     const int P1 = (n1 + 7) & ~7;
     const int Ktot = P1 + 1 + n2 + n3;
-    double *dM = md.dM + r0, *zM = md.zM + r0, *dval = md.dval + r0;
+    real_t *dM = md.dM + r0, *zM = md.zM + r0, *dval = md.dval + r0;
     int *kposM = md.kposM + r0, *invK = md.invK + nd.kbase, *dest = md.dest + r0, *dsrc = md.dsrc + r0;
     for (int p = b; p < e; ++p) {
         const int r = role[p], code = r & 15;
@@ -343,24 +344,24 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
     if (scans) {
         // moment scans of the survivors for the root start estimates: prefix
         // sums (inclusive) of z^2, z^2 d^2, z^2 d^4 and the same suffix sums
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+        real_t a0 = 0.0, a1 = 0.0, a2 = 0.0;
         for (int k = ik0; k < ik0 + ck; ++k) {
-            const double z2 = zM[k] * zM[k], d2 = dM[k] * dM[k];
+            const real_t z2 = zM[k] * zM[k], d2 = dM[k] * dM[k];
             a0 += z2; a1 += z2 * d2; a2 += z2 * d2 * d2;
         }
-        double *pz = md.pz + r0;
+        real_t *pz = md.pz + r0;
         const long long sn = md.n;
-        double c0 = block_excl_scan_d(a0, dsum, false), c1 = block_excl_scan_d(a1, dsum, false),
+        real_t c0 = block_excl_scan_d(a0, dsum, false), c1 = block_excl_scan_d(a1, dsum, false),
                c2 = block_excl_scan_d(a2, dsum, false);
         for (int k = ik0; k < ik0 + ck; ++k) {
-            const double z2 = zM[k] * zM[k], d2 = dM[k] * dM[k];
+            const real_t z2 = zM[k] * zM[k], d2 = dM[k] * dM[k];
             c0 += z2; c1 += z2 * d2; c2 += z2 * d2 * d2;
             pz[k] = c0; pz[sn + k] = c1; pz[2 * sn + k] = c2;
         }
         c0 = block_excl_scan_d(a0, dsum, true); c1 = block_excl_scan_d(a1, dsum, true);
         c2 = block_excl_scan_d(a2, dsum, true);
         for (int k = ik0 + ck - 1; k >= ik0; --k) {
-            const double z2 = zM[k] * zM[k], d2 = dM[k] * dM[k];
+            const real_t z2 = zM[k] * zM[k], d2 = dM[k] * dM[k];
             c0 += z2; c1 += z2 * d2; c2 += z2 * d2 * d2;
             pz[3 * sn + k] = c0; pz[4 * sn + k] = c1; pz[5 * sn + k] = c2;
         }
@@ -368,13 +369,13 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
     __syncthreads();
     // rho = sum of the survivors' z^2 (the secular solver's upper bound for
     // the last root and one of the MLP features)
-    double zz = 0.0;
+    real_t zz = 0.0;
     for (int k = t; k < N; k += T) zz = fma(zM[k], zM[k], zz);
     zz = warp_sum(zz);
     if ((t & 31) == 0) dsum[t >> 5] = zz;
     __syncthreads();
     if (t == 0) {
-        double rho = 0.0;
+        real_t rho = 0.0;
         for (int w = 0; w < (T >> 5); ++w) rho += dsum[w];
         NodeState s;
         s.N = N; s.n1 = n1; s.n2 = n2; s.n3 = n3; s.P1 = P1; s.Ktot = Ktot;
@@ -384,7 +385,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
         const int Ktop = P1 + 1 + n2, Kbot = Ktot - P1;
         GemmProb *pr = probs + 4 * (size_t)blockIdx.x;
         // U: top rows 0..nl (incl. the coupling row), bottom rows nl+1..m-1
-        double *Uo = md.U[nd.buf], *Vo = md.V[nd.buf];
+        real_t *Uo = md.U[nd.buf], *Vo = md.V[nd.buf];
         pr[0] = GemmProb{md.Wt + wb, md.UM + wb, Uo + (size_t)r0 * ld + r0, m, Ktot, (int)ld,
                          nl + 1, N, Ktop};
         pr[1] = GemmProb{md.Wt + wb + (nl + 1) + (size_t)P1 * m, md.UM + wb + P1,
@@ -399,23 +400,23 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
 
 // ------------------------------------------------------------------ gather
 struct ColSrc {
-    const double *U, *V;
+    const real_t *U, *V;
     long long ld;
     int r0, nl, nr, sqre;
-    double cq, sq;
-    __device__ double u(int c, int r) const {       // r in [0, m)
-        if (c == 0) return (r == nl) ? 1.0 : 0.0;
-        if (c <= nl) return (r < nl) ? U[(size_t)(r0 + c - 1) * ld + r0 + r] : 0.0;
-        return (r > nl) ? U[(size_t)(r0 + nl + 1 + (c - nl - 1)) * ld + r0 + r] : 0.0;
+    real_t cq, sq;
+    __device__ real_t u(int c, int r) const {       // r in [0, m)
+        if (c == 0) return (r == nl) ? R(1) : R(0);
+        if (c <= nl) return (r < nl) ? U[(size_t)(r0 + c - 1) * ld + r0 + r] : R(0);
+        return (r > nl) ? U[(size_t)(r0 + nl + 1 + (c - nl - 1)) * ld + r0 + r] : R(0);
     }
-    __device__ double q1(int r) const { return (r <= nl) ? V[(size_t)(r0 + nl) * ld + r0 + r] : 0.0; }
-    __device__ double q2(int r) const {
-        return (sqre && r > nl) ? V[(size_t)(r0 + nl + 1 + nr) * ld + r0 + r] : 0.0;
+    __device__ real_t q1(int r) const { return (r <= nl) ? V[(size_t)(r0 + nl) * ld + r0 + r] : R(0); }
+    __device__ real_t q2(int r) const {
+        return (sqre && r > nl) ? V[(size_t)(r0 + nl + 1 + nr) * ld + r0 + r] : R(0);
     }
-    __device__ double v(int c, int r) const {       // r in [0, m + sqre)
+    __device__ real_t v(int c, int r) const {       // r in [0, m + sqre)
         if (c == 0) return cq * q1(r) + sq * q2(r);
-        if (c <= nl) return (r <= nl) ? V[(size_t)(r0 + c - 1) * ld + r0 + r] : 0.0;
-        return (r > nl) ? V[(size_t)(r0 + nl + 1 + (c - nl - 1)) * ld + r0 + r] : 0.0;
+        if (c <= nl) return (r <= nl) ? V[(size_t)(r0 + c - 1) * ld + r0 + r] : R(0);
+        return (r > nl) ? V[(size_t)(r0 + nl + 1 + (c - nl - 1)) * ld + r0 + r] : R(0);
     }
 };
 
@@ -430,17 +431,17 @@ __global__ void __launch_bounds__(128) k_merge_gather(const NodeDesc *__restrict
     const int m = nd.m, nl = nd.nl, sqre = nd.sqre, mc = m + sqre, r0 = nd.r0;
     const int r = md.role[r0 + p], code = r & 15;
     const int *src = md.src + r0, *dest = md.dest + r0, *slist = md.slist + r0;
-    const double *rc = md.rc + r0, *rs = md.rs + r0;
+    const real_t *rc = md.rc + r0, *rs = md.rs + r0;
     ColSrc cs{md.U[1 - nd.buf], md.V[1 - nd.buf], (long long)md.n, r0, nl, m - nl - 1, sqre, ns.cq, ns.sq};
     const long long wb = (long long)r0 * md.wstride, ld = md.n;
-    double *W = md.Wt + wb, *Qm = md.Qt + wb;
+    real_t *W = md.Wt + wb, *Qm = md.Qt + wb;
     // survivors go to the K-ordered workspace W~ / Q~ (leading dimension m / m+sqre);
     // deflated vectors straight to their final column N + slot of the node block
-    double *Uo = md.U[nd.buf] + (size_t)r0 * ld + r0, *Vo = md.V[nd.buf] + (size_t)r0 * ld + r0;
-    auto ucol = [&](int dst) -> double * {
+    real_t *Uo = md.U[nd.buf] + (size_t)r0 * ld + r0, *Vo = md.V[nd.buf] + (size_t)r0 * ld + r0;
+    auto ucol = [&](int dst) -> real_t * {
         return dst >= 0 ? W + (size_t)dst * m : Uo + (size_t)(ns.N + (-dst - 1)) * ld;
     };
-    auto vcol = [&](int dst) -> double * {
+    auto vcol = [&](int dst) -> real_t * {
         return dst >= 0 ? Qm + (size_t)dst * mc : Vo + (size_t)(ns.N + (-dst - 1)) * ld;
     };
 
@@ -459,10 +460,10 @@ __global__ void __launch_bounds__(128) k_merge_gather(const NodeDesc *__restrict
             }
         }
         for (int row = threadIdx.x; row < mc; row += blockDim.x) {
-            double y = cs.v(0, row);
+            real_t y = cs.v(0, row);
             for (int j = 1; j <= a; ++j) {
                 const int q = slist[j];
-                const double x = cs.v(src[q], row), c = rc[q], s = rs[q];
+                const real_t x = cs.v(src[q], row), c = rc[q], s = rs[q];
                 vcol(dest[q])[row] = -s * y + c * x;
                 y = c * y + s * x;
             }
@@ -477,11 +478,11 @@ __global__ void __launch_bounds__(128) k_merge_gather(const NodeDesc *__restrict
     if (code == ROLE_CHAIN) {                          // chain start: walk to its end
         const int k0 = md.sidx[r0 + p];
         for (int row = threadIdx.x; row < m; row += blockDim.x) {
-            double y = cs.u(src[p], row);
+            real_t y = cs.u(src[p], row);
             int prev = p;
             for (int k = k0 + 1; k < m; ++k) {
                 const int q = slist[k];
-                const double x = cs.u(src[q], row), c = rc[q], s = rs[q];
+                const real_t x = cs.u(src[q], row), c = rc[q], s = rs[q];
                 ucol(dest[prev])[row] = c * y - s * x;
                 y = s * y + c * x;
                 prev = q;
@@ -490,11 +491,11 @@ __global__ void __launch_bounds__(128) k_merge_gather(const NodeDesc *__restrict
             ucol(dest[prev])[row] = y;
         }
         for (int row = threadIdx.x; row < mc; row += blockDim.x) {
-            double y = cs.v(src[p], row);
+            real_t y = cs.v(src[p], row);
             int prev = p;
             for (int k = k0 + 1; k < m; ++k) {
                 const int q = slist[k];
-                const double x = cs.v(src[q], row), c = rc[q], s = rs[q];
+                const real_t x = cs.v(src[q], row), c = rc[q], s = rs[q];
                 vcol(dest[prev])[row] = c * y - s * x;
                 y = s * y + c * x;
                 prev = q;
@@ -506,7 +507,7 @@ __global__ void __launch_bounds__(128) k_merge_gather(const NodeDesc *__restrict
     }
     // singleton survivor or small-z deflation: plain copy
     const int c = src[p];
-    double *ud = ucol(dest[p]), *vd = vcol(dest[p]);
+    real_t *ud = ucol(dest[p]), *vd = vcol(dest[p]);
     for (int row = threadIdx.x; row < m; row += blockDim.x) ud[row] = cs.u(c, row);
     for (int row = threadIdx.x; row < mc; row += blockDim.x) vd[row] = cs.v(c, row);
 }
@@ -521,16 +522,16 @@ __global__ void __launch_bounds__(256) k_merge_finish(const NodeDesc *__restrict
     const MatDesc md = mats[nd.mat];
     const NodeState ns = state[nd.id];
     const int r0 = nd.r0, N = ns.N, ndef = ns.ndef;
-    const double *om = md.omega + r0, *dv = md.dval + r0;
+    const real_t *om = md.omega + r0, *dv = md.dval + r0;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        const double w = om[i];
+        const real_t w = om[i];
         int lo = 0, hi = ndef;           // # deflated values < w
         while (lo < hi) { int mid = (lo + hi) >> 1; if (dv[mid] < w) lo = mid + 1; else hi = mid; }
         md.D[r0 + i] = w;
         md.Q[r0 + i + lo] = i;
     }
     for (int s = threadIdx.x; s < ndef; s += blockDim.x) {
-        const double v = dv[s];
+        const real_t v = dv[s];
         int lo = 0, hi = N;              // # roots <= v
         while (lo < hi) { int mid = (lo + hi) >> 1; if (om[mid] <= v) lo = mid + 1; else hi = mid; }
         md.D[r0 + N + s] = v;
@@ -538,12 +539,13 @@ __global__ void __launch_bounds__(256) k_merge_finish(const NodeDesc *__restrict
     }
 }
 
-__global__ void __launch_bounds__(PREP_THREADS) k_deflate_single(int m, const double *d, const double *z,
-                                                                 double tol, int *keep, double *zout,
-                                                                 double *dval, int *scratch_i,
-                                                                 double *scratch_d) {
+#ifndef BDC_FP32   // step entry point: FP64 only
+__global__ void __launch_bounds__(PREP_THREADS) k_deflate_single(int m, const real_t *d, const real_t *z,
+                                                                 real_t tol, int *keep, real_t *zout,
+                                                                 real_t *dval, int *scratch_i,
+                                                                 real_t *scratch_d) {
     __shared__ int wsum[PREP_THREADS / 32 + 1];
-    double *zs = scratch_d, *rc = scratch_d + m, *rs = scratch_d + 2 * m;
+    real_t *zs = scratch_d, *rc = scratch_d + m, *rs = scratch_d + 2 * m;
     int *slist = scratch_i, *sidx = scratch_i + m, *role = scratch_i + 2 * m;
     for (int p = threadIdx.x; p < m; p += blockDim.x) zs[p] = z[p];
     __syncthreads();
@@ -552,10 +554,12 @@ __global__ void __launch_bounds__(PREP_THREADS) k_deflate_single(int m, const do
     for (int p = threadIdx.x; p < m; p += blockDim.x) {
         const int code = role[p] & 15;
         keep[p] = (code == ROLE_KEEP);
-        zout[p] = (code == ROLE_KEEP) ? zs[p] : 0.0;
-        dval[p] = (code == ROLE_ZERO) ? 0.0 : (code == ROLE_KEEP ? 0.0 : d[p]);
+        zout[p] = (code == ROLE_KEEP) ? zs[p] : R(0);
+        dval[p] = (code == ROLE_ZERO) ? R(0) : (code == ROLE_KEEP ? R(0) : d[p]);
     }
 }
+
+#endif
 
 }  // namespace
 
@@ -582,23 +586,26 @@ cudaError_t launch_merge_finish(const NodeDesc *nodes, int nnodes, const MatDesc
     return cudaGetLastError();
 }
 
-cudaError_t launch_deflate_single(int m, const double *d, const double *z, double tol, int *keep,
-                                  double *zout, double *dval, cudaStream_t st) {
+#ifndef BDC_FP32
+cudaError_t launch_deflate_single(int m, const real_t *d, const real_t *z, real_t tol, int *keep,
+                                  real_t *zout, real_t *dval, cudaStream_t st) {
     if (m <= 0) return cudaSuccess;
     void *si = nullptr, *sd = nullptr;
     cudaError_t e = cudaMallocAsync(&si, sizeof(int) * 3 * (size_t)m, st);
     if (e != cudaSuccess) return e;
-    e = cudaMallocAsync(&sd, sizeof(double) * 3 * (size_t)m, st);
+    e = cudaMallocAsync(&sd, sizeof(real_t) * 3 * (size_t)m, st);
     if (e != cudaSuccess) { cudaFreeAsync(si, st); return e; }
-    k_deflate_single<<<1, PREP_THREADS, 0, st>>>(m, d, z, tol, keep, zout, dval, (int *)si, (double *)sd);
+    k_deflate_single<<<1, PREP_THREADS, 0, st>>>(m, d, z, tol, keep, zout, dval, (int *)si, (real_t *)sd);
     e = cudaGetLastError();
     cudaFreeAsync(si, st);
     cudaFreeAsync(sd, st);
     return e;
 }
+#endif
 
-}  // namespace bdc
+}  // namespace BDC_NS
 
+#ifndef BDC_FP32   // allocation-free step entry point: FP64 only
 // ---------------------------------------------------------------------------
 // Allocation-free deflation.
 //
@@ -617,13 +624,13 @@ cudaError_t launch_deflate_single(int m, const double *d, const double *z, doubl
 // the caller.  Every scratch entry a call reads is written earlier by the
 // same call, so nothing has to be cleared between calls.
 // ---------------------------------------------------------------------------
-namespace bdc {
+namespace BDC_NS {
 namespace {
 
 constexpr int kNoAllocMax = BDC_DEFLATE_NOALLOC_MAX;
 constexpr size_t kNoAllocDoubles = 3 * (size_t)kNoAllocMax;   // zs, rc, rs
 constexpr size_t kNoAllocInts = 3 * (size_t)kNoAllocMax;      // slist, sidx, role
-static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocDoubles * sizeof(double) +
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocDoubles * sizeof(real_t) +
                                                                   kNoAllocInts * sizeof(int)];
 
 // device address of g_noalloc_scratch, looked up once per device (the host
@@ -649,7 +656,8 @@ cudaError_t noalloc_scratch(void **out) {
 }
 
 }  // namespace
-}  // namespace bdc
+}  // namespace BDC_NS
+
 
 extern "C" int bdc_deflate_noalloc(int m, const double *d, const double *z, double tol, int *keep, double *zout,
                                    double *dval, bdc_stream_t stream) {
@@ -660,8 +668,9 @@ extern "C" int bdc_deflate_noalloc(int m, const double *d, const double *z, doub
     if (m == 0) return 0;
     void *base = nullptr;
     if (noalloc_scratch(&base) != cudaSuccess) return BDC_ERR_CUDA;
-    double *sd = (double *)base;
-    int *si = (int *)((char *)base + kNoAllocDoubles * sizeof(double));
+    real_t *sd = (real_t *)base;
+    int *si = (int *)((char *)base + kNoAllocDoubles * sizeof(real_t));
     k_deflate_single<<<1, PREP_THREADS, 0, (cudaStream_t)stream>>>(m, d, z, tol, keep, zout, dval, si, sd);
     return cudaGetLastError() == cudaSuccess ? 0 : BDC_ERR_CUDA;
 }
+#endif  // BDC_FP32

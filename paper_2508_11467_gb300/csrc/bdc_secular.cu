@@ -21,33 +21,37 @@
 //            column); k_vectors_warp does the same with a warp per column
 //            for merges of order <= 1024.
 //
-// All arithmetic is FP64.
+// All arithmetic is in real_t: FP64, or FP32 in the FP32 build.  The root
+// starts (k_root_start, bdc_mlp.cuh) and the standalone step kernels are
+// FP64 only.
 #include "bdc_internal.cuh"
+#ifndef BDC_FP32
 #include "bdc_mlp.cuh"
+#endif
 
-namespace bdc {
+namespace BDC_NS {
 
 namespace {
 
 struct Sums {
-    double psi, dpsi, phi, dphi;
+    real_t psi, dpsi, phi, dphi;
 };
 
 // pole sums at x = w^2 - d_o^2; left group j <= i (psi < 0), right j > i
-__device__ __forceinline__ Sums pole_sums(const double *__restrict__ d, const double *__restrict__ z,
-                                          int N, int i, double dor, double x, int lane) {
-    Sums s{0.0, 0.0, 0.0, 0.0};
+__device__ __forceinline__ Sums pole_sums(const real_t *__restrict__ d, const real_t *__restrict__ z,
+                                          int N, int i, real_t dor, real_t x, int lane) {
+    Sums s{R(0.0), R(0.0), R(0.0), R(0.0)};
     for (int j = lane; j <= i; j += 32) {
-        const double dj = d[j], zj = z[j];
-        const double del = (dj - dor) * (dj + dor) - x;
-        const double t = zj / del;
+        const real_t dj = d[j], zj = z[j];
+        const real_t del = (dj - dor) * (dj + dor) - x;
+        const real_t t = zj / del;
         s.psi = fma(zj, t, s.psi);
         s.dpsi = fma(t, t, s.dpsi);
     }
     for (int j = i + 1 + lane; j < N; j += 32) {
-        const double dj = d[j], zj = z[j];
-        const double del = (dj - dor) * (dj + dor) - x;
-        const double t = zj / del;
+        const real_t dj = d[j], zj = z[j];
+        const real_t del = (dj - dor) * (dj + dor) - x;
+        const real_t t = zj / del;
         s.phi = fma(zj, t, s.phi);
         s.dphi = fma(t, t, s.dphi);
     }
@@ -60,50 +64,50 @@ __device__ __forceinline__ Sums pole_sums(const double *__restrict__ d, const do
 
 struct RootState {
     int o;                       // origin pole index
-    double dor;                  // d_o
-    double lo, hi;               // bracket for x = w^2 - d_o^2
-    double lamL, lamR;           // the two interval poles relative to d_o^2
-    double x;
-    double dl, du;               // the interval poles d_i, d_{i+1}
+    real_t dor;                  // d_o
+    real_t lo, hi;               // bracket for x = w^2 - d_o^2
+    real_t lamL, lamR;           // the two interval poles relative to d_o^2
+    real_t x;
+    real_t dl, du;               // the interval poles d_i, d_{i+1}
     Sums s;
 };
 
 // Safeguarded rational iteration from r.x; returns the iterations used or
 // -1 when max_iter did not suffice.  All lanes return the same result.
-__device__ __forceinline__ int root_iterate(const double *__restrict__ d, const double *__restrict__ z, int N, int i, bool last,
+__device__ __forceinline__ int root_iterate(const real_t *__restrict__ d, const real_t *__restrict__ z, int N, int i, bool last,
                             int max_iter, RootState &r) {
     const int lane = threadIdx.x & 31;
     int it = 0;
     for (;;) {
-        const double f = 1.0 + r.s.psi + r.s.phi;
-        const double scale = 1.0 + r.s.phi - r.s.psi;
-        if (fabs(f) <= 16.0 * kEps * scale) break;
-        if (f > 0.0) r.hi = r.x; else r.lo = r.x;
+        const real_t f = R(1.0) + r.s.psi + r.s.phi;
+        const real_t scale = R(1.0) + r.s.phi - r.s.psi;
+        if (fabs(f) <= R(16.0) * kEps * scale) break;
+        if (f > R(0.0)) r.hi = r.x; else r.lo = r.x;
         if (it >= max_iter) return -1;
         // rational model through the two nearest poles (value and slope)
-        const double DL = r.lamL - r.x;
-        double eta;
+        const real_t DL = r.lamL - r.x;
+        real_t eta;
         bool ok = true;
         if (!last) {
-            const double DR = r.lamR - r.x;
-            const double sL = DL * DL * r.s.dpsi, sR = DR * DR * r.s.dphi;
-            const double C = f - DL * r.s.dpsi - DR * r.s.dphi;
-            const double a = C * (DL + DR) + sL + sR;
-            const double b = C * DL * DR + sL * DR + sR * DL;
-            if (C == 0.0) {
+            const real_t DR = r.lamR - r.x;
+            const real_t sL = DL * DL * r.s.dpsi, sR = DR * DR * r.s.dphi;
+            const real_t C = f - DL * r.s.dpsi - DR * r.s.dphi;
+            const real_t a = C * (DL + DR) + sL + sR;
+            const real_t b = C * DL * DR + sL * DR + sR * DL;
+            if (C == R(0.0)) {
                 eta = b / a;
             } else {
-                const double disc = sqrt(fabs(a * a - 4.0 * b * C));
-                eta = (a > 0.0) ? (2.0 * b / (a + disc)) : ((a - disc) / (2.0 * C));
+                const real_t disc = sqrt(fabs(a * a - R(4.0) * b * C));
+                eta = (a > R(0.0)) ? (R(2.0) * b / (a + disc)) : ((a - disc) / (R(2.0) * C));
             }
         } else {
-            const double sL = DL * DL * r.s.dpsi;
-            const double C = f - DL * r.s.dpsi;
-            if (C > 0.0) eta = DL + sL / C; else { eta = 0.0; ok = false; }
+            const real_t sL = DL * DL * r.s.dpsi;
+            const real_t C = f - DL * r.s.dpsi;
+            if (C > R(0.0)) eta = DL + sL / C; else { eta = R(0.0); ok = false; }
         }
-        double xn = r.x + eta;
-        if (!ok || !(xn > r.lo && xn < r.hi)) xn = 0.5 * (r.lo + r.hi);
-        const double step = xn - r.x;
+        real_t xn = r.x + eta;
+        if (!ok || !(xn > r.lo && xn < r.hi)) xn = R(0.5) * (r.lo + r.hi);
+        const real_t step = xn - r.x;
         r.x = xn;
         ++it;
         if (!last) {
@@ -111,15 +115,15 @@ __device__ __forceinline__ int root_iterate(const double *__restrict__ d, const 
             // midpoint is re-expressed from the other pole (x and D2 are
             // within a factor 2, so x -+ D2 is exact); from the midpoint start
             // the bracket never crosses, from a predicted start it may
-            const double D2 = r.lamR - r.lamL;
-            if (r.o == i && r.x > 0.5 * D2) {
-                r.o = i + 1; r.dor = r.du; r.x -= D2; r.lo -= D2; r.hi -= D2; r.lamL = -D2; r.lamR = 0.0;
-            } else if (r.o == i + 1 && r.x < -0.5 * D2) {
-                r.o = i; r.dor = r.dl; r.x += D2; r.lo += D2; r.hi += D2; r.lamL = 0.0; r.lamR = D2;
+            const real_t D2 = r.lamR - r.lamL;
+            if (r.o == i && r.x > R(0.5) * D2) {
+                r.o = i + 1; r.dor = r.du; r.x -= D2; r.lo -= D2; r.hi -= D2; r.lamL = -D2; r.lamR = R(0.0);
+            } else if (r.o == i + 1 && r.x < -R(0.5) * D2) {
+                r.o = i; r.dor = r.dl; r.x += D2; r.lo += D2; r.hi += D2; r.lamL = R(0.0); r.lamR = D2;
             }
         }
         r.s = pole_sums(d, z, N, i, r.dor, r.x, lane);
-        if (fabs(step) <= 4.0 * kEps * fabs(r.x)) break;
+        if (fabs(step) <= R(4.0) * kEps * fabs(r.x)) break;
     }
     return it;
 }
@@ -130,8 +134,8 @@ __device__ __forceinline__ int root_iterate(const double *__restrict__ d, const 
 // a predicted logit, see bdc_mlp.cuh); with it the solver starts there
 // instead of evaluating the interval midpoint, and polishes from the nearer
 // pole if the prediction chose the farther one.
-__device__ __forceinline__ int solve_root(const double *__restrict__ d, const double *__restrict__ z, int N, int i,
-                          int max_iter, double zz, int &org_out, double &tau_out, double &x_out, double vstart) {
+__device__ __forceinline__ int solve_root(const real_t *__restrict__ d, const real_t *__restrict__ z, int N, int i,
+                          int max_iter, real_t zz, int &org_out, real_t &tau_out, real_t &x_out, real_t vstart) {
     const int lane = threadIdx.x & 31;
     if (N == 1) {
         org_out = 0;
@@ -140,54 +144,54 @@ __device__ __forceinline__ int solve_root(const double *__restrict__ d, const do
         return 0;
     }
     const bool last = (i == N - 1);
-    const double dl = d[i];
-    const double du = last ? sqrt(dl * dl + zz) : d[i + 1];
-    const double h = 0.5 * (du - dl);
+    const real_t dl = d[i];
+    const real_t du = last ? sqrt(dl * dl + zz) : d[i + 1];
+    const real_t h = R(0.5) * (du - dl);
     const bool use_mlp = !last && (vstart == vstart);
     RootState r;
     r.dl = dl;
     r.du = du;
     if (use_mlp) {
-        const double D2 = (du - dl) * (du + dl);
-        if (vstart > 0.0) {
-            r.o = i; r.dor = dl; r.lo = 0.0; r.hi = D2; r.lamL = 0.0; r.lamR = D2; r.x = vstart * D2;
+        const real_t D2 = (du - dl) * (du + dl);
+        if (vstart > R(0.0)) {
+            r.o = i; r.dor = dl; r.lo = R(0.0); r.hi = D2; r.lamL = R(0.0); r.lamR = D2; r.x = vstart * D2;
         } else {
-            r.o = i + 1; r.dor = du; r.lo = -D2; r.hi = 0.0; r.lamL = -D2; r.lamR = 0.0; r.x = vstart * D2;
+            r.o = i + 1; r.dor = du; r.lo = -D2; r.hi = R(0.0); r.lamL = -D2; r.lamR = R(0.0); r.x = vstart * D2;
         }
-        if (!(r.x > r.lo && r.x < r.hi)) r.x = 0.5 * (r.lo + r.hi);
+        if (!(r.x > r.lo && r.x < r.hi)) r.x = R(0.5) * (r.lo + r.hi);
         r.s = pole_sums(d, z, N, i, r.dor, r.x, lane);
     } else if (!last) {
         // sign of f at the interval midpoint picks the nearer pole as origin
-        const double xmid = h * (2.0 * dl + h);
+        const real_t xmid = h * (R(2.0) * dl + h);
         r.s = pole_sums(d, z, N, i, dl, xmid, lane);
-        const double fmid = 1.0 + r.s.psi + r.s.phi;
-        if (fmid >= 0.0) {
-            r.o = i; r.dor = dl; r.lo = 0.0; r.hi = xmid;
-            r.lamL = 0.0; r.lamR = (du - dl) * (du + dl);
+        const real_t fmid = R(1.0) + r.s.psi + r.s.phi;
+        if (fmid >= R(0.0)) {
+            r.o = i; r.dor = dl; r.lo = R(0.0); r.hi = xmid;
+            r.lamL = R(0.0); r.lamR = (du - dl) * (du + dl);
             r.x = xmid;
         } else {
-            r.o = i + 1; r.dor = du; r.lo = -h * (2.0 * du - h); r.hi = 0.0;
-            r.lamL = -(du - dl) * (du + dl); r.lamR = 0.0;
+            r.o = i + 1; r.dor = du; r.lo = -h * (R(2.0) * du - h); r.hi = R(0.0);
+            r.lamL = -(du - dl) * (du + dl); r.lamR = R(0.0);
             r.x = r.lo;                    // the same point, measured from d_{i+1}
         }
     } else {
-        r.o = i; r.dor = dl; r.lo = 0.0; r.hi = zz;
-        r.lamL = 0.0; r.lamR = 0.0;
-        r.x = 0.5 * zz;
+        r.o = i; r.dor = dl; r.lo = R(0.0); r.hi = zz;
+        r.lamL = R(0.0); r.lamR = R(0.0);
+        r.x = R(0.5) * zz;
         r.s = pole_sums(d, z, N, i, r.dor, r.x, lane);
     }
     int it = root_iterate(d, z, N, i, last, max_iter, r);
     if (use_mlp && it >= 0) {
         // the origin must be the nearer pole (no cancellation in d_j - w)
-        const double D2 = (du - dl) * (du + dl);
+        const real_t D2 = (du - dl) * (du + dl);
         bool sw = false;
-        if (r.o == i && r.x > 0.5 * D2) {
-            r.o = i + 1; r.dor = du; r.x -= D2; r.lo = -D2; r.hi = 0.0; r.lamL = -D2; r.lamR = 0.0; sw = true;
-        } else if (r.o == i + 1 && r.x < -0.5 * D2) {
-            r.o = i; r.dor = dl; r.x += D2; r.lo = 0.0; r.hi = D2; r.lamL = 0.0; r.lamR = D2; sw = true;
+        if (r.o == i && r.x > R(0.5) * D2) {
+            r.o = i + 1; r.dor = du; r.x -= D2; r.lo = -D2; r.hi = R(0.0); r.lamL = -D2; r.lamR = R(0.0); sw = true;
+        } else if (r.o == i + 1 && r.x < -R(0.5) * D2) {
+            r.o = i; r.dor = dl; r.x += D2; r.lo = R(0.0); r.hi = D2; r.lamL = R(0.0); r.lamR = D2; sw = true;
         }
         if (sw) {
-            if (!(r.x > r.lo && r.x < r.hi)) r.x = 0.5 * (r.lo + r.hi);
+            if (!(r.x > r.lo && r.x < r.hi)) r.x = R(0.5) * (r.lo + r.hi);
             r.s = pole_sums(d, z, N, i, r.dor, r.x, lane);
             const int it2 = root_iterate(d, z, N, i, last, max_iter, r);
             it = (it2 < 0) ? -1 : it + 1 + it2;
@@ -200,6 +204,7 @@ __device__ __forceinline__ int solve_root(const double *__restrict__ d, const do
     return it;
 }
 
+#ifndef BDC_FP32   // root starts: FP64 only
 // far-pole moment sums of root i from the merge's prefix (poles j <= i-9)
 // and suffix (poles j >= i+10) sums
 __device__ __forceinline__ void far_from_scans(const double *__restrict__ pz, long long stride, int N, int i,
@@ -283,6 +288,7 @@ __global__ void __launch_bounds__(128) k_root_start(const NodeDesc *__restrict__
         for (int k = 0; k < kMlpIn; ++k) md.fs[(size_t)(nd.r0 + i) * kMlpIn + k] = f[k];
     }
 }
+#endif  // BDC_FP32
 
 __global__ void __launch_bounds__(256, 2) k_secular(const NodeDesc *__restrict__ nodes,
                                                  const MatDesc *__restrict__ mats,
@@ -295,13 +301,13 @@ __global__ void __launch_bounds__(256, 2) k_secular(const NodeDesc *__restrict__
     const NodeState ns = state[nd.id];
     if (i >= ns.N) return;
     const MatDesc md = mats[nd.mat];
-    const double *d = md.dM + nd.r0, *z = md.zM + nd.r0;
+    const real_t *d = md.dM + nd.r0, *z = md.zM + nd.r0;
     const int N = ns.N;
-    const double zz = ns.rho;                       // sum z^2 (computed by the merge prep)
-    double vstart = __longlong_as_double(0x7ff8000000000000ll);   // NaN: plain start
+    const real_t zz = ns.rho;                       // sum z^2 (computed by the merge prep)
+    real_t vstart = R(NAN);                                    // NaN: plain start
     if (seed_mode != BDC_SEED_PLAIN && i < N - 1) vstart = md.ystart[nd.r0 + i];
     int o;
-    double tau, x;
+    real_t tau, x;
     const int it = solve_root(d, z, N, i, max_iter, zz, o, tau, x, vstart);
     if (lane == 0) {
         md.org[nd.r0 + i] = o;
@@ -309,6 +315,7 @@ __global__ void __launch_bounds__(256, 2) k_secular(const NodeDesc *__restrict__
         md.omega[nd.r0 + i] = d[o] + tau;
         if (it < 0) atomicAdd(md.info, 1);
         atomicAdd(&state[nd.id].iters, (unsigned long long)(it < 0 ? max_iter : it));
+#ifndef BDC_FP32
         if (md.feat != nullptr && i < N - 1 && it >= 0) {
             // harvest (features, y - y_q): the network learns the correction
             const double D2 = (d[i + 1] - d[i]) * (d[i + 1] + d[i]);
@@ -320,9 +327,11 @@ __global__ void __launch_bounds__(256, 2) k_secular(const NodeDesc *__restrict__
                 md.targ[slot] = clamp40(root_logit(o, i, x, D2) - md.yq[nd.r0 + i]);
             }
         }
+#endif
     }
 }
 
+#ifndef BDC_FP32   // standalone step kernels: FP64 only
 __device__ __forceinline__ double warp_sumsq(const double *__restrict__ z, int N, int lane) {
     double zz = 0.0;
     for (int j = lane; j < N; j += 32) zz = fma(z[j], z[j], zz);
@@ -376,27 +385,29 @@ __global__ void __launch_bounds__(256) k_mlp_features_single(int N, const double
     if (lane == 0 && yq_out) yq_out[i] = yq;
 }
 
+#endif  // BDC_FP32
+
 // |z~_i|^2 of Eq. (bdc-zi), 0-based: (w_{N-1}^2 - d_i^2) *
 //   prod_{k<i} (w_k^2 - d_i^2)/(d_k^2 - d_i^2) * prod_{i<=k<N-1} (w_k^2 - d_i^2)/(d_{k+1}^2 - d_i^2)
-__device__ __forceinline__ double lowner_one(const double *__restrict__ d, const double *__restrict__ z,
-                                             const int *__restrict__ org, const double *__restrict__ tau,
+__device__ __forceinline__ real_t lowner_one(const real_t *__restrict__ d, const real_t *__restrict__ z,
+                                             const int *__restrict__ org, const real_t *__restrict__ tau,
                                              int N, int i, int lane) {
-    const double di = d[i];
-    double prod = 1.0;
+    const real_t di = d[i];
+    real_t prod = R(1.0);
     for (int k = lane; k < N - 1; k += 32) {
         const int ok = org[k];
-        const double wmd = (d[ok] - di) + tau[k];        // w_k - d_i
-        const double wpd = d[ok] + tau[k] + di;          // w_k + d_i
+        const real_t wmd = (d[ok] - di) + tau[k];        // w_k - d_i
+        const real_t wpd = d[ok] + tau[k] + di;          // w_k + d_i
         const int kk = (k < i) ? k : k + 1;
-        const double den = (d[kk] - di) * (d[kk] + di);
+        const real_t den = (d[kk] - di) * (d[kk] + di);
         prod *= (wmd * wpd) / den;
     }
     for (int o = 16; o > 0; o >>= 1) prod *= __shfl_down_sync(0xffffffffu, prod, o);
     prod = __shfl_sync(0xffffffffu, prod, 0);
     const int oN = org[N - 1];
-    const double last = ((d[oN] - di) + tau[N - 1]) * (d[oN] + tau[N - 1] + di);
-    const double zt = sqrt(fabs(last * prod));
-    return (z[i] < 0.0) ? -zt : zt;
+    const real_t last = ((d[oN] - di) + tau[N - 1]) * (d[oN] + tau[N - 1] + di);
+    const real_t zt = sqrt(fabs(last * prod));
+    return (z[i] < R(0.0)) ? -zt : zt;
 }
 
 __global__ void __launch_bounds__(256) k_lowner(const NodeDesc *__restrict__ nodes,
@@ -410,10 +421,11 @@ __global__ void __launch_bounds__(256) k_lowner(const NodeDesc *__restrict__ nod
     if (i >= ns.N) return;
     const MatDesc md = mats[nd.mat];
     const int r0 = nd.r0;
-    const double zt = lowner_one(md.dM + r0, md.zM + r0, md.org + r0, md.tau + r0, ns.N, i, lane);
+    const real_t zt = lowner_one(md.dM + r0, md.zM + r0, md.org + r0, md.tau + r0, ns.N, i, lane);
     if (lane == 0) md.zt[r0 + i] = zt;
 }
 
+#ifndef BDC_FP32
 __global__ void __launch_bounds__(256) k_lowner_single(int N, const double *d, const double *z,
                                                        const int *org, const double *tau, double *zt) {
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
@@ -421,42 +433,43 @@ __global__ void __launch_bounds__(256) k_lowner_single(int N, const double *d, c
     const double v = lowner_one(d, z, org, tau, N, i, lane);
     if (lane == 0) zt[i] = v;
 }
+#endif
 
-__device__ __forceinline__ double block_sum256(double v, double *sh) {
+__device__ __forceinline__ real_t block_sum256(real_t v, real_t *sh) {
     v = warp_sum(v);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (lane == 0) sh[w] = v;
     __syncthreads();
-    double r = 0.0;
+    real_t r = R(0.0);
     for (int k = 0; k < (int)(blockDim.x >> 5); ++k) r += sh[k];
     __syncthreads();
     return r;
 }
 
 // column i of U_M and V_M, rows in K order (invK: K position -> M index, -1 = zero row)
-__device__ void vectors_one(const double *__restrict__ d, const double *__restrict__ zt, int N, int i,
-                            int o, double tau, const int *__restrict__ invK, int Ktot,
-                            double *__restrict__ UMcol, double *__restrict__ VMcol, double *sh) {
-    const double dor = d[o];
-    double sv = 0.0, su = 0.0;
+__device__ void vectors_one(const real_t *__restrict__ d, const real_t *__restrict__ zt, int N, int i,
+                            int o, real_t tau, const int *__restrict__ invK, int Ktot,
+                            real_t *__restrict__ UMcol, real_t *__restrict__ VMcol, real_t *sh) {
+    const real_t dor = d[o];
+    real_t sv = R(0.0), su = R(0.0);
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
-        const double dj = d[j];
-        const double v = zt[j] / (((dj - dor) - tau) * (dj + dor + tau));
-        const double u = (j == 0) ? -1.0 : dj * v;
+        const real_t dj = d[j];
+        const real_t v = zt[j] / (((dj - dor) - tau) * (dj + dor + tau));
+        const real_t u = (j == 0) ? -R(1.0) : dj * v;
         sv = fma(v, v, sv);
         su = fma(u, u, su);
     }
     sv = block_sum256(sv, sh);
     su = block_sum256(su, sh);
-    const double iv = 1.0 / sqrt(sv), iu = 1.0 / sqrt(su);
+    const real_t iv = R(1.0) / sqrt(sv), iu = R(1.0) / sqrt(su);
     for (int p = threadIdx.x; p < Ktot; p += blockDim.x) {
         const int j = invK ? invK[p] : p;
-        double uo = 0.0, vo = 0.0;
+        real_t uo = R(0.0), vo = R(0.0);
         if (j >= 0) {
-            const double dj = d[j];
-            const double v = zt[j] / (((dj - dor) - tau) * (dj + dor + tau));
+            const real_t dj = d[j];
+            const real_t v = zt[j] / (((dj - dor) - tau) * (dj + dor + tau));
             vo = v * iv;
-            uo = ((j == 0) ? -1.0 : dj * v) * iu;
+            uo = ((j == 0) ? -R(1.0) : dj * v) * iu;
         }
         UMcol[p] = uo;
         VMcol[p] = vo;
@@ -466,7 +479,7 @@ __device__ void vectors_one(const double *__restrict__ d, const double *__restri
 __global__ void __launch_bounds__(256) k_vectors(const NodeDesc *__restrict__ nodes,
                                                  const MatDesc *__restrict__ mats,
                                                  const NodeState *__restrict__ state, int mmax) {
-    __shared__ double sh[8];
+    __shared__ real_t sh[8];
     const int node = blockIdx.x / mmax, i = blockIdx.x % mmax;
     const NodeDesc nd = nodes[node];
     const NodeState ns = state[nd.id];
@@ -493,35 +506,36 @@ __global__ void __launch_bounds__(256) k_vectors_warp(const NodeDesc *__restrict
     const MatDesc md = mats[nd.mat];
     const int r0 = nd.r0, N = ns.N, Ktot = ns.Ktot;
     const long long wb = (long long)r0 * md.wstride;
-    const double *d = md.dM + r0, *zt = md.zt + r0;
+    const real_t *d = md.dM + r0, *zt = md.zt + r0;
     const int *invK = md.invK + nd.kbase;
-    const double dor = d[md.org[r0 + i]], tau = md.tau[r0 + i];
-    double sv = 0.0, su = 0.0;
+    const real_t dor = d[md.org[r0 + i]], tau = md.tau[r0 + i];
+    real_t sv = R(0.0), su = R(0.0);
     for (int j = lane; j < N; j += 32) {
-        const double dj = d[j];
-        const double v = zt[j] / (((dj - dor) - tau) * (dj + dor + tau));
-        const double u = (j == 0) ? -1.0 : dj * v;
+        const real_t dj = d[j];
+        const real_t v = zt[j] / (((dj - dor) - tau) * (dj + dor + tau));
+        const real_t u = (j == 0) ? -R(1.0) : dj * v;
         sv = fma(v, v, sv);
         su = fma(u, u, su);
     }
     sv = warp_sum(sv);
     su = warp_sum(su);
-    const double iv = 1.0 / sqrt(sv), iu = 1.0 / sqrt(su);
-    double *UMcol = md.UM + wb + (size_t)i * Ktot, *VMcol = md.VM + wb + (size_t)i * Ktot;
+    const real_t iv = R(1.0) / sqrt(sv), iu = R(1.0) / sqrt(su);
+    real_t *UMcol = md.UM + wb + (size_t)i * Ktot, *VMcol = md.VM + wb + (size_t)i * Ktot;
     for (int p = lane; p < Ktot; p += 32) {
         const int j = invK[p];
-        double uo = 0.0, vo = 0.0;
+        real_t uo = R(0.0), vo = R(0.0);
         if (j >= 0) {
-            const double dj = d[j];
-            const double v = zt[j] / (((dj - dor) - tau) * (dj + dor + tau));
+            const real_t dj = d[j];
+            const real_t v = zt[j] / (((dj - dor) - tau) * (dj + dor + tau));
             vo = v * iv;
-            uo = ((j == 0) ? -1.0 : dj * v) * iu;
+            uo = ((j == 0) ? -R(1.0) : dj * v) * iu;
         }
         UMcol[p] = uo;
         VMcol[p] = vo;
     }
 }
 
+#ifndef BDC_FP32
 __global__ void __launch_bounds__(256) k_mvectors_single(int N, const double *d, const double *zt,
                                                          const int *org, const double *tau, double *UM,
                                                          int ldum, double *VM, int ldvm) {
@@ -529,6 +543,7 @@ __global__ void __launch_bounds__(256) k_mvectors_single(int N, const double *d,
     const int i = blockIdx.x;
     vectors_one(d, zt, N, i, org[i], tau[i], nullptr, N, UM + (size_t)i * ldum, VM + (size_t)i * ldvm, sh);
 }
+#endif
 
 }  // namespace
 
@@ -537,6 +552,10 @@ cudaError_t launch_secular(const NodeDesc *nodes, int nnodes, const MatDesc *mat
                            cudaStream_t st) {
     if (nnodes <= 0) return cudaSuccess;
     const long long roots = (long long)nnodes * mmax;
+#ifdef BDC_FP32
+    if (seed_mode != BDC_SEED_PLAIN || harvest) return cudaErrorInvalidValue;   // starts: FP64 only
+    (void)mlp;
+#else
     if (seed_mode != BDC_SEED_PLAIN || harvest) {
         const size_t smem = (seed_mode == BDC_SEED_MLP) ? sizeof(float) * kMlpParams : 0;
         if (smem > 48 * 1024) return cudaErrorInvalidValue;
@@ -545,6 +564,7 @@ cudaError_t launch_secular(const NodeDesc *nodes, int nnodes, const MatDesc *mat
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
+#endif
     k_secular<<<(unsigned)((roots + 7) / 8), 256, 0, st>>>(nodes, mats, state, mmax, max_iter, nnodes,
                                                            seed_mode);
     cudaError_t e = cudaGetLastError();
@@ -565,6 +585,7 @@ cudaError_t launch_vectors(const NodeDesc *nodes, int nnodes, const MatDesc *mat
     return cudaGetLastError();
 }
 
+#ifndef BDC_FP32   // standalone step entry points: FP64 only
 cudaError_t launch_secular_single(int N, const double *d, const double *z, int *org, double *tau,
                                   double *omega, int max_iter, int *info, int seed_mode, const float *mlp,
                                   int *iters, cudaStream_t st) {
@@ -595,5 +616,6 @@ cudaError_t launch_mvectors_single(int N, const double *d, const double *zt, con
     k_mvectors_single<<<N, 256, 0, st>>>(N, d, zt, org, tau, UM, ldum, VM, ldvm);
     return cudaGetLastError();
 }
+#endif  // BDC_FP32
 
-}  // namespace bdc
+}  // namespace BDC_NS

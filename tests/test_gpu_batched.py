@@ -153,3 +153,74 @@ def test_autotune_picks_a_candidate_and_caches(bdc):
     S, U, VT = plan.result(5)
     _check(*mats[5], S, U, VT)
     plan.close()
+
+
+# ---------------------------------------------------------------- FP32
+def _check32(d, e, S, U, VT, tol_scale=1e-5):
+    """FP32 bar: 1e-5 n on sigma, residual and orthogonality, measured in FP64
+    against the oracle of the FP32-rounded input."""
+    d = d.astype(np.float32).astype(np.float64)
+    e = e.astype(np.float32).astype(np.float64)
+    n = len(d)
+    tol = tol_scale * n
+    s = S.double().cpu().numpy()
+    assert np.all(np.diff(s) <= 0) and np.all(s >= 0)
+    assert check.sigma_rel_err(s, oracle.sigma_only(d, e)) <= tol
+    assert oracle.residual(d, e, s, U.double().cpu().numpy(), VT.double().cpu().numpy()) <= tol
+    assert _orth(U.double()) <= tol and _orth(VT.double().t()) <= tol
+
+
+def test_fp32_batch_matches_oracle(bdc):
+    mats = inputs.batch(64, seed=3, lo=32, hi=300)
+    ns, D, E = _flat(mats)
+    plan = bdc.BatchPlan(D.float(), E.float(), ns, dtype=torch.float32)
+    plan.launch()
+    torch.cuda.synchronize()
+    assert int(plan.info.abs().max()) == 0
+    for b, (d, e) in enumerate(mats):
+        S, U, VT = plan.result(b)
+        assert S.dtype == torch.float32
+        _check32(d, e, S, U, VT)
+    plan.close()
+
+
+@pytest.mark.parametrize("kind", ["graded", "clustered", "ones"])
+def test_fp32_other_inputs(bdc, kind):
+    mats = [inputs.make(kind, n, 11 + n) for n in (33, 200, 513)]
+    ns, D, E = _flat(mats)
+    plan = bdc.BatchPlan(D.float(), E.float(), ns, dtype=torch.float32)
+    plan.launch()
+    torch.cuda.synchronize()
+    assert int(plan.info.abs().max()) == 0
+    for b, (d, e) in enumerate(mats):
+        _check32(d, e, *plan.result(b))
+    plan.close()
+
+
+def test_fp32_config4_2048_matrices(bdc):
+    mats = inputs.batch(2048, seed=3)
+    ns, D, E = _flat(mats)
+    plan = bdc.BatchPlan(D.float(), E.float(), ns, dtype=torch.float32)
+    plan.launch()
+    plan.launch()
+    torch.cuda.synchronize()
+    assert int(plan.info.abs().max()) == 0
+    order = np.argsort(ns)
+    pick = sorted(set(order[np.linspace(0, len(ns) - 1, 16).astype(int)].tolist() + [int(order[-1])]))
+    for b in pick:
+        _check32(*mats[b], *plan.result(b))
+    plan.close()
+
+
+def test_fp32_rejects_fp64_only_options(bdc):
+    ns = np.array([40, 50], dtype=np.int32)
+    D = torch.ones(90, device="cuda")
+    with pytest.raises(bdc.BDCError):
+        bdc.BatchPlan(D, D, ns, prec="exact", dtype=torch.float32)
+
+
+def test_fp32_autotune(bdc):
+    ns = inputs.batch_sizes(256, seed=4)
+    leaf, mm, ms = bdc.autotune(ns, reps=2, dtype=torch.float32)
+    assert leaf in (8, 12, 16, 24, 32) and ms > 0
+    assert bdc.autotune(ns, reps=2, dtype=torch.float32) == (leaf, mm, ms)
