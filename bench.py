@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--leaf", type=int, default=16)
     ap.add_argument("--slices", type=int, default=0, help="0 = automatic (6 up to n=8192, 7 above)")
     ap.add_argument("--mixed-min", type=int, default=0, help="smallest merge order using split BF16 (0 = auto)")
+    ap.add_argument("--batched", action="store_true",
+                    help="config 4: 2048 bidiagonals, n log-uniform in [32, 1024], one CUDA-graph launch per batch")
+    ap.add_argument("--dtype", default="fp64", choices=["fp64", "fp32"], help="batched mode working precision")
     ap.add_argument("--start", default="mlp", choices=["plain", "analytic", "mlp"],
                     help="secular root start: interval midpoint, analytic estimate, or analytic + trained MLP")
     ap.add_argument("--no-e2e", action="store_true")
@@ -165,8 +168,127 @@ def run_reference(a, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(a):
+    """Config 4: the whole batch per step, replayed as one CUDA graph."""
+    import torch
+
+    from paper_2508_11467_gb300 import bdc, build, inputs
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    build.build()
+    bdc.lib()
+    count = 2048
+    mats = inputs.batch(count, seed=3)
+    ns = np.array([len(d) for d, _ in mats], dtype=np.int32)
+    off = np.concatenate([[0], np.cumsum(ns)])
+    Dh = np.zeros(int(off[-1]))
+    Eh = np.zeros(int(off[-1]))
+    for b, (d, e) in enumerate(mats):
+        Dh[off[b]:off[b] + len(d)] = d
+        Eh[off[b]:off[b] + len(e)] = e
+    dt = torch.float32 if a.dtype == "fp32" else torch.float64
+    D_pin = torch.from_numpy(Dh).to(dt).pin_memory()
+    E_pin = torch.from_numpy(Eh).to(dt).pin_memory()
+    t0 = time.perf_counter()
+    leaf, mm, tune_ms = bdc.autotune(ns, "fp64", reps=2, dtype=dt)
+    tune_s = time.perf_counter() - t0
+    plan = bdc.BatchPlan(D_pin.to(dev), E_pin.to(dev), ns, leaf=leaf, dtype=dt)
+    st = torch.cuda.current_stream()
+    for _ in range(a.warmup):
+        plan.launch()
+    torch.cuda.synchronize()
+    if int(plan.info.abs().max()) != 0:
+        raise RuntimeError("device status " + str(int(plan.info.abs().max())))
+    clocks = ClockSampler(0)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(st)
+    for _ in range(a.steps):
+        plan.launch()
+    ev1.record(st)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / a.steps
+    # end to end: H2D of every d, e; the graph; D2H of every S, U, V^T
+    esz = 4 if a.dtype == "fp32" else 8
+    S_h = torch.empty_like(plan.S, device="cpu").pin_memory()
+    U_h = torch.empty_like(plan.U, device="cpu").pin_memory()
+    VT_h = torch.empty_like(plan.VT, device="cpu").pin_memory()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    k2 = max(1, min(a.steps, 3))
+    f0.record(st)
+    for _ in range(k2):
+        plan.d.copy_(D_pin, non_blocking=True)
+        plan.e.copy_(E_pin, non_blocking=True)
+        plan.launch()
+        S_h.copy_(plan.S, non_blocking=True)
+        U_h.copy_(plan.U, non_blocking=True)
+        VT_h.copy_(plan.VT, non_blocking=True)
+    f1.record(st)
+    torch.cuda.synchronize()
+    ems = f0.elapsed_time(f1) / k2
+    # accuracy of a spread of matrices (torch/cuBLAS checkers in FP64)
+    order = np.argsort(ns)
+    worst = {"residual": 0.0, "orth": 0.0}
+    for b in order[np.linspace(0, count - 1, 12).astype(int)]:
+        S, U, VT = plan.result(int(b))
+        d = torch.from_numpy(mats[b][0]).to(dev).to(dt).double()
+        e = torch.from_numpy(mats[b][1]).to(dev).to(dt).double()
+        U, VT, S = U.double(), VT.double(), S.double()
+        V = VT.t()
+        BV = d[:, None] * V
+        BV[:-1] += e[:, None] * V[1:]
+        res = float(torch.linalg.norm(BV - U * S[None, :]) / torch.sqrt((d * d).sum() + (e * e).sum()))
+        G = U.t() @ U
+        G.diagonal().sub_(1.0)
+        worst["residual"] = max(worst["residual"], res)
+        worst["orth"] = max(worst["orth"], float(torch.linalg.norm(G)))
+    # the FP64 QR oracle on host cores, per matrix, on a bounded sample
+    cpu = None
+    if not a.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        sample = [int(b) for b in order[np.linspace(0, count - 1, 24).astype(int)]]
+        t0 = time.perf_counter()
+        for b in sample:
+            oracle.bdsqr(*mats[b])
+        t = time.perf_counter() - t0
+        n3 = float(np.sum(ns.astype(np.float64) ** 3))
+        s3 = float(np.sum(ns[sample].astype(np.float64) ** 3))
+        cpu_s = t * n3 / s3
+        cpu = {"value": count / cpu_s, "unit": "matrices/s", "cores": 1, "kind": "oracle",
+               "sample": f"Golub-Kahan QR with U,V on 24 of the 2048 matrices (spread over the sizes) = {t:.2f} s "
+                         f"on 1 host core, scaled by sum n^3 to the batch"}
+    flops = float(np.sum((8.0 / 3.0) * ns.astype(np.float64) ** 3))
+    line = {
+        "metric": "2048 bidiagonals (n log-uniform in [32,1024]) SVD (sigma+U,V) throughput",
+        "value": count / (ms * 1e-3), "unit": "matrices/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if a.dtype == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": "2048 upper bidiagonals, n = floor(exp(U(ln 32, ln 1024))) seed 3, d,e~U(0.5,1.5)",
+                   "leaf": leaf, "autotune_s": tune_s, "launch": "one CUDA graph per batch (bdc_plan_launch)",
+                   "l2": "U, V and workspace of the batch (> 5 GB) exceed L2"},
+        "gflops_paper_model": flops / (ms * 1e-3) / 1e9,
+        "accuracy": worst,
+        "roofline": None,
+        "gpu_launches": None,
+        "e2e": {"value": count / (ems * 1e-3), "unit": "matrices/s", "h2d_bytes_per_step": int(2 * esz * off[-1]),
+                "d2h_bytes_per_step": int(esz * (off[-1] + 2 * plan.U.numel()))},
+        "cpu_baseline": cpu,
+        "clocks": clk,
+    }
+    plan.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
+    if a.batched and a.impl != "reference":
+        run_batched(a)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

@@ -74,7 +74,7 @@ typedef struct {
     int checked;       /* reserved, must be 0                              */
     const float *mlp;  /* device pointer to MLP weights when seed = MLP    */
     int mixed_min;     /* split-BF16 products only for merges of order >= mixed_min,
-                          FP64 products below (0 = automatic: 256)          */
+                          FP64 products below (0 = automatic: 128)          */
     int reserved;      /* must be 0                                        */
 } bdc_opts;
 

@@ -27,7 +27,8 @@ namespace BDC_NS {
 // another in the sliced operand arrays, rows bounded by Mmax[p], columns by Nmax[p]
 cudaError_t launch_gemm_mixed(const GemmProb *probs, int nprobs, const int *Mmax, const int *Nmax, int kmax,
                               int prec, int slices, void *scratch, size_t scratch_bytes, cudaStream_t st);
-size_t gemm_mixed_scratch(long long rows_total, long long cols_total, int kmax, int prec, int slices);
+size_t gemm_mixed_scratch(long long rows_total, long long cols_total, int kmax, int prec, int slices,
+                          long long tiles);
 #endif
 
 namespace {
@@ -169,10 +170,16 @@ Plan make_plan(int nmat, const int *ns, const bdc_opts &o) {
     if (o.prec != BDC_FP64) {
         size_t mb = 0;
         for (size_t h = 0; h < p.heights.size(); ++h) {
-            long long rows = 0, cols = 0;
-            for (auto &nd : p.heights[h]) { rows += 2 * (nd.m + 1); cols += 4 * nd.m; }
+            long long rows = 0, cols = 0, tiles = 0;
+            for (auto &nd : p.heights[h]) {
+                rows += 2 * (nd.m + 1);
+                cols += 4 * nd.m;
+                // the four products' 128 x 128 tiles (rows as in run_plan, nd.m columns each)
+                const int Mx[4] = {nd.nl + 1, nd.m - nd.nl - 1, nd.nl + 1, nd.m + nd.sqre - nd.nl - 1};
+                for (int j = 0; j < 4; ++j) tiles += (long long)((Mx[j] + 127) / 128) * ((nd.m + 127) / 128);
+            }
             mb = std::max(mb, gemm_mixed_scratch(rows, cols, p.hmmax[h] + 9, o.prec,
-                                                 o.slices > 0 ? o.slices : 6));
+                                                 o.slices > 0 ? o.slices : 6, tiles));
         }
         p.off_mixed = off;
         p.mixed_bytes = mb;
@@ -544,7 +551,7 @@ bdc_opts resolve(const bdc_opts *o, int nmax) {
     if (r.leaf <= 0) r.leaf = kDefaultLeaf;
     if (r.max_iter <= 0) r.max_iter = kDefaultMaxIter;
     if (r.slices <= 0) r.slices = auto_slices(nmax);
-    if (r.mixed_min <= 0) r.mixed_min = 256;   // measured crossover (n = 16384)
+    if (r.mixed_min <= 0) r.mixed_min = 128;   // measured crossover (n = 16384, persistent product kernel)
     return r;
 }
 
@@ -989,7 +996,8 @@ int bdc_deflate(int m, const double *d, const double *z, double tol, int *keep, 
 size_t bdc_gemm_workspace(int M, int N, int K, int prec, int slices) {
     if (M < 0 || N < 0 || K < 0) return 0;
     size_t b = align256(sizeof(GemmProb)) + 256;
-    if (prec != BDC_FP64) b += gemm_mixed_scratch(M, N, K, prec, slices > 0 ? slices : 6);
+    if (prec != BDC_FP64)
+        b += gemm_mixed_scratch(M, N, K, prec, slices > 0 ? slices : 6, (long long)((M + 127) / 128) * ((N + 127) / 128));
     return b;
 }
 

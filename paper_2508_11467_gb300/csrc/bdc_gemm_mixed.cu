@@ -69,6 +69,9 @@ __device__ __forceinline__ unsigned long long gtimer() {
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
 }
+__device__ __forceinline__ void mbar_inval(uint64_t *bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
@@ -324,7 +327,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
                                                      const GemmProb *__restrict__ probs,
                                                      const MixProb *__restrict__ mix, int nprobs,
                                                      const int *__restrict__ Ea, const int *__restrict__ Fb,
-                                                     int *__restrict__ err) {
+                                                     int *__restrict__ err, const int2 *__restrict__ tiles,
+                                                     const int *__restrict__ ntiles) {
     constexpr int TILE = TM * TK * 2;                 // one 128 x 32 BF16 slice tile (A or B)
     constexpr int STAGE_BYTES = 2 * S * TILE;
     // kind::f16 instruction descriptor: D = F32, A = B = BF16, K-major,
@@ -340,30 +344,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
     uint32_t *tmem_slot = (uint32_t *)(accempty + 2);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
 
-    int lo = 0, hi = nprobs - 1;
-    while (lo < hi) { int mid = (lo + hi + 1) >> 1; if (mix[mid].tile0 <= (int)blockIdx.x) lo = mid; else hi = mid - 1; }
-    const int p = lo;
-    const GemmProb pr = probs[p];
-    const MixProb mx = mix[p];
-    // grouped rasterization: bands of 8 row blocks walk the column blocks
-    // together, so the CTAs resident at one time share A and B tiles in L2
-    const int t = blockIdx.x - mx.tile0;
-    const int tilesM = (mx.Mmax + TM - 1) / TM;
-    constexpr int G = 8;
-    const int band = t / (G * mx.tilesN), in_band = t % (G * mx.tilesN);
-    const int bm0 = band * G, bsz = min(G, tilesM - bm0);
-    const int m0 = (bm0 + in_band % bsz) * TM, n0 = (in_band / bsz) * TNX;
-    if (m0 >= pr.M || n0 >= pr.N || pr.K <= 0) return;
-    const int nk = (pr.K + TK - 1) / TK;
-
+    (void)nprobs;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < NSTAGE; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
-        for (int i = 0; i < 2; ++i) { mbar_init(&accfull[i], 1); mbar_init(&accempty[i], 32 * EPI_WARPS); }
-        *abort_flag = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    }
+    // persistent: the CTA walks the device-built list of non-empty tiles
+    // (sizes after deflation), so no CTA is launched for an empty tile
+    const int count = *ntiles;
+    if ((int)blockIdx.x >= count) return;
+    if (threadIdx.x == 0) *abort_flag = 0;
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -372,6 +359,22 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
     __syncthreads();
     fence_after();
     const uint32_t tmem = *tmem_slot;
+
+    for (int ti = blockIdx.x; ti < count; ti += gridDim.x) {
+    const int2 tc = tiles[ti];
+    const int p = tc.x;
+    const GemmProb pr = probs[p];
+    const MixProb mx = mix[p];
+    const int m0 = (tc.y >> 16) * TM, n0 = (tc.y & 0xffff) * TNX;
+    const int nk = (pr.K + TK - 1) / TK;
+    // fresh barriers for every tile (the previous tile's are drained and invalidated)
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < NSTAGE; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
+        for (int i = 0; i < 2; ++i) { mbar_init(&accfull[i], 1); mbar_init(&accempty[i], 32 * EPI_WARPS); }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
 
     if (warp == 0) {
         // ------------------------------------------------ TMA producer
@@ -614,10 +617,52 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
         }
         fence_before();
     }
+    // tile end: the MMA's last commits to the stage barriers arrive
+    // asynchronously; wait for them before the barriers are reused
+    if (warp == 1 && lane == 0 && !*abort_flag) {
+        for (int b = 0; b < NSTAGE; ++b) {
+            const int nb = (nk + NSTAGE - 1 - b) / NSTAGE;   // stages s < nk with s % NSTAGE == b
+            if (nb > 0) mbar_wait(&empty[b], (uint32_t)((nb - 1) & 1), err, abort_flag);
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (*abort_flag) break;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < NSTAGE; ++i) { mbar_inval(&full[i]); mbar_inval(&empty[i]); }
+        for (int i = 0; i < 2; ++i) { mbar_inval(&accfull[i]); mbar_inval(&accempty[i]); }
+    }
+    __syncthreads();
+    fence_after();
+    }   // tiles
     __syncthreads();
     if (warp == 1) {
         fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+    }
+}
+
+// list of the non-empty 128 x 128 tiles of every product (one CTA per
+// product, sizes as deflated on the device); bands of 8 row blocks walk the
+// column blocks together so that neighbouring tiles share operands in L2
+__global__ void k_tile_list(const GemmProb *__restrict__ probs, const MixProb *__restrict__ mix,
+                            int2 *__restrict__ tiles, int *__restrict__ ntiles) {
+    const int p = blockIdx.x;
+    const GemmProb pr = probs[p];
+    const MixProb mx = mix[p];
+    const int M = min(pr.M, mx.Mmax), N = min(pr.N, mx.Nmax);
+    if (M <= 0 || N <= 0 || pr.K <= 0) return;
+    const int tilesM = (M + TM - 1) / TM, tilesN = (N + TNX - 1) / TNX;
+    const int cnt = tilesM * tilesN;
+    __shared__ int base;
+    if (threadIdx.x == 0) base = atomicAdd(ntiles, cnt);
+    __syncthreads();
+    constexpr int G = 8;
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+        const int band = t / (G * tilesN), in_band = t % (G * tilesN);
+        const int bm0 = band * G, bsz = min(G, tilesM - bm0);
+        const int mb = bm0 + in_band % bsz, nb = in_band / bsz;
+        tiles[base + t] = make_int2(p, (mb << 16) | nb);
     }
 }
 
@@ -656,22 +701,34 @@ bool make_map(CUtensorMap *m, void *base, int rows, int Kld, int S, int box_rows
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t offA, offB, offE, offF, offErr, offMix, offRb, offCb, total;
+    size_t offA, offB, offE, offF, offErr, offMix, offRb, offCb, offTiles, total;
 };
 
-Layout layout(long long rowsA, long long colsB, int Kld, int S, int nprobs) {
+// tiles: capacity of the non-empty tile list (the no-deflation bound)
+Layout layout(long long rowsA, long long colsB, int Kld, int S, int nprobs, long long tiles) {
     Layout L{};
     size_t o = 0;
     L.offA = o; o += align256((size_t)S * rowsA * Kld * 2);
     L.offB = o; o += align256((size_t)S * colsB * Kld * 2);
     L.offE = o; o += align256(sizeof(int) * (size_t)rowsA);
     L.offF = o; o += align256(sizeof(int) * (size_t)colsB);
-    L.offErr = o; o += 256;
+    L.offErr = o; o += 256;                       // error word, tile count at +16
     L.offMix = o; o += align256(sizeof(MixProb) * (size_t)nprobs);
     L.offRb = o; o += align256(sizeof(int) * (size_t)nprobs);
     L.offCb = o; o += align256(sizeof(int) * (size_t)nprobs);
+    L.offTiles = o; o += align256(sizeof(int2) * (size_t)tiles);
     L.total = o;
     return L;
+}
+
+int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+    }
+    return n;
 }
 
 template <int S, bool EXACT>
@@ -721,7 +778,9 @@ cudaError_t run_mixed(const GemmProb *probs, int nprobs, const std::vector<MixPr
     hp += align256(sizeof(int) * nprobs);
     std::memcpy(hp, hcb.data(), sizeof(int) * nprobs);
     if (e == cudaSuccess) e = cudaMemcpyAsync(cb, hp, sizeof(int) * nprobs, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), st);
+    int *ntiles = err + 4;
+    int2 *tlist = (int2 *)(scratch + L.offTiles);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, 32, st);   // error word and tile count
     if (e != cudaSuccess) return e;
 
     k_slice_a<S, EXACT><<<rbt, 256, 0, st>>>(probs, dmix, nprobs, rbt, rb, As, E, rowsA, Kld);
@@ -746,23 +805,29 @@ cudaError_t run_mixed(const GemmProb *probs, int nprobs, const std::vector<MixPr
     });
     if (attr_err != cudaSuccess) return attr_err;
     if (tiles <= 0) return cudaSuccess;
+    k_tile_list<<<nprobs, 128, 0, st>>>(probs, dmix, tlist, ntiles);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int grid = tiles < sm_count() ? tiles : sm_count();   // persistent: one CTA per SM
     if constexpr (EXACT) {
-        k_mma<S, MODE_E><<<tiles, THREADS, smem, st>>>(ma, mb, probs, dmix, nprobs, E, F, err);
+        k_mma<S, MODE_E><<<grid, THREADS, smem, st>>>(ma, mb, probs, dmix, nprobs, E, F, err, tlist, ntiles);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        if constexpr (S > 4) k_mma<S, MODE_L><<<tiles, THREADS, smem, st>>>(ma, mb, probs, dmix, nprobs, E, F, err);
+        if constexpr (S > 4)
+            k_mma<S, MODE_L><<<grid, THREADS, smem, st>>>(ma, mb, probs, dmix, nprobs, E, F, err, tlist, ntiles);
     } else {
-        k_mma<S, MODE_X3><<<tiles, THREADS, smem, st>>>(ma, mb, probs, dmix, nprobs, E, F, err);
+        k_mma<S, MODE_X3><<<grid, THREADS, smem, st>>>(ma, mb, probs, dmix, nprobs, E, F, err, tlist, ntiles);
     }
     return cudaGetLastError();
 }
 
 }  // namespace
 
-size_t gemm_mixed_scratch(long long rows_total, long long cols_total, int kmax, int prec, int slices) {
+// tiles: the largest sum over one launch's products of ceil(Mmax/128) ceil(Nmax/128)
+size_t gemm_mixed_scratch(long long rows_total, long long cols_total, int kmax, int prec, int slices,
+                          long long tiles) {
     const int S = (prec == BDC_MIXED_BF16X3) ? 2 : slices;
     const int Kld = (kmax + TK - 1) / TK * TK;
     const int nprobs = 1 << 16;
-    return layout(rows_total + TM, cols_total + TN_MAX, Kld, S, nprobs).total + 1024;
+    return layout(rows_total + TM, cols_total + TN_MAX, Kld, S, nprobs, tiles).total + 1024;
 }
 
 // probs: device problem table (M, N, K known on the device); hm: host layout
@@ -772,7 +837,9 @@ cudaError_t launch_gemm_mixed_tab(const GemmProb *probs, int nprobs, const std::
     if (nprobs <= 0) return cudaSuccess;
     const int S = (prec == BDC_MIXED_BF16X3) ? 2 : slices;
     const int Kld = (kmax + TK - 1) / TK * TK;
-    const Layout L = layout(rowsA + TM, colsB + TN_MAX, Kld, S, nprobs);
+    long long tiles = 0;
+    for (const MixProb &m : hm) tiles += (long long)((m.Mmax + TM - 1) / TM) * m.tilesN;
+    const Layout L = layout(rowsA + TM, colsB + TN_MAX, Kld, S, nprobs, tiles);
     if (L.total > scratch_bytes) return cudaErrorInvalidValue;
     char *sc = (char *)scratch;
     const int ra = rowsA + TM, cbn = colsB + TN_MAX;
