@@ -89,6 +89,20 @@ void bdc_opts_default(bdc_opts *o);
 int bdc_svd(int n, const double *d, const double *e, double *U, double *S, double *VT,
             int ldu, int ldvt, bdc_stream_t stream);
 
+/* Singular values only (the paper's Sec. 4.2 solve without vectors): the
+ * same tree, deflation and secular roots, but each node keeps only the first
+ * and last rows of its right vectors (the rows the parent's z is formed
+ * from, Sec. 4.2.1) instead of the U, V panels: no vector formation, no
+ * merge products, O(n) memory.  S[n] descending (device).  The _ex form
+ * takes a caller workspace (bdc_svd_values_workspace bytes) and a device
+ * status word, like bdc_svd_ex; o->prec is ignored (no products), o->seed
+ * and o->mlp select the root starts as in bdc_svd_ex.  bdc_svd_values uses
+ * the defaults and is synchronous. */
+size_t bdc_svd_values_workspace(int n, const bdc_opts *o);
+int bdc_svd_values_ex(int n, const double *d, const double *e, double *S, const bdc_opts *o, void *work,
+                      size_t lwork, int *d_info, bdc_stream_t stream);
+int bdc_svd_values(int n, const double *d, const double *e, double *S, bdc_stream_t stream);
+
 /* Workspace bytes needed by bdc_svd_ex for order n and options o. */
 size_t bdc_svd_workspace(int n, const bdc_opts *o);
 

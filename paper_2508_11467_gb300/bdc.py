@@ -40,6 +40,9 @@ _SIGS = {
     "bdc_svd_workspace": (_SZ, [_I, _VP]),
     "bdc_svd_ex": (_I, [_I, _VP, _VP, _VP, _VP, _VP, _I, _I, _VP, _VP, _SZ, _VP, _VP]),
     "bdc_svd_batched_workspace": (_SZ, [_I, _VP, _VP]),
+    "bdc_svd_values_workspace": (_SZ, [_I, _VP]),
+    "bdc_svd_values_ex": (_I, [_I, _VP, _VP, _VP, _VP, _VP, _SZ, _VP, _VP]),
+    "bdc_svd_values": (_I, [_I, _VP, _VP, _VP, _VP]),
     "bdc_svd_batched": (_I, [_I, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP, _VP]),
     "bdc_secular_solve": (_I, [_I, _VP, _VP, _VP, _VP, _VP, _I, _VP, _VP]),
     "bdc_lowner_z": (_I, [_I, _VP, _VP, _VP, _VP, _VP, _VP]),
@@ -198,6 +201,24 @@ def svd(d, e, *, prec="fp64", leaf=16, max_iter=64, slices=0, seed="plain", mlp=
     if check and code != 0:
         raise BDCError("bdc_svd_ex (device status)", code)
     return S[:n], Ut.t(), VTt.t(), code
+
+
+def svd_values(d, e, *, leaf=16, max_iter=64, seed="plain", mlp=None, stream=None, check=True):
+    """Singular values only (descending), CUDA float64; and the status code."""
+    d = _dev(d)
+    n = d.shape[0]
+    e = _dev(e) if n > 1 else torch.zeros(1, dtype=torch.float64, device=d.device)
+    o = make_opts("fp64", leaf, max_iter, 0, seed, mlp, 0)
+    S = torch.empty(max(n, 1), dtype=torch.float64, device=d.device)
+    info = torch.zeros(1, dtype=torch.int32, device=d.device)
+    lw = int(lib().bdc_svd_values_workspace(n, ctypes.byref(o)))
+    work = torch.empty(lw + 256, dtype=torch.uint8, device=d.device)
+    _check("bdc_svd_values_ex", lib().bdc_svd_values_ex(n, _ptr(d), _ptr(e), _ptr(S), ctypes.byref(o), _ptr(work),
+                                                         work.numel(), _ptr(info), _stream(stream)))
+    code = int(info.item())
+    if check and code != 0:
+        raise BDCError("bdc_svd_values_ex (device status)", code)
+    return S[:n], code
 
 
 def svd_sync(d, e, stream=None):

@@ -73,6 +73,7 @@ int note(cudaError_t e) {
 
 struct Plan {
     int nmat = 0;
+    int vals = 0;                          // singular values only (no U, V panels)
     int leaf = kDefaultLeaf;
     std::vector<int> n;                    // per matrix
     std::vector<NodeDesc> leaves;
@@ -91,22 +92,30 @@ struct Plan {
     size_t total = 0;
 };
 
-size_t per_matrix_bytes(int n) {
+size_t per_matrix_bytes(int n, int vals = 0) {
     const size_t N = (size_t)n;
     size_t b = 0;
     b += align256(sizeof(real_t) * 2 * N);            // dsc, esc
-    b += align256(sizeof(real_t) * 4 * N * N);        // U, V (two copies each)
+    if (vals) {
+        b += align256(sizeof(real_t) * 4 * (N + 1));  // vf, vl (two copies each)
+        b += align256(sizeof(real_t) * 8 * N + 64);    // FK, LK (K-indexed, like invK)
+    } else {
+        b += align256(sizeof(real_t) * 4 * N * N);    // U, V (two copies each)
+    }
     b += align256(sizeof(real_t) * 20 * N + 64);      // D ds zs rc rs dM zM zt tau omega dval scale pz(6n) ystart yq
     b += align256(sizeof(float) * 11 * N);            // fs (root features)
     b += align256(sizeof(int) * (13 * N + 128));      // Q src role org kposM dsrc dest slist sidx invK(4n) info
-    const size_t big = (N + 1) * (N + 16) + 64;
-    b += 4 * align256(sizeof(real_t) * big);          // Wt Qt UM VM
+    if (!vals) {
+        const size_t big = (N + 1) * (N + 16) + 64;
+        b += 4 * align256(sizeof(real_t) * big);      // Wt Qt UM VM
+    }
     return b;
 }
 
-Plan make_plan(int nmat, const int *ns, const bdc_opts &o) {
+Plan make_plan(int nmat, const int *ns, const bdc_opts &o, int vals = 0) {
     Plan p;
     p.nmat = nmat;
+    p.vals = vals;
     p.leaf = o.leaf > 0 ? o.leaf : kDefaultLeaf;
     if (p.leaf < 4) p.leaf = 4;
     p.n.assign(ns, ns + nmat);
@@ -164,10 +173,10 @@ Plan make_plan(int nmat, const int *ns, const bdc_opts &o) {
     p.off_probs = off; off += align256(sizeof(GemmProb) * std::max(p.maxprobs, 1));
     for (int mi = 0; mi < nmat; ++mi) {
         p.off_mat_data.push_back(off);
-        off += per_matrix_bytes(std::max(ns[mi], 1));
+        off += per_matrix_bytes(std::max(ns[mi], 1), vals);
     }
 #ifndef BDC_FP32
-    if (o.prec != BDC_FP64) {
+    if (o.prec != BDC_FP64 && !vals) {
         size_t mb = 0;
         for (size_t h = 0; h < p.heights.size(); ++h) {
             long long rows = 0, cols = 0, tiles = 0;
@@ -191,17 +200,25 @@ Plan make_plan(int nmat, const int *ns, const bdc_opts &o) {
 }
 
 // fill the matrix descriptor of matrix mi from the carved workspace
-MatDesc carve(char *base, size_t off, int n) {
+MatDesc carve(char *base, size_t off, int n, int vals = 0) {
     MatDesc md{};
     const size_t N = (size_t)std::max(n, 1);
     char *p = base + off;
     auto take = [&](size_t bytes) { char *r = p; p += align256(bytes); return r; };
     md.n = n;
+    md.vals = vals;
     md.wstride = (long long)N + 16;
     real_t *de = (real_t *)take(sizeof(real_t) * 2 * N);
     md.dsc = de; md.esc = de + N;
-    real_t *uv = (real_t *)take(sizeof(real_t) * 4 * N * N);
-    md.U[0] = uv; md.V[0] = uv + N * N; md.U[1] = uv + 2 * N * N; md.V[1] = uv + 3 * N * N;
+    if (vals) {
+        real_t *rows = (real_t *)take(sizeof(real_t) * 4 * (N + 1));
+        md.vf[0] = rows; md.vl[0] = rows + (N + 1); md.vf[1] = rows + 2 * (N + 1); md.vl[1] = rows + 3 * (N + 1);
+        real_t *fk = (real_t *)take(sizeof(real_t) * 8 * N + 64);
+        md.FK = fk; md.LK = fk + 4 * N;
+    } else {
+        real_t *uv = (real_t *)take(sizeof(real_t) * 4 * N * N);
+        md.U[0] = uv; md.V[0] = uv + N * N; md.U[1] = uv + 2 * N * N; md.V[1] = uv + 3 * N * N;
+    }
     real_t *dd = (real_t *)take(sizeof(real_t) * 20 * N + 64);
     md.D = dd; md.ds = dd + N; md.zs = dd + 2 * N; md.rc = dd + 3 * N; md.rs = dd + 4 * N;
     md.dM = dd + 5 * N; md.zM = dd + 6 * N; md.zt = dd + 7 * N; md.tau = dd + 8 * N;
@@ -213,11 +230,13 @@ MatDesc carve(char *base, size_t off, int n) {
     md.dsrc = ii + 5 * N; md.dest = ii + 6 * N; md.slist = ii + 7 * N; md.sidx = ii + 8 * N;
     md.invK = ii + 9 * N;                 // K-indexed: r0 + 8 * (index within height) + K
     md.info = ii + 13 * N + 64;
-    const size_t big = (N + 1) * (N + 16) + 64;
-    md.Wt = (real_t *)take(sizeof(real_t) * big);
-    md.Qt = (real_t *)take(sizeof(real_t) * big);
-    md.UM = (real_t *)take(sizeof(real_t) * big);
-    md.VM = (real_t *)take(sizeof(real_t) * big);
+    if (!vals) {
+        const size_t big = (N + 1) * (N + 16) + 64;
+        md.Wt = (real_t *)take(sizeof(real_t) * big);
+        md.Qt = (real_t *)take(sizeof(real_t) * big);
+        md.UM = (real_t *)take(sizeof(real_t) * big);
+        md.VM = (real_t *)take(sizeof(real_t) * big);
+    }
     return md;
 }
 
@@ -263,6 +282,13 @@ __global__ void k_scale(const MatDesc *__restrict__ mats) {
 __global__ void k_info(const MatDesc *__restrict__ mats, int nmat, int *__restrict__ out) {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m < nmat) out[m] = *mats[m].info;
+}
+
+// values only: S descending and unscaled
+__global__ void k_final_values(const MatDesc *__restrict__ mats) {
+    const MatDesc md = mats[blockIdx.y];
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < md.n) md.So[c] = md.D[md.Q[md.n - 1 - c]] * md.scale[0];
 }
 
 __global__ void k_final(const MatDesc *__restrict__ mats, int tiles_per_side) {
@@ -335,6 +361,7 @@ struct ProfCall {
     std::vector<NodeDesc> merges;
     int pairs;
     int mixed_min;   // merges of order >= mixed_min ran the split products
+    int vals;        // singular values only: no vectors, no products
 };
 struct Profiler {
     bool on = false;
@@ -413,7 +440,7 @@ int run_plan(const Plan &p, const bdc_opts &o, char *work, std::vector<MatDesc> 
              cudaStream_t st) {
     // per-matrix data pointers
     for (int mi = 0; mi < p.nmat; ++mi) {
-        MatDesc c = carve(work, p.off_mat_data[mi], mats[mi].n);
+        MatDesc c = carve(work, p.off_mat_data[mi], mats[mi].n, p.vals);
         c.d_in = mats[mi].d_in; c.e_in = mats[mi].e_in;
         c.Uo = mats[mi].Uo; c.So = mats[mi].So; c.VTo = mats[mi].VTo;
         c.ldu = mats[mi].ldu; c.ldvt = mats[mi].ldvt;
@@ -447,7 +474,7 @@ int run_plan(const Plan &p, const bdc_opts &o, char *work, std::vector<MatDesc> 
     const int pairs = (o.prec == BDC_MIXED_EXACT) ? (o.slices * (o.slices + 1)) / 2
                       : (o.prec == BDC_MIXED_BF16X3) ? 3 : 1;
     if (g_prof.on) {
-        ProfCall pc{dstate, p.nnodes, {}, pairs, o.prec == BDC_FP64 ? (1 << 30) : o.mixed_min};
+        ProfCall pc{dstate, p.nnodes, {}, pairs, o.prec == BDC_FP64 ? (1 << 30) : o.mixed_min, p.vals};
         for (auto &h : p.heights) pc.merges.insert(pc.merges.end(), h.begin(), h.end());
         g_prof.calls.push_back(std::move(pc));
     }
@@ -461,7 +488,10 @@ int run_plan(const Plan &p, const bdc_opts &o, char *work, std::vector<MatDesc> 
             StageScope sc(st, BDC_STAGE_PREP, 1, 0.0);
             if ((e = launch_merge_prep(dn, nn, dmats, dstate, dprobs, mm, scans, st)) != cudaSuccess) return note(e);
         }
-        {   // reads the children's U, V halves (8 m^2 B), writes W~ and Q~ (16 m^2 B)
+        if (p.vals) {   // values only: two rows of V instead of the panels
+            StageScope sc(st, BDC_STAGE_GATHER, 1, 0.0);
+            if ((e = launch_gather_rows(dn, nn, dmats, dstate, mm, st)) != cudaSuccess) return note(e);
+        } else {   // reads the children's U, V halves (8 m^2 B), writes W~ and Q~ (16 m^2 B)
             StageScope sc(st, BDC_STAGE_GATHER, 1, 24.0 * m2);
             if ((e = launch_merge_gather(dn, nn, dmats, dstate, mm, st)) != cudaSuccess) return note(e);
         }
@@ -470,11 +500,14 @@ int run_plan(const Plan &p, const bdc_opts &o, char *work, std::vector<MatDesc> 
             if ((e = launch_secular(dn, nn, dmats, dstate, mm, max_iter, o.seed, o.mlp, harvest, st)) != cudaSuccess)
                 return note(e);
         }
-        {   // writes U_M and V_M: 16 N Ktot B (added from the node states)
+        if (p.vals) {   // the survivors' first/last rows of V; no vectors, no products
+            StageScope sc(st, BDC_STAGE_VECTORS, 1, 0.0);
+            if ((e = launch_rows_update(dn, nn, dmats, dstate, mm, st)) != cudaSuccess) return note(e);
+        } else {   // writes U_M and V_M: 16 N Ktot B (added from the node states)
             StageScope sc(st, BDC_STAGE_VECTORS, 1, 0.0);
             if ((e = launch_vectors(dn, nn, dmats, dstate, mm, st)) != cudaSuccess) return note(e);
         }
-        {   // 2 M N K per product as deflated, x slice pairs (added from the node states)
+        if (!p.vals) {   // 2 M N K per product as deflated, x slice pairs (added from the node states)
             // FP64: one launch; split BF16: two slicing kernels + the exact-group
             // and (for more than 4 slices) the low-group product kernels
             // small merges use the FP64 products: the split path's fixed costs
@@ -507,7 +540,14 @@ int run_plan(const Plan &p, const bdc_opts &o, char *work, std::vector<MatDesc> 
             if ((e = launch_merge_finish(dn, nn, dmats, dstate, mm, st)) != cudaSuccess) return note(e);
         }
     }
-    if (p.nmat > 0) {
+    if (p.nmat > 0 && p.vals) {
+        StageScope sc(st, BDC_STAGE_FINAL, (p.nmat + 65534) / 65535, 0.0);
+        for (int m0 = 0; m0 < p.nmat; m0 += 65535) {
+            const int nm = std::min(65535, p.nmat - m0);
+            k_final_values<<<dim3((unsigned)(p.nmax + 255) / 256, nm), 256, 0, st>>>(dmats + m0);
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) return note(e);
+    } else if (p.nmat > 0) {
         // reads U, V (16 n^2 B), writes U, V^T (16 n^2 B)
         StageScope sc(st, BDC_STAGE_FINAL, (p.nmat + 65534) / 65535, 32.0 * nsq);
         const int tps = (p.nmax + 31) / 32;
@@ -655,6 +695,57 @@ int bdc_svd(int n, const double *d, const double *e, double *U, double *S, doubl
     if (rc == 0) {
         if (cudaMemcpyAsync(&hinfo, dinfo, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = BDC_ERR_CUDA;
     }
+    cudaFreeAsync(work, st);
+    if (int r = note(cudaStreamSynchronize(st))) return r;
+    return rc != 0 ? rc : hinfo;
+}
+
+size_t bdc_svd_values_workspace(int n, const bdc_opts *o) {
+    if (n < 0) return 0;
+    const bdc_opts r = resolve(o, n);
+    const int nn = n;
+    return make_plan(1, &nn, r, 1).total;
+}
+
+int bdc_svd_values_ex(int n, const double *d, const double *e, double *S, const bdc_opts *o, void *work,
+                      size_t lwork, int *d_info, bdc_stream_t stream) {
+    if (n < 0) return -1;
+    if (n > 0 && !d) return -2;
+    if (n > 1 && !e) return -3;
+    if (n > 0 && !S) return -4;
+    bdc_opts r = resolve(o, n);
+    r.prec = BDC_FP64;   // no products
+    if (check_opts(r)) return -5;
+    if (!d_info) return -8;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n == 0) return note(cudaMemsetAsync(d_info, 0, sizeof(int), st));
+    const Plan p = make_plan(1, &n, r, 1);
+    if (!work) return -6;
+    if (lwork < p.total) return -7;
+    char *w = (char *)(((uintptr_t)work + 255) & ~(uintptr_t)255);
+    if ((size_t)(w - (char *)work) + p.total - 256 > lwork) return -7;
+    std::vector<MatDesc> mats(1);
+    mats[0].n = n; mats[0].d_in = d; mats[0].e_in = e; mats[0].So = S;
+    return run_plan(p, r, w, mats, d_info, st);
+}
+
+int bdc_svd_values(int n, const double *d, const double *e, double *S, bdc_stream_t stream) {
+    if (n < 0) return -1;
+    if (n > 0 && !d) return -2;
+    if (n > 1 && !e) return -3;
+    if (n > 0 && !S) return -4;
+    if (n == 0) return 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    bdc_opts o;
+    bdc_opts_default(&o);
+    const size_t lw = bdc_svd_values_workspace(n, &o) + 512;
+    void *work = nullptr;
+    if (int r = note(cudaMallocAsync(&work, lw, st))) return r;
+    int *dinfo = (int *)((char *)work + lw - 64);
+    int rc = bdc_svd_values_ex(n, d, e, S, &o, work, lw - 128, dinfo, stream);
+    int hinfo = 0;
+    if (rc == 0 && cudaMemcpyAsync(&hinfo, dinfo, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        rc = BDC_ERR_CUDA;
     cudaFreeAsync(work, st);
     if (int r = note(cudaStreamSynchronize(st))) return r;
     return rc != 0 ? rc : hinfo;
@@ -1087,10 +1178,11 @@ int bdc_profile_end(double *ms, long long *launches, double *work) {
             const double top = nd.nl + 1, botU = nd.m - nd.nl - 1, botV = nd.m + nd.sqre - nd.nl - 1;
             // mixed_min compares with the height's largest order (as the launch
             // decision does); per node this is exact up to that granularity
-            w[BDC_STAGE_GEMM] += 2.0 * N * (2.0 * top * Ktop + (botU + botV) * Kbot) *
-                                 (nd.pad >= pc.mixed_min ? pc.pairs : 1);
             g_sec_roots += ns.N;
             g_sec_iters += (long long)ns.iters;
+            if (pc.vals) continue;
+            w[BDC_STAGE_GEMM] += 2.0 * N * (2.0 * top * Ktop + (botU + botV) * Kbot) *
+                                 (nd.pad >= pc.mixed_min ? pc.pairs : 1);
             w[BDC_STAGE_VECTORS] += 16.0 * N * ns.Ktot;
             w[BDC_STAGE_GATHER] += 0.0;
         }

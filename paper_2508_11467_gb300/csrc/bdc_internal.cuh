@@ -89,6 +89,11 @@ struct MatDesc {
     float *targ;             // harvest targets [hcap]
     int *hcount;             // harvest counter (device)
     int hcap;                // harvest capacity
+    // singular values only: no U, V panels; each node keeps the first and
+    // last rows of its V (the rows z is formed from), copy = depth % 2
+    int vals;                // 1 = singular values only
+    real_t *vf[2], *vl[2];   // [n + 1], node column c at r0 + c
+    real_t *FK, *LK;         // K-indexed (from kbase): first/last-row entries of the survivors' columns
 };
 
 struct NodeDesc {
@@ -179,6 +184,11 @@ cudaError_t launch_vectors(const NodeDesc *nodes, int nnodes, const MatDesc *mat
                            const NodeState *state, int mmax, cudaStream_t st);
 cudaError_t launch_gemm64(const GemmProb *probs, int nprobs, int mmax_rows, int nmax_cols,
                           cudaStream_t st);
+// singular values only (first and last rows of V instead of the panels)
+cudaError_t launch_gather_rows(const NodeDesc *nodes, int nnodes, const MatDesc *mats,
+                               const NodeState *state, int mmax, cudaStream_t st);
+cudaError_t launch_rows_update(const NodeDesc *nodes, int nnodes, const MatDesc *mats,
+                               const NodeState *state, int mmax, cudaStream_t st);
 cudaError_t launch_merge_finish(const NodeDesc *nodes, int nnodes, const MatDesc *mats,
                                 const NodeState *state, int mmax, cudaStream_t st);
 cudaError_t launch_final(const MatDesc *mats, int nmat, int nmax, cudaStream_t st);

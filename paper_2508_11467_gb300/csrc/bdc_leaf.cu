@@ -41,7 +41,10 @@ __global__ void __launch_bounds__(32) k_leaf(const NodeDesc *__restrict__ leaves
     const NodeDesc nd = leaves[blockIdx.x];
     const MatDesc md = mats[nd.mat];
     const int m = nd.m, sq = nd.sqre, mc = m + sq;
-    const int ldu = L, ldv = L + 1;
+    // singular values only: U is not accumulated and V keeps just its first
+    // and last rows (2 x mc, rows 0 and mc-1 of the leaf's V)
+    const bool vals = md.vals != 0;
+    const int ldu = L, ldv = vals ? 2 : L + 1, vrows = vals ? 2 : mc;
     real_t *Us = sm;
     real_t *Vs = Us + (size_t)L * L;
     real_t *dd = Vs + (size_t)(L + 1) * (L + 1);
@@ -53,10 +56,14 @@ __global__ void __launch_bounds__(32) k_leaf(const NodeDesc *__restrict__ leaves
     int *perm = (int *)(s2 + (L + 1));
     volatile LeafCtl *ctl = (volatile LeafCtl *)(perm + L + 2);
 
-    for (int j = 0; j < m; ++j)
-        for (int r = lane; r < m; r += 32) Us[j * ldu + r] = (r == j) ? R(1) : R(0);
+    if (!vals)
+        for (int j = 0; j < m; ++j)
+            for (int r = lane; r < m; r += 32) Us[j * ldu + r] = (r == j) ? R(1) : R(0);
     for (int j = 0; j < mc; ++j)
-        for (int r = lane; r < mc; r += 32) Vs[j * ldv + r] = (r == j) ? R(1) : R(0);
+        for (int r = lane; r < vrows; r += 32) {
+            const int row = (vals && r == 1) ? mc - 1 : r;
+            Vs[j * ldv + r] = (row == j) ? R(1) : R(0);
+        }
     for (int i = lane; i < m; i += 32) dd[i] = md.dsc[nd.r0 + i];
     for (int i = lane; i < m - 1 + sq; i += 32) ee[i] = md.esc[nd.r0 + i];
     if (lane == 0) { ctl->info = 0; ctl->hi = m - 1; }
@@ -76,7 +83,7 @@ __global__ void __launch_bounds__(32) k_leaf(const NodeDesc *__restrict__ leaves
             ee[m - 1] = R(0);
         }
         __syncwarp();
-        for (int j = m - 1; j >= 0; --j) rot_rows(Vs, ldv, mc, lane, j, m, c1[j], s1[j]);
+        for (int j = m - 1; j >= 0; --j) rot_rows(Vs, ldv, vrows, lane, j, m, c1[j], s1[j]);
         __syncwarp();
     }
 
@@ -188,14 +195,16 @@ __global__ void __launch_bounds__(32) k_leaf(const NodeDesc *__restrict__ leaves
         if (act == ACT_DONE) break;
         if (act == ACT_SWEEP) {
             const int lo = ctl->lo, hi = ctl->hi;
-            for (int k = lo; k < hi; ++k) rot_rows(Vs, ldv, mc, lane, k, k + 1, c1[k], s1[k]);
-            for (int k = lo; k < hi; ++k) rot_rows(Us, ldu, m, lane, k, k + 1, c2[k], s2[k]);
+            for (int k = lo; k < hi; ++k) rot_rows(Vs, ldv, vrows, lane, k, k + 1, c1[k], s1[k]);
+            if (!vals)
+                for (int k = lo; k < hi; ++k) rot_rows(Us, ldu, m, lane, k, k + 1, c2[k], s2[k]);
         } else if (act == ACT_CHASE_ROW) {
             const int kz = ctl->k, cnt = ctl->cnt;
-            for (int j = kz + 1; j <= kz + cnt; ++j) rot_rows(Us, ldu, m, lane, j, kz, c2[j], s2[j]);
+            if (!vals)
+                for (int j = kz + 1; j <= kz + cnt; ++j) rot_rows(Us, ldu, m, lane, j, kz, c2[j], s2[j]);
         } else if (act == ACT_CHASE_COL) {
             const int hi = ctl->hi, jend = ctl->k;
-            for (int j = hi - 1; j >= jend; --j) rot_rows(Vs, ldv, mc, lane, j, hi, c1[j], s1[j]);
+            for (int j = hi - 1; j >= jend; --j) rot_rows(Vs, ldv, vrows, lane, j, hi, c1[j], s1[j]);
         }
         __syncwarp();
     }
@@ -203,7 +212,7 @@ __global__ void __launch_bounds__(32) k_leaf(const NodeDesc *__restrict__ leaves
     // non-negative values: flip the matching right vector
     for (int j = 0; j < m; ++j) {
         if (dd[j] < R(0)) {
-            for (int r = lane; r < mc; r += 32) Vs[j * ldv + r] = -Vs[j * ldv + r];
+            for (int r = lane; r < vrows; r += 32) Vs[j * ldv + r] = -Vs[j * ldv + r];
         }
     }
     __syncwarp();
@@ -222,14 +231,26 @@ __global__ void __launch_bounds__(32) k_leaf(const NodeDesc *__restrict__ leaves
     __syncwarp();
     const long long ld = md.n;
     const int r0 = nd.r0;
-    real_t *Uo = md.U[nd.buf], *Vo = md.V[nd.buf];
-    for (int p = 0; p < m; ++p) {
-        const int j = perm[p];
-        for (int r = lane; r < m; r += 32) Uo[(size_t)(r0 + p) * ld + r0 + r] = Us[j * ldu + r];
-        for (int r = lane; r < mc; r += 32) Vo[(size_t)(r0 + p) * ld + r0 + r] = Vs[j * ldv + r];
+    if (vals) {
+        real_t *VF = md.vf[nd.buf], *VL = md.vl[nd.buf];
+        for (int p = lane; p < m; p += 32) {
+            VF[r0 + p] = Vs[perm[p] * ldv + 0];
+            VL[r0 + p] = Vs[perm[p] * ldv + 1];
+        }
+        if (sq && lane == 0) {
+            VF[r0 + m] = Vs[m * ldv + 0];
+            VL[r0 + m] = Vs[m * ldv + 1];
+        }
+    } else {
+        real_t *Uo = md.U[nd.buf], *Vo = md.V[nd.buf];
+        for (int p = 0; p < m; ++p) {
+            const int j = perm[p];
+            for (int r = lane; r < m; r += 32) Uo[(size_t)(r0 + p) * ld + r0 + r] = Us[j * ldu + r];
+            for (int r = lane; r < mc; r += 32) Vo[(size_t)(r0 + p) * ld + r0 + r] = Vs[j * ldv + r];
+        }
+        if (sq)
+            for (int r = lane; r < mc; r += 32) Vo[(size_t)(r0 + m) * ld + r0 + r] = Vs[m * ldv + r];
     }
-    if (sq)
-        for (int r = lane; r < mc; r += 32) Vo[(size_t)(r0 + m) * ld + r0 + r] = Vs[m * ldv + r];
     for (int p = lane; p < m; p += 32) {
         md.D[r0 + p] = dd[perm[p]];
         md.Q[r0 + p] = p;

@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
         while (lo < hi) { int mid = (lo + hi) >> 1; if (DR[QR[mid]] < v) lo = mid + 1; else hi = mid; }
         const int pos = 1 + p + lo;
         ds[pos] = v;
-        zs[pos] = alpha * Vc[(size_t)(r0L + j) * ld + r0L + nl];
+        zs[pos] = alpha * (md.vals ? md.vl[1 - nd.buf][r0L + j] : Vc[(size_t)(r0L + j) * ld + r0L + nl]);
         src[pos] = 1 + j;
         dmax = fmax(dmax, fabs(v));
     }
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
         while (lo < hi) { int mid = (lo + hi) >> 1; if (DL[QL[mid]] <= v) lo = mid + 1; else hi = mid; }
         const int pos = 1 + q + lo;
         ds[pos] = v;
-        zs[pos] = beta * Vc[(size_t)(r0R + j) * ld + r0R];
+        zs[pos] = beta * (md.vals ? md.vf[1 - nd.buf][r0R + j] : Vc[(size_t)(r0R + j) * ld + r0R]);
         src[pos] = nl + 1 + j;
         dmax = fmax(dmax, fabs(v));
     }
@@ -260,10 +260,10 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
     if (t == 0) {
         // d_0 = 0 column: alpha * (last entry of q_1), folded with beta * (first
         // entry of q_2) when the right child is rectangular
-        real_t z0 = alpha * Vc[(size_t)(r0L + nl) * ld + r0L + nl];
-        real_t cq = 1.0, sq = 0.0;
+        real_t z0 = alpha * (md.vals ? md.vl[1 - nd.buf][r0L + nl] : Vc[(size_t)(r0L + nl) * ld + r0L + nl]);
+        real_t cq = R(1), sq = R(0);
         if (sqre) {
-            const real_t b0 = beta * Vc[(size_t)(r0R + nr) * ld + r0R];
+            const real_t b0 = beta * (md.vals ? md.vf[1 - nd.buf][r0R + nr] : Vc[(size_t)(r0R + nr) * ld + r0R]);
             real_t r;
             make_rot(z0, b0, cq, sq, r);
             z0 = r;
@@ -512,6 +512,86 @@ __global__ void __launch_bounds__(128) k_merge_gather(const NodeDesc *__restrict
     for (int row = threadIdx.x; row < mc; row += blockDim.x) vd[row] = cs.v(c, row);
 }
 
+// ------------------------------------------------------------------ gather (values only)
+// The same deflation bookkeeping as k_merge_gather on just two rows of V:
+// the node's first row (inside the left child's rows) and last row (inside
+// the right child's rows).  One thread per sorted position; survivors go to
+// the K-indexed FK / LK, deflated columns and the new null vector straight
+// to the node's first/last-row arrays.
+struct RowSrc {
+    const real_t *VF, *VL;       // children's first / last rows (copy 1 - buf)
+    int r0, r0R, nl, nr, sqre;
+    real_t cq, sq;
+    __device__ real_t f(int c) const {     // first row of pre-deflation column c
+        if (c == 0) return cq * VF[r0 + nl];
+        return (c <= nl) ? VF[r0 + c - 1] : R(0);
+    }
+    __device__ real_t l(int c) const {     // last row
+        if (c == 0) return sqre ? sq * VL[r0R + nr] : R(0);
+        return (c > nl) ? VL[r0R + (c - nl - 1)] : R(0);
+    }
+};
+
+__global__ void __launch_bounds__(128) k_gather_rows(const NodeDesc *__restrict__ nodes,
+                                                     const MatDesc *__restrict__ mats,
+                                                     const NodeState *__restrict__ state, int mmax, int nnodes) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int node = (int)(idx / mmax), p = (int)(idx % mmax);
+    if (node >= nnodes) return;
+    const NodeDesc nd = nodes[node];
+    if (p >= nd.m) return;
+    const MatDesc md = mats[nd.mat];
+    const NodeState ns = state[nd.id];
+    const int m = nd.m, nl = nd.nl, sqre = nd.sqre, r0 = nd.r0;
+    const int r = md.role[r0 + p], code = r & 15;
+    const int *src = md.src + r0, *dest = md.dest + r0, *slist = md.slist + r0;
+    const real_t *rc = md.rc + r0, *rs = md.rs + r0;
+    const RowSrc cs{md.vf[1 - nd.buf], md.vl[1 - nd.buf], r0, r0 + nl + 1, nl, m - nl - 1, sqre, ns.cq, ns.sq};
+    real_t *FK = md.FK + nd.kbase, *LK = md.LK + nd.kbase;
+    real_t *VF = md.vf[nd.buf] + r0, *VL = md.vl[nd.buf] + r0;
+    auto put = [&](int dst, real_t fv, real_t lv) {
+        if (dst >= 0) { FK[dst] = fv; LK[dst] = lv; }
+        else { VF[ns.N + (-dst - 1)] = fv; VL[ns.N + (-dst - 1)] = lv; }
+    };
+    if (p == 0) {
+        // the d_0 column absorbs the zero-deflated group by one-sided rotations
+        real_t yf = cs.f(0), yl = cs.l(0);
+        for (int j = 1; j <= ns.nzero; ++j) {
+            const int q = slist[j];
+            const real_t xf = cs.f(src[q]), xl = cs.l(src[q]), c = rc[q], s = rs[q];
+            put(dest[q], -s * yf + c * xf, -s * yl + c * xl);
+            yf = c * yf + s * xf;
+            yl = c * yl + s * xl;
+        }
+        FK[ns.P1] = yf;
+        LK[ns.P1] = yl;
+        if (sqre) {   // the new right null vector: last column of the node
+            VF[m] = -ns.sq * md.vf[1 - nd.buf][r0 + nl];
+            VL[m] = ns.cq * md.vl[1 - nd.buf][r0 + nl + 1 + (m - nl - 1)];
+        }
+        return;
+    }
+    if (code == ROLE_ZERO) return;
+    if ((r & FL_MEMBER) && !(r & FL_START)) return;   // handled by its chain's first member
+    if (code == ROLE_CHAIN) {
+        const int k0 = md.sidx[r0 + p];
+        real_t yf = cs.f(src[p]), yl = cs.l(src[p]);
+        int prev = p;
+        for (int k = k0 + 1; k < m; ++k) {
+            const int q = slist[k];
+            const real_t xf = cs.f(src[q]), xl = cs.l(src[q]), c = rc[q], s = rs[q];
+            put(dest[prev], c * yf - s * xf, c * yl - s * xl);
+            yf = s * yf + c * xf;
+            yl = s * yl + c * xl;
+            prev = q;
+            if ((md.role[r0 + q] & 15) == ROLE_KEEP) break;
+        }
+        put(dest[prev], yf, yl);
+        return;
+    }
+    put(dest[p], cs.f(src[p]), cs.l(src[p]));
+}
+
 // ------------------------------------------------------------------ finish
 // node values (roots, then deflated values) and their ascending order; the
 // vectors are already in place (products and gather write the node block)
@@ -575,6 +655,14 @@ cudaError_t launch_merge_gather(const NodeDesc *nodes, int nnodes, const MatDesc
                                 const NodeState *state, int mmax, cudaStream_t st) {
     if (nnodes <= 0) return cudaSuccess;
     k_merge_gather<<<(unsigned)nnodes * mmax, 128, 0, st>>>(nodes, mats, state, mmax);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_rows(const NodeDesc *nodes, int nnodes, const MatDesc *mats,
+                               const NodeState *state, int mmax, cudaStream_t st) {
+    if (nnodes <= 0) return cudaSuccess;
+    const long long t = (long long)nnodes * mmax;
+    k_gather_rows<<<(unsigned)((t + 127) / 128), 128, 0, st>>>(nodes, mats, state, mmax, nnodes);
     return cudaGetLastError();
 }
 

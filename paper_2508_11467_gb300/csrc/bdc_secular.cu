@@ -535,6 +535,43 @@ __global__ void __launch_bounds__(256) k_vectors_warp(const NodeDesc *__restrict
     }
 }
 
+// values only: the node's first and last rows of V for the survivors, row
+// times the normalised v_i of Eq. (M-svd-vec) computed on the fly (one warp
+// per root; no U_M / V_M is stored)
+__global__ void __launch_bounds__(256) k_rows_update(const NodeDesc *__restrict__ nodes,
+                                                     const MatDesc *__restrict__ mats,
+                                                     const NodeState *__restrict__ state, int mmax, int nnodes) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int node = warp / mmax, i = warp % mmax;
+    if (node >= nnodes) return;
+    const NodeDesc nd = nodes[node];
+    const NodeState ns = state[nd.id];
+    if (i >= ns.N) return;
+    const MatDesc md = mats[nd.mat];
+    const int r0 = nd.r0, N = ns.N;
+    const real_t *d = md.dM + r0, *zt = md.zt + r0;
+    const int *kpos = md.kposM + r0;
+    const real_t *FK = md.FK + nd.kbase, *LK = md.LK + nd.kbase;
+    const real_t dor = d[md.org[r0 + i]], tau = md.tau[r0 + i];
+    real_t sv = R(0), sf = R(0), sl = R(0);
+    for (int j = lane; j < N; j += 32) {
+        const real_t dj = d[j];
+        const real_t v = zt[j] / (((dj - dor) - tau) * (dj + dor + tau));
+        const int kp = kpos[j];
+        sv = fma(v, v, sv);
+        sf = fma(FK[kp], v, sf);
+        sl = fma(LK[kp], v, sl);
+    }
+    sv = warp_sum(sv);
+    sf = warp_sum(sf);
+    sl = warp_sum(sl);
+    if (lane == 0) {
+        const real_t iv = R(1) / sqrt(sv);
+        md.vf[nd.buf][r0 + i] = sf * iv;
+        md.vl[nd.buf][r0 + i] = sl * iv;
+    }
+}
+
 #ifndef BDC_FP32
 __global__ void __launch_bounds__(256) k_mvectors_single(int N, const double *d, const double *zt,
                                                          const int *org, const double *tau, double *UM,
@@ -582,6 +619,14 @@ cudaError_t launch_vectors(const NodeDesc *nodes, int nnodes, const MatDesc *mat
     } else {
         k_vectors<<<(unsigned)nnodes * mmax, 256, 0, st>>>(nodes, mats, state, mmax);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rows_update(const NodeDesc *nodes, int nnodes, const MatDesc *mats, const NodeState *state,
+                               int mmax, cudaStream_t st) {
+    if (nnodes <= 0) return cudaSuccess;
+    const long long warps = (long long)nnodes * mmax;
+    k_rows_update<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(nodes, mats, state, mmax, nnodes);
     return cudaGetLastError();
 }
 
