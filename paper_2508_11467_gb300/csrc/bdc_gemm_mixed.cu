@@ -149,6 +149,39 @@ __device__ __forceinline__ double ldexp_safe(double x, int e) {
     return x * pow2(e);
 }
 
+// v 2^e rounded to nearest (ties to even) as an FP64 value, built with
+// integer operations only (GB300's FP64 pipe is 1.6 op/clk/SM, the integer
+// pipes are far wider); falls back to FP64 arithmetic when the result
+// leaves the normal range
+__device__ __forceinline__ double i64_ldexp(long long v, int e) {
+    if (v == 0) return 0.0;
+    const unsigned long long sign = (unsigned long long)v & 0x8000000000000000ull;
+    const unsigned long long a = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+    const int lz = __clzll((long long)a);
+    const unsigned long long m = a << lz;            // leading one at bit 63
+    unsigned long long mant = m >> 11;               // 53 bits with the leading one
+    const unsigned long long rest = m & 0x7FFull;
+    if (rest > 0x400ull || (rest == 0x400ull && (mant & 1ull))) mant += 1ull;
+    int ex = 63 - lz + e;                            // unbiased exponent of the result
+    if (mant >> 53) { mant >>= 1; ex += 1; }         // rounding carried into bit 53
+    if (ex < -1022 || ex > 1023) return ldexp_safe((double)v, e);
+    return __longlong_as_double((long long)(sign | ((unsigned long long)(ex + 1023) << 52) |
+                                            (mant & 0x000FFFFFFFFFFFFFull)));
+}
+
+// x 2^e exactly for an FP32 value x (integer operations; FP64 fallback
+// outside the normal range and for subnormal x)
+__device__ __forceinline__ double f32_ldexp(float x, int e) {
+    const unsigned int b = __float_as_uint(x);
+    const int ef = (int)((b >> 23) & 0xFF);
+    if ((b & 0x7FFFFFFFu) == 0u) return 0.0;
+    const int ex = ef - 127 + e;
+    if (ef == 0 || ef == 0xFF || ex < -1022 || ex > 1023) return ldexp_safe((double)x, e);
+    const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
+    return __longlong_as_double((long long)(sign | ((unsigned long long)(ex + 1023) << 52) |
+                                            ((unsigned long long)(b & 0x7FFFFFu) << 29)));
+}
+
 // --------------------------------------------------------------- slicing
 // exponent E with 2^E >= 2 max|x| > 2^(E-1)  (0 for an all-zero set)
 __device__ __forceinline__ int scale_exp(unsigned long long maxbits) {
@@ -558,7 +591,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
                     const int col = n0 + 64 * half + i;
                     if (row < pr.M && col < pr.N)
                         pr.C[(size_t)col * pr.ldc + row] =
-                            ldexp_safe((double)(long long)(L[i] - corr), Er + Fb[mx.b_col0 + col] - 40);
+                            i64_ldexp((long long)(L[i] - corr), Er + Fb[mx.b_col0 + col] - 40);
                 }
             }
         } else if constexpr (MODE == MODE_L) {
@@ -594,7 +627,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
                     if (row < pr.M && col < pr.N) {
                         const int e = Er + Fb[mx.b_col0 + col];
                         double *c = pr.C + (size_t)col * pr.ldc + row;
-                        *c += ldexp_safe((double)SL[i], e - 16);
+                        *c += f32_ldexp(SL[i], e - 16);
                     }
                 }
             }
@@ -610,7 +643,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
                         const int col = n0 + 64 * half + 16 * cb + i;
-                        if (row < pr.M && col < pr.N) pr.C[(size_t)col * pr.ldc + row] = (double)v[i];
+                        if (row < pr.M && col < pr.N) pr.C[(size_t)col * pr.ldc + row] = f32_ldexp(v[i], 0);
                     }
                 }
             }
