@@ -507,7 +507,7 @@ def main():
         "config": {"workload": workload_name(a), "n": n, "prec": a.prec, "leaf": a.leaf,
                    "slices": (a.slices or (6 if n <= 8192 else 7)) if a.prec == "exact" else None,
                    "l2": "inputs larger than L2 (U, V and workspace > 10 GB per step)",
-                   "start": a.start, "parallelism": f"replicas x{world}"},
+                   "start": a.start, "fp32_root_start": True, "parallelism": f"replicas x{world}"},
         "gflops_paper_model": flops_model / (ms * 1e-3) / 1e9,
         "status": status,
         "accuracy": acc,

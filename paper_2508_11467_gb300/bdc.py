@@ -27,7 +27,7 @@ PREC = {"fp64": BDC_FP64, "bf16x3": BDC_MIXED_BF16X3, "exact": BDC_MIXED_EXACT, 
 class Opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("seed", ctypes.c_int), ("leaf", ctypes.c_int),
                 ("max_iter", ctypes.c_int), ("slices", ctypes.c_int), ("checked", ctypes.c_int),
-                ("mlp", ctypes.c_void_p), ("mixed_min", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("mlp", ctypes.c_void_p), ("mixed_min", ctypes.c_int), ("fp32_start", ctypes.c_int)]
 
 
 _lock = threading.Lock()
@@ -158,9 +158,11 @@ def _dev(t, dtype=torch.float64):
     return t.to(dtype).contiguous()
 
 
-def make_opts(prec="fp64", leaf=16, max_iter=64, slices=0, seed="plain", mlp=None, mixed_min=0) -> Opts:
+def make_opts(prec="fp64", leaf=16, max_iter=64, slices=0, seed="plain", mlp=None, mixed_min=0,
+              fp32_start=True) -> Opts:
     o = Opts()
     lib().bdc_opts_default(ctypes.byref(o))
+    o.fp32_start = 1 if fp32_start else 0
     o.mixed_min = int(mixed_min)
     o.prec = PREC[prec] if isinstance(prec, str) else int(prec)
     o.leaf = int(leaf)
@@ -176,7 +178,7 @@ def workspace_bytes(n: int, opts: Opts) -> int:
 
 
 def svd(d, e, *, prec="fp64", leaf=16, max_iter=64, slices=0, seed="plain", mlp=None,
-        stream=None, work=None, check=True, mixed_min=0):
+        stream=None, work=None, check=True, mixed_min=0, fp32_start=True):
     """SVD of the upper bidiagonal (d, e) on the GPU.
 
     Returns (S, U, VT) as CUDA float64 tensors (U column-major: U[:, i] is a
@@ -185,7 +187,7 @@ def svd(d, e, *, prec="fp64", leaf=16, max_iter=64, slices=0, seed="plain", mlp=
     d = _dev(d)
     n = d.shape[0]
     e = _dev(e) if n > 1 else torch.zeros(1, dtype=torch.float64, device=d.device)
-    o = make_opts(prec, leaf, max_iter, slices, seed, mlp, mixed_min)
+    o = make_opts(prec, leaf, max_iter, slices, seed, mlp, mixed_min, fp32_start)
     # column-major outputs: allocate the transpose and view it back
     Ut = torch.empty((n, n), dtype=torch.float64, device=d.device)
     VTt = torch.empty((n, n), dtype=torch.float64, device=d.device)
@@ -203,12 +205,12 @@ def svd(d, e, *, prec="fp64", leaf=16, max_iter=64, slices=0, seed="plain", mlp=
     return S[:n], Ut.t(), VTt.t(), code
 
 
-def svd_values(d, e, *, leaf=16, max_iter=64, seed="plain", mlp=None, stream=None, check=True):
+def svd_values(d, e, *, leaf=16, max_iter=64, seed="plain", mlp=None, stream=None, check=True, fp32_start=True):
     """Singular values only (descending), CUDA float64; and the status code."""
     d = _dev(d)
     n = d.shape[0]
     e = _dev(e) if n > 1 else torch.zeros(1, dtype=torch.float64, device=d.device)
-    o = make_opts("fp64", leaf, max_iter, 0, seed, mlp, 0)
+    o = make_opts("fp64", leaf, max_iter, 0, seed, mlp, 0, fp32_start)
     S = torch.empty(max(n, 1), dtype=torch.float64, device=d.device)
     info = torch.zeros(1, dtype=torch.int32, device=d.device)
     lw = int(lib().bdc_svd_values_workspace(n, ctypes.byref(o)))

@@ -104,6 +104,7 @@ size_t per_matrix_bytes(int n, int vals = 0) {
     }
     b += align256(sizeof(real_t) * 20 * N + 64);      // D ds zs rc rs dM zM zt tau omega dval scale pz(6n) ystart yq
     b += align256(sizeof(float) * 11 * N);            // fs (root features)
+    b += align256(sizeof(float) * 2 * N);             // d32, z32 (FP32 root pre-iterations)
     b += align256(sizeof(int) * (13 * N + 128));      // Q src role org kposM dsrc dest slist sidx invK(4n) info
     if (!vals) {
         const size_t big = (N + 1) * (N + 16) + 64;
@@ -225,6 +226,8 @@ MatDesc carve(char *base, size_t off, int n, int vals = 0) {
     md.omega = dd + 9 * N; md.dval = dd + 10 * N; md.scale = dd + 11 * N; md.pz = dd + 12 * N;
     md.ystart = dd + 18 * N; md.yq = dd + 19 * N;
     md.fs = (float *)take(sizeof(float) * 11 * N);
+    float *dz32 = (float *)take(sizeof(float) * 2 * N);
+    md.d32 = dz32; md.z32 = dz32 + N;
     int *ii = (int *)take(sizeof(int) * (13 * N + 128));
     md.Q = ii; md.src = ii + N; md.role = ii + 2 * N; md.org = ii + 3 * N; md.kposM = ii + 4 * N;
     md.dsrc = ii + 5 * N; md.dest = ii + 6 * N; md.slist = ii + 7 * N; md.sidx = ii + 8 * N;
@@ -362,6 +365,7 @@ struct ProfCall {
     int pairs;
     int mixed_min;   // merges of order >= mixed_min ran the split products
     int vals;        // singular values only: no vectors, no products
+    NodeState *host = nullptr;   // pinned copy of the node states, taken at the end of the call
 };
 struct Profiler {
     bool on = false;
@@ -497,7 +501,8 @@ int run_plan(const Plan &p, const bdc_opts &o, char *work, std::vector<MatDesc> 
         }
         {
             StageScope sc(st, BDC_STAGE_SECULAR, (o.seed != BDC_SEED_PLAIN || harvest) ? 3 : 2, 0.0);
-            if ((e = launch_secular(dn, nn, dmats, dstate, mm, max_iter, o.seed, o.mlp, harvest, st)) != cudaSuccess)
+            if ((e = launch_secular(dn, nn, dmats, dstate, mm, max_iter, o.seed, o.mlp, harvest, o.fp32_start,
+                                    st)) != cudaSuccess)
                 return note(e);
         }
         if (p.vals) {   // the survivors' first/last rows of V; no vectors, no products
@@ -558,6 +563,18 @@ int run_plan(const Plan &p, const bdc_opts &o, char *work, std::vector<MatDesc> 
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return note(e);
     }
+    // stage profiling: copy the node states now (the workspace may be reused
+    // before bdc_profile_end reads them)
+    if (g_prof.on && !g_prof.calls.empty() && g_prof.calls.back().dstate == dstate && !g_prof.calls.back().host) {
+        ProfCall &pc = g_prof.calls.back();
+        if (cudaMallocHost((void **)&pc.host, sizeof(NodeState) * std::max(pc.nnodes, 1)) == cudaSuccess) {
+            if ((e = cudaMemcpyAsync(pc.host, dstate, sizeof(NodeState) * pc.nnodes, cudaMemcpyDeviceToHost, st)) !=
+                cudaSuccess)
+                return note(e);
+        } else {
+            pc.host = nullptr;
+        }
+    }
     // gather the per-matrix status words into the caller's d_info
     if (p.nmat > 0) {
         k_info<<<(p.nmat + 255) / 256, 256, 0, st>>>(dmats, p.nmat, d_info_out);
@@ -604,7 +621,7 @@ int check_opts(const bdc_opts &o) {
     if (o.seed == BDC_SEED_MLP && !o.mlp) return 1;
     if (o.leaf < 4 || o.leaf > 64) return 1;
     if (o.slices < 2 || o.slices > 7) return 1;
-    if (o.checked != 0 || o.reserved != 0) return 1;
+    if (o.checked != 0 || o.fp32_start < 0 || o.fp32_start > 1) return 1;
     return 0;
 }
 
@@ -624,6 +641,7 @@ void bdc_opts_default(bdc_opts *o) {
     o->leaf = kDefaultLeaf;
     o->max_iter = kDefaultMaxIter;
     o->slices = 0;   // automatic: 6 for n <= 8192, 7 above
+    o->fp32_start = 1;
 }
 
 size_t bdc_svd_workspace(int n, const bdc_opts *o) {
@@ -1145,6 +1163,9 @@ int bdc_gemm(int M, int N, int K, const double *A, int lda, const double *B, int
 int bdc_profile_begin(int on) {
     for (auto &ev : g_prof.ev) { cudaEventDestroy(ev.a); cudaEventDestroy(ev.b); }
     g_prof.ev.clear();
+    if (!g_prof.calls.empty()) cudaDeviceSynchronize();
+    for (auto &pc : g_prof.calls)
+        if (pc.host) cudaFreeHost(pc.host);
     g_prof.calls.clear();
     g_sec_roots = g_sec_iters = 0;
     g_prof.on = on != 0;
@@ -1166,12 +1187,16 @@ int bdc_profile_end(double *ms, long long *launches, double *work) {
         cudaEventDestroy(ev.b);
     }
     g_prof.ev.clear();
+    cudaDeviceSynchronize();
     for (auto &pc : g_prof.calls) {
         std::vector<NodeState> hs(pc.nnodes);
-        if (cudaMemcpy(hs.data(), pc.dstate, sizeof(NodeState) * pc.nnodes, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        if (!pc.host) {
             rc = BDC_ERR_CUDA;
             continue;
         }
+        std::memcpy(hs.data(), pc.host, sizeof(NodeState) * pc.nnodes);
+        cudaFreeHost(pc.host);
+        pc.host = nullptr;
         for (const NodeDesc &nd : pc.merges) {
             const NodeState &ns = hs[nd.id];
             const double N = ns.N, Ktop = ns.P1 + 1 + ns.n2, Kbot = ns.Ktot - ns.P1;

@@ -85,6 +85,7 @@ struct MatDesc {
     real_t *ystart;          // per-root start fractions (seeded starts), indexed r0 + i
     real_t *yq;              // per-root analytic estimates (harvest)
     float *fs;               // per-root features [n][kMlpIn] (harvest)
+    float *d32, *z32;        // FP32 copies of the survivors' d, z (M order, from r0)
     float *feat;             // optional MLP harvest: features [hcap][kMlpIn] (nullptr = off)
     float *targ;             // harvest targets [hcap]
     int *hcount;             // harvest counter (device)
@@ -179,7 +180,7 @@ cudaError_t launch_merge_gather(const NodeDesc *nodes, int nnodes, const MatDesc
                                 const NodeState *state, int mmax, cudaStream_t st);
 cudaError_t launch_secular(const NodeDesc *nodes, int nnodes, const MatDesc *mats,
                            NodeState *state, int mmax, int max_iter, int seed_mode,
-                           const float *mlp, int harvest, cudaStream_t st);
+                           const float *mlp, int harvest, int fp32_start, cudaStream_t st);
 cudaError_t launch_vectors(const NodeDesc *nodes, int nnodes, const MatDesc *mats,
                            const NodeState *state, int mmax, cudaStream_t st);
 cudaError_t launch_gemm64(const GemmProb *probs, int nprobs, int mmax_rows, int nmax_cols,

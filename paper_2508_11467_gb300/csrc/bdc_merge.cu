@@ -324,6 +324,8 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
             }
             dM[ik] = ds[p];
             zM[ik] = zs[p];
+            md.d32[r0 + ik] = (float)ds[p];
+            md.z32[r0 + ik] = (float)zs[p];
             kposM[ik] = kp;
             invK[kp] = ik;
             dest[p] = kp;

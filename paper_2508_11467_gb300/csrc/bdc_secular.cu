@@ -128,14 +128,68 @@ __device__ __forceinline__ int root_iterate(const real_t *__restrict__ d, const 
     return it;
 }
 
+// FP32 pre-iteration of root i (not the last) from r.x: the same rational
+// model and bracket as root_iterate, on FP32 copies of d and z with the two
+// interval poles' shifted differences taken exactly from r (0 and +-D2).
+// FP32 runs on GB300 at ~80x the FP64 rate, so this is nearly free; it stops
+// at a relative step of 2^-17 (or after 6 steps) and the FP64 iteration
+// then finishes from there.  Other poles within ~2^-23 relative of the
+// origin are only approximate in FP32: that costs FP64 steps, never
+// accuracy.  Updates r.x (r.lo, r.hi untouched); all lanes agree.
+__device__ __forceinline__ void fp32_phase(const float *__restrict__ d32, const float *__restrict__ z32, int N,
+                                           int i, RootState &r) {
+    const int lane = threadIdx.x & 31;
+    const float D2 = (float)(r.lamR - r.lamL);
+    const float lamL = (float)r.lamL, lamR = (float)r.lamR;
+    const float dor = d32[r.o];
+    float x = (float)r.x, lo = (float)r.lo, hi = (float)r.hi;
+    const float di = (r.o == i) ? 0.f : -D2, di1 = (r.o == i) ? D2 : 0.f;   // d_i^2 - d_o^2, d_{i+1}^2 - d_o^2
+    for (int it = 0; it < 6; ++it) {
+        float psi = 0.f, dpsi = 0.f, phi = 0.f, dphi = 0.f;
+        for (int j = lane; j < N; j += 32) {
+            const float dj = d32[j], zj = z32[j];
+            const float c = (j == i) ? di : (j == i + 1) ? di1 : (dj - dor) * (dj + dor);
+            const float t = zj / (c - x);
+            if (j <= i) { psi = fmaf(zj, t, psi); dpsi = fmaf(t, t, dpsi); }
+            else { phi = fmaf(zj, t, phi); dphi = fmaf(t, t, dphi); }
+        }
+        psi = warp_sum(psi); dpsi = warp_sum(dpsi); phi = warp_sum(phi); dphi = warp_sum(dphi);
+        const float f = 1.f + psi + phi;
+        if (!(f == f)) return;                               // no usable FP32 information
+        if (f > 0.f) hi = x; else lo = x;
+        const float DL = lamL - x, DR = lamR - x;
+        const float sL = DL * DL * dpsi, sR = DR * DR * dphi;
+        const float C = f - DL * dpsi - DR * dphi;
+        const float a = C * (DL + DR) + sL + sR;
+        const float b = C * DL * DR + sL * DR + sR * DL;
+        float eta;
+        if (C == 0.f) {
+            eta = b / a;
+        } else {
+            const float disc = sqrtf(fabsf(a * a - 4.f * b * C));
+            eta = (a > 0.f) ? (2.f * b / (a + disc)) : ((a - disc) / (2.f * C));
+        }
+        float xn = x + eta;
+        if (!(xn > lo && xn < hi)) xn = 0.5f * (lo + hi);
+        const float step = xn - x;
+        x = xn;
+        if (fabsf(step) <= 0x1p-17f * fabsf(x)) break;
+    }
+    const real_t xd = (real_t)x;
+    if (xd > r.lo && xd < r.hi) r.x = xd;
+}
+
 // Solve root i of (d, z) (N entries, d[0] = 0 < d[1] < ...).  Returns the
 // number of iterations used, or -1 if not converged.  All lanes return the
 // same result.  vstart (NaN = none) is a predicted start (start_fraction of
 // a predicted logit, see bdc_mlp.cuh); with it the solver starts there
-// instead of evaluating the interval midpoint, and polishes from the nearer
-// pole if the prediction chose the farther one.
+// instead of evaluating the interval midpoint.  d32, z32 (nullptr = none):
+// FP32 copies for fp32_phase, which then also replaces the FP64 midpoint
+// evaluation that picks the origin.  A start that may sit on the farther
+// half is polished from the nearer pole at the end.
 __device__ __forceinline__ int solve_root(const real_t *__restrict__ d, const real_t *__restrict__ z, int N, int i,
-                          int max_iter, real_t zz, int &org_out, real_t &tau_out, real_t &x_out, real_t vstart) {
+                          int max_iter, real_t zz, int &org_out, real_t &tau_out, real_t &x_out, real_t vstart,
+                          const float *__restrict__ d32 = nullptr, const float *__restrict__ z32 = nullptr) {
     const int lane = threadIdx.x & 31;
     if (N == 1) {
         org_out = 0;
@@ -147,10 +201,25 @@ __device__ __forceinline__ int solve_root(const real_t *__restrict__ d, const re
     const real_t dl = d[i];
     const real_t du = last ? sqrt(dl * dl + zz) : d[i + 1];
     const real_t h = R(0.5) * (du - dl);
-    const bool use_mlp = !last && (vstart == vstart);
+    const bool pre32 = !last && d32 != nullptr;
+    const bool use_mlp = !last && ((vstart == vstart) || pre32);
     RootState r;
     r.dl = dl;
     r.du = du;
+    if (pre32 && !(vstart == vstart)) {
+        // FP32 sign at the interval midpoint picks the origin (a wrong pick
+        // near the midpoint is repaired by the origin switch)
+        const float xm = (float)(h * (R(2.0) * dl + h)), D2f = (float)((du - dl) * (du + dl));
+        const float di = (float)dl;
+        float s = 0.f;
+        for (int j = lane; j < N; j += 32) {
+            const float dj = d32[j], zj = z32[j];
+            const float c = (j == i) ? 0.f : (j == i + 1) ? D2f : (dj - di) * (dj + di);
+            s = fmaf(zj, zj / (c - xm), s);
+        }
+        s = warp_sum(s);
+        vstart = (1.f + s >= 0.f) ? R(0.25) : R(-0.25);     // the midpoint seen from the chosen pole
+    }
     if (use_mlp) {
         const real_t D2 = (du - dl) * (du + dl);
         if (vstart > R(0.0)) {
@@ -159,6 +228,7 @@ __device__ __forceinline__ int solve_root(const real_t *__restrict__ d, const re
             r.o = i + 1; r.dor = du; r.lo = -D2; r.hi = R(0.0); r.lamL = -D2; r.lamR = R(0.0); r.x = vstart * D2;
         }
         if (!(r.x > r.lo && r.x < r.hi)) r.x = R(0.5) * (r.lo + r.hi);
+        if (pre32) fp32_phase(d32, z32, N, i, r);
         r.s = pole_sums(d, z, N, i, r.dor, r.x, lane);
     } else if (!last) {
         // sign of f at the interval midpoint picks the nearer pole as origin
@@ -293,7 +363,7 @@ __global__ void __launch_bounds__(128) k_root_start(const NodeDesc *__restrict__
 __global__ void __launch_bounds__(256, 2) k_secular(const NodeDesc *__restrict__ nodes,
                                                  const MatDesc *__restrict__ mats,
                                                  NodeState *__restrict__ state, int mmax,
-                                                 int max_iter, int nnodes, int seed_mode) {
+                                                 int max_iter, int nnodes, int seed_mode, int fp32_start) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     const int node = warp / mmax, i = warp % mmax;
     if (node >= nnodes) return;
@@ -308,7 +378,8 @@ __global__ void __launch_bounds__(256, 2) k_secular(const NodeDesc *__restrict__
     if (seed_mode != BDC_SEED_PLAIN && i < N - 1) vstart = md.ystart[nd.r0 + i];
     int o;
     real_t tau, x;
-    const int it = solve_root(d, z, N, i, max_iter, zz, o, tau, x, vstart);
+    const int it = solve_root(d, z, N, i, max_iter, zz, o, tau, x, vstart,
+                              fp32_start ? md.d32 + nd.r0 : nullptr, fp32_start ? md.z32 + nd.r0 : nullptr);
     if (lane == 0) {
         md.org[nd.r0 + i] = o;
         md.tau[nd.r0 + i] = tau;
@@ -585,8 +656,11 @@ __global__ void __launch_bounds__(256) k_mvectors_single(int N, const double *d,
 }  // namespace
 
 cudaError_t launch_secular(const NodeDesc *nodes, int nnodes, const MatDesc *mats, NodeState *state,
-                           int mmax, int max_iter, int seed_mode, const float *mlp, int harvest,
+                           int mmax, int max_iter, int seed_mode, const float *mlp, int harvest, int fp32_start,
                            cudaStream_t st) {
+#ifdef BDC_FP32
+    fp32_start = 0;   // already single precision
+#endif
     if (nnodes <= 0) return cudaSuccess;
     const long long roots = (long long)nnodes * mmax;
 #ifdef BDC_FP32
@@ -603,7 +677,7 @@ cudaError_t launch_secular(const NodeDesc *nodes, int nnodes, const MatDesc *mat
     }
 #endif
     k_secular<<<(unsigned)((roots + 7) / 8), 256, 0, st>>>(nodes, mats, state, mmax, max_iter, nnodes,
-                                                           seed_mode);
+                                                           seed_mode, fp32_start);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_lowner<<<(unsigned)((roots + 7) / 8), 256, 0, st>>>(nodes, mats, state, mmax, nnodes);

@@ -187,3 +187,20 @@ def test_bf16x3_literal_split_error_is_reported(bdc):
     res = oracle.residual(d, e, s, U.cpu().numpy(), VT.cpu().numpy())
     assert info == 0 and np.all(np.isfinite(s))
     assert 1e-9 < res < 1e-2
+
+
+@pytest.mark.parametrize("kind,seed", [("uniform", 0), ("graded", 1), ("clustered", 2)])
+def test_fp32_start_parity_and_fp64_iterations(bdc, kind, seed):
+    """FP32 pre-iterations of the secular roots: the FP64 finish keeps the
+    FP64 bar, and the FP64 root-finder steps drop on deflating inputs."""
+    n = 4096
+    d, e = inputs.make(kind, n, seed)
+    its = {}
+    for pre in (False, True):
+        bdc.profile_begin()
+        _check_full(bdc, d, e, fp32_start=pre)
+        prof = bdc.profile_end()
+        its[pre] = prof["secular"]["iters"] / max(prof["secular"]["roots"], 1)
+    print(f"{kind}: FP64 steps per root without / with FP32 start {its[False]:.3f} / {its[True]:.3f}")
+    if kind != "clustered":
+        assert its[True] <= 0.7 * its[False], its
