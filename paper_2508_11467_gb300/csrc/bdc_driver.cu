@@ -100,7 +100,8 @@ size_t per_matrix_bytes(int n, int vals = 0) {
         b += align256(sizeof(real_t) * 4 * (N + 1));  // vf, vl (two copies each)
         b += align256(sizeof(real_t) * 8 * N + 64);    // FK, LK (K-indexed, like invK)
     } else {
-        b += align256(sizeof(real_t) * 4 * N * N);    // U, V (two copies each)
+        b += align256(sizeof(real_t) * 2 * N * N);    // U, V column slots
+        b += align256(sizeof(int) * 8 * (N + 1));     // slot maps us[2], vs[2]; row ranges ulo uhi vlo vhi
     }
     b += align256(sizeof(real_t) * 20 * N + 64);      // D ds zs rc rs dM zM zt tau omega dval scale pz(6n) ystart yq
     b += align256(sizeof(float) * 11 * N);            // fs (root features)
@@ -217,8 +218,11 @@ MatDesc carve(char *base, size_t off, int n, int vals = 0) {
         real_t *fk = (real_t *)take(sizeof(real_t) * 8 * N + 64);
         md.FK = fk; md.LK = fk + 4 * N;
     } else {
-        real_t *uv = (real_t *)take(sizeof(real_t) * 4 * N * N);
-        md.U[0] = uv; md.V[0] = uv + N * N; md.U[1] = uv + 2 * N * N; md.V[1] = uv + 3 * N * N;
+        real_t *uv = (real_t *)take(sizeof(real_t) * 2 * N * N);
+        md.U = uv; md.V = uv + N * N;
+        int *sl = (int *)take(sizeof(int) * 8 * (N + 1));
+        md.us[0] = sl; md.us[1] = sl + (N + 1); md.vs[0] = sl + 2 * (N + 1); md.vs[1] = sl + 3 * (N + 1);
+        md.ulo = sl + 4 * (N + 1); md.uhi = sl + 5 * (N + 1); md.vlo = sl + 6 * (N + 1); md.vhi = sl + 7 * (N + 1);
     }
     real_t *dd = (real_t *)take(sizeof(real_t) * 20 * N + 64);
     md.D = dd; md.ds = dd + N; md.zs = dd + 2 * N; md.rc = dd + 3 * N; md.rs = dd + 4 * N;
@@ -303,17 +307,30 @@ __global__ void k_final(const MatDesc *__restrict__ mats, int tiles_per_side) {
     if (c0 >= n || j0 >= n) return;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
     const real_t s = md.scale[0];
-    // U: output column c = source column Q[n-1-c], rows j0..j0+31
+    // U: output column c = the root's column Q[n-1-c] (slots of copy 0: the
+    // root has depth 0), rows j0..j0+31; rows outside a slot's range are zero.
+    // The tile's 32 columns: slots and ranges staged once in shared memory.
+    __shared__ int cg[2][32], clo[2][32], chi[2][32];
+    if (threadIdx.x < 32) {
+        const int c = c0 + threadIdx.x;
+        if (c < n) {
+            const int src = md.Q[n - 1 - c];
+            const int gu = md.us[0][src], gv = md.vs[0][src];
+            cg[0][threadIdx.x] = gu; clo[0][threadIdx.x] = md.ulo[gu]; chi[0][threadIdx.x] = md.uhi[gu];
+            cg[1][threadIdx.x] = gv; clo[1][threadIdx.x] = md.vlo[gv]; chi[1][threadIdx.x] = md.vhi[gv];
+            if (tj == 0) md.So[c] = md.D[src] * s;
+        }
+    }
+    __syncthreads();
     for (int cc = ty; cc < 32; cc += 8) {
         const int c = c0 + cc;
         if (c >= n) break;
-        const int src = md.Q[n - 1 - c];
         const int j = j0 + tx;
         if (j < n) {
-            md.Uo[(size_t)c * md.ldu + j] = md.U[0][(size_t)src * n + j];   // the root has depth 0
-            tile[cc][tx] = md.V[0][(size_t)src * n + j];
+            md.Uo[(size_t)c * md.ldu + j] =
+                (j >= clo[0][cc] && j < chi[0][cc]) ? md.U[(size_t)cg[0][cc] * n + j] : R(0);
+            tile[cc][tx] = (j >= clo[1][cc] && j < chi[1][cc]) ? md.V[(size_t)cg[1][cc] * n + j] : R(0);
         }
-        if (tj == 0 && tx == 0) md.So[c] = md.D[src] * s;
     }
     __syncthreads();
     // VT(c, j) = V(j, src(c)): write down columns j of VT, contiguous in c

@@ -76,15 +76,15 @@ __global__ void __launch_bounds__(256) k_gemm32(const GemmProb *__restrict__ pro
         }
     }
     float *__restrict__ C = pr.C;
-    const int ldc = pr.ldc;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const int gn = n0 + tn + j;
         if (gn >= N) continue;
+        float *__restrict__ Cc = C + gemm_col(pr, gn);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int gm = m0 + tm + i;
-            if (gm < M) C[(size_t)gn * ldc + gm] = acc[i][j];
+            if (gm < M) Cc[gm] = acc[i][j];
         }
     }
 }
@@ -161,7 +161,6 @@ __global__ void __launch_bounds__(128) k_gemm64(const GemmProb *__restrict__ pro
     }
     // fragment (g, 2 tg + {0,1}) of each 8 x 8 tile
     double *__restrict__ C = pr.C;
-    const int ldc = pr.ldc;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int gm = m0 + wm + i * 8 + g;
@@ -169,8 +168,8 @@ __global__ void __launch_bounds__(128) k_gemm64(const GemmProb *__restrict__ pro
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int gn = n0 + wn + j * 8 + 2 * tg;
-            if (gn < N) C[(size_t)gn * ldc + gm] = acc[i][j][0];
-            if (gn + 1 < N) C[(size_t)(gn + 1) * ldc + gm] = acc[i][j][1];
+            if (gn < N) C[gemm_col(pr, gn) + gm] = acc[i][j][0];
+            if (gn + 1 < N) C[gemm_col(pr, gn + 1) + gm] = acc[i][j][1];
         }
     }
 }

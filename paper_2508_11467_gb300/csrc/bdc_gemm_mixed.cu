@@ -590,7 +590,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
                 for (int i = 0; i < 64; ++i) {
                     const int col = n0 + 64 * half + i;
                     if (row < pr.M && col < pr.N)
-                        pr.C[(size_t)col * pr.ldc + row] =
+                        pr.C[gemm_col(pr, col) + row] =
                             i64_ldexp((long long)(L[i] - corr), Er + Fb[mx.b_col0 + col] - 40);
                 }
             }
@@ -626,7 +626,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
                     const int col = n0 + 64 * half + i;
                     if (row < pr.M && col < pr.N) {
                         const int e = Er + Fb[mx.b_col0 + col];
-                        double *c = pr.C + (size_t)col * pr.ldc + row;
+                        double *c = pr.C + gemm_col(pr, col) + row;
                         *c += f32_ldexp(SL[i], e - 16);
                     }
                 }
@@ -643,7 +643,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
                         const int col = n0 + 64 * half + 16 * cb + i;
-                        if (row < pr.M && col < pr.N) pr.C[(size_t)col * pr.ldc + row] = f32_ldexp(v[i], 0);
+                        if (row < pr.M && col < pr.N) pr.C[gemm_col(pr, col) + row] = f32_ldexp(v[i], 0);
                     }
                 }
             }

@@ -1,12 +1,19 @@
 // Internal data layout and helpers of the GB300 bidiagonal divide-and-conquer.
 //
 // Layout in HBM (one "matrix" = one bidiagonal problem of order n):
-//   U, V      two copies each, n x n column-major (ld = n).  Every node of the
-//             split tree owns the diagonal block starting at (r0, r0): m x m in
-//             U and (m+sqre) x (m+sqre) in V (Sec. 4.2.1: B_1 is (k-1) x k, the
-//             coupling row k, B_2 below) of copy (depth % 2): a node reads its
-//             children from the other copy, so vectors can be written to their
-//             final place while the children are still being read.
+//   U, V      n x n column-major (ld = n), one copy each.  A node of the split
+//             tree covers rows r0..r0+m-1 (Sec. 4.2.1: B_1 is (k-1) x k, the
+//             coupling row k, B_2 below).  Its columns are not stored in a
+//             block of their own: node column c lives in the slot (global
+//             column index) us[b][r0 + c] of U and vs[b][r0 + c] of V, b =
+//             depth % 2 (the maps are double-buffered: a node writes its map
+//             while its children's maps are read).  A slot holds data only
+//             in rows [lo, hi) of the node that last wrote it (ulo/uhi,
+//             vlo/vhi); every reader treats the other rows as zero.  A column
+//             that a merge deflates keeps its slot untouched; survivors are
+//             gathered into W~/Q~ and the merge products write the new
+//             columns back into the survivors' slots, so deflated columns are
+//             never copied.
 //   D, Q      n entries: D[r0+j] = value of node column j, Q[r0+p] = local
 //             column of the p-th smallest value (node-local ascending order).
 //   merge scratch (indexed from r0 or from the node's kbase) and four big
@@ -62,7 +69,9 @@ struct MatDesc {
     real_t *Uo, *So, *VTo;   // user outputs
     real_t *dsc, *esc;       // scaled copies (esc[n-1] = 0)
     real_t *scale;           // [1] scale factor applied to d, e
-    real_t *U[2], *V[2];     // node blocks, copy = tree depth % 2
+    real_t *U, *V;           // column slots (n x n each, ld = n)
+    int *us[2], *vs[2];      // node column -> slot, copy = tree depth % 2 (n + 1 each)
+    int *ulo, *uhi, *vlo, *vhi;   // per slot: rows holding data [lo, hi) (n + 1 each)
     real_t *D;               // node values
     int *Q;                  // node-local ascending order
     // merge scratch, per node from r0 (size n) unless noted
@@ -123,12 +132,18 @@ struct NodeState {
     real_t rho;                 // sum of z^2 over the survivors (after deflation)
 };
 
-// one product C = A * B (column-major, real_t), used by the merge GEMMs
+// one product C = A * B (column-major, real_t), used by the merge GEMMs;
+// with cmap, column j of the result is stored at C + cmap[j] * ldc
 struct GemmProb {
     const real_t *A; const real_t *B; real_t *C;
     int lda, ldb, ldc;
     int M, N, K;
+    const int *cmap;
 };
+
+__host__ __device__ __forceinline__ size_t gemm_col(const GemmProb &p, int j) {
+    return (size_t)(p.cmap ? p.cmap[j] : j) * (size_t)p.ldc;
+}
 
 // role codes for sorted positions (merge)
 enum : int {

@@ -242,7 +242,8 @@ __global__ void __launch_bounds__(32) k_leaf(const NodeDesc *__restrict__ leaves
             VL[r0 + m] = Vs[m * ldv + 1];
         }
     } else {
-        real_t *Uo = md.U[nd.buf], *Vo = md.V[nd.buf];
+        // node column p in slot r0 + p (rows r0..r0+m-1 of U, r0..r0+mc-1 of V)
+        real_t *Uo = md.U, *Vo = md.V;
         for (int p = 0; p < m; ++p) {
             const int j = perm[p];
             for (int r = lane; r < m; r += 32) Uo[(size_t)(r0 + p) * ld + r0 + r] = Us[j * ldu + r];
@@ -250,6 +251,16 @@ __global__ void __launch_bounds__(32) k_leaf(const NodeDesc *__restrict__ leaves
         }
         if (sq)
             for (int r = lane; r < mc; r += 32) Vo[(size_t)(r0 + m) * ld + r0 + r] = Vs[m * ldv + r];
+        for (int p = lane; p < mc; p += 32) {
+            if (p < m) {
+                md.us[nd.buf][r0 + p] = r0 + p;
+                md.ulo[r0 + p] = r0;
+                md.uhi[r0 + p] = r0 + m;
+            }
+            md.vs[nd.buf][r0 + p] = r0 + p;
+            md.vlo[r0 + p] = r0;
+            md.vhi[r0 + p] = r0 + mc;
+        }
     }
     for (int p = lane; p < m; p += 32) {
         md.D[r0 + p] = dd[perm[p]];

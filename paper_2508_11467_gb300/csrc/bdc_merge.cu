@@ -228,7 +228,12 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
     real_t *ds = md.ds + r0, *zs = md.zs + r0;
     int *src = md.src + r0;
     const real_t alpha = md.dsc[r0 + nl], beta = md.esc[r0 + nl];
-    const real_t *Vc = md.V[1 - nd.buf];                 // children's right vectors
+    // children's right vectors: node column j of a child lives in slot
+    // vs[1 - buf][child r0 + j]; rows outside the slot's range read as zero
+    const int *cvs = md.vs[1 - nd.buf], *cus = md.us[1 - nd.buf];
+    auto vrow = [&](int g, long long row) -> real_t {
+        return (row >= md.vlo[g] && row < md.vhi[g]) ? md.V[(size_t)g * ld + row] : R(0);
+    };
 
     // ---- z and the merged ascending order (children are sorted through Q)
     const int *QL = md.Q + r0L, *QR = md.Q + r0R;
@@ -241,7 +246,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
         while (lo < hi) { int mid = (lo + hi) >> 1; if (DR[QR[mid]] < v) lo = mid + 1; else hi = mid; }
         const int pos = 1 + p + lo;
         ds[pos] = v;
-        zs[pos] = alpha * (md.vals ? md.vl[1 - nd.buf][r0L + j] : Vc[(size_t)(r0L + j) * ld + r0L + nl]);
+        zs[pos] = alpha * (md.vals ? md.vl[1 - nd.buf][r0L + j] : vrow(cvs[r0L + j], r0L + nl));
         src[pos] = 1 + j;
         dmax = fmax(dmax, fabs(v));
     }
@@ -252,7 +257,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
         while (lo < hi) { int mid = (lo + hi) >> 1; if (DL[QL[mid]] <= v) lo = mid + 1; else hi = mid; }
         const int pos = 1 + q + lo;
         ds[pos] = v;
-        zs[pos] = beta * (md.vals ? md.vf[1 - nd.buf][r0R + j] : Vc[(size_t)(r0R + j) * ld + r0R]);
+        zs[pos] = beta * (md.vals ? md.vf[1 - nd.buf][r0R + j] : vrow(cvs[r0R + j], r0R));
         src[pos] = nl + 1 + j;
         dmax = fmax(dmax, fabs(v));
     }
@@ -260,10 +265,10 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
     if (t == 0) {
         // d_0 = 0 column: alpha * (last entry of q_1), folded with beta * (first
         // entry of q_2) when the right child is rectangular
-        real_t z0 = alpha * (md.vals ? md.vl[1 - nd.buf][r0L + nl] : Vc[(size_t)(r0L + nl) * ld + r0L + nl]);
+        real_t z0 = alpha * (md.vals ? md.vl[1 - nd.buf][r0L + nl] : vrow(cvs[r0L + nl], r0L + nl));
         real_t cq = R(1), sq = R(0);
         if (sqre) {
-            const real_t b0 = beta * (md.vals ? md.vf[1 - nd.buf][r0R + nr] : Vc[(size_t)(r0R + nr) * ld + r0R]);
+            const real_t b0 = beta * (md.vals ? md.vf[1 - nd.buf][r0R + nr] : vrow(cvs[r0R + nr], r0R));
             real_t r;
             make_rot(z0, b0, cq, sq, r);
             z0 = r;
@@ -313,8 +318,17 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
     const int Ktot = P1 + 1 + n2 + n3;
     real_t *dM = md.dM + r0, *zM = md.zM + r0, *dval = md.dval + r0;
     int *kposM = md.kposM + r0, *invK = md.invK + nd.kbase, *dest = md.dest + r0, *dsrc = md.dsrc + r0;
+    // slots of the node's columns (values-only nodes have none): a survivor's
+    // new column goes to the slot of its source column (the d_0 column's to
+    // the free coupling column of U and to q_1's slot in V), a deflated
+    // column stays in its slot
+    const bool slots = !md.vals;
+    int *nus = slots ? md.us[nd.buf] + r0 : nullptr, *nvs = slots ? md.vs[nd.buf] + r0 : nullptr;
+    auto slot_u = [&](int c) { return c == 0 ? r0 + nl : (c <= nl ? cus[r0L + c - 1] : cus[r0R + (c - nl - 1)]); };
+    auto slot_v = [&](int c) { return c == 0 ? cvs[r0L + nl] : (c <= nl ? cvs[r0L + c - 1] : cvs[r0R + (c - nl - 1)]); };
     for (int p = b; p < e; ++p) {
         const int r = role[p], code = r & 15;
+        int col;                                     // node column of sorted position p
         if (code == ROLE_KEEP) {
             int kp;
             if (p == 0) kp = P1;
@@ -329,19 +343,27 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
             kposM[ik] = kp;
             invK[kp] = ik;
             dest[p] = kp;
+            col = ik;
             ++ik;
         } else if (code == ROLE_ZERO) {
-            dval[iz] = 0.0;
+            dval[iz] = R(0);
             dsrc[iz] = p;
             dest[p] = -(1 + iz);
+            col = N + iz;
             ++iz;
         } else {
             const int slot = nz + io++;
             dval[slot] = ds[p];
             dsrc[slot] = p;
             dest[p] = -(1 + slot);
+            col = N + slot;
+        }
+        if (slots) {
+            nus[col] = slot_u(src[p]);
+            nvs[col] = slot_v(src[p]);
         }
     }
+    if (slots && sqre && t == 0) nvs[m] = cvs[r0R + nr];   // the new null vector takes q_2's slot
     for (int kp = n1 + t; kp < P1; kp += T) invK[kp] = -1;
     if (scans) {
         // moment scans of the survivors for the root start estimates: prefix
@@ -386,42 +408,58 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
         const long long wb = (long long)r0 * md.wstride;
         const int Ktop = P1 + 1 + n2, Kbot = Ktot - P1;
         GemmProb *pr = probs + 4 * (size_t)blockIdx.x;
-        // U: top rows 0..nl (incl. the coupling row), bottom rows nl+1..m-1
-        real_t *Uo = md.U[nd.buf], *Vo = md.V[nd.buf];
-        pr[0] = GemmProb{md.Wt + wb, md.UM + wb, Uo + (size_t)r0 * ld + r0, m, Ktot, (int)ld,
-                         nl + 1, N, Ktop};
-        pr[1] = GemmProb{md.Wt + wb + (nl + 1) + (size_t)P1 * m, md.UM + wb + P1,
-                         Uo + (size_t)r0 * ld + r0 + nl + 1, m, Ktot, (int)ld, m - nl - 1, N, Kbot};
+        // U: top rows 0..nl (incl. the coupling row), bottom rows nl+1..m-1;
+        // survivor i's column goes to the slot us[buf][r0 + i]
+        const int *cu = md.us[nd.buf] + r0, *cv = md.vs[nd.buf] + r0;
+        pr[0] = GemmProb{md.Wt + wb, md.UM + wb, md.U + r0, m, Ktot, (int)ld, nl + 1, N, Ktop, cu};
+        pr[1] = GemmProb{md.Wt + wb + (nl + 1) + (size_t)P1 * m, md.UM + wb + P1, md.U + r0 + nl + 1, m, Ktot,
+                         (int)ld, m - nl - 1, N, Kbot, cu};
         // V: top rows 0..nl (left child's columns), bottom rows nl+1..mc-1
-        pr[2] = GemmProb{md.Qt + wb, md.VM + wb, Vo + (size_t)r0 * ld + r0, mc, Ktot, (int)ld,
-                         nl + 1, N, Ktop};
-        pr[3] = GemmProb{md.Qt + wb + (nl + 1) + (size_t)P1 * mc, md.VM + wb + P1,
-                         Vo + (size_t)r0 * ld + r0 + nl + 1, mc, Ktot, (int)ld, mc - nl - 1, N, Kbot};
+        pr[2] = GemmProb{md.Qt + wb, md.VM + wb, md.V + r0, mc, Ktot, (int)ld, nl + 1, N, Ktop, cv};
+        pr[3] = GemmProb{md.Qt + wb + (nl + 1) + (size_t)P1 * mc, md.VM + wb + P1, md.V + r0 + nl + 1, mc, Ktot,
+                         (int)ld, mc - nl - 1, N, Kbot, cv};
     }
 }
 
 // ------------------------------------------------------------------ gather
+// Columns of the node before deflation: c = 0 is the d_0 column (U: the unit
+// vector of the coupling row; V: cq q_1 + sq q_2), c = 1..nl the left
+// child's columns, c > nl the right child's.  Child columns are read from
+// their slots (rows outside a slot's range are zero).
 struct ColSrc {
     const real_t *U, *V;
     long long ld;
-    int r0, nl, nr, sqre;
+    int r0, nl, nr, sqre, r0R;
     real_t cq, sq;
+    const int *cus, *cvs;                    // children's slot maps
+    const int *ulo, *uhi, *vlo, *vhi;
+    __device__ int uslot(int c) const { return c <= nl ? cus[r0 + c - 1] : cus[r0R + (c - nl - 1)]; }
+    __device__ int vslot(int c) const { return c <= nl ? cvs[r0 + c - 1] : cvs[r0R + (c - nl - 1)]; }
+    __device__ real_t uat(int g, int r) const {     // node row r of U slot g
+        const long long row = r0 + r;
+        return (row >= ulo[g] && row < uhi[g]) ? U[(size_t)g * ld + row] : R(0);
+    }
+    __device__ real_t vat(int g, int r) const {
+        const long long row = r0 + r;
+        return (row >= vlo[g] && row < vhi[g]) ? V[(size_t)g * ld + row] : R(0);
+    }
     __device__ real_t u(int c, int r) const {       // r in [0, m)
         if (c == 0) return (r == nl) ? R(1) : R(0);
-        if (c <= nl) return (r < nl) ? U[(size_t)(r0 + c - 1) * ld + r0 + r] : R(0);
-        return (r > nl) ? U[(size_t)(r0 + nl + 1 + (c - nl - 1)) * ld + r0 + r] : R(0);
+        return uat(uslot(c), r);
     }
-    __device__ real_t q1(int r) const { return (r <= nl) ? V[(size_t)(r0 + nl) * ld + r0 + r] : R(0); }
-    __device__ real_t q2(int r) const {
-        return (sqre && r > nl) ? V[(size_t)(r0 + nl + 1 + nr) * ld + r0 + r] : R(0);
-    }
+    __device__ int q1slot() const { return cvs[r0 + nl]; }
+    __device__ int q2slot() const { return cvs[r0R + nr]; }
     __device__ real_t v(int c, int r) const {       // r in [0, m + sqre)
-        if (c == 0) return cq * q1(r) + sq * q2(r);
-        if (c <= nl) return (r <= nl) ? V[(size_t)(r0 + c - 1) * ld + r0 + r] : R(0);
-        return (r > nl) ? V[(size_t)(r0 + nl + 1 + (c - nl - 1)) * ld + r0 + r] : R(0);
+        if (c == 0) return cq * vat(q1slot(), r) + (sqre ? sq * vat(q2slot(), r) : R(0));
+        return vat(vslot(c), r);
     }
 };
 
+// One CTA per sorted position of every node: survivors are copied into the
+// K-ordered W~ / Q~ (the products' operands); deflated columns stay in their
+// slots, except the members of close-value chains and the columns deflated
+// against d_0, which are rotated in place (the rotation of Sec. 4.2.1 acts
+// on the node's whole row range, so their slots' ranges become the node's).
 __global__ void __launch_bounds__(128) k_merge_gather(const NodeDesc *__restrict__ nodes,
                                                       const MatDesc *__restrict__ mats,
                                                       const NodeState *__restrict__ state, int mmax) {
@@ -434,44 +472,45 @@ __global__ void __launch_bounds__(128) k_merge_gather(const NodeDesc *__restrict
     const int r = md.role[r0 + p], code = r & 15;
     const int *src = md.src + r0, *dest = md.dest + r0, *slist = md.slist + r0;
     const real_t *rc = md.rc + r0, *rs = md.rs + r0;
-    ColSrc cs{md.U[1 - nd.buf], md.V[1 - nd.buf], (long long)md.n, r0, nl, m - nl - 1, sqre, ns.cq, ns.sq};
+    const ColSrc cs{md.U, md.V, (long long)md.n, r0, nl, m - nl - 1, sqre, r0 + nl + 1, ns.cq, ns.sq,
+                    md.us[1 - nd.buf], md.vs[1 - nd.buf], md.ulo, md.uhi, md.vlo, md.vhi};
     const long long wb = (long long)r0 * md.wstride, ld = md.n;
     real_t *W = md.Wt + wb, *Qm = md.Qt + wb;
-    // survivors go to the K-ordered workspace W~ / Q~ (leading dimension m / m+sqre);
-    // deflated vectors straight to their final column N + slot of the node block
-    real_t *Uo = md.U[nd.buf] + (size_t)r0 * ld + r0, *Vo = md.V[nd.buf] + (size_t)r0 * ld + r0;
-    auto ucol = [&](int dst) -> real_t * {
-        return dst >= 0 ? W + (size_t)dst * m : Uo + (size_t)(ns.N + (-dst - 1)) * ld;
-    };
-    auto vcol = [&](int dst) -> real_t * {
-        return dst >= 0 ? Qm + (size_t)dst * mc : Vo + (size_t)(ns.N + (-dst - 1)) * ld;
-    };
+    real_t *U = md.U + r0, *V = md.V + r0;           // row r0 of every slot
 
     if (p == 0) {
         const int a = ns.nzero;
         // padding columns of the K order (between the top block and index 0)
         for (int kp = ns.n1; kp < ns.P1; ++kp) {
-            for (int row = threadIdx.x; row < m; row += blockDim.x) W[(size_t)kp * m + row] = 0.0;
-            for (int row = threadIdx.x; row < mc; row += blockDim.x) Qm[(size_t)kp * mc + row] = 0.0;
+            for (int row = threadIdx.x; row < m; row += blockDim.x) W[(size_t)kp * m + row] = R(0);
+            for (int row = threadIdx.x; row < mc; row += blockDim.x) Qm[(size_t)kp * mc + row] = R(0);
         }
-        for (int row = threadIdx.x; row < m; row += blockDim.x) {
-            W[(size_t)ns.P1 * m + row] = cs.u(0, row);
-            for (int j = 1; j <= a; ++j) {
-                const int q = slist[j];
-                ucol(dest[q])[row] = cs.u(src[q], row);
-            }
-        }
+        // U: the d_0 column is the unit vector; columns deflated against d_0
+        // keep their U columns (the rotation is one-sided)
+        for (int row = threadIdx.x; row < m; row += blockDim.x) W[(size_t)ns.P1 * m + row] = cs.u(0, row);
+        // V: the d_0 column absorbs them one by one, in place
+        const int g1 = cs.q1slot(), g2 = sqre ? cs.q2slot() : 0;
         for (int row = threadIdx.x; row < mc; row += blockDim.x) {
-            real_t y = cs.v(0, row);
+            const real_t q1 = cs.vat(g1, row), q2 = sqre ? cs.vat(g2, row) : R(0);
+            real_t y = ns.cq * q1 + ns.sq * q2;
             for (int j = 1; j <= a; ++j) {
                 const int q = slist[j];
-                const real_t x = cs.v(src[q], row), c = rc[q], s = rs[q];
-                vcol(dest[q])[row] = -s * y + c * x;
+                const int g = cs.vslot(src[q]);
+                const real_t x = cs.vat(g, row), c = rc[q], s = rs[q];
+                V[(size_t)g * ld + row] = -s * y + c * x;
                 y = c * y + s * x;
             }
             Qm[(size_t)ns.P1 * mc + row] = y;
-            // the new right null vector: last column of the node's V block
-            if (sqre) Vo[(size_t)m * ld + row] = -ns.sq * cs.q1(row) + ns.cq * cs.q2(row);
+            // the new right null vector replaces q_2 in its slot
+            if (sqre) V[(size_t)g2 * ld + row] = -ns.sq * q1 + ns.cq * q2;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int j = 1; j <= a; ++j) {
+                const int g = cs.vslot(src[slist[j]]);
+                md.vlo[g] = r0; md.vhi[g] = r0 + mc;
+            }
+            if (sqre) { md.vlo[g2] = r0; md.vhi[g2] = r0 + mc; }
         }
         return;
     }
@@ -479,18 +518,20 @@ __global__ void __launch_bounds__(128) k_merge_gather(const NodeDesc *__restrict
     if ((r & FL_MEMBER) && !(r & FL_START)) return;   // handled by its chain's first member
     if (code == ROLE_CHAIN) {                          // chain start: walk to its end
         const int k0 = md.sidx[r0 + p];
+        // every member but a surviving last one is rotated in its own slot
         for (int row = threadIdx.x; row < m; row += blockDim.x) {
             real_t y = cs.u(src[p], row);
             int prev = p;
             for (int k = k0 + 1; k < m; ++k) {
                 const int q = slist[k];
                 const real_t x = cs.u(src[q], row), c = rc[q], s = rs[q];
-                ucol(dest[prev])[row] = c * y - s * x;
+                U[(size_t)cs.uslot(src[prev]) * ld + row] = c * y - s * x;
                 y = s * y + c * x;
                 prev = q;
                 if ((md.role[r0 + q] & 15) == ROLE_KEEP) break;
             }
-            ucol(dest[prev])[row] = y;
+            if (dest[prev] >= 0) W[(size_t)dest[prev] * m + row] = y;
+            else U[(size_t)cs.uslot(src[prev]) * ld + row] = y;
         }
         for (int row = threadIdx.x; row < mc; row += blockDim.x) {
             real_t y = cs.v(src[p], row);
@@ -498,20 +539,37 @@ __global__ void __launch_bounds__(128) k_merge_gather(const NodeDesc *__restrict
             for (int k = k0 + 1; k < m; ++k) {
                 const int q = slist[k];
                 const real_t x = cs.v(src[q], row), c = rc[q], s = rs[q];
-                vcol(dest[prev])[row] = c * y - s * x;
+                V[(size_t)cs.vslot(src[prev]) * ld + row] = c * y - s * x;
                 y = s * y + c * x;
                 prev = q;
                 if ((md.role[r0 + q] & 15) == ROLE_KEEP) break;
             }
-            vcol(dest[prev])[row] = y;
+            if (dest[prev] >= 0) Qm[(size_t)dest[prev] * mc + row] = y;
+            else V[(size_t)cs.vslot(src[prev]) * ld + row] = y;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int prev = p;
+            for (int k = k0 + 1; k < m; ++k) {
+                const int q = slist[k];
+                md.ulo[cs.uslot(src[prev])] = r0; md.uhi[cs.uslot(src[prev])] = r0 + m;
+                md.vlo[cs.vslot(src[prev])] = r0; md.vhi[cs.vslot(src[prev])] = r0 + mc;
+                prev = q;
+                if ((md.role[r0 + q] & 15) == ROLE_KEEP) break;
+            }
+            if (dest[prev] < 0) {
+                md.ulo[cs.uslot(src[prev])] = r0; md.uhi[cs.uslot(src[prev])] = r0 + m;
+                md.vlo[cs.vslot(src[prev])] = r0; md.vhi[cs.vslot(src[prev])] = r0 + mc;
+            }
         }
         return;
     }
-    // singleton survivor or small-z deflation: plain copy
-    const int c = src[p];
-    real_t *ud = ucol(dest[p]), *vd = vcol(dest[p]);
-    for (int row = threadIdx.x; row < m; row += blockDim.x) ud[row] = cs.u(c, row);
-    for (int row = threadIdx.x; row < mc; row += blockDim.x) vd[row] = cs.v(c, row);
+    // a deflated column keeps its slot; a survivor is copied into W~ / Q~
+    if (dest[p] < 0) return;
+    const int c = src[p], gu = cs.uslot(c), gv = cs.vslot(c);
+    real_t *ud = W + (size_t)dest[p] * m, *vd = Qm + (size_t)dest[p] * mc;
+    for (int row = threadIdx.x; row < m; row += blockDim.x) ud[row] = cs.uat(gu, row);
+    for (int row = threadIdx.x; row < mc; row += blockDim.x) vd[row] = cs.vat(gv, row);
 }
 
 // ------------------------------------------------------------------ gather (values only)
@@ -605,6 +663,14 @@ __global__ void __launch_bounds__(256) k_merge_finish(const NodeDesc *__restrict
     const NodeState ns = state[nd.id];
     const int r0 = nd.r0, N = ns.N, ndef = ns.ndef;
     const real_t *om = md.omega + r0, *dv = md.dval + r0;
+    if (!md.vals) {
+        // the products wrote the survivors' columns over the node's rows
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+            const int gu = md.us[nd.buf][r0 + i], gv = md.vs[nd.buf][r0 + i];
+            md.ulo[gu] = r0; md.uhi[gu] = r0 + nd.m;
+            md.vlo[gv] = r0; md.vhi[gv] = r0 + nd.m + nd.sqre;
+        }
+    }
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         const real_t w = om[i];
         int lo = 0, hi = ndef;           // # deflated values < w
