@@ -66,7 +66,7 @@ thread_local char g_last_err[256] = "";
 int note(cudaError_t e) {
     if (e != cudaSuccess) {
         std::snprintf(g_last_err, sizeof(g_last_err), "%s (%d)", cudaGetErrorString(e), (int)e);
-        return note(e);
+        return BDC_ERR_CUDA;
     }
     return 0;
 }

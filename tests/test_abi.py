@@ -60,3 +60,16 @@ def test_argument_errors_without_gpu(libpath):
     assert L.bdc_svd(4, fake, fake, fake, fake, fake, 3, 4, None) == -7
     assert L.bdc_svd(4, fake, fake, fake, fake, fake, 4, 2, None) == -8
     assert L.bdc_svd(0, None, None, None, None, None, 1, 1, None) == 0
+
+
+def test_cuda_failure_returns_error_code_without_gpu(libpath):
+    """With no CUDA device the first CUDA call fails: the entry point returns
+    BDC_ERR_CUDA and records the message (no crash, no retry loop)."""
+    import ctypes
+    import torch
+    if torch.cuda.is_available() or os.path.exists("/dev/nvidia0"):
+        pytest.skip("needs a machine without a CUDA device")
+    from paper_2508_11467_gb300 import bdc
+    L = bdc.lib()
+    fake = ctypes.c_void_p(16)       # never dereferenced: the workspace allocation fails first
+    assert L.bdc_svd_values(4, fake, fake, fake, None) == bdc.BDC_ERR_CUDA
