@@ -89,6 +89,7 @@ struct Plan {
     std::vector<size_t> off_mat_data;      // per matrix
     std::vector<size_t> off_height_nodes;  // per height, into the nodes area
     size_t off_mixed = 0, mixed_bytes = 0;
+    size_t off_leaflog = 0;                // leaf rotation logs (not with vals)
     size_t total = 0;
 };
 
@@ -176,6 +177,10 @@ Plan make_plan(int nmat, const int *ns, const bdc_opts &o, int vals = 0) {
     for (int mi = 0; mi < nmat; ++mi) {
         p.off_mat_data.push_back(off);
         off += per_matrix_bytes(std::max(ns[mi], 1), vals);
+    }
+    if (!vals && !p.leaves.empty()) {
+        p.off_leaflog = off;
+        off += align256(leaf_log_bytes(p.leafmax) * p.leaves.size());
     }
 #ifndef BDC_FP32
     if (o.prec != BDC_FP64 && !vals) {
@@ -489,7 +494,8 @@ int run_plan(const Plan &p, const bdc_opts &o, char *work, std::vector<MatDesc> 
     }
     {
         StageScope sc(st, BDC_STAGE_LEAF, p.leaves.empty() ? 0 : 1, 0.0);
-        if ((e = launch_leaves(dleaves, (int)p.leaves.size(), dmats, p.leafmax, 30, st)) != cudaSuccess)
+        if ((e = launch_leaves(dleaves, (int)p.leaves.size(), dmats, p.leafmax, 30, p.vals,
+                               p.vals ? nullptr : work + p.off_leaflog, st)) != cudaSuccess)
             return note(e);
     }
     const int pairs = (o.prec == BDC_MIXED_EXACT) ? (o.slices * (o.slices + 1)) / 2

@@ -187,8 +187,10 @@ __device__ __forceinline__ void set_error(int *info, int code) {
 // ------------------------------------------------------ host-side launchers
 // (each returns cudaGetLastError() of its launches)
 cudaError_t launch_scale(const MatDesc *mats, int nmat, int nmax, cudaStream_t st);
+// leaves: `log` = leaf_log_bytes(leafmax) per leaf (unused, may be null, when vals)
+size_t leaf_log_bytes(int leafmax);
 cudaError_t launch_leaves(const NodeDesc *leaves, int nleaves, const MatDesc *mats, int leafmax,
-                          int max_sweeps, cudaStream_t st);
+                          int max_sweeps, int vals, void *log, cudaStream_t st);
 cudaError_t launch_merge_prep(const NodeDesc *nodes, int nnodes, const MatDesc *mats,
                               NodeState *state, GemmProb *probs, int mmax, int scans, cudaStream_t st);
 cudaError_t launch_merge_gather(const NodeDesc *nodes, int nnodes, const MatDesc *mats,

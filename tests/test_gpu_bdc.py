@@ -204,3 +204,26 @@ def test_fp32_start_parity_and_fp64_iterations(bdc, kind, seed):
     print(f"{kind}: FP64 steps per root without / with FP32 start {its[False]:.3f} / {its[True]:.3f}")
     if kind != "clustered":
         assert its[True] <= 0.7 * its[False], its
+
+
+@pytest.mark.parametrize("entries", [0, 40, 1300])
+@pytest.mark.parametrize("kind", ["uniform", "graded"])
+def test_leaf_log_overflow_fallback(bdc, monkeypatch, entries, kind):
+    """Leaves whose rotation log would overflow are iterated by the vectors
+    kernel itself: with the log capacity lowered (all leaves overflow at 0
+    and 40 entries, some at 1300) the SVD still meets the FP64 bar and agrees
+    with the logged path."""
+    d, e = inputs.make(kind, 700, 21)
+    S0, _, _, _ = _run(bdc, d, e, leaf=16)
+    monkeypatch.setenv("BDC_LEAF_LOG_ENTRIES", str(entries))
+    _check_full(bdc, d, e, leaf=16)
+    S1, _, _, _ = _run(bdc, d, e, leaf=16)
+    assert float((S1 - S0).abs().max()) <= 1e-13 * 700 * float(S0[0])
+
+
+@pytest.mark.parametrize("leaf", [4, 7, 33, 64])
+def test_leaf_sizes_wide_range(bdc, leaf):
+    """Leaf sizes across the allowed range (log capacity and lane layout scale with L)."""
+    for kind, seed in (("uniform", 3), ("graded", 4)):
+        d, e = inputs.make(kind, 1000, seed)
+        _check_full(bdc, d, e, leaf=leaf)
