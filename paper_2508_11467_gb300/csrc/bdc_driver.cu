@@ -256,7 +256,7 @@ MatDesc carve(char *base, size_t off, int n, int vals = 0) {
 __global__ void k_scale(const MatDesc *__restrict__ mats) {
     __shared__ real_t sh[32];
     __shared__ int bad;
-    const MatDesc md = mats[blockIdx.x];
+    const MatDesc &md = mats[blockIdx.x];
     const int n = md.n;
     if (threadIdx.x == 0) bad = 0;
     __syncthreads();
@@ -298,14 +298,14 @@ __global__ void k_info(const MatDesc *__restrict__ mats, int nmat, int *__restri
 
 // values only: S descending and unscaled
 __global__ void k_final_values(const MatDesc *__restrict__ mats) {
-    const MatDesc md = mats[blockIdx.y];
+    const MatDesc &md = mats[blockIdx.y];
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c < md.n) md.So[c] = md.D[md.Q[md.n - 1 - c]] * md.scale[0];
 }
 
 __global__ void k_final(const MatDesc *__restrict__ mats, int tiles_per_side) {
     __shared__ real_t tile[32][33];
-    const MatDesc md = mats[blockIdx.z];
+    const MatDesc &md = mats[blockIdx.z];
     const int n = md.n;
     const int tc = blockIdx.x % tiles_per_side, tj = blockIdx.x / tiles_per_side;
     const int c0 = tc * 32, j0 = tj * 32;
@@ -544,7 +544,11 @@ int run_plan(const Plan &p, const bdc_opts &o, char *work, std::vector<MatDesc> 
             const int gl = !mixed_here ? 1 : (o.prec == BDC_MIXED_EXACT && o.slices > 4) ? 4 : 3;
             StageScope sc(st, BDC_STAGE_GEMM, gl, 0.0);
             if (!mixed_here) {
-                e = launch_gemm64(dprobs, 4 * nn, mm + 1, mm, st);
+                // rows of the four products: nl + 1 (tops), m - nl - 1, m + sqre - nl - 1
+                int rows = 1;
+                for (const NodeDesc &nd : p.heights[h])
+                    rows = std::max(rows, std::max(nd.nl + 1, nd.m + nd.sqre - nd.nl - 1));
+                e = launch_gemm64(dprobs, 4 * nn, rows, mm, st);
             }
 #ifndef BDC_FP32
             else {

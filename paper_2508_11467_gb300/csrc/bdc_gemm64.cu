@@ -6,8 +6,9 @@
 // of 4 x 4 outputs, operands staged k-major in padded shared tiles (float4
 // reads), the next K step prefetched into registers.
 //
-// FP64 build: tensor-core FP64 (DMMA, mma.sync.m8n8k4.f64).  CTA tile 64 x 64, K step 16,
-// four warps of 32 x 32 (4 x 4 fragments of 8 x 8).  Shared tiles are padded
+// FP64 build: tensor-core FP64 (DMMA, mma.sync.m8n8k4.f64).  CTA tile 64 x 64
+// (32 x 32, 32 x 64 or 64 x 32 for small problems), K step 16, warps of
+// 32 x 32 (4 x 4 fragments of 8 x 8).  Shared tiles are padded
 // so that the fragment loads of a warp hit every bank exactly twice (the
 // minimum for 32 doubles).  The next K step is prefetched into registers while
 // the current one is multiplied.  Problems whose actual size (known only on
@@ -89,9 +90,7 @@ __global__ void __launch_bounds__(256) k_gemm32(const GemmProb *__restrict__ pro
     }
 }
 #else
-constexpr int BM = 64, BN = 64, BK = 16;
-constexpr int SA = BM + 8;   // As[k][m] row stride (doubles)
-constexpr int SB = BK + 4;   // Bs[n][k] row stride
+constexpr int BK = 16;
 
 __device__ __forceinline__ void dmma(double (&c)[2], double a, double b) {
     asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
@@ -99,14 +98,22 @@ __device__ __forceinline__ void dmma(double (&c)[2], double a, double b) {
                  : "d"(a), "d"(b));
 }
 
-__global__ void __launch_bounds__(128) k_gemm64(const GemmProb *__restrict__ probs, int tilesN) {
+// CTA tile (32 WM) x (32 WN): WM x WN warps of 32 x 32 each; the small
+// tiles serve merges whose blocks are a few dozen rows (a 64 x 64 tile
+// there multiplies mostly zeros at GB300's modest FP64 tensor rate)
+template <int WM, int WN>
+__global__ void __launch_bounds__(32 * WM * WN) k_gemm64(const GemmProb *__restrict__ probs, int tilesN) {
+    constexpr int BM = 32 * WM, BN = 32 * WN, T = 32 * WM * WN;
+    constexpr int SA = BM + 8;   // As[k][m] row stride (doubles)
+    constexpr int SB = BK + 4;   // Bs[n][k] row stride
+    constexpr int LA = BM * BK / T, LB = BN * BK / T;   // elements per thread
     __shared__ double As[BK * SA];
     __shared__ double Bs[BN * SB];
     const GemmProb pr = probs[blockIdx.y];
     const int m0 = (blockIdx.x / tilesN) * BM, n0 = (blockIdx.x % tilesN) * BN;
     if (m0 >= pr.M || n0 >= pr.N) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    const int wm = (warp / WN) * 32, wn = (warp % WN) * 32;
     const int g = lane >> 2, tg = lane & 3;
     const double *__restrict__ A = pr.A;
     const double *__restrict__ B = pr.B;
@@ -118,26 +125,34 @@ __global__ void __launch_bounds__(128) k_gemm64(const GemmProb *__restrict__ pro
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j][0] = acc[i][j][1] = 0.0;
 
-    // global -> register staging: A tile (64 m x 16 k), B tile (16 k x 64 n)
-    double ra[8], rb[8];
+    // global -> register staging: A tile (BM m x BK k), B tile (BK k x BN n)
+    double ra[LA], rb[LB];
     auto load = [&](int k0) {
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
-            const int idx = tid + r * 128;       // 0..1023
-            const int am = idx & 63, ak = idx >> 6;
+        for (int r = 0; r < LA; ++r) {
+            const int idx = tid + r * T;
+            const int am = idx % BM, ak = idx / BM;
             const int gm = m0 + am, gk = k0 + ak;
             ra[r] = (gm < M && gk < K) ? A[(size_t)gk * lda + gm] : 0.0;
-            const int bk = idx & 15, bn = idx >> 4;
-            const int gn = n0 + bn, gk2 = k0 + bk;
-            rb[r] = (gn < N && gk2 < K) ? B[(size_t)gn * ldb + gk2] : 0.0;
+        }
+#pragma unroll
+        for (int r = 0; r < LB; ++r) {
+            const int idx = tid + r * T;
+            const int bk = idx % BK, bn = idx / BK;
+            const int gn = n0 + bn, gk = k0 + bk;
+            rb[r] = (gn < N && gk < K) ? B[(size_t)gn * ldb + gk] : 0.0;
         }
     };
     auto store = [&]() {
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
-            const int idx = tid + r * 128;
-            As[(idx >> 6) * SA + (idx & 63)] = ra[r];
-            Bs[(idx >> 4) * SB + (idx & 15)] = rb[r];
+        for (int r = 0; r < LA; ++r) {
+            const int idx = tid + r * T;
+            As[(idx / BM) * SA + (idx % BM)] = ra[r];
+        }
+#pragma unroll
+        for (int r = 0; r < LB; ++r) {
+            const int idx = tid + r * T;
+            Bs[(idx / BK) * SB + (idx % BK)] = rb[r];
         }
     };
     load(0);
@@ -180,14 +195,24 @@ __global__ void __launch_bounds__(128) k_gemm64(const GemmProb *__restrict__ pro
 
 cudaError_t launch_gemm64(const GemmProb *probs, int nprobs, int mmax_rows, int nmax_cols, cudaStream_t st) {
     if (nprobs <= 0 || mmax_rows <= 0 || nmax_cols <= 0) return cudaSuccess;
-    const int tilesN = (nmax_cols + BN - 1) / BN, tilesM = (mmax_rows + BM - 1) / BM;
+#ifdef BDC_FP32
+    const int bm = BM, bn = BN;
+#else
+    // 32-row / 32-column tiles when the problems are that small
+    const int wm = mmax_rows <= 32 ? 1 : 2, wn = nmax_cols <= 32 ? 1 : 2;
+    const int bm = 32 * wm, bn = 32 * wn;
+#endif
+    const int tilesN = (nmax_cols + bn - 1) / bn, tilesM = (mmax_rows + bm - 1) / bm;
     for (int p0 = 0; p0 < nprobs; p0 += 65535) {
         const int np = (nprobs - p0 < 65535) ? nprobs - p0 : 65535;
         dim3 grid((unsigned)tilesN * tilesM, np);
 #ifdef BDC_FP32
         k_gemm32<<<grid, 256, 0, st>>>(probs + p0, tilesN);
 #else
-        k_gemm64<<<grid, 128, 0, st>>>(probs + p0, tilesN);
+        if (wm == 1 && wn == 1) k_gemm64<1, 1><<<grid, 32, 0, st>>>(probs + p0, tilesN);
+        else if (wm == 1) k_gemm64<1, 2><<<grid, 64, 0, st>>>(probs + p0, tilesN);
+        else if (wn == 1) k_gemm64<2, 1><<<grid, 64, 0, st>>>(probs + p0, tilesN);
+        else k_gemm64<2, 2><<<grid, 128, 0, st>>>(probs + p0, tilesN);
 #endif
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;

@@ -13,7 +13,7 @@
 // charges an instruction the same whether 1 or 32 lanes issue it, so the
 // chain is not run by one lane of a warp while 31 wait.  Two kernels:
 //   k_leaf_rotations  the QR iteration on d and e alone, one leaf per lane
-//                     (ceil(leaves / SMs) leaves per warp, one warp per SM),
+//                     (ceil(leaves / (4 SMs)) leaves per warp),
 //                     writing every action and its rotations to a per-leaf
 //                     log;
 //   k_leaf_vectors    one warp per leaf: replays the log on U and V (each lane
@@ -76,6 +76,34 @@ __device__ __forceinline__ void leaf_rot(real_t f, real_t g, real_t &c, real_t &
     }
     make_rot(f, g, c, s, r);
 #endif
+}
+
+// |x| as an ordered integer: for non-negative values the bit patterns sort
+// like the values, so magnitude tests need no floating-point instruction
+#ifdef BDC_FP32
+typedef int rbits_t;
+constexpr int kMant = 23, kEpsExp = 23;   // kEps = 2^-23
+__device__ __forceinline__ rbits_t abits(real_t x) { return __float_as_int(x) & 0x7fffffff; }
+#else
+typedef long long rbits_t;
+constexpr int kMant = 52, kEpsExp = 52;   // kEps = 2^-52
+__device__ __forceinline__ rbits_t abits(real_t x) { return __double_as_longlong(x) & 0x7fffffffffffffffll; }
+#endif
+
+// The leaf's negligibility test |e| <= kEps (|d1| + |d2|) or |e| <= tabs,
+// decided on the bit patterns where that is exact (|e| > 2^(1-kEpsExp)
+// max|d| is never negligible, |e| <= 2^-kEpsExp max|d| always is) and in
+// floating point only in the factor-2 band between (same results as the
+// floating-point test alone).
+__device__ __forceinline__ bool negligible(real_t e, real_t d1, real_t d2, rbits_t tabs) {
+    const rbits_t be = abits(e);
+    if (be <= tabs) return true;
+    const rbits_t b1 = abits(d1), b2 = abits(d2), bm = b1 > b2 ? b1 : b2;
+    if (bm >= ((rbits_t)(kEpsExp + 1) << kMant)) {
+        if (be > bm - ((rbits_t)(kEpsExp - 1) << kMant)) return false;
+        if (be <= bm - ((rbits_t)kEpsExp << kMant)) return true;
+    }
+    return fabs(e) <= kEps * (fabs(d1) + fabs(d2));
 }
 
 // ---------------------------------------------------------------- kernel 1
@@ -148,28 +176,31 @@ __global__ void __launch_bounds__(32) k_leaf_rotations(const NodeDesc *__restric
         act(ACT_SQRE, m, 0);
     }
 
-    // leaf-local norm for the zero-diagonal threshold
-    real_t bn = R(0);
-    for (int i = 0; i < m; ++i) bn = fmax(bn, fabs(dd[i]));
-    for (int i = 0; i < m - 1; ++i) bn = fmax(bn, fabs(ee[i]));
-    const real_t dtiny = kEps * bn;
+    // leaf-local norm for the zero-diagonal threshold (max of the bit patterns)
+    rbits_t bb = 0;
+    for (int i = 0; i < m; ++i) { const rbits_t b = abits(dd[i]); bb = b > bb ? b : bb; }
+    for (int i = 0; i < m - 1; ++i) { const rbits_t b = abits(ee[i]); bb = b > bb ? b : bb; }
+#ifdef BDC_FP32
+    const real_t dtiny = kEps * __int_as_float(bb);
+#else
+    const real_t dtiny = kEps * __longlong_as_double(bb);
+#endif
+    const rbits_t tiny_b = abits(dtiny), tabs = abits(dtiny * kEps);
 
     long long budget = (long long)max_sweeps * (m > 0 ? m : 1);
     int info = 0, hi = m - 1;
     while (!ovf && hi > 0) {
-        if (fabs(ee[hi - 1]) <= kEps * (fabs(dd[hi - 1]) + fabs(dd[hi])) || fabs(ee[hi - 1]) <= dtiny * kEps) {
+        if (negligible(ee[hi - 1], dd[hi - 1], dd[hi], tabs)) {
             ee[hi - 1] = R(0);
             --hi;
             continue;
         }
         int lo = hi - 1;
-        while (lo > 0 && fabs(ee[lo - 1]) > kEps * (fabs(dd[lo - 1]) + fabs(dd[lo])) &&
-               fabs(ee[lo - 1]) > dtiny * kEps)
-            --lo;
+        while (lo > 0 && !negligible(ee[lo - 1], dd[lo - 1], dd[lo], tabs)) --lo;
         if (lo > 0) ee[lo - 1] = R(0);
         int kz = -1;
         for (int k = lo; k <= hi; ++k)
-            if (fabs(dd[k]) <= dtiny) { kz = k; break; }
+            if (abits(dd[k]) <= tiny_b) { kz = k; break; }
         if (kz < 0 && budget-- <= 0) {
             int cnt = 0;
             for (int i = 0; i < hi; ++i) cnt += (ee[i] != R(0));
@@ -217,30 +248,40 @@ __global__ void __launch_bounds__(32) k_leaf_rotations(const NodeDesc *__restric
         const real_t sg = (delta >= R(0)) ? R(1) : R(-1);
         const real_t den = delta + sg * hypot(delta, t12);
         const real_t mu = (den != R(0)) ? t22 - t12 * t12 / den : t22;
-        real_t y = dd[lo] * dd[lo] - mu;
-        real_t z = dd[lo] * ee[lo];
+        // the chain runs in registers: dk, ek are d_k, e_k as updated by the
+        // previous step, dk1, ek1 the untouched d_{k+1}, e_{k+1}, loaded one
+        // step ahead; every store is final (e_{k-1} takes the next step's r)
+        real_t dk = dd[lo], ek = ee[lo];
+        real_t dk1 = dd[lo + 1], ek1 = (lo + 1 < hi) ? ee[lo + 1] : R(0);
+        real_t y = dk * dk - mu;
+        real_t z = dk * ek;
         for (int k = lo; k < hi; ++k) {
+            const real_t dk2 = (k + 2 <= hi) ? dd[k + 2] : R(0);
+            const real_t ek2 = (k + 2 < hi) ? ee[k + 2] : R(0);
             real_t c, s, r;
             leaf_rot(y, z, c, s, r);
             if (k > lo) ee[k - 1] = r;
-            real_t dk = dd[k], ek = ee[k], dk1 = dd[k + 1];
-            dd[k] = c * dk + s * ek;
-            ee[k] = -s * dk + c * ek;
+            const real_t dka = c * dk + s * ek;
+            const real_t eka = -s * dk + c * ek;
             const real_t bulge = s * dk1;
-            dd[k + 1] = c * dk1;
+            const real_t dk1a = c * dk1;
             put(c, s);
             if (vals) vrot(k, k + 1, c, s);
-            leaf_rot(dd[k], bulge, c, s, r);
+            leaf_rot(dka, bulge, c, s, r);
             dd[k] = r;
-            ek = ee[k]; dk1 = dd[k + 1];
-            ee[k] = c * ek + s * dk1;
-            dd[k + 1] = -s * ek + c * dk1;
+            const real_t ekb = c * eka + s * dk1a;      // e_k after this step (y of the next)
+            const real_t dk1b = -s * eka + c * dk1a;    // d_{k+1} after this step
             if (k < hi - 1) {
-                const real_t ek1 = ee[k + 1];
                 z = s * ek1;
-                ee[k + 1] = c * ek1;
-                y = ee[k];
+                ek = c * ek1;
+                y = ekb;
+            } else {
+                ee[k] = ekb;
+                dd[k + 1] = dk1b;
             }
+            dk = dk1b;
+            dk1 = dk2;
+            ek1 = ek2;
             if (!vals) { cs[nc] = c; cs[nc + 1] = s; }
             nc += 2;
         }
@@ -584,13 +625,11 @@ cudaError_t launch_leaves(const NodeDesc *leaves, int nleaves, const MatDesc *ma
                           int max_sweeps, int vals, void *log, cudaStream_t st) {
     if (nleaves <= 0) return cudaSuccess;
     const int L = leafmax;
-    // FP64: the sweeps are bound by the SM's FP64 pipe, one warp per SM runs
-    // them at the shortest latency; FP32: four warps per SM hide latency
-#ifdef BDC_FP32
+    // up to four warps per SM, one per sub-partition: the chain of one leaf
+    // is bound by the issue rate of its sub-partition's FP64 unit, so the
+    // leaves are spread over as many sub-partitions as possible before they
+    // share a warp
     const int target = 4 * leaf_sm_count();
-#else
-    const int target = leaf_sm_count();
-#endif
     // log capacity: cs_cap(L) entries; the environment variable
     // BDC_LEAF_LOG_ENTRIES can lower it (tests use it to send leaves through
     // the fallback iteration of k_leaf_vectors)

@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
     __shared__ int wsum[PREP_THREADS / 32 + 1];
     __shared__ real_t dsum[PREP_THREADS / 32 + 1];
     const NodeDesc nd = nodes[blockIdx.x];
-    const MatDesc md = mats[nd.mat];
+    const MatDesc &md = mats[nd.mat];
     const int m = nd.m, nl = nd.nl, nr = m - nl - 1, sqre = nd.sqre, mc = m + sqre;
     const int r0 = nd.r0, r0L = r0, r0R = r0 + nl + 1;
     const long long ld = md.n;
@@ -466,7 +466,7 @@ __global__ void __launch_bounds__(128) k_merge_gather(const NodeDesc *__restrict
     const int node = blockIdx.x / mmax, p = blockIdx.x % mmax;
     const NodeDesc nd = nodes[node];
     if (p >= nd.m) return;
-    const MatDesc md = mats[nd.mat];
+    const MatDesc &md = mats[nd.mat];
     const NodeState ns = state[nd.id];
     const int m = nd.m, nl = nd.nl, sqre = nd.sqre, mc = m + sqre, r0 = nd.r0;
     const int r = md.role[r0 + p], code = r & 15;
@@ -600,7 +600,7 @@ __global__ void __launch_bounds__(128) k_gather_rows(const NodeDesc *__restrict_
     if (node >= nnodes) return;
     const NodeDesc nd = nodes[node];
     if (p >= nd.m) return;
-    const MatDesc md = mats[nd.mat];
+    const MatDesc &md = mats[nd.mat];
     const NodeState ns = state[nd.id];
     const int m = nd.m, nl = nd.nl, sqre = nd.sqre, r0 = nd.r0;
     const int r = md.role[r0 + p], code = r & 15;
@@ -659,7 +659,7 @@ __global__ void __launch_bounds__(256) k_merge_finish(const NodeDesc *__restrict
                                                       const MatDesc *__restrict__ mats,
                                                       const NodeState *__restrict__ state) {
     const NodeDesc nd = nodes[blockIdx.x];
-    const MatDesc md = mats[nd.mat];
+    const MatDesc &md = mats[nd.mat];
     const NodeState ns = state[nd.id];
     const int r0 = nd.r0, N = ns.N, ndef = ns.ndef;
     const real_t *om = md.omega + r0, *dv = md.dval + r0;

@@ -1,13 +1,14 @@
 // Merge step of Algorithm 2, part (b) (lasd3 without the products):
 //
-// k_secular  one warp per root of the secular equation (Eq. M-svd-val)
+// k_secular  one lane group per root of the secular equation (Eq. M-svd-val)
 //            f(w) = 1 + sum_j z_j^2 / (d_j^2 - w^2), root i in (d_i, d_{i+1}).
 //            The unknown is held relative to the nearer pole d_o as
 //            x = w^2 - d_o^2 (then tau = w - d_o), so d_j^2 - w^2 is formed as
 //            (d_j - d_o)(d_j + d_o) - x without cancellation.  Each step fits
 //            the two nearest poles with a rational model matching f and f'
 //            (a "middle way" step in the sense of R.-C. Li), safeguarded by a
-//            bracket; lanes split the pole sums and reduce with shuffles.
+//            bracket; the group's lanes (4 to 32, about 16 poles each)
+//            split the pole sums and reduce with shuffles.
 //            Stopping rule: |f| <= 16 eps (1 + sum |terms|), or a step below
 //            4 eps |x|.  Optionally the start comes from a small MLP
 //            (bdc_mlp.cuh) instead of the interval midpoint; the stopping
@@ -33,32 +34,61 @@ namespace BDC_NS {
 
 namespace {
 
+// A root (or Loewner product) is served by a group of G lanes (G = 4, 8,
+// 16 or 32, aligned within the warp): the per-pole work is split over the
+// group and the scalar steps of the iteration are shared by G lanes, not
+// 32.  Group reductions shuffle within the group's own lanes.
+template <int G>
+__device__ __forceinline__ unsigned group_mask() {
+    if (G == 32) return 0xffffffffu;
+    return ((1u << (G & 31)) - 1u) << ((threadIdx.x & 31) & ~(G - 1));
+}
+template <int G, typename T>
+__device__ __forceinline__ T group_sum(T v) {
+    const unsigned m = group_mask<G>();
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(m, v, o);
+    return v;
+}
+template <int G, typename T>
+__device__ __forceinline__ T group_prod(T v) {
+    const unsigned m = group_mask<G>();
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v *= __shfl_xor_sync(m, v, o);
+    return v;
+}
+// lanes per group for a merge with N survivors: about 16 poles per lane
+__device__ __forceinline__ int group_size(int N) {
+    return N <= 64 ? 4 : N <= 128 ? 8 : N <= 256 ? 16 : 32;
+}
+
 struct Sums {
     real_t psi, dpsi, phi, dphi;
 };
 
 // pole sums at x = w^2 - d_o^2; left group j <= i (psi < 0), right j > i
+template <int G>
 __device__ __forceinline__ Sums pole_sums(const real_t *__restrict__ d, const real_t *__restrict__ z,
                                           int N, int i, real_t dor, real_t x, int lane) {
     Sums s{R(0.0), R(0.0), R(0.0), R(0.0)};
-    for (int j = lane; j <= i; j += 32) {
+    for (int j = lane; j <= i; j += G) {
         const real_t dj = d[j], zj = z[j];
         const real_t del = (dj - dor) * (dj + dor) - x;
         const real_t t = zj / del;
         s.psi = fma(zj, t, s.psi);
         s.dpsi = fma(t, t, s.dpsi);
     }
-    for (int j = i + 1 + lane; j < N; j += 32) {
+    for (int j = i + 1 + lane; j < N; j += G) {
         const real_t dj = d[j], zj = z[j];
         const real_t del = (dj - dor) * (dj + dor) - x;
         const real_t t = zj / del;
         s.phi = fma(zj, t, s.phi);
         s.dphi = fma(t, t, s.dphi);
     }
-    s.psi = warp_sum(s.psi);
-    s.dpsi = warp_sum(s.dpsi);
-    s.phi = warp_sum(s.phi);
-    s.dphi = warp_sum(s.dphi);
+    s.psi = group_sum<G>(s.psi);
+    s.dpsi = group_sum<G>(s.dpsi);
+    s.phi = group_sum<G>(s.phi);
+    s.dphi = group_sum<G>(s.dphi);
     return s;
 }
 
@@ -74,9 +104,10 @@ struct RootState {
 
 // Safeguarded rational iteration from r.x; returns the iterations used or
 // -1 when max_iter did not suffice.  All lanes return the same result.
+template <int G>
 __device__ __forceinline__ int root_iterate(const real_t *__restrict__ d, const real_t *__restrict__ z, int N, int i, bool last,
                             int max_iter, RootState &r) {
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & (G - 1);
     int it = 0;
     for (;;) {
         const real_t f = R(1.0) + r.s.psi + r.s.phi;
@@ -122,7 +153,7 @@ __device__ __forceinline__ int root_iterate(const real_t *__restrict__ d, const 
                 r.o = i; r.dor = r.dl; r.x += D2; r.lo += D2; r.hi += D2; r.lamL = R(0.0); r.lamR = D2;
             }
         }
-        r.s = pole_sums(d, z, N, i, r.dor, r.x, lane);
+        r.s = pole_sums<G>(d, z, N, i, r.dor, r.x, lane);
         if (fabs(step) <= R(4.0) * kEps * fabs(r.x)) break;
     }
     return it;
@@ -136,9 +167,10 @@ __device__ __forceinline__ int root_iterate(const real_t *__restrict__ d, const 
 // then finishes from there.  Other poles within ~2^-23 relative of the
 // origin are only approximate in FP32: that costs FP64 steps, never
 // accuracy.  Updates r.x (r.lo, r.hi untouched); all lanes agree.
+template <int G>
 __device__ __forceinline__ void fp32_phase(const float *__restrict__ d32, const float *__restrict__ z32, int N,
                                            int i, RootState &r) {
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & (G - 1);
     const float D2 = (float)(r.lamR - r.lamL);
     const float lamL = (float)r.lamL, lamR = (float)r.lamR;
     const float dor = d32[r.o];
@@ -146,14 +178,14 @@ __device__ __forceinline__ void fp32_phase(const float *__restrict__ d32, const 
     const float di = (r.o == i) ? 0.f : -D2, di1 = (r.o == i) ? D2 : 0.f;   // d_i^2 - d_o^2, d_{i+1}^2 - d_o^2
     for (int it = 0; it < 6; ++it) {
         float psi = 0.f, dpsi = 0.f, phi = 0.f, dphi = 0.f;
-        for (int j = lane; j < N; j += 32) {
+        for (int j = lane; j < N; j += G) {
             const float dj = d32[j], zj = z32[j];
             const float c = (j == i) ? di : (j == i + 1) ? di1 : (dj - dor) * (dj + dor);
             const float t = zj / (c - x);
             if (j <= i) { psi = fmaf(zj, t, psi); dpsi = fmaf(t, t, dpsi); }
             else { phi = fmaf(zj, t, phi); dphi = fmaf(t, t, dphi); }
         }
-        psi = warp_sum(psi); dpsi = warp_sum(dpsi); phi = warp_sum(phi); dphi = warp_sum(dphi);
+        psi = group_sum<G>(psi); dpsi = group_sum<G>(dpsi); phi = group_sum<G>(phi); dphi = group_sum<G>(dphi);
         const float f = 1.f + psi + phi;
         if (!(f == f)) return;                               // no usable FP32 information
         if (f > 0.f) hi = x; else lo = x;
@@ -187,10 +219,11 @@ __device__ __forceinline__ void fp32_phase(const float *__restrict__ d32, const 
 // FP32 copies for fp32_phase, which then also replaces the FP64 midpoint
 // evaluation that picks the origin.  A start that may sit on the farther
 // half is polished from the nearer pole at the end.
+template <int G>
 __device__ __forceinline__ int solve_root(const real_t *__restrict__ d, const real_t *__restrict__ z, int N, int i,
                           int max_iter, real_t zz, int &org_out, real_t &tau_out, real_t &x_out, real_t vstart,
                           const float *__restrict__ d32 = nullptr, const float *__restrict__ z32 = nullptr) {
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & (G - 1);
     if (N == 1) {
         org_out = 0;
         tau_out = fabs(z[0]);
@@ -212,12 +245,12 @@ __device__ __forceinline__ int solve_root(const real_t *__restrict__ d, const re
         const float xm = (float)(h * (R(2.0) * dl + h)), D2f = (float)((du - dl) * (du + dl));
         const float di = (float)dl;
         float s = 0.f;
-        for (int j = lane; j < N; j += 32) {
+        for (int j = lane; j < N; j += G) {
             const float dj = d32[j], zj = z32[j];
             const float c = (j == i) ? 0.f : (j == i + 1) ? D2f : (dj - di) * (dj + di);
             s = fmaf(zj, zj / (c - xm), s);
         }
-        s = warp_sum(s);
+        s = group_sum<G>(s);
         vstart = (1.f + s >= 0.f) ? R(0.25) : R(-0.25);     // the midpoint seen from the chosen pole
     }
     if (use_mlp) {
@@ -228,12 +261,12 @@ __device__ __forceinline__ int solve_root(const real_t *__restrict__ d, const re
             r.o = i + 1; r.dor = du; r.lo = -D2; r.hi = R(0.0); r.lamL = -D2; r.lamR = R(0.0); r.x = vstart * D2;
         }
         if (!(r.x > r.lo && r.x < r.hi)) r.x = R(0.5) * (r.lo + r.hi);
-        if (pre32) fp32_phase(d32, z32, N, i, r);
-        r.s = pole_sums(d, z, N, i, r.dor, r.x, lane);
+        if (pre32) fp32_phase<G>(d32, z32, N, i, r);
+        r.s = pole_sums<G>(d, z, N, i, r.dor, r.x, lane);
     } else if (!last) {
         // sign of f at the interval midpoint picks the nearer pole as origin
         const real_t xmid = h * (R(2.0) * dl + h);
-        r.s = pole_sums(d, z, N, i, dl, xmid, lane);
+        r.s = pole_sums<G>(d, z, N, i, dl, xmid, lane);
         const real_t fmid = R(1.0) + r.s.psi + r.s.phi;
         if (fmid >= R(0.0)) {
             r.o = i; r.dor = dl; r.lo = R(0.0); r.hi = xmid;
@@ -248,9 +281,9 @@ __device__ __forceinline__ int solve_root(const real_t *__restrict__ d, const re
         r.o = i; r.dor = dl; r.lo = R(0.0); r.hi = zz;
         r.lamL = R(0.0); r.lamR = R(0.0);
         r.x = R(0.5) * zz;
-        r.s = pole_sums(d, z, N, i, r.dor, r.x, lane);
+        r.s = pole_sums<G>(d, z, N, i, r.dor, r.x, lane);
     }
-    int it = root_iterate(d, z, N, i, last, max_iter, r);
+    int it = root_iterate<G>(d, z, N, i, last, max_iter, r);
     if (use_mlp && it >= 0) {
         // the origin must be the nearer pole (no cancellation in d_j - w)
         const real_t D2 = (du - dl) * (du + dl);
@@ -262,8 +295,8 @@ __device__ __forceinline__ int solve_root(const real_t *__restrict__ d, const re
         }
         if (sw) {
             if (!(r.x > r.lo && r.x < r.hi)) r.x = R(0.5) * (r.lo + r.hi);
-            r.s = pole_sums(d, z, N, i, r.dor, r.x, lane);
-            const int it2 = root_iterate(d, z, N, i, last, max_iter, r);
+            r.s = pole_sums<G>(d, z, N, i, r.dor, r.x, lane);
+            const int it2 = root_iterate<G>(d, z, N, i, last, max_iter, r);
             it = (it2 < 0) ? -1 : it + 1 + it2;
         }
     }
@@ -343,7 +376,7 @@ __global__ void __launch_bounds__(128) k_root_start(const NodeDesc *__restrict__
     const NodeDesc nd = nodes[node];
     const int N = state[nd.id].N;
     if (i >= N - 1) return;
-    const MatDesc md = mats[nd.mat];
+    const MatDesc &md = mats[nd.mat];
     const double *d = md.dM + nd.r0, *z = md.zM + nd.r0;
     FarSums L, R;
     far_from_scans(md.pz + nd.r0, md.n, N, i, L, R);
@@ -360,27 +393,19 @@ __global__ void __launch_bounds__(128) k_root_start(const NodeDesc *__restrict__
 }
 #endif  // BDC_FP32
 
-__global__ void __launch_bounds__(256, 2) k_secular(const NodeDesc *__restrict__ nodes,
-                                                 const MatDesc *__restrict__ mats,
-                                                 NodeState *__restrict__ state, int mmax,
-                                                 int max_iter, int nnodes, int seed_mode, int fp32_start) {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    const int node = warp / mmax, i = warp % mmax;
-    if (node >= nnodes) return;
-    const NodeDesc nd = nodes[node];
-    const NodeState ns = state[nd.id];
-    if (i >= ns.N) return;
-    const MatDesc md = mats[nd.mat];
+// root i of one merge by a group of G lanes
+template <int G>
+__device__ __forceinline__ void secular_group(const NodeDesc &nd, const MatDesc &md, NodeState *__restrict__ state,
+                                              int N, real_t zz, int i, int max_iter, int seed_mode,
+                                              int fp32_start) {
     const real_t *d = md.dM + nd.r0, *z = md.zM + nd.r0;
-    const int N = ns.N;
-    const real_t zz = ns.rho;                       // sum z^2 (computed by the merge prep)
     real_t vstart = R(NAN);                                    // NaN: plain start
     if (seed_mode != BDC_SEED_PLAIN && i < N - 1) vstart = md.ystart[nd.r0 + i];
     int o;
     real_t tau, x;
-    const int it = solve_root(d, z, N, i, max_iter, zz, o, tau, x, vstart,
-                              fp32_start ? md.d32 + nd.r0 : nullptr, fp32_start ? md.z32 + nd.r0 : nullptr);
-    if (lane == 0) {
+    const int it = solve_root<G>(d, z, N, i, max_iter, zz, o, tau, x, vstart,
+                                 fp32_start ? md.d32 + nd.r0 : nullptr, fp32_start ? md.z32 + nd.r0 : nullptr);
+    if ((threadIdx.x & (G - 1)) == 0) {
         md.org[nd.r0 + i] = o;
         md.tau[nd.r0 + i] = tau;
         md.omega[nd.r0 + i] = d[o] + tau;
@@ -399,6 +424,30 @@ __global__ void __launch_bounds__(256, 2) k_secular(const NodeDesc *__restrict__
             }
         }
 #endif
+    }
+}
+
+// Warp w of a node (mmax warps per node) serves roots w * (32 / G) + (lane / G),
+// G = group_size(N) from the node's survivor count, known only here.
+__global__ void __launch_bounds__(256, 2) k_secular(const NodeDesc *__restrict__ nodes,
+                                                 const MatDesc *__restrict__ mats,
+                                                 NodeState *__restrict__ state, int mmax,
+                                                 int max_iter, int nnodes, int seed_mode, int fp32_start) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int node = warp / mmax, w = warp % mmax;
+    if (node >= nnodes) return;
+    const NodeDesc nd = nodes[node];
+    const NodeState ns = state[nd.id];
+    const int N = ns.N, G = group_size(N), per = 32 / G;
+    const int i = w * per + lane / G;
+    if (i >= N) return;                              // whole groups leave together
+    const MatDesc &md = mats[nd.mat];
+    const real_t zz = ns.rho;                        // sum z^2 (computed by the merge prep)
+    switch (G) {
+    case 4: secular_group<4>(nd, md, state, N, zz, i, max_iter, seed_mode, fp32_start); break;
+    case 8: secular_group<8>(nd, md, state, N, zz, i, max_iter, seed_mode, fp32_start); break;
+    case 16: secular_group<16>(nd, md, state, N, zz, i, max_iter, seed_mode, fp32_start); break;
+    default: secular_group<32>(nd, md, state, N, zz, i, max_iter, seed_mode, fp32_start); break;
     }
 }
 
@@ -427,7 +476,7 @@ __global__ void __launch_bounds__(256, 2) k_secular_single(int N, const double *
     }
     int o;
     double t, x;
-    const int it = solve_root(d, z, N, i, max_iter, zz, o, t, x, ystart);
+    const int it = solve_root<32>(d, z, N, i, max_iter, zz, o, t, x, ystart);
     if (lane == 0) {
         org[i] = o;
         tau[i] = t;
@@ -460,12 +509,18 @@ __global__ void __launch_bounds__(256) k_mlp_features_single(int N, const double
 
 // |z~_i|^2 of Eq. (bdc-zi), 0-based: (w_{N-1}^2 - d_i^2) *
 //   prod_{k<i} (w_k^2 - d_i^2)/(d_k^2 - d_i^2) * prod_{i<=k<N-1} (w_k^2 - d_i^2)/(d_{k+1}^2 - d_i^2)
+// by a group of G lanes.  FP64: numerators and denominators are multiplied
+// separately and divided once per 8 factors (a division costs about nine
+// FP64 operations on GB300), sooner when either product falls below
+// 2^-300; every factor of the product lies in (0, 1] by interlacing.
+template <int G>
 __device__ __forceinline__ real_t lowner_one(const real_t *__restrict__ d, const real_t *__restrict__ z,
                                              const int *__restrict__ org, const real_t *__restrict__ tau,
                                              int N, int i, int lane) {
     const real_t di = d[i];
     real_t prod = R(1.0);
-    for (int k = lane; k < N - 1; k += 32) {
+#ifdef BDC_FP32
+    for (int k = lane; k < N - 1; k += G) {
         const int ok = org[k];
         const real_t wmd = (d[ok] - di) + tau[k];        // w_k - d_i
         const real_t wpd = d[ok] + tau[k] + di;          // w_k + d_i
@@ -473,8 +528,27 @@ __device__ __forceinline__ real_t lowner_one(const real_t *__restrict__ d, const
         const real_t den = (d[kk] - di) * (d[kk] + di);
         prod *= (wmd * wpd) / den;
     }
-    for (int o = 16; o > 0; o >>= 1) prod *= __shfl_down_sync(0xffffffffu, prod, o);
-    prod = __shfl_sync(0xffffffffu, prod, 0);
+#else
+    double num = 1.0, den = 1.0;
+    int cnt = 0;
+    constexpr long long kLow = (long long)(1023 - 300) << 52;   // bits of 2^-300
+    for (int k = lane; k < N - 1; k += G) {
+        const int ok = org[k];
+        const double wmd = (d[ok] - di) + tau[k];        // w_k - d_i
+        const double wpd = d[ok] + tau[k] + di;          // w_k + d_i
+        const int kk = (k < i) ? k : k + 1;
+        num *= wmd * wpd;
+        den *= (d[kk] - di) * (d[kk] + di);
+        if (++cnt == 8 || (__double_as_longlong(num) & 0x7fffffffffffffffll) < kLow ||
+            (__double_as_longlong(den) & 0x7fffffffffffffffll) < kLow) {
+            prod *= num / den;
+            num = den = 1.0;
+            cnt = 0;
+        }
+    }
+    if (cnt) prod *= num / den;
+#endif
+    prod = group_prod<G>(prod);
     const int oN = org[N - 1];
     const real_t last = ((d[oN] - di) + tau[N - 1]) * (d[oN] + tau[N - 1] + di);
     const real_t zt = sqrt(fabs(last * prod));
@@ -485,15 +559,25 @@ __global__ void __launch_bounds__(256) k_lowner(const NodeDesc *__restrict__ nod
                                                 const MatDesc *__restrict__ mats,
                                                 const NodeState *__restrict__ state, int mmax, int nnodes) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    const int node = warp / mmax, i = warp % mmax;
+    const int node = warp / mmax, w = warp % mmax;
     if (node >= nnodes) return;
     const NodeDesc nd = nodes[node];
     const NodeState ns = state[nd.id];
-    if (i >= ns.N) return;
-    const MatDesc md = mats[nd.mat];
-    const int r0 = nd.r0;
-    const real_t zt = lowner_one(md.dM + r0, md.zM + r0, md.org + r0, md.tau + r0, ns.N, i, lane);
-    if (lane == 0) md.zt[r0 + i] = zt;
+    const int N = ns.N, G = group_size(N), per = 32 / G;
+    const int i = w * per + lane / G;
+    if (i >= N) return;                              // whole groups leave together
+    const MatDesc &md = mats[nd.mat];
+    const int r0 = nd.r0, gl = lane & (G - 1);
+    const real_t *d = md.dM + r0, *z = md.zM + r0, *tau = md.tau + r0;
+    const int *org = md.org + r0;
+    real_t zt;
+    switch (G) {
+    case 4: zt = lowner_one<4>(d, z, org, tau, N, i, gl); break;
+    case 8: zt = lowner_one<8>(d, z, org, tau, N, i, gl); break;
+    case 16: zt = lowner_one<16>(d, z, org, tau, N, i, gl); break;
+    default: zt = lowner_one<32>(d, z, org, tau, N, i, gl); break;
+    }
+    if (gl == 0) md.zt[r0 + i] = zt;
 }
 
 #ifndef BDC_FP32
@@ -501,7 +585,7 @@ __global__ void __launch_bounds__(256) k_lowner_single(int N, const double *d, c
                                                        const int *org, const double *tau, double *zt) {
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (i >= N) return;
-    const double v = lowner_one(d, z, org, tau, N, i, lane);
+    const double v = lowner_one<32>(d, z, org, tau, N, i, lane);
     if (lane == 0) zt[i] = v;
 }
 #endif
@@ -555,54 +639,77 @@ __global__ void __launch_bounds__(256) k_vectors(const NodeDesc *__restrict__ no
     const NodeDesc nd = nodes[node];
     const NodeState ns = state[nd.id];
     if (i >= ns.N) return;
-    const MatDesc md = mats[nd.mat];
+    const MatDesc &md = mats[nd.mat];
     const int r0 = nd.r0;
     const long long wb = (long long)r0 * md.wstride;
     vectors_one(md.dM + r0, md.zt + r0, ns.N, i, md.org[r0 + i], md.tau[r0 + i], md.invK + nd.kbase,
                 ns.Ktot, md.UM + wb + (size_t)i * ns.Ktot, md.VM + wb + (size_t)i * ns.Ktot, sh);
 }
 
-// the same with one warp per column (8 columns per CTA), for heights whose
-// merges are small: a whole CTA per short column is mostly idle threads
+// The same with a lane group per column (G = 4 to 32 lanes, about 16 rows
+// each), for heights whose merges have N <= 1024 survivors: each lane keeps
+// its entries v_j (j = lane, lane + G, ...) in registers between the norm and
+// the write, so every entry costs one division; rows are written at their K
+// positions (kposM), the padding rows [n1, P1) of the K order as zeros.
+template <int G, int T>
+__device__ __forceinline__ void vectors_group(const real_t *__restrict__ d, const real_t *__restrict__ zt,
+                                              const int *__restrict__ kpos, int N, int n1, int P1, real_t dor,
+                                              real_t tau, real_t *__restrict__ UMcol, real_t *__restrict__ VMcol,
+                                              int gl) {
+    real_t vr[T];
+    real_t sv = R(0.0), su = R(0.0);
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        const int j = gl + t * G;
+        real_t v = R(0.0);
+        if (j < N) {
+            const real_t dj = d[j];
+            v = zt[j] / (((dj - dor) - tau) * (dj + dor + tau));
+            const real_t u = (j == 0) ? -R(1.0) : dj * v;
+            sv = fma(v, v, sv);
+            su = fma(u, u, su);
+        }
+        vr[t] = v;
+    }
+    sv = group_sum<G>(sv);
+    su = group_sum<G>(su);
+    const real_t iv = R(1.0) / sqrt(sv), iu = R(1.0) / sqrt(su);
+    for (int p = n1 + gl; p < P1; p += G) { UMcol[p] = R(0.0); VMcol[p] = R(0.0); }
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        const int j = gl + t * G;
+        if (j < N) {
+            const int kp = kpos[j];
+            VMcol[kp] = vr[t] * iv;
+            UMcol[kp] = ((j == 0) ? -R(1.0) : d[j] * vr[t]) * iu;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) k_vectors_warp(const NodeDesc *__restrict__ nodes,
                                                       const MatDesc *__restrict__ mats,
                                                       const NodeState *__restrict__ state, int mmax,
                                                       int nnodes) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    const int node = warp / mmax, i = warp % mmax;
+    const int node = warp / mmax, w = warp % mmax;
     if (node >= nnodes) return;
     const NodeDesc nd = nodes[node];
     const NodeState ns = state[nd.id];
-    if (i >= ns.N) return;
-    const MatDesc md = mats[nd.mat];
-    const int r0 = nd.r0, N = ns.N, Ktot = ns.Ktot;
+    const int N = ns.N, G = group_size(N), per = 32 / G;
+    const int i = w * per + lane / G;
+    if (i >= N) return;                              // whole groups leave together
+    const MatDesc &md = mats[nd.mat];
+    const int r0 = nd.r0, Ktot = ns.Ktot, gl = lane & (G - 1);
     const long long wb = (long long)r0 * md.wstride;
     const real_t *d = md.dM + r0, *zt = md.zt + r0;
-    const int *invK = md.invK + nd.kbase;
+    const int *kpos = md.kposM + r0;
     const real_t dor = d[md.org[r0 + i]], tau = md.tau[r0 + i];
-    real_t sv = R(0.0), su = R(0.0);
-    for (int j = lane; j < N; j += 32) {
-        const real_t dj = d[j];
-        const real_t v = zt[j] / (((dj - dor) - tau) * (dj + dor + tau));
-        const real_t u = (j == 0) ? -R(1.0) : dj * v;
-        sv = fma(v, v, sv);
-        su = fma(u, u, su);
-    }
-    sv = warp_sum(sv);
-    su = warp_sum(su);
-    const real_t iv = R(1.0) / sqrt(sv), iu = R(1.0) / sqrt(su);
     real_t *UMcol = md.UM + wb + (size_t)i * Ktot, *VMcol = md.VM + wb + (size_t)i * Ktot;
-    for (int p = lane; p < Ktot; p += 32) {
-        const int j = invK[p];
-        real_t uo = R(0.0), vo = R(0.0);
-        if (j >= 0) {
-            const real_t dj = d[j];
-            const real_t v = zt[j] / (((dj - dor) - tau) * (dj + dor + tau));
-            vo = v * iv;
-            uo = ((j == 0) ? -R(1.0) : dj * v) * iu;
-        }
-        UMcol[p] = uo;
-        VMcol[p] = vo;
+    switch (G) {
+    case 4: vectors_group<4, 16>(d, zt, kpos, N, ns.n1, ns.P1, dor, tau, UMcol, VMcol, gl); break;
+    case 8: vectors_group<8, 16>(d, zt, kpos, N, ns.n1, ns.P1, dor, tau, UMcol, VMcol, gl); break;
+    case 16: vectors_group<16, 16>(d, zt, kpos, N, ns.n1, ns.P1, dor, tau, UMcol, VMcol, gl); break;
+    default: vectors_group<32, 32>(d, zt, kpos, N, ns.n1, ns.P1, dor, tau, UMcol, VMcol, gl); break;
     }
 }
 
@@ -618,7 +725,7 @@ __global__ void __launch_bounds__(256) k_rows_update(const NodeDesc *__restrict_
     const NodeDesc nd = nodes[node];
     const NodeState ns = state[nd.id];
     if (i >= ns.N) return;
-    const MatDesc md = mats[nd.mat];
+    const MatDesc &md = mats[nd.mat];
     const int r0 = nd.r0, N = ns.N;
     const real_t *d = md.dM + r0, *zt = md.zt + r0;
     const int *kpos = md.kposM + r0;
