@@ -55,8 +55,10 @@ def parse():
     ap.add_argument("--batched", action="store_true",
                     help="config 4: 2048 bidiagonals, n log-uniform in [32, 1024], one CUDA-graph launch per batch")
     ap.add_argument("--dtype", default="fp64", choices=["fp64", "fp32"], help="batched mode working precision")
-    ap.add_argument("--start", default="mlp", choices=["plain", "analytic", "mlp"],
-                    help="secular root start: interval midpoint, analytic estimate, or analytic + trained MLP")
+    ap.add_argument("--start", default="plain", choices=["plain", "analytic", "mlp"],
+                    help="timed secular root start: interval midpoint (FP32 pre-iterations), analytic estimate, "
+                         "or analytic + trained MLP; the other two are reported from untimed runs")
+    ap.add_argument("--no-mlp", action="store_true", help="skip training the root-start MLP (and its comparison)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true")
@@ -319,7 +321,7 @@ def main():
     # uniform (seed 4) and graded (seed 5) bidiagonals
     P = None
     train_info = None
-    if a.start == "mlp":
+    if a.start == "mlp" or not a.no_mlp:
         t0 = time.perf_counter()
         H = bdc.Harvest(1 << 21, device=dev)
         for kind, sd in (("uniform", 4), ("graded", 5)):
@@ -467,24 +469,27 @@ def main():
             stages[k]["hbm_frac"] = stages[k]["GBps"] / hbm
     launches = int(sum(v["launches"] for v in prof.values()) / a.steps) * a.steps
 
-    # the root-start comparison: one untimed run with the plain midpoint start
+    # the root-start comparison: one untimed run with each other start rule
+    # (FP64 iterations per root, secular stage time, SVD time)
     root_start = {"mode": a.start, "iters_per_root": stages["secular"].get("iters_per_root"),
                   "secular_ms_per_step": stages["secular"]["ms_per_step"], "mlp_training": train_info}
-    if a.start != "plain":
-        o_plain = bdc.make_opts(a.prec, a.leaf, 64, a.slices, seed="plain", mixed_min=a.mixed_min)
+    for other in ("plain", "analytic", "mlp"):
+        if other == a.start or (other == "mlp" and P is None):
+            continue
+        o_cmp = bdc.make_opts(a.prec, a.leaf, 64, a.slices, seed=other, mlp=P, mixed_min=a.mixed_min)
         bdc.profile_begin()
         q0 = torch.cuda.Event(enable_timing=True)
         q1 = torch.cuda.Event(enable_timing=True)
         q0.record(st)
         rc = L.bdc_svd_ex(n, bdc._ptr(d), bdc._ptr(e), bdc._ptr(Ut), bdc._ptr(S), bdc._ptr(VTt), n, n,
-                          ctypes.byref(o_plain), bdc._ptr(work), work.numel(), bdc._ptr(info),
+                          ctypes.byref(o_cmp), bdc._ptr(work), work.numel(), bdc._ptr(info),
                           ctypes.c_void_p(st.cuda_stream))
         q1.record(st)
         torch.cuda.synchronize()
         pp = bdc.profile_end()
         if rc == 0 and pp["secular"].get("roots"):
-            root_start["plain"] = {"iters_per_root": pp["secular"]["iters"] / pp["secular"]["roots"],
-                                   "secular_ms": pp["secular"]["ms"], "svd_ms": q0.elapsed_time(q1)}
+            root_start[other] = {"iters_per_root": pp["secular"]["iters"] / pp["secular"]["roots"],
+                                 "secular_ms": pp["secular"]["ms"], "svd_ms": q0.elapsed_time(q1)}
 
     cpu = None
     if not a.no_cpu_baseline and world == 1:

@@ -189,12 +189,14 @@ __global__ void __launch_bounds__(32) k_leaf_rotations(const NodeDesc *__restric
 
     long long budget = (long long)max_sweeps * (m > 0 ? m : 1);
     int info = 0, hi = m - 1;
-    while (!ovf && hi > 0) {
-        if (negligible(ee[hi - 1], dd[hi - 1], dd[hi], tabs)) {
+    // One action per pass, the bottom deflations of a pass included, so that
+    // the lanes of a warp (different leaves) start their sweeps together
+    while (!ovf) {
+        while (hi > 0 && negligible(ee[hi - 1], dd[hi - 1], dd[hi], tabs)) {
             ee[hi - 1] = R(0);
             --hi;
-            continue;
         }
+        if (hi <= 0) break;
         int lo = hi - 1;
         while (lo > 0 && !negligible(ee[lo - 1], dd[lo - 1], dd[lo], tabs)) --lo;
         if (lo > 0) ee[lo - 1] = R(0);

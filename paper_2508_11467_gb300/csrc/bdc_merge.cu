@@ -19,6 +19,7 @@
 // uses the original z, so survivors of it are found with a block scan; the
 // close-value test only compares consecutive survivors, so chains of close
 // values are independent and each is walked by one thread.
+#include <algorithm>
 #include <mutex>
 
 #include "bdc_internal.cuh"
@@ -235,31 +236,52 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
         return (row >= md.vlo[g] && row < md.vhi[g]) ? md.V[(size_t)g * ld + row] : R(0);
     };
 
-    // ---- z and the merged ascending order (children are sorted through Q)
+    // ---- the merged ascending order (children are sorted through Q; ties:
+    // left first).  Merge path: thread t merges output positions [k0, k1),
+    // an equal share, from the split of the two lists found by a binary
+    // search on its diagonal; then z of every position, independently.
     const int *QL = md.Q + r0L, *QR = md.Q + r0R;
     const real_t *DL = md.D + r0L, *DR = md.D + r0R;
     real_t dmax = 0.0;
-    for (int p = t; p < nl; p += T) {
-        const int j = QL[p];
-        const real_t v = DL[j];
-        int lo = 0, hi = nr;                 // # right values < v (ties: left first)
-        while (lo < hi) { int mid = (lo + hi) >> 1; if (DR[QR[mid]] < v) lo = mid + 1; else hi = mid; }
-        const int pos = 1 + p + lo;
-        ds[pos] = v;
-        zs[pos] = alpha * (md.vals ? md.vl[1 - nd.buf][r0L + j] : vrow(cvs[r0L + j], r0L + nl));
-        src[pos] = 1 + j;
-        dmax = fmax(dmax, fabs(v));
+    {
+        const int mt = nl + nr, S = (mt + T - 1) / T;
+        const int k0 = min(mt, t * S), k1 = min(mt, k0 + S);
+        if (k0 < k1) {
+            int lo = max(0, k0 - nr), hi = min(k0, nl);
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (DL[QL[mid]] <= DR[QR[k0 - mid - 1]]) lo = mid + 1; else hi = mid;
+            }
+            int i = lo, j = k0 - lo;
+            real_t a = (i < nl) ? DL[QL[i]] : R(INFINITY);
+            real_t b = (j < nr) ? DR[QR[j]] : R(INFINITY);
+            for (int k = k0; k < k1; ++k) {
+                if (j >= nr || (i < nl && a <= b)) {
+                    ds[1 + k] = a;
+                    src[1 + k] = 1 + QL[i];
+                    dmax = fmax(dmax, fabs(a));
+                    ++i;
+                    a = (i < nl) ? DL[QL[i]] : R(INFINITY);
+                } else {
+                    ds[1 + k] = b;
+                    src[1 + k] = nl + 1 + QR[j];
+                    dmax = fmax(dmax, fabs(b));
+                    ++j;
+                    b = (j < nr) ? DR[QR[j]] : R(INFINITY);
+                }
+            }
+        }
     }
-    for (int q = t; q < nr; q += T) {
-        const int j = QR[q];
-        const real_t v = DR[j];
-        int lo = 0, hi = nl;                 // # left values <= v
-        while (lo < hi) { int mid = (lo + hi) >> 1; if (DL[QL[mid]] <= v) lo = mid + 1; else hi = mid; }
-        const int pos = 1 + q + lo;
-        ds[pos] = v;
-        zs[pos] = beta * (md.vals ? md.vf[1 - nd.buf][r0R + j] : vrow(cvs[r0R + j], r0R));
-        src[pos] = nl + 1 + j;
-        dmax = fmax(dmax, fabs(v));
+    __syncthreads();
+    for (int pos = 1 + t; pos < m; pos += T) {
+        const int c = src[pos];
+        if (c <= nl) {
+            const int j = c - 1;
+            zs[pos] = alpha * (md.vals ? md.vl[1 - nd.buf][r0L + j] : vrow(cvs[r0L + j], r0L + nl));
+        } else {
+            const int j = c - nl - 1;
+            zs[pos] = beta * (md.vals ? md.vf[1 - nd.buf][r0R + j] : vrow(cvs[r0R + j], r0R));
+        }
     }
     __shared__ real_t s_cq, s_sq;
     if (t == 0) {
@@ -671,19 +693,23 @@ __global__ void __launch_bounds__(256) k_merge_finish(const NodeDesc *__restrict
             md.vlo[gv] = r0; md.vhi[gv] = r0 + nd.m + nd.sqre;
         }
     }
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        const real_t w = om[i];
-        int lo = 0, hi = ndef;           // # deflated values < w
-        while (lo < hi) { int mid = (lo + hi) >> 1; if (dv[mid] < w) lo = mid + 1; else hi = mid; }
-        md.D[r0 + i] = w;
-        md.Q[r0 + i + lo] = i;
-    }
-    for (int s = threadIdx.x; s < ndef; s += blockDim.x) {
-        const real_t v = dv[s];
-        int lo = 0, hi = N;              // # roots <= v
-        while (lo < hi) { int mid = (lo + hi) >> 1; if (om[mid] <= v) lo = mid + 1; else hi = mid; }
-        md.D[r0 + N + s] = v;
-        md.Q[r0 + s + lo] = N + s;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) md.D[r0 + i] = om[i];
+    for (int s = threadIdx.x; s < ndef; s += blockDim.x) md.D[r0 + N + s] = dv[s];
+    // ascending order of roots (ascending) and deflated values (ascending),
+    // roots first on ties: merge path, an equal share of positions per thread
+    const int mt = N + ndef, T = blockDim.x, S = (mt + T - 1) / T;
+    const int k0 = min(mt, (int)threadIdx.x * S), k1 = min(mt, k0 + S);
+    if (k0 < k1) {
+        int lo = max(0, k0 - ndef), hi = min(k0, N);
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (om[mid] <= dv[k0 - mid - 1]) lo = mid + 1; else hi = mid;
+        }
+        int i = lo, j = k0 - lo;
+        for (int k = k0; k < k1; ++k) {
+            if (j >= ndef || (i < N && om[i] <= dv[j])) md.Q[r0 + k] = i++;
+            else md.Q[r0 + k] = N + j++;
+        }
     }
 }
 
@@ -713,16 +739,18 @@ __global__ void __launch_bounds__(PREP_THREADS) k_deflate_single(int m, const re
 
 cudaError_t launch_merge_prep(const NodeDesc *nodes, int nnodes, const MatDesc *mats, NodeState *state,
                               GemmProb *probs, int mmax, int scans, cudaStream_t st) {
-    (void)mmax;
     if (nnodes <= 0) return cudaSuccess;
-    k_merge_prep<<<nnodes, PREP_THREADS, 0, st>>>(nodes, mats, state, probs, scans);
+    // a warp per 32 entries of the largest node, up to PREP_THREADS
+    const int T = std::min(PREP_THREADS, std::max(32, (mmax + 1 + 31) / 32 * 32));
+    k_merge_prep<<<nnodes, T, 0, st>>>(nodes, mats, state, probs, scans);
     return cudaGetLastError();
 }
 
 cudaError_t launch_merge_gather(const NodeDesc *nodes, int nnodes, const MatDesc *mats,
                                 const NodeState *state, int mmax, cudaStream_t st) {
     if (nnodes <= 0) return cudaSuccess;
-    k_merge_gather<<<(unsigned)nnodes * mmax, 128, 0, st>>>(nodes, mats, state, mmax);
+    const int T = mmax < 32 ? 32 : mmax < 64 ? 64 : 128;   // threads over the rows of a column
+    k_merge_gather<<<(unsigned)nnodes * mmax, T, 0, st>>>(nodes, mats, state, mmax);
     return cudaGetLastError();
 }
 
@@ -737,8 +765,8 @@ cudaError_t launch_gather_rows(const NodeDesc *nodes, int nnodes, const MatDesc 
 cudaError_t launch_merge_finish(const NodeDesc *nodes, int nnodes, const MatDesc *mats,
                                 const NodeState *state, int mmax, cudaStream_t st) {
     if (nnodes <= 0) return cudaSuccess;
-    (void)mmax;
-    k_merge_finish<<<(unsigned)nnodes, 256, 0, st>>>(nodes, mats, state);
+    const int T = std::min(256, std::max(32, (mmax + 31) / 32 * 32));
+    k_merge_finish<<<(unsigned)nnodes, T, 0, st>>>(nodes, mats, state);
     return cudaGetLastError();
 }
 

@@ -356,10 +356,52 @@ __device__ __forceinline__ double start_fraction(double y) {
     return (y <= 0.0) ? small : -small;
 }
 
+// The analytic start alone (no network, no harvest), in FP32 on the FP32
+// copies of the survivors: the same estimate as y_q in mlp_features (near
+// poles exact, far poles by their moments, the quadratic in cancellation-free
+// form), returned as the start fraction without forming the logit:
+// sigmoid(ln(t / s)) = t / (t + s).  The FP32 root pre-iteration that follows
+// works at the same precision; a start that is not finite means "no start".
+__device__ __forceinline__ double start_analytic32(const float *__restrict__ d, const float *__restrict__ z,
+                                                   int N, int i, const FarSums &L, const FarSums &Rs) {
+    const float dl = d[i], du = d[i + 1];
+    const float gap = du - dl, D2 = gap * (du + dl);
+    const float m = 0.5f * (dl + du), m2 = m * m;
+    const float a = z[i] * z[i] / D2, b = z[i + 1] * z[i + 1] / D2;
+    float bn = 0.f;
+    const int jlo = i - kMlpNear > 0 ? i - kMlpNear : 0;
+    const int jhi = i + 1 + kMlpNear < N - 1 ? i + 1 + kMlpNear : N - 1;
+    for (int j = jlo; j <= jhi; ++j) {
+        if (j == i || j == i + 1) continue;
+        const float dj = d[j];
+        bn += z[j] * z[j] / ((dj - m) * (dj + m));
+    }
+    auto far32 = [&](const FarSums &s) {
+        const float m0 = (float)s.m0;
+        if (!(m0 > 0.f)) return 0.f;
+        const float mu = (float)s.m1 / m0;
+        const float var = fmaxf((float)s.m2 / m0 - mu * mu, 0.f);
+        const float den = mu - m2;
+        if (!(fabsf(den) > 0.f)) return 0.f;
+        const float r = m0 / den * (1.f + var / (den * den));
+        return isfinite(r) ? r : 0.f;
+    };
+    const float c = 1.f + bn + far32(L) + far32(Rs);
+    const float p = c + a + b, q = a + b - c;
+    const float rp = sqrtf(fmaxf(p * p - 4.f * c * a, 0.f)), rq = sqrtf(fmaxf(q * q + 4.f * c * b, 0.f));
+    const float t = (p >= 0.f) ? 2.f * a / (p + rp) : (p - rp) / (2.f * c);
+    const float sc = (q >= 0.f) ? 2.f * b / (q + rq) : (q - rq) / (-2.f * c);
+    const float tot = t + sc;
+    if (!(t > 0.f && sc > 0.f && isfinite(tot))) return __longlong_as_double(0x7ff8000000000000ll);
+    constexpr float kMin = 2.3195228e-16f;           // sigmoid(-36): the logit is limited to +-36
+    return (t <= sc) ? (double)fmaxf(t / tot, kMin) : -(double)fmaxf(sc / tot, kMin);
+}
+
 // Start of every root but each merge's last: one thread per root computes
 // the features and the analytic estimate y_q, and with an MLP the corrected
 // start y_q + g (weights staged in shared memory).  Writes ystart (and,
-// when harvesting, the features and y_q for k_secular to append).
+// when harvesting, the features and y_q for k_secular to append).  The
+// analytic start alone takes start_analytic32.
 __global__ void __launch_bounds__(128) k_root_start(const NodeDesc *__restrict__ nodes,
                                                     const MatDesc *__restrict__ mats,
                                                     const NodeState *__restrict__ state, int mmax, int nnodes,
@@ -380,6 +422,10 @@ __global__ void __launch_bounds__(128) k_root_start(const NodeDesc *__restrict__
     const double *d = md.dM + nd.r0, *z = md.zM + nd.r0;
     FarSums L, R;
     far_from_scans(md.pz + nd.r0, md.n, N, i, L, R);
+    if (seed_mode == BDC_SEED_ANALYTIC && md.feat == nullptr) {
+        md.ystart[nd.r0 + i] = start_analytic32(md.d32 + nd.r0, md.z32 + nd.r0, N, i, L, R);
+        return;
+    }
     float f[kMlpIn];
     const double yq = mlp_features(d, z, N, i, state[nd.id].rho, L, R, f);
     double ys = yq;
