@@ -23,11 +23,14 @@
 //               (row maxima, then integer digit extraction), row-major
 //               K-contiguous BF16 slices [slice][row][Kld] + exponents E.
 //   k_slice_b : one warp per column (B is K-contiguous), same digits + F.
-//   k_mma     : 128 x 128 tile per CTA, K staged 32 at a time by TMA (3-D box
+//   k_mma     : persistent, one CTA per SM over the list of non-empty
+//               128 x 128 tiles; K staged 32 at a time by TMA (3-D box
 //               32 x 128 x S, 64-byte swizzle) into a 2-stage ring; warp 0
 //               issues TMA, warp 1 allocates TMEM (512 columns) and one lane
 //               issues tcgen05.mma kind::f16 (BF16 x BF16 -> FP32), warps 2-9
-//               drain and store.  Every mbarrier wait is bounded (2 s of
+//               drain and store.  Ring stages and accumulator chunks are
+//               counted across tiles, so loads and MMAs of the next tile
+//               overlap the current tile's conversion and stores.  Every mbarrier wait is bounded (2 s of
 //               %globaltimer); a timeout sets an error word and unwinds.
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -69,9 +72,6 @@ __device__ __forceinline__ unsigned long long gtimer() {
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
 }
-__device__ __forceinline__ void mbar_inval(uint64_t *bar) {
-    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
@@ -101,6 +101,14 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *e
             return false;
         }
     }
+}
+// bounded wait that ignores the abort flag: a role that stopped early still
+// lets its own asynchronous copies / MMAs land before the CTA exits
+__device__ __forceinline__ void mbar_drain(uint64_t *bar, uint32_t parity) {
+    if (mbar_try(bar, parity)) return;
+    const unsigned long long t0 = gtimer();
+    while (!mbar_try(bar, parity))
+        if (gtimer() - t0 > kWaitNs) return;
 }
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2,
                                             uint64_t *bar) {
@@ -134,11 +142,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-// exact integer of an FP32 value v = I 2^-sh with |I| < 2^22
-__device__ __forceinline__ int exact_int(float v, float scale) {
-    return __float_as_int(fmaf(v, scale, 12582912.0f)) - 0x4B400000;
-}
 
 __device__ __forceinline__ double pow2(int e) {   // 2^e for -1022 <= e <= 1023
     return __longlong_as_double((long long)(e + 1023) << 52);
@@ -380,10 +383,20 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
     (void)nprobs;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // persistent: the CTA walks the device-built list of non-empty tiles
-    // (sizes after deflation), so no CTA is launched for an empty tile
+    // (sizes after deflation), so no CTA is launched for an empty tile.  The
+    // barriers live for the whole kernel and every role walks the same tiles
+    // with running stage / chunk counters (phases continue across tiles):
+    // the producer loads the next tile and the MMAs start on it while the
+    // epilogue still converts and stores the current one.
     const int count = *ntiles;
     if ((int)blockIdx.x >= count) return;
-    if (threadIdx.x == 0) *abort_flag = 0;
+    if (threadIdx.x == 0) {
+        *abort_flag = 0;
+        for (int i = 0; i < NSTAGE; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
+        for (int i = 0; i < 2; ++i) { mbar_init(&accfull[i], 1); mbar_init(&accempty[i], 32 * EPI_WARPS); }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -393,33 +406,30 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
     fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    for (int ti = blockIdx.x; ti < count; ti += gridDim.x) {
-    const int2 tc = tiles[ti];
-    const int p = tc.x;
-    const GemmProb pr = probs[p];
-    const MixProb mx = mix[p];
-    const int m0 = (tc.y >> 16) * TM, n0 = (tc.y & 0xffff) * TNX;
-    const int nk = (pr.K + TK - 1) / TK;
-    // fresh barriers for every tile (the previous tile's are drained and invalidated)
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < NSTAGE; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
-        for (int i = 0; i < 2; ++i) { mbar_init(&accfull[i], 1); mbar_init(&accempty[i], 32 * EPI_WARPS); }
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    }
-    __syncthreads();
-
     if (warp == 0) {
         // ------------------------------------------------ TMA producer
         if (lane == 0) {
-            for (int s = 0; s < nk; ++s) {
-                const int buf = s & 1;
-                if (s >= NSTAGE && !mbar_wait(&empty[buf], ((s >> 1) - 1) & 1, err, abort_flag)) break;
-                mbar_expect_tx(&full[buf], STAGE_BYTES);
-                const uint32_t dstA = smem_u32(smem + buf * STAGE_BYTES);
-                tma_load_3d(dstA, &tmA, s * TK, mx.a_row0 + m0, 0, &full[buf]);
-                tma_load_3d(dstA + S * TILE, &tmB, s * TK, mx.b_col0 + n0, 0, &full[buf]);
+            int G = 0;                                  // stages loaded so far (all tiles)
+            bool ok = true;
+            for (int ti = blockIdx.x; ti < count && ok; ti += gridDim.x) {
+                const int2 tc = tiles[ti];
+                const MixProb mx = mix[tc.x];
+                const int m0 = (tc.y >> 16) * TM, n0 = (tc.y & 0xffff) * TNX;
+                const int nk = (probs[tc.x].K + TK - 1) / TK;
+                for (int s = 0; s < nk; ++s, ++G) {
+                    const int buf = G % NSTAGE;
+                    if (G >= NSTAGE && !mbar_wait(&empty[buf], ((G / NSTAGE) - 1) & 1, err, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(&full[buf], STAGE_BYTES);
+                    const uint32_t dstA = smem_u32(smem + buf * STAGE_BYTES);
+                    tma_load_3d(dstA, &tmA, s * TK, mx.a_row0 + m0, 0, &full[buf]);
+                    tma_load_3d(dstA + S * TILE, &tmB, s * TK, mx.b_col0 + n0, 0, &full[buf]);
+                }
             }
+            // copies still in flight (after an abort) land before the CTA exits
+            for (int g = (G > NSTAGE ? G - NSTAGE : 0); g < G; ++g) mbar_drain(&full[g % NSTAGE], (g / NSTAGE) & 1);
         }
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer (one lane)
@@ -435,206 +445,235 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
                     dA[b][i] = sdesc(a);
                     dB[b][i] = sdesc(a + S * TILE);
                 }
+            int G = 0;                                  // stages consumed so far (all tiles)
+            int nA = 0, nB = 0;                         // accumulator chunks committed: set A / set B
+                                                        // (MODE_E), tiles (MODE_X3)
             bool ok = true;
-            for (int s = 0; s < nk && ok; ++s) {
-                const int buf = s & 1;
-                if (!mbar_wait(&full[buf], (s >> 1) & 1, err, abort_flag)) { ok = false; break; }
+            // a fresh chunk of an accumulator set waits until the epilogue has
+            // drained the set's previous chunk
+            auto wait_drained = [&](int set, int done) {
+                if (done > 0 && !mbar_wait(&accempty[set], (done - 1) & 1, err, abort_flag)) ok = false;
                 fence_after();
-                // operand "addresses" below are (buffer, tile index, K step) handles
-                auto mma = [&](uint32_t col, int ia, int ib, int kk, uint32_t acc) {
-                    const uint64_t a = (buf ? dA[1][ia] : dA[0][ia]) + 2 * kk;
-                    const uint64_t b = (buf ? dB[1][ib] : dB[0][ib]) + 2 * kk;
-                    asm volatile(
-                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, "
-                        "p;\n}\n" ::"r"(tmem + col),
-                        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-                        : "memory");
-                };
-                if constexpr (MODE == MODE_X3) {
-#pragma unroll
-                    for (int kk = 0; kk < 2; ++kk) {
-                        mma(0, 0, 0, kk, (s == 0 && kk == 0) ? 0u : 1u);
-                        mma(0, 0, 1, kk, 1u);
-                        mma(0, 1, 0, kk, 1u);
-                    }
-                    umma_commit(&empty[buf]);
-                    if (s == nk - 1) umma_commit(&accfull[0]);
-                } else if constexpr (MODE == MODE_L) {
-                    const int b = s & 1;                       // accumulator buffer of this stage
-                    if (s >= 2) {
-                        if (!mbar_wait(&accempty[b], ((s >> 1) - 1) & 1, err, abort_flag)) { ok = false; break; }
-                        fence_after();
-                    }
-                    const uint32_t c4 = 256 * b, cl = 256 * b + 128;
-#pragma unroll
-                    for (int kk = 0; kk < 2; ++kk) {
-#pragma unroll
-                        for (int i = 0; i <= 4; ++i)
-                            if (i < S && 4 - i < S)
-                                mma(c4, i, 4 - i, kk, (kk == 0 && i == 0) ? 0u : 1u);
-                        bool first = true;
-#pragma unroll
-                        for (int g = 5; g <= S - 1; ++g)
-#pragma unroll
-                            for (int i = 0; i <= g; ++i) {
-                                const int j = g - i;
-                                if (i >= S || j >= S) continue;
-                                mma(cl, i, j, kk, (kk == 0 && first) ? 0u : 1u);
-                                first = false;
-                            }
-                    }
-                    umma_commit(&empty[buf]);
-                    umma_commit(&accfull[b]);
-                } else {
-                    // MODE_E: set A = {g0 @0, g3 @384}, set B = {g1 @128, g2 @256}
-                    auto issueA = [&](bool fresh) {
+            };
+            for (int ti = blockIdx.x; ti < count && ok; ti += gridDim.x) {
+                const int nk = (probs[tiles[ti].x].K + TK - 1) / TK;
+                for (int s = 0; s < nk && ok; ++s, ++G) {
+                    const int buf = G % NSTAGE;
+                    if (!mbar_wait(&full[buf], (G / NSTAGE) & 1, err, abort_flag)) { ok = false; break; }
+                    fence_after();
+                    // operand "addresses" below are (buffer, tile index, K step) handles
+                    auto mma = [&](uint32_t col, int ia, int ib, int kk, uint32_t acc) {
+                        const uint64_t a = (buf ? dA[1][ia] : dA[0][ia]) + 2 * kk;
+                        const uint64_t b = (buf ? dB[1][ib] : dB[0][ib]) + 2 * kk;
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, "
+                            "p;\n}\n" ::"r"(tmem + col),
+                            "l"(a), "l"(b), "r"(idesc), "r"(acc)
+                            : "memory");
+                    };
+                    if constexpr (MODE == MODE_X3) {
+                        if (s == 0) wait_drained(0, nA);
+                        if (!ok) break;
 #pragma unroll
                         for (int kk = 0; kk < 2; ++kk) {
-                            mma(0, 0, 0, kk, (fresh && kk == 0) ? 0u : 1u);
-#pragma unroll
-                            for (int i = 0; i <= 3; ++i) mma(384, i, 3 - i, kk, (fresh && kk == 0 && i == 0) ? 0u : 1u);
+                            mma(0, 0, 0, kk, (s == 0 && kk == 0) ? 0u : 1u);
+                            mma(0, 0, 1, kk, 1u);
+                            mma(0, 1, 0, kk, 1u);
                         }
-                    };
-                    auto issueB = [&](bool fresh) {
-#pragma unroll
-                        for (int kk = 0; kk < 2; ++kk) {
-#pragma unroll
-                            for (int i = 0; i <= 1; ++i) mma(128, i, 1 - i, kk, (fresh && kk == 0 && i == 0) ? 0u : 1u);
-#pragma unroll
-                            for (int i = 0; i <= 2; ++i) mma(256, i, 2 - i, kk, (fresh && kk == 0 && i == 0) ? 0u : 1u);
-                        }
-                    };
-                    if ((s & 1) == 0) {
-                        issueB(s == 0);                    // set B continues (starts at s = 0)
-                        if (s >= 2) {                      // set A starts a chunk: its drain must be done
-                            if (!mbar_wait(&accempty[0], ((s >> 1) - 1) & 1, err, abort_flag)) { ok = false; }
+                        umma_commit(&empty[buf]);
+                        if (s == nk - 1) { umma_commit(&accfull[0]); ++nA; }
+                    } else if constexpr (MODE == MODE_L) {
+                        const int b = G & 1;                   // accumulator buffer of this stage
+                        if (G >= 2) {
+                            if (!mbar_wait(&accempty[b], ((G >> 1) - 1) & 1, err, abort_flag)) { ok = false; break; }
                             fence_after();
                         }
-                        if (ok) issueA(true);
+                        const uint32_t c4 = 256 * b, cl = 256 * b + 128;
+#pragma unroll
+                        for (int kk = 0; kk < 2; ++kk) {
+#pragma unroll
+                            for (int i = 0; i <= 4; ++i)
+                                if (i < S && 4 - i < S)
+                                    mma(c4, i, 4 - i, kk, (kk == 0 && i == 0) ? 0u : 1u);
+                            bool first = true;
+#pragma unroll
+                            for (int g = 5; g <= S - 1; ++g)
+#pragma unroll
+                                for (int i = 0; i <= g; ++i) {
+                                    const int j = g - i;
+                                    if (i >= S || j >= S) continue;
+                                    mma(cl, i, j, kk, (kk == 0 && first) ? 0u : 1u);
+                                    first = false;
+                                }
+                        }
+                        umma_commit(&empty[buf]);
+                        umma_commit(&accfull[b]);
                     } else {
-                        issueA(false);
-                        if (!mbar_wait(&accempty[1], ((s - 1) >> 1) & 1, err, abort_flag)) { ok = false; }
-                        fence_after();
-                        if (ok) issueB(true);
+                        // MODE_E: set A = {g0 @0, g3 @384}, set B = {g1 @128, g2 @256}
+                        auto issueA = [&](bool fresh) {
+#pragma unroll
+                            for (int kk = 0; kk < 2; ++kk) {
+                                mma(0, 0, 0, kk, (fresh && kk == 0) ? 0u : 1u);
+#pragma unroll
+                                for (int i = 0; i <= 3; ++i) mma(384, i, 3 - i, kk, (fresh && kk == 0 && i == 0) ? 0u : 1u);
+                            }
+                        };
+                        auto issueB = [&](bool fresh) {
+#pragma unroll
+                            for (int kk = 0; kk < 2; ++kk) {
+#pragma unroll
+                                for (int i = 0; i <= 1; ++i) mma(128, i, 1 - i, kk, (fresh && kk == 0 && i == 0) ? 0u : 1u);
+#pragma unroll
+                                for (int i = 0; i <= 2; ++i) mma(256, i, 2 - i, kk, (fresh && kk == 0 && i == 0) ? 0u : 1u);
+                            }
+                        };
+                        bool issued = false;
+                        if ((s & 1) == 0) {
+                            if (s == 0) wait_drained(1, nB);   // set B starts a chunk at a tile's first stage
+                            if (ok) { issueB(s == 0); issued = true; }   // and continues at the other even stages
+                            if (ok) wait_drained(0, nA);       // set A starts a chunk
+                            if (ok) issueA(true);
+                        } else {
+                            issueA(false);
+                            issued = true;
+                            wait_drained(1, nB);
+                            if (ok) issueB(true);
+                        }
+                        if (!ok) {
+                            // stopped part-way: the MMAs already issued still report to the
+                            // stage barrier, which the drain below waits for
+                            if (issued) { umma_commit(&empty[buf]); ++G; }
+                            break;
+                        }
+                        umma_commit(&empty[buf]);
+                        if (((s & 1) == 0) || s == nk - 1) { umma_commit(&accfull[1]); ++nB; }   // set B chunk ends
+                        if (((s & 1) == 1) || s == nk - 1) { umma_commit(&accfull[0]); ++nA; }   // set A chunk ends
                     }
-                    umma_commit(&empty[buf]);
-                    if (((s & 1) == 0) || s == nk - 1) umma_commit(&accfull[1]);   // set B chunk ends
-                    if (((s & 1) == 1) || s == nk - 1) umma_commit(&accfull[0]);   // set A chunk ends
                 }
             }
+            // every MMA issued has completed (its stage's commit arrived) before
+            // the CTA frees TMEM and exits
+            for (int g = (G > NSTAGE ? G - NSTAGE : 0); g < G; ++g) mbar_drain(&empty[g % NSTAGE], (g / NSTAGE) & 1);
         }
     } else {
         // ------------------------------------------------ epilogue (warps 2..9)
         const int q = warp & 3;                    // TMEM lane quarter this warp may access
         const int half = (warp - 2) >> 2;          // column half
-        const int row = m0 + 32 * q + lane;
         const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16) + 64 * half;
         bool ok = true;
-        if constexpr (MODE == MODE_E) {
-            // unsigned: the magic offsets wrap modulo 2^64 and cancel exactly at the end
-            unsigned long long L[64];
+        int cA = 0, cB = 0;                        // drains done: set A / set B (MODE_E), tiles (MODE_X3)
+        int GL = 0;                                // stages drained (MODE_L)
+        for (int ti = blockIdx.x; ti < count && ok; ti += gridDim.x) {
+            const int2 tc = tiles[ti];
+            const GemmProb pr = probs[tc.x];
+            const MixProb mx = mix[tc.x];
+            const int m0 = (tc.y >> 16) * TM, n0 = (tc.y & 0xffff) * TNX;
+            const int nk = (pr.K + TK - 1) / TK;
+            const int row = m0 + 32 * q + lane;
+            if constexpr (MODE == MODE_E) {
+                // unsigned: the magic offsets wrap modulo 2^64 and cancel exactly at the end
+                unsigned long long L[64];
 #pragma unroll
-            for (int i = 0; i < 64; ++i) L[i] = 0;
-            int cA = 0, cB = 0;
-            for (int s = 0; s < nk && ok; ++s) {
-                if (((s & 1) == 0) || s == nk - 1) {                // set B: g1, g2
-                    if (!mbar_wait(&accfull[1], cB & 1, err, abort_flag)) { ok = false; break; }
+                for (int i = 0; i < 64; ++i) L[i] = 0;
+                int tA = 0, tB = 0;                    // this tile's drains
+                for (int s = 0; s < nk && ok; ++s) {
+                    if (((s & 1) == 0) || s == nk - 1) {                // set B: g1, g2
+                        if (!mbar_wait(&accfull[1], cB & 1, err, abort_flag)) { ok = false; break; }
+                        fence_after();
+#pragma unroll
+                        for (int cb = 0; cb < 4; ++cb) {
+                            float v1[16], v2[16];
+                            tmem_ld16(tl + 128 + 16 * cb, v1);
+                            tmem_ld16(tl + 256 + 16 * cb, v2);
+                            tmem_wait_ld();
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) {
+                                // raw magic bits b = I + 0x4B400000; the offsets are removed once at the end
+                                const unsigned b1 = __float_as_uint(fmaf(v1[i], 256.0f, 12582912.0f));
+                                const unsigned b2 = __float_as_uint(fmaf(v2[i], 65536.0f, 12582912.0f));
+                                L[16 * cb + i] += ((unsigned long long)b1 << 16) + ((unsigned long long)b2 << 8);
+                            }
+                        }
+                        fence_before();
+                        mbar_arrive(&accempty[1]);
+                        ++cB; ++tB;
+                    }
+                    if (((s & 1) == 1) || s == nk - 1) {                // set A: g0, g3
+                        if (!mbar_wait(&accfull[0], cA & 1, err, abort_flag)) { ok = false; break; }
+                        fence_after();
+#pragma unroll
+                        for (int cb = 0; cb < 4; ++cb) {
+                            float v0[16], v3[16];
+                            tmem_ld16(tl + 16 * cb, v0);
+                            tmem_ld16(tl + 384 + 16 * cb, v3);
+                            tmem_wait_ld();
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) {
+                                const unsigned b0 = __float_as_uint(fmaf(v0[i], 1.0f, 12582912.0f));
+                                const unsigned b3 = __float_as_uint(fmaf(v3[i], 16777216.0f, 12582912.0f));
+                                L[16 * cb + i] += ((unsigned long long)b0 << 24) + (unsigned long long)b3;
+                            }
+                        }
+                        fence_before();
+                        mbar_arrive(&accempty[0]);
+                        ++cA; ++tA;
+                    }
+                }
+                if (ok) {
+                    // remove the magic offsets: every set-A drain added M (2^24 + 1),
+                    // every set-B drain M (2^16 + 2^8), M = 0x4B400000
+                    const unsigned long long M = 0x4B400000ull;
+                    const unsigned long long corr = (unsigned long long)tA * M * ((1ull << 24) + 1) +
+                                                    (unsigned long long)tB * M * ((1ull << 16) + (1ull << 8));
+                    const int Er = (row < pr.M) ? Ea[mx.a_row0 + row] : 0;
+#pragma unroll
+                    for (int i = 0; i < 64; ++i) {
+                        const int col = n0 + 64 * half + i;
+                        if (row < pr.M && col < pr.N)
+                            pr.C[gemm_col(pr, col) + row] =
+                                i64_ldexp((long long)(L[i] - corr), Er + Fb[mx.b_col0 + col] - 40);
+                    }
+                }
+            } else if constexpr (MODE == MODE_L) {
+                // group 4 is exact per stage (and weighs <= 2^-32), groups >= 5 weigh
+                // <= 2^-40: both are summed over the stages in FP32 registers
+                float SL[64];
+#pragma unroll
+                for (int i = 0; i < 64; ++i) SL[i] = 0.f;
+                for (int s = 0; s < nk; ++s, ++GL) {
+                    const int b = GL & 1;
+                    if (!mbar_wait(&accfull[b], (GL >> 1) & 1, err, abort_flag)) { ok = false; break; }
                     fence_after();
 #pragma unroll
                     for (int cb = 0; cb < 4; ++cb) {
-                        float v1[16], v2[16];
-                        tmem_ld16(tl + 128 + 16 * cb, v1);
-                        tmem_ld16(tl + 256 + 16 * cb, v2);
+                        float v4[16], vl[16];
+                        tmem_ld16(tl + 256 * b + 16 * cb, v4);
+                        if (S > 5) tmem_ld16(tl + 256 * b + 128 + 16 * cb, vl);
                         tmem_wait_ld();
 #pragma unroll
                         for (int i = 0; i < 16; ++i) {
-                            // raw magic bits b = I + 0x4B400000; the offsets are removed once at the end
-                            const unsigned b1 = __float_as_uint(fmaf(v1[i], 256.0f, 12582912.0f));
-                            const unsigned b2 = __float_as_uint(fmaf(v2[i], 65536.0f, 12582912.0f));
-                            L[16 * cb + i] += ((unsigned long long)b1 << 16) + ((unsigned long long)b2 << 8);
+                            SL[16 * cb + i] += v4[i];
+                            if (S > 5) SL[16 * cb + i] += vl[i];
                         }
                     }
                     fence_before();
-                    mbar_arrive(&accempty[1]);
-                    ++cB;
+                    mbar_arrive(&accempty[b]);
                 }
-                if (((s & 1) == 1) || s == nk - 1) {                // set A: g0, g3
-                    if (!mbar_wait(&accfull[0], cA & 1, err, abort_flag)) { ok = false; break; }
-                    fence_after();
+                if (ok) {
+                    const int Er = (row < pr.M) ? Ea[mx.a_row0 + row] : 0;
 #pragma unroll
-                    for (int cb = 0; cb < 4; ++cb) {
-                        float v0[16], v3[16];
-                        tmem_ld16(tl + 16 * cb, v0);
-                        tmem_ld16(tl + 384 + 16 * cb, v3);
-                        tmem_wait_ld();
-#pragma unroll
-                        for (int i = 0; i < 16; ++i) {
-                            const unsigned b0 = __float_as_uint(fmaf(v0[i], 1.0f, 12582912.0f));
-                            const unsigned b3 = __float_as_uint(fmaf(v3[i], 16777216.0f, 12582912.0f));
-                            L[16 * cb + i] += ((unsigned long long)b0 << 24) + (unsigned long long)b3;
+                    for (int i = 0; i < 64; ++i) {
+                        const int col = n0 + 64 * half + i;
+                        if (row < pr.M && col < pr.N) {
+                            const int e = Er + Fb[mx.b_col0 + col];
+                            double *c = pr.C + gemm_col(pr, col) + row;
+                            *c += f32_ldexp(SL[i], e - 16);
                         }
                     }
-                    fence_before();
-                    mbar_arrive(&accempty[0]);
-                    ++cA;
                 }
-            }
-            if (ok) {
-                // remove the magic offsets: every set-A drain added M (2^24 + 1),
-                // every set-B drain M (2^16 + 2^8), M = 0x4B400000
-                const unsigned long long M = 0x4B400000ull;
-                const unsigned long long corr =
-                    (unsigned long long)cA * M * ((1ull << 24) + 1) + (unsigned long long)cB * M * ((1ull << 16) + (1ull << 8));
-                const int Er = (row < pr.M) ? Ea[mx.a_row0 + row] : 0;
-#pragma unroll
-                for (int i = 0; i < 64; ++i) {
-                    const int col = n0 + 64 * half + i;
-                    if (row < pr.M && col < pr.N)
-                        pr.C[gemm_col(pr, col) + row] =
-                            i64_ldexp((long long)(L[i] - corr), Er + Fb[mx.b_col0 + col] - 40);
-                }
-            }
-        } else if constexpr (MODE == MODE_L) {
-            // group 4 is exact per stage (and weighs <= 2^-32), groups >= 5 weigh
-            // <= 2^-40: both are summed over the stages in FP32 registers
-            float SL[64];
-#pragma unroll
-            for (int i = 0; i < 64; ++i) SL[i] = 0.f;
-            for (int s = 0; s < nk; ++s) {
-                const int b = s & 1;
-                if (!mbar_wait(&accfull[b], (s >> 1) & 1, err, abort_flag)) { ok = false; break; }
+            } else {
+                if (!mbar_wait(&accfull[0], cA & 1, err, abort_flag)) { ok = false; break; }
                 fence_after();
-#pragma unroll
-                for (int cb = 0; cb < 4; ++cb) {
-                    float v4[16], vl[16];
-                    tmem_ld16(tl + 256 * b + 16 * cb, v4);
-                    if (S > 5) tmem_ld16(tl + 256 * b + 128 + 16 * cb, vl);
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        SL[16 * cb + i] += v4[i];
-                        if (S > 5) SL[16 * cb + i] += vl[i];
-                    }
-                }
-                fence_before();
-                mbar_arrive(&accempty[b]);
-            }
-            if (ok) {
-                const int Er = (row < pr.M) ? Ea[mx.a_row0 + row] : 0;
-#pragma unroll
-                for (int i = 0; i < 64; ++i) {
-                    const int col = n0 + 64 * half + i;
-                    if (row < pr.M && col < pr.N) {
-                        const int e = Er + Fb[mx.b_col0 + col];
-                        double *c = pr.C + gemm_col(pr, col) + row;
-                        *c += f32_ldexp(SL[i], e - 16);
-                    }
-                }
-            }
-        } else {
-            if (!mbar_wait(&accfull[0], 0, err, abort_flag)) ok = false;
-            fence_after();
-            if (ok) {
 #pragma unroll
                 for (int cb = 0; cb < 4; ++cb) {
                     float v[16];
@@ -646,28 +685,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
                         if (row < pr.M && col < pr.N) pr.C[gemm_col(pr, col) + row] = f32_ldexp(v[i], 0);
                     }
                 }
+                fence_before();
+                mbar_arrive(&accempty[0]);
+                ++cA;
             }
         }
-        fence_before();
-    }
-    // tile end: the MMA's last commits to the stage barriers arrive
-    // asynchronously; wait for them before the barriers are reused
-    if (warp == 1 && lane == 0 && !*abort_flag) {
-        for (int b = 0; b < NSTAGE; ++b) {
-            const int nb = (nk + NSTAGE - 1 - b) / NSTAGE;   // stages s < nk with s % NSTAGE == b
-            if (nb > 0) mbar_wait(&empty[b], (uint32_t)((nb - 1) & 1), err, abort_flag);
-        }
+        (void)cB;
     }
     fence_before();
-    __syncthreads();
-    if (*abort_flag) break;
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < NSTAGE; ++i) { mbar_inval(&full[i]); mbar_inval(&empty[i]); }
-        for (int i = 0; i < 2; ++i) { mbar_inval(&accfull[i]); mbar_inval(&accempty[i]); }
-    }
-    __syncthreads();
-    fence_after();
-    }   // tiles
     __syncthreads();
     if (warp == 1) {
         fence_after();
