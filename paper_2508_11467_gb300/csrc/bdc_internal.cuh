@@ -172,6 +172,28 @@ __device__ __forceinline__ int warp_isum(int v) {
     return v;
 }
 
+// z / x for the pole sums and vector entries.  FP64: GB300 issues an FP64
+// division as about eight FP64-pipe operations; here the hardware reciprocal
+// estimate (PTX rcp.approx.ftz.f64, about 20 bits) is refined by two
+// Newton-Raphson reciprocal steps r <- r + r (1 - x r) (each squares the
+// relative error) and multiplied by z: four FMAs and a product, within about
+// an ulp of z / x.  Outside 2^-1000 <= |x| <= 2^1000 the plain quotient.
+__device__ __forceinline__ real_t quot(real_t z, real_t x) {
+#ifdef BDC_FP32
+    return z / x;
+#else
+    const long long xb = __double_as_longlong(x) & 0x7fffffffffffffffll;
+    if (xb < (23ll << 52) || xb > (2023ll << 52)) return z / x;
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    double e = fma(-x, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-x, r, 1.0);
+    r = fma(r, e, r);
+    return z * r;
+#endif
+}
+
 // plane rotation with c f + s g = r, -s f + c g = 0
 __device__ __forceinline__ void make_rot(real_t f, real_t g, real_t &c, real_t &s, real_t &r) {
     if (g == R(0)) { c = R(1); s = R(0); r = f; return; }

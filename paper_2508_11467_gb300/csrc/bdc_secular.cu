@@ -13,14 +13,12 @@
 //            4 eps |x|.  Optionally the start comes from a small MLP
 //            (bdc_mlp.cuh) instead of the interval midpoint; the stopping
 //            rule is the same, so the MLP only changes the iteration count.
-// k_lowner   one warp per i: |z~_i| of Eq. (bdc-zi) as a product over k of
-//            (w_k^2 - d_i^2) / (d_{k'}^2 - d_i^2) (every factor lies in (0, 1]
-//            by interlacing), lane partial products, then a shuffle product
-//            reduction; sign from z_i.
-// k_vectors  one CTA per column i: v_i, u_i of Eq. (M-svd-vec), normalised,
-//            written in the K order of the merge product (coalesced down the
-//            column); k_vectors_warp does the same with a warp per column
-//            for merges of order <= 1024.
+// k_lowner   one lane group per i: |z~_i| of Eq. (bdc-zi) as a product over
+//            k of (w_k^2 - d_i^2) / (d_{k'}^2 - d_i^2) (every factor lies in
+//            (0, 1] by interlacing), lane partial products, then a shuffle
+//            product reduction; sign from z_i.
+// k_vectors_warp  one lane group per column i: v_i, u_i of Eq. (M-svd-vec),
+//            normalised, written in the K order of the merge product.
 //
 // All arithmetic is in real_t: FP64, or FP32 in the FP32 build.  The root
 // starts (k_root_start, bdc_mlp.cuh) and the standalone step kernels are
@@ -71,19 +69,36 @@ template <int G>
 __device__ __forceinline__ Sums pole_sums(const real_t *__restrict__ d, const real_t *__restrict__ z,
                                           int N, int i, real_t dor, real_t x, int lane) {
     Sums s{R(0.0), R(0.0), R(0.0), R(0.0)};
-    for (int j = lane; j <= i; j += G) {
-        const real_t dj = d[j], zj = z[j];
-        const real_t del = (dj - dor) * (dj + dor) - x;
-        const real_t t = zj / del;
-        s.psi = fma(zj, t, s.psi);
-        s.dpsi = fma(t, t, s.dpsi);
-    }
-    for (int j = i + 1 + lane; j < N; j += G) {
-        const real_t dj = d[j], zj = z[j];
-        const real_t del = (dj - dor) * (dj + dor) - x;
-        const real_t t = zj / del;
-        s.phi = fma(zj, t, s.phi);
-        s.dphi = fma(t, t, s.dphi);
+    if constexpr (G < 32) {
+        // several roots per warp split their poles at different i: one loop
+        // over all poles (the same trip count for every group of the warp)
+        for (int j = lane; j < N; j += G) {
+            const real_t dj = d[j], zj = z[j];
+            const real_t del = (dj - dor) * (dj + dor) - x;
+            const real_t t = quot(zj, del);
+            if (j <= i) {
+                s.psi = fma(zj, t, s.psi);
+                s.dpsi = fma(t, t, s.dpsi);
+            } else {
+                s.phi = fma(zj, t, s.phi);
+                s.dphi = fma(t, t, s.dphi);
+            }
+        }
+    } else {
+        for (int j = lane; j <= i; j += G) {
+            const real_t dj = d[j], zj = z[j];
+            const real_t del = (dj - dor) * (dj + dor) - x;
+            const real_t t = quot(zj, del);
+            s.psi = fma(zj, t, s.psi);
+            s.dpsi = fma(t, t, s.dpsi);
+        }
+        for (int j = i + 1 + lane; j < N; j += G) {
+            const real_t dj = d[j], zj = z[j];
+            const real_t del = (dj - dor) * (dj + dor) - x;
+            const real_t t = quot(zj, del);
+            s.phi = fma(zj, t, s.phi);
+            s.dphi = fma(t, t, s.dphi);
+        }
     }
     s.psi = group_sum<G>(s.psi);
     s.dpsi = group_sum<G>(s.dpsi);
@@ -636,6 +651,7 @@ __global__ void __launch_bounds__(256) k_lowner_single(int N, const double *d, c
 }
 #endif
 
+#ifndef BDC_FP32   // the single-problem vector kernel: FP64 only
 __device__ __forceinline__ real_t block_sum256(real_t v, real_t *sh) {
     v = warp_sum(v);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -647,7 +663,8 @@ __device__ __forceinline__ real_t block_sum256(real_t v, real_t *sh) {
     return r;
 }
 
-// column i of U_M and V_M, rows in K order (invK: K position -> M index, -1 = zero row)
+// column i of U_M and V_M, rows in K order (invK: K position -> M index, -1 =
+// zero row; nullptr = identity), one CTA (standalone step entry point)
 __device__ void vectors_one(const real_t *__restrict__ d, const real_t *__restrict__ zt, int N, int i,
                             int o, real_t tau, const int *__restrict__ invK, int Ktot,
                             real_t *__restrict__ UMcol, real_t *__restrict__ VMcol, real_t *sh) {
@@ -655,7 +672,7 @@ __device__ void vectors_one(const real_t *__restrict__ d, const real_t *__restri
     real_t sv = R(0.0), su = R(0.0);
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
         const real_t dj = d[j];
-        const real_t v = zt[j] / (((dj - dor) - tau) * (dj + dor + tau));
+        const real_t v = quot(zt[j], ((dj - dor) - tau) * (dj + dor + tau));
         const real_t u = (j == 0) ? -R(1.0) : dj * v;
         sv = fma(v, v, sv);
         su = fma(u, u, su);
@@ -668,7 +685,7 @@ __device__ void vectors_one(const real_t *__restrict__ d, const real_t *__restri
         real_t uo = R(0.0), vo = R(0.0);
         if (j >= 0) {
             const real_t dj = d[j];
-            const real_t v = zt[j] / (((dj - dor) - tau) * (dj + dor + tau));
+            const real_t v = quot(zt[j], ((dj - dor) - tau) * (dj + dor + tau));
             vo = v * iv;
             uo = ((j == 0) ? -R(1.0) : dj * v) * iu;
         }
@@ -677,20 +694,7 @@ __device__ void vectors_one(const real_t *__restrict__ d, const real_t *__restri
     }
 }
 
-__global__ void __launch_bounds__(256) k_vectors(const NodeDesc *__restrict__ nodes,
-                                                 const MatDesc *__restrict__ mats,
-                                                 const NodeState *__restrict__ state, int mmax) {
-    __shared__ real_t sh[8];
-    const int node = blockIdx.x / mmax, i = blockIdx.x % mmax;
-    const NodeDesc nd = nodes[node];
-    const NodeState ns = state[nd.id];
-    if (i >= ns.N) return;
-    const MatDesc &md = mats[nd.mat];
-    const int r0 = nd.r0;
-    const long long wb = (long long)r0 * md.wstride;
-    vectors_one(md.dM + r0, md.zt + r0, ns.N, i, md.org[r0 + i], md.tau[r0 + i], md.invK + nd.kbase,
-                ns.Ktot, md.UM + wb + (size_t)i * ns.Ktot, md.VM + wb + (size_t)i * ns.Ktot, sh);
-}
+#endif  // BDC_FP32
 
 // The same with a lane group per column (G = 4 to 32 lanes, about 16 rows
 // each), for heights whose merges have N <= 1024 survivors: each lane keeps
@@ -710,7 +714,7 @@ __device__ __forceinline__ void vectors_group(const real_t *__restrict__ d, cons
         real_t v = R(0.0);
         if (j < N) {
             const real_t dj = d[j];
-            v = zt[j] / (((dj - dor) - tau) * (dj + dor + tau));
+            v = quot(zt[j], ((dj - dor) - tau) * (dj + dor + tau));
             const real_t u = (j == 0) ? -R(1.0) : dj * v;
             sv = fma(v, v, sv);
             su = fma(u, u, su);
@@ -729,6 +733,33 @@ __device__ __forceinline__ void vectors_group(const real_t *__restrict__ d, cons
             VMcol[kp] = vr[t] * iv;
             UMcol[kp] = ((j == 0) ? -R(1.0) : d[j] * vr[t]) * iu;
         }
+    }
+}
+
+// the same for N > 32 * 32 survivors (a warp per column, entries recomputed
+// for the write instead of cached)
+__device__ __forceinline__ void vectors_warp_long(const real_t *__restrict__ d, const real_t *__restrict__ zt,
+                                                  const int *__restrict__ kpos, int N, int n1, int P1, real_t dor,
+                                                  real_t tau, real_t *__restrict__ UMcol,
+                                                  real_t *__restrict__ VMcol, int lane) {
+    real_t sv = R(0.0), su = R(0.0);
+    for (int j = lane; j < N; j += 32) {
+        const real_t dj = d[j];
+        const real_t v = quot(zt[j], ((dj - dor) - tau) * (dj + dor + tau));
+        const real_t u = (j == 0) ? -R(1.0) : dj * v;
+        sv = fma(v, v, sv);
+        su = fma(u, u, su);
+    }
+    sv = warp_sum(sv);
+    su = warp_sum(su);
+    const real_t iv = R(1.0) / sqrt(sv), iu = R(1.0) / sqrt(su);
+    for (int p = n1 + lane; p < P1; p += 32) { UMcol[p] = R(0.0); VMcol[p] = R(0.0); }
+    for (int j = lane; j < N; j += 32) {
+        const real_t dj = d[j];
+        const real_t v = quot(zt[j], ((dj - dor) - tau) * (dj + dor + tau));
+        const int kp = kpos[j];
+        VMcol[kp] = v * iv;
+        UMcol[kp] = ((j == 0) ? -R(1.0) : dj * v) * iu;
     }
 }
 
@@ -755,7 +786,10 @@ __global__ void __launch_bounds__(256) k_vectors_warp(const NodeDesc *__restrict
     case 4: vectors_group<4, 16>(d, zt, kpos, N, ns.n1, ns.P1, dor, tau, UMcol, VMcol, gl); break;
     case 8: vectors_group<8, 16>(d, zt, kpos, N, ns.n1, ns.P1, dor, tau, UMcol, VMcol, gl); break;
     case 16: vectors_group<16, 16>(d, zt, kpos, N, ns.n1, ns.P1, dor, tau, UMcol, VMcol, gl); break;
-    default: vectors_group<32, 32>(d, zt, kpos, N, ns.n1, ns.P1, dor, tau, UMcol, VMcol, gl); break;
+    default:
+        if (N <= 32 * 32) vectors_group<32, 32>(d, zt, kpos, N, ns.n1, ns.P1, dor, tau, UMcol, VMcol, gl);
+        else vectors_warp_long(d, zt, kpos, N, ns.n1, ns.P1, dor, tau, UMcol, VMcol, gl);
+        break;
     }
 }
 
@@ -780,7 +814,7 @@ __global__ void __launch_bounds__(256) k_rows_update(const NodeDesc *__restrict_
     real_t sv = R(0), sf = R(0), sl = R(0);
     for (int j = lane; j < N; j += 32) {
         const real_t dj = d[j];
-        const real_t v = zt[j] / (((dj - dor) - tau) * (dj + dor + tau));
+        const real_t v = quot(zt[j], ((dj - dor) - tau) * (dj + dor + tau));
         const int kp = kpos[j];
         sv = fma(v, v, sv);
         sf = fma(FK[kp], v, sf);
@@ -840,12 +874,8 @@ cudaError_t launch_secular(const NodeDesc *nodes, int nnodes, const MatDesc *mat
 cudaError_t launch_vectors(const NodeDesc *nodes, int nnodes, const MatDesc *mats, const NodeState *state,
                            int mmax, cudaStream_t st) {
     if (nnodes <= 0) return cudaSuccess;
-    if (mmax <= 1024) {
-        const long long warps = (long long)nnodes * mmax;
-        k_vectors_warp<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(nodes, mats, state, mmax, nnodes);
-    } else {
-        k_vectors<<<(unsigned)nnodes * mmax, 256, 0, st>>>(nodes, mats, state, mmax);
-    }
+    const long long warps = (long long)nnodes * mmax;
+    k_vectors_warp<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(nodes, mats, state, mmax, nnodes);
     return cudaGetLastError();
 }
 
