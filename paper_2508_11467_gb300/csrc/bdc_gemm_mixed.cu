@@ -25,13 +25,15 @@
 //   k_slice_b : one warp per column (B is K-contiguous), same digits + F.
 //   k_mma     : persistent, one CTA per SM over the list of non-empty
 //               128 x 128 tiles; K staged 32 at a time by TMA (3-D box
-//               32 x 128 x S, 64-byte swizzle) into a 2-stage ring; warp 0
+//               32 x 128 x slices, 64-byte swizzle) into a ring of 2-4 stages
+//               (the exact-group kernel loads slices 1..4 only); warp 0
 //               issues TMA, warp 1 allocates TMEM (512 columns) and one lane
 //               issues tcgen05.mma kind::f16 (BF16 x BF16 -> FP32), warps 2-9
 //               drain and store.  Ring stages and accumulator chunks are
 //               counted across tiles, so loads and MMAs of the next tile
-//               overlap the current tile's conversion and stores.  Every mbarrier wait is bounded (2 s of
-//               %globaltimer); a timeout sets an error word and unwinds.
+//               overlap the current tile's conversion and stores.  Every
+//               mbarrier wait is bounded (2 s of %globaltimer); a timeout
+//               sets an error word and unwinds.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -55,7 +57,6 @@ struct MixProb {
 namespace {
 
 constexpr int TM = 128, TK = 32, TN_MAX = 128;
-constexpr int NSTAGE = 2;
 constexpr int EPI_WARPS = 8;
 constexpr int THREADS = 32 * (2 + EPI_WARPS);
 constexpr unsigned long long kWaitNs = 2000000000ull;   // bounded waits: 2 s
@@ -357,6 +358,21 @@ __global__ void __launch_bounds__(256) k_slice_b(const GemmProb *__restrict__ pr
 enum { MODE_E = 0, MODE_L = 1, MODE_X3 = 2 };
 constexpr int TNX = 128;
 
+// Slices loaded per stage (MODE_E multiplies slices 1..4 only), bytes per
+// stage, and ring depth: as many stages as fit in ~200 KB of shared memory,
+// 2 to 4 (a deeper ring hides more TMA latency; the operand traffic per
+// MMA is what bounds these small-K products)
+template <int S, int MODE>
+__host__ __device__ constexpr int stage_slices() { return (MODE == MODE_E && S > 4) ? 4 : S; }
+template <int S, int MODE>
+__host__ __device__ constexpr int stage_bytes() { return 2 * stage_slices<S, MODE>() * TM * TK * 2; }
+template <int S, int MODE>
+__host__ __device__ constexpr int stage_count() {
+    return (200 * 1024) / stage_bytes<S, MODE>() < 2 ? 2
+           : (200 * 1024) / stage_bytes<S, MODE>() > 4 ? 4
+                                                         : (200 * 1024) / stage_bytes<S, MODE>();
+}
+
 template <int S, int MODE>
 __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUtensorMap tmA,
                                                      const __grid_constant__ CUtensorMap tmB,
@@ -366,7 +382,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
                                                      int *__restrict__ err, const int2 *__restrict__ tiles,
                                                      const int *__restrict__ ntiles) {
     constexpr int TILE = TM * TK * 2;                 // one 128 x 32 BF16 slice tile (A or B)
-    constexpr int STAGE_BYTES = 2 * S * TILE;
+    constexpr int SL = stage_slices<S, MODE>();       // slices per operand in a stage
+    constexpr int STAGE_BYTES = stage_bytes<S, MODE>();
+    constexpr int NSTAGE = stage_count<S, MODE>();
     // kind::f16 instruction descriptor: D = F32, A = B = BF16, K-major,
     // N/8 in bits 17-22, M/16 in bits 24-28
     constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TNX >> 3) << 17) |
@@ -425,7 +443,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
                     mbar_expect_tx(&full[buf], STAGE_BYTES);
                     const uint32_t dstA = smem_u32(smem + buf * STAGE_BYTES);
                     tma_load_3d(dstA, &tmA, s * TK, mx.a_row0 + m0, 0, &full[buf]);
-                    tma_load_3d(dstA + S * TILE, &tmB, s * TK, mx.b_col0 + n0, 0, &full[buf]);
+                    tma_load_3d(dstA + SL * TILE, &tmB, s * TK, mx.b_col0 + n0, 0, &full[buf]);
                 }
             }
             // copies still in flight (after an abort) land before the CTA exits
@@ -434,17 +452,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer (one lane)
         if (lane == 0) {
-            // descriptors of every slice tile of both ring buffers, computed once;
-            // the K step of 16 (32 B) adds 2 to the 16-byte address field
-            uint64_t dA[NSTAGE][S], dB[NSTAGE][S];
-#pragma unroll
-            for (int b = 0; b < NSTAGE; ++b)
-#pragma unroll
-                for (int i = 0; i < S; ++i) {
-                    const uint32_t a = smem_u32(smem + b * STAGE_BYTES + i * TILE);
-                    dA[b][i] = sdesc(a);
-                    dB[b][i] = sdesc(a + S * TILE);
-                }
+            // descriptor of the ring's first tile; a slice tile's descriptor adds
+            // its byte offset / 16 to the 14-bit address field (shared memory
+            // addresses stay below 256 KB, so the field never carries), and the
+            // K step of 16 (32 B) adds 2
+            const uint64_t d0 = sdesc(smem_u32(smem));
             int G = 0;                                  // stages consumed so far (all tiles)
             int nA = 0, nB = 0;                         // accumulator chunks committed: set A / set B
                                                         // (MODE_E), tiles (MODE_X3)
@@ -463,8 +475,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
                     fence_after();
                     // operand "addresses" below are (buffer, tile index, K step) handles
                     auto mma = [&](uint32_t col, int ia, int ib, int kk, uint32_t acc) {
-                        const uint64_t a = (buf ? dA[1][ia] : dA[0][ia]) + 2 * kk;
-                        const uint64_t b = (buf ? dB[1][ib] : dB[0][ib]) + 2 * kk;
+                        const uint64_t a = d0 + (uint64_t)((buf * STAGE_BYTES + ia * TILE) >> 4) + 2 * kk;
+                        const uint64_t b = d0 + (uint64_t)((buf * STAGE_BYTES + (SL + ib) * TILE) >> 4) + 2 * kk;
                         asm volatile(
                             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, "
                             "p;\n}\n" ::"r"(tmem + col),
@@ -743,13 +755,14 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// 3-D map over [slice][row][Kld] BF16 with a 32 x box_rows x S box and 64 B swizzle
-bool make_map(CUtensorMap *m, void *base, int rows, int Kld, int S, int box_rows) {
+// 3-D map over [slice][row][Kld] BF16 (S slices) with a 32 x box_rows x
+// box_slices box (slices 0 .. box_slices-1) and 64 B swizzle
+bool make_map(CUtensorMap *m, void *base, int rows, int Kld, int S, int box_slices, int box_rows) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[3] = {(cuuint64_t)Kld, (cuuint64_t)rows, (cuuint64_t)S};
     cuuint64_t strides[2] = {(cuuint64_t)Kld * 2, (cuuint64_t)rows * Kld * 2};
-    cuuint32_t box[3] = {TK, (cuuint32_t)box_rows, (cuuint32_t)S};
+    cuuint32_t box[3] = {TK, (cuuint32_t)box_rows, (cuuint32_t)box_slices};
     cuuint32_t estr[3] = {1, 1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
               CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
@@ -846,19 +859,28 @@ cudaError_t run_mixed(const GemmProb *probs, int nprobs, const std::vector<MixPr
     k_slice_b<S, EXACT><<<(cbt + 7) / 8, 256, 0, st>>>(probs, dmix, nprobs, cb, cbt, Bs, F, colsB, Kld);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
-    CUtensorMap ma, mb;
-    if (!make_map(&ma, As, rowsA, Kld, S, TM) || !make_map(&mb, Bs, colsB, Kld, S, TNX)) return cudaErrorInvalidValue;
-    const size_t smem = NSTAGE * (size_t)(2 * S * TM * TK * 2) + 1024 + 256;
+    // tensor maps: boxes of all S slices, and (exact mode) of the first
+    // stage_slices<S, MODE_E> slices for the exact-group kernel
+    constexpr int SE = stage_slices<S, MODE_E>();
+    CUtensorMap ma, mb, mae, mbe;
+    if (!make_map(&ma, As, rowsA, Kld, S, S, TM) || !make_map(&mb, Bs, colsB, Kld, S, S, TNX))
+        return cudaErrorInvalidValue;
+    if (EXACT && (!make_map(&mae, As, rowsA, Kld, S, SE, TM) || !make_map(&mbe, Bs, colsB, Kld, S, SE, TNX)))
+        return cudaErrorInvalidValue;
+    auto smem_of = [](int stage, int count) { return (size_t)stage * count + 1024 + 256; };
+    const size_t smemE = smem_of(stage_bytes<S, MODE_E>(), stage_count<S, MODE_E>());
+    const size_t smemL = smem_of(stage_bytes<S, MODE_L>(), stage_count<S, MODE_L>());
+    const size_t smemX = smem_of(stage_bytes<S, MODE_X3>(), stage_count<S, MODE_X3>());
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [&] {
         if constexpr (EXACT) {
-            attr_err = cudaFuncSetAttribute(k_mma<S, MODE_E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            attr_err = cudaFuncSetAttribute(k_mma<S, MODE_E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemE);
             if (attr_err == cudaSuccess)
                 attr_err =
-                    cudaFuncSetAttribute(k_mma<S, MODE_L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                    cudaFuncSetAttribute(k_mma<S, MODE_L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemL);
         } else {
-            attr_err = cudaFuncSetAttribute(k_mma<S, MODE_X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            attr_err = cudaFuncSetAttribute(k_mma<S, MODE_X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemX);
         }
     });
     if (attr_err != cudaSuccess) return attr_err;
@@ -867,12 +889,12 @@ cudaError_t run_mixed(const GemmProb *probs, int nprobs, const std::vector<MixPr
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int grid = tiles < sm_count() ? tiles : sm_count();   // persistent: one CTA per SM
     if constexpr (EXACT) {
-        k_mma<S, MODE_E><<<grid, THREADS, smem, st>>>(ma, mb, probs, dmix, nprobs, E, F, err, tlist, ntiles);
+        k_mma<S, MODE_E><<<grid, THREADS, smemE, st>>>(mae, mbe, probs, dmix, nprobs, E, F, err, tlist, ntiles);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if constexpr (S > 4)
-            k_mma<S, MODE_L><<<grid, THREADS, smem, st>>>(ma, mb, probs, dmix, nprobs, E, F, err, tlist, ntiles);
+            k_mma<S, MODE_L><<<grid, THREADS, smemL, st>>>(ma, mb, probs, dmix, nprobs, E, F, err, tlist, ntiles);
     } else {
-        k_mma<S, MODE_X3><<<grid, THREADS, smem, st>>>(ma, mb, probs, dmix, nprobs, E, F, err, tlist, ntiles);
+        k_mma<S, MODE_X3><<<grid, THREADS, smemX, st>>>(ma, mb, probs, dmix, nprobs, E, F, err, tlist, ntiles);
     }
     return cudaGetLastError();
 }
