@@ -192,10 +192,14 @@ def run_batched(a):
     dt = torch.float32 if a.dtype == "fp32" else torch.float64
     D_pin = torch.from_numpy(Dh).to(dt).pin_memory()
     E_pin = torch.from_numpy(Eh).to(dt).pin_memory()
+    # FP64 batches take the split-BF16 products (FP64-accurate, autotuned
+    # mixed_min) unless --prec fp64 asks for FP64 tensor-core products
+    prec = "fp64" if a.dtype == "fp32" else a.prec
     t0 = time.perf_counter()
-    leaf, mm, tune_ms = bdc.autotune(ns, "fp64", reps=2, dtype=dt)
+    leaf, mm, tune_ms = bdc.autotune(ns, prec, slices=a.slices, reps=2, dtype=dt)
     tune_s = time.perf_counter() - t0
-    plan = bdc.BatchPlan(D_pin.to(dev), E_pin.to(dev), ns, leaf=leaf, dtype=dt)
+    plan = bdc.BatchPlan(D_pin.to(dev), E_pin.to(dev), ns, prec=prec, leaf=leaf, mixed_min=mm, slices=a.slices,
+                         dtype=dt)
     st = torch.cuda.current_stream()
     for _ in range(a.warmup):
         plan.launch()
@@ -271,7 +275,8 @@ def run_batched(a):
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if a.dtype == "fp32" else "f64", "data": "synthetic",
         "config": {"workload": "2048 upper bidiagonals, n = floor(exp(U(ln 32, ln 1024))) seed 3, d,e~U(0.5,1.5)",
-                   "leaf": leaf, "autotune_s": tune_s, "launch": "one CUDA graph per batch (bdc_plan_launch)",
+                   "prec": prec, "slices": a.slices if a.slices else "auto (6 up to n = 8192)",
+                   "leaf": leaf, "mixed_min": mm if prec != "fp64" else None, "autotune_s": tune_s, "launch": "one CUDA graph per batch (bdc_plan_launch)",
                    "l2": "U, V and workspace of the batch (> 5 GB) exceed L2"},
         "gflops_paper_model": flops / (ms * 1e-3) / 1e9,
         "accuracy": worst,

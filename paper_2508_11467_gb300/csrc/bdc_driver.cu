@@ -960,7 +960,7 @@ int autotune_impl(int batch, const int *h_n, bdc_opts *o, int reps, double *ms_o
         sn += h_n[b]; sn2 += (long long)h_n[b] * h_n[b];
     }
     const std::vector<int> leaves = {8, 12, 16, 24, 32};
-    const std::vector<int> mins = {128, 256, 512, 1024, 4096};   // 4096: FP64 products everywhere
+    const std::vector<int> mins = {32, 64, 128, 256, 512, 4096};   // 4096: FP64 products everywhere
     size_t lw = 0;
     for (int L : leaves) {
         bdc_opts c = base;

@@ -142,7 +142,7 @@ def test_autotune_picks_a_candidate_and_caches(bdc):
     assert (leaf2, mm2, ms2) == (leaf, mm, ms)
     assert time.perf_counter() - t0 < 0.5
     leaf3, mm3, _ = bdc.autotune(ns, "exact", reps=1)
-    assert leaf3 in (8, 12, 16, 24, 32) and mm3 in (128, 256, 512, 1024, 4096)
+    assert leaf3 in (8, 12, 16, 24, 32) and mm3 in (32, 64, 128, 256, 512, 4096)
     # the chosen configuration solves the batch correctly
     mats = inputs.batch(256, seed=3)
     _, D, E = _flat(mats)
