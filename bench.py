@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--kind", default="uniform", choices=["uniform", "graded", "clustered", "ones"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--leaf", type=int, default=16)
-    ap.add_argument("--slices", type=int, default=0, help="0 = automatic (6 up to n=8192, 7 above)")
+    ap.add_argument("--slices", type=int, default=0, help="0 = automatic (7)")
     ap.add_argument("--mixed-min", type=int, default=0, help="smallest merge order using split BF16 (0 = auto)")
     ap.add_argument("--batched", action="store_true",
                     help="config 4: 2048 bidiagonals, n log-uniform in [32, 1024], one CUDA-graph launch per batch")
@@ -275,7 +275,7 @@ def run_batched(a):
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if a.dtype == "fp32" else "f64", "data": "synthetic",
         "config": {"workload": "2048 upper bidiagonals, n = floor(exp(U(ln 32, ln 1024))) seed 3, d,e~U(0.5,1.5)",
-                   "prec": prec, "slices": a.slices if a.slices else "auto (6 up to n = 8192)",
+                   "prec": prec, "slices": a.slices if a.slices else 7,
                    "leaf": leaf, "mixed_min": mm if prec != "fp64" else None, "autotune_s": tune_s, "launch": "one CUDA graph per batch (bdc_plan_launch)",
                    "l2": "U, V and workspace of the batch (> 5 GB) exceed L2"},
         "gflops_paper_model": flops / (ms * 1e-3) / 1e9,
@@ -515,7 +515,7 @@ def main():
         "dtype": "f64" if a.prec == "fp64" else "f64 (merge products: bf16 slices, exact int accumulation)",
         "data": "synthetic",
         "config": {"workload": workload_name(a), "n": n, "prec": a.prec, "leaf": a.leaf,
-                   "slices": (a.slices or (6 if n <= 8192 else 7)) if a.prec == "exact" else None,
+                   "slices": (a.slices or 7) if a.prec == "exact" else None,
                    "l2": "inputs larger than L2 (U, V and workspace > 10 GB per step)",
                    "start": a.start, "fp32_root_start": True, "parallelism": f"replicas x{world}"},
         "gflops_paper_model": flops_model / (ms * 1e-3) / 1e9,

@@ -70,7 +70,7 @@ typedef struct {
     int seed;          /* bdc_seed                                        */
     int leaf;          /* leaf size L (4..64; 0 = default 16)             */
     int max_iter;      /* secular / QR iteration cap (0 = default 64)     */
-    int slices;        /* BDC_MIXED_EXACT slice count 4..7 (0 = automatic: 6 for n <= 8192, 7 above) */
+    int slices;        /* BDC_MIXED_EXACT slice count 4..7 (0 = automatic: 7)    */
     int checked;       /* reserved, must be 0                              */
     const float *mlp;  /* device pointer to MLP weights when seed = MLP    */
     int mixed_min;     /* split-BF16 products only for merges of order >= mixed_min,

@@ -208,13 +208,21 @@ __device__ __forceinline__ void digits(double x, int E, int (&n)[S]) {
         else if (shift > -63) X = (mant + (1ll << (-shift - 1))) >> (-shift);
         if (b >> 63) X = -X;
     }
+    // balanced base-256 digits from the bytes of X (two's complement), least
+    // significant first, on 32-bit words: a byte of 128 or more becomes
+    // byte - 256 and carries one into the next
+    const unsigned lo = (unsigned)X, hi = (unsigned)((unsigned long long)X >> 32);
+    int c = 0;
 #pragma unroll
-    for (int s = S - 1; s >= 0; --s) {
-        const long long dgt = ((X + 128) & 255) - 128;
-        n[s] = (int)dgt;
-        X = (X - dgt) >> 8;
+    for (int k = 0; k < S; ++k) {
+        const unsigned w = (k < 4) ? lo : hi;
+        const int t = (int)((w >> (8 * (k & 3))) & 255u) + c;
+        c = (t + 128) >> 8;
+        n[S - 1 - k] = t - (c << 8);
     }
-    n[0] += (int)(X << 8);   // carry out of the top digit (only when |x| 2^-E = 1/2)
+    // what is left above the S digits joins the top one (only when |x| 2^-E = 1/2)
+    const int rem = (8 * S >= 32) ? ((int)hi >> (8 * S >= 32 ? 8 * S - 32 : 0)) : (int)(X >> (8 * S < 64 ? 8 * S : 0));
+    n[0] += (rem + c) << 8;
 }
 
 __device__ __forceinline__ __nv_bfloat16 slice_bf16(int n, int s) {   // n 2^-8s (s = 0-based slice)

@@ -165,6 +165,14 @@ def test_mixed_exact_n4096(bdc, kind, seed):
     assert res <= 1e-12 and ou <= 1e-12 * 4096 and ov <= 1e-12 * 4096
 
 
+@pytest.mark.parametrize("kind,seed", [("uniform", 3), ("clustered", 4)])
+def test_mixed_exact_auto_slices_fp64_bar(bdc, kind, seed):
+    """Automatic slice count (7): the split-BF16 products meet the FP64 bar
+    itself (sigma, residual and orthogonality <= 1e-13 n)."""
+    d, e = inputs.make(kind, 4096, seed)
+    _check_full(bdc, d, e, prec="exact")
+
+
 @pytest.mark.parametrize("n,leaf", [(33, 16), (300, 16), (1000, 32)])
 def test_mixed_exact_small(bdc, n, leaf):
     d, e = inputs.uniform(n, 40 + n)
