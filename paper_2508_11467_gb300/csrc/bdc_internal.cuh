@@ -172,6 +172,17 @@ __device__ __forceinline__ int warp_isum(int v) {
     return v;
 }
 
+// |x| as an ordered integer: for non-negative values the bit patterns sort
+// like the values, so magnitude comparisons need no floating-point
+// instruction (GB300's FP64 unit takes 64 cycles per warp instruction)
+#ifdef BDC_FP32
+typedef int rbits_t;
+__device__ __forceinline__ rbits_t abits(real_t x) { return __float_as_int(x) & 0x7fffffff; }
+#else
+typedef long long rbits_t;
+__device__ __forceinline__ rbits_t abits(real_t x) { return __double_as_longlong(x) & 0x7fffffffffffffffll; }
+#endif
+
 // z / x for the pole sums and vector entries.  FP64: GB300 issues an FP64
 // division as about eight FP64-pipe operations; here the hardware reciprocal
 // estimate (PTX rcp.approx.ftz.f64, about 20 bits) is refined by two

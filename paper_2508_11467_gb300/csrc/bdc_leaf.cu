@@ -78,16 +78,10 @@ __device__ __forceinline__ void leaf_rot(real_t f, real_t g, real_t &c, real_t &
 #endif
 }
 
-// |x| as an ordered integer: for non-negative values the bit patterns sort
-// like the values, so magnitude tests need no floating-point instruction
 #ifdef BDC_FP32
-typedef int rbits_t;
 constexpr int kMant = 23, kEpsExp = 23;   // kEps = 2^-23
-__device__ __forceinline__ rbits_t abits(real_t x) { return __float_as_int(x) & 0x7fffffff; }
 #else
-typedef long long rbits_t;
 constexpr int kMant = 52, kEpsExp = 52;   // kEps = 2^-52
-__device__ __forceinline__ rbits_t abits(real_t x) { return __double_as_longlong(x) & 0x7fffffffffffffffll; }
 #endif
 
 // The leaf's negligibility test |e| <= kEps (|d1| + |d2|) or |e| <= tabs,

@@ -55,16 +55,6 @@ __device__ __forceinline__ int block_excl_scan(int v, int *wsum, int &total) {
     return base + x - v;
 }
 
-__device__ __forceinline__ real_t block_max(real_t v, real_t *dsum) {
-    v = warp_max(v);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (lane == 0) dsum[w] = v;
-    __syncthreads();
-    real_t r = 0.0;
-    for (int i = 0; i < nw; ++i) r = fmax(r, dsum[i]);
-    __syncthreads();
-    return r;
-}
 
 __device__ __forceinline__ int block_isum(int v, int *wsum) {
     int t;
@@ -136,15 +126,16 @@ __device__ int deflate_core(int m, real_t tol, const real_t *ds, real_t *zs, con
     // z_0 (paired with d_0 = 0) is clamped up to tol, never deflated
     if (t == 0) {
         real_t z0 = zs[0];
-        if (fabs(z0) < tol) zs[0] = (z0 < R(0)) ? -tol : tol;
+        if (abits(z0) < abits(tol)) zs[0] = (z0 < R(0)) ? -tol : tol;
     }
     __syncthreads();
+    const rbits_t tolb = abits(tol);
     int cnt = 0;
-    for (int p = b; p < e; ++p) cnt += (p == 0 || fabs(zs[p]) > tol);
+    for (int p = b; p < e; ++p) cnt += (p == 0 || abits(zs[p]) > tolb);
     int ns;
     int k = block_excl_scan(cnt, wsum, ns);
     for (int p = b; p < e; ++p) {
-        if (p == 0 || fabs(zs[p]) > tol) {
+        if (p == 0 || abits(zs[p]) > tolb) {
             slist[k] = p; sidx[p] = k; ++k;
         } else {
             sidx[p] = -1;
@@ -156,7 +147,7 @@ __device__ int deflate_core(int m, real_t tol, const real_t *ds, real_t *zs, con
     const int sseg = (ns + T - 1) / T;
     const int sb = min(ns, t * sseg), se = min(ns, sb + sseg);
     int za = 0;
-    for (int kk = max(sb, 1); kk < se; ++kk) za += (ds[slist[kk]] <= tol);
+    for (int kk = max(sb, 1); kk < se; ++kk) za += (abits(ds[slist[kk]]) <= tolb);
     const int a = block_isum(za, wsum);
     for (int kk = sb; kk < se; ++kk) {
         const int p = slist[kk];
@@ -240,9 +231,9 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
     // left first).  Merge path: thread t merges output positions [k0, k1),
     // an equal share, from the split of the two lists found by a binary
     // search on its diagonal; then z of every position, independently.
+    // (node values are non-negative: they are compared as bit patterns)
     const int *QL = md.Q + r0L, *QR = md.Q + r0R;
     const real_t *DL = md.D + r0L, *DR = md.D + r0R;
-    real_t dmax = 0.0;
     {
         const int mt = nl + nr, S = (mt + T - 1) / T;
         const int k0 = min(mt, t * S), k1 = min(mt, k0 + S);
@@ -250,28 +241,28 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
             int lo = max(0, k0 - nr), hi = min(k0, nl);
             while (lo < hi) {
                 const int mid = (lo + hi) >> 1;
-                if (DL[QL[mid]] <= DR[QR[k0 - mid - 1]]) lo = mid + 1; else hi = mid;
+                if (abits(DL[QL[mid]]) <= abits(DR[QR[k0 - mid - 1]])) lo = mid + 1; else hi = mid;
             }
             int i = lo, j = k0 - lo;
             real_t a = (i < nl) ? DL[QL[i]] : R(INFINITY);
             real_t b = (j < nr) ? DR[QR[j]] : R(INFINITY);
             for (int k = k0; k < k1; ++k) {
-                if (j >= nr || (i < nl && a <= b)) {
+                if (j >= nr || (i < nl && abits(a) <= abits(b))) {
                     ds[1 + k] = a;
                     src[1 + k] = 1 + QL[i];
-                    dmax = fmax(dmax, fabs(a));
                     ++i;
                     a = (i < nl) ? DL[QL[i]] : R(INFINITY);
                 } else {
                     ds[1 + k] = b;
                     src[1 + k] = nl + 1 + QR[j];
-                    dmax = fmax(dmax, fabs(b));
                     ++j;
                     b = (j < nr) ? DR[QR[j]] : R(INFINITY);
                 }
             }
         }
     }
+    // the largest value ends one of the two sorted lists
+    const real_t dmax = fmax(nl > 0 ? DL[QL[nl - 1]] : R(0), nr > 0 ? DR[QR[nr - 1]] : R(0));
     __syncthreads();
     for (int pos = 1 + t; pos < m; pos += T) {
         const int c = src[pos];
@@ -300,7 +291,6 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
         src[0] = 0;
         s_cq = cq; s_sq = sq;
     }
-    dmax = block_max(dmax, dsum);
     // 8 eps ||M|| with ||M|| ~ max(|d|, |alpha|, |beta|); the floor (2^-400 in
     // FP64, 2^-60 in FP32) keeps an all-zero node well defined (tol^2 stays a
     // normal number)

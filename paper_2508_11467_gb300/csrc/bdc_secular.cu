@@ -56,9 +56,11 @@ __device__ __forceinline__ T group_prod(T v) {
     return v;
 }
 // lanes per group for a merge with N survivors: about 16 poles per lane
+// (at most 16 below G = 32: the vector kernel caches 16 entries per lane)
 __device__ __forceinline__ int group_size(int N) {
     return N <= 64 ? 4 : N <= 128 ? 8 : N <= 256 ? 16 : 32;
 }
+static_assert(64 <= 4 * 16 && 128 <= 8 * 16 && 256 <= 16 * 16, "group_size must keep N <= 16 G below G = 32");
 
 struct Sums {
     real_t psi, dpsi, phi, dphi;
@@ -196,7 +198,7 @@ __device__ __forceinline__ void fp32_phase(const float *__restrict__ d32, const 
         for (int j = lane; j < N; j += G) {
             const float dj = d32[j], zj = z32[j];
             const float c = (j == i) ? di : (j == i + 1) ? di1 : (dj - dor) * (dj + dor);
-            const float t = zj / (c - x);
+            const float t = __fdividef(zj, c - x);   // approximate: this phase only starts the FP64 one
             if (j <= i) { psi = fmaf(zj, t, psi); dpsi = fmaf(t, t, dpsi); }
             else { phi = fmaf(zj, t, phi); dphi = fmaf(t, t, dphi); }
         }
@@ -263,7 +265,7 @@ __device__ __forceinline__ int solve_root(const real_t *__restrict__ d, const re
         for (int j = lane; j < N; j += G) {
             const float dj = d32[j], zj = z32[j];
             const float c = (j == i) ? 0.f : (j == i + 1) ? D2f : (dj - di) * (dj + di);
-            s = fmaf(zj, zj / (c - xm), s);
+            s = fmaf(zj, __fdividef(zj, c - xm), s);
         }
         s = group_sum<G>(s);
         vstart = (1.f + s >= 0.f) ? R(0.25) : R(-0.25);     // the midpoint seen from the chosen pole
@@ -782,6 +784,8 @@ __global__ void __launch_bounds__(256) k_vectors_warp(const NodeDesc *__restrict
     const int *kpos = md.kposM + r0;
     const real_t dor = d[md.org[r0 + i]], tau = md.tau[r0 + i];
     real_t *UMcol = md.UM + wb + (size_t)i * Ktot, *VMcol = md.VM + wb + (size_t)i * Ktot;
+    // the register cache holds 16 entries per lane below G = 32 (group_size
+    // keeps N <= 16 G there)
     switch (G) {
     case 4: vectors_group<4, 16>(d, zt, kpos, N, ns.n1, ns.P1, dor, tau, UMcol, VMcol, gl); break;
     case 8: vectors_group<8, 16>(d, zt, kpos, N, ns.n1, ns.P1, dor, tau, UMcol, VMcol, gl); break;
