@@ -590,6 +590,22 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
             const int m0 = (tc.y >> 16) * TM, n0 = (tc.y & 0xffff) * TNX;
             const int nk = (pr.K + TK - 1) / TK;
             const int row = m0 + 32 * q + lane;
+            const int c0 = n0 + 64 * half;
+            const bool rowok = row < pr.M;
+            const long long ldc = pr.ldc;
+            // this warp's 64 columns: their exponents F and output columns (slots),
+            // two coalesced loads per lane, handed to the final loop by shuffles
+            // instead of one dependent global load per column
+            int fbl[2], cml[2];
+            auto column_tables = [&]() {
+#pragma unroll
+                for (int h2 = 0; h2 < 2; ++h2) {
+                    const int col = c0 + 32 * h2 + lane;
+                    const bool cok = col < pr.N;
+                    fbl[h2] = (cok && MODE != MODE_X3) ? Fb[mx.b_col0 + col] : 0;
+                    cml[h2] = cok ? (pr.cmap ? pr.cmap[col] : col) : 0;
+                }
+            };
             if constexpr (MODE == MODE_E) {
                 // unsigned: the magic offsets wrap modulo 2^64 and cancel exactly at the end
                 unsigned long long L[64];
@@ -639,19 +655,30 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
                         ++cA; ++tA;
                     }
                 }
+                ok = __all_sync(0xffffffffu, ok);          // the shuffles below need the whole warp
                 if (ok) {
                     // remove the magic offsets: every set-A drain added M (2^24 + 1),
                     // every set-B drain M (2^16 + 2^8), M = 0x4B400000
                     const unsigned long long M = 0x4B400000ull;
                     const unsigned long long corr = (unsigned long long)tA * M * ((1ull << 24) + 1) +
                                                     (unsigned long long)tB * M * ((1ull << 16) + (1ull << 8));
-                    const int Er = (row < pr.M) ? Ea[mx.a_row0 + row] : 0;
+                    const int Er = rowok ? Ea[mx.a_row0 + row] : 0;
+                    column_tables();
 #pragma unroll
-                    for (int i = 0; i < 64; ++i) {
-                        const int col = n0 + 64 * half + i;
-                        if (row < pr.M && col < pr.N)
-                            pr.C[gemm_col(pr, col) + row] =
-                                i64_ldexp((long long)(L[i] - corr), Er + Fb[mx.b_col0 + col] - 40);
+                    for (int cb = 0; cb < 8; ++cb) {
+                        int F[8], cj[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const int k = 8 * cb + i;
+                            F[i] = __shfl_sync(0xffffffffu, fbl[k >> 5], k & 31);
+                            cj[i] = __shfl_sync(0xffffffffu, cml[k >> 5], k & 31);
+                        }
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const int k = 8 * cb + i;
+                            if (rowok && c0 + k < pr.N)
+                                pr.C[cj[i] * ldc + row] = i64_ldexp((long long)(L[k] - corr), Er + F[i] - 40);
+                        }
                     }
                 }
             } else if constexpr (MODE == MODE_L) {
@@ -679,21 +706,36 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
                     fence_before();
                     mbar_arrive(&accempty[b]);
                 }
+                ok = __all_sync(0xffffffffu, ok);          // the shuffles below need the whole warp
                 if (ok) {
-                    const int Er = (row < pr.M) ? Ea[mx.a_row0 + row] : 0;
+                    // C += 2^(E+F-16) SL, 8 columns at a time: their loads of C are
+                    // issued together
+                    const int Er = rowok ? Ea[mx.a_row0 + row] : 0;
+                    column_tables();
 #pragma unroll
-                    for (int i = 0; i < 64; ++i) {
-                        const int col = n0 + 64 * half + i;
-                        if (row < pr.M && col < pr.N) {
-                            const int e = Er + Fb[mx.b_col0 + col];
-                            double *c = pr.C + gemm_col(pr, col) + row;
-                            *c += f32_ldexp(SL[i], e - 16);
+                    for (int cb = 0; cb < 8; ++cb) {
+                        int F[8];
+                        long long off[8];
+                        double cv[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const int k = 8 * cb + i;
+                            F[i] = __shfl_sync(0xffffffffu, fbl[k >> 5], k & 31);
+                            off[i] = __shfl_sync(0xffffffffu, cml[k >> 5], k & 31) * ldc;
+                            cv[i] = (rowok && c0 + k < pr.N) ? pr.C[off[i] + row] : 0.0;
+                        }
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const int k = 8 * cb + i;
+                            if (rowok && c0 + k < pr.N) pr.C[off[i] + row] = cv[i] + f32_ldexp(SL[k], Er + F[i] - 16);
                         }
                     }
                 }
             } else {
-                if (!mbar_wait(&accfull[0], cA & 1, err, abort_flag)) { ok = false; break; }
+                if (!mbar_wait(&accfull[0], cA & 1, err, abort_flag)) ok = false;
+                if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }   // the shuffles need the whole warp
                 fence_after();
+                column_tables();
 #pragma unroll
                 for (int cb = 0; cb < 4; ++cb) {
                     float v[16];
@@ -701,8 +743,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
                     tmem_wait_ld();
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
-                        const int col = n0 + 64 * half + 16 * cb + i;
-                        if (row < pr.M && col < pr.N) pr.C[gemm_col(pr, col) + row] = f32_ldexp(v[i], 0);
+                        const int k = 16 * cb + i;
+                        const long long off = __shfl_sync(0xffffffffu, cml[k >> 5], k & 31) * ldc;
+                        if (rowok && c0 + k < pr.N) pr.C[off + row] = f32_ldexp(v[i], 0);
                     }
                 }
                 fence_before();
