@@ -28,8 +28,9 @@
 //               32 x 128 x slices, 64-byte swizzle) into a ring of 2-4 stages
 //               (the exact-group kernel loads slices 1..4 only); warp 0
 //               issues TMA, warp 1 allocates TMEM (512 columns) and one lane
-//               issues tcgen05.mma kind::f16 (BF16 x BF16 -> FP32), warps 2-9
-//               drain and store.  Ring stages and accumulator chunks are
+//               issues tcgen05.mma kind::f16 (BF16 x BF16 -> FP32), warps
+//               2-17 (4 per TMEM lane quarter, 32 columns each) drain and
+//               store.  Ring stages and accumulator chunks are
 //               counted across tiles, so loads and MMAs of the next tile
 //               overlap the current tile's conversion and stores.  Every
 //               mbarrier wait is bounded (2 s of %globaltimer); a timeout
@@ -57,8 +58,9 @@ struct MixProb {
 namespace {
 
 constexpr int TM = 128, TK = 32, TN_MAX = 128;
-constexpr int EPI_WARPS = 8;
+constexpr int EPI_WARPS = 16;
 constexpr int THREADS = 32 * (2 + EPI_WARPS);
+constexpr int CPT = TN_MAX * 4 / EPI_WARPS;      // accumulator columns per epilogue thread (32)
 constexpr unsigned long long kWaitNs = 2000000000ull;   // bounded waits: 2 s
 
 // ------------------------------------------------------------ PTX helpers
@@ -141,6 +143,14 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
         : "r"(taddr));
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
@@ -253,6 +263,7 @@ __global__ void __launch_bounds__(256) k_slice_a(const GemmProb *__restrict__ pr
     if (EXACT) {
         unsigned long long mx2 = 0;
         if (rowok)
+            #pragma unroll 4
             for (int k = tc; k < K; k += 8) {
                 const unsigned long long b = (unsigned long long)__double_as_longlong(pr.A[(size_t)k * pr.lda + row]) &
                                              0x7FFFFFFFFFFFFFFFull;
@@ -319,6 +330,7 @@ __global__ void __launch_bounds__(256) k_slice_b(const GemmProb *__restrict__ pr
     if (EXACT) {
         unsigned long long m = 0;
         if (colok)
+            #pragma unroll 4
             for (int k = lane; k < K; k += 32) {
                 const unsigned long long b = (unsigned long long)__double_as_longlong(col[k]) & 0x7FFFFFFFFFFFFFFFull;
                 m = b > m ? b : m;
@@ -332,6 +344,7 @@ __global__ void __launch_bounds__(256) k_slice_b(const GemmProb *__restrict__ pr
     }
     __nv_bfloat16 *dst = Bs + (size_t)(mx.b_col0 + c) * Kld;
     const int Kend = min(Kld, (K + TK - 1) / TK * TK);
+    #pragma unroll 4
     for (int k = lane; k < Kend; k += 32) {
         const double x = (colok && k < K) ? col[k] : 0.0;
         if (EXACT) {
@@ -578,8 +591,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
     } else {
         // ------------------------------------------------ epilogue (warps 2..9)
         const int q = warp & 3;                    // TMEM lane quarter this warp may access
-        const int half = (warp - 2) >> 2;          // column half
-        const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16) + 64 * half;
+        const int part = (warp - 2) >> 2;          // column part (CPT columns)
+        const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16) + CPT * part;
         bool ok = true;
         int cA = 0, cB = 0;                        // drains done: set A / set B (MODE_E), tiles (MODE_X3)
         int GL = 0;                                // stages drained (MODE_L)
@@ -590,16 +603,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
             const int m0 = (tc.y >> 16) * TM, n0 = (tc.y & 0xffff) * TNX;
             const int nk = (pr.K + TK - 1) / TK;
             const int row = m0 + 32 * q + lane;
-            const int c0 = n0 + 64 * half;
+            const int c0 = n0 + CPT * part;
             const bool rowok = row < pr.M;
             const long long ldc = pr.ldc;
-            // this warp's 64 columns: their exponents F and output columns (slots),
-            // two coalesced loads per lane, handed to the final loop by shuffles
+            // this warp's CPT columns: their exponents F and output columns
+            // (slots), coalesced loads, handed to the final loop by shuffles
             // instead of one dependent global load per column
-            int fbl[2], cml[2];
+            int fbl[CPT / 32], cml[CPT / 32];
             auto column_tables = [&]() {
 #pragma unroll
-                for (int h2 = 0; h2 < 2; ++h2) {
+                for (int h2 = 0; h2 < CPT / 32; ++h2) {
                     const int col = c0 + 32 * h2 + lane;
                     const bool cok = col < pr.N;
                     fbl[h2] = (cok && MODE != MODE_X3) ? Fb[mx.b_col0 + col] : 0;
@@ -608,26 +621,26 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
             };
             if constexpr (MODE == MODE_E) {
                 // unsigned: the magic offsets wrap modulo 2^64 and cancel exactly at the end
-                unsigned long long L[64];
+                unsigned long long L[CPT];
 #pragma unroll
-                for (int i = 0; i < 64; ++i) L[i] = 0;
+                for (int i = 0; i < CPT; ++i) L[i] = 0;
                 int tA = 0, tB = 0;                    // this tile's drains
                 for (int s = 0; s < nk && ok; ++s) {
                     if (((s & 1) == 0) || s == nk - 1) {                // set B: g1, g2
                         if (!mbar_wait(&accfull[1], cB & 1, err, abort_flag)) { ok = false; break; }
                         fence_after();
 #pragma unroll
-                        for (int cb = 0; cb < 4; ++cb) {
-                            float v1[16], v2[16];
-                            tmem_ld16(tl + 128 + 16 * cb, v1);
-                            tmem_ld16(tl + 256 + 16 * cb, v2);
+                        for (int cb = 0; cb < CPT / 8; ++cb) {
+                            float v1[8], v2[8];
+                            tmem_ld8(tl + 128 + 8 * cb, v1);
+                            tmem_ld8(tl + 256 + 8 * cb, v2);
                             tmem_wait_ld();
 #pragma unroll
-                            for (int i = 0; i < 16; ++i) {
+                            for (int i = 0; i < 8; ++i) {
                                 // raw magic bits b = I + 0x4B400000; the offsets are removed once at the end
                                 const unsigned b1 = __float_as_uint(fmaf(v1[i], 256.0f, 12582912.0f));
                                 const unsigned b2 = __float_as_uint(fmaf(v2[i], 65536.0f, 12582912.0f));
-                                L[16 * cb + i] += ((unsigned long long)b1 << 16) + ((unsigned long long)b2 << 8);
+                                L[8 * cb + i] += ((unsigned long long)b1 << 16) + ((unsigned long long)b2 << 8);
                             }
                         }
                         fence_before();
@@ -638,16 +651,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
                         if (!mbar_wait(&accfull[0], cA & 1, err, abort_flag)) { ok = false; break; }
                         fence_after();
 #pragma unroll
-                        for (int cb = 0; cb < 4; ++cb) {
-                            float v0[16], v3[16];
-                            tmem_ld16(tl + 16 * cb, v0);
-                            tmem_ld16(tl + 384 + 16 * cb, v3);
+                        for (int cb = 0; cb < CPT / 8; ++cb) {
+                            float v0[8], v3[8];
+                            tmem_ld8(tl + 8 * cb, v0);
+                            tmem_ld8(tl + 384 + 8 * cb, v3);
                             tmem_wait_ld();
 #pragma unroll
-                            for (int i = 0; i < 16; ++i) {
+                            for (int i = 0; i < 8; ++i) {
                                 const unsigned b0 = __float_as_uint(fmaf(v0[i], 1.0f, 12582912.0f));
                                 const unsigned b3 = __float_as_uint(fmaf(v3[i], 16777216.0f, 12582912.0f));
-                                L[16 * cb + i] += ((unsigned long long)b0 << 24) + (unsigned long long)b3;
+                                L[8 * cb + i] += ((unsigned long long)b0 << 24) + (unsigned long long)b3;
                             }
                         }
                         fence_before();
@@ -665,7 +678,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
                     const int Er = rowok ? Ea[mx.a_row0 + row] : 0;
                     column_tables();
 #pragma unroll
-                    for (int cb = 0; cb < 8; ++cb) {
+                    for (int cb = 0; cb < CPT / 8; ++cb) {
                         int F[8], cj[8];
 #pragma unroll
                         for (int i = 0; i < 8; ++i) {
@@ -684,23 +697,23 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
             } else if constexpr (MODE == MODE_L) {
                 // group 4 is exact per stage (and weighs <= 2^-32), groups >= 5 weigh
                 // <= 2^-40: both are summed over the stages in FP32 registers
-                float SL[64];
+                float SL[CPT];
 #pragma unroll
-                for (int i = 0; i < 64; ++i) SL[i] = 0.f;
+                for (int i = 0; i < CPT; ++i) SL[i] = 0.f;
                 for (int s = 0; s < nk; ++s, ++GL) {
                     const int b = GL & 1;
                     if (!mbar_wait(&accfull[b], (GL >> 1) & 1, err, abort_flag)) { ok = false; break; }
                     fence_after();
 #pragma unroll
-                    for (int cb = 0; cb < 4; ++cb) {
-                        float v4[16], vl[16];
-                        tmem_ld16(tl + 256 * b + 16 * cb, v4);
-                        if (S > 5) tmem_ld16(tl + 256 * b + 128 + 16 * cb, vl);
+                    for (int cb = 0; cb < CPT / 8; ++cb) {
+                        float v4[8], vl[8];
+                        tmem_ld8(tl + 256 * b + 8 * cb, v4);
+                        if (S > 5) tmem_ld8(tl + 256 * b + 128 + 8 * cb, vl);
                         tmem_wait_ld();
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) {
-                            SL[16 * cb + i] += v4[i];
-                            if (S > 5) SL[16 * cb + i] += vl[i];
+                        for (int i = 0; i < 8; ++i) {
+                            SL[8 * cb + i] += v4[i];
+                            if (S > 5) SL[8 * cb + i] += vl[i];
                         }
                     }
                     fence_before();
@@ -713,7 +726,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
                     const int Er = rowok ? Ea[mx.a_row0 + row] : 0;
                     column_tables();
 #pragma unroll
-                    for (int cb = 0; cb < 8; ++cb) {
+                    for (int cb = 0; cb < CPT / 8; ++cb) {
                         int F[8];
                         long long off[8];
                         double cv[8];
@@ -737,7 +750,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
                 fence_after();
                 column_tables();
 #pragma unroll
-                for (int cb = 0; cb < 4; ++cb) {
+                for (int cb = 0; cb < CPT / 16; ++cb) {
                     float v[16];
                     tmem_ld16(tl + 16 * cb, v);
                     tmem_wait_ld();
