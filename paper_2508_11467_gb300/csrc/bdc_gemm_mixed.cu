@@ -450,11 +450,20 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
         if (lane == 0) {
             int G = 0;                                  // stages loaded so far (all tiles)
             bool ok = true;
+            // the next tile's coordinates are loaded while this one streams
+            int2 tcn = tiles[blockIdx.x];
+            MixProb mxn = mix[tcn.x];
+            int Kn = probs[tcn.x].K;
             for (int ti = blockIdx.x; ti < count && ok; ti += gridDim.x) {
-                const int2 tc = tiles[ti];
-                const MixProb mx = mix[tc.x];
+                const int2 tc = tcn;
+                const MixProb mx = mxn;
                 const int m0 = (tc.y >> 16) * TM, n0 = (tc.y & 0xffff) * TNX;
-                const int nk = (probs[tc.x].K + TK - 1) / TK;
+                const int nk = (Kn + TK - 1) / TK;
+                if (ti + (int)gridDim.x < count) {
+                    tcn = tiles[ti + gridDim.x];
+                    mxn = mix[tcn.x];
+                    Kn = probs[tcn.x].K;
+                }
                 for (int s = 0; s < nk; ++s, ++G) {
                     const int buf = G % NSTAGE;
                     if (G >= NSTAGE && !mbar_wait(&empty[buf], ((G / NSTAGE) - 1) & 1, err, abort_flag)) {
@@ -488,8 +497,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
                 if (done > 0 && !mbar_wait(&accempty[set], (done - 1) & 1, err, abort_flag)) ok = false;
                 fence_after();
             };
+            int Kn = probs[tiles[blockIdx.x].x].K;     // the next tile's K, loaded ahead
             for (int ti = blockIdx.x; ti < count && ok; ti += gridDim.x) {
-                const int nk = (probs[tiles[ti].x].K + TK - 1) / TK;
+                const int nk = (Kn + TK - 1) / TK;
+                if (ti + (int)gridDim.x < count) Kn = probs[tiles[ti + gridDim.x].x].K;
                 for (int s = 0; s < nk && ok; ++s, ++G) {
                     const int buf = G % NSTAGE;
                     if (!mbar_wait(&full[buf], (G / NSTAGE) & 1, err, abort_flag)) { ok = false; break; }

@@ -798,25 +798,15 @@ __global__ void __launch_bounds__(256) k_vectors_warp(const NodeDesc *__restrict
 }
 
 // values only: the node's first and last rows of V for the survivors, row
-// times the normalised v_i of Eq. (M-svd-vec) computed on the fly (one warp
-// per root; no U_M / V_M is stored)
-__global__ void __launch_bounds__(256) k_rows_update(const NodeDesc *__restrict__ nodes,
-                                                     const MatDesc *__restrict__ mats,
-                                                     const NodeState *__restrict__ state, int mmax, int nnodes) {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    const int node = warp / mmax, i = warp % mmax;
-    if (node >= nnodes) return;
-    const NodeDesc nd = nodes[node];
-    const NodeState ns = state[nd.id];
-    if (i >= ns.N) return;
-    const MatDesc &md = mats[nd.mat];
-    const int r0 = nd.r0, N = ns.N;
-    const real_t *d = md.dM + r0, *zt = md.zt + r0;
-    const int *kpos = md.kposM + r0;
-    const real_t *FK = md.FK + nd.kbase, *LK = md.LK + nd.kbase;
-    const real_t dor = d[md.org[r0 + i]], tau = md.tau[r0 + i];
+// times the normalised v_i of Eq. (M-svd-vec) computed on the fly (a lane
+// group per root; no U_M / V_M is stored)
+template <int G>
+__device__ __forceinline__ void rows_group(const real_t *__restrict__ d, const real_t *__restrict__ zt,
+                                           const int *__restrict__ kpos, const real_t *__restrict__ FK,
+                                           const real_t *__restrict__ LK, int N, real_t dor, real_t tau,
+                                           real_t *vf, real_t *vl, int gl) {
     real_t sv = R(0), sf = R(0), sl = R(0);
-    for (int j = lane; j < N; j += 32) {
+    for (int j = gl; j < N; j += G) {
         const real_t dj = d[j];
         const real_t v = quot(zt[j], ((dj - dor) - tau) * (dj + dor + tau));
         const int kp = kpos[j];
@@ -824,13 +814,39 @@ __global__ void __launch_bounds__(256) k_rows_update(const NodeDesc *__restrict_
         sf = fma(FK[kp], v, sf);
         sl = fma(LK[kp], v, sl);
     }
-    sv = warp_sum(sv);
-    sf = warp_sum(sf);
-    sl = warp_sum(sl);
-    if (lane == 0) {
+    sv = group_sum<G>(sv);
+    sf = group_sum<G>(sf);
+    sl = group_sum<G>(sl);
+    if (gl == 0) {
         const real_t iv = R(1) / sqrt(sv);
-        md.vf[nd.buf][r0 + i] = sf * iv;
-        md.vl[nd.buf][r0 + i] = sl * iv;
+        *vf = sf * iv;
+        *vl = sl * iv;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_rows_update(const NodeDesc *__restrict__ nodes,
+                                                     const MatDesc *__restrict__ mats,
+                                                     const NodeState *__restrict__ state, int mmax, int nnodes) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int node = warp / mmax, w = warp % mmax;
+    if (node >= nnodes) return;
+    const NodeDesc nd = nodes[node];
+    const NodeState ns = state[nd.id];
+    const int N = ns.N, G = group_size(N), per = 32 / G;
+    const int i = w * per + lane / G;
+    if (i >= N) return;                              // whole groups leave together
+    const MatDesc &md = mats[nd.mat];
+    const int r0 = nd.r0, gl = lane & (G - 1);
+    const real_t *d = md.dM + r0, *zt = md.zt + r0;
+    const int *kpos = md.kposM + r0;
+    const real_t *FK = md.FK + nd.kbase, *LK = md.LK + nd.kbase;
+    const real_t dor = d[md.org[r0 + i]], tau = md.tau[r0 + i];
+    real_t *vf = md.vf[nd.buf] + r0 + i, *vl = md.vl[nd.buf] + r0 + i;
+    switch (G) {
+    case 4: rows_group<4>(d, zt, kpos, FK, LK, N, dor, tau, vf, vl, gl); break;
+    case 8: rows_group<8>(d, zt, kpos, FK, LK, N, dor, tau, vf, vl, gl); break;
+    case 16: rows_group<16>(d, zt, kpos, FK, LK, N, dor, tau, vf, vl, gl); break;
+    default: rows_group<32>(d, zt, kpos, FK, LK, N, dor, tau, vf, vl, gl); break;
     }
 }
 
