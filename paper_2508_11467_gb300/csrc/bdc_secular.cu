@@ -180,7 +180,7 @@ __device__ __forceinline__ int root_iterate(const real_t *__restrict__ d, const 
 // model and bracket as root_iterate, on FP32 copies of d and z with the two
 // interval poles' shifted differences taken exactly from r (0 and +-D2).
 // FP32 runs on GB300 at ~80x the FP64 rate, so this is nearly free; it stops
-// at a relative step of 2^-17 (or after 6 steps) and the FP64 iteration
+// at a relative step of 2^-17 (or after 8 steps) and the FP64 iteration
 // then finishes from there.  Other poles within ~2^-23 relative of the
 // origin are only approximate in FP32: that costs FP64 steps, never
 // accuracy.  Updates r.x (r.lo, r.hi untouched); all lanes agree.
@@ -193,7 +193,7 @@ __device__ __forceinline__ void fp32_phase(const float *__restrict__ d32, const 
     const float dor = d32[r.o];
     float x = (float)r.x, lo = (float)r.lo, hi = (float)r.hi;
     const float di = (r.o == i) ? 0.f : -D2, di1 = (r.o == i) ? D2 : 0.f;   // d_i^2 - d_o^2, d_{i+1}^2 - d_o^2
-    for (int it = 0; it < 6; ++it) {
+    for (int it = 0; it < 8; ++it) {
         float psi = 0.f, dpsi = 0.f, phi = 0.f, dphi = 0.f;
         for (int j = lane; j < N; j += G) {
             const float dj = d32[j], zj = z32[j];
