@@ -235,8 +235,13 @@ __device__ __forceinline__ void digits(double x, int E, int (&n)[S]) {
     n[0] += (rem + c) << 8;
 }
 
-__device__ __forceinline__ __nv_bfloat16 slice_bf16(int n, int s) {   // n 2^-8s (s = 0-based slice)
-    return __float2bfloat16_rn(__int2float_rn(n) * __uint_as_float((uint32_t)(127 - 8 * s) << 23));
+// n 2^-8s (s = 0-based slice, |n| <= 256) in BF16 without conversion
+// instructions: n becomes an FP32 value exactly by the 1.5 2^23 offset trick
+// (one FP32 add), scales by 2^-8s (one multiply), and having at most 8
+// significant bits its BF16 pattern is the top half of the FP32 pattern
+__device__ __forceinline__ __nv_bfloat16 slice_bf16(int n, int s) {
+    const float f = (__int_as_float(0x4B400000 + n) - 12582912.0f) * __uint_as_float((uint32_t)(127 - 8 * s) << 23);
+    return __ushort_as_bfloat16((unsigned short)(__float_as_uint(f) >> 16));
 }
 
 // A operand: 32 rows per CTA (256 threads), A column-major
