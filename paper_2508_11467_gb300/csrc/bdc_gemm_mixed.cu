@@ -38,6 +38,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -244,21 +245,19 @@ __device__ __forceinline__ __nv_bfloat16 slice_bf16(int n, int s) {
     return __ushort_as_bfloat16((unsigned short)(__float_as_uint(f) >> 16));
 }
 
-// A operand: 32 rows per CTA (256 threads), A column-major
+// A operand: 32 rows per CTA (256 threads), A column-major; grid (row blocks
+// of the largest product, products from p0), blocks past their product's
+// rows exit
 template <int S, bool EXACT>
 __global__ void __launch_bounds__(256) k_slice_a(const GemmProb *__restrict__ probs, const MixProb *__restrict__ mix,
-                                                int nprobs, int row_blocks_total, const int *__restrict__ rb_start,
-                                                __nv_bfloat16 *__restrict__ As, int *__restrict__ Ea, int rowsA,
-                                                int Kld) {
+                                                int p0, __nv_bfloat16 *__restrict__ As, int *__restrict__ Ea,
+                                                int rowsA, int Kld) {
     __shared__ unsigned long long smax[8][33];
     __shared__ __nv_bfloat16 tile[S][32][72];
-    // locate the product of this row block
-    int lo = 0, hi = nprobs - 1;
-    while (lo < hi) { int mid = (lo + hi + 1) >> 1; if (rb_start[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1; }
-    const int p = lo;
+    const int p = p0 + blockIdx.y;
     const GemmProb pr = probs[p];
     const MixProb mx = mix[p];
-    const int r0 = (blockIdx.x - rb_start[p]) * 32;
+    const int r0 = blockIdx.x * 32;
     if (r0 >= mx.Mmax) return;
     const int tr = threadIdx.x & 31, tc = threadIdx.x >> 5;   // row within block, column lane
     const int row = r0 + tr;
@@ -314,19 +313,17 @@ __global__ void __launch_bounds__(256) k_slice_a(const GemmProb *__restrict__ pr
     }
 }
 
-// B operand: one warp per column (column-major B is K-contiguous)
+// B operand: one warp per column (column-major B is K-contiguous); grid
+// (columns of the largest product / 8, products from p0), warps past their
+// product's columns exit
 template <int S, bool EXACT>
 __global__ void __launch_bounds__(256) k_slice_b(const GemmProb *__restrict__ probs, const MixProb *__restrict__ mix,
-                                                int nprobs, const int *__restrict__ cb_start, int cols_total,
-                                                __nv_bfloat16 *__restrict__ Bs, int *__restrict__ Fb, int colsB, int Kld) {
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (gw >= cols_total) return;
-    int lo = 0, hi = nprobs - 1;
-    while (lo < hi) { int mid = (lo + hi + 1) >> 1; if (cb_start[mid] <= gw) lo = mid; else hi = mid - 1; }
-    const int p = lo;
+                                                int p0, __nv_bfloat16 *__restrict__ Bs, int *__restrict__ Fb, int colsB,
+                                                int Kld) {
+    const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int p = p0 + blockIdx.y;
     const GemmProb pr = probs[p];
     const MixProb mx = mix[p];
-    const int c = gw - cb_start[p];
     if (c >= mx.Nmax) return;
     const bool colok = c < pr.N;
     const int K = pr.K;
@@ -852,7 +849,7 @@ bool make_map(CUtensorMap *m, void *base, int rows, int Kld, int S, int box_slic
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t offA, offB, offE, offF, offErr, offMix, offRb, offCb, offTiles, total;
+    size_t offA, offB, offE, offF, offErr, offMix, offTiles, total;
 };
 
 // tiles: capacity of the non-empty tile list (the no-deflation bound)
@@ -865,8 +862,6 @@ Layout layout(long long rowsA, long long colsB, int Kld, int S, int nprobs, long
     L.offF = o; o += align256(sizeof(int) * (size_t)colsB);
     L.offErr = o; o += 256;                       // error word, tile count at +16
     L.offMix = o; o += align256(sizeof(MixProb) * (size_t)nprobs);
-    L.offRb = o; o += align256(sizeof(int) * (size_t)nprobs);
-    L.offCb = o; o += align256(sizeof(int) * (size_t)nprobs);
     L.offTiles = o; o += align256(sizeof(int2) * (size_t)tiles);
     L.total = o;
     return L;
@@ -889,13 +884,11 @@ cudaError_t run_mixed(const GemmProb *probs, int nprobs, const std::vector<MixPr
     __nv_bfloat16 *Bs = (__nv_bfloat16 *)(scratch + L.offB);
     int *E = (int *)(scratch + L.offE), *F = (int *)(scratch + L.offF), *err = (int *)(scratch + L.offErr);
     MixProb *dmix = (MixProb *)(scratch + L.offMix);
-    int *rb = (int *)(scratch + L.offRb), *cb = (int *)(scratch + L.offCb);
-    // row-block and column starts
-    std::vector<int> hrb(nprobs), hcb(nprobs);
-    int rbt = 0, cbt = 0, tiles = 0;
+    // largest row and column counts of one product (the slicing grids)
+    int mrows = 1, ncols = 1, tiles = 0;
     for (int p = 0; p < nprobs; ++p) {
-        hrb[p] = rbt; rbt += (hm[p].Mmax + 31) / 32;
-        hcb[p] = cbt; cbt += hm[p].Nmax;
+        mrows = std::max(mrows, hm[p].Mmax);
+        ncols = std::max(ncols, hm[p].Nmax);
         tiles = hm[p].tile0 + ((hm[p].Mmax + TM - 1) / TM) * hm[p].tilesN;
     }
     if (hm.size() && hm[0].tilesN != (hm[0].Nmax + TNX - 1) / TNX) return cudaErrorInvalidValue;
@@ -905,7 +898,7 @@ cudaError_t run_mixed(const GemmProb *probs, int nprobs, const std::vector<MixPr
     static char *ring = nullptr;
     static size_t ring_off = 0;
     constexpr size_t kRing = 64ull << 20;
-    const size_t need = sizeof(MixProb) * nprobs + 2 * sizeof(int) * nprobs + 3 * 256;
+    const size_t need = sizeof(MixProb) * nprobs + 256;
     if (need > kRing) return cudaErrorInvalidValue;
     char *h = (char *)plan_pinned_alloc(need);
     if (!h) {
@@ -923,21 +916,19 @@ cudaError_t run_mixed(const GemmProb *probs, int nprobs, const std::vector<MixPr
     char *hp = h;
     std::memcpy(hp, hm.data(), sizeof(MixProb) * nprobs);
     cudaError_t e = cudaMemcpyAsync(dmix, hp, sizeof(MixProb) * nprobs, cudaMemcpyHostToDevice, st);
-    hp += align256(sizeof(MixProb) * nprobs);
-    std::memcpy(hp, hrb.data(), sizeof(int) * nprobs);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(rb, hp, sizeof(int) * nprobs, cudaMemcpyHostToDevice, st);
-    hp += align256(sizeof(int) * nprobs);
-    std::memcpy(hp, hcb.data(), sizeof(int) * nprobs);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(cb, hp, sizeof(int) * nprobs, cudaMemcpyHostToDevice, st);
+
     int *ntiles = err + 4;
     int2 *tlist = (int2 *)(scratch + L.offTiles);
     if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, 32, st);   // error word and tile count
     if (e != cudaSuccess) return e;
 
-    k_slice_a<S, EXACT><<<rbt, 256, 0, st>>>(probs, dmix, nprobs, rbt, rb, As, E, rowsA, Kld);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_slice_b<S, EXACT><<<(cbt + 7) / 8, 256, 0, st>>>(probs, dmix, nprobs, cb, cbt, Bs, F, colsB, Kld);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    for (int p0 = 0; p0 < nprobs; p0 += 65535) {
+        const int np = std::min(nprobs - p0, 65535);
+        k_slice_a<S, EXACT><<<dim3((mrows + 31) / 32, np), 256, 0, st>>>(probs, dmix, p0, As, E, rowsA, Kld);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_slice_b<S, EXACT><<<dim3((ncols + 7) / 8, np), 256, 0, st>>>(probs, dmix, p0, Bs, F, colsB, Kld);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
 
     // tensor maps: boxes of all S slices, and (exact mode) of the first
     // stage_slices<S, MODE_E> slices for the exact-group kernel
