@@ -6,9 +6,12 @@
 //            x = w^2 - d_o^2 (then tau = w - d_o), so d_j^2 - w^2 is formed as
 //            (d_j - d_o)(d_j + d_o) - x without cancellation.  Each step fits
 //            the two nearest poles with a rational model matching f and f'
-//            (a "middle way" step in the sense of R.-C. Li), safeguarded by a
-//            bracket; the group's lanes (4 to 32, about 16 poles each)
-//            split the pole sums and reduce with shuffles.
+//            (a "middle way" step in the sense of R.-C. Li), solved for the
+//            new iterate itself, safeguarded by a bracket; the last root
+//            lumps the other poles at d_{N-2} and keeps its own exact.  An
+//            FP32 pre-iteration starts the FP64 one.  The group's lanes (4
+//            to 32, about 16 poles each) split the pole sums and reduce
+//            with shuffles.
 //            Stopping rule: |f| <= 16 eps (1 + sum |terms|), or a step below
 //            4 eps |x|.  Optionally the start comes from a small MLP
 //            (bdc_mlp.cuh) instead of the interval midpoint; the stopping
@@ -66,19 +69,21 @@ struct Sums {
     real_t psi, dpsi, phi, dphi;
 };
 
-// pole sums at x = w^2 - d_o^2; left group j <= i (psi < 0), right j > i
+// pole sums at x = w^2 - d_o^2; left group j <= k (psi), right j > k (phi).
+// Interior roots split at k = i (psi < 0 < phi); the last root at k = N-2,
+// so that phi is its origin pole's term alone.
 template <int G>
 __device__ __forceinline__ Sums pole_sums(const real_t *__restrict__ d, const real_t *__restrict__ z,
-                                          int N, int i, real_t dor, real_t x, int lane) {
+                                          int N, int k, real_t dor, real_t x, int lane) {
     Sums s{R(0.0), R(0.0), R(0.0), R(0.0)};
     if constexpr (G < 32) {
-        // several roots per warp split their poles at different i: one loop
+        // several roots per warp split their poles at different k: one loop
         // over all poles (the same trip count for every group of the warp)
         for (int j = lane; j < N; j += G) {
             const real_t dj = d[j], zj = z[j];
             const real_t del = (dj - dor) * (dj + dor) - x;
             const real_t t = quot(zj, del);
-            if (j <= i) {
+            if (j <= k) {
                 s.psi = fma(zj, t, s.psi);
                 s.dpsi = fma(t, t, s.dpsi);
             } else {
@@ -87,14 +92,14 @@ __device__ __forceinline__ Sums pole_sums(const real_t *__restrict__ d, const re
             }
         }
     } else {
-        for (int j = lane; j <= i; j += G) {
+        for (int j = lane; j <= k; j += G) {
             const real_t dj = d[j], zj = z[j];
             const real_t del = (dj - dor) * (dj + dor) - x;
             const real_t t = quot(zj, del);
             s.psi = fma(zj, t, s.psi);
             s.dpsi = fma(t, t, s.dpsi);
         }
-        for (int j = i + 1 + lane; j < N; j += G) {
+        for (int j = k + 1 + lane; j < N; j += G) {
             const real_t dj = d[j], zj = z[j];
             const real_t del = (dj - dor) * (dj + dor) - x;
             const real_t t = quot(zj, del);
@@ -119,42 +124,50 @@ struct RootState {
     Sums s;
 };
 
+// Next iterate from the rational model of f (Eq. M-svd-val) at x: psi's poles
+// lumped into one at lamL and phi's into one at lamR, each matching value
+// and slope at x, plus a constant C.  The model's quadratic is solved for
+// the new iterate y itself, measured from the origin pole (one of lamL,
+// lamR is 0, so the constant coefficient has a single term), rather than
+// for a step from x: x + step would cancel for a root within eps |x| of
+// its pole and leave only bisection to reach it.  An interior root takes
+// the model root between lamL and lamR (the quadratic's smaller one); the
+// last root (psi: every pole but the origin, lumped at lamL = d_{N-2}^2 -
+// d_{N-1}^2; phi: the origin term alone, exact) the one right of 0.
+// Returns NaN when the model has no such root.
+template <typename T>
+__device__ __forceinline__ T model_next(T f, T dpsi, T dphi, T x, T lamL, T lamR, bool last) {
+    const T DL = lamL - x, DR = lamR - x;
+    const T sL = DL * DL * dpsi, sR = DR * DR * dphi;
+    const T C = f - DL * dpsi - DR * dphi;
+    const T a = C * (lamL + lamR) + sL + sR;
+    const T b = sL * lamR + sR * lamL;
+    if (!last) {
+        if (C == T(0)) return b / a;
+        const T disc = sqrt(fabs(a * a - T(4) * b * C));
+        return (a > T(0)) ? (T(2) * b / (a + disc)) : ((a - disc) / (T(2) * C));
+    }
+    if (!(C > T(0))) return T(NAN);
+    const T disc = sqrt(fabs(a * a - T(4) * b * C));
+    return (a >= T(0)) ? ((a + disc) / (T(2) * C)) : (T(2) * b / (a - disc));
+}
+
 // Safeguarded rational iteration from r.x; returns the iterations used or
 // -1 when max_iter did not suffice.  All lanes return the same result.
 template <int G>
 __device__ __forceinline__ int root_iterate(const real_t *__restrict__ d, const real_t *__restrict__ z, int N, int i, bool last,
                             int max_iter, RootState &r) {
     const int lane = threadIdx.x & (G - 1);
+    const int k = last ? i - 1 : i;
     int it = 0;
     for (;;) {
         const real_t f = R(1.0) + r.s.psi + r.s.phi;
-        const real_t scale = R(1.0) + r.s.phi - r.s.psi;
+        const real_t scale = R(1.0) + fabs(r.s.psi) + fabs(r.s.phi);
         if (fabs(f) <= R(16.0) * kEps * scale) break;
         if (f > R(0.0)) r.hi = r.x; else r.lo = r.x;
         if (it >= max_iter) return -1;
-        // rational model through the two nearest poles (value and slope)
-        const real_t DL = r.lamL - r.x;
-        real_t eta;
-        bool ok = true;
-        if (!last) {
-            const real_t DR = r.lamR - r.x;
-            const real_t sL = DL * DL * r.s.dpsi, sR = DR * DR * r.s.dphi;
-            const real_t C = f - DL * r.s.dpsi - DR * r.s.dphi;
-            const real_t a = C * (DL + DR) + sL + sR;
-            const real_t b = C * DL * DR + sL * DR + sR * DL;
-            if (C == R(0.0)) {
-                eta = b / a;
-            } else {
-                const real_t disc = sqrt(fabs(a * a - R(4.0) * b * C));
-                eta = (a > R(0.0)) ? (R(2.0) * b / (a + disc)) : ((a - disc) / (R(2.0) * C));
-            }
-        } else {
-            const real_t sL = DL * DL * r.s.dpsi;
-            const real_t C = f - DL * r.s.dpsi;
-            if (C > R(0.0)) eta = DL + sL / C; else { eta = R(0.0); ok = false; }
-        }
-        real_t xn = r.x + eta;
-        if (!ok || !(xn > r.lo && xn < r.hi)) xn = R(0.5) * (r.lo + r.hi);
+        real_t xn = model_next<real_t>(f, r.s.dpsi, r.s.dphi, r.x, r.lamL, r.lamR, last);
+        if (!(xn > r.lo && xn < r.hi)) xn = R(0.5) * (r.lo + r.hi);
         const real_t step = xn - r.x;
         r.x = xn;
         ++it;
@@ -170,55 +183,43 @@ __device__ __forceinline__ int root_iterate(const real_t *__restrict__ d, const 
                 r.o = i; r.dor = r.dl; r.x += D2; r.lo += D2; r.hi += D2; r.lamL = R(0.0); r.lamR = D2;
             }
         }
-        r.s = pole_sums<G>(d, z, N, i, r.dor, r.x, lane);
+        r.s = pole_sums<G>(d, z, N, k, r.dor, r.x, lane);
         if (fabs(step) <= R(4.0) * kEps * fabs(r.x)) break;
     }
     return it;
 }
 
-// FP32 pre-iteration of root i (not the last) from r.x: the same rational
-// model and bracket as root_iterate, on FP32 copies of d and z with the two
-// interval poles' shifted differences taken exactly from r (0 and +-D2).
-// FP32 runs on GB300 at ~80x the FP64 rate, so this is nearly free; it stops
-// at a relative step of 2^-17 (or after 8 steps) and the FP64 iteration
+// FP32 pre-iteration of root i from r.x: the same rational model and
+// bracket as root_iterate, on FP32 copies of d and z, with the shifted
+// differences of the two poles the model lumps at (j = k and k + 1: lamL
+// and lamR) taken exactly from r.  FP32 runs on GB300 at ~80x the FP64
+// rate, so this is nearly free; it stops at a relative step of 2^-17 (or
+// after 16 steps, or where an FP32 sum overflows) and the FP64 iteration
 // then finishes from there.  Other poles within ~2^-23 relative of the
 // origin are only approximate in FP32: that costs FP64 steps, never
 // accuracy.  Updates r.x (r.lo, r.hi untouched); all lanes agree.
 template <int G>
 __device__ __forceinline__ void fp32_phase(const float *__restrict__ d32, const float *__restrict__ z32, int N,
-                                           int i, RootState &r) {
+                                           int i, bool last, RootState &r) {
     const int lane = threadIdx.x & (G - 1);
-    const float D2 = (float)(r.lamR - r.lamL);
+    const int k = last ? i - 1 : i;
     const float lamL = (float)r.lamL, lamR = (float)r.lamR;
     const float dor = d32[r.o];
     float x = (float)r.x, lo = (float)r.lo, hi = (float)r.hi;
-    const float di = (r.o == i) ? 0.f : -D2, di1 = (r.o == i) ? D2 : 0.f;   // d_i^2 - d_o^2, d_{i+1}^2 - d_o^2
-    for (int it = 0; it < 8; ++it) {
+    for (int it = 0; it < 16; ++it) {
         float psi = 0.f, dpsi = 0.f, phi = 0.f, dphi = 0.f;
         for (int j = lane; j < N; j += G) {
             const float dj = d32[j], zj = z32[j];
-            const float c = (j == i) ? di : (j == i + 1) ? di1 : (dj - dor) * (dj + dor);
+            const float c = (j == k) ? lamL : (j == k + 1) ? lamR : (dj - dor) * (dj + dor);
             const float t = __fdividef(zj, c - x);   // approximate: this phase only starts the FP64 one
-            if (j <= i) { psi = fmaf(zj, t, psi); dpsi = fmaf(t, t, dpsi); }
+            if (j <= k) { psi = fmaf(zj, t, psi); dpsi = fmaf(t, t, dpsi); }
             else { phi = fmaf(zj, t, phi); dphi = fmaf(t, t, dphi); }
         }
         psi = group_sum<G>(psi); dpsi = group_sum<G>(dpsi); phi = group_sum<G>(phi); dphi = group_sum<G>(dphi);
         const float f = 1.f + psi + phi;
-        if (!(f == f)) return;                               // no usable FP32 information
+        if (!(fabsf(f) + dpsi + dphi < INFINITY)) break;   // no usable FP32 information at x
         if (f > 0.f) hi = x; else lo = x;
-        const float DL = lamL - x, DR = lamR - x;
-        const float sL = DL * DL * dpsi, sR = DR * DR * dphi;
-        const float C = f - DL * dpsi - DR * dphi;
-        const float a = C * (DL + DR) + sL + sR;
-        const float b = C * DL * DR + sL * DR + sR * DL;
-        float eta;
-        if (C == 0.f) {
-            eta = b / a;
-        } else {
-            const float disc = sqrtf(fabsf(a * a - 4.f * b * C));
-            eta = (a > 0.f) ? (2.f * b / (a + disc)) : ((a - disc) / (2.f * C));
-        }
-        float xn = x + eta;
+        float xn = model_next<float>(f, dpsi, dphi, x, lamL, lamR, last);
         if (!(xn > lo && xn < hi)) xn = 0.5f * (lo + hi);
         const float step = xn - x;
         x = xn;
@@ -251,12 +252,12 @@ __device__ __forceinline__ int solve_root(const real_t *__restrict__ d, const re
     const real_t dl = d[i];
     const real_t du = last ? sqrt(dl * dl + zz) : d[i + 1];
     const real_t h = R(0.5) * (du - dl);
-    const bool pre32 = !last && d32 != nullptr;
+    const bool pre32 = d32 != nullptr;
     const bool use_mlp = !last && ((vstart == vstart) || pre32);
     RootState r;
     r.dl = dl;
     r.du = du;
-    if (pre32 && !(vstart == vstart)) {
+    if (pre32 && !last && !(vstart == vstart)) {
         // FP32 sign at the interval midpoint picks the origin (a wrong pick
         // near the midpoint is repaired by the origin switch)
         const float xm = (float)(h * (R(2.0) * dl + h)), D2f = (float)((du - dl) * (du + dl));
@@ -278,7 +279,7 @@ __device__ __forceinline__ int solve_root(const real_t *__restrict__ d, const re
             r.o = i + 1; r.dor = du; r.lo = -D2; r.hi = R(0.0); r.lamL = -D2; r.lamR = R(0.0); r.x = vstart * D2;
         }
         if (!(r.x > r.lo && r.x < r.hi)) r.x = R(0.5) * (r.lo + r.hi);
-        if (pre32) fp32_phase<G>(d32, z32, N, i, r);
+        if (pre32) fp32_phase<G>(d32, z32, N, i, false, r);
         r.s = pole_sums<G>(d, z, N, i, r.dor, r.x, lane);
     } else if (!last) {
         // sign of f at the interval midpoint picks the nearer pole as origin
@@ -295,10 +296,14 @@ __device__ __forceinline__ int solve_root(const real_t *__restrict__ d, const re
             r.x = r.lo;                    // the same point, measured from d_{i+1}
         }
     } else {
+        // last root, w in (d_{N-1}, sqrt(d_{N-1}^2 + |z|^2)): origin d_{N-1};
+        // the other poles lumped at d_{N-2}^2 - d_{N-1}^2
+        const real_t dp = d[i - 1];
         r.o = i; r.dor = dl; r.lo = R(0.0); r.hi = zz;
-        r.lamL = R(0.0); r.lamR = R(0.0);
+        r.lamL = -(dl - dp) * (dl + dp); r.lamR = R(0.0);
         r.x = R(0.5) * zz;
-        r.s = pole_sums<G>(d, z, N, i, r.dor, r.x, lane);
+        if (pre32) fp32_phase<G>(d32, z32, N, i, true, r);
+        r.s = pole_sums<G>(d, z, N, i - 1, r.dor, r.x, lane);
     }
     int it = root_iterate<G>(d, z, N, i, last, max_iter, r);
     if (use_mlp && it >= 0) {
