@@ -253,44 +253,69 @@ MatDesc carve(char *base, size_t off, int n, int vals = 0) {
 }
 
 // ------------------------------------------------------------------ kernels
-__global__ void k_scale(const MatDesc *__restrict__ mats) {
-    __shared__ real_t sh[32];
-    __shared__ int bad;
+#ifdef BDC_FP32
+constexpr int kMantBits = 23, kExpMax = 255;
+__device__ __forceinline__ rbits_t rbits(real_t v) { return __float_as_int(v); }
+__device__ __forceinline__ real_t from_bits(rbits_t b) { return __int_as_float(b); }
+#else
+constexpr int kMantBits = 52, kExpMax = 2047;
+__device__ __forceinline__ rbits_t rbits(real_t v) { return __double_as_longlong(v); }
+__device__ __forceinline__ real_t from_bits(rbits_t b) { return __longlong_as_double(b); }
+#endif
+
+// v 2^-ex for finite v: by exponent-field arithmetic (integer operations)
+// when v and the result are normal numbers, else scalbn (zeros, entries
+// that fall below the normal range).  One CTA scales a whole matrix, and
+// its FP64 rate (a few operations per clock) would bound the kernel.
+__device__ __forceinline__ real_t scale_pow2(real_t v, int ex) {
+    const rbits_t b = rbits(v);
+    const int e = (int)((b >> kMantBits) & kExpMax);
+    if (e != 0 && e - ex >= 1 && e - ex < kExpMax) return from_bits(b - ((rbits_t)ex << kMantBits));
+    return scalbn(v, -ex);
+}
+
+// Scale by the power of two 2^ex <= max |entry| < 2^(ex+1): exact (no
+// rounding in or out).  The maximum and the finiteness test are taken on
+// the bit patterns (integer comparisons).
+__global__ void __launch_bounds__(1024) k_scale(const MatDesc *__restrict__ mats) {
+    __shared__ rbits_t sh[32];
     const MatDesc &md = mats[blockIdx.x];
     const int n = md.n;
-    if (threadIdx.x == 0) bad = 0;
-    __syncthreads();
-    real_t mx = R(0);
-    int nonfinite = 0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const real_t v = md.d_in[i];
-        nonfinite |= !isfinite(v);
-        mx = fmax(mx, fabs(v));
-        if (i + 1 < n) {
-            const real_t w = md.e_in[i];
-            nonfinite |= !isfinite(w);
-            mx = fmax(mx, fabs(w));
+    constexpr rbits_t kInfBits = (rbits_t)kExpMax << kMantBits;   // |v| bits >= this: Inf or NaN
+    rbits_t mx = 0;
+    // four entries of d and of e per thread in flight (one CTA reads the
+    // whole matrix: latency, not bandwidth, bounds this loop)
+    const int T = blockDim.x;
+    for (int i0 = threadIdx.x; i0 < n; i0 += 4 * T) {
+        real_t v[4], w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * T;
+            v[u] = (i < n) ? md.d_in[i] : R(0);
+            w[u] = (i + 1 < n) ? md.e_in[i] : R(0);
         }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) mx = max(mx, max(abits(v[u]), abits(w[u])));
     }
-    mx = warp_max(mx);
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, (rbits_t)__shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
-    if (nonfinite) atomicOr(&bad, 1);
     __syncthreads();
-    real_t s = R(0);
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s = fmax(s, sh[k]);
-    const bool nf = bad != 0;
-    const real_t se = (nf || s == R(0)) ? R(1) : s;
+    rbits_t sb = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) sb = max(sb, sh[k]);
+    const bool nf = sb >= kInfBits;
+    const real_t s = from_bits(sb);
+    const int ex = (nf || sb == 0) ? 0 : ilogb(s);
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        md.dsc[i] = nf ? R(0) : md.d_in[i] / se;
-        md.esc[i] = (nf || i + 1 >= n) ? R(0) : md.e_in[i] / se;
+        md.dsc[i] = nf ? R(0) : scale_pow2(md.d_in[i], ex);
+        md.esc[i] = (nf || i + 1 >= n) ? R(0) : scale_pow2(md.e_in[i], ex);
     }
     if (threadIdx.x == 0) {
-        md.scale[0] = nf ? R(0) : s;
+        md.scale[0] = (nf || s == R(0)) ? R(0) : scalbn(R(1), ex);   // a zero matrix has zero values
         md.info[0] = nf ? BDC_ERR_NONFINITE : 0;
     }
 }
 
-// final order (descending), unscale, U columns and V^T rows (tiled transpose)
+// status word of every matrix
 __global__ void k_info(const MatDesc *__restrict__ mats, int nmat, int *__restrict__ out) {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m < nmat) out[m] = *mats[m].info;
@@ -303,18 +328,24 @@ __global__ void k_final_values(const MatDesc *__restrict__ mats) {
     if (c < md.n) md.So[c] = md.D[md.Q[md.n - 1 - c]] * md.scale[0];
 }
 
-__global__ void k_final(const MatDesc *__restrict__ mats, int tiles_per_side) {
+// Final order (descending), unscale, U columns and V^T rows (tiled
+// transpose).  One CTA per strip of 32 output columns x FINAL_ROWS rows: the strip's
+// column sources (slot and row range of U and V) are read once, then the
+// strip is written as 32 x 32 tiles, V through shared memory (transposed).
+// Each thread loads its four U and four V entries of a tile before any
+// store, so the loads of a tile are in flight together.
+constexpr int FINAL_ROWS = 512;
+__global__ void __launch_bounds__(256) k_final(const MatDesc *__restrict__ mats, int tiles_per_side) {
     __shared__ real_t tile[32][33];
     const MatDesc &md = mats[blockIdx.z];
     const int n = md.n;
-    const int tc = blockIdx.x % tiles_per_side, tj = blockIdx.x / tiles_per_side;
-    const int c0 = tc * 32, j0 = tj * 32;
-    if (c0 >= n || j0 >= n) return;
+    const int c0 = blockIdx.x * 32, jb = blockIdx.y * FINAL_ROWS;
+    if (c0 >= n || jb >= n) return;
+    const int je = min(n, jb + FINAL_ROWS);
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
     const real_t s = md.scale[0];
     // U: output column c = the root's column Q[n-1-c] (slots of copy 0: the
-    // root has depth 0), rows j0..j0+31; rows outside a slot's range are zero.
-    // The tile's 32 columns: slots and ranges staged once in shared memory.
+    // root has depth 0), rows outside a slot's range are zero
     __shared__ int cg[2][32], clo[2][32], chi[2][32];
     if (threadIdx.x < 32) {
         const int c = c0 + threadIdx.x;
@@ -323,25 +354,37 @@ __global__ void k_final(const MatDesc *__restrict__ mats, int tiles_per_side) {
             const int gu = md.us[0][src], gv = md.vs[0][src];
             cg[0][threadIdx.x] = gu; clo[0][threadIdx.x] = md.ulo[gu]; chi[0][threadIdx.x] = md.uhi[gu];
             cg[1][threadIdx.x] = gv; clo[1][threadIdx.x] = md.vlo[gv]; chi[1][threadIdx.x] = md.vhi[gv];
-            if (tj == 0) md.So[c] = md.D[src] * s;
+            if (blockIdx.y == 0) md.So[c] = md.D[src] * s;
+        } else {
+            cg[0][threadIdx.x] = cg[1][threadIdx.x] = 0;
+            clo[0][threadIdx.x] = chi[0][threadIdx.x] = clo[1][threadIdx.x] = chi[1][threadIdx.x] = 0;
         }
     }
     __syncthreads();
-    for (int cc = ty; cc < 32; cc += 8) {
-        const int c = c0 + cc;
-        if (c >= n) break;
+    for (int j0 = jb; j0 < je; j0 += 32) {
         const int j = j0 + tx;
-        if (j < n) {
-            md.Uo[(size_t)c * md.ldu + j] =
-                (j >= clo[0][cc] && j < chi[0][cc]) ? md.U[(size_t)cg[0][cc] * n + j] : R(0);
-            tile[cc][tx] = (j >= clo[1][cc] && j < chi[1][cc]) ? md.V[(size_t)cg[1][cc] * n + j] : R(0);
+        real_t u[4], v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int cc = ty + 8 * q;
+            const bool ok = j < n && c0 + cc < n;
+            u[q] = (ok && j >= clo[0][cc] && j < chi[0][cc]) ? md.U[(size_t)cg[0][cc] * n + j] : R(0);
+            v[q] = (ok && j >= clo[1][cc] && j < chi[1][cc]) ? md.V[(size_t)cg[1][cc] * n + j] : R(0);
         }
-    }
-    __syncthreads();
-    // VT(c, j) = V(j, src(c)): write down columns j of VT, contiguous in c
-    for (int jj = ty; jj < 32; jj += 8) {
-        const int j = j0 + jj, c = c0 + tx;
-        if (j < n && c < n) md.VTo[(size_t)j * md.ldvt + c] = tile[tx][jj];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int cc = ty + 8 * q, c = c0 + cc;
+            if (j < n && c < n) md.Uo[(size_t)c * md.ldu + j] = u[q];
+            tile[cc][tx] = v[q];
+        }
+        __syncthreads();
+        // VT(c, j) = V(j, src(c)): write down rows j of VT, contiguous in c
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int jj = ty + 8 * q, jr = j0 + jj, c = c0 + tx;
+            if (jr < n && c < n) md.VTo[(size_t)jr * md.ldvt + c] = tile[tx][jj];
+        }
+        __syncthreads();
     }
 }
 
@@ -489,7 +532,7 @@ int run_plan(const Plan &p, const bdc_opts &o, char *work, std::vector<MatDesc> 
     for (int mi = 0; mi < p.nmat; ++mi) nsq += (double)mats[mi].n * mats[mi].n;
     if (p.nmat > 0) {
         StageScope sc(st, BDC_STAGE_SCALE, 1, 0.0);
-        k_scale<<<p.nmat, 256, 0, st>>>(dmats);
+        k_scale<<<p.nmat, 1024, 0, st>>>(dmats);
         if ((e = cudaGetLastError()) != cudaSuccess) return note(e);
     }
     {
@@ -580,12 +623,14 @@ int run_plan(const Plan &p, const bdc_opts &o, char *work, std::vector<MatDesc> 
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return note(e);
     } else if (p.nmat > 0) {
-        // reads U, V (16 n^2 B), writes U, V^T (16 n^2 B)
-        StageScope sc(st, BDC_STAGE_FINAL, (p.nmat + 65534) / 65535, 32.0 * nsq);
+        // writes U, V^T (16 n^2 B); reads only the slots' row ranges of U, V
+        // (at most another 16 n^2 B, far less after deflation): the writes
+        // are the algorithmic bytes counted
+        StageScope sc(st, BDC_STAGE_FINAL, (p.nmat + 65534) / 65535, 16.0 * nsq);
         const int tps = (p.nmax + 31) / 32;
         for (int m0 = 0; m0 < p.nmat; m0 += 65535) {
             const int nm = std::min(65535, p.nmat - m0);
-            dim3 grid((unsigned)tps * tps, 1, nm);
+            dim3 grid((unsigned)tps, (unsigned)(p.nmax + FINAL_ROWS - 1) / FINAL_ROWS, nm);
             k_final<<<grid, 256, 0, st>>>(dmats + m0, tps);
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return note(e);

@@ -22,7 +22,7 @@
 //   k_slice_a : 32 rows per CTA, two passes over K through shared memory
 //               (row maxima, then integer digit extraction), row-major
 //               K-contiguous BF16 slices [slice][row][Kld] + exponents E.
-//   k_slice_b : one warp per column (B is K-contiguous), same digits + F.
+//   k_slice_b : 8 or 32 lanes per column (B is K-contiguous), same digits + F.
 //   k_mma     : persistent, one CTA per SM over the list of non-empty
 //               128 x 128 tiles; K staged 32 at a time by TMA (3-D box
 //               32 x 128 x slices, 64-byte swizzle) into a ring of 2-4 stages
@@ -59,6 +59,7 @@ struct MixProb {
 namespace {
 
 constexpr int TM = 128, TK = 32, TN_MAX = 128;
+constexpr int TNX = 128;   // tile width along N of the MMA kernels
 constexpr int EPI_WARPS = 16;
 constexpr int THREADS = 32 * (2 + EPI_WARPS);
 constexpr int CPT = TN_MAX * 4 / EPI_WARPS;      // accumulator columns per epilogue thread (32)
@@ -313,18 +314,25 @@ __global__ void __launch_bounds__(256) k_slice_a(const GemmProb *__restrict__ pr
     }
 }
 
-// B operand: one warp per column (column-major B is K-contiguous); grid
-// (columns of the largest product / 8, products from p0), warps past their
-// product's columns exit
-template <int S, bool EXACT>
+// B operand: LANES lanes per column (column-major B is K-contiguous),
+// 32 / LANES columns per warp; grid (columns of the host bound of the
+// largest product / (256 / LANES), products from p0).  K is a merge's
+// survivor count: eight lanes per column for the small merges (a few
+// dozen K, where a whole warp per column would mostly wait on its loads),
+// a warp per column for the large ones.  Only the columns the MMA tiles
+// read are written: those below N, and zeros up to N rounded up to the
+// tile width; lanes past them exit (N, the survivor count, is known only on
+// the device and is often far below the host bound)
+template <int S, bool EXACT, int LANES>
 __global__ void __launch_bounds__(256) k_slice_b(const GemmProb *__restrict__ probs, const MixProb *__restrict__ mix,
                                                 int p0, __nv_bfloat16 *__restrict__ Bs, int *__restrict__ Fb, int colsB,
                                                 int Kld) {
-    const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int c = (blockIdx.x * blockDim.x + threadIdx.x) / LANES, l = threadIdx.x & (LANES - 1);
+    const unsigned gmask = (LANES == 32) ? 0xffffffffu : ((1u << (LANES & 31)) - 1) << (threadIdx.x & (32 - LANES));
     const int p = p0 + blockIdx.y;
     const GemmProb pr = probs[p];
     const MixProb mx = mix[p];
-    if (c >= mx.Nmax) return;
+    if (c >= mx.Nmax || c >= (pr.N + TNX - 1) / TNX * TNX) return;   // whole lane groups leave together
     const bool colok = c < pr.N;
     const int K = pr.K;
     const double *col = pr.B + (size_t)c * pr.ldb;
@@ -333,21 +341,21 @@ __global__ void __launch_bounds__(256) k_slice_b(const GemmProb *__restrict__ pr
         unsigned long long m = 0;
         if (colok)
             #pragma unroll 4
-            for (int k = lane; k < K; k += 32) {
+            for (int k = l; k < K; k += LANES) {
                 const unsigned long long b = (unsigned long long)__double_as_longlong(col[k]) & 0x7FFFFFFFFFFFFFFFull;
                 m = b > m ? b : m;
             }
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long y = __shfl_xor_sync(0xffffffffu, m, o);
+        for (int o = LANES / 2; o > 0; o >>= 1) {
+            const unsigned long long y = __shfl_xor_sync(gmask, m, o);
             m = y > m ? y : m;
         }
         F = scale_exp(m);
-        if (lane == 0) Fb[mx.b_col0 + c] = colok ? F : 0;
+        if (l == 0) Fb[mx.b_col0 + c] = colok ? F : 0;
     }
     __nv_bfloat16 *dst = Bs + (size_t)(mx.b_col0 + c) * Kld;
     const int Kend = min(Kld, (K + TK - 1) / TK * TK);
     #pragma unroll 4
-    for (int k = lane; k < Kend; k += 32) {
+    for (int k = l; k < Kend; k += LANES) {
         const double x = (colok && k < K) ? col[k] : 0.0;
         if (EXACT) {
             int n[S];
@@ -379,7 +387,6 @@ __global__ void __launch_bounds__(256) k_slice_b(const GemmProb *__restrict__ pr
 //   MODE_X3  BF16x3: (hi, lo) pairs (0,0), (0,1), (1,0) in one accumulator
 //            over the whole K.  Writes C.
 enum { MODE_E = 0, MODE_L = 1, MODE_X3 = 2 };
-constexpr int TNX = 128;
 
 // Slices loaded per stage (MODE_E multiplies slices 1..4 only), bytes per
 // stage, and ring depth: as many stages as fit in ~200 KB of shared memory,
@@ -926,7 +933,10 @@ cudaError_t run_mixed(const GemmProb *probs, int nprobs, const std::vector<MixPr
         const int np = std::min(nprobs - p0, 65535);
         k_slice_a<S, EXACT><<<dim3((mrows + 31) / 32, np), 256, 0, st>>>(probs, dmix, p0, As, E, rowsA, Kld);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        k_slice_b<S, EXACT><<<dim3((ncols + 7) / 8, np), 256, 0, st>>>(probs, dmix, p0, Bs, F, colsB, Kld);
+        if (ncols <= 128)
+            k_slice_b<S, EXACT, 8><<<dim3((ncols + 31) / 32, np), 256, 0, st>>>(probs, dmix, p0, Bs, F, colsB, Kld);
+        else
+            k_slice_b<S, EXACT, 32><<<dim3((ncols + 7) / 8, np), 256, 0, st>>>(probs, dmix, p0, Bs, F, colsB, Kld);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
 

@@ -264,14 +264,42 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
     // the largest value ends one of the two sorted lists
     const real_t dmax = fmax(nl > 0 ? DL[QL[nl - 1]] : R(0), nr > 0 ? DR[QR[nr - 1]] : R(0));
     __syncthreads();
-    for (int pos = 1 + t; pos < m; pos += T) {
-        const int c = src[pos];
-        if (c <= nl) {
-            const int j = c - 1;
-            zs[pos] = alpha * (md.vals ? md.vl[1 - nd.buf][r0L + j] : vrow(cvs[r0L + j], r0L + nl));
+    // z of every position: alpha times the last row of a left child's right
+    // vector, beta times the first row of a right child's.  Four positions
+    // per thread in flight: each level of the chain (source column, its
+    // slot, the slot's range and entry) is loaded for all four before the
+    // next, and the slot entry unconditionally (it lies inside the slot
+    // column whatever its range), so the loads do not wait on one another.
+    for (int pos0 = 1 + t; pos0 < m; pos0 += 4 * T) {
+        int jx[4];
+        bool left[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int pos = pos0 + u * T;
+            const int c = (pos < m) ? src[pos] : 1;
+            left[u] = c <= nl;
+            jx[u] = left[u] ? r0L + c - 1 : r0R + (c - nl - 1);
+        }
+        real_t zv[4];
+        if (md.vals) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) zv[u] = left[u] ? md.vl[1 - nd.buf][jx[u]] : md.vf[1 - nd.buf][jx[u]];
         } else {
-            const int j = c - nl - 1;
-            zs[pos] = beta * (md.vals ? md.vf[1 - nd.buf][r0R + j] : vrow(cvs[r0R + j], r0R));
+            int g[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) g[u] = cvs[jx[u]];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const long long row = left[u] ? r0L + nl : r0R;
+                const int lo = md.vlo[g[u]], hi = md.vhi[g[u]];
+                const real_t v = md.V[(size_t)g[u] * ld + row];
+                zv[u] = (row >= lo && row < hi) ? v : R(0);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int pos = pos0 + u * T;
+            if (pos < m) zs[pos] = (left[u] ? alpha : beta) * zv[u];
         }
     }
     __shared__ real_t s_cq, s_sq;
@@ -338,41 +366,56 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
     int *nus = slots ? md.us[nd.buf] + r0 : nullptr, *nvs = slots ? md.vs[nd.buf] + r0 : nullptr;
     auto slot_u = [&](int c) { return c == 0 ? r0 + nl : (c <= nl ? cus[r0L + c - 1] : cus[r0R + (c - nl - 1)]); };
     auto slot_v = [&](int c) { return c == 0 ? cvs[r0L + nl] : (c <= nl ? cvs[r0L + c - 1] : cvs[r0R + (c - nl - 1)]); };
-    for (int p = b; p < e; ++p) {
-        const int r = role[p], code = r & 15;
-        int col;                                     // node column of sorted position p
-        if (code == ROLE_KEEP) {
-            int kp;
-            if (p == 0) kp = P1;
-            else {
-                const int ty = (r >> 8) & 3;
-                kp = (ty == 1) ? i1++ : (ty == 3) ? (P1 + 1 + i2++) : (P1 + 1 + n2 + i3++);
-            }
-            dM[ik] = ds[p];
-            zM[ik] = zs[p];
-            md.d32[r0 + ik] = (float)ds[p];
-            md.z32[r0 + ik] = (float)zs[p];
-            kposM[ik] = kp;
-            invK[kp] = ik;
-            dest[p] = kp;
-            col = ik;
-            ++ik;
-        } else if (code == ROLE_ZERO) {
-            dval[iz] = R(0);
-            dsrc[iz] = p;
-            dest[p] = -(1 + iz);
-            col = N + iz;
-            ++iz;
-        } else {
-            const int slot = nz + io++;
-            dval[slot] = ds[p];
-            dsrc[slot] = p;
-            dest[p] = -(1 + slot);
-            col = N + slot;
+    // four positions at a time: their roles, sources and slots are loaded
+    // before any of their stores (which the compiler may not move loads past)
+    for (int p0 = b; p0 < e; p0 += 4) {
+        int rl[4], su[4], sv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int p = min(p0 + u, e - 1);
+            rl[u] = role[p];
+            su[u] = sv[u] = 0;
+            if (slots) { const int c = src[p]; su[u] = slot_u(c); sv[u] = slot_v(c); }
         }
-        if (slots) {
-            nus[col] = slot_u(src[p]);
-            nvs[col] = slot_v(src[p]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int p = p0 + u;
+            if (p >= e) break;
+            const int r = rl[u], code = r & 15;
+            int col;                                     // node column of sorted position p
+            if (code == ROLE_KEEP) {
+                int kp;
+                if (p == 0) kp = P1;
+                else {
+                    const int ty = (r >> 8) & 3;
+                    kp = (ty == 1) ? i1++ : (ty == 3) ? (P1 + 1 + i2++) : (P1 + 1 + n2 + i3++);
+                }
+                dM[ik] = ds[p];
+                zM[ik] = zs[p];
+                md.d32[r0 + ik] = (float)ds[p];
+                md.z32[r0 + ik] = (float)zs[p];
+                kposM[ik] = kp;
+                invK[kp] = ik;
+                dest[p] = kp;
+                col = ik;
+                ++ik;
+            } else if (code == ROLE_ZERO) {
+                dval[iz] = R(0);
+                dsrc[iz] = p;
+                dest[p] = -(1 + iz);
+                col = N + iz;
+                ++iz;
+            } else {
+                const int slot = nz + io++;
+                dval[slot] = ds[p];
+                dsrc[slot] = p;
+                dest[p] = -(1 + slot);
+                col = N + slot;
+            }
+            if (slots) {
+                nus[col] = su[u];
+                nvs[col] = sv[u];
+            }
         }
     }
     if (slots && sqre && t == 0) nvs[m] = cvs[r0R + nr];   // the new null vector takes q_2's slot
@@ -467,15 +510,45 @@ struct ColSrc {
     }
 };
 
-// One CTA per sorted position of every node: survivors are copied into the
-// K-ordered W~ / Q~ (the products' operands); deflated columns stay in their
-// slots, except the members of close-value chains and the columns deflated
-// against d_0, which are rotated in place (the rotation of Sec. 4.2.1 acts
-// on the node's whole row range, so their slots' ranges become the node's).
-__global__ void __launch_bounds__(128) k_merge_gather(const NodeDesc *__restrict__ nodes,
+// copy rows [0, n) of a slot column (data in rows [lo, hi), zero elsewhere)
+// to dst, by nthr threads from tid: four loads in flight per thread before
+// their stores (source and destination may not alias as far as the compiler
+// knows, so it would not hoist them itself)
+__device__ __forceinline__ void copy_slot(real_t *__restrict__ dst, const real_t *__restrict__ src, int n,
+                                          long long lo, long long hi, int tid, int nthr) {
+    for (int r = tid; r < n; r += 4 * nthr) {
+        real_t v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int row = r + u * nthr;
+            v[u] = (row < n && row >= lo && row < hi) ? src[row] : R(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int row = r + u * nthr;
+            if (row < n) dst[row] = v[u];
+        }
+    }
+}
+
+// One column task per sorted position of every node: survivors are copied
+// into the K-ordered W~ / Q~ (the products' operands); deflated columns stay
+// in their slots, except the members of close-value chains and the columns
+// deflated against d_0, which are rotated in place (the rotation of Sec.
+// 4.2.1 acts on the node's whole row range, so their slots' ranges become
+// the node's).  CPB = 1: a CTA per task, its threads over the rows (large
+// nodes); CPB = 4: a warp per task, four per CTA (small nodes, where a CTA
+// per column of a few dozen rows would be all launch and descriptor loads).
+template <int CPB>
+__global__ void __launch_bounds__(256) k_merge_gather(const NodeDesc *__restrict__ nodes,
                                                       const MatDesc *__restrict__ mats,
-                                                      const NodeState *__restrict__ state, int mmax) {
-    const int node = blockIdx.x / mmax, p = blockIdx.x % mmax;
+                                                      const NodeState *__restrict__ state, int mmax, int ntasks) {
+    const int task = blockIdx.x * CPB + (CPB == 1 ? 0 : (int)(threadIdx.x >> 5));
+    const int tid = (CPB == 1) ? (int)threadIdx.x : (int)(threadIdx.x & 31);
+    const int nthr = (CPB == 1) ? (int)blockDim.x : 32;
+    auto sync = [] { if (CPB == 1) __syncthreads(); else __syncwarp(); };
+    if (task >= ntasks) return;                  // a whole warp (CPB = 4) or CTA (CPB = 1)
+    const int node = task / mmax, p = task % mmax;
     const NodeDesc nd = nodes[node];
     if (p >= nd.m) return;
     const MatDesc &md = mats[nd.mat];
@@ -494,15 +567,15 @@ __global__ void __launch_bounds__(128) k_merge_gather(const NodeDesc *__restrict
         const int a = ns.nzero;
         // padding columns of the K order (between the top block and index 0)
         for (int kp = ns.n1; kp < ns.P1; ++kp) {
-            for (int row = threadIdx.x; row < m; row += blockDim.x) W[(size_t)kp * m + row] = R(0);
-            for (int row = threadIdx.x; row < mc; row += blockDim.x) Qm[(size_t)kp * mc + row] = R(0);
+            for (int row = tid; row < m; row += nthr) W[(size_t)kp * m + row] = R(0);
+            for (int row = tid; row < mc; row += nthr) Qm[(size_t)kp * mc + row] = R(0);
         }
         // U: the d_0 column is the unit vector; columns deflated against d_0
         // keep their U columns (the rotation is one-sided)
-        for (int row = threadIdx.x; row < m; row += blockDim.x) W[(size_t)ns.P1 * m + row] = cs.u(0, row);
+        for (int row = tid; row < m; row += nthr) W[(size_t)ns.P1 * m + row] = cs.u(0, row);
         // V: the d_0 column absorbs them one by one, in place
         const int g1 = cs.q1slot(), g2 = sqre ? cs.q2slot() : 0;
-        for (int row = threadIdx.x; row < mc; row += blockDim.x) {
+        for (int row = tid; row < mc; row += nthr) {
             const real_t q1 = cs.vat(g1, row), q2 = sqre ? cs.vat(g2, row) : R(0);
             real_t y = ns.cq * q1 + ns.sq * q2;
             for (int j = 1; j <= a; ++j) {
@@ -516,8 +589,8 @@ __global__ void __launch_bounds__(128) k_merge_gather(const NodeDesc *__restrict
             // the new right null vector replaces q_2 in its slot
             if (sqre) V[(size_t)g2 * ld + row] = -ns.sq * q1 + ns.cq * q2;
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
+        sync();
+        if (tid == 0) {
             for (int j = 1; j <= a; ++j) {
                 const int g = cs.vslot(src[slist[j]]);
                 md.vlo[g] = r0; md.vhi[g] = r0 + mc;
@@ -531,7 +604,7 @@ __global__ void __launch_bounds__(128) k_merge_gather(const NodeDesc *__restrict
     if (code == ROLE_CHAIN) {                          // chain start: walk to its end
         const int k0 = md.sidx[r0 + p];
         // every member but a surviving last one is rotated in its own slot
-        for (int row = threadIdx.x; row < m; row += blockDim.x) {
+        for (int row = tid; row < m; row += nthr) {
             real_t y = cs.u(src[p], row);
             int prev = p;
             for (int k = k0 + 1; k < m; ++k) {
@@ -545,7 +618,7 @@ __global__ void __launch_bounds__(128) k_merge_gather(const NodeDesc *__restrict
             if (dest[prev] >= 0) W[(size_t)dest[prev] * m + row] = y;
             else U[(size_t)cs.uslot(src[prev]) * ld + row] = y;
         }
-        for (int row = threadIdx.x; row < mc; row += blockDim.x) {
+        for (int row = tid; row < mc; row += nthr) {
             real_t y = cs.v(src[p], row);
             int prev = p;
             for (int k = k0 + 1; k < m; ++k) {
@@ -559,8 +632,8 @@ __global__ void __launch_bounds__(128) k_merge_gather(const NodeDesc *__restrict
             if (dest[prev] >= 0) Qm[(size_t)dest[prev] * mc + row] = y;
             else V[(size_t)cs.vslot(src[prev]) * ld + row] = y;
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
+        sync();
+        if (tid == 0) {
             int prev = p;
             for (int k = k0 + 1; k < m; ++k) {
                 const int q = slist[k];
@@ -579,9 +652,9 @@ __global__ void __launch_bounds__(128) k_merge_gather(const NodeDesc *__restrict
     // a deflated column keeps its slot; a survivor is copied into W~ / Q~
     if (dest[p] < 0) return;
     const int c = src[p], gu = cs.uslot(c), gv = cs.vslot(c);
-    real_t *ud = W + (size_t)dest[p] * m, *vd = Qm + (size_t)dest[p] * mc;
-    for (int row = threadIdx.x; row < m; row += blockDim.x) ud[row] = cs.uat(gu, row);
-    for (int row = threadIdx.x; row < mc; row += blockDim.x) vd[row] = cs.vat(gv, row);
+    copy_slot(W + (size_t)dest[p] * m, md.U + (size_t)gu * ld + r0, m, md.ulo[gu] - r0, md.uhi[gu] - r0, tid, nthr);
+    copy_slot(Qm + (size_t)dest[p] * mc, md.V + (size_t)gv * ld + r0, mc, md.vlo[gv] - r0, md.vhi[gv] - r0, tid,
+              nthr);
 }
 
 // ------------------------------------------------------------------ gather (values only)
@@ -739,8 +812,13 @@ cudaError_t launch_merge_prep(const NodeDesc *nodes, int nnodes, const MatDesc *
 cudaError_t launch_merge_gather(const NodeDesc *nodes, int nnodes, const MatDesc *mats,
                                 const NodeState *state, int mmax, cudaStream_t st) {
     if (nnodes <= 0) return cudaSuccess;
-    const int T = mmax < 32 ? 32 : mmax < 64 ? 64 : 128;   // threads over the rows of a column
-    k_merge_gather<<<(unsigned)nnodes * mmax, T, 0, st>>>(nodes, mats, state, mmax);
+    const int ntasks = nnodes * mmax;
+    if (mmax <= 256) {
+        // a warp per column task, four per CTA
+        k_merge_gather<4><<<(unsigned)(ntasks + 3) / 4, 128, 0, st>>>(nodes, mats, state, mmax, ntasks);
+    } else {
+        k_merge_gather<1><<<(unsigned)ntasks, 256, 0, st>>>(nodes, mats, state, mmax, ntasks);
+    }
     return cudaGetLastError();
 }
 

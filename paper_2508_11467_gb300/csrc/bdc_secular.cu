@@ -69,44 +69,64 @@ struct Sums {
     real_t psi, dpsi, phi, dphi;
 };
 
+// Per-lane cache of the shifted poles lam_j = (d_j - d_o)(d_j + d_o) of a
+// root's current origin o, in shared memory (column stride 32, up to
+// kLamCache terms per lane): every pole sum at a new x of the same origin
+// then forms d_j^2 - w^2 = lam_j - x with one subtraction instead of three
+// FP64 operations.  (One more rounding than the fused form: lam_j - x
+// cancels only for j = o, where lam_o = 0 exactly, or for a farther pole
+// than the other interval pole, which the nearer-pole origin rules out.)
+constexpr int kLamCache = 16;
+struct LamCache {
+    real_t *p;   // this lane's column (nullptr: no cache)
+    int o;       // origin of the cached entries (-1: none)
+};
+
 // pole sums at x = w^2 - d_o^2; left group j <= k (psi), right j > k (phi).
 // Interior roots split at k = i (psi < 0 < phi); the last root at k = N-2,
 // so that phi is its origin pole's term alone.
 template <int G>
 __device__ __forceinline__ Sums pole_sums(const real_t *__restrict__ d, const real_t *__restrict__ z,
-                                          int N, int k, real_t dor, real_t x, int lane) {
+                                          int N, int k, int o, real_t dor, real_t x, int lane, LamCache &lc) {
     Sums s{R(0.0), R(0.0), R(0.0), R(0.0)};
+    const bool use = lc.p != nullptr && lc.o == o, fill = lc.p != nullptr && !use;
+    int t = 0;                                   // this lane's term number (its cache slot)
+    auto shifted = [&](int j) -> real_t {
+        if (use && t < kLamCache) return lc.p[32 * t];
+        const real_t dj = d[j];
+        const real_t lam = (dj - dor) * (dj + dor);
+        if (fill && t < kLamCache) lc.p[32 * t] = lam;
+        return lam;
+    };
     if constexpr (G < 32) {
         // several roots per warp split their poles at different k: one loop
         // over all poles (the same trip count for every group of the warp)
-        for (int j = lane; j < N; j += G) {
-            const real_t dj = d[j], zj = z[j];
-            const real_t del = (dj - dor) * (dj + dor) - x;
-            const real_t t = quot(zj, del);
+        for (int j = lane; j < N; j += G, ++t) {
+            const real_t zj = z[j];
+            const real_t tq = quot(zj, shifted(j) - x);
             if (j <= k) {
-                s.psi = fma(zj, t, s.psi);
-                s.dpsi = fma(t, t, s.dpsi);
+                s.psi = fma(zj, tq, s.psi);
+                s.dpsi = fma(tq, tq, s.dpsi);
             } else {
-                s.phi = fma(zj, t, s.phi);
-                s.dphi = fma(t, t, s.dphi);
+                s.phi = fma(zj, tq, s.phi);
+                s.dphi = fma(tq, tq, s.dphi);
             }
         }
     } else {
-        for (int j = lane; j <= k; j += G) {
-            const real_t dj = d[j], zj = z[j];
-            const real_t del = (dj - dor) * (dj + dor) - x;
-            const real_t t = quot(zj, del);
-            s.psi = fma(zj, t, s.psi);
-            s.dpsi = fma(t, t, s.dpsi);
+        for (int j = lane; j <= k; j += G, ++t) {
+            const real_t zj = z[j];
+            const real_t tq = quot(zj, shifted(j) - x);
+            s.psi = fma(zj, tq, s.psi);
+            s.dpsi = fma(tq, tq, s.dpsi);
         }
-        for (int j = k + 1 + lane; j < N; j += G) {
-            const real_t dj = d[j], zj = z[j];
-            const real_t del = (dj - dor) * (dj + dor) - x;
-            const real_t t = quot(zj, del);
-            s.phi = fma(zj, t, s.phi);
-            s.dphi = fma(t, t, s.dphi);
+        for (int j = k + 1 + lane; j < N; j += G, ++t) {
+            const real_t zj = z[j];
+            const real_t tq = quot(zj, shifted(j) - x);
+            s.phi = fma(zj, tq, s.phi);
+            s.dphi = fma(tq, tq, s.dphi);
         }
     }
+    if (fill) lc.o = o;
     s.psi = group_sum<G>(s.psi);
     s.dpsi = group_sum<G>(s.dpsi);
     s.phi = group_sum<G>(s.phi);
@@ -122,6 +142,7 @@ struct RootState {
     real_t x;
     real_t dl, du;               // the interval poles d_i, d_{i+1}
     Sums s;
+    LamCache lc;
 };
 
 // Next iterate from the rational model of f (Eq. M-svd-val) at x: psi's poles
@@ -183,7 +204,7 @@ __device__ __forceinline__ int root_iterate(const real_t *__restrict__ d, const 
                 r.o = i; r.dor = r.dl; r.x += D2; r.lo += D2; r.hi += D2; r.lamL = R(0.0); r.lamR = D2;
             }
         }
-        r.s = pole_sums<G>(d, z, N, k, r.dor, r.x, lane);
+        r.s = pole_sums<G>(d, z, N, k, r.o, r.dor, r.x, lane, r.lc);
         if (fabs(step) <= R(4.0) * kEps * fabs(r.x)) break;
     }
     return it;
@@ -240,7 +261,8 @@ __device__ __forceinline__ void fp32_phase(const float *__restrict__ d32, const 
 template <int G>
 __device__ __forceinline__ int solve_root(const real_t *__restrict__ d, const real_t *__restrict__ z, int N, int i,
                           int max_iter, real_t zz, int &org_out, real_t &tau_out, real_t &x_out, real_t vstart,
-                          const float *__restrict__ d32 = nullptr, const float *__restrict__ z32 = nullptr) {
+                          const float *__restrict__ d32 = nullptr, const float *__restrict__ z32 = nullptr,
+                          real_t *lam_cache = nullptr) {
     const int lane = threadIdx.x & (G - 1);
     if (N == 1) {
         org_out = 0;
@@ -257,6 +279,7 @@ __device__ __forceinline__ int solve_root(const real_t *__restrict__ d, const re
     RootState r;
     r.dl = dl;
     r.du = du;
+    r.lc = LamCache{lam_cache, -1};
     if (pre32 && !last && !(vstart == vstart)) {
         // FP32 sign at the interval midpoint picks the origin (a wrong pick
         // near the midpoint is repaired by the origin switch)
@@ -280,11 +303,11 @@ __device__ __forceinline__ int solve_root(const real_t *__restrict__ d, const re
         }
         if (!(r.x > r.lo && r.x < r.hi)) r.x = R(0.5) * (r.lo + r.hi);
         if (pre32) fp32_phase<G>(d32, z32, N, i, false, r);
-        r.s = pole_sums<G>(d, z, N, i, r.dor, r.x, lane);
+        r.s = pole_sums<G>(d, z, N, i, r.o, r.dor, r.x, lane, r.lc);
     } else if (!last) {
         // sign of f at the interval midpoint picks the nearer pole as origin
         const real_t xmid = h * (R(2.0) * dl + h);
-        r.s = pole_sums<G>(d, z, N, i, dl, xmid, lane);
+        r.s = pole_sums<G>(d, z, N, i, i, dl, xmid, lane, r.lc);
         const real_t fmid = R(1.0) + r.s.psi + r.s.phi;
         if (fmid >= R(0.0)) {
             r.o = i; r.dor = dl; r.lo = R(0.0); r.hi = xmid;
@@ -303,7 +326,7 @@ __device__ __forceinline__ int solve_root(const real_t *__restrict__ d, const re
         r.lamL = -(dl - dp) * (dl + dp); r.lamR = R(0.0);
         r.x = R(0.5) * zz;
         if (pre32) fp32_phase<G>(d32, z32, N, i, true, r);
-        r.s = pole_sums<G>(d, z, N, i - 1, r.dor, r.x, lane);
+        r.s = pole_sums<G>(d, z, N, i - 1, r.o, r.dor, r.x, lane, r.lc);
     }
     int it = root_iterate<G>(d, z, N, i, last, max_iter, r);
     if (use_mlp && it >= 0) {
@@ -317,7 +340,7 @@ __device__ __forceinline__ int solve_root(const real_t *__restrict__ d, const re
         }
         if (sw) {
             if (!(r.x > r.lo && r.x < r.hi)) r.x = R(0.5) * (r.lo + r.hi);
-            r.s = pole_sums<G>(d, z, N, i, r.dor, r.x, lane);
+            r.s = pole_sums<G>(d, z, N, i, r.o, r.dor, r.x, lane, r.lc);
             const int it2 = root_iterate<G>(d, z, N, i, last, max_iter, r);
             it = (it2 < 0) ? -1 : it + 1 + it2;
         }
@@ -465,14 +488,15 @@ __global__ void __launch_bounds__(128) k_root_start(const NodeDesc *__restrict__
 template <int G>
 __device__ __forceinline__ void secular_group(const NodeDesc &nd, const MatDesc &md, NodeState *__restrict__ state,
                                               int N, real_t zz, int i, int max_iter, int seed_mode,
-                                              int fp32_start) {
+                                              int fp32_start, real_t *lam_cache) {
     const real_t *d = md.dM + nd.r0, *z = md.zM + nd.r0;
     real_t vstart = R(NAN);                                    // NaN: plain start
     if (seed_mode != BDC_SEED_PLAIN && i < N - 1) vstart = md.ystart[nd.r0 + i];
     int o;
     real_t tau, x;
     const int it = solve_root<G>(d, z, N, i, max_iter, zz, o, tau, x, vstart,
-                                 fp32_start ? md.d32 + nd.r0 : nullptr, fp32_start ? md.z32 + nd.r0 : nullptr);
+                                 fp32_start ? md.d32 + nd.r0 : nullptr, fp32_start ? md.z32 + nd.r0 : nullptr,
+                                 lam_cache);
     if ((threadIdx.x & (G - 1)) == 0) {
         md.org[nd.r0 + i] = o;
         md.tau[nd.r0 + i] = tau;
@@ -511,11 +535,13 @@ __global__ void __launch_bounds__(256, 2) k_secular(const NodeDesc *__restrict__
     if (i >= N) return;                              // whole groups leave together
     const MatDesc &md = mats[nd.mat];
     const real_t zz = ns.rho;                        // sum z^2 (computed by the merge prep)
+    __shared__ real_t s_lam[8][kLamCache * 32];       // shifted poles of each lane's root (pole_sums)
+    real_t *lc = &s_lam[threadIdx.x >> 5][lane];
     switch (G) {
-    case 4: secular_group<4>(nd, md, state, N, zz, i, max_iter, seed_mode, fp32_start); break;
-    case 8: secular_group<8>(nd, md, state, N, zz, i, max_iter, seed_mode, fp32_start); break;
-    case 16: secular_group<16>(nd, md, state, N, zz, i, max_iter, seed_mode, fp32_start); break;
-    default: secular_group<32>(nd, md, state, N, zz, i, max_iter, seed_mode, fp32_start); break;
+    case 4: secular_group<4>(nd, md, state, N, zz, i, max_iter, seed_mode, fp32_start, lc); break;
+    case 8: secular_group<8>(nd, md, state, N, zz, i, max_iter, seed_mode, fp32_start, lc); break;
+    case 16: secular_group<16>(nd, md, state, N, zz, i, max_iter, seed_mode, fp32_start, lc); break;
+    default: secular_group<32>(nd, md, state, N, zz, i, max_iter, seed_mode, fp32_start, lc); break;
     }
 }
 
