@@ -610,7 +610,7 @@ __global__ void __launch_bounds__(256) k_mlp_features_single(int N, const double
 template <int G>
 __device__ __forceinline__ real_t lowner_one(const real_t *__restrict__ d, const real_t *__restrict__ z,
                                              const int *__restrict__ org, const real_t *__restrict__ tau,
-                                             int N, int i, int lane) {
+                                             const real_t *__restrict__ omega, int N, int i, int lane) {
     const real_t di = d[i];
     real_t prod = R(1.0);
 #ifdef BDC_FP32
@@ -629,7 +629,7 @@ __device__ __forceinline__ real_t lowner_one(const real_t *__restrict__ d, const
     for (int k = lane; k < N - 1; k += G) {
         const int ok = org[k];
         const double wmd = (d[ok] - di) + tau[k];        // w_k - d_i
-        const double wpd = d[ok] + tau[k] + di;          // w_k + d_i
+        const double wpd = (omega ? omega[k] : d[ok] + tau[k]) + di;   // w_k + d_i
         const int kk = (k < i) ? k : k + 1;
         num *= wmd * wpd;
         den *= (d[kk] - di) * (d[kk] + di);
@@ -666,10 +666,10 @@ __global__ void __launch_bounds__(256) k_lowner(const NodeDesc *__restrict__ nod
     const int *org = md.org + r0;
     real_t zt;
     switch (G) {
-    case 4: zt = lowner_one<4>(d, z, org, tau, N, i, gl); break;
-    case 8: zt = lowner_one<8>(d, z, org, tau, N, i, gl); break;
-    case 16: zt = lowner_one<16>(d, z, org, tau, N, i, gl); break;
-    default: zt = lowner_one<32>(d, z, org, tau, N, i, gl); break;
+    case 4: zt = lowner_one<4>(d, z, org, tau, md.omega + r0, N, i, gl); break;
+    case 8: zt = lowner_one<8>(d, z, org, tau, md.omega + r0, N, i, gl); break;
+    case 16: zt = lowner_one<16>(d, z, org, tau, md.omega + r0, N, i, gl); break;
+    default: zt = lowner_one<32>(d, z, org, tau, md.omega + r0, N, i, gl); break;
     }
     if (gl == 0) md.zt[r0 + i] = zt;
 }
@@ -679,7 +679,7 @@ __global__ void __launch_bounds__(256) k_lowner_single(int N, const double *d, c
                                                        const int *org, const double *tau, double *zt) {
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (i >= N) return;
-    const double v = lowner_one<32>(d, z, org, tau, N, i, lane);
+    const double v = lowner_one<32>(d, z, org, tau, nullptr, N, i, lane);
     if (lane == 0) zt[i] = v;
 }
 #endif
@@ -702,10 +702,11 @@ __device__ void vectors_one(const real_t *__restrict__ d, const real_t *__restri
                             int o, real_t tau, const int *__restrict__ invK, int Ktot,
                             real_t *__restrict__ UMcol, real_t *__restrict__ VMcol, real_t *sh) {
     const real_t dor = d[o];
+    const real_t wsum = dor + tau;   // w_i: d_j + w_i formed once per entry (a sum of positives)
     real_t sv = R(0.0), su = R(0.0);
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
         const real_t dj = d[j];
-        const real_t v = quot(zt[j], ((dj - dor) - tau) * (dj + dor + tau));
+        const real_t v = quot(zt[j], ((dj - dor) - tau) * (dj + wsum));
         const real_t u = (j == 0) ? -R(1.0) : dj * v;
         sv = fma(v, v, sv);
         su = fma(u, u, su);
@@ -718,7 +719,7 @@ __device__ void vectors_one(const real_t *__restrict__ d, const real_t *__restri
         real_t uo = R(0.0), vo = R(0.0);
         if (j >= 0) {
             const real_t dj = d[j];
-            const real_t v = quot(zt[j], ((dj - dor) - tau) * (dj + dor + tau));
+            const real_t v = quot(zt[j], ((dj - dor) - tau) * (dj + wsum));
             vo = v * iv;
             uo = ((j == 0) ? -R(1.0) : dj * v) * iu;
         }
@@ -739,6 +740,7 @@ __device__ __forceinline__ void vectors_group(const real_t *__restrict__ d, cons
                                               const int *__restrict__ kpos, int N, int n1, int P1, real_t dor,
                                               real_t tau, real_t *__restrict__ UMcol, real_t *__restrict__ VMcol,
                                               int gl) {
+    const real_t wsum = dor + tau;   // w_i: d_j + w_i formed once per entry (a sum of positives)
     real_t vr[T];
     real_t sv = R(0.0), su = R(0.0);
 #pragma unroll
@@ -747,7 +749,7 @@ __device__ __forceinline__ void vectors_group(const real_t *__restrict__ d, cons
         real_t v = R(0.0);
         if (j < N) {
             const real_t dj = d[j];
-            v = quot(zt[j], ((dj - dor) - tau) * (dj + dor + tau));
+            v = quot(zt[j], ((dj - dor) - tau) * (dj + wsum));
             const real_t u = (j == 0) ? -R(1.0) : dj * v;
             sv = fma(v, v, sv);
             su = fma(u, u, su);
@@ -775,10 +777,11 @@ __device__ __forceinline__ void vectors_warp_long(const real_t *__restrict__ d, 
                                                   const int *__restrict__ kpos, int N, int n1, int P1, real_t dor,
                                                   real_t tau, real_t *__restrict__ UMcol,
                                                   real_t *__restrict__ VMcol, int lane) {
+    const real_t wsum = dor + tau;   // w_i: d_j + w_i formed once per entry (a sum of positives)
     real_t sv = R(0.0), su = R(0.0);
     for (int j = lane; j < N; j += 32) {
         const real_t dj = d[j];
-        const real_t v = quot(zt[j], ((dj - dor) - tau) * (dj + dor + tau));
+        const real_t v = quot(zt[j], ((dj - dor) - tau) * (dj + wsum));
         const real_t u = (j == 0) ? -R(1.0) : dj * v;
         sv = fma(v, v, sv);
         su = fma(u, u, su);
@@ -789,7 +792,7 @@ __device__ __forceinline__ void vectors_warp_long(const real_t *__restrict__ d, 
     for (int p = n1 + lane; p < P1; p += 32) { UMcol[p] = R(0.0); VMcol[p] = R(0.0); }
     for (int j = lane; j < N; j += 32) {
         const real_t dj = d[j];
-        const real_t v = quot(zt[j], ((dj - dor) - tau) * (dj + dor + tau));
+        const real_t v = quot(zt[j], ((dj - dor) - tau) * (dj + wsum));
         const int kp = kpos[j];
         VMcol[kp] = v * iv;
         UMcol[kp] = ((j == 0) ? -R(1.0) : dj * v) * iu;
@@ -836,10 +839,11 @@ __device__ __forceinline__ void rows_group(const real_t *__restrict__ d, const r
                                            const int *__restrict__ kpos, const real_t *__restrict__ FK,
                                            const real_t *__restrict__ LK, int N, real_t dor, real_t tau,
                                            real_t *vf, real_t *vl, int gl) {
+    const real_t wsum = dor + tau;   // w_i: d_j + w_i formed once per entry (a sum of positives)
     real_t sv = R(0), sf = R(0), sl = R(0);
     for (int j = gl; j < N; j += G) {
         const real_t dj = d[j];
-        const real_t v = quot(zt[j], ((dj - dor) - tau) * (dj + dor + tau));
+        const real_t v = quot(zt[j], ((dj - dor) - tau) * (dj + wsum));
         const int kp = kpos[j];
         sv = fma(v, v, sv);
         sf = fma(FK[kp], v, sf);
