@@ -720,6 +720,24 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
                 float SL[CPT];
 #pragma unroll
                 for (int i = 0; i < CPT; ++i) SL[i] = 0.f;
+                // the final read-modify-write of C waits on its loads while the
+                // next tile's stages wait on this warp: pull this warp's 32 rows of
+                // its CPT columns into L2 now (lane = column, 256 B each), while
+                // the stages below accumulate
+                const int Er = rowok ? Ea[mx.a_row0 + row] : 0;
+                column_tables();
+                {
+                    const int rw0 = m0 + 32 * q;
+#pragma unroll
+                    for (int h2 = 0; h2 < CPT / 32; ++h2) {
+                        const int col = c0 + 32 * h2 + lane;
+                        if (col < pr.N && rw0 < pr.M) {
+                            const double *pc = pr.C + (long long)cml[h2] * ldc + rw0;
+                            asm volatile("prefetch.global.L2 [%0];" ::"l"(pc));
+                            if (rw0 + 16 < pr.M) asm volatile("prefetch.global.L2 [%0];" ::"l"(pc + 16));
+                        }
+                    }
+                }
                 for (int s = 0; s < nk; ++s, ++GL) {
                     const int b = GL & 1;
                     if (!mbar_wait(&accfull[b], (GL >> 1) & 1, err, abort_flag)) { ok = false; break; }
@@ -743,8 +761,6 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
                 if (ok) {
                     // C += 2^(E+F-16) SL, 8 columns at a time: their loads of C are
                     // issued together
-                    const int Er = rowok ? Ea[mx.a_row0 + row] : 0;
-                    column_tables();
 #pragma unroll
                     for (int cb = 0; cb < CPT / 8; ++cb) {
                         int F[8];
