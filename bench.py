@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--n", type=int, default=16384)
     ap.add_argument("--kind", default="uniform", choices=["uniform", "graded", "clustered", "ones"])
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--leaf", type=int, default=16)
+    ap.add_argument("--leaf", type=int, default=8)
     ap.add_argument("--slices", type=int, default=0, help="0 = automatic (7)")
     ap.add_argument("--mixed-min", type=int, default=0, help="smallest merge order using split BF16 (0 = auto)")
     ap.add_argument("--batched", action="store_true",

@@ -68,7 +68,7 @@ typedef enum { BDC_SEED_PLAIN = 0, BDC_SEED_MLP = 1, BDC_SEED_ANALYTIC = 2 } bdc
 typedef struct {
     int prec;          /* bdc_precision                                   */
     int seed;          /* bdc_seed                                        */
-    int leaf;          /* leaf size L (4..64; 0 = default 16)             */
+    int leaf;          /* leaf size L (4..64; 0 = default 8)              */
     int max_iter;      /* secular / QR iteration cap (0 = default 64)     */
     int slices;        /* BDC_MIXED_EXACT slice count 4..7 (0 = automatic: 7)    */
     int checked;       /* reserved, must be 0                              */
@@ -81,7 +81,7 @@ typedef struct {
                           same stopping rule (bdc_opts_default: 1)        */
 } bdc_opts;
 
-/* Fill *o with the defaults (FP64, plain seed, leaf 16, automatic slices). */
+/* Fill *o with the defaults (FP64, plain seed, leaf 8, automatic slices). */
 void bdc_opts_default(bdc_opts *o);
 
 /* SVD of the n x n upper bidiagonal (d, e), FP64 defaults, synchronous:

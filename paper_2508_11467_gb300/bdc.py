@@ -158,7 +158,7 @@ def _dev(t, dtype=torch.float64):
     return t.to(dtype).contiguous()
 
 
-def make_opts(prec="fp64", leaf=16, max_iter=64, slices=0, seed="plain", mlp=None, mixed_min=0,
+def make_opts(prec="fp64", leaf=0, max_iter=64, slices=0, seed="plain", mlp=None, mixed_min=0,
               fp32_start=True) -> Opts:
     o = Opts()
     lib().bdc_opts_default(ctypes.byref(o))
@@ -177,7 +177,7 @@ def workspace_bytes(n: int, opts: Opts) -> int:
     return int(lib().bdc_svd_workspace(int(n), ctypes.byref(opts)))
 
 
-def svd(d, e, *, prec="fp64", leaf=16, max_iter=64, slices=0, seed="plain", mlp=None,
+def svd(d, e, *, prec="fp64", leaf=0, max_iter=64, slices=0, seed="plain", mlp=None,
         stream=None, work=None, check=True, mixed_min=0, fp32_start=True):
     """SVD of the upper bidiagonal (d, e) on the GPU.
 
@@ -205,7 +205,7 @@ def svd(d, e, *, prec="fp64", leaf=16, max_iter=64, slices=0, seed="plain", mlp=
     return S[:n], Ut.t(), VTt.t(), code
 
 
-def svd_values(d, e, *, leaf=16, max_iter=64, seed="plain", mlp=None, stream=None, check=True, fp32_start=True):
+def svd_values(d, e, *, leaf=0, max_iter=64, seed="plain", mlp=None, stream=None, check=True, fp32_start=True):
     """Singular values only (descending), CUDA float64; and the status code."""
     d = _dev(d)
     n = d.shape[0]
@@ -236,7 +236,7 @@ def svd_sync(d, e, stream=None):
     return S[:n], Ut.t(), VTt.t(), rc
 
 
-def svd_batched(ds, es, *, prec="fp64", leaf=16, max_iter=64, slices=0, stream=None, work=None):
+def svd_batched(ds, es, *, prec="fp64", leaf=0, max_iter=64, slices=0, stream=None, work=None):
     """Batched SVD of bidiagonals of uneven sizes (lists of CUDA tensors)."""
     import numpy as np
     B = len(ds)
@@ -393,7 +393,7 @@ class Harvest:
         return self.feat[:k], self.targ[:k]
 
 
-def svd_harvest(d, e, harvest: Harvest, *, prec="fp64", leaf=16, max_iter=64, slices=0, stream=None,
+def svd_harvest(d, e, harvest: Harvest, *, prec="fp64", leaf=0, max_iter=64, slices=0, stream=None,
                 check=True, mixed_min=0):
     """svd() that appends every merge root's (features, target) to `harvest`."""
     d = _dev(d)
@@ -496,7 +496,7 @@ class BatchPlan:
     offsets sum(ns[:b]**2).  Built by bdc_plan_create; launch() enqueues the
     whole solve on the stream."""
 
-    def __init__(self, d_flat, e_flat, ns, *, prec="fp64", leaf=16, max_iter=64, slices=0, seed="plain",
+    def __init__(self, d_flat, e_flat, ns, *, prec="fp64", leaf=0, max_iter=64, slices=0, seed="plain",
                  mlp=None, mixed_min=0, dtype=torch.float64):
         import numpy as np
         self.ns = np.asarray(ns, dtype=np.int32)

@@ -34,7 +34,7 @@ size_t gemm_mixed_scratch(long long rows_total, long long cols_total, int kmax, 
 namespace {
 
 // leaf 16: measured best on GB300 (n = 16384; the paper's 32 was best on MI210/V100)
-constexpr int kDefaultLeaf = 16;
+constexpr int kDefaultLeaf = 8;    // measured at n = 16384: leaves 0.76 -> 0.21 ms, one more merge level +0.2 ms
 constexpr int kDefaultMaxIter = 64;
 
 struct TreeNode {

@@ -163,15 +163,19 @@ __global__ void __launch_bounds__(32 * WM * WN) k_gemm64(const GemmProb *__restr
         if (k0 + BK < K) load(k0 + BK);
 #pragma unroll
         for (int kk = 0; kk < BK; kk += 4) {
+            if (k0 + kk >= K) break;               // zero padding of the last K block
             double af[4], bf[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) af[i] = As[(kk + tg) * SA + wm + i * 8 + g];
 #pragma unroll
             for (int j = 0; j < 4; ++j) bf[j] = Bs[(wn + j * 8 + g) * SB + kk + tg];
+            // 8 x 8 fragments wholly outside M x N are skipped (warp-uniform):
+            // a merge of order 16 has blocks of about 8 x 16 in a 32 x 32 tile
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) dmma(acc[i][j], af[i], bf[j]);
+                for (int j = 0; j < 4; ++j)
+                    if (m0 + wm + i * 8 < M && n0 + wn + j * 8 < N) dmma(acc[i][j], af[i], bf[j]);
         }
     }
     // fragment (g, 2 tg + {0,1}) of each 8 x 8 tile
