@@ -332,28 +332,46 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
     const int *role = md.role + r0;
 
     // ---- survivor numbering (M order = ascending), type groups, deflated slots
-    const int seg = (m + T - 1) / T;
-    const int b = min(m, t * seg), e = min(m, b + seg);
-    int ck = 0, c1 = 0, c2 = 0, c3 = 0, cz = 0, co = 0;
-    for (int p = b; p < e; ++p) {
-        const int r = role[p], code = r & 15;
+    // Warp w numbers the positions [wb, we), 32 consecutive ones at a time
+    // (lane = position): the category counts of a chunk come from ballots,
+    // a position's index from the population count of the lower lanes, so
+    // that every load and store of a chunk is coalesced.  Categories: 0
+    // survivor, 1..3 its type group (1: left only, 2: right only, 3: both),
+    // 4 deflated against d_0, 5 other deflated.
+    const int lane = t & 31, wid = t >> 5, nwarp = T >> 5;
+    const int wseg = ((m + nwarp - 1) / nwarp + 31) & ~31;
+    const int wb = min(m, wid * wseg), we = min(m, wb + wseg);
+    const unsigned lt = (1u << lane) - 1u;       // lanes below this one
+    auto category = [&](int p, int r, int &grp) {   // survivor: grp = type group (0 for p = 0)
+        const int code = r & 15;
+        grp = 0;
         if (code == ROLE_KEEP) {
-            ++ck;
-            if (p > 0) { const int ty = (r >> 8) & 3; c1 += (ty == 1); c3 += (ty == 2); c2 += (ty == 3); }
-        } else if (code == ROLE_ZERO) {
-            ++cz;
-        } else {
-            ++co;
+            if (p > 0) { const int ty = (r >> 8) & 3; grp = (ty == 1) ? 1 : (ty == 2) ? 2 : 3; }
+            return 0;
         }
+        return (code == ROLE_ZERO) ? 4 : 5;
+    };
+    int cnt[6] = {0, 0, 0, 0, 0, 0};             // this warp's counts (lane 0 keeps them)
+    for (int p0 = wb; p0 < we; p0 += 32) {
+        const int p = p0 + lane;
+        int grp = -1, cat = -1;
+        if (p < we) cat = category(p, role[p], grp);
+        cnt[0] += __popc(__ballot_sync(0xffffffffu, cat == 0));
+        cnt[1] += __popc(__ballot_sync(0xffffffffu, cat == 0 && grp == 1));
+        cnt[2] += __popc(__ballot_sync(0xffffffffu, cat == 0 && grp == 3));
+        cnt[3] += __popc(__ballot_sync(0xffffffffu, cat == 0 && grp == 2));
+        cnt[4] += __popc(__ballot_sync(0xffffffffu, cat == 4));
+        cnt[5] += __popc(__ballot_sync(0xffffffffu, cat == 5));
     }
+    // warp bases: exclusive scans over the warps (one value per warp, in lane 0)
     int N, n1, n2, n3, nz, no;
-    int ik = block_excl_scan(ck, wsum, N);
-    const int ik0 = ik;                       // this thread's survivors: [ik0, ik0 + ck)
-    int i1 = block_excl_scan(c1, wsum, n1);
-    int i2 = block_excl_scan(c2, wsum, n2);
-    int i3 = block_excl_scan(c3, wsum, n3);
-    int iz = block_excl_scan(cz, wsum, nz);
-    int io = block_excl_scan(co, wsum, no);
+    int base[6];
+    base[0] = __shfl_sync(0xffffffffu, block_excl_scan(lane == 0 ? cnt[0] : 0, wsum, N), 0);
+    base[1] = __shfl_sync(0xffffffffu, block_excl_scan(lane == 0 ? cnt[1] : 0, wsum, n1), 0);
+    base[2] = __shfl_sync(0xffffffffu, block_excl_scan(lane == 0 ? cnt[2] : 0, wsum, n2), 0);
+    base[3] = __shfl_sync(0xffffffffu, block_excl_scan(lane == 0 ? cnt[3] : 0, wsum, n3), 0);
+    base[4] = __shfl_sync(0xffffffffu, block_excl_scan(lane == 0 ? cnt[4] : 0, wsum, nz), 0);
+    base[5] = __shfl_sync(0xffffffffu, block_excl_scan(lane == 0 ? cnt[5] : 0, wsum, no), 0);
     const int P1 = (n1 + 7) & ~7;
     const int Ktot = P1 + 1 + n2 + n3;
     real_t *dM = md.dM + r0, *zM = md.zM + r0, *dval = md.dval + r0;
@@ -366,63 +384,67 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
     int *nus = slots ? md.us[nd.buf] + r0 : nullptr, *nvs = slots ? md.vs[nd.buf] + r0 : nullptr;
     auto slot_u = [&](int c) { return c == 0 ? r0 + nl : (c <= nl ? cus[r0L + c - 1] : cus[r0R + (c - nl - 1)]); };
     auto slot_v = [&](int c) { return c == 0 ? cvs[r0L + nl] : (c <= nl ? cvs[r0L + c - 1] : cvs[r0R + (c - nl - 1)]); };
-    // four positions at a time: their roles, sources and slots are loaded
-    // before any of their stores (which the compiler may not move loads past)
-    for (int p0 = b; p0 < e; p0 += 4) {
-        int rl[4], su[4], sv[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int p = min(p0 + u, e - 1);
-            rl[u] = role[p];
-            su[u] = sv[u] = 0;
-            if (slots) { const int c = src[p]; su[u] = slot_u(c); sv[u] = slot_v(c); }
+    for (int p0 = wb; p0 < we; p0 += 32) {
+        const int p = p0 + lane;
+        const bool in = p < we;
+        int grp = -1, cat = -1, su = 0, sv = 0;
+        real_t dsp = R(0), zsp = R(0);
+        if (in) {
+            cat = category(p, role[p], grp);
+            dsp = ds[p];
+            zsp = zs[p];
+            if (slots) { const int c = src[p]; su = slot_u(c); sv = slot_v(c); }
         }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int p = p0 + u;
-            if (p >= e) break;
-            const int r = rl[u], code = r & 15;
+        const unsigned bk = __ballot_sync(0xffffffffu, cat == 0), b1 = __ballot_sync(0xffffffffu, cat == 0 && grp == 1),
+                       b2 = __ballot_sync(0xffffffffu, cat == 0 && grp == 3),
+                       b3 = __ballot_sync(0xffffffffu, cat == 0 && grp == 2),
+                       bz = __ballot_sync(0xffffffffu, cat == 4), bo = __ballot_sync(0xffffffffu, cat == 5);
+        if (in) {
             int col;                                     // node column of sorted position p
-            if (code == ROLE_KEEP) {
-                int kp;
-                if (p == 0) kp = P1;
-                else {
-                    const int ty = (r >> 8) & 3;
-                    kp = (ty == 1) ? i1++ : (ty == 3) ? (P1 + 1 + i2++) : (P1 + 1 + n2 + i3++);
-                }
-                dM[ik] = ds[p];
-                zM[ik] = zs[p];
-                md.d32[r0 + ik] = (float)ds[p];
-                md.z32[r0 + ik] = (float)zs[p];
+            if (cat == 0) {
+                const int ik = base[0] + __popc(bk & lt);
+                const int kp = (grp == 0) ? P1
+                             : (grp == 1) ? base[1] + __popc(b1 & lt)
+                             : (grp == 3) ? P1 + 1 + base[2] + __popc(b2 & lt)
+                                          : P1 + 1 + n2 + base[3] + __popc(b3 & lt);
+                dM[ik] = dsp;
+                zM[ik] = zsp;
+                md.d32[r0 + ik] = (float)dsp;
+                md.z32[r0 + ik] = (float)zsp;
                 kposM[ik] = kp;
                 invK[kp] = ik;
                 dest[p] = kp;
                 col = ik;
-                ++ik;
-            } else if (code == ROLE_ZERO) {
+            } else if (cat == 4) {
+                const int iz = base[4] + __popc(bz & lt);
                 dval[iz] = R(0);
                 dsrc[iz] = p;
                 dest[p] = -(1 + iz);
                 col = N + iz;
-                ++iz;
             } else {
-                const int slot = nz + io++;
-                dval[slot] = ds[p];
+                const int slot = nz + base[5] + __popc(bo & lt);
+                dval[slot] = dsp;
                 dsrc[slot] = p;
                 dest[p] = -(1 + slot);
                 col = N + slot;
             }
             if (slots) {
-                nus[col] = su[u];
-                nvs[col] = sv[u];
+                nus[col] = su;
+                nvs[col] = sv;
             }
         }
+        base[0] += __popc(bk); base[1] += __popc(b1); base[2] += __popc(b2);
+        base[3] += __popc(b3); base[4] += __popc(bz); base[5] += __popc(bo);
     }
     if (slots && sqre && t == 0) nvs[m] = cvs[r0R + nr];   // the new null vector takes q_2's slot
     for (int kp = n1 + t; kp < P1; kp += T) invK[kp] = -1;
     if (scans) {
         // moment scans of the survivors for the root start estimates: prefix
-        // sums (inclusive) of z^2, z^2 d^2, z^2 d^4 and the same suffix sums
+        // sums (inclusive) of z^2, z^2 d^2, z^2 d^4 and the same suffix sums;
+        // thread t takes the survivors [ik0, ik0 + ck) (written by other threads)
+        __syncthreads();
+        const int kseg = (N + T - 1) / T;
+        const int ik0 = min(N, t * kseg), ck = min(N, ik0 + kseg) - ik0;
         real_t a0 = 0.0, a1 = 0.0, a2 = 0.0;
         for (int k = ik0; k < ik0 + ck; ++k) {
             const real_t z2 = zM[k] * zM[k], d2 = dM[k] * dM[k];

@@ -52,6 +52,52 @@ def test_secular_roots_match_oracle(bdc, N, seed, gap):
     assert np.all(np.abs(f) <= 64 * EPS * scale)
 
 
+def _M_near_poles(N=200, seed=11):
+    # roots within ~1e-27 (relative) of their poles: poles clustered at the
+    # origin (0, 2.3e-11, 3.1e-10, 6.2e-9) with weights down to 1e-14, a pair
+    # of tiny weights in the interior and a weak last pole (the shapes that
+    # the top merges of an n = 16384 uniform matrix produce)
+    rng = np.random.default_rng(seed)
+    d = np.concatenate(([0.0, 2.2654e-11, 3.1e-10, 6.2e-9], np.sort(rng.uniform(1e-3, 1.0, N - 4))))
+    for i in range(5, N):
+        d[i] = max(d[i], d[i - 1] + 1e-4)
+    z = rng.uniform(0.05, 0.5, N) * rng.choice([-1.0, 1.0], N)
+    z[0], z[1], z[2], z[3] = 0.104, -8.82e-15, 6.6e-12, 3.3e-13
+    z[50], z[51] = 3e-13, -2e-14
+    z[N - 1] = 3.9e-6
+    return d, z
+
+
+def test_secular_near_pole_roots(bdc):
+    # The rational model's quadratic is solved for the new iterate, measured
+    # from the origin pole, not for a step added to the old one: a root within
+    # eps |x| of its pole is reached by the model, not by bisection (a numpy
+    # model of the step form needs up to 15 steps here, of the iterate form 7)
+    d, z = _M_near_poles()
+    org, tau, om, it, info = bdc.secular_solve_ex(_cu(d), _cu(z))
+    torch.cuda.synchronize()
+    assert int(info.item()) == 0
+    o_org, o_tau, o_om = merge.secular_roots(d, z)
+    om_g = om.cpu().numpy()
+    assert np.max(np.abs(om_g - o_om) / o_om) <= 64 * EPS
+    # w = d_o + tau rounds onto the pole for these roots: interlacing holds
+    # for (org, tau), the representation the vectors use
+    og, tg = org.cpu().numpy(), tau.cpu().numpy()
+    i = np.arange(len(d))
+    assert np.all((og == i) | (og == i + 1))
+    assert np.all(np.where(og == i, tg > 0, tg < 0))
+    assert np.all(om_g >= d) and np.all(om_g[:-1] <= d[1:])
+    f, scale = merge.secular_f(d, z, og, tg)
+    assert np.all(np.abs(f) <= 64 * EPS * scale)
+    # the offsets from the origin pole agree with the oracle's (to a few
+    # hundred ulps of the offset itself: the roots near an interval's middle,
+    # offset ~1e-3 from a pole ~0.5, carry ~eps |w| of rounding in either
+    # solver; the near-pole offsets, 1e-38 to 1e-31, agree to a few ulps)
+    same = og == o_org
+    assert np.all(np.abs(tg[same] - o_tau[same]) <= 256 * EPS * np.abs(o_tau[same]))
+    assert int(it.max().item()) <= 10
+
+
 @pytest.mark.parametrize("N,seed", [(1, 7), (3, 8), (64, 9), (513, 10)])
 def test_lowner_matches_oracle(bdc, N, seed):
     d, z = _M(N, seed, 1e-4)
