@@ -46,6 +46,33 @@ def test_secular_roots_are_singular_values_of_M(N, seed):
     assert np.all(np.abs(f) <= 64 * N * EPS * scale)
 
 
+def test_secular_roots_near_tiny_weight_poles_first_order():
+    # A pole d_o with a tiny weight z_o has a root w with x = w^2 - d_o^2
+    # = z_o^2 / g(d_o) up to a relative O(x) term, where g is f without the
+    # z_o term (Eq. M-svd-val: z_o^2 / (d_o^2 - w^2) + g(w) = 0); so
+    # tau = w - d_o = x / (w + d_o) ~ x / (2 d_o).  The bisection oracle
+    # resolves these offsets (1e-38 .. 1e-20) to their own relative accuracy.
+    rng = np.random.default_rng(11)
+    N = 200
+    d = np.concatenate(([0.0, 2.2654e-11, 3.1e-10, 6.2e-9], np.sort(rng.uniform(1e-3, 1.0, N - 4))))
+    for i in range(5, N):
+        d[i] = max(d[i], d[i - 1] + 1e-4)
+    z = rng.uniform(0.05, 0.5, N) * rng.choice([-1.0, 1.0], N)
+    z[0], z[1], z[2], z[3] = 0.104, -8.82e-15, 6.6e-12, 3.3e-13
+    z[50], z[51] = 3e-13, -2e-14
+    org, tau, omega = merge.secular_roots(d, z)
+    for o in (1, 2, 3, 50, 51):
+        rest = np.arange(N) != o
+        g = 1.0 + np.sum(z[rest] ** 2 / ((d[rest] - d[o]) * (d[rest] + d[o])))
+        x = z[o] ** 2 / g
+        tau_pred = x / (2.0 * d[o])
+        i = (o - 1) if x < 0 else o               # the root on that side of d_o
+        assert org[i] == o
+        assert abs(tau[i] - tau_pred) <= 1e-12 * abs(tau_pred)
+    f, scale = merge.secular_f(d, z, org, tau)
+    assert np.all(np.abs(f) <= 64 * N * EPS * scale)
+
+
 def test_lowner_reproduces_z_when_separated():
     d, z = _random_M(60, 9, gap=1e-2)
     org, tau, _ = merge.secular_roots(d, z)
