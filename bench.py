@@ -145,6 +145,24 @@ def cpu_baseline_oracle(n_target: int, kind: str, seed: int, n_sample: int = 102
                       f"= {t:.3f} s on 1 host core, scaled by (n/{n_sample})^3 to n={n_target}"}
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest x over the ranks: N replicas finish a step when the slowest
+    one does, so a step's time is the maximum of the ranks' times."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_seconds_per_svd(ms_max: float, world: int) -> float:
+    """Whole-job seconds per SVD: N replicas each solve one SVD per step of
+    ms_max milliseconds (the slowest rank's), N SVDs per step."""
+    return ms_max / 1e3 / world
+
+
 def run_reference(a, rank, world):
     if rank != 0:
         return
@@ -294,6 +312,8 @@ def run_batched(a):
 def main():
     a = parse()
     if a.batched and a.impl != "reference":
+        if int(os.environ.get("WORLD_SIZE", "1")) > 1:
+            raise SystemExit("--batched measures one GPU; run it without torchrun")
         run_batched(a)
         return
     rank = int(os.environ.get("RANK", "0"))
@@ -383,11 +403,7 @@ def main():
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1) / a.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / a.steps, world, dev)
     status = int(info.item())
 
     # end to end through the C ABI from pinned host buffers: H2D inputs, SVD, D2H S, U, V^T
@@ -414,12 +430,8 @@ def main():
             VT_h.copy_(VTt, non_blocking=True)
         f1.record(st)
         torch.cuda.synchronize()
-        ems = f0.elapsed_time(f1) / k2
-        if world > 1:
-            t = torch.tensor([ems], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": ems / 1e3 / world, "unit": "s", "h2d_bytes_per_step": int(8 * (2 * n - 1)),
+        ems = max_over_ranks(f0.elapsed_time(f1) / k2, world, dev)
+        e2e = {"value": replica_seconds_per_svd(ems, world), "unit": "s", "h2d_bytes_per_step": int(8 * (2 * n - 1)),
                "d2h_bytes_per_step": int(8 * (n + 2 * n * n))}
 
     # accuracy of the timed result (checkers use torch / cuBLAS, never the library's GEMM)
@@ -503,7 +515,7 @@ def main():
     flops_model = 8.0 / 3.0 * n ** 3
     line = {
         "metric": METRIC,
-        "value": ms / 1e3 / world,
+        "value": replica_seconds_per_svd(ms, world),
         "unit": "s",
         "n_gpus": world,
         "steps": a.steps,
