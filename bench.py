@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--slices", type=int, default=0, help="0 = automatic (7)")
     ap.add_argument("--mixed-min", type=int, default=0, help="smallest merge order using split BF16 (0 = auto)")
     ap.add_argument("--batched", action="store_true",
-                    help="config 4: 2048 bidiagonals, n log-uniform in [32, 1024], one CUDA-graph launch per batch")
+                    help="2048 bidiagonals, n log-uniform in [32, 1024], one CUDA-graph launch per batch")
     ap.add_argument("--dtype", default="fp64", choices=["fp64", "fp32"], help="batched mode working precision")
     ap.add_argument("--start", default="plain", choices=["plain", "analytic", "mlp"],
                     help="timed secular root start: interval midpoint (FP32 pre-iterations), analytic estimate, "
@@ -189,7 +189,7 @@ def run_reference(a, rank, world):
 
 
 def run_batched(a):
-    """Config 4: the whole batch per step, replayed as one CUDA graph."""
+    """The 2048-matrix batch (n log-uniform in [32, 1024]): the whole batch per step, replayed as one CUDA graph."""
     import torch
 
     from paper_2508_11467_gb300 import bdc, build, inputs
