@@ -4,11 +4,15 @@
 Workload: one n x n upper bidiagonal (default n = 16384, d, e ~ U(0.5, 1.5),
 seed 0), singular values and both vector sets, through the C ABI
 (bdc_svd_ex).  A step is one whole SVD (all stages of Algorithm 2).
-The metric is time per SVD (lower is better).
+The metric is time per SVD (lower is better).  The same invocation times the
+three forms the metric compares, with the same warm-up and step counts:
+split-BF16 merge products (the timed value), FP64 merge products, and split
+BF16 with the MLP-seeded secular roots.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--prec exact|fp64|bf16x3]
                   [--start mlp|analytic|plain]
   python bench.py --impl reference ...   # the FP64 CPU oracle on host cores
+  python bench.py --batched [--dtype fp32] # the 2048-matrix batch on its own line
 
 Multi-GPU runs (torchrun) are independent replicas (weak scaling): every rank
 solves its own matrix; value = max-over-ranks step time / N.
@@ -16,8 +20,11 @@ solves its own matrix; value = max-over-ranks step time / N.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
+import multiprocessing as mp
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -32,16 +39,23 @@ if ROOT not in sys.path:
 
 METRIC = "n=16384 bidiagonal SVD (σ+U,V) time, mixed vs FP64 at ≤1e-12 residual; %roofline"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
-# FP64 tensor-core (mma.sync f64) rate measured on this part by a throughput
-# probe: 6.66 MAC/clk/SM x 152 SMs x 2.07 GHz x 2 = 4.19 TFLOP/s
-FP64_DMMA_TFLOPS = 4.19
+FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
+# FP64 rates of this part measured by throughput probes (per SM per clock):
+# mma.sync.m8n8k4.f64 6.66 MAC; DFMA 1.99 lane operations (independent chains
+# on every SM: 626.7 G DFMA/s = 1.253 TFLOP/s at 2070 MHz)
+FP64_DMMA_MAC_PER_CLK_SM = 6.66
+FP64_ALU_OPS_PER_CLK_SM = 1.99
+SMS = 152
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_bdc_exact_uniform_n16384.md")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2508_11467_gb300", "csrc", f) for f in
+                  ("bdc_gemm_mixed.cu", "bdc_secular.cu", "bdc_merge.cu", "bdc_driver.cu", "bdc_leaf.cu",
+                   "bdc_gemm64.cu", "bdc_internal.cuh")]
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default=os.environ.get("BDC_BENCH_PREC", "exact"),
@@ -53,12 +67,14 @@ def parse():
     ap.add_argument("--slices", type=int, default=0, help="0 = automatic (7)")
     ap.add_argument("--mixed-min", type=int, default=0, help="smallest merge order using split BF16 (0 = auto)")
     ap.add_argument("--batched", action="store_true",
-                    help="2048 bidiagonals, n log-uniform in [32, 1024], one CUDA-graph launch per batch")
+                    help="only the 2048-matrix batch (n log-uniform in [32, 1024]), one CUDA-graph launch per batch")
     ap.add_argument("--dtype", default="fp64", choices=["fp64", "fp32"], help="batched mode working precision")
     ap.add_argument("--start", default="plain", choices=["plain", "analytic", "mlp"],
-                    help="timed secular root start: interval midpoint (FP32 pre-iterations), analytic estimate, "
-                         "or analytic + trained MLP; the other two are reported from untimed runs")
-    ap.add_argument("--no-mlp", action="store_true", help="skip training the root-start MLP (and its comparison)")
+                    help="secular root start of the timed form: interval midpoint (FP32 pre-iterations), "
+                         "analytic estimate, or analytic + trained MLP")
+    ap.add_argument("--no-mlp", action="store_true", help="skip training the root-start MLP (and its timing)")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-product comparison")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched keys of the headline line")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true")
@@ -92,7 +108,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
@@ -121,28 +137,84 @@ class ClockSampler:
                 "sm_max_mhz": max(smax) if smax else None, "reasons": reasons, "samples": len(rows)}
 
 
-def workload_name(a):
+def workload_name(kind, n, seed):
     rec = {"uniform": "d,e~U(0.5,1.5)", "graded": "d_i=10^(-8i/n)U(0.5,1.5), e=0.5d",
-           "clustered": "d=e=1+1e-10 N(0,1)", "ones": "d=e=1"}[a.kind]
-    return f"upper bidiagonal n={a.n} {rec} seed {a.seed}, sigma+U+V"
+           "clustered": "d=e=1+1e-10 N(0,1)", "ones": "d=e=1"}[kind]
+    return f"upper bidiagonal n={n} {rec} seed {seed}, sigma+U+V"
 
 
-def cpu_baseline_oracle(n_target: int, kind: str, seed: int, n_sample: int = 1024, reps: int = 2):
-    """Time the FP64 QR oracle (with vectors) on a bounded sample and scale by n^3."""
+def host_cores():
+    try:
+        aff = sorted(os.sched_getaffinity(0))
+    except AttributeError:
+        aff = list(range(os.cpu_count() or 1))
+    return aff
+
+
+# ------------------------------------------------------------- CPU oracle runs
+def _oracle_sigma_job(args):
+    """One sigma-only QR of the (kind, n, seed) bidiagonal; seconds."""
+    kind, n, seed = args
     import oracle
     from paper_2508_11467_gb300 import inputs
+    d, e = inputs.make(kind, n, seed)
+    t0 = time.perf_counter()
+    oracle.sigma_only(d, e)
+    return time.perf_counter() - t0
+
+
+def _oracle_full_job(args):
+    """One QR with U and V of the (kind, n, seed) bidiagonal; seconds."""
+    kind, n, seed = args
+    import oracle
+    from paper_2508_11467_gb300 import inputs
+    d, e = inputs.make(kind, n, seed)
+    t0 = time.perf_counter()
+    oracle.bdsqr(d, e)
+    return time.perf_counter() - t0
+
+
+def oracle_parallel(job, args_list, workers):
+    """Run oracle jobs in a pool of `workers` spawned processes (spawn: the
+    parent may hold a CUDA context); returns (wall seconds, per-job seconds)."""
+    import oracle
     oracle.build()
-    d, e = inputs.make(kind, n_sample, seed)
-    times = []
-    for _ in range(reps):
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers) as pool:
+        pool.map(_noop, range(workers))          # start-up (interpreter, imports) outside the timing
         t0 = time.perf_counter()
-        oracle.bdsqr(d, e)
-        times.append(time.perf_counter() - t0)
-    t = min(times)
-    scale = (n_target / n_sample) ** 3
-    return {"value": t * scale, "unit": "s", "cores": 1, "kind": "oracle",
-            "sample": f"Golub-Kahan QR with U,V at n={n_sample} ({kind}, seed {seed}), best of {reps} "
-                      f"= {t:.3f} s on 1 host core, scaled by (n/{n_sample})^3 to n={n_target}"}
+        per = pool.map(job, args_list, chunksize=1)
+        wall = time.perf_counter() - t0
+    return wall, per
+
+
+def _noop(_):
+    import oracle  # noqa: F401
+    from paper_2508_11467_gb300 import inputs  # noqa: F401
+    return 0
+
+
+def cpu_baseline_measured(kind, n, seed, d, e, sigma_seconds):
+    """The FP64 QR oracle measured on this host: the sigma-only QR of the
+    bench matrix itself (timed by the caller, sigma_seconds, 1 core), and the
+    QR with vectors at n=1024 on 1 core and on all cores of the affinity set
+    (independent matrices, one per core).  The n^3 scaling to n is a separate,
+    labelled field."""
+    aff = host_cores()
+    cores = len(aff)
+    nv = 1024
+    t1 = _oracle_full_job((kind, nv, seed))
+    wall, per = oracle_parallel(_oracle_full_job, [(kind, nv, seed + k) for k in range(cores)], cores)
+    return {"value": sigma_seconds, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": f"sigma-only Golub-Kahan QR of this n={n} {kind} seed {seed} matrix (the sigma reference "
+                      f"of accuracy), 1 host core",
+            "nproc": os.cpu_count(), "affinity": f"{len(aff)} cores ({aff[0]}..{aff[-1]})",
+            "with_vectors": {"n": nv, "s_1core": t1, "s_per_svd_all_cores": wall / cores, "cores": cores,
+                             "per_job_s_median": statistics.median(per),
+                             "sample": f"Golub-Kahan QR with U,V at n={nv} ({kind}), 1 core; and {cores} "
+                                       f"matrices (seeds {seed}..{seed + cores - 1}) on {cores} cores"},
+            "with_vectors_n3_extrapolated_to_n_s_1core": {"value": t1 * (n / nv) ** 3, "model": "s_1core x (n/1024)^3",
+                                                           "measured": False}}
 
 
 def max_over_ranks(x: float, world: int, device) -> float:
@@ -164,40 +236,43 @@ def replica_seconds_per_svd(ms_max: float, world: int) -> float:
 
 
 def run_reference(a, rank, world):
+    """The FP64 CPU oracle as the reference arm: each step is the sigma-only
+    Golub-Kahan QR of the workload matrix (the QR with vectors at n=16384
+    runs for hours); the steps run concurrently, one per host core of the
+    affinity set, and the value is the wall time of the timed steps / steps."""
     if rank != 0:
         return
-    for _ in range(a.warmup):
-        cpu_baseline_oracle(a.n, a.kind, a.seed, reps=1)
-    vals = []
-    t0 = time.perf_counter()
-    for _ in range(a.steps):
-        vals.append(cpu_baseline_oracle(a.n, a.kind, a.seed, reps=1)["value"])
-    wall = time.perf_counter() - t0
-    cb = cpu_baseline_oracle.__defaults__
-    v = float(np.median(vals))
+    aff = host_cores()
+    workers = max(1, min(len(aff), max(a.steps, a.warmup)))
+    args = (a.kind, a.n, a.seed)
+    wwall, _ = oracle_parallel(_oracle_sigma_job, [args] * a.warmup, workers) if a.warmup > 0 else (0.0, [])
+    wall, per = oracle_parallel(_oracle_sigma_job, [args] * a.steps, workers)
+    v = wall / a.steps
     line = {
         "metric": METRIC, "value": v, "unit": "s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": {"workload": workload_name(a), "n": a.n, "impl": "FP64 CPU oracle (Golub-Kahan QR)"},
-        "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
-                         "sample": f"Golub-Kahan QR with U,V at n={cb[0]}, scaled by n^3; "
-                                   f"{a.steps} steps in {wall:.1f} s"},
+        "config": {"workload": workload_name(a.kind, a.n, a.seed), "n": a.n,
+                   "impl": "FP64 CPU oracle (Golub-Kahan QR), singular values only"},
+        "cpu_baseline": {"value": v, "unit": "s", "cores": workers, "kind": "oracle",
+                         "sample": f"sigma-only QR of the n={a.n} {a.kind} seed {a.seed} matrix, {a.steps} steps "
+                                   f"run concurrently on {workers} host cores ({wall:.1f} s wall; one step alone "
+                                   f"{statistics.median(per):.1f} s median); no vectors",
+                         "nproc": os.cpu_count(), "affinity_cores": len(aff)},
         "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def run_batched(a):
-    """The 2048-matrix batch (n log-uniform in [32, 1024]): the whole batch per step, replayed as one CUDA graph."""
+# ------------------------------------------------------------------ batched
+def batched_run(a, dtype_name, steps, warmup, with_oracle=False):
+    """The 2048-matrix batch (n log-uniform in [32, 1024], seed 3): autotuned
+    plan replayed as one CUDA graph per batch; returns a dict of results."""
     import torch
 
-    from paper_2508_11467_gb300 import bdc, build, inputs
+    from paper_2508_11467_gb300 import bdc, inputs
 
     dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
-    build.build()
-    bdc.lib()
     count = 2048
     mats = inputs.batch(count, seed=3)
     ns = np.array([len(d) for d, _ in mats], dtype=np.int32)
@@ -207,42 +282,37 @@ def run_batched(a):
     for b, (d, e) in enumerate(mats):
         Dh[off[b]:off[b] + len(d)] = d
         Eh[off[b]:off[b] + len(e)] = e
-    dt = torch.float32 if a.dtype == "fp32" else torch.float64
+    dt = torch.float32 if dtype_name == "fp32" else torch.float64
     D_pin = torch.from_numpy(Dh).to(dt).pin_memory()
     E_pin = torch.from_numpy(Eh).to(dt).pin_memory()
-    # FP64 batches take the split-BF16 products (FP64-accurate, autotuned
-    # mixed_min) unless --prec fp64 asks for FP64 tensor-core products
-    prec = "fp64" if a.dtype == "fp32" else a.prec
+    prec = "fp64" if dtype_name == "fp32" else a.prec
     t0 = time.perf_counter()
-    leaf, mm, tune_ms = bdc.autotune(ns, prec, slices=a.slices, reps=2, dtype=dt)
+    leaf, mm, _ = bdc.autotune(ns, prec, slices=a.slices, reps=2, dtype=dt)
     tune_s = time.perf_counter() - t0
     plan = bdc.BatchPlan(D_pin.to(dev), E_pin.to(dev), ns, prec=prec, leaf=leaf, mixed_min=mm, slices=a.slices,
                          dtype=dt)
     st = torch.cuda.current_stream()
-    for _ in range(a.warmup):
+    for _ in range(warmup):
         plan.launch()
     torch.cuda.synchronize()
     if int(plan.info.abs().max()) != 0:
         raise RuntimeError("device status " + str(int(plan.info.abs().max())))
-    clocks = ClockSampler(0)
-    clocks.start()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(st)
-    for _ in range(a.steps):
+    for _ in range(steps):
         plan.launch()
     ev1.record(st)
     torch.cuda.synchronize()
-    clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1) / a.steps
+    ms = ev0.elapsed_time(ev1) / steps
     # end to end: H2D of every d, e; the graph; D2H of every S, U, V^T
-    esz = 4 if a.dtype == "fp32" else 8
+    esz = 4 if dtype_name == "fp32" else 8
     S_h = torch.empty_like(plan.S, device="cpu").pin_memory()
     U_h = torch.empty_like(plan.U, device="cpu").pin_memory()
     VT_h = torch.empty_like(plan.VT, device="cpu").pin_memory()
     f0 = torch.cuda.Event(enable_timing=True)
     f1 = torch.cuda.Event(enable_timing=True)
-    k2 = max(1, min(a.steps, 3))
+    k2 = max(1, min(steps, 3))
     f0.record(st)
     for _ in range(k2):
         plan.d.copy_(D_pin, non_blocking=True)
@@ -256,8 +326,8 @@ def run_batched(a):
     ems = f0.elapsed_time(f1) / k2
     # accuracy of a spread of matrices (torch/cuBLAS checkers in FP64)
     order = np.argsort(ns)
-    worst = {"residual": 0.0, "orth": 0.0}
-    for b in order[np.linspace(0, count - 1, 12).astype(int)]:
+    worst = {"residual": 0.0, "orth": 0.0, "checked": 16}
+    for b in order[np.linspace(0, count - 1, 16).astype(int)]:
         S, U, VT = plan.result(int(b))
         d = torch.from_numpy(mats[b][0]).to(dev).to(dt).double()
         e = torch.from_numpy(mats[b][1]).to(dev).to(dt).double()
@@ -270,43 +340,132 @@ def run_batched(a):
         G.diagonal().sub_(1.0)
         worst["residual"] = max(worst["residual"], res)
         worst["orth"] = max(worst["orth"], float(torch.linalg.norm(G)))
-    # the FP64 QR oracle on host cores, per matrix, on a bounded sample
-    cpu = None
-    if not a.no_cpu_baseline:
-        import oracle
-        oracle.build()
-        sample = [int(b) for b in order[np.linspace(0, count - 1, 24).astype(int)]]
-        t0 = time.perf_counter()
-        for b in sample:
-            oracle.bdsqr(*mats[b])
-        t = time.perf_counter() - t0
+    out = {"matrices_per_s": count / (ms * 1e-3), "ms_per_batch": ms, "leaf": leaf,
+           "mixed_min": mm if prec != "fp64" else None, "prec": prec, "autotune_s": tune_s,
+           "e2e_matrices_per_s": count / (ems * 1e-3), "accuracy": worst,
+           "h2d_bytes": int(2 * esz * off[-1]), "d2h_bytes": int(esz * (off[-1] + 2 * plan.U.numel())),
+           "gflops_model_8n3_3": float(np.sum((8.0 / 3.0) * ns.astype(np.float64) ** 3)) / (ms * 1e-3) / 1e9}
+    if with_oracle:
+        # the FP64 QR oracle with vectors, every matrix of a spread of 64, on all cores
+        sample = [int(b) for b in order[np.linspace(0, count - 1, 64).astype(int)]]
+        cores = len(host_cores())
+        wall, _ = oracle_parallel(_oracle_batch_job, [(3, b) for b in sample], cores)
         n3 = float(np.sum(ns.astype(np.float64) ** 3))
         s3 = float(np.sum(ns[sample].astype(np.float64) ** 3))
-        cpu_s = t * n3 / s3
-        cpu = {"value": count / cpu_s, "unit": "matrices/s", "cores": 1, "kind": "oracle",
-               "sample": f"Golub-Kahan QR with U,V on 24 of the 2048 matrices (spread over the sizes) = {t:.2f} s "
-                         f"on 1 host core, scaled by sum n^3 to the batch"}
-    flops = float(np.sum((8.0 / 3.0) * ns.astype(np.float64) ** 3))
+        out["cpu_baseline"] = {"value": count / (wall * n3 / s3), "unit": "matrices/s", "cores": cores,
+                               "kind": "oracle",
+                               "sample": f"Golub-Kahan QR with U,V on 64 of the 2048 matrices (spread over the "
+                                         f"sizes) in {wall:.2f} s on {cores} cores, scaled by sum n^3 to the batch"}
+    plan.close()
+    del plan
+    torch.cuda.empty_cache()
+    return out
+
+
+def _oracle_batch_job(args):
+    seed, b = args
+    import oracle
+    from paper_2508_11467_gb300 import inputs
+    d, e = inputs.batch(2048, seed=seed)[b]
+    oracle.bdsqr(d, e)
+    return 0
+
+
+def run_batched(a):
+    """--batched: the batch on its own JSON line (matrices/s)."""
+    import torch
+
+    from paper_2508_11467_gb300 import bdc, build
+
+    torch.cuda.set_device(0)
+    build.build()
+    bdc.lib()
+    clocks = ClockSampler(0)
+    clocks.start()
+    r = batched_run(a, a.dtype, a.steps, a.warmup, with_oracle=not a.no_cpu_baseline)
+    clk = clocks.stop()
     line = {
         "metric": "2048 bidiagonals (n log-uniform in [32,1024]) SVD (sigma+U,V) throughput",
-        "value": count / (ms * 1e-3), "unit": "matrices/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
-        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "value": r["matrices_per_s"], "unit": "matrices/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": r["ms_per_batch"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if a.dtype == "fp32" else "f64", "data": "synthetic",
         "config": {"workload": "2048 upper bidiagonals, n = floor(exp(U(ln 32, ln 1024))) seed 3, d,e~U(0.5,1.5)",
-                   "prec": prec, "slices": a.slices if a.slices else 7,
-                   "leaf": leaf, "mixed_min": mm if prec != "fp64" else None, "autotune_s": tune_s, "launch": "one CUDA graph per batch (bdc_plan_launch)",
+                   "prec": r["prec"], "leaf": r["leaf"], "mixed_min": r["mixed_min"], "autotune_s": r["autotune_s"],
+                   "launch": "one CUDA graph per batch (bdc_plan_launch)",
                    "l2": "U, V and workspace of the batch (> 5 GB) exceed L2"},
-        "gflops_paper_model": flops / (ms * 1e-3) / 1e9,
-        "accuracy": worst,
-        "roofline": None,
-        "gpu_launches": None,
-        "e2e": {"value": count / (ems * 1e-3), "unit": "matrices/s", "h2d_bytes_per_step": int(2 * esz * off[-1]),
-                "d2h_bytes_per_step": int(esz * (off[-1] + 2 * plan.U.numel()))},
-        "cpu_baseline": cpu,
-        "clocks": clk,
+        "gflops_model_8n3_3": r["gflops_model_8n3_3"],
+        "accuracy": r["accuracy"], "roofline": None, "gpu_launches": None,
+        "e2e": {"value": r["e2e_matrices_per_s"], "unit": "matrices/s", "h2d_bytes_per_step": r["h2d_bytes"],
+                "d2h_bytes_per_step": r["d2h_bytes"]},
+        "cpu_baseline": r.get("cpu_baseline"), "clocks": clk,
     }
-    plan.close()
     print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ rooflines
+def kernel_sources_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def read_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
+    None when there is none or the kernel sources changed since it was taken
+    (the summary records the hash of the kernel sources it measured)."""
+    try:
+        txt = open(TRAFFIC_FILE).read()
+    except OSError:
+        return None
+    m = re.search(r"^sources:\s*([0-9a-f]{16})", txt, re.M)
+    if not m or m.group(1) != kernel_sources_hash():
+        return None
+    m = re.search(rf"^traffic_per_launch\s+{re.escape(kernel)}\s+([0-9.eE+]+)", txt, re.M)
+    return float(m.group(1)) if m else None
+
+
+STAGE_KERNELS = {"scale": "k_scale", "leaf": "k_leaf_rotations + k_leaf_vectors", "prep": "k_merge_prep",
+                 "gather": "k_merge_gather", "secular": "k_secular (+ k_root_start)", "lowner": "k_lowner",
+                 "vectors": "k_vectors_warp", "slice": "k_slice_a + k_slice_b",
+                 "gemm": "k_mma (tcgen05) / k_gemm64 (DMMA f64)", "finish": "k_merge_finish", "final": "k_final"}
+
+
+def stage_table(prof, steps, peaks, clock_mhz, fp64_products):
+    """Per stage: time, launches, algorithmic bytes and FP64 operations, the
+    achieved rates and their fractions of the measured HBM copy bandwidth, the
+    FP64 ALU rate and the tensor peak; `bound` names the roofline that binds."""
+    hbm = float(peaks.get("hbm_gbs", FALLBACK["hbm_gbs"]))
+    clk = (clock_mhz or 2070.0) * 1e6
+    fp64_alu = FP64_ALU_OPS_PER_CLK_SM * SMS * clk / 1e9          # G FP64 ops / s
+    fp64_dmma = 2 * FP64_DMMA_MAC_PER_CLK_SM * SMS * clk / 1e12   # TFLOP/s
+    bf16 = float(peaks.get("bf16_tflops", FALLBACK["bf16_tflops"]))
+    out = {}
+    for k, v in prof.items():
+        if v["ms"] <= 0:
+            continue
+        t = v["ms"] * 1e-3
+        row = {"kernel": STAGE_KERNELS.get(k, k), "ms_per_step": v["ms"] / steps,
+               "launches_per_step": v["launches"] / steps}
+        if k == "gemm":
+            tf = v["work"] / t / 1e12
+            peak = fp64_dmma if fp64_products else bf16
+            row.update({"tflops_executed": tf, "tensor_peak_tflops": peak, "tensor_frac": tf / peak,
+                        "bound": "tensor", "work_per_step": v["work"] / steps})
+        else:
+            gbs = v["work"] / t / 1e9
+            fg = v["fp64"] / t / 1e9
+            row.update({"bytes_per_step": v["work"] / steps, "GBps": gbs, "hbm_frac": gbs / hbm,
+                        "fp64_ops_per_step": v["fp64"] / steps, "fp64_gops": fg, "fp64_frac": fg / fp64_alu})
+            row["bound"] = "fp64" if row["fp64_frac"] > row["hbm_frac"] else "hbm"
+            if max(row["fp64_frac"], row["hbm_frac"]) < 0.05:
+                row["bound"] += " (latency: below 5% of both)"
+        out[k] = row
+    if prof["secular"].get("roots"):
+        out.setdefault("secular", {})["roots_per_step"] = prof["secular"]["roots"] / steps
+        out["secular"]["iters_per_root"] = prof["secular"]["iters"] / prof["secular"]["roots"]
+    return out, {"hbm_gbs": hbm, "fp64_alu_gops": fp64_alu, "fp64_dmma_tflops": fp64_dmma, "bf16_tflops": bf16}
 
 
 def main():
@@ -322,6 +481,8 @@ def main():
     if a.impl == "reference":
         run_reference(a, rank, world)
         return
+
+    import ctypes
 
     import torch
     import torch.distributed as dist
@@ -341,29 +502,25 @@ def main():
     e_pin = torch.from_numpy(e_h).pin_memory()
     d = d_pin.to(dev)
     e = e_pin.to(dev)
-    # root starts: the MLP is trained here, before any timing, with the
-    # library's own kernels on roots harvested from FP64 runs of n = 8192
-    # uniform (seed 4) and graded (seed 5) bidiagonals
+    # root starts: the MLP is trained here, before any timing, by the
+    # library (bdc_mlp_train: roots harvested from FP64 solves of an n = 8192
+    # uniform and an n = 8192 graded bidiagonal generated on the device)
     P = None
     train_info = None
     if a.start == "mlp" or not a.no_mlp:
         t0 = time.perf_counter()
-        H = bdc.Harvest(1 << 21, device=dev)
-        for kind, sd in (("uniform", 4), ("graded", 5)):
-            dh, eh = inputs.make(kind, 8192, sd)
-            bdc.svd_harvest(torch.from_numpy(dh).to(dev), torch.from_numpy(eh).to(dev), H)
-        F, R = H.data()
-        P, losses = bdc.mlp_train(F, R, steps=1500, lr=3e-3, seed=0, huber=0.25)
+        P, losses, samples = bdc.mlp_train_harvest(n=8192, steps=1500, lr=3e-3, huber=0.25, seed=1)
         torch.cuda.synchronize()
-        g = bdc.mlp_predict(P, F)
-        train_info = {"samples": int(F.shape[0]), "steps": 1500, "loss": [float(losses[0]), float(losses[-1])],
-                      "median_abs_err_analytic": float(R.abs().median()),
-                      "median_abs_err_mlp": float((g - R).abs().median()),
+        train_info = {"samples": samples, "steps": 1500, "loss": [float(losses[0]), float(losses[-1])],
                       "seconds": time.perf_counter() - t0,
-                      "data": "harvest of n=8192 uniform seed 4 + graded seed 5 (FP64 runs)"}
-        del H
-    o = bdc.make_opts(a.prec, a.leaf, 64, a.slices, seed=a.start, mlp=P, mixed_min=a.mixed_min)
-    lw = bdc.workspace_bytes(n, o)
+                      "data": "bdc_mlp_train: n=8192 uniform + graded bidiagonals generated on the device (seed 1)"}
+
+    forms = {"mixed": bdc.make_opts(a.prec, a.leaf, 64, a.slices, seed=a.start, mlp=P, mixed_min=a.mixed_min)}
+    if not a.no_fp64 and a.prec != "fp64":
+        forms["fp64"] = bdc.make_opts("fp64", a.leaf, 64, 0, seed="plain")
+    if P is not None and a.start != "mlp" and a.prec != "fp64":
+        forms["mixed_mlp"] = bdc.make_opts(a.prec, a.leaf, 64, a.slices, seed="mlp", mlp=P, mixed_min=a.mixed_min)
+    lw = max(bdc.workspace_bytes(n, o) for o in forms.values())
     work = torch.empty(lw + 256, dtype=torch.uint8, device=dev)
     Ut = torch.empty((n, n), dtype=torch.float64, device=dev)
     VTt = torch.empty((n, n), dtype=torch.float64, device=dev)
@@ -371,72 +528,23 @@ def main():
     info = torch.zeros(1, dtype=torch.int32, device=dev)
     st = torch.cuda.current_stream()
 
-    import ctypes
-
-    def step(dd, ee):
-        rc = L.bdc_svd_ex(n, bdc._ptr(dd), bdc._ptr(ee), bdc._ptr(Ut), bdc._ptr(S), bdc._ptr(VTt), n, n,
+    def step(o, dd, ee, U_=Ut, S_=S, VT_=VTt, stream=st):
+        rc = L.bdc_svd_ex(n, bdc._ptr(dd), bdc._ptr(ee), bdc._ptr(U_), bdc._ptr(S_), bdc._ptr(VT_), n, n,
                           ctypes.byref(o), bdc._ptr(work), work.numel(), bdc._ptr(info),
-                          ctypes.c_void_p(st.cuda_stream))
+                          ctypes.c_void_p(stream.cuda_stream))
         if rc != 0:
             raise RuntimeError(f"bdc_svd_ex failed: {rc} {bdc.status_string(rc)}")
 
-    for _ in range(a.warmup):
-        step(d, e)
-    torch.cuda.synchronize()
-    if int(info.item()) != 0:
-        raise RuntimeError(f"device status {int(info.item())}: {bdc.status_string(int(info.item()))}")
+    # sigma reference: the oracle's sigma-only QR of this matrix (also the CPU baseline)
+    sigma_ref = sigma_s = None
+    if rank == 0 and not (a.no_check and a.no_cpu_baseline):
+        import oracle
+        oracle.build()
+        t0 = time.perf_counter()
+        sigma_ref = oracle.sigma_only(d_h, e_h)
+        sigma_s = time.perf_counter() - t0
 
-    clocks = ClockSampler(local)
-    clocks.start()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    bdc.profile_begin()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(st)
-    for _ in range(a.steps):
-        step(d, e)
-    ev1.record(st)
-    torch.cuda.synchronize()
-    prof = bdc.profile_end()
-    if world > 1:
-        dist.barrier()
-    clk = clocks.stop()
-    ms = max_over_ranks(ev0.elapsed_time(ev1) / a.steps, world, dev)
-    status = int(info.item())
-
-    # end to end through the C ABI from pinned host buffers: H2D inputs, SVD, D2H S, U, V^T
-    e2e = None
-    if not a.no_e2e:
-        S_h = torch.empty(n, dtype=torch.float64).pin_memory()
-        U_h = torch.empty((n, n), dtype=torch.float64).pin_memory()
-        VT_h = torch.empty((n, n), dtype=torch.float64).pin_memory()
-        d2 = torch.empty_like(d)
-        e2 = torch.empty_like(e)
-        k2 = max(1, min(a.steps, 3))
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-        f0 = torch.cuda.Event(enable_timing=True)
-        f1 = torch.cuda.Event(enable_timing=True)
-        f0.record(st)
-        for _ in range(k2):
-            d2.copy_(d_pin, non_blocking=True)
-            e2.copy_(e_pin, non_blocking=True)
-            step(d2, e2)
-            S_h.copy_(S, non_blocking=True)
-            U_h.copy_(Ut, non_blocking=True)
-            VT_h.copy_(VTt, non_blocking=True)
-        f1.record(st)
-        torch.cuda.synchronize()
-        ems = max_over_ranks(f0.elapsed_time(f1) / k2, world, dev)
-        e2e = {"value": replica_seconds_per_svd(ems, world), "unit": "s", "h2d_bytes_per_step": int(8 * (2 * n - 1)),
-               "d2h_bytes_per_step": int(8 * (n + 2 * n * n))}
-
-    # accuracy of the timed result (checkers use torch / cuBLAS, never the library's GEMM)
-    acc = None
-    if not a.no_check and rank == 0:
+    def accuracy():
         U = Ut.t()
         VT = VTt.t()
         V = VT.t()
@@ -455,6 +563,106 @@ def main():
         acc = {"residual": res, "orth_u_sample": float(torch.linalg.norm(Gu)),
                "orth_v_sample": float(torch.linalg.norm(Gv)),
                "orth_sample": "256 random columns against all n, Frobenius"}
+        if sigma_ref is not None:
+            s = S.cpu().numpy()
+            acc["sigma_rel_err"] = float(np.max(np.abs(s - sigma_ref)) / sigma_ref[0])
+            acc["sigma_ref"] = "oracle sigma-only QR (FP64, host)"
+        return acc
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    timed = {}
+    accs = {}
+    for name, o in forms.items():
+        for _ in range(a.warmup):
+            step(o, d, e)
+        torch.cuda.synchronize()
+        if int(info.item()) != 0:
+            raise RuntimeError(f"{name}: device status {int(info.item())}: {bdc.status_string(int(info.item()))}")
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(st)
+        for _ in range(a.steps):
+            step(o, d, e)
+        ev1.record(st)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        timed[name] = max_over_ranks(ev0.elapsed_time(ev1) / a.steps, world, dev)
+        if int(info.item()) != 0:
+            raise RuntimeError(f"{name}: device status {int(info.item())}")
+        if not a.no_check and rank == 0:
+            accs[name] = accuracy()
+    clk = clocks.stop()
+    ms = timed["mixed"]
+    status = int(info.item())
+
+    # stage split: one profiled (untimed) SVD of each form after the timed ones
+    profs = {}
+    for name, o in forms.items():
+        bdc.profile_begin()
+        step(o, d, e)
+        torch.cuda.synchronize()
+        profs[name] = bdc.profile_end()
+
+    # end to end through the C ABI from pinned host buffers: H2D of d, e, the
+    # SVD, D2H of S, U, V^T every step; outputs double-buffered so that the
+    # device-to-host copy of step k (copy stream) overlaps the SVD of step k+1
+    e2e = None
+    if not a.no_e2e:
+        o = forms["mixed"]
+        cs = torch.cuda.Stream(device=dev)
+        outs = [(Ut, S, VTt)] + [(torch.empty_like(Ut), torch.empty_like(S), torch.empty_like(VTt))]
+        hosts = [(torch.empty((n, n), dtype=torch.float64).pin_memory(),
+                  torch.empty(n, dtype=torch.float64).pin_memory(),
+                  torch.empty((n, n), dtype=torch.float64).pin_memory()) for _ in range(2)]
+        d2 = torch.empty_like(d)
+        e2 = torch.empty_like(e)
+        svd_done = [torch.cuda.Event() for _ in range(2)]
+        copy_done = [torch.cuda.Event() for _ in range(2)]
+        k2 = max(2, a.steps)
+
+        def e2e_run(k_steps):
+            for k in range(k_steps):
+                b = k % 2
+                if k >= 2:
+                    st.wait_event(copy_done[b])          # host buffer b and outputs b are free again
+                d2.copy_(d_pin, non_blocking=True)
+                e2.copy_(e_pin, non_blocking=True)
+                U_, S_, VT_ = outs[b]
+                step(o, d2, e2, U_, S_, VT_)
+                svd_done[b].record(st)
+                cs.wait_event(svd_done[b])
+                with torch.cuda.stream(cs):
+                    hU, hS, hVT = hosts[b]
+                    hS.copy_(S_, non_blocking=True)
+                    hU.copy_(U_, non_blocking=True)
+                    hVT.copy_(VT_, non_blocking=True)
+                copy_done[b].record(cs)
+            for b in range(2):
+                st.wait_event(copy_done[b])
+
+        e2e_run(2)                                       # warm-up (page-in of the pinned buffers)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(st)
+        e2e_run(k2)
+        f1.record(st)
+        torch.cuda.synchronize()
+        ems = max_over_ranks(f0.elapsed_time(f1) / k2, world, dev)
+        ok = bool(torch.equal(hosts[(k2 - 1) % 2][1], S.cpu()))
+        e2e = {"value": replica_seconds_per_svd(ems, world), "unit": "s", "h2d_bytes_per_step": int(8 * (2 * n - 1)),
+               "d2h_bytes_per_step": int(8 * (n + 2 * n * n)), "steps": k2,
+               "pipeline": "outputs double-buffered: D2H of step k on a copy stream overlaps the SVD of step k+1",
+               "result_matches_device_run": ok}
+        del outs, hosts
 
     if rank != 0:
         if world > 1:
@@ -462,57 +670,65 @@ def main():
         return
 
     peaks, peak_src = load_peaks()
-    g = prof["gemm"]
-    dominant = max(prof, key=lambda k: prof[k]["ms"])
-    if a.prec == "fp64":
-        gemm_peak, gemm_unit_src = FP64_DMMA_TFLOPS, "FP64 mma.sync rate from a throughput probe on this GB300"
+    sm_mhz = (clk or {}).get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
+    stages = {}
+    pk = None
+    for name, pr in profs.items():
+        stages[name], pk = stage_table(pr, 1, peaks, sm_mhz, fp64_products=(name == "fp64"))
+    main_stages = stages["mixed"]
+    dominant = max(main_stages, key=lambda k: main_stages[k].get("ms_per_step", 0.0))
+    dom = main_stages[dominant]
+    if dom["bound"] == "tensor":
+        roofline = {"bound": "tensor", "achieved": dom["tflops_executed"], "peak": dom["tensor_peak_tflops"],
+                    "unit": "TFLOP/s", "frac": dom["tensor_frac"]}
+        roofline["peak_source"] = (f"bf16_tflops burst ({peak_src}; an ms-scale kernel timed alone)"
+                                   if a.prec != "fp64" else "FP64 mma.sync probe rate x clock")
+    elif dom["bound"].startswith("fp64"):
+        roofline = {"bound": "alu", "achieved": dom["fp64_gops"], "peak": pk["fp64_alu_gops"], "unit": "GFLOP/s",
+                    "frac": dom["fp64_frac"],
+                    "peak_source": f"FP64 lane operations: {FP64_ALU_OPS_PER_CLK_SM}/clk/SM (DFMA probe) x {SMS} SMs "
+                                   f"x {sm_mhz:.0f} MHz (median SM clock of the timed region)"}
     else:
-        gemm_peak, gemm_unit_src = float(peaks.get("bf16_tflops_sustained", FALLBACK["bf16_tflops_sustained"])), \
-            f"bf16_tflops_sustained ({peak_src})"
-    achieved = g["work"] / (g["ms"] * 1e-3) / 1e12 if g["ms"] > 0 else 0.0
-    roofline = {"bound": "tensor", "achieved": achieved, "peak": gemm_peak, "unit": "TFLOP/s",
-                "frac": achieved / gemm_peak if gemm_peak else None, "traffic": None,
-                "kernel": "merge products (" + ("DMMA f64" if a.prec == "fp64" else "tcgen05 bf16 slices") + ")",
-                "peak_source": gemm_unit_src, "dominant_stage": dominant}
-    stages = {k: {"ms_per_step": v["ms"] / a.steps, "launches_per_step": v["launches"] / a.steps,
-                  "work_per_step": v["work"] / a.steps} for k, v in prof.items()}
-    if prof["secular"].get("roots"):
-        stages["secular"]["roots_per_step"] = prof["secular"]["roots"] / a.steps
-        stages["secular"]["iters_per_root"] = prof["secular"]["iters"] / prof["secular"]["roots"]
-    hbm = float(peaks.get("hbm_gbs", FALLBACK["hbm_gbs"]))
-    for k in ("gather", "vectors", "finish", "final"):
-        if prof[k]["ms"] > 0:
-            stages[k]["GBps"] = prof[k]["work"] / (prof[k]["ms"] * 1e-3) / 1e9
-            stages[k]["hbm_frac"] = stages[k]["GBps"] / hbm
-    launches = int(sum(v["launches"] for v in prof.values()) / a.steps) * a.steps
+        roofline = {"bound": "hbm", "achieved": dom["GBps"], "peak": pk["hbm_gbs"], "unit": "GB/s",
+                    "frac": dom["hbm_frac"], "peak_source": f"hbm_gbs ({peak_src})"}
+    roofline["kernel"] = dom["kernel"]
+    roofline["stage"] = dominant
+    roofline["stage_ms_per_step"] = dom["ms_per_step"]
+    roofline["traffic"] = read_traffic(dominant)
+    roofline["traffic_note"] = ("dram__bytes_read.sum + dram__bytes_write.sum per launch, " + os.path.relpath(
+        TRAFFIC_FILE, ROOT)) if roofline["traffic"] is not None else "no ncu capture of the current kernel sources"
+    launches = int(sum(v["launches"] for v in profs["mixed"].values()))
 
-    # the root-start comparison: one untimed run with each other start rule
-    # (FP64 iterations per root, secular stage time, SVD time)
-    root_start = {"mode": a.start, "iters_per_root": stages["secular"].get("iters_per_root"),
-                  "secular_ms_per_step": stages["secular"]["ms_per_step"], "mlp_training": train_info}
-    for other in ("plain", "analytic", "mlp"):
-        if other == a.start or (other == "mlp" and P is None):
-            continue
-        o_cmp = bdc.make_opts(a.prec, a.leaf, 64, a.slices, seed=other, mlp=P, mixed_min=a.mixed_min)
-        bdc.profile_begin()
-        q0 = torch.cuda.Event(enable_timing=True)
-        q1 = torch.cuda.Event(enable_timing=True)
-        q0.record(st)
-        rc = L.bdc_svd_ex(n, bdc._ptr(d), bdc._ptr(e), bdc._ptr(Ut), bdc._ptr(S), bdc._ptr(VTt), n, n,
-                          ctypes.byref(o_cmp), bdc._ptr(work), work.numel(), bdc._ptr(info),
-                          ctypes.c_void_p(st.cuda_stream))
-        q1.record(st)
-        torch.cuda.synchronize()
-        pp = bdc.profile_end()
-        if rc == 0 and pp["secular"].get("roots"):
-            root_start[other] = {"iters_per_root": pp["secular"]["iters"] / pp["secular"]["roots"],
-                                 "secular_ms": pp["secular"]["ms"], "svd_ms": q0.elapsed_time(q1)}
+    root_start = {"mode": a.start, "iters_per_root": main_stages.get("secular", {}).get("iters_per_root"),
+                  "mlp_training": train_info}
+    if "mixed_mlp" in stages:
+        root_start["mlp"] = {"iters_per_root": stages["mixed_mlp"].get("secular", {}).get("iters_per_root"),
+                             "svd_ms": timed["mixed_mlp"],
+                             "secular_ms": stages["mixed_mlp"].get("secular", {}).get("ms_per_step")}
+
+    comparison = {"mixed_ms": timed["mixed"]}
+    if "fp64" in timed:
+        comparison.update({"fp64_ms": timed["fp64"], "fp64_over_mixed": timed["fp64"] / timed["mixed"]})
+    if "mixed_mlp" in timed:
+        comparison.update({"mixed_mlp_ms": timed["mixed_mlp"], "fp64_over_mixed_mlp":
+                           (timed["fp64"] / timed["mixed_mlp"]) if "fp64" in timed else None,
+                           "mixed_mlp_over_mixed": timed["mixed_mlp"] / timed["mixed"]})
+
+    batch = None
+    if not a.no_batch and world == 1:
+        del work, Ut, VTt
+        torch.cuda.empty_cache()
+        batch = {}
+        for dt in ("fp64", "fp32"):
+            r = batched_run(a, dt, a.steps, a.warmup)
+            batch[dt] = {k: r[k] for k in ("matrices_per_s", "ms_per_batch", "e2e_matrices_per_s", "leaf",
+                                           "mixed_min", "prec", "accuracy")}
+        batch["workload"] = "2048 bidiagonals, n = floor(exp(U(ln 32, ln 1024))) seed 3, d,e~U(0.5,1.5); one graph"
 
     cpu = None
-    if not a.no_cpu_baseline and world == 1:
-        cpu = cpu_baseline_oracle(n, a.kind, a.seed)
+    if not a.no_cpu_baseline and world == 1 and sigma_s is not None:
+        cpu = cpu_baseline_measured(a.kind, n, a.seed, d_h, e_h, sigma_s)
 
-    flops_model = 8.0 / 3.0 * n ** 3
     line = {
         "metric": METRIC,
         "value": replica_seconds_per_svd(ms, world),
@@ -526,17 +742,24 @@ def main():
         "vs_baseline": None,
         "dtype": "f64" if a.prec == "fp64" else "f64 (merge products: bf16 slices, exact int accumulation)",
         "data": "synthetic",
-        "config": {"workload": workload_name(a), "n": n, "prec": a.prec, "leaf": a.leaf,
+        "config": {"workload": workload_name(a.kind, n, a.seed), "n": n, "prec": a.prec, "leaf": a.leaf,
                    "slices": (a.slices or 7) if a.prec == "exact" else None,
                    "l2": "inputs larger than L2 (U, V and workspace > 10 GB per step)",
                    "start": a.start, "fp32_root_start": True, "parallelism": f"replicas x{world}"},
-        "gflops_paper_model": flops_model / (ms * 1e-3) / 1e9,
+        "comparison": comparison,
         "status": status,
-        "accuracy": acc,
+        "accuracy": accs.get("mixed"),
+        "accuracy_fp64": accs.get("fp64"),
+        "accuracy_mixed_mlp": accs.get("mixed_mlp"),
         "roofline": roofline,
-        "stages": stages,
+        "peaks": pk,
+        "stages": main_stages,
+        "stages_fp64": stages.get("fp64"),
         "root_start": root_start,
-        "gpu_launches": launches,
+        "batched": batch,
+        "gpu_launches": launches * a.steps,
+        "gflops_model_8n3_3": 8.0 / 3.0 * n ** 3 / (ms * 1e-3) / 1e9,
+        "gflops_model_note": "the paper's (8/3) n^3 flop model / time; deflation removes most of that work here",
         "e2e": e2e,
         "cpu_baseline": cpu,
         "clocks": clk,

@@ -22,7 +22,10 @@
  *     +k (k > 0) when k leaf QR iterations or secular roots failed to
  *     converge (results are then not reliable); BDC_ERR_CUDA for a CUDA
  *     launch / allocation failure; BDC_ERR_TIMEOUT when a bounded device
- *     wait gave up; BDC_ERR_NONFINITE when d or e holds NaN or Inf.
+ *     wait gave up; BDC_ERR_NONFINITE when d or e holds NaN or Inf (a code
+ *     of its own, negative, so that it cannot be read as a count of
+ *     non-converged problems); BDC_ERR_CHECK when checked mode found a
+ *     violated invariant.
  *   - Streams: all work is enqueued on `stream` (0 = legacy default).
  */
 #ifndef BDC_H
@@ -41,6 +44,7 @@ typedef struct CUstream_st *bdc_stream_t; /* same object as cudaStream_t */
 #define BDC_ERR_TIMEOUT   (-1001)
 #define BDC_ERR_NONFINITE (-1002)
 #define BDC_ERR_INTERNAL  (-1003)
+#define BDC_ERR_CHECK     (-1004)
 
 /* Precision of the merge products W~ U_M and Q~ V_M (Eq. bdc-Mv2Bv-u-vt).
  *   BDC_FP64          FP64 products.
@@ -71,7 +75,16 @@ typedef struct {
     int leaf;          /* leaf size L (4..64; 0 = default 8)              */
     int max_iter;      /* secular / QR iteration cap (0 = default 64)     */
     int slices;        /* BDC_MIXED_EXACT slice count 4..7 (0 = automatic: 7)    */
-    int checked;       /* reserved, must be 0                              */
+    int checked;       /* 1: checked mode: after every merge's deflation
+                          and secular solve and after the final sort, device
+                          kernels verify the invariants of the solve (counts
+                          and K order of the survivors, strictly ascending
+                          survivor values from d_0 = 0, non-zero z, the K
+                          positions a permutation, slots inside [0, n),
+                          each root on its interval's side of its origin,
+                          finite z~, S finite, non-negative, descending) and
+                          a violation sets the status to BDC_ERR_CHECK
+                          instead of trapping (0 = off)                   */
     const float *mlp;  /* device pointer to MLP weights when seed = MLP    */
     int mixed_min;     /* split-BF16 products only for merges of order >= mixed_min,
                           FP64 products below (0 = automatic: 64)           */
@@ -79,7 +92,23 @@ typedef struct {
                           pole sums on FP32 copies of d and z, the two
                           interval poles exact), then finishes in FP64 to the
                           same stopping rule (bdc_opts_default: 1)        */
+    int vectors;       /* bdc_vectors: which singular vectors bdc_svd_ex
+                          forms (0 = both)                                */
 } bdc_opts;
+
+/* Singular vectors formed by bdc_svd_ex (Sec. 4.2 with vectors for one
+ * side only, the "next" partial-vector variants of the solve):
+ *   BDC_VEC_BOTH  U and V^T;
+ *   BDC_VEC_V     V^T only: the merges skip the U side (its gathers, vector
+ *                 columns, products and output); U may be NULL and ldu is
+ *                 not checked;
+ *   BDC_VEC_U     U only: solved as BDC_VEC_V on J B^T J (J the reversal,
+ *                 an upper bidiagonal with diagonal d reversed and
+ *                 superdiagonal e reversed, whose right singular vectors are
+ *                 J U), the final kernel writing them back in row-reversed
+ *                 order; VT may be NULL and ldvt is not checked.
+ * The singular values are those of B in every mode. */
+typedef enum { BDC_VEC_BOTH = 0, BDC_VEC_V = 1, BDC_VEC_U = 2 } bdc_vectors;
 
 /* Fill *o with the defaults (FP64, plain seed, leaf 8, automatic slices). */
 void bdc_opts_default(bdc_opts *o);
@@ -218,9 +247,11 @@ int bdc_deflate(int m, const double *d, const double *z, double tol, int *keep, 
  * returns -1 before any work is queued.  No cudaMalloc / cudaFree or other
  * allocating call is made.  The first call on a device looks the array's
  * device address up (cudaGetSymbolAddress) with that device current; make
- * that first call before capturing a stream.  All calls share the array, so
- * calls that can run at the same time on the GPU race and must be ordered
- * by the caller. */
+ * that first call before capturing a stream.  The address is kept for the
+ * life of the process: after cudaDeviceReset on a device (a new context and
+ * a new copy of the array) this entry point must not be called again on that
+ * device in the same process.  All calls share the array, so calls that can
+ * run at the same time on the GPU race and must be ordered by the caller. */
 #define BDC_DEFLATE_NOALLOC_MAX 65536
 int bdc_deflate_noalloc(int m, const double *d, const double *z, double tol, int *keep, double *zout,
                         double *dval, bdc_stream_t stream);
@@ -318,23 +349,86 @@ int bdc_mlp_adam(float *params, const float *grad, float *m, float *v, int step,
  * the root solver runs. */
 int bdc_mlp_predict(const float *params, const float *feat, int count, float *out, bdc_stream_t stream);
 
+/* Fit params (device, bdc_mlp_param_count floats) to `count` harvested
+ * pairs: bdc_mlp_init(seed), then `steps` full-batch Adam steps (beta1 0.9,
+ * beta2 0.999, eps 1e-8) on the Huber loss of bdc_mlp_grad, the learning
+ * rate decaying linearly from lr (step 1) to lr / 10 (the last step).
+ * losses (device, `steps` floats, may be NULL) gets the loss before each
+ * step.  Allocates its scratch with cudaMallocAsync on `stream`;
+ * asynchronous.  Returns -1 (params), -2 (count <= 0 or feat, targ NULL),
+ * -5 (steps < 0), -6 (lr <= 0), -7 (huber NaN) or BDC_ERR_CUDA. */
+int bdc_mlp_fit(float *params, const float *feat, const float *targ, int count, int steps, float lr, float huber,
+                unsigned long long seed, float *losses, bdc_stream_t stream);
+
+/* Harvest and training in one call (the learned start of the secular roots
+ * is trained on roots that FP64 solves of this library produce):
+ *   1. two n x n bidiagonals are generated on the device from a
+ *      counter-based generator keyed by t->seed: uniform d, e ~ U(0.5, 1.5)
+ *      and graded d_k = 10^(-8k/n) U(0.5, 1.5), e_k = d_k / 2;
+ *   2. both are solved with FP64 products and plain starts (the other
+ *      fields of *o, e.g. leaf and max_iter, apply; o may be NULL) while
+ *      every merge root but each merge's last is harvested (bdc_svd_harvest,
+ *      at most 2^21 samples);
+ *   3. bdc_mlp_fit(t->steps, t->lr, t->huber, t->seed) on the samples.
+ * params: device output (bdc_mlp_param_count floats); losses: device,
+ * t->steps floats, may be NULL; *samples (host, may be NULL): samples
+ * harvested; out_path (may be NULL): the parameters are also written there
+ * as raw little-endian FP32.  t may be NULL (all defaults).  Synchronous:
+ * allocates and frees its buffers (about 16 n^2 + 100 MB bytes plus the
+ * workspace of one solve) on `stream` and returns when training is done.
+ * Returns 0; -1 (options), -2 (training options), -3 (params NULL), -6
+ * (out_path not writable); a positive count when a harvest solve did not
+ * converge; BDC_ERR_INTERNAL when nothing was harvested; BDC_ERR_CUDA. */
+typedef struct {
+    int n;                   /* order of the harvest bidiagonals, 16..65536 (0 = 8192) */
+    int steps;               /* Adam steps (0 = 1500) */
+    float lr;                /* initial learning rate (0 = 3e-3) */
+    float huber;             /* Huber threshold (0 = 0.25; < 0: squared loss) */
+    unsigned long long seed; /* generator and initialisation seed */
+} bdc_mlp_train_opts;
+int bdc_mlp_train(const bdc_opts *o, const bdc_mlp_train_opts *t, float *params, float *losses, int *samples,
+                  const char *out_path, bdc_stream_t stream);
+
 /* ---------------- stage profiling (CUDA events, host side) ---------------
  * bdc_profile_begin(1) makes every later call record a CUDA event pair
- * around each stage launch on the call's stream; bdc_profile_end() waits
+ * around each stage's launches on the call's stream; bdc_profile_end() waits
  * for them and returns, per stage kind k (BDC_STAGE_*), the summed device
  * milliseconds in ms[k], the launch count in launches[k] and the summed
- * algorithmic work in work[k]: for the products the flops 2 M N K of every
- * product at its deflated size (times the slice pairs of the split BF16
- * paths), for the data-movement stages the bytes they must read and write.
- * Arrays have BDC_NSTAGES
- * entries (any may be NULL).  Not thread safe; not for graph capture. */
+ * algorithmic work in work[k]:
+ *   BDC_STAGE_GEMM     tensor flops 2 M N K of every merge product at its
+ *                      deflated size, times the slice pairs of the split
+ *                      BF16 paths (the products the tensor cores execute);
+ *   every other stage  the bytes it must move through HBM (reads + writes)
+ *                      at the deflated sizes: scale 32 n; leaf the leaves'
+ *                      U, V blocks; prep 80 m per merge; gather the N
+ *                      survivor columns of W~, Q~ written in full and their
+ *                      child-block rows read (12 N (m + m + sqre)); secular
+ *                      and Loewner 0 (d, z stay in cache); vectors 16 N Ktot
+ *                      (U_M, V_M written); slice (8 + 2 S)(M K + K N) per
+ *                      split product; finish 24 m; final 16 n^2 (U, V^T
+ *                      written).
+ * BDC_STAGE_SLICE and BDC_STAGE_LOWNER are split out of BDC_STAGE_GEMM and
+ * BDC_STAGE_SECULAR (operand slicing of the split-BF16 products; the z~
+ * products of Eq. bdc-zi).  Arrays have BDC_NSTAGES entries (any may be
+ * NULL).  Not thread safe; not for graph capture. */
 enum { BDC_STAGE_SCALE = 0, BDC_STAGE_LEAF, BDC_STAGE_PREP, BDC_STAGE_GATHER, BDC_STAGE_SECULAR,
-       BDC_STAGE_VECTORS, BDC_STAGE_GEMM, BDC_STAGE_FINISH, BDC_STAGE_FINAL, BDC_NSTAGES };
+       BDC_STAGE_VECTORS, BDC_STAGE_GEMM, BDC_STAGE_FINISH, BDC_STAGE_FINAL, BDC_STAGE_SLICE, BDC_STAGE_LOWNER,
+       BDC_NSTAGES };
 int bdc_profile_begin(int on);
 int bdc_profile_end(double *ms, long long *launches, double *work);
 /* After bdc_profile_end: secular roots solved and root-finder iterations
  * spent (summed over the recorded calls), *roots and *iters (host). */
 int bdc_profile_secular(long long *roots, long long *iters);
+/* After bdc_profile_end: FP64 operations (lane operations, an FMA counted
+ * once) per stage kind, fp64[BDC_NSTAGES] (host), from the recorded calls'
+ * deflated sizes, root-finder iterations and leaf rotation counts:
+ *   secular  9 per pole term, N terms per pole-sum evaluation, 1 + iters
+ *            evaluations per root (the FP32 pre-iterations not counted);
+ *   Loewner  10 per factor, N - 1 factors per z~ entry;
+ *   vectors  15 per entry of U_M, V_M (one quotient and the norms);
+ *   leaf     17 per logged rotation (forming and applying it to d, e) and
+ *            6 per rotation per row of U or V it is replayed on. */
+int bdc_profile_fp64(double *fp64);
 
 /* Text of the last CUDA error the library saw on this thread ("" if none);
  * reading it clears it. */

@@ -115,6 +115,24 @@ def sigma_only(d, e, max_sweeps: int = 30):
     return s[:n]
 
 
+def _sigma_job(de):
+    return sigma_only(*de)
+
+
+def sigma_only_many(mats, workers=None):
+    """sigma_only of every (d, e) in `mats`, in order, over a pool of
+    spawned worker processes (the matrices are independent; each one is
+    solved by the same single-threaded QR)."""
+    import multiprocessing as mp
+    build()
+    mats = [(np.asarray(d, dtype=np.float64), np.asarray(e, dtype=np.float64)) for d, e in mats]
+    workers = workers or max(1, min(len(mats), len(os.sched_getaffinity(0))))
+    if workers <= 1 or len(mats) <= 1:
+        return [sigma_only(d, e) for d, e in mats]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return pool.map(_sigma_job, mats, chunksize=max(1, len(mats) // (4 * workers)))
+
+
 def sturm_count(d, e, x: float) -> int:
     """Eigenvalues below x of the Golub-Kahan tridiagonal of (d, e)."""
     lib = _load()

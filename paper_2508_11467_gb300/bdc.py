@@ -20,14 +20,15 @@ LIB_PATH = _build.LIB
 BDC_FP64, BDC_MIXED_BF16X3, BDC_MIXED_EXACT = 0, 1, 2
 BDC_SEED_PLAIN, BDC_SEED_MLP, BDC_SEED_ANALYTIC = 0, 1, 2
 SEED = {"plain": BDC_SEED_PLAIN, "mlp": BDC_SEED_MLP, "analytic": BDC_SEED_ANALYTIC}
-BDC_ERR_CUDA, BDC_ERR_TIMEOUT, BDC_ERR_NONFINITE, BDC_ERR_INTERNAL = -1000, -1001, -1002, -1003
+BDC_ERR_CUDA, BDC_ERR_TIMEOUT, BDC_ERR_NONFINITE, BDC_ERR_INTERNAL, BDC_ERR_CHECK = -1000, -1001, -1002, -1003, -1004
 PREC = {"fp64": BDC_FP64, "bf16x3": BDC_MIXED_BF16X3, "exact": BDC_MIXED_EXACT, "mixed": BDC_MIXED_EXACT}
 
 
 class Opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("seed", ctypes.c_int), ("leaf", ctypes.c_int),
                 ("max_iter", ctypes.c_int), ("slices", ctypes.c_int), ("checked", ctypes.c_int),
-                ("mlp", ctypes.c_void_p), ("mixed_min", ctypes.c_int), ("fp32_start", ctypes.c_int)]
+                ("mlp", ctypes.c_void_p), ("mixed_min", ctypes.c_int), ("fp32_start", ctypes.c_int),
+                ("vectors", ctypes.c_int)]
 
 
 _lock = threading.Lock()
@@ -63,6 +64,8 @@ _SIGS = {
     "bdc_mlp_adam": (_I, [_VP, _VP, _VP, _VP, _I, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                           ctypes.c_float, _VP]),
     "bdc_mlp_predict": (_I, [_VP, _VP, _I, _VP, _VP]),
+    "bdc_mlp_fit": (_I, [_VP, _VP, _VP, _I, _I, ctypes.c_float, ctypes.c_float, ctypes.c_ulonglong, _VP, _VP]),
+    "bdc_mlp_train": (_I, [_VP, _VP, _VP, _VP, _VP, ctypes.c_char_p, _VP]),
     "bdc_plan_create": (_I, [_VP, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "bdc_plan_launch": (_I, [_VP, _VP]),
     "bdc_plan_destroy": (None, [_VP]),
@@ -75,10 +78,11 @@ _SIGS = {
     "bdc_profile_begin": (_I, [_I]),
     "bdc_profile_end": (_I, [_VP, _VP, _VP]),
     "bdc_profile_secular": (_I, [_VP, _VP]),
+    "bdc_profile_fp64": (_I, [_VP]),
     "bdc_last_error_string": (ctypes.c_char_p, []),
 }
 
-STAGES = ["scale", "leaf", "prep", "gather", "secular", "vectors", "gemm", "finish", "final"]
+STAGES = ["scale", "leaf", "prep", "gather", "secular", "vectors", "gemm", "finish", "final", "slice", "lowner"]
 
 
 def profile_begin():
@@ -86,16 +90,21 @@ def profile_begin():
 
 
 def profile_end():
-    """Per-stage device ms, launch counts and algorithmic work since profile_begin()."""
+    """Per-stage device ms, launch counts, algorithmic work (tensor flops for
+    "gemm", HBM bytes for the others) and FP64 operations since
+    profile_begin()."""
     import numpy as np
     k = len(STAGES)
     ms = np.zeros(k)
     ln = np.zeros(k, dtype=np.int64)
     wk = np.zeros(k)
+    f64 = np.zeros(k)
     _check("bdc_profile_end", lib().bdc_profile_end(ms.ctypes.data_as(ctypes.c_void_p),
                                                      ln.ctypes.data_as(ctypes.c_void_p),
                                                      wk.ctypes.data_as(ctypes.c_void_p)))
-    out = {s: {"ms": float(ms[i]), "launches": int(ln[i]), "work": float(wk[i])} for i, s in enumerate(STAGES)}
+    lib().bdc_profile_fp64(f64.ctypes.data_as(ctypes.c_void_p))
+    out = {s: {"ms": float(ms[i]), "launches": int(ln[i]), "work": float(wk[i]), "fp64": float(f64[i])}
+           for i, s in enumerate(STAGES)}
     r, it = ctypes.c_longlong(0), ctypes.c_longlong(0)
     lib().bdc_profile_secular(ctypes.byref(r), ctypes.byref(it))
     out["secular"]["roots"] = int(r.value)
@@ -158,11 +167,16 @@ def _dev(t, dtype=torch.float64):
     return t.to(dtype).contiguous()
 
 
+VECTORS = {"both": 0, "v": 1, "u": 2}
+
+
 def make_opts(prec="fp64", leaf=0, max_iter=64, slices=0, seed="plain", mlp=None, mixed_min=0,
-              fp32_start=True) -> Opts:
+              fp32_start=True, vectors="both", checked=False) -> Opts:
     o = Opts()
     lib().bdc_opts_default(ctypes.byref(o))
+    o.checked = 1 if checked else 0
     o.fp32_start = 1 if fp32_start else 0
+    o.vectors = VECTORS[vectors] if isinstance(vectors, str) else int(vectors)
     o.mixed_min = int(mixed_min)
     o.prec = PREC[prec] if isinstance(prec, str) else int(prec)
     o.leaf = int(leaf)
@@ -178,19 +192,20 @@ def workspace_bytes(n: int, opts: Opts) -> int:
 
 
 def svd(d, e, *, prec="fp64", leaf=0, max_iter=64, slices=0, seed="plain", mlp=None,
-        stream=None, work=None, check=True, mixed_min=0, fp32_start=True):
+        stream=None, work=None, check=True, mixed_min=0, fp32_start=True, vectors="both", checked=False):
     """SVD of the upper bidiagonal (d, e) on the GPU.
 
     Returns (S, U, VT) as CUDA float64 tensors (U column-major: U[:, i] is a
-    left vector; VT[i, :] a right vector) and the status code.
+    left vector; VT[i, :] a right vector) and the status code.  vectors="v"
+    forms V^T only (U is None), vectors="u" U only (VT is None).
     """
     d = _dev(d)
     n = d.shape[0]
     e = _dev(e) if n > 1 else torch.zeros(1, dtype=torch.float64, device=d.device)
-    o = make_opts(prec, leaf, max_iter, slices, seed, mlp, mixed_min, fp32_start)
+    o = make_opts(prec, leaf, max_iter, slices, seed, mlp, mixed_min, fp32_start, vectors, checked)
     # column-major outputs: allocate the transpose and view it back
-    Ut = torch.empty((n, n), dtype=torch.float64, device=d.device)
-    VTt = torch.empty((n, n), dtype=torch.float64, device=d.device)
+    Ut = torch.empty((n, n), dtype=torch.float64, device=d.device) if vectors != "v" else None
+    VTt = torch.empty((n, n), dtype=torch.float64, device=d.device) if vectors != "u" else None
     S = torch.empty(max(n, 1), dtype=torch.float64, device=d.device)
     info = torch.zeros(1, dtype=torch.int32, device=d.device)
     lw = workspace_bytes(n, o)
@@ -202,7 +217,7 @@ def svd(d, e, *, prec="fp64", leaf=0, max_iter=64, slices=0, seed="plain", mlp=N
     code = int(info.item())
     if check and code != 0:
         raise BDCError("bdc_svd_ex (device status)", code)
-    return S[:n], Ut.t(), VTt.t(), code
+    return S[:n], (Ut.t() if Ut is not None else None), (VTt.t() if VTt is not None else None), code
 
 
 def svd_values(d, e, *, leaf=0, max_iter=64, seed="plain", mlp=None, stream=None, check=True, fp32_start=True):
@@ -452,24 +467,35 @@ def mlp_predict(P, feat, stream=None):
 
 
 def mlp_train(feat, targ, steps=1500, lr=3e-3, seed=0, huber=0.25, stream=None):
-    """Full-batch Adam on the harvested pairs with the library's kernels
-    (Huber loss, threshold `huber`); the learning rate decays linearly to
-    lr/10.  Returns (params, losses)."""
-    P = mlp_init(feat, targ, seed, stream)
-    m = torch.zeros_like(P)
-    v = torch.zeros_like(P)
-    count = int(feat.shape[0])
-    lw = int(lib().bdc_mlp_grad_workspace(count))
-    work = torch.empty(max(lw, 1), dtype=torch.uint8, device=P.device)
-    losses = torch.empty(steps, dtype=torch.float32, device=P.device)
-    g = torch.empty_like(P)
-    for k in range(1, steps + 1):
-        lr_k = lr * (1.0 - 0.9 * (k - 1) / max(steps - 1, 1))
-        _check("bdc_mlp_grad", lib().bdc_mlp_grad(_ptr(P), _ptr(feat), _ptr(targ), count, float(huber), _ptr(g),
-                                                   _ptr(losses[k - 1:k]), _ptr(work), work.numel(),
-                                                   _stream(stream)))
-        mlp_adam(P, g, m, v, k, lr_k, stream=stream)
-    return P, losses
+    """bdc_mlp_fit: initialisation and full-batch Adam on the harvested pairs
+    (Huber loss, threshold `huber`; learning rate decaying linearly to
+    lr/10).  Returns (params, losses), both on the device."""
+    P = torch.empty(mlp_param_count(), dtype=torch.float32, device=feat.device)
+    losses = torch.empty(max(int(steps), 1), dtype=torch.float32, device=feat.device)
+    _check("bdc_mlp_fit", lib().bdc_mlp_fit(_ptr(P), _ptr(feat), _ptr(targ), int(feat.shape[0]), int(steps),
+                                             float(lr), float(huber), int(seed), _ptr(losses), _stream(stream)))
+    return P, losses[:int(steps)]
+
+
+class MlpTrainOpts(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("steps", ctypes.c_int), ("lr", ctypes.c_float), ("huber", ctypes.c_float),
+                ("seed", ctypes.c_ulonglong)]
+
+
+def mlp_train_harvest(n=8192, steps=1500, lr=3e-3, huber=0.25, seed=0, leaf=0, out_path=None, device="cuda",
+                      stream=None):
+    """bdc_mlp_train: harvest roots from FP64 solves of an n x n uniform and
+    an n x n graded bidiagonal generated on the device, then fit the network.
+    Returns (params, losses, samples)."""
+    P = torch.empty(mlp_param_count(), dtype=torch.float32, device=device)
+    losses = torch.empty(max(int(steps), 1), dtype=torch.float32, device=device)
+    t = MlpTrainOpts(int(n), int(steps), float(lr), float(huber), int(seed))
+    o = make_opts("fp64", leaf)
+    cnt = ctypes.c_int(0)
+    _check("bdc_mlp_train", lib().bdc_mlp_train(ctypes.byref(o), ctypes.byref(t), _ptr(P), _ptr(losses),
+                                                 ctypes.byref(cnt), out_path.encode() if out_path else None,
+                                                 _stream(stream)))
+    return P, losses[:int(steps)], int(cnt.value)
 
 
 def mlp_save(P, path):

@@ -37,7 +37,7 @@ def _headers_mtime() -> float:
     return max((os.path.getmtime(h) for h in hs), default=0.0)
 
 
-FP32_SOURCES = ("bdc_driver.cu", "bdc_leaf.cu", "bdc_merge.cu", "bdc_secular.cu", "bdc_gemm64.cu")
+FP32_SOURCES = ("bdc_driver.cu", "bdc_leaf.cu", "bdc_merge.cu", "bdc_secular.cu", "bdc_gemm64.cu", "bdc_check.cu")
 
 
 def _compile(job, hdr_mtime: float, force: bool) -> str:

@@ -13,6 +13,7 @@
 // prep (z, sort, deflation) -> gather (rotations, permutation) -> secular
 // roots + z~ -> vectors of M~ -> merge products -> finish -> final sort.
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -26,7 +27,7 @@ namespace BDC_NS {
 // mixed-precision product path (bdc_gemm_mixed.cu): products packed one after
 // another in the sliced operand arrays, rows bounded by Mmax[p], columns by Nmax[p]
 cudaError_t launch_gemm_mixed(const GemmProb *probs, int nprobs, const int *Mmax, const int *Nmax, int kmax,
-                              int prec, int slices, void *scratch, size_t scratch_bytes, cudaStream_t st);
+                              int prec, int slices, void *scratch, size_t scratch_bytes, int *err, cudaStream_t st);
 size_t gemm_mixed_scratch(long long rows_total, long long cols_total, int kmax, int prec, int slices,
                           long long tiles);
 #endif
@@ -86,6 +87,7 @@ struct Plan {
     int nmax = 0;
     // workspace layout (byte offsets)
     size_t off_mats = 0, off_leaves = 0, off_nodes = 0, off_state = 0, off_probs = 0;
+    size_t off_err = 0;                    // error word of the bounded device waits (product kernels)
     std::vector<size_t> off_mat_data;      // per matrix
     std::vector<size_t> off_height_nodes;  // per height, into the nodes area
     size_t off_mixed = 0, mixed_bytes = 0;
@@ -174,6 +176,7 @@ Plan make_plan(int nmat, const int *ns, const bdc_opts &o, int vals = 0) {
     off += align256(std::max<size_t>(nodes_bytes, 1));
     p.off_state = off; off += align256(sizeof(NodeState) * std::max(p.nnodes, 1));
     p.off_probs = off; off += align256(sizeof(GemmProb) * std::max(p.maxprobs, 1));
+    p.off_err = off; off += 256;
     for (int mi = 0; mi < nmat; ++mi) {
         p.off_mat_data.push_back(off);
         off += per_matrix_bytes(std::max(ns[mi], 1), vals);
@@ -293,7 +296,7 @@ __global__ void __launch_bounds__(1024) k_scale(const MatDesc *__restrict__ mats
             const int i = i0 + u * T;
             v[u] = (i < n) ? md.d_in[i] : R(0);
             w[u] = (i + 1 < n) ? md.e_in[i] : R(0);
-        }
+        }   // (the maximum does not depend on the order: rev reads below)
 #pragma unroll
         for (int u = 0; u < 4; ++u) mx = max(mx, max(abits(v[u]), abits(w[u])));
     }
@@ -305,9 +308,11 @@ __global__ void __launch_bounds__(1024) k_scale(const MatDesc *__restrict__ mats
     const bool nf = sb >= kInfBits;
     const real_t s = from_bits(sb);
     const int ex = (nf || sb == 0) ? 0 : ilogb(s);
+    // rev: the solve runs on J B^T J, diagonal d and superdiagonal e reversed
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        md.dsc[i] = nf ? R(0) : scale_pow2(md.d_in[i], ex);
-        md.esc[i] = (nf || i + 1 >= n) ? R(0) : scale_pow2(md.e_in[i], ex);
+        const int id = md.rev ? n - 1 - i : i, ie = md.rev ? n - 2 - i : i;
+        md.dsc[i] = nf ? R(0) : scale_pow2(md.d_in[id], ex);
+        md.esc[i] = (nf || i + 1 >= n) ? R(0) : scale_pow2(md.e_in[ie], ex);
     }
     if (threadIdx.x == 0) {
         md.scale[0] = (nf || s == R(0)) ? R(0) : scalbn(R(1), ex);   // a zero matrix has zero values
@@ -315,10 +320,12 @@ __global__ void __launch_bounds__(1024) k_scale(const MatDesc *__restrict__ mats
     }
 }
 
-// status word of every matrix
-__global__ void k_info(const MatDesc *__restrict__ mats, int nmat, int *__restrict__ out) {
+// status word of every matrix; a bounded wait that gave up in any product
+// launch of the call (error word *err) makes every matrix report the timeout
+__global__ void k_info(const MatDesc *__restrict__ mats, int nmat, const int *__restrict__ err,
+                       int *__restrict__ out) {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m < nmat) out[m] = *mats[m].info;
+    if (m < nmat) out[m] = (*err != 0) ? BDC_ERR_TIMEOUT : *mats[m].info;
 }
 
 // values only: S descending and unscaled
@@ -351,8 +358,10 @@ __global__ void __launch_bounds__(256) k_final(const MatDesc *__restrict__ mats,
         const int c = c0 + threadIdx.x;
         if (c < n) {
             const int src = md.Q[n - 1 - c];
-            const int gu = md.us[0][src], gv = md.vs[0][src];
-            cg[0][threadIdx.x] = gu; clo[0][threadIdx.x] = md.ulo[gu]; chi[0][threadIdx.x] = md.uhi[gu];
+            const int gu = md.want_u ? md.us[0][src] : 0, gv = md.vs[0][src];
+            cg[0][threadIdx.x] = gu;
+            clo[0][threadIdx.x] = md.want_u ? md.ulo[gu] : 0;
+            chi[0][threadIdx.x] = md.want_u ? md.uhi[gu] : 0;
             cg[1][threadIdx.x] = gv; clo[1][threadIdx.x] = md.vlo[gv]; chi[1][threadIdx.x] = md.vhi[gv];
             if (blockIdx.y == 0) md.So[c] = md.D[src] * s;
         } else {
@@ -361,6 +370,26 @@ __global__ void __launch_bounds__(256) k_final(const MatDesc *__restrict__ mats,
         }
     }
     __syncthreads();
+    if (md.rev) {
+        // left vectors only: the right vectors of J B^T J are J U, so U's
+        // column c is the root's V column read bottom up (no transpose)
+        for (int j0 = jb; j0 < je; j0 += 32) {
+            const int j = j0 + tx;
+            real_t v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int cc = ty + 8 * q;
+                const bool ok = j < n && c0 + cc < n;
+                v[q] = (ok && j >= clo[1][cc] && j < chi[1][cc]) ? md.V[(size_t)cg[1][cc] * n + j] : R(0);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int c = c0 + ty + 8 * q;
+                if (j < n && c < n) md.Uo[(size_t)c * md.ldu + (n - 1 - j)] = v[q];
+            }
+        }
+        return;
+    }
     for (int j0 = jb; j0 < je; j0 += 32) {
         const int j = j0 + tx;
         real_t u[4], v[4];
@@ -368,13 +397,13 @@ __global__ void __launch_bounds__(256) k_final(const MatDesc *__restrict__ mats,
         for (int q = 0; q < 4; ++q) {
             const int cc = ty + 8 * q;
             const bool ok = j < n && c0 + cc < n;
-            u[q] = (ok && j >= clo[0][cc] && j < chi[0][cc]) ? md.U[(size_t)cg[0][cc] * n + j] : R(0);
+            u[q] = (ok && md.want_u && j >= clo[0][cc] && j < chi[0][cc]) ? md.U[(size_t)cg[0][cc] * n + j] : R(0);
             v[q] = (ok && j >= clo[1][cc] && j < chi[1][cc]) ? md.V[(size_t)cg[1][cc] * n + j] : R(0);
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int cc = ty + 8 * q, c = c0 + cc;
-            if (j < n && c < n) md.Uo[(size_t)c * md.ldu + j] = u[q];
+            if (md.want_u && j < n && c < n) md.Uo[(size_t)c * md.ldu + j] = u[q];
             tile[cc][tx] = v[q];
         }
         __syncthreads();
@@ -388,13 +417,91 @@ __global__ void __launch_bounds__(256) k_final(const MatDesc *__restrict__ mats,
     }
 }
 
-// Pinned host memory owned by a plan: while a plan captures its launch
-// sequence into a CUDA graph, every host->device copy of descriptors and
-// tables reads from blocks that live as long as the plan (the graph replays
-// those copies), instead of the shared cache and ring of one-shot calls.
+// Pinned host memory owned by a graph: while a plan captures its launch
+// sequence (or a caller captures one of the entry points into a graph of
+// their own), every host->device copy of descriptors and tables reads from
+// blocks that live as long as that graph (the graph replays those copies),
+// instead of the shared cache and ring of one-shot calls.
 thread_local std::vector<void *> *g_arena = nullptr;
 
+// Blocks of caller-captured graphs that have been destroyed: a CUDA user
+// object attached to the graph hands them over when its last reference goes
+// (its callback may make no CUDA call), and a later uncaptured call frees
+// them.
+std::mutex g_deferred_mu;
+std::vector<void *> g_deferred;
+
+void CUDART_CB release_graph_blocks(void *p) {
+    auto *v = static_cast<std::vector<void *> *>(p);
+    {
+        std::lock_guard<std::mutex> lk(g_deferred_mu);
+        g_deferred.insert(g_deferred.end(), v->begin(), v->end());
+    }
+    delete v;
+}
+
+void free_deferred_blocks() {
+    std::vector<void *> v;
+    {
+        std::lock_guard<std::mutex> lk(g_deferred_mu);
+        v.swap(g_deferred);
+    }
+    for (void *q : v) cudaFreeHost(q);
+}
+
 }  // namespace
+
+// An entry point called on a stream that is being captured by the caller:
+// the host blocks its copies read are allocated for this capture only and
+// handed to the capture's graph as a user object, so they stay valid for as
+// long as the graph (or an executable instantiated from it) exists, whatever
+// later calls do with the shared caches.  Host allocations run with this
+// thread's capture mode set to relaxed (a pinned allocation is not stream
+// work).  Outside a capture, blocks of destroyed graphs are freed here.
+struct CallerCapture {
+    cudaStream_t st;
+    std::vector<void *> *blocks = nullptr;
+    cudaStreamCaptureMode mode = cudaStreamCaptureModeRelaxed;
+    explicit CallerCapture(cudaStream_t s) : st(s) {
+        if (g_arena) return;                         // a plan capture owns its blocks itself
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return;
+        if (cs == cudaStreamCaptureStatusActive) {
+            blocks = new std::vector<void *>();
+            g_arena = blocks;
+            cudaThreadExchangeStreamCaptureMode(&mode);
+        } else if (cs == cudaStreamCaptureStatusNone) {
+            free_deferred_blocks();
+        }
+    }
+    // attach the blocks to the graph being captured; returns rc, or
+    // BDC_ERR_CUDA when the blocks could not be attached
+    int finish(int rc) {
+        if (!blocks) return rc;
+        g_arena = nullptr;
+        cudaThreadExchangeStreamCaptureMode(&mode);
+        std::vector<void *> *v = blocks;
+        blocks = nullptr;
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaGraph_t g = nullptr;
+        cudaUserObject_t obj = nullptr;
+        cudaError_t e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &g);
+        if (e == cudaSuccess && (cs != cudaStreamCaptureStatusActive || !g)) e = cudaErrorStreamCaptureInvalidated;
+        if (e == cudaSuccess)
+            e = cudaUserObjectCreate(&obj, v, release_graph_blocks, 1, cudaUserObjectNoDestructorSync);
+        if (e != cudaSuccess) {
+            release_graph_blocks(v);                 // freed by a later uncaptured call
+            return rc != 0 ? rc : note(e);
+        }
+        e = cudaGraphRetainUserObject(g, obj, 1, cudaGraphUserObjectMove);
+        if (e != cudaSuccess) {
+            cudaUserObjectRelease(obj, 1);
+            return rc != 0 ? rc : note(e);
+        }
+        return rc;
+    }
+    ~CallerCapture() { finish(0); }
+};
 
 void *plan_pinned_alloc(size_t bytes) {
     if (!g_arena) return nullptr;
@@ -427,7 +534,10 @@ struct ProfCall {
     const NodeState *dstate;
     int nnodes;
     std::vector<NodeDesc> merges;
+    std::vector<NodeDesc> leaves;
     int pairs;
+    int want_u;      // the U side was formed (both vector sets)
+    int slices;      // split-BF16 slice count (operand bytes of the slicing)
     int mixed_min;   // merges of order >= mixed_min ran the split products
     int vals;        // singular values only: no vectors, no products
     NodeState *host = nullptr;   // pinned copy of the node states, taken at the end of the call
@@ -439,27 +549,41 @@ struct Profiler {
 };
 Profiler g_prof;
 long long g_sec_roots = 0, g_sec_iters = 0;
+double g_fp64[BDC_NSTAGES] = {0};
 
-struct StageScope {
-    cudaStream_t st;
-    int stage;
-    long long launches;
-    double work;
-    cudaEvent_t a = nullptr, b = nullptr;
-    StageScope(cudaStream_t s, int k, long long l, double w) : st(s), stage(k), launches(l), work(w) {
-        if (g_prof.on) {
-            cudaEventCreate(&a);
-            cudaEventCreate(&b);
-            cudaEventRecord(a, st);
-        }
+}  // namespace
+
+StageScope::StageScope(cudaStream_t s, int k, long long l, double w) : st(s), stage(k), launches(l), work(w) {
+    if (g_prof.on) {
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        cudaEventRecord(a, st);
     }
-    ~StageScope() {
-        if (g_prof.on && a) {
-            cudaEventRecord(b, st);
-            g_prof.ev.push_back(ProfEvent{stage, a, b, launches, work});
-        }
+}
+StageScope::~StageScope() {
+    if (g_prof.on && a) {
+        cudaEventRecord(b, st);
+        g_prof.ev.push_back(ProfEvent{stage, a, b, launches, work});
     }
-};
+}
+
+unsigned long long test_wait_ns() {
+    if (const char *env = std::getenv("BDC_TEST_WAIT_NS")) {
+        const long long v = std::atoll(env);
+        if (v > 0) return (unsigned long long)v;
+    }
+    return 2000000000ull;
+}
+int test_stall() {
+    const char *env = std::getenv("BDC_TEST_STALL");
+    return (env && std::atoi(env) == 1) ? 1 : 0;
+}
+bool test_corrupt_root() {
+    const char *env = std::getenv("BDC_TEST_CORRUPT_ROOT");
+    return env && std::atoi(env) == 1;
+}
+
+namespace {
 
 // upload descriptors for the plan into the workspace (graph-capturable copy
 // from a pinned blob that stays alive in a bounded cache)
@@ -514,10 +638,15 @@ int run_plan(const Plan &p, const bdc_opts &o, char *work, std::vector<MatDesc> 
         c.Uo = mats[mi].Uo; c.So = mats[mi].So; c.VTo = mats[mi].VTo;
         c.ldu = mats[mi].ldu; c.ldvt = mats[mi].ldvt;
         c.feat = mats[mi].feat; c.targ = mats[mi].targ; c.hcount = mats[mi].hcount; c.hcap = mats[mi].hcap;
+        // one side only: V^T (U side skipped), or U as the right vectors of J B^T J
+        c.want_u = (o.vectors == BDC_VEC_BOTH) ? 1 : 0;
+        c.rev = (o.vectors == BDC_VEC_U) ? 1 : 0;
         mats[mi] = c;
     }
     cudaError_t e = upload(p, work, mats, st);
     if (e != cudaSuccess) return note(e);
+    int *derr = (int *)(work + p.off_err);
+    if ((e = cudaMemsetAsync(derr, 0, sizeof(int), st)) != cudaSuccess) return note(e);
     const MatDesc *dmats = (const MatDesc *)(work + p.off_mats);
     const NodeDesc *dleaves = (const NodeDesc *)(work + p.off_leaves);
     NodeState *dstate = (NodeState *)(work + p.off_state);
@@ -528,23 +657,34 @@ int run_plan(const Plan &p, const bdc_opts &o, char *work, std::vector<MatDesc> 
     for (int mi = 0; mi < p.nmat; ++mi) harvest |= (mats[mi].feat != nullptr);
     const int scans = (o.seed != BDC_SEED_PLAIN) || harvest;
 
-    double nsq = 0.0;
-    for (int mi = 0; mi < p.nmat; ++mi) nsq += (double)mats[mi].n * mats[mi].n;
-    if (p.nmat > 0) {
-        StageScope sc(st, BDC_STAGE_SCALE, 1, 0.0);
+    double nsq = 0.0, nsum = 0.0;
+    for (int mi = 0; mi < p.nmat; ++mi) {
+        nsq += (double)mats[mi].n * mats[mi].n;
+        nsum += mats[mi].n;
+    }
+    if (p.nmat > 0) {   // reads d, e and writes their scaled copies
+        StageScope sc(st, BDC_STAGE_SCALE, 1, 32.0 * nsum);
         k_scale<<<p.nmat, 1024, 0, st>>>(dmats);
         if ((e = cudaGetLastError()) != cudaSuccess) return note(e);
     }
     {
-        StageScope sc(st, BDC_STAGE_LEAF, p.leaves.empty() ? 0 : 1, 0.0);
-        if ((e = launch_leaves(dleaves, (int)p.leaves.size(), dmats, p.leafmax, 30, p.vals,
-                               p.vals ? nullptr : work + p.off_leaflog, st)) != cudaSuccess)
+        // the leaves' U and V blocks (written once; values only: two rows)
+        double lb = 0.0;
+        for (const NodeDesc &lf : p.leaves)
+            lb += p.vals ? 16.0 * (lf.m + 1) : 8.0 * ((double)lf.m * lf.m + (double)(lf.m + lf.sqre) * (lf.m + lf.sqre));
+        StageScope sc(st, BDC_STAGE_LEAF, p.leaves.empty() ? 0 : (p.vals ? 1 : 2), lb);
+        // QR sweeps per leaf row: 30, or max_iter when that is smaller
+        const int sweeps = std::min(30, o.max_iter > 0 ? o.max_iter : kDefaultMaxIter);
+        if ((e = launch_leaves(dleaves, (int)p.leaves.size(), dmats, p.leafmax, sweeps, p.vals,
+                               p.vals ? nullptr : work + p.off_leaflog, dstate, st)) != cudaSuccess)
             return note(e);
     }
     const int pairs = (o.prec == BDC_MIXED_EXACT) ? (o.slices * (o.slices + 1)) / 2
                       : (o.prec == BDC_MIXED_BF16X3) ? 3 : 1;
     if (g_prof.on) {
-        ProfCall pc{dstate, p.nnodes, {}, pairs, o.prec == BDC_FP64 ? (1 << 30) : o.mixed_min, p.vals};
+        ProfCall pc{dstate, p.nnodes, {}, p.leaves, pairs, o.vectors == BDC_VEC_BOTH ? 1 : 0,
+                    o.prec == BDC_MIXED_EXACT ? o.slices : (o.prec == BDC_MIXED_BF16X3 ? 2 : 0),
+                    o.prec == BDC_FP64 ? (1 << 30) : o.mixed_min, p.vals};
         for (auto &h : p.heights) pc.merges.insert(pc.merges.end(), h.begin(), h.end());
         g_prof.calls.push_back(std::move(pc));
     }
@@ -552,25 +692,27 @@ int run_plan(const Plan &p, const bdc_opts &o, char *work, std::vector<MatDesc> 
         const int nn = (int)p.heights[h].size();
         const int mm = p.hmmax[h];
         const NodeDesc *dn = (const NodeDesc *)(work + p.off_nodes + p.off_height_nodes[h]);
-        double m2 = 0.0;
-        for (const NodeDesc &nd : p.heights[h]) m2 += (double)nd.m * nd.m;
-        {
-            StageScope sc(st, BDC_STAGE_PREP, 1, 0.0);
+        double msum = 0.0;
+        for (const NodeDesc &nd : p.heights[h]) msum += nd.m;
+        {   // O(m) bookkeeping per merge (about ten m-long arrays read or written)
+            StageScope sc(st, BDC_STAGE_PREP, 1, 80.0 * msum);
             if ((e = launch_merge_prep(dn, nn, dmats, dstate, dprobs, mm, scans, st)) != cudaSuccess) return note(e);
         }
+        if (o.checked && (e = launch_check_prep(dn, nn, dmats, dstate, st)) != cudaSuccess) return note(e);
         if (p.vals) {   // values only: two rows of V instead of the panels
             StageScope sc(st, BDC_STAGE_GATHER, 1, 0.0);
             if ((e = launch_gather_rows(dn, nn, dmats, dstate, mm, st)) != cudaSuccess) return note(e);
-        } else {   // reads the children's U, V halves (8 m^2 B), writes W~ and Q~ (16 m^2 B)
-            StageScope sc(st, BDC_STAGE_GATHER, 1, 24.0 * m2);
+        } else {   // survivors' columns of W~ and Q~ (bytes added from the node states)
+            StageScope sc(st, BDC_STAGE_GATHER, 1, 0.0);
             if ((e = launch_merge_gather(dn, nn, dmats, dstate, mm, st)) != cudaSuccess) return note(e);
         }
-        {
-            StageScope sc(st, BDC_STAGE_SECULAR, (o.seed != BDC_SEED_PLAIN || harvest) ? 3 : 2, 0.0);
-            if ((e = launch_secular(dn, nn, dmats, dstate, mm, max_iter, o.seed, o.mlp, harvest, o.fp32_start,
-                                    st)) != cudaSuccess)
-                return note(e);
-        }
+        if ((e = launch_secular(dn, nn, dmats, dstate, mm, max_iter, o.seed, o.mlp, harvest, o.fp32_start, st)) !=
+            cudaSuccess)
+            return note(e);
+        if (o.checked &&
+            (e = launch_check_roots(dn, nn, dmats, dstate, mm, h + 1 == p.heights.size() && test_corrupt_root(), st)) !=
+                cudaSuccess)
+            return note(e);
         if (p.vals) {   // the survivors' first/last rows of V; no vectors, no products
             StageScope sc(st, BDC_STAGE_VECTORS, 1, 0.0);
             if ((e = launch_rows_update(dn, nn, dmats, dstate, mm, st)) != cudaSuccess) return note(e);
@@ -584,9 +726,8 @@ int run_plan(const Plan &p, const bdc_opts &o, char *work, std::vector<MatDesc> 
             // small merges use the FP64 products: the split path's fixed costs
             // (slicing, two kernels, TMEM set-up per tile) dominate there
             const bool mixed_here = (o.prec != BDC_FP64) && mm >= o.mixed_min;
-            const int gl = !mixed_here ? 1 : (o.prec == BDC_MIXED_EXACT && o.slices > 4) ? 4 : 3;
-            StageScope sc(st, BDC_STAGE_GEMM, gl, 0.0);
             if (!mixed_here) {
+                StageScope sc(st, BDC_STAGE_GEMM, 1, 0.0);
                 // rows of the four products: nl + 1 (tops), m - nl - 1, m + sqre - nl - 1
                 int rows = 1;
                 for (const NodeDesc &nd : p.heights[h])
@@ -605,13 +746,13 @@ int run_plan(const Plan &p, const bdc_opts &o, char *work, std::vector<MatDesc> 
                     for (int j = 0; j < 4; ++j) Nx[4 * k + j] = nd.m;
                 }
                 e = launch_gemm_mixed(dprobs, 4 * nn, Mx.data(), Nx.data(), mm + 9, o.prec,
-                                      o.slices > 0 ? o.slices : 6, work + p.off_mixed, p.mixed_bytes, st);
+                                      o.slices > 0 ? o.slices : 6, work + p.off_mixed, p.mixed_bytes, derr, st);
             }
 #endif
             if (e != cudaSuccess) return note(e);
         }
-        {
-            StageScope sc(st, BDC_STAGE_FINISH, 1, 0.0);
+        {   // node values and their order (O(m) per merge)
+            StageScope sc(st, BDC_STAGE_FINISH, 1, 24.0 * msum);
             if ((e = launch_merge_finish(dn, nn, dmats, dstate, mm, st)) != cudaSuccess) return note(e);
         }
     }
@@ -623,10 +764,10 @@ int run_plan(const Plan &p, const bdc_opts &o, char *work, std::vector<MatDesc> 
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return note(e);
     } else if (p.nmat > 0) {
-        // writes U, V^T (16 n^2 B); reads only the slots' row ranges of U, V
-        // (at most another 16 n^2 B, far less after deflation): the writes
-        // are the algorithmic bytes counted
-        StageScope sc(st, BDC_STAGE_FINAL, (p.nmat + 65534) / 65535, 16.0 * nsq);
+        // writes U, V^T (16 n^2 B; 8 n^2 with one side); reads only the slots'
+        // row ranges of U, V (at most as much again, far less after
+        // deflation): the writes are the algorithmic bytes counted
+        StageScope sc(st, BDC_STAGE_FINAL, (p.nmat + 65534) / 65535, (o.vectors ? 8.0 : 16.0) * nsq);
         const int tps = (p.nmax + 31) / 32;
         for (int m0 = 0; m0 < p.nmat; m0 += 65535) {
             const int nm = std::min(65535, p.nmat - m0);
@@ -647,9 +788,10 @@ int run_plan(const Plan &p, const bdc_opts &o, char *work, std::vector<MatDesc> 
             pc.host = nullptr;
         }
     }
+    if (o.checked && p.nmat > 0 && (e = launch_check_final(dmats, p.nmat, st)) != cudaSuccess) return note(e);
     // gather the per-matrix status words into the caller's d_info
     if (p.nmat > 0) {
-        k_info<<<(p.nmat + 255) / 256, 256, 0, st>>>(dmats, p.nmat, d_info_out);
+        k_info<<<(p.nmat + 255) / 256, 256, 0, st>>>(dmats, p.nmat, derr, d_info_out);
         if ((e = cudaGetLastError()) != cudaSuccess) return note(e);
     }
     return 0;
@@ -696,7 +838,8 @@ int check_opts(const bdc_opts &o) {
     if (o.seed == BDC_SEED_MLP && !o.mlp) return 1;
     if (o.leaf < 4 || o.leaf > 64) return 1;
     if (o.slices < 2 || o.slices > 7) return 1;
-    if (o.checked != 0 || o.fp32_start < 0 || o.fp32_start > 1) return 1;
+    if (o.checked < 0 || o.checked > 1 || o.fp32_start < 0 || o.fp32_start > 1) return 1;
+    if (o.vectors < 0 || o.vectors > 2) return 1;
     return 0;
 }
 
@@ -728,9 +871,13 @@ size_t bdc_svd_workspace(int n, const bdc_opts *o) {
 
 int bdc_svd_ex(int n, const double *d, const double *e, double *U, double *S, double *VT, int ldu, int ldvt,
                const bdc_opts *o, void *work, size_t lwork, int *d_info, bdc_stream_t stream) {
-    int a = check_args(n, d, e, U, S, VT, ldu, ldvt);
-    if (a) return a;
     const bdc_opts r = resolve(o, n);
+    // one side only: the other output is not written and may be NULL
+    double *const dummy = reinterpret_cast<double *>(16);
+    const bool noU = r.vectors == BDC_VEC_V, noV = r.vectors == BDC_VEC_U;
+    int a = check_args(n, d, e, noU ? dummy : U, S, noV ? dummy : VT, noU ? std::max(1, n) : ldu,
+                       noV ? std::max(1, n) : ldvt);
+    if (a) return a;
     if (check_opts(r)) return -9;
     if (!d_info) return -12;
     cudaStream_t st = (cudaStream_t)stream;
@@ -743,7 +890,8 @@ int bdc_svd_ex(int n, const double *d, const double *e, double *U, double *S, do
     std::vector<MatDesc> mats(1);
     mats[0].n = n; mats[0].d_in = d; mats[0].e_in = e;
     mats[0].Uo = U; mats[0].So = S; mats[0].VTo = VT; mats[0].ldu = ldu; mats[0].ldvt = ldvt;
-    return run_plan(p, r, w, mats, d_info, st);
+    CallerCapture cc(st);
+    return cc.finish(run_plan(p, r, w, mats, d_info, st));
 }
 
 int bdc_svd_harvest(int n, const double *d, const double *e, double *U, double *S, double *VT, int ldu, int ldvt,
@@ -766,7 +914,8 @@ int bdc_svd_harvest(int n, const double *d, const double *e, double *U, double *
     mats[0].n = n; mats[0].d_in = d; mats[0].e_in = e;
     mats[0].Uo = U; mats[0].So = S; mats[0].VTo = VT; mats[0].ldu = ldu; mats[0].ldvt = ldvt;
     mats[0].feat = feat; mats[0].targ = targ; mats[0].hcount = d_count; mats[0].hcap = cap;
-    return run_plan(p, r, w, mats, d_info, st);
+    CallerCapture cc(st);
+    return cc.finish(run_plan(p, r, w, mats, d_info, st));
 }
 
 int bdc_svd(int n, const double *d, const double *e, double *U, double *S, double *VT, int ldu, int ldvt,
@@ -807,7 +956,8 @@ int bdc_svd_values_ex(int n, const double *d, const double *e, double *S, const 
     if (n > 1 && !e) return -3;
     if (n > 0 && !S) return -4;
     bdc_opts r = resolve(o, n);
-    r.prec = BDC_FP64;   // no products
+    r.prec = BDC_FP64;   // no products, no vectors
+    r.vectors = BDC_VEC_BOTH;
     if (check_opts(r)) return -5;
     if (!d_info) return -8;
     cudaStream_t st = (cudaStream_t)stream;
@@ -819,7 +969,8 @@ int bdc_svd_values_ex(int n, const double *d, const double *e, double *S, const 
     if ((size_t)(w - (char *)work) + p.total - 256 > lwork) return -7;
     std::vector<MatDesc> mats(1);
     mats[0].n = n; mats[0].d_in = d; mats[0].e_in = e; mats[0].So = S;
-    return run_plan(p, r, w, mats, d_info, st);
+    CallerCapture cc(st);
+    return cc.finish(run_plan(p, r, w, mats, d_info, st));
 }
 
 int bdc_svd_values(int n, const double *d, const double *e, double *S, bdc_stream_t stream) {
@@ -871,6 +1022,21 @@ __global__ void k_fill_uniform(real_t *__restrict__ x, long long count, unsigned
     x[k] = (real_t)(0.5 + (double)(z >> 11) * 0x1.0p-53);
 }
 
+// graded harvest input: d_k = 10^(-8k/n) (0.5 + u_k), e_k = d_k / 2 (u_k as in
+// k_fill_uniform); d and e both have n entries (e's last is not read)
+__global__ void k_fill_graded(real_t *__restrict__ d, real_t *__restrict__ e, int n, unsigned long long seed) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    unsigned long long z = seed * 0x9E3779B97F4A7C15ull + (unsigned long long)k + 1;
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    const double v = exp10(-8.0 * (double)k / (double)n) * (0.5 + (double)(z >> 11) * 0x1.0p-53);
+    d[k] = (real_t)v;
+    e[k] = (real_t)(0.5 * v);
+}
+
 struct TuneResult {
     int leaf, mixed_min;
     double ms;
@@ -899,7 +1065,7 @@ int batched_setup(int batch, const int *h_n, const real_t *const *d, const real_
     int nmax = 0;
     for (int b = 0; b < batch; ++b) nmax = std::max(nmax, h_n[b]);
     r = resolve(o, nmax);
-    if (check_opts(r)) return -10;
+    if (check_opts(r) || r.vectors != BDC_VEC_BOTH) return -10;   // batches form both vector sets
     if (!d_info) return -13;
     p = make_plan(batch, h_n, r);
     if (!work) return -11;
@@ -1109,7 +1275,8 @@ int bdc_svd_batched(int batch, const int *h_n, const double *const *d, const dou
     std::vector<MatDesc> mats;
     if (int a = batched_setup(batch, h_n, d, e, U, S, VT, h_ldu, h_ldvt, o, work, lwork, d_info, p, r, w, mats))
         return a;
-    return run_plan(p, r, w, mats, d_info, (cudaStream_t)stream);
+    CallerCapture cc((cudaStream_t)stream);
+    return cc.finish(run_plan(p, r, w, mats, d_info, (cudaStream_t)stream));
 }
 
 int bdc_plan_create(bdc_plan *plan, int batch, const int *h_n, const double *const *d, const double *const *e,
@@ -1179,7 +1346,7 @@ int bdc_deflate(int m, const double *d, const double *z, double tol, int *keep, 
 
 size_t bdc_gemm_workspace(int M, int N, int K, int prec, int slices) {
     if (M < 0 || N < 0 || K < 0) return 0;
-    size_t b = align256(sizeof(GemmProb)) + 256;
+    size_t b = align256(sizeof(GemmProb)) + 256 + 256;
     if (prec != BDC_FP64)
         b += gemm_mixed_scratch(M, N, K, prec, slices > 0 ? slices : 6, (long long)((M + 127) / 128) * ((N + 127) / 128));
     return b;
@@ -1206,33 +1373,38 @@ int bdc_gemm(int M, int N, int K, const double *A, int lda, const double *B, int
     cudaStream_t st = (cudaStream_t)stream;
     char *w = (char *)(((uintptr_t)work + 255) & ~(uintptr_t)255);
     GemmProb pr{A, B, C, lda, ldb, ldc, M, N, K};
-    // the problem descriptor lives in the workspace; copied from a pinned slot
+    CallerCapture cc(st);
+    // the problem descriptor lives in the workspace; copied from a pinned slot:
+    // the capture's own block when the stream is being captured
     static std::mutex mu;
     static GemmProb *hp = nullptr;
-    {
+    GemmProb *hs = (GemmProb *)plan_pinned_alloc(sizeof(GemmProb));
+    if (!hs) {
         std::lock_guard<std::mutex> lk(mu);
         if (!hp) { if (int r = note(cudaMallocHost(&hp, sizeof(GemmProb) * 1024))) return r; }
-    }
-    // a fresh pinned slot per call (ring of 1024), synchronised on wrap-around
-    static int slot = 0;
-    GemmProb *hs;
-    {
-        std::lock_guard<std::mutex> lk(mu);
+        // a fresh pinned slot per call (ring of 1024), synchronised on wrap-around
+        static int slot = 0;
         if (slot == 1024) { cudaStreamSynchronize(st); slot = 0; }
         hs = hp + slot++;
     }
     *hs = pr;
-    if (int r = note(cudaMemcpyAsync(w, hs, sizeof(GemmProb), cudaMemcpyHostToDevice, st))) return r;
+    if (int r = note(cudaMemcpyAsync(w, hs, sizeof(GemmProb), cudaMemcpyHostToDevice, st))) return cc.finish(r);
     cudaError_t e;
+    // error word of the product kernels' bounded waits (not reported: this
+    // entry point has no device status word; C is unspecified after a timeout)
+    int *err = (int *)(w + align256(sizeof(GemmProb)));
+    char *scr = w + align256(sizeof(GemmProb)) + 256;
     if (K == 0) {
         e = cudaMemset2DAsync(C, sizeof(double) * ldc, 0, sizeof(double) * M, N, st);
     } else if (prec == BDC_FP64) {
         e = launch_gemm64((const GemmProb *)w, 1, M, N, st);
     } else {
-        e = launch_gemm_mixed((const GemmProb *)w, 1, &M, &N, K, prec, slices, w + align256(sizeof(GemmProb)),
-                              lwork - (size_t)(w - (char *)work) - align256(sizeof(GemmProb)), st);
+        e = cudaMemsetAsync(err, 0, sizeof(int), st);
+        if (e == cudaSuccess)
+            e = launch_gemm_mixed((const GemmProb *)w, 1, &M, &N, K, prec, slices, scr,
+                                  lwork - (size_t)(scr - (char *)work), err, st);
     }
-    return note(e);
+    return cc.finish(note(e));
 }
 
 int bdc_profile_begin(int on) {
@@ -1243,7 +1415,14 @@ int bdc_profile_begin(int on) {
         if (pc.host) cudaFreeHost(pc.host);
     g_prof.calls.clear();
     g_sec_roots = g_sec_iters = 0;
+    for (double &x : g_fp64) x = 0.0;
     g_prof.on = on != 0;
+    return 0;
+}
+
+int bdc_profile_fp64(double *fp64) {
+    if (fp64)
+        for (int k = 0; k < BDC_NSTAGES; ++k) fp64[k] = g_fp64[k];
     return 0;
 }
 
@@ -1272,6 +1451,12 @@ int bdc_profile_end(double *ms, long long *launches, double *work) {
         std::memcpy(hs.data(), pc.host, sizeof(NodeState) * pc.nnodes);
         cudaFreeHost(pc.host);
         pc.host = nullptr;
+        for (const NodeDesc &lf : pc.leaves) {
+            // each logged rotation: ~17 FP64 operations to form it and update d, e;
+            // replayed on the m (U) or m + sqre (V) rows of the leaf: 6 per row
+            const double rot = (double)hs[lf.id].iters;
+            g_fp64[BDC_STAGE_LEAF] += rot * (17.0 + (pc.vals ? 12.0 : 6.0 * (lf.m + 0.5 * lf.sqre)));
+        }
         for (const NodeDesc &nd : pc.merges) {
             const NodeState &ns = hs[nd.id];
             const double N = ns.N, Ktop = ns.P1 + 1 + ns.n2, Kbot = ns.Ktot - ns.P1;
@@ -1280,11 +1465,25 @@ int bdc_profile_end(double *ms, long long *launches, double *work) {
             // decision does); per node this is exact up to that granularity
             g_sec_roots += ns.N;
             g_sec_iters += (long long)ns.iters;
-            if (pc.vals) continue;
-            w[BDC_STAGE_GEMM] += 2.0 * N * (2.0 * top * Ktop + (botU + botV) * Kbot) *
-                                 (nd.pad >= pc.mixed_min ? pc.pairs : 1);
-            w[BDC_STAGE_VECTORS] += 16.0 * N * ns.Ktot;
-            w[BDC_STAGE_GATHER] += 0.0;
+            // secular: 1 + iters pole-sum evaluations per root, N terms each, ~9
+            // FP64 operations per term; Loewner: N - 1 factors per entry, ~10 each
+            g_fp64[BDC_STAGE_SECULAR] += 9.0 * N * (N + (double)ns.iters);
+            g_fp64[BDC_STAGE_LOWNER] += 10.0 * N * (N > 1 ? N - 1 : 0);
+            if (pc.vals) {
+                g_fp64[BDC_STAGE_VECTORS] += 9.0 * N * N;   // two rows of V: one quotient and three FMAs per entry
+                continue;
+            }
+            const bool split = nd.pad >= pc.mixed_min;
+            const double sides = pc.want_u ? 2.0 : 1.0;
+            const double aEl = pc.want_u ? (2.0 * top * Ktop + (botU + botV) * Kbot) : (top * Ktop + botV * Kbot);
+            w[BDC_STAGE_GEMM] += 2.0 * N * aEl * (split ? pc.pairs : 1);
+            if (split)   // FP64 operands read once, S BF16 slices written: A blocks (rows x K), B blocks (K x N)
+                w[BDC_STAGE_SLICE] += (8.0 + 2.0 * pc.slices) * (aEl + sides * N * (Ktop + Kbot));
+            w[BDC_STAGE_VECTORS] += 8.0 * sides * N * ns.Ktot;
+            g_fp64[BDC_STAGE_VECTORS] += (pc.want_u ? 15.0 : 10.0) * N * N;
+            // the N survivor columns of W~ (m rows) and Q~ (m + sqre rows) written
+            // in full, their child-block rows (about half) read
+            w[BDC_STAGE_GATHER] += 12.0 * N * ((pc.want_u ? nd.m : 0) + nd.m + nd.sqre);
         }
     }
     g_prof.calls.clear();
@@ -1346,6 +1545,105 @@ int bdc_mlp_predict(const float *params, const float *feat, int count, float *ou
     return note(launch_mlp_predict(params, feat, count, out, (cudaStream_t)stream));
 }
 
+int bdc_mlp_fit(float *params, const float *feat, const float *targ, int count, int steps, float lr, float huber,
+                unsigned long long seed, float *losses, bdc_stream_t stream) {
+    if (!params) return -1;
+    if (count <= 0 || !feat || !targ) return -2;
+    if (steps < 0) return -5;
+    if (!(lr > 0.f)) return -6;
+    if (!(huber == huber)) return -7;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int P = mlp_param_count();
+    const size_t gw = mlp_grad_workspace(count);
+    // Adam moments, gradient, the loss of each step, the gradient scratch
+    const size_t bytes = sizeof(float) * (3 * (size_t)P + 64) + align256(gw) + sizeof(float) * (size_t)(steps + 1);
+    char *scr = nullptr;
+    if (int r = note(cudaMallocAsync((void **)&scr, bytes + 512, st))) return r;
+    float *m = (float *)scr, *v = m + P, *g = v + P;
+    char *gwork = (char *)(((uintptr_t)(g + P + 64) + 255) & ~(uintptr_t)255);
+    float *lossbuf = (float *)(gwork + align256(gw));
+    int rc = note(cudaMemsetAsync(scr, 0, sizeof(float) * 2 * (size_t)P, st));
+    if (!rc) rc = note(launch_mlp_init(params, feat, count, seed, st));
+    // full-batch Adam, learning rate decaying linearly from lr to lr / 10
+    for (int k = 1; k <= steps && !rc; ++k) {
+        const float lr_k = lr * (1.0f - 0.9f * (float)(k - 1) / (float)(steps > 1 ? steps - 1 : 1));
+        rc = note(launch_mlp_grad(params, feat, targ, count, huber, g, lossbuf + (k - 1), (float *)gwork, st));
+        if (!rc) rc = note(launch_mlp_adam(params, g, m, v, k, lr_k, 0.9f, 0.999f, 1e-8f, st));
+    }
+    if (!rc && losses && steps > 0)
+        rc = note(cudaMemcpyAsync(losses, lossbuf, sizeof(float) * steps, cudaMemcpyDeviceToDevice, st));
+    cudaFreeAsync(scr, st);
+    return rc;
+}
+
+int bdc_mlp_train(const bdc_opts *o, const bdc_mlp_train_opts *t, float *params, float *losses, int *samples,
+                  const char *out_path, bdc_stream_t stream) {
+    if (!params) return -3;
+    bdc_mlp_train_opts c{};
+    if (t) c = *t;
+    if (c.n == 0) c.n = 8192;
+    if (c.steps == 0) c.steps = 1500;
+    if (c.lr == 0.f) c.lr = 3e-3f;
+    if (c.huber == 0.f) c.huber = 0.25f;
+    if (c.n < 16 || c.n > 65536 || c.steps < 0 || !(c.lr > 0.f)) return -2;
+    bdc_opts r = resolve(o, c.n);
+    r.prec = BDC_FP64;               // roots of FP64 solves
+    r.seed = BDC_SEED_PLAIN;
+    r.mlp = nullptr;
+    if (check_opts(r)) return -1;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = c.n;
+    const Plan p = make_plan(1, &n, r);
+    const int F = mlp_feature_count();
+    const int cap = 1 << 21;
+    const size_t nn = (size_t)n;
+    // inputs (d, e of both matrices), outputs of one solve, workspace, harvest
+    const size_t bytes = align256(sizeof(double) * 4 * nn) + align256(sizeof(double) * 2 * nn * nn) +
+                         align256(sizeof(double) * nn) + 256 + align256(p.total) +
+                         align256(sizeof(float) * (size_t)cap * (F + 1)) + 256;
+    char *buf = nullptr;
+    if (int rr = note(cudaMallocAsync((void **)&buf, bytes + 256, st))) return rr;
+    char *q = (char *)(((uintptr_t)buf + 255) & ~(uintptr_t)255);
+    auto take = [&](size_t b) { char *x = q; q += align256(b); return x; };
+    double *du = (double *)take(sizeof(double) * 4 * nn), *eu = du + nn, *dg = eu + nn, *eg = dg + nn;
+    double *Ub = (double *)take(sizeof(double) * 2 * nn * nn), *VTb = Ub + nn * nn;
+    double *Sb = (double *)take(sizeof(double) * nn);
+    int *info = (int *)take(256), *cnt = info + 4;
+    char *work = take(p.total);
+    float *feat = (float *)take(sizeof(float) * (size_t)cap * (F + 1)), *targ = feat + (size_t)cap * F;
+    int rc = note(cudaMemsetAsync(cnt, 0, sizeof(int), st));
+    const unsigned long long s0 = c.seed * 4ull;
+    if (!rc) {
+        k_fill_uniform<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(du, (long long)nn, s0 + 1);
+        k_fill_uniform<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(eu, (long long)nn, s0 + 2);
+        k_fill_graded<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(dg, eg, n, s0 + 3);
+        rc = note(cudaGetLastError());
+    }
+    for (int k = 0; k < 2 && !rc; ++k) {
+        const double *dd = k ? dg : du, *ee = k ? eg : eu;
+        rc = bdc_svd_harvest(n, dd, ee, Ub, Sb, VTb, n, n, &r, work, p.total, info, feat, targ, cap, cnt, stream);
+    }
+    int hcount = 0, hinfo = 0;
+    if (!rc) rc = note(cudaMemcpyAsync(&hcount, cnt, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (!rc) rc = note(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (!rc) rc = note(cudaStreamSynchronize(st));
+    if (!rc && hinfo != 0) rc = hinfo;
+    const int count = std::min(hcount, cap);
+    if (samples) *samples = count;
+    if (!rc && count <= 0) rc = BDC_ERR_INTERNAL;
+    if (!rc) rc = bdc_mlp_fit(params, feat, targ, count, c.steps, c.lr, c.huber, c.seed, losses, stream);
+    cudaFreeAsync(buf, st);
+    if (int r2 = note(cudaStreamSynchronize(st))) rc = rc ? rc : r2;
+    if (!rc && out_path) {   // raw little-endian FP32, param_count values
+        std::vector<float> h((size_t)mlp_param_count());
+        rc = note(cudaMemcpy(h.data(), params, sizeof(float) * h.size(), cudaMemcpyDeviceToHost));
+        FILE *f = rc ? nullptr : std::fopen(out_path, "wb");
+        if (!rc && (!f || std::fwrite(h.data(), sizeof(float), h.size(), f) != h.size())) rc = -6;
+        if (f) std::fclose(f);
+    }
+    return rc;
+}
+
 const char *bdc_last_error_string(void) {
     static thread_local char out[256];
     std::memcpy(out, g_last_err, sizeof(out));
@@ -1361,6 +1659,7 @@ const char *bdc_status_string(int code) {
         case BDC_ERR_TIMEOUT: return "a bounded device wait gave up";
         case BDC_ERR_NONFINITE: return "d or e holds NaN or Inf";
         case BDC_ERR_INTERNAL: return "internal error";
+        case BDC_ERR_CHECK: return "checked mode: an invariant of the solve was violated";
         default: return "illegal argument";
     }
 }
@@ -1391,7 +1690,8 @@ int bdc_svd_batched_f32(int batch, const int *h_n, const float *const *d, const 
     std::vector<MatDesc> mats;
     if (int a = batched_setup(batch, h_n, d, e, U, S, VT, h_ldu, h_ldvt, o, work, lwork, d_info, p, r, w, mats))
         return a;
-    return run_plan(p, r, w, mats, d_info, (cudaStream_t)stream);
+    CallerCapture cc((cudaStream_t)stream);
+    return cc.finish(run_plan(p, r, w, mats, d_info, (cudaStream_t)stream));
 }
 
 int bdc_plan_create_f32(bdc_plan *plan, int batch, const int *h_n, const float *const *d, const float *const *e,

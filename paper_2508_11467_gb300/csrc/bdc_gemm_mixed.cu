@@ -63,7 +63,7 @@ constexpr int TNX = 128;   // tile width along N of the MMA kernels
 constexpr int EPI_WARPS = 16;
 constexpr int THREADS = 32 * (2 + EPI_WARPS);
 constexpr int CPT = TN_MAX * 4 / EPI_WARPS;      // accumulator columns per epilogue thread (32)
-constexpr unsigned long long kWaitNs = 2000000000ull;   // bounded waits: 2 s
+constexpr unsigned long long kDrainNs = 2000000000ull;   // bounded drains of in-flight work: 2 s
 
 // ------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -93,14 +93,16 @@ __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// bounded wait; returns false (and flags err) after kWaitNs
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err, volatile int *abort_flag) {
+// bounded wait; returns false (and flags err) after wait_ns nanoseconds
+// (2 s unless the BDC_TEST_WAIT_NS hook shortens it)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err, volatile int *abort_flag,
+                                          unsigned long long wait_ns) {
     if (mbar_try(bar, parity)) return true;
     const unsigned long long t0 = gtimer();
     for (;;) {
         if (mbar_try(bar, parity)) return true;
         if (*abort_flag) return false;
-        if (gtimer() - t0 > kWaitNs) {
+        if (gtimer() - t0 > wait_ns) {
             atomicCAS(err, 0, 1);
             *abort_flag = 1;
             return false;
@@ -108,12 +110,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *e
     }
 }
 // bounded wait that ignores the abort flag: a role that stopped early still
-// lets its own asynchronous copies / MMAs land before the CTA exits
+// lets its own asynchronous copies / MMAs land before the CTA exits (always
+// the full 2 s: the test hook never shortens it)
 __device__ __forceinline__ void mbar_drain(uint64_t *bar, uint32_t parity) {
     if (mbar_try(bar, parity)) return;
     const unsigned long long t0 = gtimer();
     while (!mbar_try(bar, parity))
-        if (gtimer() - t0 > kWaitNs) return;
+        if (gtimer() - t0 > kDrainNs) return;
 }
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2,
                                             uint64_t *bar) {
@@ -259,7 +262,7 @@ __global__ void __launch_bounds__(256) k_slice_a(const GemmProb *__restrict__ pr
     const GemmProb pr = probs[p];
     const MixProb mx = mix[p];
     const int r0 = blockIdx.x * 32;
-    if (r0 >= mx.Mmax) return;
+    if (r0 >= mx.Mmax || pr.M <= 0 || pr.N <= 0) return;   // empty products have no tiles to feed
     const int tr = threadIdx.x & 31, tc = threadIdx.x >> 5;   // row within block, column lane
     const int row = r0 + tr;
     const bool rowok = row < pr.M;
@@ -332,7 +335,8 @@ __global__ void __launch_bounds__(256) k_slice_b(const GemmProb *__restrict__ pr
     const int p = p0 + blockIdx.y;
     const GemmProb pr = probs[p];
     const MixProb mx = mix[p];
-    if (c >= mx.Nmax || c >= (pr.N + TNX - 1) / TNX * TNX) return;   // whole lane groups leave together
+    // whole lane groups leave together; empty products have no tiles to feed
+    if (c >= mx.Nmax || c >= (pr.N + TNX - 1) / TNX * TNX || pr.M <= 0) return;
     const bool colok = c < pr.N;
     const int K = pr.K;
     const double *col = pr.B + (size_t)c * pr.ldb;
@@ -410,7 +414,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
                                                      const MixProb *__restrict__ mix, int nprobs,
                                                      const int *__restrict__ Ea, const int *__restrict__ Fb,
                                                      int *__restrict__ err, const int2 *__restrict__ tiles,
-                                                     const int *__restrict__ ntiles) {
+                                                     const int *__restrict__ ntiles, unsigned long long wait_ns,
+                                                     int stall) {
     constexpr int TILE = TM * TK * 2;                 // one 128 x 32 BF16 slice tile (A or B)
     constexpr int SL = stage_slices<S, MODE>();       // slices per operand in a stage
     constexpr int STAGE_BYTES = stage_bytes<S, MODE>();
@@ -475,10 +480,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
                 }
                 for (int s = 0; s < nk; ++s, ++G) {
                     const int buf = G % NSTAGE;
-                    if (G >= NSTAGE && !mbar_wait(&empty[buf], ((G / NSTAGE) - 1) & 1, err, abort_flag)) {
+                    if (G >= NSTAGE && !mbar_wait(&empty[buf], ((G / NSTAGE) - 1) & 1, err, abort_flag, wait_ns)) {
                         ok = false;
                         break;
                     }
+                    // test hook (BDC_TEST_STALL): CTA 0 never loads its first stage,
+                    // so the MMA issuer's wait on that stage's barrier must give up
+                    if (stall && blockIdx.x == 0 && G == 0) continue;
                     mbar_expect_tx(&full[buf], STAGE_BYTES);
                     const uint32_t dstA = smem_u32(smem + buf * STAGE_BYTES);
                     tma_load_3d(dstA, &tmA, s * TK, mx.a_row0 + m0, 0, &full[buf]);
@@ -486,7 +494,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
                 }
             }
             // copies still in flight (after an abort) land before the CTA exits
-            for (int g = (G > NSTAGE ? G - NSTAGE : 0); g < G; ++g) mbar_drain(&full[g % NSTAGE], (g / NSTAGE) & 1);
+            // (a stage skipped by the test hook has none)
+            for (int g = (G > NSTAGE ? G - NSTAGE : 0); g < G; ++g)
+                if (!(stall && blockIdx.x == 0 && g == 0)) mbar_drain(&full[g % NSTAGE], (g / NSTAGE) & 1);
         }
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer (one lane)
@@ -503,7 +513,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
             // a fresh chunk of an accumulator set waits until the epilogue has
             // drained the set's previous chunk
             auto wait_drained = [&](int set, int done) {
-                if (done > 0 && !mbar_wait(&accempty[set], (done - 1) & 1, err, abort_flag)) ok = false;
+                if (done > 0 && !mbar_wait(&accempty[set], (done - 1) & 1, err, abort_flag, wait_ns)) ok = false;
                 fence_after();
             };
             int Kn = probs[tiles[blockIdx.x].x].K;     // the next tile's K, loaded ahead
@@ -512,7 +522,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
                 if (ti + (int)gridDim.x < count) Kn = probs[tiles[ti + gridDim.x].x].K;
                 for (int s = 0; s < nk && ok; ++s, ++G) {
                     const int buf = G % NSTAGE;
-                    if (!mbar_wait(&full[buf], (G / NSTAGE) & 1, err, abort_flag)) { ok = false; break; }
+                    if (!mbar_wait(&full[buf], (G / NSTAGE) & 1, err, abort_flag, wait_ns)) { ok = false; break; }
                     fence_after();
                     // operand "addresses" below are (buffer, tile index, K step) handles
                     auto mma = [&](uint32_t col, int ia, int ib, int kk, uint32_t acc) {
@@ -538,7 +548,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
                     } else if constexpr (MODE == MODE_L) {
                         const int b = G & 1;                   // accumulator buffer of this stage
                         if (G >= 2) {
-                            if (!mbar_wait(&accempty[b], ((G >> 1) - 1) & 1, err, abort_flag)) { ok = false; break; }
+                            if (!mbar_wait(&accempty[b], ((G >> 1) - 1) & 1, err, abort_flag, wait_ns)) { ok = false; break; }
                             fence_after();
                         }
                         const uint32_t c4 = 256 * b, cl = 256 * b + 128;
@@ -647,7 +657,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
                 int tA = 0, tB = 0;                    // this tile's drains
                 for (int s = 0; s < nk && ok; ++s) {
                     if (((s & 1) == 0) || s == nk - 1) {                // set B: g1, g2
-                        if (!mbar_wait(&accfull[1], cB & 1, err, abort_flag)) { ok = false; break; }
+                        if (!mbar_wait(&accfull[1], cB & 1, err, abort_flag, wait_ns)) { ok = false; break; }
                         fence_after();
 #pragma unroll
                         for (int cb = 0; cb < CPT / 8; ++cb) {
@@ -668,7 +678,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
                         ++cB; ++tB;
                     }
                     if (((s & 1) == 1) || s == nk - 1) {                // set A: g0, g3
-                        if (!mbar_wait(&accfull[0], cA & 1, err, abort_flag)) { ok = false; break; }
+                        if (!mbar_wait(&accfull[0], cA & 1, err, abort_flag, wait_ns)) { ok = false; break; }
                         fence_after();
 #pragma unroll
                         for (int cb = 0; cb < CPT / 8; ++cb) {
@@ -740,7 +750,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
                 }
                 for (int s = 0; s < nk; ++s, ++GL) {
                     const int b = GL & 1;
-                    if (!mbar_wait(&accfull[b], (GL >> 1) & 1, err, abort_flag)) { ok = false; break; }
+                    if (!mbar_wait(&accfull[b], (GL >> 1) & 1, err, abort_flag, wait_ns)) { ok = false; break; }
                     fence_after();
 #pragma unroll
                     for (int cb = 0; cb < CPT / 8; ++cb) {
@@ -781,7 +791,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mma(const __grid_constant__ CUte
                     }
                 }
             } else {
-                if (!mbar_wait(&accfull[0], cA & 1, err, abort_flag)) ok = false;
+                if (!mbar_wait(&accfull[0], cA & 1, err, abort_flag, wait_ns)) ok = false;
                 if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }   // the shuffles need the whole warp
                 fence_after();
                 column_tables();
@@ -902,10 +912,10 @@ int sm_count() {
 
 template <int S, bool EXACT>
 cudaError_t run_mixed(const GemmProb *probs, int nprobs, const std::vector<MixProb> &hm, int rowsA, int colsB,
-                      int Kld, char *scratch, const Layout &L, cudaStream_t st) {
+                      int Kld, char *scratch, const Layout &L, int *err, cudaStream_t st) {
     __nv_bfloat16 *As = (__nv_bfloat16 *)(scratch + L.offA);
     __nv_bfloat16 *Bs = (__nv_bfloat16 *)(scratch + L.offB);
-    int *E = (int *)(scratch + L.offE), *F = (int *)(scratch + L.offF), *err = (int *)(scratch + L.offErr);
+    int *E = (int *)(scratch + L.offE), *F = (int *)(scratch + L.offF);
     MixProb *dmix = (MixProb *)(scratch + L.offMix);
     // largest row and column counts of one product (the slicing grids)
     int mrows = 1, ncols = 1, tiles = 0;
@@ -940,20 +950,23 @@ cudaError_t run_mixed(const GemmProb *probs, int nprobs, const std::vector<MixPr
     std::memcpy(hp, hm.data(), sizeof(MixProb) * nprobs);
     cudaError_t e = cudaMemcpyAsync(dmix, hp, sizeof(MixProb) * nprobs, cudaMemcpyHostToDevice, st);
 
-    int *ntiles = err + 4;
+    int *ntiles = (int *)(scratch + L.offErr);
     int2 *tlist = (int2 *)(scratch + L.offTiles);
-    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, 32, st);   // error word and tile count
+    if (e == cudaSuccess) e = cudaMemsetAsync(ntiles, 0, sizeof(int), st);   // tile count
     if (e != cudaSuccess) return e;
 
-    for (int p0 = 0; p0 < nprobs; p0 += 65535) {
-        const int np = std::min(nprobs - p0, 65535);
-        k_slice_a<S, EXACT><<<dim3((mrows + 31) / 32, np), 256, 0, st>>>(probs, dmix, p0, As, E, rowsA, Kld);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        if (ncols <= 128)
-            k_slice_b<S, EXACT, 8><<<dim3((ncols + 31) / 32, np), 256, 0, st>>>(probs, dmix, p0, Bs, F, colsB, Kld);
-        else
-            k_slice_b<S, EXACT, 32><<<dim3((ncols + 7) / 8, np), 256, 0, st>>>(probs, dmix, p0, Bs, F, colsB, Kld);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    {   // operand slicing
+        StageScope slice_scope(st, BDC_STAGE_SLICE, 2, 0.0);
+        for (int p0 = 0; p0 < nprobs; p0 += 65535) {
+            const int np = std::min(nprobs - p0, 65535);
+            k_slice_a<S, EXACT><<<dim3((mrows + 31) / 32, np), 256, 0, st>>>(probs, dmix, p0, As, E, rowsA, Kld);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            if (ncols <= 128)
+                k_slice_b<S, EXACT, 8><<<dim3((ncols + 31) / 32, np), 256, 0, st>>>(probs, dmix, p0, Bs, F, colsB, Kld);
+            else
+                k_slice_b<S, EXACT, 32><<<dim3((ncols + 7) / 8, np), 256, 0, st>>>(probs, dmix, p0, Bs, F, colsB, Kld);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
     }
 
     // tensor maps: boxes of all S slices, and (exact mode) of the first
@@ -982,16 +995,22 @@ cudaError_t run_mixed(const GemmProb *probs, int nprobs, const std::vector<MixPr
     });
     if (attr_err != cudaSuccess) return attr_err;
     if (tiles <= 0) return cudaSuccess;
+    StageScope mma_scope(st, BDC_STAGE_GEMM, (EXACT && S > 4) ? 3 : 2, 0.0);
+    const unsigned long long wait_ns = test_wait_ns();
+    const int stall = test_stall();
     k_tile_list<<<nprobs, 128, 0, st>>>(probs, dmix, tlist, ntiles);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int grid = tiles < sm_count() ? tiles : sm_count();   // persistent: one CTA per SM
     if constexpr (EXACT) {
-        k_mma<S, MODE_E><<<grid, THREADS, smemE, st>>>(mae, mbe, probs, dmix, nprobs, E, F, err, tlist, ntiles);
+        k_mma<S, MODE_E><<<grid, THREADS, smemE, st>>>(mae, mbe, probs, dmix, nprobs, E, F, err, tlist, ntiles,
+                                                       wait_ns, stall);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if constexpr (S > 4)
-            k_mma<S, MODE_L><<<grid, THREADS, smemL, st>>>(ma, mb, probs, dmix, nprobs, E, F, err, tlist, ntiles);
+            k_mma<S, MODE_L><<<grid, THREADS, smemL, st>>>(ma, mb, probs, dmix, nprobs, E, F, err, tlist, ntiles,
+                                                           wait_ns, 0);
     } else {
-        k_mma<S, MODE_X3><<<grid, THREADS, smemX, st>>>(ma, mb, probs, dmix, nprobs, E, F, err, tlist, ntiles);
+        k_mma<S, MODE_X3><<<grid, THREADS, smemX, st>>>(ma, mb, probs, dmix, nprobs, E, F, err, tlist, ntiles,
+                                                        wait_ns, stall);
     }
     return cudaGetLastError();
 }
@@ -1010,7 +1029,7 @@ size_t gemm_mixed_scratch(long long rows_total, long long cols_total, int kmax, 
 // probs: device problem table (M, N, K known on the device); hm: host layout
 cudaError_t launch_gemm_mixed_tab(const GemmProb *probs, int nprobs, const std::vector<MixProb> &hm, int rowsA,
                                   int colsB, int kmax, int prec, int slices, void *scratch, size_t scratch_bytes,
-                                  cudaStream_t st) {
+                                  int *err, cudaStream_t st) {
     if (nprobs <= 0) return cudaSuccess;
     const int S = (prec == BDC_MIXED_BF16X3) ? 2 : slices;
     const int Kld = (kmax + TK - 1) / TK * TK;
@@ -1020,19 +1039,19 @@ cudaError_t launch_gemm_mixed_tab(const GemmProb *probs, int nprobs, const std::
     if (L.total > scratch_bytes) return cudaErrorInvalidValue;
     char *sc = (char *)scratch;
     const int ra = rowsA + TM, cbn = colsB + TN_MAX;
-    if (prec == BDC_MIXED_BF16X3) return run_mixed<2, false>(probs, nprobs, hm, ra, cbn, Kld, sc, L, st);
+    if (prec == BDC_MIXED_BF16X3) return run_mixed<2, false>(probs, nprobs, hm, ra, cbn, Kld, sc, L, err, st);
     switch (S) {
-        case 4: return run_mixed<4, true>(probs, nprobs, hm, ra, cbn, Kld, sc, L, st);
-        case 5: return run_mixed<5, true>(probs, nprobs, hm, ra, cbn, Kld, sc, L, st);
-        case 6: return run_mixed<6, true>(probs, nprobs, hm, ra, cbn, Kld, sc, L, st);
-        case 7: return run_mixed<7, true>(probs, nprobs, hm, ra, cbn, Kld, sc, L, st);
+        case 4: return run_mixed<4, true>(probs, nprobs, hm, ra, cbn, Kld, sc, L, err, st);
+        case 5: return run_mixed<5, true>(probs, nprobs, hm, ra, cbn, Kld, sc, L, err, st);
+        case 6: return run_mixed<6, true>(probs, nprobs, hm, ra, cbn, Kld, sc, L, err, st);
+        case 7: return run_mixed<7, true>(probs, nprobs, hm, ra, cbn, Kld, sc, L, err, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
 // simple layout: products packed one after another (rows by M bound, columns by N bound)
 cudaError_t launch_gemm_mixed(const GemmProb *probs, int nprobs, const int *Mmax, const int *Nmax, int kmax, int prec,
-                              int slices, void *scratch, size_t scratch_bytes, cudaStream_t st) {
+                              int slices, void *scratch, size_t scratch_bytes, int *err, cudaStream_t st) {
     std::vector<MixProb> hm(nprobs);
     int rows = 0, cols = 0, tiles = 0;
     const int tn = TNX;
@@ -1045,12 +1064,8 @@ cudaError_t launch_gemm_mixed(const GemmProb *probs, int nprobs, const int *Mmax
         rows += m.Mmax; cols += m.Nmax;
         hm[p] = m;
     }
-    return launch_gemm_mixed_tab(probs, nprobs, hm, rows, cols, kmax, prec, slices, scratch, scratch_bytes, st);
+    return launch_gemm_mixed_tab(probs, nprobs, hm, rows, cols, kmax, prec, slices, scratch, scratch_bytes, err, st);
 }
 
-int gemm_mixed_error(void *scratch, long long rows_total, long long cols_total, int kmax, int prec, int slices) {
-    (void)scratch; (void)rows_total; (void)cols_total; (void)kmax; (void)prec; (void)slices;
-    return 0;
-}
 
 }  // namespace bdc

@@ -102,6 +102,10 @@ struct MatDesc {
     // singular values only: no U, V panels; each node keeps the first and
     // last rows of its V (the rows z is formed from), copy = depth % 2
     int vals;                // 1 = singular values only
+    int want_u;              // 0: no U side (right vectors only; every merge skips W~, U_M, the
+                             // U products and the U output)
+    int rev;                 // 1: the solve runs on J B^T J (d, e read reversed) and its right
+                             // vectors are written, rows reversed, as U (left vectors only)
     real_t *vf[2], *vl[2];   // [n + 1], node column c at r0 + c
     real_t *FK, *LK;         // K-indexed (from kbase): first/last-row entries of the survivors' columns
 };
@@ -223,7 +227,7 @@ cudaError_t launch_scale(const MatDesc *mats, int nmat, int nmax, cudaStream_t s
 // leaves: `log` = leaf_log_bytes(leafmax) per leaf (unused, may be null, when vals)
 size_t leaf_log_bytes(int leafmax);
 cudaError_t launch_leaves(const NodeDesc *leaves, int nleaves, const MatDesc *mats, int leafmax,
-                          int max_sweeps, int vals, void *log, cudaStream_t st);
+                          int max_sweeps, int vals, void *log, NodeState *state, cudaStream_t st);
 cudaError_t launch_merge_prep(const NodeDesc *nodes, int nnodes, const MatDesc *mats,
                               NodeState *state, GemmProb *probs, int mmax, int scans, cudaStream_t st);
 cudaError_t launch_merge_gather(const NodeDesc *nodes, int nnodes, const MatDesc *mats,
@@ -244,13 +248,48 @@ cudaError_t launch_merge_finish(const NodeDesc *nodes, int nnodes, const MatDesc
                                 const NodeState *state, int mmax, cudaStream_t st);
 cudaError_t launch_final(const MatDesc *mats, int nmat, int nmax, cudaStream_t st);
 
+// checked mode (bdc_check.cu): invariants after the deflation, after the
+// secular solve (corrupt: the BDC_TEST_CORRUPT_ROOT test hook) and at the end
+cudaError_t launch_check_prep(const NodeDesc *nodes, int nnodes, const MatDesc *mats, const NodeState *state,
+                              cudaStream_t st);
+cudaError_t launch_check_roots(const NodeDesc *nodes, int nnodes, const MatDesc *mats, const NodeState *state,
+                               int mmax, bool corrupt, cudaStream_t st);
+cudaError_t launch_check_final(const MatDesc *mats, int nmat, cudaStream_t st);
+
 // standalone step kernels (step entry points)
 cudaError_t launch_secular_single(int N, const double *d, const double *z, int *org, double *tau,
                                   double *omega, int max_iter, int *info, int seed_mode, const float *mlp,
                                   int *iters, cudaStream_t st);
-// pinned host memory owned by the plan being captured (nullptr when no plan
-// capture is active on this thread; callers then use their own buffers)
+// pinned host memory owned by the plan being captured, or by the graph of a
+// caller's stream capture (nullptr when no capture is active on this thread;
+// callers then use their own buffers)
 void *plan_pinned_alloc(size_t bytes);
+
+// Stage profiling (bdc_profile_begin / bdc_profile_end): while profiling is
+// on, a StageScope records a CUDA event pair around the launches made in its
+// lifetime and books them to stage kind `stage` (BDC_STAGE_*) with the
+// given launch count and algorithmic work; a no-op otherwise.
+struct StageScope {
+    cudaStream_t st;
+    int stage;
+    long long launches;
+    double work;
+    cudaEvent_t a = nullptr, b = nullptr;
+    StageScope(cudaStream_t s, int k, long long l, double w);
+    ~StageScope();
+};
+
+// Test hooks of the bounded device waits (read from the environment at each
+// launch; both off by default): BDC_TEST_WAIT_NS sets the wait limit of the
+// tensor-core product kernels in nanoseconds (default 2 s), and
+// BDC_TEST_STALL=1 makes CTA 0 of each product launch skip the load of its
+// first stage, so the barrier of that stage is never signalled and the wait
+// on it must give up, set the error word and unwind.
+unsigned long long test_wait_ns();
+int test_stall();
+// BDC_TEST_CORRUPT_ROOT=1 (checked mode only): root 0 of the top merge is
+// moved to the wrong side of its origin, which the root check must report
+bool test_corrupt_root();
 
 // MLP training (bdc_mlp.cu)
 size_t mlp_grad_workspace(int count);

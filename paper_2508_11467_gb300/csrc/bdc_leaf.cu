@@ -111,7 +111,7 @@ struct LaneVec {
 __global__ void __launch_bounds__(32) k_leaf_rotations(const NodeDesc *__restrict__ leaves,
                                                        const MatDesc *__restrict__ mats, int nleaves, int L,
                                                        int per_warp, int max_sweeps, int ccap,
-                                                       char *__restrict__ log) {
+                                                       char *__restrict__ log, NodeState *__restrict__ state) {
     extern __shared__ real_t sm[];
     const int lane = threadIdx.x;
     const int li = blockIdx.x * per_warp + lane;
@@ -284,6 +284,9 @@ __global__ void __launch_bounds__(32) k_leaf_rotations(const NodeDesc *__restric
         act(ACT_SWEEP, lo, hi);
     }
 
+    // rotations formed (the stage profiler's FP64 operation count); leaves
+    // have no other use for their node state
+    state[nd.id].iters = (unsigned long long)(nc / 2);
     if (!vals) {
         if (ovf) { hdr[0] = -1; return; }       // k_leaf_vectors iterates this leaf itself
         for (int i = 0; i < m; ++i) md.D[r0 + i] = dd[i];   // signed; sorted by k_leaf_vectors
@@ -618,7 +621,7 @@ int leaf_sm_count() {
 size_t leaf_log_bytes(int leafmax) { return log_stride(leafmax < 1 ? 1 : leafmax); }
 
 cudaError_t launch_leaves(const NodeDesc *leaves, int nleaves, const MatDesc *mats, int leafmax,
-                          int max_sweeps, int vals, void *log, cudaStream_t st) {
+                          int max_sweeps, int vals, void *log, NodeState *state, cudaStream_t st) {
     if (nleaves <= 0) return cudaSuccess;
     const int L = leafmax;
     // up to four warps per SM, one per sub-partition: the chain of one leaf
@@ -643,7 +646,7 @@ cudaError_t launch_leaves(const NodeDesc *leaves, int nleaves, const MatDesc *ma
         if (e != cudaSuccess) return e;
     }
     k_leaf_rotations<<<(nleaves + per_warp - 1) / per_warp, 32, smem1, st>>>(leaves, mats, nleaves, L, per_warp,
-                                                                             max_sweeps, ccap, (char *)log);
+                                                                             max_sweeps, ccap, (char *)log, state);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || vals) return e;
     const size_t smem2 = sizeof(real_t) * ((size_t)L * L + (size_t)(L + 1) * (L + 1) + 6 * (size_t)(L + 1)) +

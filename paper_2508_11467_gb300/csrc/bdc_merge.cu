@@ -486,11 +486,13 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
         const int Ktop = P1 + 1 + n2, Kbot = Ktot - P1;
         GemmProb *pr = probs + 4 * (size_t)blockIdx.x;
         // U: top rows 0..nl (incl. the coupling row), bottom rows nl+1..m-1;
-        // survivor i's column goes to the slot us[buf][r0 + i]
+        // survivor i's column goes to the slot us[buf][r0 + i] (empty
+        // products, M = N = 0, when the U side is not formed)
         const int *cu = md.us[nd.buf] + r0, *cv = md.vs[nd.buf] + r0;
-        pr[0] = GemmProb{md.Wt + wb, md.UM + wb, md.U + r0, m, Ktot, (int)ld, nl + 1, N, Ktop, cu};
+        const int uN = md.want_u ? N : 0;
+        pr[0] = GemmProb{md.Wt + wb, md.UM + wb, md.U + r0, m, Ktot, (int)ld, md.want_u ? nl + 1 : 0, uN, Ktop, cu};
         pr[1] = GemmProb{md.Wt + wb + (nl + 1) + (size_t)P1 * m, md.UM + wb + P1, md.U + r0 + nl + 1, m, Ktot,
-                         (int)ld, m - nl - 1, N, Kbot, cu};
+                         (int)ld, md.want_u ? m - nl - 1 : 0, uN, Kbot, cu};
         // V: top rows 0..nl (left child's columns), bottom rows nl+1..mc-1
         pr[2] = GemmProb{md.Qt + wb, md.VM + wb, md.V + r0, mc, Ktot, (int)ld, nl + 1, N, Ktop, cv};
         pr[3] = GemmProb{md.Qt + wb + (nl + 1) + (size_t)P1 * mc, md.VM + wb + P1, md.V + r0 + nl + 1, mc, Ktot,
@@ -585,16 +587,19 @@ __global__ void __launch_bounds__(256) k_merge_gather(const NodeDesc *__restrict
     real_t *W = md.Wt + wb, *Qm = md.Qt + wb;
     real_t *U = md.U + r0, *V = md.V + r0;           // row r0 of every slot
 
+    const bool wu = md.want_u != 0;              // the U side is formed (W~)
     if (p == 0) {
         const int a = ns.nzero;
         // padding columns of the K order (between the top block and index 0)
         for (int kp = ns.n1; kp < ns.P1; ++kp) {
-            for (int row = tid; row < m; row += nthr) W[(size_t)kp * m + row] = R(0);
+            if (wu)
+                for (int row = tid; row < m; row += nthr) W[(size_t)kp * m + row] = R(0);
             for (int row = tid; row < mc; row += nthr) Qm[(size_t)kp * mc + row] = R(0);
         }
         // U: the d_0 column is the unit vector; columns deflated against d_0
         // keep their U columns (the rotation is one-sided)
-        for (int row = tid; row < m; row += nthr) W[(size_t)ns.P1 * m + row] = cs.u(0, row);
+        if (wu)
+            for (int row = tid; row < m; row += nthr) W[(size_t)ns.P1 * m + row] = cs.u(0, row);
         // V: the d_0 column absorbs them one by one, in place
         const int g1 = cs.q1slot(), g2 = sqre ? cs.q2slot() : 0;
         for (int row = tid; row < mc; row += nthr) {
@@ -626,7 +631,7 @@ __global__ void __launch_bounds__(256) k_merge_gather(const NodeDesc *__restrict
     if (code == ROLE_CHAIN) {                          // chain start: walk to its end
         const int k0 = md.sidx[r0 + p];
         // every member but a surviving last one is rotated in its own slot
-        for (int row = tid; row < m; row += nthr) {
+        for (int row = tid; row < (wu ? m : 0); row += nthr) {
             real_t y = cs.u(src[p], row);
             int prev = p;
             for (int k = k0 + 1; k < m; ++k) {
@@ -659,13 +664,13 @@ __global__ void __launch_bounds__(256) k_merge_gather(const NodeDesc *__restrict
             int prev = p;
             for (int k = k0 + 1; k < m; ++k) {
                 const int q = slist[k];
-                md.ulo[cs.uslot(src[prev])] = r0; md.uhi[cs.uslot(src[prev])] = r0 + m;
+                if (wu) { md.ulo[cs.uslot(src[prev])] = r0; md.uhi[cs.uslot(src[prev])] = r0 + m; }
                 md.vlo[cs.vslot(src[prev])] = r0; md.vhi[cs.vslot(src[prev])] = r0 + mc;
                 prev = q;
                 if ((md.role[r0 + q] & 15) == ROLE_KEEP) break;
             }
             if (dest[prev] < 0) {
-                md.ulo[cs.uslot(src[prev])] = r0; md.uhi[cs.uslot(src[prev])] = r0 + m;
+                if (wu) { md.ulo[cs.uslot(src[prev])] = r0; md.uhi[cs.uslot(src[prev])] = r0 + m; }
                 md.vlo[cs.vslot(src[prev])] = r0; md.vhi[cs.vslot(src[prev])] = r0 + mc;
             }
         }
@@ -673,8 +678,12 @@ __global__ void __launch_bounds__(256) k_merge_gather(const NodeDesc *__restrict
     }
     // a deflated column keeps its slot; a survivor is copied into W~ / Q~
     if (dest[p] < 0) return;
-    const int c = src[p], gu = cs.uslot(c), gv = cs.vslot(c);
-    copy_slot(W + (size_t)dest[p] * m, md.U + (size_t)gu * ld + r0, m, md.ulo[gu] - r0, md.uhi[gu] - r0, tid, nthr);
+    const int c = src[p], gv = cs.vslot(c);
+    if (wu) {
+        const int gu = cs.uslot(c);
+        copy_slot(W + (size_t)dest[p] * m, md.U + (size_t)gu * ld + r0, m, md.ulo[gu] - r0, md.uhi[gu] - r0, tid,
+                  nthr);
+    }
     copy_slot(Qm + (size_t)dest[p] * mc, md.V + (size_t)gv * ld + r0, mc, md.vlo[gv] - r0, md.vhi[gv] - r0, tid,
               nthr);
 }
@@ -908,7 +917,9 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocDoubles
                                                                   kNoAllocInts * sizeof(int)];
 
 // device address of g_noalloc_scratch, looked up once per device (the host
-// symbol is only a stand-in and must never be passed to a kernel)
+// symbol is only a stand-in and must never be passed to a kernel); kept for
+// the life of the process, so it is stale after cudaDeviceReset on that
+// device (documented as a limit of the entry point)
 constexpr int kMaxDevices = 64;
 void *g_noalloc_ptr[kMaxDevices] = {nullptr};
 std::mutex g_noalloc_mu;

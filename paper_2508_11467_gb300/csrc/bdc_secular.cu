@@ -739,7 +739,7 @@ template <int G, int T>
 __device__ __forceinline__ void vectors_group(const real_t *__restrict__ d, const real_t *__restrict__ zt,
                                               const int *__restrict__ kpos, int N, int n1, int P1, real_t dor,
                                               real_t tau, real_t *__restrict__ UMcol, real_t *__restrict__ VMcol,
-                                              int gl) {
+                                              int gl, bool wu) {
     const real_t wsum = dor + tau;   // w_i: d_j + w_i formed once per entry (a sum of positives)
     real_t vr[T];
     real_t sv = R(0.0), su = R(0.0);
@@ -759,14 +759,17 @@ __device__ __forceinline__ void vectors_group(const real_t *__restrict__ d, cons
     sv = group_sum<G>(sv);
     su = group_sum<G>(su);
     const real_t iv = R(1.0) / sqrt(sv), iu = R(1.0) / sqrt(su);
-    for (int p = n1 + gl; p < P1; p += G) { UMcol[p] = R(0.0); VMcol[p] = R(0.0); }
+    for (int p = n1 + gl; p < P1; p += G) {
+        if (wu) UMcol[p] = R(0.0);
+        VMcol[p] = R(0.0);
+    }
 #pragma unroll
     for (int t = 0; t < T; ++t) {
         const int j = gl + t * G;
         if (j < N) {
             const int kp = kpos[j];
             VMcol[kp] = vr[t] * iv;
-            UMcol[kp] = ((j == 0) ? -R(1.0) : d[j] * vr[t]) * iu;
+            if (wu) UMcol[kp] = ((j == 0) ? -R(1.0) : d[j] * vr[t]) * iu;
         }
     }
 }
@@ -776,7 +779,7 @@ __device__ __forceinline__ void vectors_group(const real_t *__restrict__ d, cons
 __device__ __forceinline__ void vectors_warp_long(const real_t *__restrict__ d, const real_t *__restrict__ zt,
                                                   const int *__restrict__ kpos, int N, int n1, int P1, real_t dor,
                                                   real_t tau, real_t *__restrict__ UMcol,
-                                                  real_t *__restrict__ VMcol, int lane) {
+                                                  real_t *__restrict__ VMcol, int lane, bool wu) {
     const real_t wsum = dor + tau;   // w_i: d_j + w_i formed once per entry (a sum of positives)
     real_t sv = R(0.0), su = R(0.0);
     for (int j = lane; j < N; j += 32) {
@@ -789,13 +792,16 @@ __device__ __forceinline__ void vectors_warp_long(const real_t *__restrict__ d, 
     sv = warp_sum(sv);
     su = warp_sum(su);
     const real_t iv = R(1.0) / sqrt(sv), iu = R(1.0) / sqrt(su);
-    for (int p = n1 + lane; p < P1; p += 32) { UMcol[p] = R(0.0); VMcol[p] = R(0.0); }
+    for (int p = n1 + lane; p < P1; p += 32) {
+        if (wu) UMcol[p] = R(0.0);
+        VMcol[p] = R(0.0);
+    }
     for (int j = lane; j < N; j += 32) {
         const real_t dj = d[j];
         const real_t v = quot(zt[j], ((dj - dor) - tau) * (dj + wsum));
         const int kp = kpos[j];
         VMcol[kp] = v * iv;
-        UMcol[kp] = ((j == 0) ? -R(1.0) : dj * v) * iu;
+        if (wu) UMcol[kp] = ((j == 0) ? -R(1.0) : dj * v) * iu;
     }
 }
 
@@ -820,13 +826,14 @@ __global__ void __launch_bounds__(256) k_vectors_warp(const NodeDesc *__restrict
     real_t *UMcol = md.UM + wb + (size_t)i * Ktot, *VMcol = md.VM + wb + (size_t)i * Ktot;
     // the register cache holds 16 entries per lane below G = 32 (group_size
     // keeps N <= 16 G there)
+    const bool wu = md.want_u != 0;
     switch (G) {
-    case 4: vectors_group<4, 16>(d, zt, kpos, N, ns.n1, ns.P1, dor, tau, UMcol, VMcol, gl); break;
-    case 8: vectors_group<8, 16>(d, zt, kpos, N, ns.n1, ns.P1, dor, tau, UMcol, VMcol, gl); break;
-    case 16: vectors_group<16, 16>(d, zt, kpos, N, ns.n1, ns.P1, dor, tau, UMcol, VMcol, gl); break;
+    case 4: vectors_group<4, 16>(d, zt, kpos, N, ns.n1, ns.P1, dor, tau, UMcol, VMcol, gl, wu); break;
+    case 8: vectors_group<8, 16>(d, zt, kpos, N, ns.n1, ns.P1, dor, tau, UMcol, VMcol, gl, wu); break;
+    case 16: vectors_group<16, 16>(d, zt, kpos, N, ns.n1, ns.P1, dor, tau, UMcol, VMcol, gl, wu); break;
     default:
-        if (N <= 32 * 32) vectors_group<32, 32>(d, zt, kpos, N, ns.n1, ns.P1, dor, tau, UMcol, VMcol, gl);
-        else vectors_warp_long(d, zt, kpos, N, ns.n1, ns.P1, dor, tau, UMcol, VMcol, gl);
+        if (N <= 32 * 32) vectors_group<32, 32>(d, zt, kpos, N, ns.n1, ns.P1, dor, tau, UMcol, VMcol, gl, wu);
+        else vectors_warp_long(d, zt, kpos, N, ns.n1, ns.P1, dor, tau, UMcol, VMcol, gl, wu);
         break;
     }
 }
@@ -905,6 +912,9 @@ cudaError_t launch_secular(const NodeDesc *nodes, int nnodes, const MatDesc *mat
 #endif
     if (nnodes <= 0) return cudaSuccess;
     const long long roots = (long long)nnodes * mmax;
+    cudaError_t e = cudaSuccess;
+    {
+    StageScope sc(st, BDC_STAGE_SECULAR, (seed_mode != BDC_SEED_PLAIN || harvest) ? 2 : 1, 0.0);
 #ifdef BDC_FP32
     if (seed_mode != BDC_SEED_PLAIN || harvest) return cudaErrorInvalidValue;   // starts: FP64 only
     (void)mlp;
@@ -914,14 +924,16 @@ cudaError_t launch_secular(const NodeDesc *nodes, int nnodes, const MatDesc *mat
         if (smem > 48 * 1024) return cudaErrorInvalidValue;
         k_root_start<<<(unsigned)((roots + 127) / 128), 128, smem, st>>>(nodes, mats, state, mmax, nnodes,
                                                                           seed_mode, mlp);
-        cudaError_t e = cudaGetLastError();
+        e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
 #endif
     k_secular<<<(unsigned)((roots + 7) / 8), 256, 0, st>>>(nodes, mats, state, mmax, max_iter, nnodes,
                                                            seed_mode, fp32_start);
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    }
+    StageScope sc(st, BDC_STAGE_LOWNER, 1, 0.0);
     k_lowner<<<(unsigned)((roots + 7) / 8), 256, 0, st>>>(nodes, mats, state, mmax, nnodes);
     return cudaGetLastError();
 }

@@ -102,8 +102,43 @@ def test_plan_graph_equals_direct_call_and_replays(bdc):
     plan.close()
 
 
+def _residual_gpu(d, e, S, U, VT):
+    d = torch.as_tensor(d, device="cuda", dtype=torch.float64)
+    e = torch.as_tensor(e, device="cuda", dtype=torch.float64)
+    U, VT, S = U.double(), VT.double(), S.double()
+    V = VT.t()
+    BV = d[:, None] * V
+    BV[:-1] += e[:, None] * V[1:]
+    return float(torch.linalg.norm(BV - U * S[None, :]) / torch.sqrt((d * d).sum() + (e * e).sum()))
+
+
+def _check_batch(mats, plan, tol_scale, rounded=False):
+    """Every matrix's singular values against the oracle (sigma-only QR of
+    each matrix); residual and orthogonality of 256 matrices spread over the
+    sizes (cuBLAS checkers on the device)."""
+    if rounded:   # FP32: the oracle of the FP32-rounded input
+        mats = [(d.astype(np.float32).astype(np.float64), e.astype(np.float32).astype(np.float64)) for d, e in mats]
+    refs = oracle.sigma_only_many(mats)
+    ns = np.array([len(d) for d, _ in mats])
+    worst = 0.0
+    for b, (d, e) in enumerate(mats):
+        s = plan.result(b)[0].double().cpu().numpy()
+        assert np.all(np.diff(s) <= 0) and np.all(s >= 0), b
+        err = check.sigma_rel_err(s, refs[b])
+        assert err <= tol_scale * ns[b], (b, ns[b], err)
+        worst = max(worst, err / ns[b])
+    order = np.argsort(ns)
+    for b in order[np.linspace(0, len(ns) - 1, 256).astype(int)]:
+        S, U, VT = plan.result(int(b))
+        tol = tol_scale * ns[b]
+        assert _residual_gpu(*mats[b], S, U, VT) <= tol, b
+        assert _orth(U.double()) <= tol and _orth(VT.double().t()) <= tol, b
+    print(f"worst sigma error / n over {len(mats)} matrices: {worst:.2e}")
+
+
 def test_config4_2048_matrices(bdc):
-    """2048 bidiagonals, n log-uniform in [32, 1024], one graph launch."""
+    """2048 bidiagonals, n log-uniform in [32, 1024], one graph launch: every
+    matrix's singular values against the oracle."""
     mats = inputs.batch(2048, seed=3)
     ns, D, E = _flat(mats)
     assert ns.min() >= 32 and ns.max() <= 1024
@@ -111,11 +146,19 @@ def test_config4_2048_matrices(bdc):
     plan.launch()
     torch.cuda.synchronize()
     assert int(plan.info.abs().max()) == 0
-    order = np.argsort(ns)
-    pick = sorted(set(order[np.linspace(0, len(ns) - 1, 16).astype(int)].tolist() + [int(order[-1])]))
-    for b in pick:
-        S, U, VT = plan.result(b)
-        _check(*mats[b], S, U, VT)
+    _check_batch(mats, plan, 1e-13)
+    plan.close()
+
+
+def test_config4_2048_matrices_split_products(bdc):
+    """The same batch with the split-BF16 products (the benchmark's FP64 batch)."""
+    mats = inputs.batch(2048, seed=3)
+    ns, D, E = _flat(mats)
+    plan = bdc.BatchPlan(D, E, ns, prec="exact", mixed_min=64)
+    plan.launch()
+    torch.cuda.synchronize()
+    assert int(plan.info.abs().max()) == 0
+    _check_batch(mats, plan, 1e-13)
     plan.close()
 
 
@@ -205,10 +248,7 @@ def test_fp32_config4_2048_matrices(bdc):
     plan.launch()
     torch.cuda.synchronize()
     assert int(plan.info.abs().max()) == 0
-    order = np.argsort(ns)
-    pick = sorted(set(order[np.linspace(0, len(ns) - 1, 16).astype(int)].tolist() + [int(order[-1])]))
-    for b in pick:
-        _check32(*mats[b], *plan.result(b))
+    _check_batch(mats, plan, 1e-5, rounded=True)
     plan.close()
 
 

@@ -56,6 +56,21 @@ def test_noalloc_matches_allocating_entry_point_twice(bdc):
         assert torch.allclose(v1[gone], v2[gone], rtol=4 * EPS, atol=0)
 
 
+def test_noalloc_at_its_size_limit(bdc):
+    """m = BDC_DEFLATE_NOALLOC_MAX uses the whole fixed array."""
+    m = bdc.NOALLOC_MAX
+    d, z = _case(m, 3)
+    tol = merge.deflation_tol(d, 0.5, 0.5)
+    dc, zc = torch.from_numpy(d).cuda(), torch.from_numpy(z).cuda()
+    k1, z1, v1 = bdc.deflate(dc, zc, tol)
+    k2, z2, v2 = bdc.deflate_noalloc(dc, zc, tol)
+    torch.cuda.synchronize()
+    assert torch.equal(k1, k2)
+    kept = k1.bool()
+    assert torch.allclose(z1[kept], z2[kept], rtol=4 * EPS, atol=0)
+    assert torch.allclose(v1[~kept], v2[~kept], rtol=4 * EPS, atol=0)
+
+
 def test_noalloc_rejects_sizes_above_its_limit(bdc):
     L = bdc.lib()
     p = ctypes.c_void_p(256)          # never dereferenced: the size check comes first
