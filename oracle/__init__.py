@@ -19,6 +19,9 @@ Contents
   in numpy FP64.
 * ``check`` -- accuracy metrics (relative sigma error, orthogonality, the
   paper's E_sigma and E_svd of Sec. 5.1).
+* ``dense_svd`` -- the dense front and back end of Sec. 4.1 and 4.3 written
+  unblocked: Householder reflectors, bidiagonalization, QR, the explicit
+  Q1, P1, Q and the whole SVD pipeline (numpy FP64).
 """
 from __future__ import annotations
 
