@@ -60,10 +60,19 @@ __device__ __forceinline__ T group_prod(T v) {
 }
 // lanes per group for a merge with N survivors: about 16 poles per lane
 // (at most 16 below G = 32: the vector kernel caches 16 entries per lane)
-__device__ __forceinline__ int group_size(int N) {
+__host__ __device__ __forceinline__ int group_size(int N) {
     return N <= 64 ? 4 : N <= 128 ? 8 : N <= 256 ? 16 : 32;
 }
 static_assert(64 <= 4 * 16 && 128 <= 8 * 16 && 256 <= 16 * 16, "group_size must keep N <= 16 G below G = 32");
+// Warps per node of the lane-group kernels for merges of order <= mmax: a
+// warp serves 32 / G roots (columns), and G = group_size(N) <= group_size(mmax)
+// for the device-side survivor count N <= mmax, so ceil(mmax / (32 / G(mmax)))
+// warps cover every root of every node; launching mmax warps per node left
+// most warps of the small merges with nothing to do.
+__host__ __device__ __forceinline__ int group_warps(int mmax) {
+    const int per = 32 / group_size(mmax);
+    return (mmax + per - 1) / per;
+}
 
 struct Sums {
     real_t psi, dpsi, phi, dphi;
@@ -523,10 +532,10 @@ __device__ __forceinline__ void secular_group(const NodeDesc &nd, const MatDesc 
 // G = group_size(N) from the node's survivor count, known only here.
 __global__ void __launch_bounds__(256, 2) k_secular(const NodeDesc *__restrict__ nodes,
                                                  const MatDesc *__restrict__ mats,
-                                                 NodeState *__restrict__ state, int mmax,
+                                                 NodeState *__restrict__ state, int wpn,
                                                  int max_iter, int nnodes, int seed_mode, int fp32_start) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    const int node = warp / mmax, w = warp % mmax;
+    const int node = warp / wpn, w = warp % wpn;
     if (node >= nnodes) return;
     const NodeDesc nd = nodes[node];
     const NodeState ns = state[nd.id];
@@ -651,9 +660,9 @@ __device__ __forceinline__ real_t lowner_one(const real_t *__restrict__ d, const
 
 __global__ void __launch_bounds__(256) k_lowner(const NodeDesc *__restrict__ nodes,
                                                 const MatDesc *__restrict__ mats,
-                                                const NodeState *__restrict__ state, int mmax, int nnodes) {
+                                                const NodeState *__restrict__ state, int wpn, int nnodes) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    const int node = warp / mmax, w = warp % mmax;
+    const int node = warp / wpn, w = warp % wpn;
     if (node >= nnodes) return;
     const NodeDesc nd = nodes[node];
     const NodeState ns = state[nd.id];
@@ -807,10 +816,10 @@ __device__ __forceinline__ void vectors_warp_long(const real_t *__restrict__ d, 
 
 __global__ void __launch_bounds__(256) k_vectors_warp(const NodeDesc *__restrict__ nodes,
                                                       const MatDesc *__restrict__ mats,
-                                                      const NodeState *__restrict__ state, int mmax,
+                                                      const NodeState *__restrict__ state, int wpn,
                                                       int nnodes) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    const int node = warp / mmax, w = warp % mmax;
+    const int node = warp / wpn, w = warp % wpn;
     if (node >= nnodes) return;
     const NodeDesc nd = nodes[node];
     const NodeState ns = state[nd.id];
@@ -868,9 +877,9 @@ __device__ __forceinline__ void rows_group(const real_t *__restrict__ d, const r
 
 __global__ void __launch_bounds__(256) k_rows_update(const NodeDesc *__restrict__ nodes,
                                                      const MatDesc *__restrict__ mats,
-                                                     const NodeState *__restrict__ state, int mmax, int nnodes) {
+                                                     const NodeState *__restrict__ state, int wpn, int nnodes) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    const int node = warp / mmax, w = warp % mmax;
+    const int node = warp / wpn, w = warp % wpn;
     if (node >= nnodes) return;
     const NodeDesc nd = nodes[node];
     const NodeState ns = state[nd.id];
@@ -912,6 +921,7 @@ cudaError_t launch_secular(const NodeDesc *nodes, int nnodes, const MatDesc *mat
 #endif
     if (nnodes <= 0) return cudaSuccess;
     const long long roots = (long long)nnodes * mmax;
+    const long long gwarps = (long long)nnodes * group_warps(mmax);
     cudaError_t e = cudaSuccess;
     {
     StageScope sc(st, BDC_STAGE_SECULAR, (seed_mode != BDC_SEED_PLAIN || harvest) ? 2 : 1, 0.0);
@@ -928,29 +938,29 @@ cudaError_t launch_secular(const NodeDesc *nodes, int nnodes, const MatDesc *mat
         if (e != cudaSuccess) return e;
     }
 #endif
-    k_secular<<<(unsigned)((roots + 7) / 8), 256, 0, st>>>(nodes, mats, state, mmax, max_iter, nnodes,
-                                                           seed_mode, fp32_start);
+    k_secular<<<(unsigned)((gwarps + 7) / 8), 256, 0, st>>>(nodes, mats, state, group_warps(mmax), max_iter,
+                                                            nnodes, seed_mode, fp32_start);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     }
     StageScope sc(st, BDC_STAGE_LOWNER, 1, 0.0);
-    k_lowner<<<(unsigned)((roots + 7) / 8), 256, 0, st>>>(nodes, mats, state, mmax, nnodes);
+    k_lowner<<<(unsigned)((gwarps + 7) / 8), 256, 0, st>>>(nodes, mats, state, group_warps(mmax), nnodes);
     return cudaGetLastError();
 }
 
 cudaError_t launch_vectors(const NodeDesc *nodes, int nnodes, const MatDesc *mats, const NodeState *state,
                            int mmax, cudaStream_t st) {
     if (nnodes <= 0) return cudaSuccess;
-    const long long warps = (long long)nnodes * mmax;
-    k_vectors_warp<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(nodes, mats, state, mmax, nnodes);
+    const long long warps = (long long)nnodes * group_warps(mmax);
+    k_vectors_warp<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(nodes, mats, state, group_warps(mmax), nnodes);
     return cudaGetLastError();
 }
 
 cudaError_t launch_rows_update(const NodeDesc *nodes, int nnodes, const MatDesc *mats, const NodeState *state,
                                int mmax, cudaStream_t st) {
     if (nnodes <= 0) return cudaSuccess;
-    const long long warps = (long long)nnodes * mmax;
-    k_rows_update<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(nodes, mats, state, mmax, nnodes);
+    const long long warps = (long long)nnodes * group_warps(mmax);
+    k_rows_update<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(nodes, mats, state, group_warps(mmax), nnodes);
     return cudaGetLastError();
 }
 
