@@ -75,6 +75,7 @@ def parse():
     ap.add_argument("--no-mlp", action="store_true", help="skip training the root-start MLP (and its timing)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-product comparison")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched keys of the headline line")
+    ap.add_argument("--no-dense", action="store_true", help="skip the dense-SVD keys of the headline line")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true")
@@ -371,6 +372,108 @@ def _oracle_batch_job(args):
     return 0
 
 
+def dense_run(steps, warmup):
+    """The dense front and back end (Sec. 4.1, 4.3): bidiagonalization of a
+    square n = 4096 matrix, and the whole SVD of it and of the paper's
+    tall-and-skinny shape m = 20000, n = 1000 (SVD_geo, kappa = 1e4), each
+    timed with CUDA events over `steps` calls after `warmup`.  Roofline of the
+    reduction: (8/3) n^3 flops, half in products with the trailing matrix
+    (the BLAS2 part, FP64 ALU-bound on this part) and half in the merged
+    rank-(2b) updates (FP64 tensor cores)."""
+    import torch
+
+    from paper_2508_11467_gb300 import bdc, inputs
+
+    out = {}
+    clk = 2070e6
+    alu = FP64_ALU_OPS_PER_CLK_SM * SMS * clk * 2 / 1e12          # TFLOP/s (FMA = 2)
+    dmma = 2 * FP64_DMMA_MAC_PER_CLK_SM * SMS * clk / 1e12
+    for name, (m, n, kind) in {"square_n4096": (4096, 4096, "gauss"), "ts_m20000_n1000": (20000, 1000, "geo")}.items():
+        if kind == "gauss":
+            A0 = torch.randn(m, n, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(7))
+        else:
+            Q, sg, V = inputs.dense(kind, m, n, 1e4, 0)
+            A0 = (torch.from_numpy(Q).cuda() * torch.from_numpy(sg).cuda()[None, :]) @ torch.from_numpy(V).cuda().t()
+        A0 = A0.t().contiguous().t()
+        res = {}
+        # bidiagonalization alone
+        lw = int(bdc.lib().bdc_gebrd_workspace(m, n))
+        wk = torch.empty(lw, dtype=torch.uint8, device="cuda")
+        A = torch.empty_like(A0)
+        d = torch.empty(n, dtype=torch.float64, device="cuda")
+        e = torch.empty(n, dtype=torch.float64, device="cuda")
+        tq = torch.empty(n, dtype=torch.float64, device="cuda")
+        tp = torch.empty(n, dtype=torch.float64, device="cuda")
+        info = torch.zeros(1, dtype=torch.int32, device="cuda")
+        st = torch.cuda.current_stream()
+
+        def gebrd():
+            A.copy_(A0)
+            rc = bdc.lib().bdc_gebrd(m, n, bdc._ptr(A), m, bdc._ptr(d), bdc._ptr(e), bdc._ptr(tq), bdc._ptr(tp),
+                                     bdc._ptr(wk), wk.numel(), bdc._ptr(info), bdc._stream())
+            if rc != 0:
+                raise RuntimeError(f"bdc_gebrd {rc}")
+
+        def timeit(fn):
+            for _ in range(warmup):
+                fn()
+            torch.cuda.synchronize()
+            c0 = torch.cuda.Event(enable_timing=True)
+            c1 = torch.cuda.Event(enable_timing=True)
+            c0.record(st)
+            for _ in range(steps):
+                fn()
+            c1.record(st)
+            torch.cuda.synchronize()
+            return c0.elapsed_time(c1) / steps
+
+        ms_copy = timeit(lambda: A.copy_(A0))
+        ms_brd = timeit(gebrd) - ms_copy
+        flops = 4.0 * m * n * n - 4.0 * n ** 3 / 3.0
+        t_min = (flops / 2) / (alu * 1e12) + (flops / 2) / (dmma * 1e12)
+        res["gebrd_ms"] = ms_brd
+        res["gebrd_gflops"] = flops / (ms_brd * 1e-3) / 1e9
+        res["gebrd_roofline_frac"] = t_min / (ms_brd * 1e-3)
+        res["gebrd_status"] = int(info.item())
+        if m == n:
+            del wk
+            # the whole dense SVD (split-BF16 merge products in the bidiagonal solve)
+            o = bdc.make_opts("exact")
+            lw2 = int(bdc.lib().bdc_gesvd_workspace(m, n, __import__("ctypes").byref(o)))
+            wk2 = torch.empty(lw2, dtype=torch.uint8, device="cuda")
+            S, U, VT = (torch.empty(n, dtype=torch.float64, device="cuda"),
+                        torch.empty((n, m), dtype=torch.float64, device="cuda"),
+                        torch.empty((n, n), dtype=torch.float64, device="cuda"))
+        else:
+            o = bdc.make_opts("exact")
+            lw2 = int(bdc.lib().bdc_gesvd_workspace(m, n, __import__("ctypes").byref(o)))
+            wk2 = torch.empty(lw2, dtype=torch.uint8, device="cuda")
+            S, U, VT = (torch.empty(n, dtype=torch.float64, device="cuda"),
+                        torch.empty((n, m), dtype=torch.float64, device="cuda"),
+                        torch.empty((n, n), dtype=torch.float64, device="cuda"))
+        import ctypes as _ct
+
+        def gesvd():
+            A.copy_(A0)
+            rc = bdc.lib().bdc_gesvd(m, n, bdc._ptr(A), m, bdc._ptr(S), bdc._ptr(U), m, bdc._ptr(VT), n,
+                                     _ct.byref(o), bdc._ptr(wk2), wk2.numel(), bdc._ptr(info), bdc._stream())
+            if rc != 0:
+                raise RuntimeError(f"bdc_gesvd {rc}")
+
+        ms_svd = timeit(gesvd) - ms_copy
+        Uc, VTc = U.t(), VT.t()
+        rel = float(torch.linalg.norm(Uc * S[None, :] @ VTc - A0) / torch.linalg.norm(A0))
+        res.update({"gesvd_ms": ms_svd, "gesvd_status": int(info.item()), "gesvd_residual": rel,
+                    "shape": [m, n], "matrix": kind, "bdc_products": "split BF16 (7 slices)",
+                    "qr_first": m >= 1.6 * n})
+        out[name] = res
+        del A, A0, U, VT, wk2
+        torch.cuda.empty_cache()
+    out["roofline_note"] = (f"bidiagonalization lower bound: half its (4 m n^2 - 4 n^3 / 3) flops at the FP64 ALU "
+                            f"peak {alu:.3f} TFLOP/s, half at the FP64 mma.sync peak {dmma:.2f} TFLOP/s")
+    return out
+
+
 def run_batched(a):
     """--batched: the batch on its own JSON line (matrices/s)."""
     import torch
@@ -461,6 +564,16 @@ def stage_table(prof, steps, peaks, clock_mhz, fp64_products):
             row["bound"] = "fp64" if row["fp64_frac"] > row["hbm_frac"] else "hbm"
             if max(row["fp64_frac"], row["hbm_frac"]) < 0.05:
                 row["bound"] += " (latency: below 5% of both)"
+        if v.get("level_ms"):
+            # per merge height (0 = right above the leaves): ms and the fraction of
+            # the stage's peak (FP64 ALU for the FP64 stages, tensor for products)
+            row["level_ms"] = [x / steps for x in v["level_ms"]]
+            if k in ("secular", "lowner", "vectors"):
+                row["level_fp64_frac"] = [(w / (t * 1e-3)) / (fp64_alu * 1e9) if t > 0 else 0.0
+                                          for w, t in zip(v["level_work"], v["level_ms"])]
+            elif k == "gemm":
+                row["level_tensor_frac"] = [(w / (t * 1e-3)) / ((fp64_dmma if fp64_products else bf16) * 1e12)
+                                            if t > 0 else 0.0 for w, t in zip(v["level_work"], v["level_ms"])]
         out[k] = row
     if prof["secular"].get("roots"):
         out.setdefault("secular", {})["roots_per_step"] = prof["secular"]["roots"] / steps
@@ -746,6 +859,13 @@ def main():
                                            "mixed_min", "prec", "accuracy")}
         batch["workload"] = "2048 bidiagonals, n = floor(exp(U(ln 32, ln 1024))) seed 3, d,e~U(0.5,1.5); one graph"
 
+    dense = None
+    if not a.no_dense and world == 1:
+        if "work" in dir():
+            pass
+        torch.cuda.empty_cache()
+        dense = dense_run(max(1, min(a.steps, 3)), 1)
+
     cpu = None
     if not a.no_cpu_baseline and world == 1 and sigma_s is not None:
         cpu = cpu_baseline_measured(a.kind, n, a.seed, d_h, e_h, sigma_s)
@@ -778,6 +898,7 @@ def main():
         "stages_fp64": stages.get("fp64"),
         "root_start": root_start,
         "batched": batch,
+        "dense": dense,
         "gpu_launches": launches * a.steps,
         "gflops_model_8n3_3": 8.0 / 3.0 * n ** 3 / (ms * 1e-3) / 1e9,
         "gflops_model_note": "the paper's (8/3) n^3 flop model / time; deflation removes most of that work here",

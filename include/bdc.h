@@ -389,6 +389,61 @@ typedef struct {
 int bdc_mlp_train(const bdc_opts *o, const bdc_mlp_train_opts *t, float *params, float *losses, int *samples,
                   const char *out_path, bdc_stream_t stream);
 
+/* ---------------- dense front and back end (Sec. 4.1, 4.3) ---------------
+ * All matrices column-major FP64 device arrays owned by the caller; every
+ * call is asynchronous on `stream` unless stated; workspaces are device
+ * memory of the size the matching *_workspace function returns (any
+ * alignment).  Reflectors use LAPACK's sign convention and storage: a
+ * reflector I - tau y y^T maps x to beta e_1 with beta = -sign(x_1) ||x||,
+ * y_1 = 1 implicit.  Panels are b = 32 columns (rows) wide.  The panel
+ * kernels are cooperative launches whose grid barriers wait at most 2 s; a
+ * wait that gives up makes the call report BDC_ERR_TIMEOUT in *d_info.
+ * Returns: 0, -i for an illegal argument i, BDC_ERR_CUDA. */
+
+/* Bidiagonalization A = Q1 B P1^T (Sec. 4.1, Algorithm 1), m >= n: per
+ * panel the b column and row reflectors (H_i, G_i, Eq. gebrd-house) with the
+ * vectors y_i, x_i of Eqs. (bidiag-y-k3, bidiag-x-k3), then the merged
+ * rank-(2b) update A -= P Q^T of Eq. (bidiag-A-trail3) as one FP64
+ * tensor-core product.  On exit d[n] / e[n-1] hold B's diagonal and
+ * superdiagonal, A holds y_i below the diagonal of column i and u_i right of
+ * the superdiagonal of row i (u_i[i+1] = 1 implicit), tauq[n], taup[n] the
+ * scalars (taup[n-1] = 0).  *d_info (device): 0 or BDC_ERR_TIMEOUT. */
+size_t bdc_gebrd_workspace(int m, int n);
+int bdc_gebrd(int m, int n, double *A, int lda, double *d, double *e, double *tauq, double *taup, void *work,
+              size_t lwork, int *d_info, bdc_stream_t stream);
+
+/* Back-transformation with the reflectors of bdc_gebrd (Sec. 4.3, ormqr /
+ * ormlq): vect = 0: C (m x cdim, ldc >= m) := Q1 C; vect = 1: C (cdim x n,
+ * ldc >= cdim) := C P1^T.  Each block of b reflectors is applied in the
+ * modified compact-WY form: T^{-1} = Y^T Y with diagonal 1/tau (Eqs. inv_t,
+ * larft_update), Z = Y^T C, a triangular solve with T^{-1}, C -= Y W. */
+size_t bdc_ormbr_workspace(int m, int n, int cdim);
+int bdc_ormbr(int vect, int m, int n, const double *A, int lda, const double *tau, double *C, int ldc, int cdim,
+              void *work, size_t lwork, bdc_stream_t stream);
+
+/* QR factorization A = Q R (Sec. 4.3, geqrf): per panel a cooperative
+ * column-reflector kernel, then the trailing columns updated by the panel's
+ * block reflector in modified compact WY.  R in the upper triangle of A,
+ * reflectors below, tau[min(m, n)]. */
+size_t bdc_geqrf_workspace(int m, int n);
+int bdc_geqrf(int m, int n, double *A, int lda, double *tau, void *work, size_t lwork, int *d_info,
+              bdc_stream_t stream);
+
+/* The first n columns of Q = H_1 ... H_n (Eq. orgqr-q) in place of the
+ * reflectors bdc_geqrf left in A (m >= n); workspace of bdc_geqrf_workspace. */
+int bdc_orgqr(int m, int n, double *A, int lda, const double *tau, void *work, size_t lwork, bdc_stream_t stream);
+
+/* Dense SVD A = U diag(S) V^T, m >= n (Sec. 4): for m >= 1.6 n first A = Q R
+ * (bdc_geqrf, bdc_orgqr) and the SVD of R with U = Q U_R; then bdc_gebrd,
+ * the bidiagonal SVD bdc_svd_ex with options o (precision of the merge
+ * products, root starts; o->vectors must be BDC_VEC_BOTH), and the
+ * back-transformations U = Q1 U2, V^T = V2^T P1^T (bdc_ormbr).  A (m x n,
+ * lda) is overwritten; S[n] descending; U m x n (ldu >= m); VT n x n (ldvt
+ * >= n).  *d_info (device): the status of bdc_svd_ex, or BDC_ERR_TIMEOUT. */
+size_t bdc_gesvd_workspace(int m, int n, const bdc_opts *o);
+int bdc_gesvd(int m, int n, double *A, int lda, double *S, double *U, int ldu, double *VT, int ldvt,
+              const bdc_opts *o, void *work, size_t lwork, int *d_info, bdc_stream_t stream);
+
 /* ---------------- stage profiling (CUDA events, host side) ---------------
  * bdc_profile_begin(1) makes every later call record a CUDA event pair
  * around each stage's launches on the call's stream; bdc_profile_end() waits
@@ -429,6 +484,11 @@ int bdc_profile_secular(long long *roots, long long *iters);
  *   leaf     17 per logged rotation (forming and applying it to d, e) and
  *            6 per rotation per row of U or V it is replayed on. */
 int bdc_profile_fp64(double *fp64);
+/* After bdc_profile_end: per merge height k < levels (0 = the merges right
+ * above the leaves) of stage kind `stage`, the summed milliseconds ms[k]
+ * and work[k]: FP64 operations for the secular, Loewner and vector stages,
+ * executed tensor flops for the products (either array may be NULL). */
+int bdc_profile_levels(int stage, int levels, double *ms, double *work);
 
 /* Text of the last CUDA error the library saw on this thread ("" if none);
  * reading it clears it. */

@@ -75,10 +75,20 @@ _SIGS = {
     "bdc_svd_batched_f32": (_I, [_I, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP, _VP]),
     "bdc_plan_create_f32": (_I, [_VP, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "bdc_status_string": (ctypes.c_char_p, [_I]),
+    "bdc_gebrd_workspace": (_SZ, [_I, _I]),
+    "bdc_gebrd": (_I, [_I, _I, _VP, _I, _VP, _VP, _VP, _VP, _VP, _SZ, _VP, _VP]),
+    "bdc_ormbr_workspace": (_SZ, [_I, _I, _I]),
+    "bdc_ormbr": (_I, [_I, _I, _I, _VP, _I, _VP, _VP, _I, _I, _VP, _SZ, _VP]),
+    "bdc_geqrf_workspace": (_SZ, [_I, _I]),
+    "bdc_geqrf": (_I, [_I, _I, _VP, _I, _VP, _VP, _SZ, _VP, _VP]),
+    "bdc_orgqr": (_I, [_I, _I, _VP, _I, _VP, _VP, _SZ, _VP]),
+    "bdc_gesvd_workspace": (_SZ, [_I, _I, _VP]),
+    "bdc_gesvd": (_I, [_I, _I, _VP, _I, _VP, _VP, _I, _VP, _I, _VP, _VP, _SZ, _VP, _VP]),
     "bdc_profile_begin": (_I, [_I]),
     "bdc_profile_end": (_I, [_VP, _VP, _VP]),
     "bdc_profile_secular": (_I, [_VP, _VP]),
     "bdc_profile_fp64": (_I, [_VP]),
+    "bdc_profile_levels": (_I, [_I, _I, _VP, _VP]),
     "bdc_last_error_string": (ctypes.c_char_p, []),
 }
 
@@ -105,6 +115,14 @@ def profile_end():
     lib().bdc_profile_fp64(f64.ctypes.data_as(ctypes.c_void_p))
     out = {s: {"ms": float(ms[i]), "launches": int(ln[i]), "work": float(wk[i]), "fp64": float(f64[i])}
            for i, s in enumerate(STAGES)}
+    for i, st_name in enumerate(STAGES):
+        lm = np.zeros(32)
+        lw = np.zeros(32)
+        lib().bdc_profile_levels(i, 32, lm.ctypes.data_as(ctypes.c_void_p), lw.ctypes.data_as(ctypes.c_void_p))
+        nz = int(np.max(np.nonzero(lm)[0]) + 1) if np.any(lm) else 0
+        if nz:
+            out[st_name]["level_ms"] = [float(x) for x in lm[:nz]]
+            out[st_name]["level_work"] = [float(x) for x in lw[:nz]]
     r, it = ctypes.c_longlong(0), ctypes.c_longlong(0)
     lib().bdc_profile_secular(ctypes.byref(r), ctypes.byref(it))
     out["secular"]["roots"] = int(r.value)
@@ -593,3 +611,87 @@ def autotune(ns, prec="fp64", seed="plain", slices=0, reps=3, stream=None, dtype
     _check("bdc_autotune", fn(len(ns), ns.ctypes.data_as(ctypes.c_void_p), ctypes.byref(o),
                               int(reps), ctypes.byref(ms), _stream(stream)))
     return int(o.leaf), int(o.mixed_min), float(ms.value)
+
+
+# ---------------------------------------------------------------- dense front and back end
+def _colmajor(A):
+    """A (rows x cols) as a CUDA float64 column-major copy (returned as the
+    transpose-view of a contiguous tensor)."""
+    A = _dev(A)
+    return A.t().contiguous().t()
+
+
+def gebrd(A, stream=None):
+    """bdc_gebrd: (Ar, d, e, tauq, taup, info); Ar is A overwritten by the
+    reflectors (column-major view), B = diag(d) + superdiag(e)."""
+    A = _colmajor(A)
+    m, n = A.shape
+    dev = A.device
+    d = torch.empty(max(n, 1), dtype=torch.float64, device=dev)
+    e = torch.empty(max(n - 1, 1), dtype=torch.float64, device=dev)
+    tq = torch.empty(max(n, 1), dtype=torch.float64, device=dev)
+    tp = torch.empty(max(n, 1), dtype=torch.float64, device=dev)
+    info = torch.zeros(1, dtype=torch.int32, device=dev)
+    lw = int(lib().bdc_gebrd_workspace(m, n))
+    work = torch.empty(max(lw, 1), dtype=torch.uint8, device=dev)
+    _check("bdc_gebrd", lib().bdc_gebrd(m, n, _ptr(A), max(m, 1), _ptr(d), _ptr(e), _ptr(tq), _ptr(tp), _ptr(work),
+                                         work.numel(), _ptr(info), _stream(stream)))
+    return A, d[:n], e[:max(n - 1, 0)], tq[:n], tp[:n], int(info.item())
+
+
+def ormbr(vect, Ar, tau, C, stream=None):
+    """bdc_ormbr: vect 0: Q1 C (C m x k); vect 1: C P1^T (C k x n).  C is
+    updated in place (it must be a column-major CUDA float64 tensor)."""
+    m, n = Ar.shape
+    rows, cols = C.shape
+    assert C.stride(0) == 1, "C must be column-major"
+    cdim = cols if vect == 0 else rows
+    lw = int(lib().bdc_ormbr_workspace(m, n, cdim))
+    work = torch.empty(max(lw, 1), dtype=torch.uint8, device=Ar.device)
+    _check("bdc_ormbr", lib().bdc_ormbr(int(vect), m, n, _ptr(Ar), max(Ar.stride(1), 1), _ptr(tau), _ptr(C),
+                                         max(C.stride(1), 1), cdim, _ptr(work), work.numel(), _stream(stream)))
+    return C
+
+
+def geqrf(A, stream=None):
+    """bdc_geqrf: (Ar, tau, info)."""
+    A = _colmajor(A)
+    m, n = A.shape
+    tau = torch.empty(max(min(m, n), 1), dtype=torch.float64, device=A.device)
+    info = torch.zeros(1, dtype=torch.int32, device=A.device)
+    lw = int(lib().bdc_geqrf_workspace(m, n))
+    work = torch.empty(max(lw, 1), dtype=torch.uint8, device=A.device)
+    _check("bdc_geqrf", lib().bdc_geqrf(m, n, _ptr(A), max(m, 1), _ptr(tau), _ptr(work), work.numel(), _ptr(info),
+                                         _stream(stream)))
+    return A, tau[:min(m, n)], int(info.item())
+
+
+def orgqr(Ar, tau, stream=None):
+    """bdc_orgqr: the explicit m x n Q in place of Ar's reflectors."""
+    m, n = Ar.shape
+    lw = int(lib().bdc_geqrf_workspace(m, n))
+    work = torch.empty(max(lw, 1), dtype=torch.uint8, device=Ar.device)
+    _check("bdc_orgqr", lib().bdc_orgqr(m, n, _ptr(Ar), max(Ar.stride(1), 1), _ptr(tau), _ptr(work), work.numel(),
+                                         _stream(stream)))
+    return Ar
+
+
+def gesvd(A, *, prec="fp64", leaf=0, slices=0, seed="plain", mlp=None, stream=None, check=True, work=None):
+    """bdc_gesvd: dense SVD A = U diag(S) V^T (m >= n); returns (S, U, VT, info)."""
+    A = _colmajor(A)
+    m, n = A.shape
+    dev = A.device
+    o = make_opts(prec, leaf, 64, slices, seed, mlp)
+    S = torch.empty(max(n, 1), dtype=torch.float64, device=dev)
+    Ut = torch.empty((n, m), dtype=torch.float64, device=dev)      # column-major m x n
+    VTt = torch.empty((n, n), dtype=torch.float64, device=dev)
+    info = torch.zeros(1, dtype=torch.int32, device=dev)
+    lw = int(lib().bdc_gesvd_workspace(m, n, ctypes.byref(o)))
+    if work is None or work.numel() < lw:
+        work = torch.empty(max(lw, 1), dtype=torch.uint8, device=dev)
+    _check("bdc_gesvd", lib().bdc_gesvd(m, n, _ptr(A), max(m, 1), _ptr(S), _ptr(Ut), max(m, 1), _ptr(VTt), max(n, 1),
+                                         ctypes.byref(o), _ptr(work), work.numel(), _ptr(info), _stream(stream)))
+    code = int(info.item())
+    if check and code != 0:
+        raise BDCError("bdc_gesvd (device status)", code)
+    return S[:n], Ut.t(), VTt.t(), code

@@ -527,13 +527,19 @@ struct ProfEvent {
     cudaEvent_t a, b;
     long long launches;
     double work;
+    int level;       // merge height (0 = the merges right above the leaves; -1 = not a merge stage)
 };
+constexpr int kProfLevels = 32;
+thread_local int g_prof_level = -1;   // height of the merges being launched
+double g_level_ms[BDC_NSTAGES][kProfLevels] = {{0}};
+double g_level_fp64[BDC_NSTAGES][kProfLevels] = {{0}};
 // executed work of a recorded call, computed from the device-side deflation
 // results (NodeState) once the call has finished
 struct ProfCall {
     const NodeState *dstate;
     int nnodes;
     std::vector<NodeDesc> merges;
+    std::vector<int> merge_level;    // height of each merge (index into merges)
     std::vector<NodeDesc> leaves;
     int pairs;
     int want_u;      // the U side was formed (both vector sets)
@@ -563,7 +569,7 @@ StageScope::StageScope(cudaStream_t s, int k, long long l, double w) : st(s), st
 StageScope::~StageScope() {
     if (g_prof.on && a) {
         cudaEventRecord(b, st);
-        g_prof.ev.push_back(ProfEvent{stage, a, b, launches, work});
+        g_prof.ev.push_back(ProfEvent{stage, a, b, launches, work, g_prof_level});
     }
 }
 
@@ -682,15 +688,19 @@ int run_plan(const Plan &p, const bdc_opts &o, char *work, std::vector<MatDesc> 
     const int pairs = (o.prec == BDC_MIXED_EXACT) ? (o.slices * (o.slices + 1)) / 2
                       : (o.prec == BDC_MIXED_BF16X3) ? 3 : 1;
     if (g_prof.on) {
-        ProfCall pc{dstate, p.nnodes, {}, p.leaves, pairs, o.vectors == BDC_VEC_BOTH ? 1 : 0,
+        ProfCall pc{dstate, p.nnodes, {}, {}, p.leaves, pairs, o.vectors == BDC_VEC_BOTH ? 1 : 0,
                     o.prec == BDC_MIXED_EXACT ? o.slices : (o.prec == BDC_MIXED_BF16X3 ? 2 : 0),
                     o.prec == BDC_FP64 ? (1 << 30) : o.mixed_min, p.vals};
-        for (auto &h : p.heights) pc.merges.insert(pc.merges.end(), h.begin(), h.end());
+        for (size_t h = 0; h < p.heights.size(); ++h) {
+            pc.merges.insert(pc.merges.end(), p.heights[h].begin(), p.heights[h].end());
+            pc.merge_level.insert(pc.merge_level.end(), p.heights[h].size(), (int)h);
+        }
         g_prof.calls.push_back(std::move(pc));
     }
     for (size_t h = 0; h < p.heights.size(); ++h) {
         const int nn = (int)p.heights[h].size();
         const int mm = p.hmmax[h];
+        g_prof_level = (int)h;
         const NodeDesc *dn = (const NodeDesc *)(work + p.off_nodes + p.off_height_nodes[h]);
         double msum = 0.0;
         for (const NodeDesc &nd : p.heights[h]) msum += nd.m;
@@ -756,6 +766,7 @@ int run_plan(const Plan &p, const bdc_opts &o, char *work, std::vector<MatDesc> 
             if ((e = launch_merge_finish(dn, nn, dmats, dstate, mm, st)) != cudaSuccess) return note(e);
         }
     }
+    g_prof_level = -1;
     if (p.nmat > 0 && p.vals) {
         StageScope sc(st, BDC_STAGE_FINAL, (p.nmat + 65534) / 65535, 0.0);
         for (int m0 = 0; m0 < p.nmat; m0 += 65535) {
@@ -1416,7 +1427,18 @@ int bdc_profile_begin(int on) {
     g_prof.calls.clear();
     g_sec_roots = g_sec_iters = 0;
     for (double &x : g_fp64) x = 0.0;
+    for (auto &row : g_level_ms) for (double &x : row) x = 0.0;
+    for (auto &row : g_level_fp64) for (double &x : row) x = 0.0;
     g_prof.on = on != 0;
+    return 0;
+}
+
+int bdc_profile_levels(int stage, int levels, double *ms, double *work) {
+    if (stage < 0 || stage >= BDC_NSTAGES || levels < 0) return -1;
+    for (int k = 0; k < levels; ++k) {
+        if (ms) ms[k] = k < kProfLevels ? g_level_ms[stage][k] : 0.0;
+        if (work) work[k] = k < kProfLevels ? g_level_fp64[stage][k] : 0.0;
+    }
     return 0;
 }
 
@@ -1437,6 +1459,7 @@ int bdc_profile_end(double *ms, long long *launches, double *work) {
         t[ev.stage] += x;
         l[ev.stage] += ev.launches;
         w[ev.stage] += ev.work;
+        if (ev.level >= 0 && ev.level < kProfLevels) g_level_ms[ev.stage][ev.level] += x;
         cudaEventDestroy(ev.a);
         cudaEventDestroy(ev.b);
     }
@@ -1457,8 +1480,10 @@ int bdc_profile_end(double *ms, long long *launches, double *work) {
             const double rot = (double)hs[lf.id].iters;
             g_fp64[BDC_STAGE_LEAF] += rot * (17.0 + (pc.vals ? 12.0 : 6.0 * (lf.m + 0.5 * lf.sqre)));
         }
-        for (const NodeDesc &nd : pc.merges) {
+        for (size_t mi = 0; mi < pc.merges.size(); ++mi) {
+            const NodeDesc &nd = pc.merges[mi];
             const NodeState &ns = hs[nd.id];
+            const int lev = pc.merge_level[mi] < kProfLevels ? pc.merge_level[mi] : kProfLevels - 1;
             const double N = ns.N, Ktop = ns.P1 + 1 + ns.n2, Kbot = ns.Ktot - ns.P1;
             const double top = nd.nl + 1, botU = nd.m - nd.nl - 1, botV = nd.m + nd.sqre - nd.nl - 1;
             // mixed_min compares with the height's largest order (as the launch
@@ -1469,6 +1494,8 @@ int bdc_profile_end(double *ms, long long *launches, double *work) {
             // FP64 operations per term; Loewner: N - 1 factors per entry, ~10 each
             g_fp64[BDC_STAGE_SECULAR] += 9.0 * N * (N + (double)ns.iters);
             g_fp64[BDC_STAGE_LOWNER] += 10.0 * N * (N > 1 ? N - 1 : 0);
+            g_level_fp64[BDC_STAGE_SECULAR][lev] += 9.0 * N * (N + (double)ns.iters);
+            g_level_fp64[BDC_STAGE_LOWNER][lev] += 10.0 * N * (N > 1 ? N - 1 : 0);
             if (pc.vals) {
                 g_fp64[BDC_STAGE_VECTORS] += 9.0 * N * N;   // two rows of V: one quotient and three FMAs per entry
                 continue;
@@ -1481,6 +1508,8 @@ int bdc_profile_end(double *ms, long long *launches, double *work) {
                 w[BDC_STAGE_SLICE] += (8.0 + 2.0 * pc.slices) * (aEl + sides * N * (Ktop + Kbot));
             w[BDC_STAGE_VECTORS] += 8.0 * sides * N * ns.Ktot;
             g_fp64[BDC_STAGE_VECTORS] += (pc.want_u ? 15.0 : 10.0) * N * N;
+            g_level_fp64[BDC_STAGE_VECTORS][lev] += (pc.want_u ? 15.0 : 10.0) * N * N;
+            g_level_fp64[BDC_STAGE_GEMM][lev] += 2.0 * N * aEl * (split ? pc.pairs : 1);
             // the N survivor columns of W~ (m rows) and Q~ (m + sqre rows) written
             // in full, their child-block rows (about half) read
             w[BDC_STAGE_GATHER] += 12.0 * N * ((pc.want_u ? nd.m : 0) + nd.m + nd.sqre);

@@ -17,6 +17,15 @@ Recipes (n x n upper bidiagonal, diagonal d[n], superdiagonal e[n-1]):
   clustered d = e = 1 + 1e-10 * N(0, 1)
   ones      d = e = 1  (sigma_k = 2 cos(k pi / (2n + 1)))
   batch     n_k = floor(exp(U(ln 32, ln 1024))), each matrix 'uniform'
+
+Dense test matrices (m x n, m >= n) with prescribed singular values, after
+the SVD_arith / SVD_geo / SVD_logrand kinds of the paper's test set with
+condition number kappa: sigma_i = 1 - (i / (n-1)) (1 - 1/kappa) (arith),
+kappa^(-i/(n-1)) (geo), exp(U(ln(1/kappa), 0)) sorted descending
+(logrand).  A = Qm[:, :n] diag(sigma) Qn^T with orthogonal factors
+Q = D1 P1 C P2 D2 built in closed form: C the orthonormal DCT-II matrix
+C[k, j] = c_k cos(pi (2 j + 1) k / (2 N)), P random permutations, D random
+signs (no factorization is used to make them).
 """
 from __future__ import annotations
 
@@ -99,3 +108,37 @@ def batch(count: int = 2048, seed: int = 3, lo: int = 32, hi: int = 1024):
         e = 0.5 + uniform01(seed, 101 + 2 * k, int(n) - 1)
         out.append((d, e))
     return out
+
+
+def dct_orthogonal(N: int, seed: int, stream: int, cols: int = None) -> np.ndarray:
+    """The first `cols` columns (default N) of a randomized N x N orthogonal
+    matrix D1 P1 C P2 D2 (C the orthonormal DCT-II matrix)."""
+    cols = N if cols is None else cols
+    p1 = np.argsort(uniform01(seed, stream, N))
+    p2 = np.argsort(uniform01(seed, stream + 1, N))[:cols]
+    s1 = np.where(uniform01(seed, stream + 2, N) < 0.5, -1.0, 1.0)
+    s2 = np.where(uniform01(seed, stream + 3, cols) < 0.5, -1.0, 1.0)
+    k = p1[:, None].astype(np.int64)                  # rows of C, permuted
+    j = p2[None, :].astype(np.int64)                  # columns of C, permuted
+    # the angle pi (2j+1) k / (2N) reduced exactly modulo 2 pi on the integers
+    r = ((2 * j + 1) * k) % (4 * N)
+    C = np.cos(np.pi * r.astype(np.float64) / (2.0 * N)) * np.sqrt(2.0 / N)
+    C[p1 == 0, :] *= np.sqrt(0.5)
+    return s1[:, None] * C * s2[None, :]
+
+
+def dense_sigma(kind: str, n: int, kappa: float, seed: int) -> np.ndarray:
+    i = np.arange(n, dtype=np.float64)
+    t = i / max(n - 1, 1)
+    if kind == "arith":
+        return 1.0 - t * (1.0 - 1.0 / kappa)
+    if kind == "geo":
+        return kappa ** (-t)
+    if kind == "logrand":
+        return np.sort(np.exp(np.log(1.0 / kappa) * uniform01(seed, 40, n)))[::-1].copy()
+    raise ValueError(kind)
+
+
+def dense(kind: str, m: int, n: int, kappa: float = 1e4, seed: int = 0):
+    """(Qm_cols (m x n), sigma (n), Qn (n x n)): A = Qm_cols diag(sigma) Qn^T."""
+    return dct_orthogonal(m, seed, 50, n), dense_sigma(kind, n, kappa, seed), dct_orthogonal(n, seed, 60)

@@ -254,6 +254,10 @@ def test_mlp_svd_parity_and_fewer_iterations(bdc, trained, kind, seed):
     assert all(stats[m][1] == r0 > 0 for m in stats)
     ipr = {m: stats[m][0] / r0 for m in stats}
     print(f"{kind}: iterations per root " + "  ".join(f"{m} {v:.3f}" for m, v in ipr.items()))
+    # with the FP64 root finder alone the learned start saves >= 15% of the
+    # iterations against the midpoint start; against its own analytic prior
+    # it is reported, not claimed (the network corrects y_q by ~0.04 in logit,
+    # too little to remove a step of the rational iteration)
     assert ipr["mlp"] <= 0.85 * ipr["plain"], ipr
     assert ipr["mlp"] <= 1.02 * ipr["analytic"], ipr
     # parity of the seeded run with the FP64 oracle (same bar as the plain path)
@@ -269,6 +273,30 @@ def test_mlp_svd_parity_and_fewer_iterations(bdc, trained, kind, seed):
     # singular values agree with the plain solve to rounding
     s0 = stats["plain"][2].cpu().numpy()
     assert np.max(np.abs(s - s0)) <= 64 * np.finfo(float).eps * s0[0]
+
+
+@pytest.mark.parametrize("kind,seed", [("uniform", 0), ("graded", 1)])
+def test_shipped_configuration_has_no_start_to_gain(bdc, trained, kind, seed):
+    """With the FP32 pre-iterations (the default) every start rule needs
+    the same FP64 work: each root takes one pole-sum evaluation at its start
+    and at least one more that confirms the step, and the FP32 phase already
+    brings every start to ~2^-17, so plain, analytic and learned starts all
+    land at ~1.1 FP64 iterations per root (2.1 evaluations).  The learned
+    start does not pay in this configuration; this test records that."""
+    P = trained[0]
+    d, e = inputs.make(kind, 4096, seed)
+    dt, et = torch.from_numpy(d).cuda(), torch.from_numpy(e).cuda()
+    ipr = {}
+    for mode in ("plain", "analytic", "mlp"):
+        bdc.profile_begin()
+        _, _, _, info = bdc.svd(dt, et, seed=mode, mlp=P if mode == "mlp" else None)
+        prof = bdc.profile_end()
+        assert info == 0
+        ipr[mode] = prof["secular"]["iters"] / prof["secular"]["roots"]
+    print(f"{kind} (FP32 pre-iterations): FP64 iterations per root " +
+          "  ".join(f"{m} {v:.3f}" for m, v in ipr.items()))
+    assert all(1.0 <= v <= 1.35 for v in ipr.values()), ipr
+    assert max(ipr.values()) <= 1.06 * min(ipr.values()), ipr
 
 
 def test_mlp_with_mixed_products(bdc, trained):
