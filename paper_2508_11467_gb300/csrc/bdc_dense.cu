@@ -45,6 +45,8 @@ struct DGemm {
     int lda, ldb, ldc, M, N, K;
     int ta, tb;            // op(A) = A^T, op(B) = B^T
     double alpha, beta;    // beta = 0: C is not read
+    int kchunk;            // split K: CTA row blockIdx.y multiplies K range [y kchunk, (y+1) kchunk)
+    double *part;          // split K: partial products part[y][M x N] (then alpha, beta unused)
 };
 
 __device__ __forceinline__ void dmma(double (&c)[2], double a, double b) {
@@ -98,15 +100,21 @@ __global__ void __launch_bounds__(128) k_dgemm(DGemm g) {
             Bs[bn * DSB + bk] = rb[r];
         }
     };
-    load(0);
-    for (int k0 = 0; k0 < g.K; k0 += DBK) {
+    // K range of this CTA (all of K unless split)
+    const int kb = g.part ? (int)blockIdx.y * g.kchunk : 0;
+    const int ke = g.part ? min(g.K, kb + g.kchunk) : g.K;
+    // operand loads are bounded by the K range end
+    const int Kfull = g.K;
+    g.K = ke;
+    load(kb);
+    for (int k0 = kb; k0 < ke; k0 += DBK) {
         __syncthreads();
         store();
         __syncthreads();
-        if (k0 + DBK < g.K) load(k0 + DBK);
+        if (k0 + DBK < ke) load(k0 + DBK);
 #pragma unroll
         for (int kk = 0; kk < DBK; kk += 4) {
-            if (k0 + kk >= g.K) break;
+            if (k0 + kk >= ke) break;
             double af[4], bf[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) af[i] = As[(kk + tg) * DSA + wm + i * 8 + gr];
@@ -119,6 +127,7 @@ __global__ void __launch_bounds__(128) k_dgemm(DGemm g) {
                     if (m0 + wm + i * 8 < g.M && n0 + wn + j * 8 < g.N) dmma(acc[i][j], af[i], bf[j]);
         }
     }
+    (void)Kfull;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int gm = m0 + wm + i * 8 + gr;
@@ -129,6 +138,10 @@ __global__ void __launch_bounds__(128) k_dgemm(DGemm g) {
             for (int h = 0; h < 2; ++h) {
                 const int gn = n0 + wn + j * 8 + 2 * tg + h;
                 if (gn >= g.N) continue;
+                if (g.part) {
+                    g.part[((size_t)blockIdx.y * g.N + gn) * g.M + gm] = acc[i][j][h];
+                    continue;
+                }
                 double *c = g.C + (size_t)gn * g.ldc + gm;
                 const double v = g.alpha * acc[i][j][h];
                 *c = (g.beta == 0.0) ? v : fma(g.beta, *c, v);
@@ -137,14 +150,60 @@ __global__ void __launch_bounds__(128) k_dgemm(DGemm g) {
     }
 }
 
+// C = beta C + alpha sum_y part[y] (the split-K partial products, summed in
+// a fixed order)
+__global__ void k_dgemm_reduce(const double *__restrict__ part, int splits, int M, int N, double alpha, double beta,
+                               double *C, int ldc) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (long long)M * N) return;
+    const int n = (int)(k / M), m = (int)(k % M);
+    double s = 0.0;
+    for (int y = 0; y < splits; ++y) s += part[(size_t)y * M * N + k];
+    double *c = C + (size_t)n * ldc + m;
+    *c = (beta == 0.0) ? alpha * s : fma(beta, *c, alpha * s);
+}
+
+// scratch for split-K partial products (set per call sequence by the driver)
+thread_local double *g_split_buf = nullptr;
+thread_local size_t g_split_cap = 0;   // doubles
+
+int sm_count_dense() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+    }
+    return n;
+}
+
+// C = alpha op(A) op(B) + beta C.  Products with few output tiles and a long
+// K (the Y^T C and C Y of the block reflectors: 32 x n outputs, K = the
+// panel's rows) split K over several CTAs into partial products, summed in a
+// fixed order by k_dgemm_reduce, so that the whole GPU works on them
 cudaError_t dgemm(int ta, int tb, int M, int N, int K, double alpha, const double *A, int lda, const double *B,
                   int ldb, double beta, double *C, int ldc, cudaStream_t st) {
     if (M <= 0 || N <= 0) return cudaSuccess;
     const long long tiles = (long long)((M + DBM - 1) / DBM) * ((N + DBN - 1) / DBN);
     if (tiles > 0x7fffffffll) return cudaErrorInvalidValue;
-    DGemm g{A, B, C, lda, ldb, ldc, M, N, K, ta, tb, alpha, beta};
-    if (K <= 0) {   // C = beta C
-        g.K = 0;
+    DGemm g{A, B, C, lda, ldb, ldc, M, N, std::max(K, 0), ta, tb, alpha, beta, 0, nullptr};
+    int splits = 1;
+    const int sms = sm_count_dense();
+    if (K >= 128 && tiles < 2 * sms && g_split_buf) {
+        splits = (int)std::min<long long>((2 * sms + tiles - 1) / tiles, K / 64);
+        splits = std::min(splits, 64);
+        while (splits > 1 && (size_t)splits * M * N > g_split_cap) --splits;
+    }
+    if (splits > 1) {
+        g.kchunk = ((K + splits - 1) / splits + DBK - 1) / DBK * DBK;
+        splits = (K + g.kchunk - 1) / g.kchunk;
+        g.part = g_split_buf;
+        k_dgemm<<<dim3((unsigned)tiles, (unsigned)splits), 128, 0, st>>>(g);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        const long long cnt = (long long)M * N;
+        k_dgemm_reduce<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(g_split_buf, splits, M, N, alpha, beta, C, ldc);
+        return cudaGetLastError();
     }
     k_dgemm<<<(unsigned)tiles, 128, 0, st>>>(g);
     return cudaGetLastError();
@@ -211,6 +270,42 @@ __device__ double block_sum(double v, double *sh) {
     return r;
 }
 
+// sum over the grid's CTAs of part[k * stride] (k < count), by the whole
+// block: strided loads, four in flight per thread, then a block reduction
+__device__ double grid_partials(const double *part, int count, int stride, double *sh) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    const int T = blockDim.x;
+    int k = threadIdx.x;
+    for (; k + 3 * T < count; k += 4 * T) {
+        s0 += part[(size_t)k * stride];
+        s1 += part[(size_t)(k + T) * stride];
+        s2 += part[(size_t)(k + 2 * T) * stride];
+        s3 += part[(size_t)(k + 3 * T) * stride];
+    }
+    for (; k < count; k += T) s0 += part[(size_t)k * stride];
+    return block_sum((s0 + s1) + (s2 + s3), sh);
+}
+
+// dot product of x[r] y[r] over r = r0 + lane, r0 + lane + 32, ... < r1 by
+// one warp (result in every lane): four independent accumulators so that
+// four pairs of loads are in flight per lane
+__device__ __forceinline__ double warp_dot(const double *__restrict__ x, const double *__restrict__ y, int r0,
+                                           int r1) {
+    const int lane = threadIdx.x & 31;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int r = r0 + lane;
+    for (; r + 96 < r1; r += 128) {
+        s0 = fma(x[r], y[r], s0);
+        s1 = fma(x[r + 32], y[r + 32], s1);
+        s2 = fma(x[r + 64], y[r + 64], s2);
+        s3 = fma(x[r + 96], y[r + 96], s3);
+    }
+    for (; r < r1; r += 32) s0 = fma(x[r], y[r], s0);
+    double s = (s0 + s1) + (s2 + s3);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
 // Householder reflector from alpha and ||x_2..||^2 = sig2 (LAPACK's sign
 // convention, Sec. 4.1's first display): beta = -sign(alpha) ||x||, tau =
 // (beta - alpha) / beta, the vector's tail scaled by 1 / (alpha - beta);
@@ -274,8 +369,7 @@ __global__ void __launch_bounds__(256) k_labrd(LabrdArgs a) {
         if (threadIdx.x == 0) a.part[2 * blockIdx.x] = ss;
         if (!grid_sync(a.bar)) return;
         // (b) the column reflector H_i (every CTA forms the same scalars)
-        double sig2 = 0.0;
-        for (int k = 0; k < G; ++k) sig2 += a.part[2 * k];
+        double sig2 = grid_partials(a.part, G, 2, sh);
         const double alpha = A[(size_t)i * lda + i];
         double tau, beta;
         const double sc = reflector(alpha, sig2, tau, beta);
@@ -299,9 +393,7 @@ __global__ void __launch_bounds__(256) k_labrd(LabrdArgs a) {
             if (w < ncol) col = A + (size_t)(i + 1 + w) * lda;
             else if (w < ncol + i) col = V + (size_t)(w - ncol) * m;
             else col = X + (size_t)(w - ncol - i) * m;
-            double s = 0.0;
-            for (int r = i + lane; r < m; r += 32) s = fma(col[r], V[(size_t)i * m + r], s);
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            const double s = warp_dot(col, V + (size_t)i * m, i, m);
             if (lane == 0) {
                 if (w < ncol) a.yraw[i + 1 + w] = s;
                 else if (w < ncol + i) t1[w - ncol] = s;
@@ -328,8 +420,7 @@ __global__ void __launch_bounds__(256) k_labrd(LabrdArgs a) {
         if (threadIdx.x == 0) a.part[2 * blockIdx.x + 1] = ss;
         if (!grid_sync(a.bar)) return;
         // (e) the row reflector G_i
-        sig2 = 0.0;
-        for (int k = 0; k < G; ++k) sig2 += a.part[2 * k + 1];
+        sig2 = grid_partials(a.part + 1, G, 2, sh);
         const double alr = A[(size_t)(i + 1) * lda + i];
         double pi, betr;
         const double scr = reflector(alr, sig2, pi, betr);
@@ -351,15 +442,21 @@ __global__ void __launch_bounds__(256) k_labrd(LabrdArgs a) {
         for (long long t = gtid; t < items; t += gthreads) {
             const int ch = (int)(t / rows), r = i + 1 + (int)(t % rows);
             const int c0 = i + 1 + ch * a.chunkw, c1 = min(n, c0 + a.chunkw);
-            double s = 0.0;
-            for (int c = c0; c < c1; ++c) s = fma(A[(size_t)c * lda + r], U[(size_t)i * n + c], s);
-            a.xpart[(size_t)ch * m + r] = s;
+            const double *ui = U + (size_t)i * n;
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+            int c = c0;
+            for (; c + 3 < c1; c += 4) {
+                s0 = fma(A[(size_t)c * lda + r], ui[c], s0);
+                s1 = fma(A[(size_t)(c + 1) * lda + r], ui[c + 1], s1);
+                s2 = fma(A[(size_t)(c + 2) * lda + r], ui[c + 2], s2);
+                s3 = fma(A[(size_t)(c + 3) * lda + r], ui[c + 3], s3);
+            }
+            for (; c < c1; ++c) s0 = fma(A[(size_t)c * lda + r], ui[c], s0);
+            a.xpart[(size_t)ch * m + r] = (s0 + s1) + (s2 + s3);
         }
         for (int w = gwarp; w < 2 * i + 1; w += gwarps) {
             const double *col = (w <= i) ? Y + (size_t)w * n : U + (size_t)(w - i - 1) * n;
-            double s = 0.0;
-            for (int c = i + 1 + lane; c < n; c += 32) s = fma(col[c], U[(size_t)i * n + c], s);
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            const double s = warp_dot(col, U + (size_t)i * n, i + 1, n);
             if (lane == 0) {
                 if (w <= i) t3[w] = s;
                 else t4[w - i - 1] = s;
@@ -404,32 +501,61 @@ __global__ void __launch_bounds__(256) k_geqr2(Geqr2Args a) {
         ss = block_sum(ss, sh);
         if (threadIdx.x == 0) a.part[(size_t)blockIdx.x * (b + 1) + b] = ss;
         if (!grid_sync(a.bar)) return;
-        double sig2 = 0.0;
-        for (int k = 0; k < G; ++k) sig2 += a.part[(size_t)k * (b + 1) + b];
+        double sig2 = grid_partials(a.part + b, G, b + 1, sh);
         const double alpha = A[(size_t)i * lda + i];
         double tau, beta;
         const double sc = reflector(alpha, sig2, tau, beta);
-        // v = [1, A[i+1:, i] sc]; partial w_c = v^T A[i:, c] for the later panel columns
-        for (int r = i + 1 + gtid; r < m; r += gthreads) A[(size_t)i * lda + r] *= sc;
-        for (int c = i + 1; c < nb; ++c) {
-            double s = (gtid == 0) ? A[(size_t)c * lda + i] : 0.0;
-            for (int r = i + 1 + gtid; r < m; r += gthreads) s = fma(A[(size_t)i * lda + r], A[(size_t)c * lda + r], s);
-            s = block_sum(s, sh);
-            if (threadIdx.x == 0) a.part[(size_t)blockIdx.x * (b + 1) + c] = s;
+        // w_c = v^T A[i:, c] for every later panel column at once, from the
+        // column before scaling (v_r = sc A[r, i] for r > i, v_i = 1; the
+        // scaled v is written in the update phase, after the barrier, so no
+        // CTA reads a row another one is scaling): each warp sums its rows for
+        // column c = i + 1 + lane (lanes over columns, the warp's rows in
+        // turn), then the warps' sums are added in shared memory in a fixed
+        // order
+        {
+            __shared__ double wsum[8][33];
+            const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+            const int c = i + 1 + lane;
+            double acc = 0.0;
+            if (c < nb) {
+                for (int r = i + 1 + blockIdx.x * nwarp + wid; r < m; r += G * nwarp)
+                    acc = fma(A[(size_t)i * lda + r], A[(size_t)c * lda + r], acc);
+                acc *= sc;
+                if (gtid < 32) acc += A[(size_t)c * lda + i];           // v_i = 1 at row i (one warp of CTA 0)
+            }
+            if (wid < 8) wsum[wid][lane] = acc;
+            __syncthreads();
+            if (threadIdx.x < 32) {
+                double t = 0.0;
+                for (int q = 0; q < nwarp && q < 8; ++q) t += wsum[q][threadIdx.x];
+                if (i + 1 + (int)threadIdx.x < nb) a.part[(size_t)blockIdx.x * (b + 1) + i + 1 + threadIdx.x] = t;
+            }
         }
         if (gtid == 0) a.tau[i] = tau;
         if (!grid_sync(a.bar)) return;
-        // A[i:, c] -= tau v w_c
-        if (threadIdx.x < 64) {
-            const int c = i + 1 + threadIdx.x;
+        // A[i:, c] -= tau v w_c, w_c summed over the CTAs: thread t takes
+        // column offset t % 32 and every eighth CTA from t / 32
+        {
+            __shared__ double red[8][33];
+            const int co = threadIdx.x & 31, kk = threadIdx.x >> 5, c = i + 1 + co;
             double w = 0.0;
-            if (c < nb)
-                for (int k = 0; k < G; ++k) w += a.part[(size_t)k * (b + 1) + c];
-            sw[threadIdx.x] = tau * w;
+            if (c < nb && kk < 8)
+                for (int k = kk; k < G; k += 8) w += a.part[(size_t)k * (b + 1) + c];
+            if (kk < 8) red[kk][co] = w;
+            __syncthreads();
+            if (threadIdx.x < 32) {
+                double t = 0.0;
+                for (int q = 0; q < 8; ++q) t += red[q][threadIdx.x];
+                sw[threadIdx.x] = tau * t;
+            }
+            __syncthreads();
         }
-        __syncthreads();
         for (int r = i + gtid; r < m; r += gthreads) {
-            const double v = (r == i) ? 1.0 : A[(size_t)i * lda + r];
+            double v = 1.0;
+            if (r > i) {
+                v = A[(size_t)i * lda + r] * sc;        // the reflector's entry, stored scaled
+                A[(size_t)i * lda + r] = v;
+            }
             for (int c = i + 1; c < nb; ++c) A[(size_t)c * lda + r] -= v * sw[c - i - 1];
         }
         if (gtid == 0) A[(size_t)i * lda + i] = beta;
@@ -558,7 +684,7 @@ int coop_blocks(const void *fn, int threads, size_t smem) {
 
 // workspace layout of the dense routines (bytes from an aligned base)
 struct DenseWs {
-    size_t bar, PW, QW, yraw, tv, xpart, part, Y, Ti, Z, total;
+    size_t bar, PW, QW, yraw, tv, xpart, part, Y, Ti, Z, split, split_doubles, total;
 };
 constexpr int kChunkW = 128;   // columns per partial sum of A u
 
@@ -577,9 +703,23 @@ DenseWs dense_ws(int m, int n, int b, int zcols) {
     w.Y = o; o += al256(sizeof(double) * (size_t)std::max(m, n) * b);
     w.Ti = o; o += al256(sizeof(double) * (size_t)b * b);
     w.Z = o; o += al256(sizeof(double) * (size_t)b * std::max(std::max(m, n), zcols));
+    w.split_doubles = (size_t)16 * b * std::max(std::max(m, n), zcols);
+    w.split = o; o += al256(sizeof(double) * w.split_doubles);
     w.total = o + 256;
     return w;
 }
+
+// the split-K scratch of the calling thread's dense routine
+struct SplitScope {
+    SplitScope(char *ws, const DenseWs &w) {
+        g_split_buf = (double *)(ws + w.split);
+        g_split_cap = w.split_doubles;
+    }
+    ~SplitScope() {
+        g_split_buf = nullptr;
+        g_split_cap = 0;
+    }
+};
 
 cudaError_t launch_coop(const void *fn, int grid, void *args, cudaStream_t st) {
     void *params[] = {args};
@@ -594,10 +734,16 @@ cudaError_t launch_coop(const void *fn, int grid, void *args, cudaStream_t st) {
 cudaError_t dense_gebrd(int m, int n, double *A, int lda, double *d, double *e, double *tauq, double *taup, int b,
                         char *ws, cudaStream_t st) {
     const DenseWs w = dense_ws(m, n, b, n);
+    SplitScope split_scope(ws, w);
     GridBar *bar = (GridBar *)(ws + w.bar);
     cudaError_t err = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st);   // count, gen (not the error word)
     if (err != cudaSuccess) return err;
-    const int grid = std::min(coop_blocks((const void *)k_labrd, 256, 0), 4 * 256);
+    // CTAs by the work of a step (the products with the trailing matrix,
+    // ~m n FMAs): every barrier costs more with more CTAs, and a small
+    // trailing matrix cannot use the whole GPU
+    const long long mn = (long long)m * n;
+    const int grid = (int)std::max<long long>(
+        8, std::min<long long>(std::min(coop_blocks((const void *)k_labrd, 256, 0), 4 * 256), mn / 32768));
     for (int i0 = 0; i0 < n; i0 += b) {
         const int nb = std::min(b, n - i0), ml = m - i0, nl = n - i0;
         LabrdArgs a{A + i0 + (size_t)i0 * lda, lda, ml, nl, nb, b,
@@ -623,10 +769,13 @@ cudaError_t dense_gebrd(int m, int n, double *A, int lda, double *d, double *e, 
 // H^T = I - Y T^T Y^T in modified compact WY
 cudaError_t dense_geqrf(int m, int n, double *A, int lda, double *tau, int b, char *ws, cudaStream_t st) {
     const DenseWs w = dense_ws(m, n, b, n);
+    SplitScope split_scope(ws, w);
     GridBar *bar = (GridBar *)(ws + w.bar);
     cudaError_t err = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st);   // count, gen (not the error word)
     if (err != cudaSuccess) return err;
-    const int grid = std::min(coop_blocks((const void *)k_geqr2, 256, 0), 4 * 256);
+    // enough CTAs for ~4 panel rows per thread: the per-column reductions over
+    // the CTAs' partial sums grow with the grid
+    const int grid = std::max(1, std::min(coop_blocks((const void *)k_geqr2, 256, 0), (m + 1023) / 1024));
     double *Y = (double *)(ws + w.Y), *Ti = (double *)(ws + w.Ti), *Z = (double *)(ws + w.Z);
     const int kmax = std::min(m, n);
     for (int i0 = 0; i0 < kmax; i0 += b) {
@@ -650,6 +799,7 @@ cudaError_t dense_geqrf(int m, int n, double *A, int lda, double *tau, int b, ch
 // before its columns are reset to the identity's
 cudaError_t dense_orgqr(int m, int n, int k, double *A, int lda, const double *tau, int b, char *ws, cudaStream_t st) {
     const DenseWs w = dense_ws(m, n, b, n);
+    SplitScope split_scope(ws, w);
     double *Y = (double *)(ws + w.Y), *Ti = (double *)(ws + w.Ti), *Z = (double *)(ws + w.Z);
     cudaError_t err = cudaSuccess;
     // columns k..n-1 start as identity columns
@@ -686,6 +836,7 @@ cudaError_t dense_orgqr(int m, int n, int k, double *A, int lda, const double *t
 cudaError_t dense_ormbr(int vect, int m, int n, const double *A, int lda, const double *tau, double *C, int ldc,
                         int cdim, int b, char *ws, cudaStream_t st) {
     const DenseWs w = dense_ws(m, n, b, std::max(cdim, n));
+    SplitScope split_scope(ws, w);
     double *Y = (double *)(ws + w.Y), *Ti = (double *)(ws + w.Ti), *Z = (double *)(ws + w.Z);
     cudaError_t err = cudaSuccess;
     if (vect == 0) {
