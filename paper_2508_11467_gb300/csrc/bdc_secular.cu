@@ -74,6 +74,20 @@ __host__ __device__ __forceinline__ int group_warps(int mmax) {
     return (mmax + per - 1) / per;
 }
 
+// Lanes per root of the secular solve: about kSecPoles poles per lane.  An
+// FP64 instruction costs its warp the same issue slot whatever the number of
+// active lanes, so the scalar steps of an iteration (model, bracket, stopping
+// test) cost a warp instruction per group of 32 / G roots: fewer lanes per
+// root share them among more roots, at the price of a longer pole loop.
+constexpr int kSecPoles = 16;
+__host__ __device__ __forceinline__ int secular_group_size(int N) {
+    return N <= 4 * kSecPoles ? 4 : N <= 8 * kSecPoles ? 8 : N <= 16 * kSecPoles ? 16 : 32;
+}
+// warps per node: ceil(N G(N) / 32) grows with N, so mmax bounds it
+__host__ __device__ __forceinline__ int secular_group_warps(int mmax) {
+    return (int)(((long long)mmax * secular_group_size(mmax) + 31) / 32);
+}
+
 struct Sums {
     real_t psi, dpsi, phi, dphi;
 };
@@ -528,8 +542,8 @@ __device__ __forceinline__ void secular_group(const NodeDesc &nd, const MatDesc 
     }
 }
 
-// Warp w of a node (mmax warps per node) serves roots w * (32 / G) + (lane / G),
-// G = group_size(N) from the node's survivor count, known only here.
+// Warp w of a node (secular_group_warps(mmax) per node) serves roots w * (32 / G) + (lane / G),
+// G = secular_group_size(N) from the node's survivor count, known only here.
 __global__ void __launch_bounds__(256, 2) k_secular(const NodeDesc *__restrict__ nodes,
                                                  const MatDesc *__restrict__ mats,
                                                  NodeState *__restrict__ state, int wpn,
@@ -539,7 +553,7 @@ __global__ void __launch_bounds__(256, 2) k_secular(const NodeDesc *__restrict__
     if (node >= nnodes) return;
     const NodeDesc nd = nodes[node];
     const NodeState ns = state[nd.id];
-    const int N = ns.N, G = group_size(N), per = 32 / G;
+    const int N = ns.N, G = secular_group_size(N), per = 32 / G;
     const int i = w * per + lane / G;
     if (i >= N) return;                              // whole groups leave together
     const MatDesc &md = mats[nd.mat];
@@ -938,8 +952,9 @@ cudaError_t launch_secular(const NodeDesc *nodes, int nnodes, const MatDesc *mat
         if (e != cudaSuccess) return e;
     }
 #endif
-    k_secular<<<(unsigned)((gwarps + 7) / 8), 256, 0, st>>>(nodes, mats, state, group_warps(mmax), max_iter,
-                                                            nnodes, seed_mode, fp32_start);
+    const long long swarps = (long long)nnodes * secular_group_warps(mmax);
+    k_secular<<<(unsigned)((swarps + 7) / 8), 256, 0, st>>>(nodes, mats, state, secular_group_warps(mmax),
+                                                             max_iter, nnodes, seed_mode, fp32_start);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     }
