@@ -27,7 +27,8 @@ namespace BDC_NS {
 // mixed-precision product path (bdc_gemm_mixed.cu): products packed one after
 // another in the sliced operand arrays, rows bounded by Mmax[p], columns by Nmax[p]
 cudaError_t launch_gemm_mixed(const GemmProb *probs, int nprobs, const int *Mmax, const int *Nmax, int kmax,
-                              int prec, int slices, void *scratch, size_t scratch_bytes, int *err, cudaStream_t st);
+                              int prec, int slices, void *scratch, size_t scratch_bytes, int *err, int phase,
+                              cudaStream_t st);
 size_t gemm_mixed_scratch(long long rows_total, long long cols_total, int kmax, int prec, int slices,
                           long long tiles);
 #endif
@@ -635,6 +636,42 @@ cudaError_t upload(const Plan &p, char *work, const std::vector<MatDesc> &mats, 
     return cudaMemcpyAsync(work, host, bytes, cudaMemcpyHostToDevice, st);
 }
 
+// Side stream of the calling thread (one per device), for the merge work
+// that overlaps the root finding, with the events that fork it from and join
+// it to the caller's stream.  Created on first use with the capture mode
+// relaxed (so also inside a capture); kept for the life of the thread (like
+// the other caches of this library, not valid after cudaDeviceReset).
+struct SideStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    ~SideStream() {
+        if (fork) cudaEventDestroy(fork);
+        if (join) cudaEventDestroy(join);
+        if (s) cudaStreamDestroy(s);
+    }
+};
+constexpr int kMaxDevices = 64;
+
+cudaError_t side_stream(SideStream *&out) {
+    thread_local SideStream sides[kMaxDevices];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    SideStream &sd = sides[dev];
+    if (!sd.join) {
+        cudaStreamCaptureMode mode = cudaStreamCaptureModeRelaxed;
+        cudaThreadExchangeStreamCaptureMode(&mode);
+        if (!sd.s) e = cudaStreamCreateWithFlags(&sd.s, cudaStreamNonBlocking);
+        if (e == cudaSuccess && !sd.fork) e = cudaEventCreateWithFlags(&sd.fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sd.join, cudaEventDisableTiming);
+        cudaThreadExchangeStreamCaptureMode(&mode);
+        if (e != cudaSuccess) return e;
+    }
+    out = &sd;
+    return cudaSuccess;
+}
+
 int run_plan(const Plan &p, const bdc_opts &o, char *work, std::vector<MatDesc> &mats, int *d_info_out,
              cudaStream_t st) {
     // per-matrix data pointers
@@ -651,6 +688,8 @@ int run_plan(const Plan &p, const bdc_opts &o, char *work, std::vector<MatDesc> 
     }
     cudaError_t e = upload(p, work, mats, st);
     if (e != cudaSuccess) return note(e);
+    SideStream *side = nullptr;
+    if (!p.vals && !p.heights.empty() && (e = side_stream(side)) != cudaSuccess) return note(e);
     int *derr = (int *)(work + p.off_err);
     if ((e = cudaMemsetAsync(derr, 0, sizeof(int), st)) != cudaSuccess) return note(e);
     const MatDesc *dmats = (const MatDesc *)(work + p.off_mats);
@@ -709,12 +748,49 @@ int run_plan(const Plan &p, const bdc_opts &o, char *work, std::vector<MatDesc> 
             if ((e = launch_merge_prep(dn, nn, dmats, dstate, dprobs, mm, scans, st)) != cudaSuccess) return note(e);
         }
         if (o.checked && (e = launch_check_prep(dn, nn, dmats, dstate, st)) != cudaSuccess) return note(e);
+        // products of this height: FP64 (one launch) or split BF16 (two
+        // slicing kernels + the exact-group and, for more than 4 slices, the
+        // low-group product kernels); small merges use the FP64 products:
+        // the split path's fixed costs (slicing, two kernels, TMEM set-up per
+        // tile) dominate there
+        const bool mixed_here = !p.vals && (o.prec != BDC_FP64) && mm >= o.mixed_min;
+        std::vector<int> Mx, Nx;
+        if (mixed_here) {
+            Mx.resize(4 * nn);
+            Nx.resize(4 * nn);
+            for (int k = 0; k < nn; ++k) {
+                const NodeDesc &nd = p.heights[h][k];
+                Mx[4 * k + 0] = nd.nl + 1;
+                Mx[4 * k + 1] = nd.m - nd.nl - 1;
+                Mx[4 * k + 2] = nd.nl + 1;
+                Mx[4 * k + 3] = nd.m + nd.sqre - nd.nl - 1;
+                for (int j = 0; j < 4; ++j) Nx[4 * k + j] = nd.m;
+            }
+        }
         if (p.vals) {   // values only: two rows of V instead of the panels
             StageScope sc(st, BDC_STAGE_GATHER, 1, 0.0);
             if ((e = launch_gather_rows(dn, nn, dmats, dstate, mm, st)) != cudaSuccess) return note(e);
-        } else {   // survivors' columns of W~ and Q~ (bytes added from the node states)
-            StageScope sc(st, BDC_STAGE_GATHER, 1, 0.0);
-            if ((e = launch_merge_gather(dn, nn, dmats, dstate, mm, st)) != cudaSuccess) return note(e);
+        } else {
+            // survivors' columns of W~ and Q~ (bytes added from the node
+            // states), then the A slices of the split products: they depend
+            // on the prep only, so they run on the side stream while the
+            // roots, the Loewner z~ and the vectors of M~ are computed (that
+            // FP64 chain leaves most of the GPU idle)
+            if ((e = cudaEventRecord(side->fork, st)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(side->s, side->fork, 0)) != cudaSuccess)
+                return note(e);
+            {
+                StageScope sc(side->s, BDC_STAGE_GATHER, 1, 0.0);
+                if ((e = launch_merge_gather(dn, nn, dmats, dstate, mm, side->s)) != cudaSuccess) return note(e);
+            }
+#ifndef BDC_FP32
+            if (mixed_here &&
+                (e = launch_gemm_mixed(dprobs, 4 * nn, Mx.data(), Nx.data(), mm + 9, o.prec,
+                                       o.slices > 0 ? o.slices : 6, work + p.off_mixed, p.mixed_bytes, derr, MIXED_A,
+                                       side->s)) != cudaSuccess)
+                return note(e);
+#endif
+            if ((e = cudaEventRecord(side->join, side->s)) != cudaSuccess) return note(e);
         }
         if ((e = launch_secular(dn, nn, dmats, dstate, mm, max_iter, o.seed, o.mlp, harvest, o.fp32_start, st)) !=
             cudaSuccess)
@@ -731,11 +807,7 @@ int run_plan(const Plan &p, const bdc_opts &o, char *work, std::vector<MatDesc> 
             if ((e = launch_vectors(dn, nn, dmats, dstate, mm, st)) != cudaSuccess) return note(e);
         }
         if (!p.vals) {   // 2 M N K per product as deflated, x slice pairs (added from the node states)
-            // FP64: one launch; split BF16: two slicing kernels + the exact-group
-            // and (for more than 4 slices) the low-group product kernels
-            // small merges use the FP64 products: the split path's fixed costs
-            // (slicing, two kernels, TMEM set-up per tile) dominate there
-            const bool mixed_here = (o.prec != BDC_FP64) && mm >= o.mixed_min;
+            if ((e = cudaStreamWaitEvent(st, side->join, 0)) != cudaSuccess) return note(e);
             if (!mixed_here) {
                 StageScope sc(st, BDC_STAGE_GEMM, 1, 0.0);
                 // rows of the four products: nl + 1 (tops), m - nl - 1, m + sqre - nl - 1
@@ -746,17 +818,9 @@ int run_plan(const Plan &p, const bdc_opts &o, char *work, std::vector<MatDesc> 
             }
 #ifndef BDC_FP32
             else {
-                std::vector<int> Mx(4 * nn), Nx(4 * nn);
-                for (int k = 0; k < nn; ++k) {
-                    const NodeDesc &nd = p.heights[h][k];
-                    Mx[4 * k + 0] = nd.nl + 1;
-                    Mx[4 * k + 1] = nd.m - nd.nl - 1;
-                    Mx[4 * k + 2] = nd.nl + 1;
-                    Mx[4 * k + 3] = nd.m + nd.sqre - nd.nl - 1;
-                    for (int j = 0; j < 4; ++j) Nx[4 * k + j] = nd.m;
-                }
                 e = launch_gemm_mixed(dprobs, 4 * nn, Mx.data(), Nx.data(), mm + 9, o.prec,
-                                      o.slices > 0 ? o.slices : 6, work + p.off_mixed, p.mixed_bytes, derr, st);
+                                      o.slices > 0 ? o.slices : 6, work + p.off_mixed, p.mixed_bytes, derr, MIXED_B,
+                                      st);
             }
 #endif
             if (e != cudaSuccess) return note(e);
@@ -1413,7 +1477,7 @@ int bdc_gemm(int M, int N, int K, const double *A, int lda, const double *B, int
         e = cudaMemsetAsync(err, 0, sizeof(int), st);
         if (e == cudaSuccess)
             e = launch_gemm_mixed((const GemmProb *)w, 1, &M, &N, K, prec, slices, scr,
-                                  lwork - (size_t)(scr - (char *)work), err, st);
+                                  lwork - (size_t)(scr - (char *)work), err, MIXED_ALL, st);
     }
     return cc.finish(note(e));
 }

@@ -912,7 +912,7 @@ int sm_count() {
 
 template <int S, bool EXACT>
 cudaError_t run_mixed(const GemmProb *probs, int nprobs, const std::vector<MixProb> &hm, int rowsA, int colsB,
-                      int Kld, char *scratch, const Layout &L, int *err, cudaStream_t st) {
+                      int Kld, char *scratch, const Layout &L, int *err, int phase, cudaStream_t st) {
     __nv_bfloat16 *As = (__nv_bfloat16 *)(scratch + L.offA);
     __nv_bfloat16 *Bs = (__nv_bfloat16 *)(scratch + L.offB);
     int *E = (int *)(scratch + L.offE), *F = (int *)(scratch + L.offF);
@@ -925,42 +925,53 @@ cudaError_t run_mixed(const GemmProb *probs, int nprobs, const std::vector<MixPr
         tiles = hm[p].tile0 + ((hm[p].Mmax + TM - 1) / TM) * hm[p].tilesN;
     }
     if (hm.size() && hm[0].tilesN != (hm[0].Nmax + TNX - 1) / TNX) return cudaErrorInvalidValue;
-    // small tables through pinned host memory: the capturing plan's own
-    // blocks, else a shared ring (copies stay valid until the ring wraps)
-    static std::mutex mu;
-    static char *ring = nullptr;
-    static size_t ring_off = 0;
-    constexpr size_t kRing = 64ull << 20;
-    const size_t need = sizeof(MixProb) * nprobs + 256;
-    if (need > kRing) return cudaErrorInvalidValue;
-    char *h = (char *)plan_pinned_alloc(need);
-    if (!h) {
-        std::lock_guard<std::mutex> lk(mu);
-        if (!ring && cudaMallocHost((void **)&ring, kRing) != cudaSuccess) return cudaErrorMemoryAllocation;
-        if (ring_off + need > kRing) {
-            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-            cudaStreamIsCapturing(st, &cs);
-            if (cs == cudaStreamCaptureStatusNone) cudaDeviceSynchronize();
-            ring_off = 0;
+    cudaError_t e = cudaSuccess;
+    if (phase & MIXED_A) {   // the product table, then the A slices (W~ / Q~ blocks only)
+        // small tables through pinned host memory: the capturing plan's own
+        // blocks, else a shared ring (copies stay valid until the ring wraps)
+        static std::mutex mu;
+        static char *ring = nullptr;
+        static size_t ring_off = 0;
+        constexpr size_t kRing = 64ull << 20;
+        const size_t need = sizeof(MixProb) * nprobs + 256;
+        if (need > kRing) return cudaErrorInvalidValue;
+        char *h = (char *)plan_pinned_alloc(need);
+        if (!h) {
+            std::lock_guard<std::mutex> lk(mu);
+            if (!ring && cudaMallocHost((void **)&ring, kRing) != cudaSuccess) return cudaErrorMemoryAllocation;
+            if (ring_off + need > kRing) {
+                cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+                cudaStreamIsCapturing(st, &cs);
+                if (cs == cudaStreamCaptureStatusNone) cudaDeviceSynchronize();
+                ring_off = 0;
+            }
+            h = ring + ring_off;
+            ring_off += (need + 255) & ~(size_t)255;
         }
-        h = ring + ring_off;
-        ring_off += (need + 255) & ~(size_t)255;
+        char *hp = h;
+        std::memcpy(hp, hm.data(), sizeof(MixProb) * nprobs);
+        e = cudaMemcpyAsync(dmix, hp, sizeof(MixProb) * nprobs, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return e;
+
+        {   // A operand slicing
+            StageScope slice_scope(st, BDC_STAGE_SLICE, 1, 0.0);
+            for (int p0 = 0; p0 < nprobs; p0 += 65535) {
+                const int np = std::min(nprobs - p0, 65535);
+                k_slice_a<S, EXACT><<<dim3((mrows + 31) / 32, np), 256, 0, st>>>(probs, dmix, p0, As, E, rowsA, Kld);
+                if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            }
+        }
     }
-    char *hp = h;
-    std::memcpy(hp, hm.data(), sizeof(MixProb) * nprobs);
-    cudaError_t e = cudaMemcpyAsync(dmix, hp, sizeof(MixProb) * nprobs, cudaMemcpyHostToDevice, st);
+    if (!(phase & MIXED_B)) return cudaSuccess;
 
     int *ntiles = (int *)(scratch + L.offErr);
     int2 *tlist = (int2 *)(scratch + L.offTiles);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ntiles, 0, sizeof(int), st);   // tile count
-    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(ntiles, 0, sizeof(int), st)) != cudaSuccess) return e;   // tile count
 
-    {   // operand slicing
-        StageScope slice_scope(st, BDC_STAGE_SLICE, 2, 0.0);
+    {   // B operand slicing
+        StageScope slice_scope(st, BDC_STAGE_SLICE, 1, 0.0);
         for (int p0 = 0; p0 < nprobs; p0 += 65535) {
             const int np = std::min(nprobs - p0, 65535);
-            k_slice_a<S, EXACT><<<dim3((mrows + 31) / 32, np), 256, 0, st>>>(probs, dmix, p0, As, E, rowsA, Kld);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
             if (ncols <= 128)
                 k_slice_b<S, EXACT, 8><<<dim3((ncols + 31) / 32, np), 256, 0, st>>>(probs, dmix, p0, Bs, F, colsB, Kld);
             else
@@ -1029,7 +1040,7 @@ size_t gemm_mixed_scratch(long long rows_total, long long cols_total, int kmax, 
 // probs: device problem table (M, N, K known on the device); hm: host layout
 cudaError_t launch_gemm_mixed_tab(const GemmProb *probs, int nprobs, const std::vector<MixProb> &hm, int rowsA,
                                   int colsB, int kmax, int prec, int slices, void *scratch, size_t scratch_bytes,
-                                  int *err, cudaStream_t st) {
+                                  int *err, int phase, cudaStream_t st) {
     if (nprobs <= 0) return cudaSuccess;
     const int S = (prec == BDC_MIXED_BF16X3) ? 2 : slices;
     const int Kld = (kmax + TK - 1) / TK * TK;
@@ -1039,19 +1050,19 @@ cudaError_t launch_gemm_mixed_tab(const GemmProb *probs, int nprobs, const std::
     if (L.total > scratch_bytes) return cudaErrorInvalidValue;
     char *sc = (char *)scratch;
     const int ra = rowsA + TM, cbn = colsB + TN_MAX;
-    if (prec == BDC_MIXED_BF16X3) return run_mixed<2, false>(probs, nprobs, hm, ra, cbn, Kld, sc, L, err, st);
+    if (prec == BDC_MIXED_BF16X3) return run_mixed<2, false>(probs, nprobs, hm, ra, cbn, Kld, sc, L, err, phase, st);
     switch (S) {
-        case 4: return run_mixed<4, true>(probs, nprobs, hm, ra, cbn, Kld, sc, L, err, st);
-        case 5: return run_mixed<5, true>(probs, nprobs, hm, ra, cbn, Kld, sc, L, err, st);
-        case 6: return run_mixed<6, true>(probs, nprobs, hm, ra, cbn, Kld, sc, L, err, st);
-        case 7: return run_mixed<7, true>(probs, nprobs, hm, ra, cbn, Kld, sc, L, err, st);
+        case 4: return run_mixed<4, true>(probs, nprobs, hm, ra, cbn, Kld, sc, L, err, phase, st);
+        case 5: return run_mixed<5, true>(probs, nprobs, hm, ra, cbn, Kld, sc, L, err, phase, st);
+        case 6: return run_mixed<6, true>(probs, nprobs, hm, ra, cbn, Kld, sc, L, err, phase, st);
+        case 7: return run_mixed<7, true>(probs, nprobs, hm, ra, cbn, Kld, sc, L, err, phase, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
 // simple layout: products packed one after another (rows by M bound, columns by N bound)
 cudaError_t launch_gemm_mixed(const GemmProb *probs, int nprobs, const int *Mmax, const int *Nmax, int kmax, int prec,
-                              int slices, void *scratch, size_t scratch_bytes, int *err, cudaStream_t st) {
+                              int slices, void *scratch, size_t scratch_bytes, int *err, int phase, cudaStream_t st) {
     std::vector<MixProb> hm(nprobs);
     int rows = 0, cols = 0, tiles = 0;
     const int tn = TNX;
@@ -1064,7 +1075,8 @@ cudaError_t launch_gemm_mixed(const GemmProb *probs, int nprobs, const int *Mmax
         rows += m.Mmax; cols += m.Nmax;
         hm[p] = m;
     }
-    return launch_gemm_mixed_tab(probs, nprobs, hm, rows, cols, kmax, prec, slices, scratch, scratch_bytes, err, st);
+    return launch_gemm_mixed_tab(probs, nprobs, hm, rows, cols, kmax, prec, slices, scratch, scratch_bytes, err, phase,
+                                 st);
 }
 
 

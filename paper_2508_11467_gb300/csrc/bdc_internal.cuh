@@ -138,6 +138,13 @@ struct NodeState {
 
 // one product C = A * B (column-major, real_t), used by the merge GEMMs;
 // with cmap, column j of the result is stored at C + cmap[j] * ldc
+// Phases of a split-BF16 product launch: MIXED_A uploads the product table
+// and slices the A operands (they need only the gathered W~ / Q~ blocks, so
+// this can run while the roots are found); MIXED_B slices the B operands
+// (U_M, V_M) and runs the tensor-core products.  MIXED_A precedes MIXED_B
+// in stream order.
+enum { MIXED_A = 1, MIXED_B = 2, MIXED_ALL = 3 };
+
 struct GemmProb {
     const real_t *A; const real_t *B; real_t *C;
     int lda, ldb, ldc;
