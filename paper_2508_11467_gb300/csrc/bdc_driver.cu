@@ -775,26 +775,41 @@ int run_plan(const Plan &p, const bdc_opts &o, char *work, std::vector<MatDesc> 
             // states), then the A slices of the split products: they depend
             // on the prep only, so they run on the side stream while the
             // roots, the Loewner z~ and the vectors of M~ are computed (that
-            // FP64 chain leaves most of the GPU idle)
-            if ((e = cudaEventRecord(side->fork, st)) != cudaSuccess ||
-                (e = cudaStreamWaitEvent(side->s, side->fork, 0)) != cudaSuccess)
+            // FP64 chain leaves most of the GPU idle).  The stage profiler
+            // times every stage alone, so it keeps them on the caller's stream.
+            const cudaStream_t gs = g_prof.on ? st : side->s;
+            if (gs != st && ((e = cudaEventRecord(side->fork, st)) != cudaSuccess ||
+                             (e = cudaStreamWaitEvent(gs, side->fork, 0)) != cudaSuccess))
                 return note(e);
             {
-                StageScope sc(side->s, BDC_STAGE_GATHER, 1, 0.0);
-                if ((e = launch_merge_gather(dn, nn, dmats, dstate, mm, side->s)) != cudaSuccess) return note(e);
+                StageScope sc(gs, BDC_STAGE_GATHER, 1, 0.0);
+                if ((e = launch_merge_gather(dn, nn, dmats, dstate, mm, gs)) != cudaSuccess) return note(e);
             }
 #ifndef BDC_FP32
             if (mixed_here &&
                 (e = launch_gemm_mixed(dprobs, 4 * nn, Mx.data(), Nx.data(), mm + 9, o.prec,
                                        o.slices > 0 ? o.slices : 6, work + p.off_mixed, p.mixed_bytes, derr, MIXED_A,
-                                       side->s)) != cudaSuccess)
+                                       gs)) != cudaSuccess)
                 return note(e);
 #endif
-            if ((e = cudaEventRecord(side->join, side->s)) != cudaSuccess) return note(e);
         }
         if ((e = launch_secular(dn, nn, dmats, dstate, mm, max_iter, o.seed, o.mlp, harvest, o.fp32_start, st)) !=
             cudaSuccess)
             return note(e);
+        // the node values and their order need only the roots: on the side
+        // stream after the gather (which reads the children's row ranges that
+        // the finish overwrites), during the Loewner z~ and the vectors
+        const bool overlap = !p.vals && !g_prof.on;
+        if (overlap) {
+            if ((e = cudaEventRecord(side->fork, st)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(side->s, side->fork, 0)) != cudaSuccess)
+                return note(e);
+            {
+                StageScope sc(side->s, BDC_STAGE_FINISH, 1, 24.0 * msum);
+                if ((e = launch_merge_finish(dn, nn, dmats, dstate, mm, side->s)) != cudaSuccess) return note(e);
+            }
+            if ((e = cudaEventRecord(side->join, side->s)) != cudaSuccess) return note(e);
+        }
         if (o.checked &&
             (e = launch_check_roots(dn, nn, dmats, dstate, mm, h + 1 == p.heights.size() && test_corrupt_root(), st)) !=
                 cudaSuccess)
@@ -807,7 +822,7 @@ int run_plan(const Plan &p, const bdc_opts &o, char *work, std::vector<MatDesc> 
             if ((e = launch_vectors(dn, nn, dmats, dstate, mm, st)) != cudaSuccess) return note(e);
         }
         if (!p.vals) {   // 2 M N K per product as deflated, x slice pairs (added from the node states)
-            if ((e = cudaStreamWaitEvent(st, side->join, 0)) != cudaSuccess) return note(e);
+            if (overlap && (e = cudaStreamWaitEvent(st, side->join, 0)) != cudaSuccess) return note(e);
             if (!mixed_here) {
                 StageScope sc(st, BDC_STAGE_GEMM, 1, 0.0);
                 // rows of the four products: nl + 1 (tops), m - nl - 1, m + sqre - nl - 1
@@ -825,7 +840,7 @@ int run_plan(const Plan &p, const bdc_opts &o, char *work, std::vector<MatDesc> 
 #endif
             if (e != cudaSuccess) return note(e);
         }
-        {   // node values and their order (O(m) per merge)
+        if (!overlap) {   // node values and their order (O(m) per merge)
             StageScope sc(st, BDC_STAGE_FINISH, 1, 24.0 * msum);
             if ((e = launch_merge_finish(dn, nn, dmats, dstate, mm, st)) != cudaSuccess) return note(e);
         }
