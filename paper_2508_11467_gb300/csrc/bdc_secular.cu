@@ -88,6 +88,15 @@ __host__ __device__ __forceinline__ int secular_group_warps(int mmax) {
     return (int)(((long long)mmax * secular_group_size(mmax) + 31) / 32);
 }
 
+// Warps per CTA of the lane-group kernels (k_secular, k_lowner,
+// k_vectors_warp, k_rows_update).  Their grids hold the warps of every node's
+// roots in node order, and deflation leaves only the first warps of a node
+// with work, so small CTAs spread the working warps over more SMs and
+// sub-partitions (each sub-partition issues one FP64 warp instruction per
+// ~64 cycles).
+constexpr int kLgWarps = 2;
+constexpr int kLgThreads = 32 * kLgWarps;
+
 struct Sums {
     real_t psi, dpsi, phi, dphi;
 };
@@ -544,7 +553,7 @@ __device__ __forceinline__ void secular_group(const NodeDesc &nd, const MatDesc 
 
 // Warp w of a node (secular_group_warps(mmax) per node) serves roots w * (32 / G) + (lane / G),
 // G = secular_group_size(N) from the node's survivor count, known only here.
-__global__ void __launch_bounds__(256, 2) k_secular(const NodeDesc *__restrict__ nodes,
+__global__ void __launch_bounds__(kLgThreads, 16 / kLgWarps) k_secular(const NodeDesc *__restrict__ nodes,
                                                  const MatDesc *__restrict__ mats,
                                                  NodeState *__restrict__ state, int wpn,
                                                  int max_iter, int nnodes, int seed_mode, int fp32_start) {
@@ -558,7 +567,7 @@ __global__ void __launch_bounds__(256, 2) k_secular(const NodeDesc *__restrict__
     if (i >= N) return;                              // whole groups leave together
     const MatDesc &md = mats[nd.mat];
     const real_t zz = ns.rho;                        // sum z^2 (computed by the merge prep)
-    __shared__ real_t s_lam[8][kLamCache * 32];       // shifted poles of each lane's root (pole_sums)
+    __shared__ real_t s_lam[kLgWarps][kLamCache * 32];   // shifted poles of each lane's root (pole_sums)
     real_t *lc = &s_lam[threadIdx.x >> 5][lane];
     switch (G) {
     case 4: secular_group<4>(nd, md, state, N, zz, i, max_iter, seed_mode, fp32_start, lc); break;
@@ -672,7 +681,7 @@ __device__ __forceinline__ real_t lowner_one(const real_t *__restrict__ d, const
     return (z[i] < R(0.0)) ? -zt : zt;
 }
 
-__global__ void __launch_bounds__(256) k_lowner(const NodeDesc *__restrict__ nodes,
+__global__ void __launch_bounds__(kLgThreads) k_lowner(const NodeDesc *__restrict__ nodes,
                                                 const MatDesc *__restrict__ mats,
                                                 const NodeState *__restrict__ state, int wpn, int nnodes) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
@@ -828,7 +837,7 @@ __device__ __forceinline__ void vectors_warp_long(const real_t *__restrict__ d, 
     }
 }
 
-__global__ void __launch_bounds__(256) k_vectors_warp(const NodeDesc *__restrict__ nodes,
+__global__ void __launch_bounds__(kLgThreads) k_vectors_warp(const NodeDesc *__restrict__ nodes,
                                                       const MatDesc *__restrict__ mats,
                                                       const NodeState *__restrict__ state, int wpn,
                                                       int nnodes) {
@@ -889,7 +898,7 @@ __device__ __forceinline__ void rows_group(const real_t *__restrict__ d, const r
     }
 }
 
-__global__ void __launch_bounds__(256) k_rows_update(const NodeDesc *__restrict__ nodes,
+__global__ void __launch_bounds__(kLgThreads) k_rows_update(const NodeDesc *__restrict__ nodes,
                                                      const MatDesc *__restrict__ mats,
                                                      const NodeState *__restrict__ state, int wpn, int nnodes) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
@@ -953,13 +962,14 @@ cudaError_t launch_secular(const NodeDesc *nodes, int nnodes, const MatDesc *mat
     }
 #endif
     const long long swarps = (long long)nnodes * secular_group_warps(mmax);
-    k_secular<<<(unsigned)((swarps + 7) / 8), 256, 0, st>>>(nodes, mats, state, secular_group_warps(mmax),
-                                                             max_iter, nnodes, seed_mode, fp32_start);
+    k_secular<<<(unsigned)((swarps + kLgWarps - 1) / kLgWarps), kLgThreads, 0, st>>>(
+        nodes, mats, state, secular_group_warps(mmax), max_iter, nnodes, seed_mode, fp32_start);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     }
     StageScope sc(st, BDC_STAGE_LOWNER, 1, 0.0);
-    k_lowner<<<(unsigned)((gwarps + 7) / 8), 256, 0, st>>>(nodes, mats, state, group_warps(mmax), nnodes);
+    k_lowner<<<(unsigned)((gwarps + kLgWarps - 1) / kLgWarps), kLgThreads, 0, st>>>(nodes, mats, state,
+                                                                                   group_warps(mmax), nnodes);
     return cudaGetLastError();
 }
 
@@ -967,7 +977,8 @@ cudaError_t launch_vectors(const NodeDesc *nodes, int nnodes, const MatDesc *mat
                            int mmax, cudaStream_t st) {
     if (nnodes <= 0) return cudaSuccess;
     const long long warps = (long long)nnodes * group_warps(mmax);
-    k_vectors_warp<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(nodes, mats, state, group_warps(mmax), nnodes);
+    k_vectors_warp<<<(unsigned)((warps + kLgWarps - 1) / kLgWarps), kLgThreads, 0, st>>>(nodes, mats, state,
+                                                                                        group_warps(mmax), nnodes);
     return cudaGetLastError();
 }
 
@@ -975,7 +986,8 @@ cudaError_t launch_rows_update(const NodeDesc *nodes, int nnodes, const MatDesc 
                                int mmax, cudaStream_t st) {
     if (nnodes <= 0) return cudaSuccess;
     const long long warps = (long long)nnodes * group_warps(mmax);
-    k_rows_update<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(nodes, mats, state, group_warps(mmax), nnodes);
+    k_rows_update<<<(unsigned)((warps + kLgWarps - 1) / kLgWarps), kLgThreads, 0, st>>>(nodes, mats, state,
+                                                                                       group_warps(mmax), nnodes);
     return cudaGetLastError();
 }
 
