@@ -205,10 +205,89 @@ __device__ int deflate_core(int m, real_t tol, const real_t *ds, real_t *zs, con
     return ns;
 }
 
+// The merged ascending order and z of positions 1..m-1 of the merges of
+// one height, for large merges: the same merge path and z formation as the
+// prep's first two phases, spread over a grid (blockIdx.x = share of the
+// node's positions, blockIdx.y = node; at most ORDER_SPAN positions per
+// thread), each thread forming z at the positions it has just placed, so
+// that the single-CTA prep of a large merge starts at the deflation.
+constexpr int ORDER_THREADS = 256, ORDER_SPAN = 4, ORDER_MIN = 4096;
+
+__global__ void __launch_bounds__(ORDER_THREADS) k_merge_order(const NodeDesc *__restrict__ nodes,
+                                                               const MatDesc *__restrict__ mats) {
+    const NodeDesc nd = nodes[blockIdx.y];
+    const MatDesc &md = mats[nd.mat];
+    const int m = nd.m, nl = nd.nl, nr = m - nl - 1;
+    const int r0 = nd.r0, r0L = r0, r0R = r0 + nl + 1;
+    const long long ld = md.n;
+    const int mt = nl + nr, T = gridDim.x * blockDim.x, t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int S = (mt + T - 1) / T;
+    const int k0 = min(mt, t * S), k1 = min(mt, k0 + S);
+    if (k0 >= k1) return;
+    real_t *ds = md.ds + r0, *zs = md.zs + r0;
+    int *src = md.src + r0;
+    const real_t alpha = md.dsc[r0 + nl], beta = md.esc[r0 + nl];
+    const int *cvs = md.vs[1 - nd.buf];
+    const int *QL = md.Q + r0L, *QR = md.Q + r0R;
+    const real_t *DL = md.D + r0L, *DR = md.D + r0R;
+    int lo = max(0, k0 - nr), hi = min(k0, nl);
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (abits(DL[QL[mid]]) <= abits(DR[QR[k0 - mid - 1]])) lo = mid + 1; else hi = mid;
+    }
+    int i = lo, j = k0 - lo;
+    real_t a = (i < nl) ? DL[QL[i]] : R(INFINITY);
+    real_t b = (j < nr) ? DR[QR[j]] : R(INFINITY);
+    int cs[ORDER_SPAN];
+#pragma unroll
+    for (int u = 0; u < ORDER_SPAN; ++u) {
+        const int k = k0 + u;
+        if (k >= k1) break;
+        if (j >= nr || (i < nl && abits(a) <= abits(b))) {
+            ds[1 + k] = a;
+            cs[u] = 1 + QL[i];
+            ++i;
+            a = (i < nl) ? DL[QL[i]] : R(INFINITY);
+        } else {
+            ds[1 + k] = b;
+            cs[u] = nl + 1 + QR[j];
+            ++j;
+            b = (j < nr) ? DR[QR[j]] : R(INFINITY);
+        }
+        src[1 + k] = cs[u];
+    }
+    // z: alpha times the last row of a left child's right vector, beta times
+    // the first row of a right child's (the loads of the span in flight together)
+    real_t zv[ORDER_SPAN];
+    bool left[ORDER_SPAN];
+#pragma unroll
+    for (int u = 0; u < ORDER_SPAN; ++u) {
+        zv[u] = R(0);
+        left[u] = true;
+        if (k0 + u >= k1) continue;
+        const int c = cs[u];
+        left[u] = c <= nl;
+        const int jx = left[u] ? r0L + c - 1 : r0R + (c - nl - 1);
+        if (md.vals) {
+            zv[u] = left[u] ? md.vl[1 - nd.buf][jx] : md.vf[1 - nd.buf][jx];
+        } else {
+            const int g = cvs[jx];
+            const long long row = left[u] ? r0L + nl : r0R;
+            const real_t v = md.V[(size_t)g * ld + row];
+            zv[u] = (row >= md.vlo[g] && row < md.vhi[g]) ? v : R(0);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < ORDER_SPAN; ++u)
+        if (k0 + u < k1) zs[1 + k0 + u] = (left[u] ? alpha : beta) * zv[u];
+}
+
+// ordered = 1: k_merge_order has written ds, src and zs at positions 1..m-1
 __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__restrict__ nodes,
                                                              const MatDesc *__restrict__ mats,
                                                              NodeState *__restrict__ state,
-                                                             GemmProb *__restrict__ probs, int scans) {
+                                                             GemmProb *__restrict__ probs, int scans,
+                                                             int ordered) {
     __shared__ int wsum[PREP_THREADS / 32 + 1];
     __shared__ real_t dsum[PREP_THREADS / 32 + 1];
     const NodeDesc nd = nodes[blockIdx.x];
@@ -234,7 +313,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
     // (node values are non-negative: they are compared as bit patterns)
     const int *QL = md.Q + r0L, *QR = md.Q + r0R;
     const real_t *DL = md.D + r0L, *DR = md.D + r0R;
-    {
+    if (!ordered) {
         const int mt = nl + nr, S = (mt + T - 1) / T;
         const int k0 = min(mt, t * S), k1 = min(mt, k0 + S);
         if (k0 < k1) {
@@ -270,7 +349,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
     // slot, the slot's range and entry) is loaded for all four before the
     // next, and the slot entry unconditionally (it lies inside the slot
     // column whatever its range), so the loads do not wait on one another.
-    for (int pos0 = 1 + t; pos0 < m; pos0 += 4 * T) {
+    for (int pos0 = 1 + t; !ordered && pos0 < m; pos0 += 4 * T) {
         int jx[4];
         bool left[4];
 #pragma unroll
@@ -834,9 +913,17 @@ __global__ void __launch_bounds__(PREP_THREADS) k_deflate_single(int m, const re
 cudaError_t launch_merge_prep(const NodeDesc *nodes, int nnodes, const MatDesc *mats, NodeState *state,
                               GemmProb *probs, int mmax, int scans, cudaStream_t st) {
     if (nnodes <= 0) return cudaSuccess;
+    // large merges: the merged order and z over a grid first
+    const int ordered = mmax >= ORDER_MIN ? 1 : 0;
+    if (ordered) {
+        const int chunks = (mmax + ORDER_THREADS * ORDER_SPAN - 1) / (ORDER_THREADS * ORDER_SPAN);
+        k_merge_order<<<dim3((unsigned)chunks, (unsigned)nnodes), ORDER_THREADS, 0, st>>>(nodes, mats);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     // a warp per 32 entries of the largest node, up to PREP_THREADS
     const int T = std::min(PREP_THREADS, std::max(32, (mmax + 1 + 31) / 32 * 32));
-    k_merge_prep<<<nnodes, T, 0, st>>>(nodes, mats, state, probs, scans);
+    k_merge_prep<<<nnodes, T, 0, st>>>(nodes, mats, state, probs, scans, ordered);
     return cudaGetLastError();
 }
 
