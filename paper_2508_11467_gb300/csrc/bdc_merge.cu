@@ -8,6 +8,9 @@
 //                typing (top / dense / bottom, the blocks of Eq. bdc-W-Q) and
 //                the K order [top | pad | d_0 column | dense | bottom] used by
 //                the merge products of Eq. (bdc-Mv2Bv-u-vt).
+// k_merge_order  (merges of order >= 4096, a grid per node) the merged order
+//                and z of the prep's first two phases, so that the prep of
+//                those merges starts at the deflation.
 // k_merge_gather (one CTA per column task) applies the rotations and writes
 //                the survivors' vectors W~ (left) and Q~ (right) into the
 //                workspace at their K position, and the deflated vectors and
