@@ -193,6 +193,91 @@ __global__ void __launch_bounds__(32 * WM * WN) k_gemm64(const GemmProb *__restr
     }
 }
 
+// Small blocks (merges whose blocks are at most 64 x 64): one warp per 32 x
+// 32 output tile, four independent tiles (of any problems) per CTA.  The
+// fragments are loaded straight from global memory (L1/L2), one K step of 4
+// ahead of the MMAs, so a tile costs its loads' latency once instead of a
+// shared-memory round trip per K block, and the warp's register budget
+// (<= 128) keeps four CTAs of four warps per SM in flight.  Fragments wholly
+// outside the block are neither loaded nor multiplied (warp-uniform).
+constexpr int SW_WARPS = 4;
+constexpr int kSmallBlock = 64;   // largest block rows / columns served by k_gemm64_warp
+
+__global__ void __launch_bounds__(32 * SW_WARPS, 4) k_gemm64_warp(const GemmProb *__restrict__ probs, int nprobs,
+                                                                   int tilesM, int tilesN) {
+    const int lane = threadIdx.x & 31;
+    const long long gw = (long long)blockIdx.x * SW_WARPS + (threadIdx.x >> 5);
+    const int tiles = tilesM * tilesN;
+    const long long p = gw / tiles;
+    if (p >= nprobs) return;
+    const GemmProb pr = probs[p];
+    const int t = (int)(gw % tiles);
+    const int m0 = (t / tilesN) * 32, n0 = (t % tilesN) * 32;
+    const int M = pr.M, N = pr.N, K = pr.K, lda = pr.lda, ldb = pr.ldb;
+    if (m0 >= M || n0 >= N) return;
+    const int fi = min(4, (M - m0 + 7) >> 3), fj = min(4, (N - n0 + 7) >> 3);   // live fragment rows / columns
+    const int g = lane >> 2, tg = lane & 3;
+    const double *__restrict__ A = pr.A;
+    const double *__restrict__ B = pr.B;
+    double acc[4][4][2];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j][0] = acc[i][j][1] = 0.0;
+    // fragments of K step k: A (row m0 + 8 i + g, column k + tg), B (row k + tg, column n0 + 8 j + g)
+    auto ldf = [&](int k, double (&af)[4], double (&bf)[4]) {
+        const int kk = k + tg;
+        const bool kok = kk < K;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int row = m0 + 8 * i + g;
+            af[i] = (i < fi && kok && row < M) ? A[(size_t)kk * lda + row] : 0.0;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int col = n0 + 8 * j + g;
+            bf[j] = (j < fj && kok && col < N) ? B[(size_t)col * ldb + kk] : 0.0;
+        }
+    };
+    auto mul = [&](const double (&af)[4], const double (&bf)[4]) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (i < fi && j < fj) dmma(acc[i][j], af[i], bf[j]);
+    };
+    double a0[4], b0[4], a1[4], b1[4];
+    ldf(0, a0, b0);
+    for (int k = 0; k < K; k += 8) {
+        if (k + 4 < K) ldf(k + 4, a1, b1);
+        mul(a0, b0);
+        if (k + 4 >= K) break;
+        if (k + 8 < K) ldf(k + 8, a0, b0);
+        mul(a1, b1);
+    }
+    // fragment (g, 2 tg + {0,1}) of each 8 x 8 tile; output columns through the column map
+    double *__restrict__ C = pr.C;
+    size_t col0[4], col1[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int gn = n0 + 8 * j + 2 * tg;
+        col0[j] = (j < fj && gn < N) ? gemm_col(pr, gn) : 0;
+        col1[j] = (j < fj && gn + 1 < N) ? gemm_col(pr, gn + 1) : 0;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int gm = m0 + 8 * i + g;
+        if (i >= fi || gm >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int gn = n0 + 8 * j + 2 * tg;
+            if (j >= fj) continue;
+            if (gn < N) C[col0[j] + gm] = acc[i][j][0];
+            if (gn + 1 < N) C[col1[j] + gm] = acc[i][j][1];
+        }
+    }
+}
+
 #endif  // BDC_FP32
 
 }  // namespace
@@ -202,6 +287,12 @@ cudaError_t launch_gemm64(const GemmProb *probs, int nprobs, int mmax_rows, int 
 #ifdef BDC_FP32
     const int bm = BM, bn = BN;
 #else
+    if (mmax_rows <= kSmallBlock && nmax_cols <= kSmallBlock) {
+        const int tm = (mmax_rows + 31) / 32, tn = (nmax_cols + 31) / 32;
+        const long long warps = (long long)nprobs * tm * tn;
+        k_gemm64_warp<<<(unsigned)((warps + SW_WARPS - 1) / SW_WARPS), 32 * SW_WARPS, 0, st>>>(probs, nprobs, tm, tn);
+        return cudaGetLastError();
+    }
     // 32-row / 32-column tiles when the problems are that small
     const int wm = mmax_rows <= 32 ? 1 : 2, wn = nmax_cols <= 32 ? 1 : 2;
     const int bm = 32 * wm, bn = 32 * wn;
