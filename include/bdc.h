@@ -87,7 +87,7 @@ typedef struct {
                           instead of trapping (0 = off)                   */
     const float *mlp;  /* device pointer to MLP weights when seed = MLP    */
     int mixed_min;     /* split-BF16 products only for merges of order >= mixed_min,
-                          FP64 products below (0 = automatic: 64)           */
+                          FP64 products below (0 = automatic: 128)           */
     int fp32_start;    /* 1: each secular root first iterates in FP32 (the
                           pole sums on FP32 copies of d and z, the two
                           interval poles exact), then finishes in FP64 to the
