@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(32 * WM * WN) k_gemm64(const GemmProb *__restr
 // (<= 128) keeps four CTAs of four warps per SM in flight.  Fragments wholly
 // outside the block are neither loaded nor multiplied (warp-uniform).
 constexpr int SW_WARPS = 4;
-constexpr int kSmallBlock = 64;   // largest block rows / columns served by k_gemm64_warp
+constexpr int kSmallRows = 64, kSmallCols = 64;   // largest blocks served by k_gemm64_warp
 
 __global__ void __launch_bounds__(32 * SW_WARPS, 4) k_gemm64_warp(const GemmProb *__restrict__ probs, int nprobs,
                                                                    int tilesM, int tilesN) {
@@ -287,7 +287,7 @@ cudaError_t launch_gemm64(const GemmProb *probs, int nprobs, int mmax_rows, int 
 #ifdef BDC_FP32
     const int bm = BM, bn = BN;
 #else
-    if (mmax_rows <= kSmallBlock && nmax_cols <= kSmallBlock) {
+    if (mmax_rows <= kSmallRows && nmax_cols <= kSmallCols) {
         const int tm = (mmax_rows + 31) / 32, tn = (nmax_cols + 31) / 32;
         const long long warps = (long long)nprobs * tm * tn;
         k_gemm64_warp<<<(unsigned)((warps + SW_WARPS - 1) / SW_WARPS), 32 * SW_WARPS, 0, st>>>(probs, nprobs, tm, tn);
