@@ -317,6 +317,8 @@ __global__ void __launch_bounds__(256) k_slice_a(const GemmProb *__restrict__ pr
     }
 }
 
+constexpr int kSliceRegs = 16;   // entries per lane held in registers by the one-pass B slicing
+
 // B operand: LANES lanes per column (column-major B is K-contiguous),
 // 32 / LANES columns per warp; grid (columns of the host bound of the
 // largest product / (256 / LANES), products from p0).  K is a merge's
@@ -325,7 +327,9 @@ __global__ void __launch_bounds__(256) k_slice_a(const GemmProb *__restrict__ pr
 // a warp per column for the large ones.  Only the columns the MMA tiles
 // read are written: those below N, and zeros up to N rounded up to the
 // tile width; lanes past them exit (N, the survivor count, is known only on
-// the device and is often far below the host bound)
+// the device and is often far below the host bound).  Columns of up to
+// LANES kSliceRegs entries are read once into registers; longer ones in two
+// passes (maximum, then digits).
 template <int S, bool EXACT, int LANES>
 __global__ void __launch_bounds__(256) k_slice_b(const GemmProb *__restrict__ probs, const MixProb *__restrict__ mix,
                                                 int p0, __nv_bfloat16 *__restrict__ Bs, int *__restrict__ Fb, int colsB,
@@ -340,6 +344,47 @@ __global__ void __launch_bounds__(256) k_slice_b(const GemmProb *__restrict__ pr
     const bool colok = c < pr.N;
     const int K = pr.K;
     const double *col = pr.B + (size_t)c * pr.ldb;
+    __nv_bfloat16 *dst = Bs + (size_t)(mx.b_col0 + c) * Kld;
+    if (K <= LANES * kSliceRegs) {
+        // one pass: the column's entries held in registers (every load issued
+        // before the maximum is needed); K <= LANES kSliceRegs covers Kend
+        double xv[kSliceRegs];
+        unsigned long long m = 0;
+#pragma unroll
+        for (int q = 0; q < kSliceRegs; ++q) {
+            const int k = l + q * LANES;
+            xv[q] = (colok && k < K) ? col[k] : 0.0;
+            const unsigned long long b = (unsigned long long)__double_as_longlong(xv[q]) & 0x7FFFFFFFFFFFFFFFull;
+            m = b > m ? b : m;
+        }
+        int F = 0;
+        if (EXACT) {
+            for (int o = LANES / 2; o > 0; o >>= 1) {
+                const unsigned long long y = __shfl_xor_sync(gmask, m, o);
+                m = y > m ? y : m;
+            }
+            F = scale_exp(m);
+            if (l == 0) Fb[mx.b_col0 + c] = colok ? F : 0;
+        }
+        const int Kend = min(Kld, (K + TK - 1) / TK * TK);
+#pragma unroll
+        for (int q = 0; q < kSliceRegs; ++q) {
+            const int k = l + q * LANES;
+            if (k >= Kend) break;
+            if (EXACT) {
+                int n[S];
+                digits<S>(xv[q], F, n);
+#pragma unroll
+                for (int s2 = 0; s2 < S; ++s2) dst[(size_t)s2 * colsB * Kld + k] = slice_bf16(n[s2], s2);
+            } else {
+                const float xf = (float)xv[q];
+                const __nv_bfloat16 h = __float2bfloat16_rn(xf);
+                dst[k] = h;
+                dst[(size_t)colsB * Kld + k] = __float2bfloat16_rn(xf - __bfloat162float(h));
+            }
+        }
+        return;
+    }
     int F = 0;
     if (EXACT) {
         unsigned long long m = 0;
@@ -356,7 +401,6 @@ __global__ void __launch_bounds__(256) k_slice_b(const GemmProb *__restrict__ pr
         F = scale_exp(m);
         if (l == 0) Fb[mx.b_col0 + c] = colok ? F : 0;
     }
-    __nv_bfloat16 *dst = Bs + (size_t)(mx.b_col0 + c) * Kld;
     const int Kend = min(Kld, (K + TK - 1) / TK * TK);
     #pragma unroll 4
     for (int k = l; k < Kend; k += LANES) {
