@@ -287,6 +287,28 @@ __device__ double grid_partials(const double *part, int count, int stride, doubl
 }
 
 // dot product of x[r] y[r] over r = r0 + lane, r0 + lane + 32, ... < r1 by
+// sum over j < cnt of a[j sa] b[j sb] + c[j sa] d[j sb] (the panel's
+// earlier columns, cnt < b): two independent FMA chains and the loads of
+// eight j in flight, instead of one dependent chain waiting on each j's loads
+__device__ __forceinline__ double dot2(const double *__restrict__ a, const double *__restrict__ b,
+                                       const double *__restrict__ c, const double *__restrict__ d, long long sa,
+                                       long long sb, int cnt) {
+    double s0 = 0.0, s1 = 0.0;
+    int j = 0;
+#pragma unroll 4
+    for (; j + 1 < cnt; j += 2) {
+        s0 = fma(a[j * sa], b[j * sb], s0);
+        s1 = fma(a[(j + 1) * sa], b[(j + 1) * sb], s1);
+        s0 = fma(c[j * sa], d[j * sb], s0);
+        s1 = fma(c[(j + 1) * sa], d[(j + 1) * sb], s1);
+    }
+    if (j < cnt) {
+        s0 = fma(a[j * sa], b[j * sb], s0);
+        s0 = fma(c[j * sa], d[j * sb], s0);
+    }
+    return s0 + s1;
+}
+
 // one warp (result in every lane): four independent accumulators so that
 // four pairs of loads are in flight per lane
 __device__ __forceinline__ double warp_dot(const double *__restrict__ x, const double *__restrict__ y, int r0,
@@ -360,8 +382,7 @@ __global__ void __launch_bounds__(256) k_labrd(LabrdArgs a) {
         double ss = 0.0;
         for (int r = i + gtid; r < m; r += gthreads) {
             double v = A[(size_t)i * lda + r];
-            for (int j = 0; j < i; ++j)
-                v -= V[(size_t)j * m + r] * Y[(size_t)j * n + i] + X[(size_t)j * m + r] * U[(size_t)j * n + i];
+            v -= dot2(V + r, Y + i, X + r, U + i, m, n, i);
             A[(size_t)i * lda + r] = v;
             if (r > i) ss = fma(v, v, ss);
         }
@@ -407,12 +428,11 @@ __global__ void __launch_bounds__(256) k_labrd(LabrdArgs a) {
         ss = 0.0;
         for (int c = i + 1 + gtid; c < n; c += gthreads) {
             double y = a.yraw[c];
-            for (int j = 0; j < i; ++j) y -= Y[(size_t)j * n + c] * t1[j] + U[(size_t)j * n + c] * t2[j];
+            y -= dot2(Y + c, t1, U + c, t2, n, 1, i);
             y *= tau;
             Y[(size_t)i * n + c] = y;
             double v = A[(size_t)c * lda + i] - y;   // V[i][i] = 1
-            for (int j = 0; j < i; ++j)
-                v -= V[(size_t)j * m + i] * Y[(size_t)j * n + c] + X[(size_t)j * m + i] * U[(size_t)j * n + c];
+            v -= dot2(Y + c, V + i, U + c, X + i, n, m, i);
             A[(size_t)c * lda + i] = v;
             if (c > i + 1) ss = fma(v, v, ss);
         }
@@ -467,8 +487,7 @@ __global__ void __launch_bounds__(256) k_labrd(LabrdArgs a) {
         for (int r = i + 1 + gtid; r < m; r += gthreads) {
             double x = 0.0;
             for (int ch = 0; ch < a.chunks; ++ch) x += a.xpart[(size_t)ch * m + r];
-            for (int j = 0; j <= i; ++j) x -= V[(size_t)j * m + r] * t3[j];
-            for (int j = 0; j < i; ++j) x -= X[(size_t)j * m + r] * t4[j];
+            x -= dot2(V + r, t3, X + r, t4, m, 1, i) + V[(size_t)i * m + r] * t3[i];
             X[(size_t)i * m + r] = pi * x;
         }
         if (!grid_sync(a.bar)) return;
