@@ -28,6 +28,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "bdc_internal.cuh"
@@ -651,9 +652,18 @@ cudaError_t apply_block(int left, int trans, int rows, int cols, const double *Y
     const int ry = left ? rows : cols;   // rows of Y
     cudaError_t e = dgemm(1, 0, nb, nb, ry, 1.0, Y, ry, Y, ry, 0.0, Ti, nb, st);
     if (e != cudaSuccess) return e;
-    k_tinv_diag<<<1, 64, 0, st>>>(Ti, nb, tau);
+    k_tinv_diag<<<1, ((nb + 31) / 32) * 32, 0, st>>>(Ti, nb, tau);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const size_t smem = sizeof(double) * nb * nb;
+    if (smem > 48 * 1024) {   // T^{-1} above the static limit: opt in to more dynamic shared memory
+        static std::once_flag once;
+        static cudaError_t attr = cudaSuccess;
+        std::call_once(once, [] {
+            attr = cudaFuncSetAttribute(k_tsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        });
+        if (attr != cudaSuccess) return attr;
+        if (smem > 200 * 1024) return cudaErrorInvalidValue;
+    }
     if (left) {
         if ((e = dgemm(1, 0, nb, cols, rows, 1.0, Y, rows, C, ldc, 0.0, Z, nb, st)) != cudaSuccess) return e;
         k_tsolve<<<(cols + 127) / 128, 128, smem, st>>>(Ti, nb, Z, nb, cols, trans ? 1 : 0);
@@ -919,6 +929,11 @@ using namespace bdc;
 namespace {
 
 constexpr int kDenseBlock = 32;   // b: columns / rows per panel (reflectors per block)
+// reflectors per block when they are applied (back-transformation, explicit
+// Q): wider blocks pass over C fewer times (Z = Y^T C and C -= Y W with
+// K = kApplyBlock); T^{-1} (kApplyBlock^2 doubles) stays in shared memory
+constexpr int kApplyBlock = 64;
+constexpr int kWsBlock = kApplyBlock > kDenseBlock ? kApplyBlock : kDenseBlock;   // workspace sizing
 constexpr double kQrRatio = 1.6;  // m >= 1.6 n: QR first (Sec. 4.3)
 
 char *align_ws(void *work) { return (char *)(((uintptr_t)work + 255) & ~(uintptr_t)255); }
@@ -931,7 +946,7 @@ struct GesvdWs {
 GesvdWs gesvd_layout(int m, int n, const bdc_opts *o) {
     GesvdWs w{};
     size_t off = 0;
-    w.dense = off; off += al256(dense_ws_bytes(m, n, kDenseBlock));
+    w.dense = off; off += al256(dense_ws_bytes(m, n, kWsBlock));
     w.vecs = off; off += al256(sizeof(double) * 4 * (size_t)n + 64);
     const bool qr = m >= kQrRatio * n;
     w.R = off; off += qr ? al256(sizeof(double) * (size_t)n * n) : 0;
@@ -947,7 +962,7 @@ extern "C" {
 
 size_t bdc_gebrd_workspace(int m, int n) {
     if (m < n || n < 0) return 0;
-    return dense_ws_bytes(m, n, kDenseBlock) + 512;
+    return dense_ws_bytes(m, n, kWsBlock) + 512;
 }
 
 int bdc_gebrd(int m, int n, double *A, int lda, double *d, double *e, double *tauq, double *taup, void *work,
@@ -982,20 +997,20 @@ int bdc_ormbr(int vect, int m, int n, const double *A, int lda, const double *ta
     if (ldc < std::max(1, vect == 0 ? m : cdim)) return -8;
     if (n == 0 || cdim == 0) return 0;
     if (!work) return -10;
-    const size_t need = dense_ws_bytes(std::max(m, cdim), std::max(n, cdim), kDenseBlock) + 512;
+    const size_t need = dense_ws_bytes(std::max(m, cdim), std::max(n, cdim), kWsBlock) + 512;
     if (lwork < need) return -11;
-    return note_cuda(dense_ormbr(vect, m, n, A, lda, tau, C, ldc, cdim, kDenseBlock, align_ws(work),
+    return note_cuda(dense_ormbr(vect, m, n, A, lda, tau, C, ldc, cdim, kApplyBlock, align_ws(work),
                                  (cudaStream_t)stream));
 }
 
 size_t bdc_ormbr_workspace(int m, int n, int cdim) {
     if (m < n || n < 0 || cdim < 0) return 0;
-    return dense_ws_bytes(std::max(m, cdim), std::max(n, cdim), kDenseBlock) + 512;
+    return dense_ws_bytes(std::max(m, cdim), std::max(n, cdim), kWsBlock) + 512;
 }
 
 size_t bdc_geqrf_workspace(int m, int n) {
     if (m < 0 || n < 0) return 0;
-    return dense_ws_bytes(std::max(m, 1), std::max(n, 1), kDenseBlock) + 512;
+    return dense_ws_bytes(std::max(m, 1), std::max(n, 1), kWsBlock) + 512;
 }
 
 int bdc_geqrf(int m, int n, double *A, int lda, double *tau, void *work, size_t lwork, int *d_info,
@@ -1026,7 +1041,7 @@ int bdc_orgqr(int m, int n, double *A, int lda, const double *tau, void *work, s
     if (n == 0) return 0;
     if (!work) return -6;
     if (lwork < bdc_geqrf_workspace(m, n)) return -7;
-    return note_cuda(dense_orgqr(m, n, n, A, lda, tau, kDenseBlock, align_ws(work), (cudaStream_t)stream));
+    return note_cuda(dense_orgqr(m, n, n, A, lda, tau, kApplyBlock, align_ws(work), (cudaStream_t)stream));
 }
 
 size_t bdc_gesvd_workspace(int m, int n, const bdc_opts *o) {
@@ -1064,19 +1079,19 @@ int bdc_gesvd(int m, int n, double *A, int lda, double *S, double *U, int ldu, d
         double *R = (double *)(ws + L.R), *UR = (double *)(ws + L.UR);
         if ((rc = note_cuda(dense_geqrf(m, n, A, lda, tq, b, dws, st)))) return rc;
         if ((rc = note_cuda(dense_copy_upper(A, lda, R, n, n, st)))) return rc;
-        if ((rc = note_cuda(dense_orgqr(m, n, n, A, lda, tq, b, dws, st)))) return rc;
+        if ((rc = note_cuda(dense_orgqr(m, n, n, A, lda, tq, kApplyBlock, dws, st)))) return rc;
         if ((rc = note_cuda(cudaMemsetAsync(tq, 0, sizeof(double) * n, st)))) return rc;
         if ((rc = note_cuda(dense_gebrd(n, n, R, n, d, e, tq, tp, b, dws, st)))) return rc;
         if ((rc = bdc_svd_ex(n, d, e, UR, S, VT, n, ldvt, o, ws + L.bdc, lwb, d_info, stream))) return rc;
-        if ((rc = note_cuda(dense_ormbr(0, n, n, R, n, tq, UR, n, n, b, dws, st)))) return rc;
-        if ((rc = note_cuda(dense_ormbr(1, n, n, R, n, tp, VT, ldvt, n, b, dws, st)))) return rc;
+        if ((rc = note_cuda(dense_ormbr(0, n, n, R, n, tq, UR, n, n, kApplyBlock, dws, st)))) return rc;
+        if ((rc = note_cuda(dense_ormbr(1, n, n, R, n, tp, VT, ldvt, n, kApplyBlock, dws, st)))) return rc;
         if ((rc = note_cuda(dense_dgemm(0, 0, m, n, n, 1.0, A, lda, UR, n, 0.0, U, ldu, st)))) return rc;
     } else {
         if ((rc = note_cuda(dense_gebrd(m, n, A, lda, d, e, tq, tp, b, dws, st)))) return rc;
         if ((rc = bdc_svd_ex(n, d, e, U, S, VT, ldu, ldvt, o, ws + L.bdc, lwb, d_info, stream))) return rc;
         if ((rc = note_cuda(dense_zero_rows(U, ldu, n, m, n, st)))) return rc;
-        if ((rc = note_cuda(dense_ormbr(0, m, n, A, lda, tq, U, ldu, n, b, dws, st)))) return rc;
-        if ((rc = note_cuda(dense_ormbr(1, m, n, A, lda, tp, VT, ldvt, n, b, dws, st)))) return rc;
+        if ((rc = note_cuda(dense_ormbr(0, m, n, A, lda, tq, U, ldu, n, kApplyBlock, dws, st)))) return rc;
+        if ((rc = note_cuda(dense_ormbr(1, m, n, A, lda, tp, VT, ldvt, n, kApplyBlock, dws, st)))) return rc;
     }
     return note_cuda(dense_read_err(dws, d_info, st));
 }
