@@ -797,6 +797,7 @@ cudaError_t dense_gebrd(int m, int n, double *A, int lda, double *d, double *e, 
 // QR (Sec. 4.3): per panel, k_geqr2 and the update of the trailing columns by
 // H^T = I - Y T^T Y^T in modified compact WY
 cudaError_t dense_geqrf(int m, int n, double *A, int lda, double *tau, int b, char *ws, cudaStream_t st) {
+    if (b < 1 || b > 32) return cudaErrorInvalidValue;   // k_geqr2: a lane per later panel column
     const DenseWs w = dense_ws(m, n, b, n);
     SplitScope split_scope(ws, w);
     GridBar *bar = (GridBar *)(ws + w.bar);
