@@ -434,10 +434,13 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
         return (code == ROLE_ZERO) ? 4 : 5;
     };
     int cnt[6] = {0, 0, 0, 0, 0, 0};             // this warp's counts (lane 0 keeps them)
+    int rnext = (wb + lane < we) ? role[wb + lane] : 0;   // the next chunk's roles, loaded one chunk ahead
     for (int p0 = wb; p0 < we; p0 += 32) {
         const int p = p0 + lane;
+        const int rp = rnext;
+        if (p + 32 < we) rnext = role[p + 32];
         int grp = -1, cat = -1;
-        if (p < we) cat = category(p, role[p], grp);
+        if (p < we) cat = category(p, rp, grp);
         cnt[0] += __popc(__ballot_sync(0xffffffffu, cat == 0));
         cnt[1] += __popc(__ballot_sync(0xffffffffu, cat == 0 && grp == 1));
         cnt[2] += __popc(__ballot_sync(0xffffffffu, cat == 0 && grp == 3));
@@ -466,16 +469,31 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
     int *nus = slots ? md.us[nd.buf] + r0 : nullptr, *nvs = slots ? md.vs[nd.buf] + r0 : nullptr;
     auto slot_u = [&](int c) { return c == 0 ? r0 + nl : (c <= nl ? cus[r0L + c - 1] : cus[r0R + (c - nl - 1)]); };
     auto slot_v = [&](int c) { return c == 0 ? cvs[r0L + nl] : (c <= nl ? cvs[r0L + c - 1] : cvs[r0R + (c - nl - 1)]); };
+    // software pipeline over the chunks (nothing read here is written in
+    // this loop): the roles, values and sources two chunks ahead and the
+    // slots of the next chunk's sources are loaded before this chunk's stores
+    auto ld_pos = [&](int q, int &rq, real_t &dq, real_t &zq, int &cq) {
+        if (q < we) { rq = role[q]; dq = ds[q]; zq = zs[q]; cq = slots ? src[q] : 0; }
+    };
+    int r1 = 0, c1 = 0, r2 = 0, c2 = 0, su1 = 0, sv1 = 0;
+    real_t d1 = R(0), z1 = R(0), d2 = R(0), z2 = R(0);
+    ld_pos(wb + lane, r1, d1, z1, c1);
+    if (slots && wb + lane < we) { su1 = slot_u(c1); sv1 = slot_v(c1); }
+    ld_pos(wb + 32 + lane, r2, d2, z2, c2);
     for (int p0 = wb; p0 < we; p0 += 32) {
         const int p = p0 + lane;
         const bool in = p < we;
-        int grp = -1, cat = -1, su = 0, sv = 0;
+        const int rp = r1, su = su1, sv = sv1;
+        const real_t dp = d1, zp = z1;
+        r1 = r2; d1 = d2; z1 = z2; c1 = c2;
+        if (slots && p + 32 < we) { su1 = slot_u(c1); sv1 = slot_v(c1); }
+        ld_pos(p + 64, r2, d2, z2, c2);
+        int grp = -1, cat = -1;
         real_t dsp = R(0), zsp = R(0);
         if (in) {
-            cat = category(p, role[p], grp);
-            dsp = ds[p];
-            zsp = zs[p];
-            if (slots) { const int c = src[p]; su = slot_u(c); sv = slot_v(c); }
+            cat = category(p, rp, grp);
+            dsp = dp;
+            zsp = zp;
         }
         const unsigned bk = __ballot_sync(0xffffffffu, cat == 0), b1 = __ballot_sync(0xffffffffu, cat == 0 && grp == 1),
                        b2 = __ballot_sync(0xffffffffu, cat == 0 && grp == 3),
