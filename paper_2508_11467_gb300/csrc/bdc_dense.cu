@@ -760,6 +760,8 @@ cudaError_t launch_coop(const void *fn, int grid, void *args, cudaStream_t st) {
 // ---------------------------------------------------------------- drivers
 // Bidiagonalization, Algorithm 1 (m >= n): per panel of b, k_labrd, then the
 // merged rank-(2b) update of the trailing matrix (one product).
+constexpr long long kLabrdWork = 8192;   // trailing-matrix entries per CTA of the panel kernel
+
 cudaError_t dense_gebrd(int m, int n, double *A, int lda, double *d, double *e, double *tauq, double *taup, int b,
                         char *ws, cudaStream_t st) {
     const DenseWs w = dense_ws(m, n, b, n);
@@ -770,11 +772,11 @@ cudaError_t dense_gebrd(int m, int n, double *A, int lda, double *d, double *e, 
     // CTAs by the work of a step (the products with the trailing matrix,
     // ~m n FMAs): every barrier costs more with more CTAs, and a small
     // trailing matrix cannot use the whole GPU
-    const long long mn = (long long)m * n;
-    const int grid = (int)std::max<long long>(
-        8, std::min<long long>(std::min(coop_blocks((const void *)k_labrd, 256, 0), 4 * 256), mn / 32768));
+    const int gmax = std::min(coop_blocks((const void *)k_labrd, 256, 0), 4 * 256);
     for (int i0 = 0; i0 < n; i0 += b) {
         const int nb = std::min(b, n - i0), ml = m - i0, nl = n - i0;
+        // per panel, by the work of its steps (~ml nl FMAs each)
+        const int grid = (int)std::max<long long>(8, std::min<long long>(gmax, (long long)ml * nl / kLabrdWork));
         LabrdArgs a{A + i0 + (size_t)i0 * lda, lda, ml, nl, nb, b,
                     d + i0, e + i0, tauq + i0, taup + i0,
                     (double *)(ws + w.PW), (double *)(ws + w.QW), (double *)(ws + w.yraw), (double *)(ws + w.tv),
