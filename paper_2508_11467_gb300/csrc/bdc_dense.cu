@@ -769,13 +769,12 @@ cudaError_t dense_gebrd(int m, int n, double *A, int lda, double *d, double *e, 
     GridBar *bar = (GridBar *)(ws + w.bar);
     cudaError_t err = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st);   // count, gen (not the error word)
     if (err != cudaSuccess) return err;
-    // CTAs by the work of a step (the products with the trailing matrix,
-    // ~m n FMAs): every barrier costs more with more CTAs, and a small
-    // trailing matrix cannot use the whole GPU
+    // CTAs per panel by the work of its steps (the products with the
+    // trailing matrix, ~ml nl FMAs): a small trailing matrix cannot use the
+    // whole GPU, and every barrier costs more with more CTAs
     const int gmax = std::min(coop_blocks((const void *)k_labrd, 256, 0), 4 * 256);
     for (int i0 = 0; i0 < n; i0 += b) {
         const int nb = std::min(b, n - i0), ml = m - i0, nl = n - i0;
-        // per panel, by the work of its steps (~ml nl FMAs each)
         const int grid = (int)std::max<long long>(8, std::min<long long>(gmax, (long long)ml * nl / kLabrdWork));
         LabrdArgs a{A + i0 + (size_t)i0 * lda, lda, ml, nl, nb, b,
                     d + i0, e + i0, tauq + i0, taup + i0,
