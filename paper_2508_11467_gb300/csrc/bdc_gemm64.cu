@@ -98,11 +98,14 @@ __device__ __forceinline__ void dmma(double (&c)[2], double a, double b) {
                  : "d"(a), "d"(b));
 }
 
-// CTA tile (32 WM) x (32 WN): WM x WN warps of 32 x 32 each; the small
+// CTA tile (32 WM) x (32 WN): WM x WN warps of 32 x 32 each, registers
+// capped so that twelve warps fit an SM (three 2 x 2 CTAs; measured: two
+// CTAs of 206 registers 29.7 ms of FP64 products at n = 16384, three 29.0,
+// four with spills 29.2); the small
 // tiles serve merges whose blocks are a few dozen rows (a 64 x 64 tile
 // there multiplies mostly zeros at GB300's modest FP64 tensor rate)
 template <int WM, int WN>
-__global__ void __launch_bounds__(32 * WM * WN) k_gemm64(const GemmProb *__restrict__ probs, int tilesN) {
+__global__ void __launch_bounds__(32 * WM * WN, 3 * 4 / (WM * WN)) k_gemm64(const GemmProb *__restrict__ probs, int tilesN) {
     constexpr int BM = 32 * WM, BN = 32 * WN, T = 32 * WM * WN;
     constexpr int SA = BM + 8;   // As[k][m] row stride (doubles)
     constexpr int SB = BK + 4;   // Bs[n][k] row stride
