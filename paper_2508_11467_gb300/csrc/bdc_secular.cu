@@ -636,8 +636,9 @@ __global__ void __launch_bounds__(256) k_mlp_features_single(int N, const double
 // |z~_i|^2 of Eq. (bdc-zi), 0-based: (w_{N-1}^2 - d_i^2) *
 //   prod_{k<i} (w_k^2 - d_i^2)/(d_k^2 - d_i^2) * prod_{i<=k<N-1} (w_k^2 - d_i^2)/(d_{k+1}^2 - d_i^2)
 // by a group of G lanes.  FP64: numerators and denominators are multiplied
-// separately and divided once per 8 factors (a division costs about nine
-// FP64 operations on GB300), sooner when either product falls below
+// separately and divided once per 8 factors (by the reciprocal-estimate
+// quotient `quot`: four FP64 operations where a division costs about nine on
+// GB300), sooner when either product falls below
 // 2^-300; every factor of the product lies in (0, 1] by interlacing.
 template <int G>
 __device__ __forceinline__ real_t lowner_one(const real_t *__restrict__ d, const real_t *__restrict__ z,
@@ -667,12 +668,12 @@ __device__ __forceinline__ real_t lowner_one(const real_t *__restrict__ d, const
         den *= (d[kk] - di) * (d[kk] + di);
         if (++cnt == 8 || (__double_as_longlong(num) & 0x7fffffffffffffffll) < kLow ||
             (__double_as_longlong(den) & 0x7fffffffffffffffll) < kLow) {
-            prod *= num / den;
+            prod *= quot(num, den);
             num = den = 1.0;
             cnt = 0;
         }
     }
-    if (cnt) prod *= num / den;
+    if (cnt) prod *= quot(num, den);
 #endif
     prod = group_prod<G>(prod);
     const int oN = org[N - 1];
