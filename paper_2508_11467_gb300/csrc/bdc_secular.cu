@@ -188,6 +188,14 @@ struct RootState {
 // last root (psi: every pole but the origin, lumped at lamL = d_{N-2}^2 -
 // d_{N-1}^2; phi: the origin term alone, exact) the one right of 0.
 // Returns NaN when the model has no such root.
+// the model step's quotients: FP32 (the pre-iterations) as written, FP64 by
+// the reciprocal-estimate quotient (within about an ulp; the iteration
+// corrects its own rounding, the stopping rule is on f)
+__device__ __forceinline__ float mdiv(float a, float b) { return a / b; }
+#ifndef BDC_FP32
+__device__ __forceinline__ double mdiv(double a, double b) { return quot(a, b); }
+#endif
+
 template <typename T>
 __device__ __forceinline__ T model_next(T f, T dpsi, T dphi, T x, T lamL, T lamR, bool last) {
     const T DL = lamL - x, DR = lamR - x;
@@ -196,13 +204,13 @@ __device__ __forceinline__ T model_next(T f, T dpsi, T dphi, T x, T lamL, T lamR
     const T a = C * (lamL + lamR) + sL + sR;
     const T b = sL * lamR + sR * lamL;
     if (!last) {
-        if (C == T(0)) return b / a;
+        if (C == T(0)) return mdiv(b, a);
         const T disc = sqrt(fabs(a * a - T(4) * b * C));
-        return (a > T(0)) ? (T(2) * b / (a + disc)) : ((a - disc) / (T(2) * C));
+        return (a > T(0)) ? mdiv(T(2) * b, a + disc) : mdiv(a - disc, T(2) * C);
     }
     if (!(C > T(0))) return T(NAN);
     const T disc = sqrt(fabs(a * a - T(4) * b * C));
-    return (a >= T(0)) ? ((a + disc) / (T(2) * C)) : (T(2) * b / (a - disc));
+    return (a >= T(0)) ? mdiv(a + disc, T(2) * C) : mdiv(T(2) * b, a - disc);
 }
 
 // Safeguarded rational iteration from r.x; returns the iterations used or
