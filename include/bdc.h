@@ -142,7 +142,15 @@ size_t bdc_svd_workspace(int n, const bdc_opts *o);
  * 256-byte aligned, at least bdc_svd_workspace(n, o)) and `d_info` (device
  * int): the status code above is written to *d_info on the stream, so the
  * whole call can be captured in a CUDA graph.  The host return value only
- * reports argument errors and launch failures. */
+ * reports argument errors and launch failures.
+ * Streams: the solves with vectors (this call, bdc_svd, the batched forms
+ * and plans) run part of each merge (the gather, the A-operand slicing, the
+ * node finish) on a second stream that the library keeps per host thread
+ * and device; it forks from `stream` by an event and joins back by an event
+ * before the merge's products, so all of the call's work is ordered before
+ * later work on `stream`, and a capture of the call records both streams
+ * into the caller's graph.  Its handles live as long as the thread, like
+ * the library's other caches (not valid after cudaDeviceReset). */
 int bdc_svd_ex(int n, const double *d, const double *e, double *U, double *S, double *VT,
                int ldu, int ldvt, const bdc_opts *o, void *work, size_t lwork,
                int *d_info, bdc_stream_t stream);
