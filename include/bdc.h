@@ -16,8 +16,9 @@
  *     n x n with leading dimension ldvt >= max(1, n): row i is the right
  *     singular vector of s_i.
  *   - Unless stated otherwise every pointer is a DEVICE pointer owned by the
- *     caller; inputs are read only.  The library keeps no pointer after a
- *     call returns and holds no state between calls.
+ *     caller; inputs are read only.  The library keeps no pointer to caller
+ *     data after a call returns; between calls it keeps only caches (launch
+ *     descriptors, pinned staging blocks, a second stream per host thread).
  *   - Return codes: 0 success; -i when argument i (1-based) is illegal;
  *     +k (k > 0) when k leaf QR iterations or secular roots failed to
  *     converge (results are then not reliable); BDC_ERR_CUDA for a CUDA
@@ -26,7 +27,10 @@
  *     of its own, negative, so that it cannot be read as a count of
  *     non-converged problems); BDC_ERR_CHECK when checked mode found a
  *     violated invariant.
- *   - Streams: all work is enqueued on `stream` (0 = legacy default).
+ *   - Streams: all work is ordered on `stream` (0 = legacy default); the
+ *     solves with vectors also run part of each merge on a per-thread second
+ *     stream forked from and joined back to `stream` by events (see
+ *     bdc_svd_ex).
  */
 #ifndef BDC_H
 #define BDC_H
