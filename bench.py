@@ -79,6 +79,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--oracle-timing", action="store_true",
+                    help="only the host oracle: QR with U,V at n = 256 and 4096 (configs 1 and 2, their three "
+                         "seeded inputs), one core each and all three on three cores; one JSON line, no GPU")
     return ap.parse_args()
 
 
@@ -216,6 +219,23 @@ def cpu_baseline_measured(kind, n, seed, d, e, sigma_seconds):
                                        f"matrices (seeds {seed}..{seed + cores - 1}) on {cores} cores"},
             "with_vectors_n3_extrapolated_to_n_s_1core": {"value": t1 * (n / nv) ** 3, "model": "s_1core x (n/1024)^3",
                                                            "measured": False}}
+
+
+def run_oracle_timing():
+    """The FP64 QR oracle with vectors at the sizes of configs 1 and 2 (n = 256
+    and 4096: uniform seed 0, graded seed 1, clustered seed 2), each matrix on
+    one core, and the three of a size on three cores at once (one matrix per
+    core).  Measured once, separately from the default bench line (the three
+    n = 4096 solves take minutes)."""
+    aff = host_cores()
+    out = {"impl": "oracle-timing", "nproc": os.cpu_count(), "affinity": f"{len(aff)} cores ({aff[0]}..{aff[-1]})",
+           "kind": "oracle", "unit": "s", "sizes": {}}
+    cases = [("uniform", 0), ("graded", 1), ("clustered", 2)]
+    for n in (256, 4096):
+        one = {f"{kind} seed {seed}": _oracle_full_job((kind, n, seed)) for kind, seed in cases}
+        wall, per = oracle_parallel(_oracle_full_job, [(kind, n, seed) for kind, seed in cases], len(cases))
+        out["sizes"][str(n)] = {"s_1core": one, "s_3_matrices_on_3_cores": wall, "per_job_s": per}
+    print(json.dumps(out), flush=True)
 
 
 def max_over_ranks(x: float, world: int, device) -> float:
@@ -585,6 +605,9 @@ def stage_table(prof, steps, peaks, clock_mhz, fp64_products):
 
 def main():
     a = parse()
+    if a.oracle_timing:
+        run_oracle_timing()
+        return
     if a.batched and a.impl != "reference":
         if int(os.environ.get("WORLD_SIZE", "1")) > 1:
             raise SystemExit("--batched measures one GPU; run it without torchrun")
