@@ -871,28 +871,31 @@ __global__ void __launch_bounds__(128) k_gather_rows(const NodeDesc *__restrict_
 // ------------------------------------------------------------------ finish
 // node values (roots, then deflated values) and their ascending order; the
 // vectors are already in place (products and gather write the node block)
+// grid (share of the node's positions, node): one CTA per node, or several
+// for large merges (the entries are independent)
 __global__ void __launch_bounds__(256) k_merge_finish(const NodeDesc *__restrict__ nodes,
                                                       const MatDesc *__restrict__ mats,
                                                       const NodeState *__restrict__ state) {
-    const NodeDesc nd = nodes[blockIdx.x];
+    const NodeDesc nd = nodes[blockIdx.y];
     const MatDesc &md = mats[nd.mat];
     const NodeState ns = state[nd.id];
     const int r0 = nd.r0, N = ns.N, ndef = ns.ndef;
     const real_t *om = md.omega + r0, *dv = md.dval + r0;
+    const int T = gridDim.x * blockDim.x, t = blockIdx.x * blockDim.x + threadIdx.x;
     if (!md.vals) {
         // the products wrote the survivors' columns over the node's rows
-        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        for (int i = t; i < N; i += T) {
             const int gu = md.us[nd.buf][r0 + i], gv = md.vs[nd.buf][r0 + i];
             md.ulo[gu] = r0; md.uhi[gu] = r0 + nd.m;
             md.vlo[gv] = r0; md.vhi[gv] = r0 + nd.m + nd.sqre;
         }
     }
-    for (int i = threadIdx.x; i < N; i += blockDim.x) md.D[r0 + i] = om[i];
-    for (int s = threadIdx.x; s < ndef; s += blockDim.x) md.D[r0 + N + s] = dv[s];
+    for (int i = t; i < N; i += T) md.D[r0 + i] = om[i];
+    for (int s2 = t; s2 < ndef; s2 += T) md.D[r0 + N + s2] = dv[s2];
     // ascending order of roots (ascending) and deflated values (ascending),
     // roots first on ties: merge path, an equal share of positions per thread
-    const int mt = N + ndef, T = blockDim.x, S = (mt + T - 1) / T;
-    const int k0 = min(mt, (int)threadIdx.x * S), k1 = min(mt, k0 + S);
+    const int mt = N + ndef, S = (mt + T - 1) / T;
+    const int k0 = min(mt, t * S), k1 = min(mt, k0 + S);
     if (k0 < k1) {
         int lo = max(0, k0 - ndef), hi = min(k0, N);
         while (lo < hi) {
@@ -938,9 +941,12 @@ cudaError_t launch_merge_prep(const NodeDesc *nodes, int nnodes, const MatDesc *
     const int ordered = mmax >= ORDER_MIN ? 1 : 0;
     if (ordered) {
         const int chunks = (mmax + ORDER_THREADS * ORDER_SPAN - 1) / (ORDER_THREADS * ORDER_SPAN);
-        k_merge_order<<<dim3((unsigned)chunks, (unsigned)nnodes), ORDER_THREADS, 0, st>>>(nodes, mats);
-        const cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
+        for (int n0 = 0; n0 < nnodes; n0 += 65535) {     // grid y: at most 65535 nodes per launch
+            const int nn = std::min(65535, nnodes - n0);
+            k_merge_order<<<dim3((unsigned)chunks, (unsigned)nn), ORDER_THREADS, 0, st>>>(nodes + n0, mats);
+            const cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
     }
     // a warp per 32 entries of the largest node, up to PREP_THREADS
     const int T = std::min(PREP_THREADS, std::max(32, (mmax + 1 + 31) / 32 * 32));
@@ -973,8 +979,14 @@ cudaError_t launch_merge_finish(const NodeDesc *nodes, int nnodes, const MatDesc
                                 const NodeState *state, int mmax, cudaStream_t st) {
     if (nnodes <= 0) return cudaSuccess;
     const int T = std::min(256, std::max(32, (mmax + 31) / 32 * 32));
-    k_merge_finish<<<(unsigned)nnodes, T, 0, st>>>(nodes, mats, state);
-    return cudaGetLastError();
+    const int chunks = std::max(1, mmax / (16 * 256));   // about 16 positions per thread for large merges
+    for (int n0 = 0; n0 < nnodes; n0 += 65535) {         // grid y: at most 65535 nodes per launch
+        const int nn = std::min(65535, nnodes - n0);
+        k_merge_finish<<<dim3((unsigned)chunks, (unsigned)nn), T, 0, st>>>(nodes + n0, mats, state);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 #ifndef BDC_FP32
