@@ -280,26 +280,35 @@ __device__ __forceinline__ real_t scale_pow2(real_t v, int ex) {
 
 // Scale by the power of two 2^ex <= max |entry| < 2^(ex+1): exact (no
 // rounding in or out).  The maximum and the finiteness test are taken on
-// the bit patterns (integer comparisons).
+// the bit patterns (integer comparisons).  One CTA reads the whole matrix,
+// so latency, not bandwidth, bounds both loops: the descriptor's fields are
+// read once into registers (the stores of the scaled copies could alias
+// the descriptor, so fields read through it would be reloaded after every
+// store), and four entries of d and of e per thread are in flight.
 __global__ void __launch_bounds__(1024) k_scale(const MatDesc *__restrict__ mats) {
     __shared__ rbits_t sh[32];
     const MatDesc &md = mats[blockIdx.x];
-    const int n = md.n;
+    const int n = md.n, rev = md.rev;
+    const real_t *__restrict__ din = md.d_in;
+    const real_t *__restrict__ ein = md.e_in;
+    real_t *__restrict__ dsc = md.dsc;
+    real_t *__restrict__ esc = md.esc;
+    real_t *scale = md.scale;
+    int *info = md.info;
     constexpr rbits_t kInfBits = (rbits_t)kExpMax << kMantBits;   // |v| bits >= this: Inf or NaN
-    rbits_t mx = 0;
-    // four entries of d and of e per thread in flight (one CTA reads the
-    // whole matrix: latency, not bandwidth, bounds this loop)
+    constexpr int U = 4;
     const int T = blockDim.x;
-    for (int i0 = threadIdx.x; i0 < n; i0 += 4 * T) {
-        real_t v[4], w[4];
+    rbits_t mx = 0;
+    for (int i0 = threadIdx.x; i0 < n; i0 += U * T) {
+        real_t v[U], w[U];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < U; ++u) {
             const int i = i0 + u * T;
-            v[u] = (i < n) ? md.d_in[i] : R(0);
-            w[u] = (i + 1 < n) ? md.e_in[i] : R(0);
+            v[u] = (i < n) ? din[i] : R(0);
+            w[u] = (i + 1 < n) ? ein[i] : R(0);
         }   // (the maximum does not depend on the order: rev reads below)
 #pragma unroll
-        for (int u = 0; u < 4; ++u) mx = max(mx, max(abits(v[u]), abits(w[u])));
+        for (int u = 0; u < U; ++u) mx = max(mx, max(abits(v[u]), abits(w[u])));
     }
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, (rbits_t)__shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
@@ -310,14 +319,27 @@ __global__ void __launch_bounds__(1024) k_scale(const MatDesc *__restrict__ mats
     const real_t s = from_bits(sb);
     const int ex = (nf || sb == 0) ? 0 : ilogb(s);
     // rev: the solve runs on J B^T J, diagonal d and superdiagonal e reversed
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const int id = md.rev ? n - 1 - i : i, ie = md.rev ? n - 2 - i : i;
-        md.dsc[i] = nf ? R(0) : scale_pow2(md.d_in[id], ex);
-        md.esc[i] = (nf || i + 1 >= n) ? R(0) : scale_pow2(md.e_in[ie], ex);
+    for (int i0 = threadIdx.x; i0 < n; i0 += U * T) {
+        real_t v[U], w[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * T;
+            const int id = rev ? n - 1 - i : i, ie = rev ? n - 2 - i : i;
+            v[u] = (i < n) ? din[id] : R(0);
+            w[u] = (i + 1 < n) ? ein[ie] : R(0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * T;
+            if (i < n) {
+                dsc[i] = nf ? R(0) : scale_pow2(v[u], ex);
+                esc[i] = (nf || i + 1 >= n) ? R(0) : scale_pow2(w[u], ex);
+            }
+        }
     }
     if (threadIdx.x == 0) {
-        md.scale[0] = (nf || s == R(0)) ? R(0) : scalbn(R(1), ex);   // a zero matrix has zero values
-        md.info[0] = nf ? BDC_ERR_NONFINITE : 0;
+        scale[0] = (nf || s == R(0)) ? R(0) : scalbn(R(1), ex);   // a zero matrix has zero values
+        info[0] = nf ? BDC_ERR_NONFINITE : 0;
     }
 }
 

@@ -21,7 +21,11 @@
 // The sequential deflation scan is parallelised exactly: the small-z test
 // uses the original z, so survivors of it are found with a block scan; the
 // close-value test only compares consecutive survivors, so chains of close
-// values are independent and each is walked by one thread.
+// values are independent and each is walked by one thread.  The scans over
+// a node's positions go by warps over chunks of 32 consecutive positions,
+// several chunks' loads in flight together: the merges at the top of the
+// tree have one CTA for thousands of positions, and a loop that waited on
+// one load per chunk would be bound by the round trips.
 #include <algorithm>
 #include <mutex>
 
@@ -32,6 +36,10 @@ namespace BDC_NS {
 namespace {
 
 constexpr int PREP_THREADS = 512;
+// chunks of 32 positions whose loads the deflation and numbering loops of
+// the prep issue together (one round trip per batch instead of per chunk)
+constexpr int kDeflBatch = 8;
+constexpr int kNumBatch = 4;      // the same for the survivor numbering (more loads per chunk)
 constexpr int FL_START = 16, FL_MEMBER = 32;
 
 __device__ __forceinline__ int block_excl_scan(int v, int *wsum, int &total) {
@@ -124,8 +132,8 @@ __device__ int deflate_core(int m, real_t tol, const real_t *ds, real_t *zs, con
                             int *slist, int *sidx, int *role, real_t *rc, real_t *rs, int *wsum,
                             int *a_out) {
     const int T = blockDim.x, t = threadIdx.x;
-    const int seg = (m + T - 1) / T;
-    const int b = min(m, t * seg), e = min(m, b + seg);
+    const int lane = t & 31, nw = T >> 5;
+    const unsigned lt = (1u << lane) - 1u;       // lanes below this one
     // z_0 (paired with d_0 = 0) is clamped up to tol, never deflated
     if (t == 0) {
         real_t z0 = zs[0];
@@ -133,16 +141,49 @@ __device__ int deflate_core(int m, real_t tol, const real_t *ds, real_t *zs, con
     }
     __syncthreads();
     const rbits_t tolb = abits(tol);
+    // survivors (position 0 and |z| > tol), numbered in ascending position
+    // order.  Warp w takes the positions [wb, we) in chunks of 32 consecutive
+    // ones (lane = position: coalesced), the loads of kDeflBatch chunks in
+    // flight together; a chunk's survivors are counted by a ballot and
+    // numbered by the population count of the lower lanes.
+    const int wspan = ((m + nw - 1) / nw + 31) & ~31;
+    const int wb = min(m, (t >> 5) * wspan), we = min(m, wb + wspan);
     int cnt = 0;
-    for (int p = b; p < e; ++p) cnt += (p == 0 || abits(zs[p]) > tolb);
+    for (int c0 = wb; c0 < we; c0 += 32 * kDeflBatch) {
+        rbits_t zb[kDeflBatch];
+#pragma unroll
+        for (int u = 0; u < kDeflBatch; ++u) {
+            const int p = c0 + 32 * u + lane;
+            zb[u] = (p < we) ? abits(zs[p]) : (rbits_t)0;
+        }
+#pragma unroll
+        for (int u = 0; u < kDeflBatch; ++u) {
+            const int p = c0 + 32 * u + lane;
+            cnt += __popc(__ballot_sync(0xffffffffu, p < we && (p == 0 || zb[u] > tolb)));
+        }
+    }
     int ns;
-    int k = block_excl_scan(cnt, wsum, ns);
-    for (int p = b; p < e; ++p) {
-        if (p == 0 || abits(zs[p]) > tolb) {
-            slist[k] = p; sidx[p] = k; ++k;
-        } else {
-            sidx[p] = -1;
-            role[p] = ROLE_DEFL;
+    int k = __shfl_sync(0xffffffffu, block_excl_scan(lane == 0 ? cnt : 0, wsum, ns), 0);
+    for (int c0 = wb; c0 < we; c0 += 32 * kDeflBatch) {
+        rbits_t zb[kDeflBatch];
+#pragma unroll
+        for (int u = 0; u < kDeflBatch; ++u) {
+            const int p = c0 + 32 * u + lane;
+            zb[u] = (p < we) ? abits(zs[p]) : (rbits_t)0;
+        }
+#pragma unroll
+        for (int u = 0; u < kDeflBatch; ++u) {
+            const int p = c0 + 32 * u + lane;
+            const bool keep = p < we && (p == 0 || zb[u] > tolb);
+            const unsigned b = __ballot_sync(0xffffffffu, keep);
+            if (keep) {
+                const int kk = k + __popc(b & lt);
+                slist[kk] = p; sidx[p] = kk;
+            } else if (p < we) {
+                sidx[p] = -1;
+                role[p] = ROLE_DEFL;
+            }
+            k += __popc(b);
         }
     }
     __syncthreads();
@@ -434,19 +475,25 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
         return (code == ROLE_ZERO) ? 4 : 5;
     };
     int cnt[6] = {0, 0, 0, 0, 0, 0};             // this warp's counts (lane 0 keeps them)
-    int rnext = (wb + lane < we) ? role[wb + lane] : 0;   // the next chunk's roles, loaded one chunk ahead
-    for (int p0 = wb; p0 < we; p0 += 32) {
-        const int p = p0 + lane;
-        const int rp = rnext;
-        if (p + 32 < we) rnext = role[p + 32];
-        int grp = -1, cat = -1;
-        if (p < we) cat = category(p, rp, grp);
-        cnt[0] += __popc(__ballot_sync(0xffffffffu, cat == 0));
-        cnt[1] += __popc(__ballot_sync(0xffffffffu, cat == 0 && grp == 1));
-        cnt[2] += __popc(__ballot_sync(0xffffffffu, cat == 0 && grp == 3));
-        cnt[3] += __popc(__ballot_sync(0xffffffffu, cat == 0 && grp == 2));
-        cnt[4] += __popc(__ballot_sync(0xffffffffu, cat == 4));
-        cnt[5] += __popc(__ballot_sync(0xffffffffu, cat == 5));
+    for (int c0 = wb; c0 < we; c0 += 32 * kDeflBatch) {
+        int rr[kDeflBatch];                      // the roles of kDeflBatch chunks, loaded together
+#pragma unroll
+        for (int u = 0; u < kDeflBatch; ++u) {
+            const int p = c0 + 32 * u + lane;
+            rr[u] = (p < we) ? role[p] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < kDeflBatch; ++u) {
+            const int p = c0 + 32 * u + lane;
+            int grp = -1, cat = -1;
+            if (p < we) cat = category(p, rr[u], grp);
+            cnt[0] += __popc(__ballot_sync(0xffffffffu, cat == 0));
+            cnt[1] += __popc(__ballot_sync(0xffffffffu, cat == 0 && grp == 1));
+            cnt[2] += __popc(__ballot_sync(0xffffffffu, cat == 0 && grp == 3));
+            cnt[3] += __popc(__ballot_sync(0xffffffffu, cat == 0 && grp == 2));
+            cnt[4] += __popc(__ballot_sync(0xffffffffu, cat == 4));
+            cnt[5] += __popc(__ballot_sync(0xffffffffu, cat == 5));
+        }
     }
     // warp bases: exclusive scans over the warps (one value per warp, in lane 0)
     int N, n1, n2, n3, nz, no;
@@ -469,72 +516,80 @@ __global__ void __launch_bounds__(PREP_THREADS) k_merge_prep(const NodeDesc *__r
     int *nus = slots ? md.us[nd.buf] + r0 : nullptr, *nvs = slots ? md.vs[nd.buf] + r0 : nullptr;
     auto slot_u = [&](int c) { return c == 0 ? r0 + nl : (c <= nl ? cus[r0L + c - 1] : cus[r0R + (c - nl - 1)]); };
     auto slot_v = [&](int c) { return c == 0 ? cvs[r0L + nl] : (c <= nl ? cvs[r0L + c - 1] : cvs[r0R + (c - nl - 1)]); };
-    // software pipeline over the chunks (nothing read here is written in
-    // this loop): the roles, values and sources two chunks ahead and the
-    // slots of the next chunk's sources are loaded before this chunk's stores
+    // batches of kNumBatch chunks (nothing read here is written in this
+    // loop): the roles, values and sources of a batch are loaded together,
+    // then the slots of its sources, before any of its stores
     auto ld_pos = [&](int q, int &rq, real_t &dq, real_t &zq, int &cq) {
         if (q < we) { rq = role[q]; dq = ds[q]; zq = zs[q]; cq = slots ? src[q] : 0; }
     };
-    int r1 = 0, c1 = 0, r2 = 0, c2 = 0, su1 = 0, sv1 = 0;
-    real_t d1 = R(0), z1 = R(0), d2 = R(0), z2 = R(0);
-    ld_pos(wb + lane, r1, d1, z1, c1);
-    if (slots && wb + lane < we) { su1 = slot_u(c1); sv1 = slot_v(c1); }
-    ld_pos(wb + 32 + lane, r2, d2, z2, c2);
-    for (int p0 = wb; p0 < we; p0 += 32) {
-        const int p = p0 + lane;
-        const bool in = p < we;
-        const int rp = r1, su = su1, sv = sv1;
-        const real_t dp = d1, zp = z1;
-        r1 = r2; d1 = d2; z1 = z2; c1 = c2;
-        if (slots && p + 32 < we) { su1 = slot_u(c1); sv1 = slot_v(c1); }
-        ld_pos(p + 64, r2, d2, z2, c2);
-        int grp = -1, cat = -1;
-        real_t dsp = R(0), zsp = R(0);
-        if (in) {
-            cat = category(p, rp, grp);
-            dsp = dp;
-            zsp = zp;
+    for (int c0 = wb; c0 < we; c0 += 32 * kNumBatch) {
+        int rq[kNumBatch], cq[kNumBatch], suq[kNumBatch], svq[kNumBatch];
+        real_t dq[kNumBatch], zq[kNumBatch];
+#pragma unroll
+        for (int u = 0; u < kNumBatch; ++u) {
+            rq[u] = cq[u] = suq[u] = svq[u] = 0;
+            dq[u] = zq[u] = R(0);
+            ld_pos(c0 + 32 * u + lane, rq[u], dq[u], zq[u], cq[u]);
         }
-        const unsigned bk = __ballot_sync(0xffffffffu, cat == 0), b1 = __ballot_sync(0xffffffffu, cat == 0 && grp == 1),
-                       b2 = __ballot_sync(0xffffffffu, cat == 0 && grp == 3),
-                       b3 = __ballot_sync(0xffffffffu, cat == 0 && grp == 2),
-                       bz = __ballot_sync(0xffffffffu, cat == 4), bo = __ballot_sync(0xffffffffu, cat == 5);
-        if (in) {
-            int col;                                     // node column of sorted position p
-            if (cat == 0) {
-                const int ik = base[0] + __popc(bk & lt);
-                const int kp = (grp == 0) ? P1
-                             : (grp == 1) ? base[1] + __popc(b1 & lt)
-                             : (grp == 3) ? P1 + 1 + base[2] + __popc(b2 & lt)
-                                          : P1 + 1 + n2 + base[3] + __popc(b3 & lt);
-                dM[ik] = dsp;
-                zM[ik] = zsp;
-                md.d32[r0 + ik] = (float)dsp;
-                md.z32[r0 + ik] = (float)zsp;
-                kposM[ik] = kp;
-                invK[kp] = ik;
-                dest[p] = kp;
-                col = ik;
-            } else if (cat == 4) {
-                const int iz = base[4] + __popc(bz & lt);
-                dval[iz] = R(0);
-                dsrc[iz] = p;
-                dest[p] = -(1 + iz);
-                col = N + iz;
-            } else {
-                const int slot = nz + base[5] + __popc(bo & lt);
-                dval[slot] = dsp;
-                dsrc[slot] = p;
-                dest[p] = -(1 + slot);
-                col = N + slot;
-            }
-            if (slots) {
-                nus[col] = su;
-                nvs[col] = sv;
-            }
+        if (slots) {
+#pragma unroll
+            for (int u = 0; u < kNumBatch; ++u)
+                if (c0 + 32 * u + lane < we) { suq[u] = slot_u(cq[u]); svq[u] = slot_v(cq[u]); }
         }
-        base[0] += __popc(bk); base[1] += __popc(b1); base[2] += __popc(b2);
-        base[3] += __popc(b3); base[4] += __popc(bz); base[5] += __popc(bo);
+#pragma unroll
+        for (int u = 0; u < kNumBatch; ++u) {
+            const int p = c0 + 32 * u + lane;
+            const bool in = p < we;
+            const int rp = rq[u], su = suq[u], sv = svq[u];
+            const real_t dp = dq[u], zp = zq[u];
+            int grp = -1, cat = -1;
+            real_t dsp = R(0), zsp = R(0);
+            if (in) {
+                cat = category(p, rp, grp);
+                dsp = dp;
+                zsp = zp;
+            }
+            const unsigned bk = __ballot_sync(0xffffffffu, cat == 0), b1 = __ballot_sync(0xffffffffu, cat == 0 && grp == 1),
+                           b2 = __ballot_sync(0xffffffffu, cat == 0 && grp == 3),
+                           b3 = __ballot_sync(0xffffffffu, cat == 0 && grp == 2),
+                           bz = __ballot_sync(0xffffffffu, cat == 4), bo = __ballot_sync(0xffffffffu, cat == 5);
+            if (in) {
+                int col;                                     // node column of sorted position p
+                if (cat == 0) {
+                    const int ik = base[0] + __popc(bk & lt);
+                    const int kp = (grp == 0) ? P1
+                                 : (grp == 1) ? base[1] + __popc(b1 & lt)
+                                 : (grp == 3) ? P1 + 1 + base[2] + __popc(b2 & lt)
+                                              : P1 + 1 + n2 + base[3] + __popc(b3 & lt);
+                    dM[ik] = dsp;
+                    zM[ik] = zsp;
+                    md.d32[r0 + ik] = (float)dsp;
+                    md.z32[r0 + ik] = (float)zsp;
+                    kposM[ik] = kp;
+                    invK[kp] = ik;
+                    dest[p] = kp;
+                    col = ik;
+                } else if (cat == 4) {
+                    const int iz = base[4] + __popc(bz & lt);
+                    dval[iz] = R(0);
+                    dsrc[iz] = p;
+                    dest[p] = -(1 + iz);
+                    col = N + iz;
+                } else {
+                    const int slot = nz + base[5] + __popc(bo & lt);
+                    dval[slot] = dsp;
+                    dsrc[slot] = p;
+                    dest[p] = -(1 + slot);
+                    col = N + slot;
+                }
+                if (slots) {
+                    nus[col] = su;
+                    nvs[col] = sv;
+                }
+            }
+            base[0] += __popc(bk); base[1] += __popc(b1); base[2] += __popc(b2);
+            base[3] += __popc(b3); base[4] += __popc(bz); base[5] += __popc(bo);
+        }
     }
     if (slots && sqre && t == 0) nvs[m] = cvs[r0R + nr];   // the new null vector takes q_2's slot
     for (int kp = n1 + t; kp < P1; kp += T) invK[kp] = -1;
