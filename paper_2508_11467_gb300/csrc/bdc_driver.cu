@@ -258,24 +258,30 @@ MatDesc carve(char *base, size_t off, int n, int vals = 0) {
 
 // ------------------------------------------------------------------ kernels
 #ifdef BDC_FP32
-constexpr int kMantBits = 23, kExpMax = 255;
+constexpr int kMantBits = 23, kExpMax = 255, kExpBias = 127;
 __device__ __forceinline__ rbits_t rbits(real_t v) { return __float_as_int(v); }
 __device__ __forceinline__ real_t from_bits(rbits_t b) { return __int_as_float(b); }
 #else
-constexpr int kMantBits = 52, kExpMax = 2047;
+constexpr int kMantBits = 52, kExpMax = 2047, kExpBias = 1023;
 __device__ __forceinline__ rbits_t rbits(real_t v) { return __double_as_longlong(v); }
 __device__ __forceinline__ real_t from_bits(rbits_t b) { return __longlong_as_double(b); }
 #endif
 
+// The rare cases of the scaling (results below the normal range, a
+// subnormal maximum), out of line: inline, the compiler may evaluate them
+// for every entry and select, and one SM's FP64 rate (a few lane operations
+// per clock) would then set the kernel's time.
+__device__ __noinline__ real_t scale_pow2_slow(real_t v, int ex) { return scalbn(v, -ex); }
+__device__ __noinline__ int ilogb_slow(real_t v) { return ilogb(v); }
+
 // v 2^-ex for finite v: by exponent-field arithmetic (integer operations)
 // when v and the result are normal numbers, else scalbn (zeros, entries
-// that fall below the normal range).  One CTA scales a whole matrix, and
-// its FP64 rate (a few operations per clock) would bound the kernel.
+// that fall below the normal range).
 __device__ __forceinline__ real_t scale_pow2(real_t v, int ex) {
     const rbits_t b = rbits(v);
     const int e = (int)((b >> kMantBits) & kExpMax);
     if (e != 0 && e - ex >= 1 && e - ex < kExpMax) return from_bits(b - ((rbits_t)ex << kMantBits));
-    return scalbn(v, -ex);
+    return scale_pow2_slow(v, ex);
 }
 
 // Scale by the power of two 2^ex <= max |entry| < 2^(ex+1): exact (no
@@ -317,7 +323,10 @@ __global__ void __launch_bounds__(1024) k_scale(const MatDesc *__restrict__ mats
     for (int k = 0; k < (int)(blockDim.x >> 5); ++k) sb = max(sb, sh[k]);
     const bool nf = sb >= kInfBits;
     const real_t s = from_bits(sb);
-    const int ex = (nf || sb == 0) ? 0 : ilogb(s);
+    // ilogb of the maximum from its exponent field (a normal number), the
+    // library call only for a subnormal maximum
+    const int eb = (int)(sb >> kMantBits);
+    const int ex = (nf || sb == 0) ? 0 : (eb != 0 ? eb - kExpBias : ilogb_slow(s));
     // rev: the solve runs on J B^T J, diagonal d and superdiagonal e reversed
     for (int i0 = threadIdx.x; i0 < n; i0 += U * T) {
         real_t v[U], w[U];
@@ -338,7 +347,7 @@ __global__ void __launch_bounds__(1024) k_scale(const MatDesc *__restrict__ mats
         }
     }
     if (threadIdx.x == 0) {
-        scale[0] = (nf || s == R(0)) ? R(0) : scalbn(R(1), ex);   // a zero matrix has zero values
+        scale[0] = (nf || sb == 0) ? R(0) : scalbn(R(1), ex);   // a zero matrix has zero values
         info[0] = nf ? BDC_ERR_NONFINITE : 0;
     }
 }

@@ -217,10 +217,25 @@ __device__ __forceinline__ real_t quot(real_t z, real_t x) {
 #endif
 }
 
-// plane rotation with c f + s g = r, -s f + c g = 0
+// plane rotation with c f + s g = r, -s f + c g = 0.  When both |f| and |g|
+// lie below kRotSmall (f and g may be subnormal: a quotient of two
+// subnormals carries only their few significant bits, and c^2 + s^2 would
+// miss 1 by far more than an ulp), c and s are formed from copies scaled up
+// by the power of two kRotUp (exact) and r is scaled back.
+#ifdef BDC_FP32
+constexpr float kRotSmall = 0x1p-63f, kRotUp = 0x1p64f, kRotDown = 0x1p-64f;
+#else
+constexpr double kRotSmall = 0x1p-511, kRotUp = 0x1p600, kRotDown = 0x1p-600;
+#endif
 __device__ __forceinline__ void make_rot(real_t f, real_t g, real_t &c, real_t &s, real_t &r) {
     if (g == R(0)) { c = R(1); s = R(0); r = f; return; }
     if (f == R(0)) { c = R(0); s = R(1); r = g; return; }
+    if (fabs(f) < kRotSmall && fabs(g) < kRotSmall) {
+        const real_t fs = f * kRotUp, gs = g * kRotUp;
+        const real_t h = hypot(fs, gs);
+        c = fs / h; s = gs / h; r = h * kRotDown;
+        return;
+    }
     const real_t h = hypot(f, g);
     c = f / h; s = g / h; r = h;
 }

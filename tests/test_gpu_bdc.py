@@ -155,6 +155,38 @@ def test_negative_and_scaled_entries(bdc):
     _check_full(bdc, d, e, leaf=16)
 
 
+def test_scaling_subnormal_maximum(bdc):
+    """Largest entry subnormal: the scale's exponent comes from ilogb (not
+    the exponent field) and every entry is scaled up by scalbn.  B and S are
+    checked after multiplying both by 2^k (exact at these magnitudes), so
+    that the checks themselves do not underflow; S keeps the spacing of the
+    subnormal range, 2^-1074, which is 2^-41 of its largest value here."""
+    n, k = 200, 1033
+    d, e = inputs.uniform(n, 11)
+    ds, es = np.ldexp(d, -k), np.ldexp(e, -k)
+    assert np.max(np.abs(np.concatenate([ds, es]))) < np.finfo(np.float64).tiny
+    S, U, VT, info = _run(bdc, ds, es, leaf=16)
+    assert info == 0
+    s = np.ldexp(S.cpu().numpy(), k)
+    du, eu = np.ldexp(ds, k), np.ldexp(es, k)      # the same (rounded) entries, scaled up exactly
+    tol = 1e-13 * n
+    assert np.all(np.diff(s) <= 0) and np.all(s >= 0)
+    assert check.sigma_rel_err(s, oracle.sigma_only(du, eu)) <= tol
+    assert oracle.residual(du, eu, s, U.cpu().numpy(), VT.cpu().numpy()) <= tol
+    assert _orth_gpu(U) <= tol and _orth_gpu(VT.t()) <= tol
+
+
+def test_scaling_entries_below_normal_range(bdc):
+    """Entries that leave the normal range once scaled (largest ~1e150, some
+    of 1e-170: ~1e-320 after scaling), which take scalbn instead of the
+    exponent arithmetic; norm-wise against the oracle on the same input."""
+    d, e = inputs.uniform(300, 12)
+    d, e = d * 1e150, e * 1e150
+    d[::7] = 1e-170
+    e[3::11] = -1e-170
+    _check_full(bdc, d, e, leaf=16)
+
+
 # ---------------------------------------------------------------- mixed precision
 @pytest.mark.parametrize("kind,seed", [("uniform", 0), ("graded", 1), ("clustered", 2)])
 def test_mixed_exact_n4096(bdc, kind, seed):
