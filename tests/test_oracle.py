@@ -70,6 +70,40 @@ def test_against_lapack(kind, n):
     assert check.e_svd(d, e, s, U, VT) <= 4 * n * EPS
 
 
+@pytest.mark.parametrize("k", [-1033, -700, 480])
+def test_power_of_two_scaling_against_lapack(k):
+    """sigma(2^k B) = 2^k sigma(B): the oracle on B scaled by 2^k (k = -1033
+    puts every entry below the normal range) against LAPACK on the same
+    entries scaled back to order one (exact).  Subnormal outputs keep the
+    spacing 2^-1074, which the tolerance adds."""
+    n = 60
+    d, e = inputs.uniform(n, 31)
+    ds, es = np.ldexp(d, k), np.ldexp(e, k)
+    du, eu = np.ldexp(ds, -k), np.ldexp(es, -k)     # the entries the oracle sees, at order one
+    ref = np.linalg.svd(oracle.dense(du, eu), compute_uv=False)
+    s, U, VT = oracle.bdsqr(ds, es)
+    su = np.ldexp(s, -k)
+    tol = 4 * n * EPS + 2.0 ** (-1074 - k) / ref[0]
+    assert check.sigma_rel_err(su, ref) <= tol
+    assert oracle.residual(du, eu, su, U, VT) <= tol
+    assert check.orth_err(U) <= 4 * n * EPS and check.orth_err(VT.T) <= 4 * n * EPS
+
+
+def test_entries_across_the_exponent_range_against_lapack():
+    """Entries of 1e150 beside entries of 1e-170 (below the normal range once
+    divided by the largest): norm-wise against LAPACK."""
+    n = 80
+    d, e = inputs.uniform(n, 32)
+    d, e = d * 1e150, e * 1e150
+    d[::7] = 1e-170
+    e[3::11] = -1e-170
+    ref = np.linalg.svd(oracle.dense(d, e), compute_uv=False)
+    s, U, VT = oracle.bdsqr(d, e)
+    assert check.sigma_rel_err(s, ref) <= 4 * n * EPS
+    assert oracle.residual(d, e, s, U, VT) <= 4 * n * EPS
+    assert check.orth_err(U) <= 4 * n * EPS and check.orth_err(VT.T) <= 4 * n * EPS
+
+
 def test_invariants_graded():
     n = 256
     d, e = inputs.graded(n, 1)
