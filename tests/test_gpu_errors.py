@@ -1,5 +1,5 @@
-"""Error paths made on the host (SURVEY-style failure detection without a GPU
-fault): forced non-convergence, a bounded device wait that gives up, and a
+"""Error paths made on the host (failure detection without a GPU fault):
+forced non-convergence, a bounded device wait that gives up, and a
 caller's CUDA graph that outlives the library's descriptor caches.
 
 * max_iter = 1: the secular roots (and leaf QR sweeps) cannot converge; the
