@@ -72,6 +72,19 @@ def test_values_edge_cases(bdc):
     assert info == bdc.BDC_ERR_NONFINITE
 
 
+def test_values_across_the_exponent_range(bdc):
+    """Entries of 1e150 beside entries of 1e-170, in rows whose d and e are
+    both below the normal range once scaled: the merge's coupling entries
+    are then subnormal, and the rotation folding them must still be
+    orthogonal (the two tracked rows of V carry it to the parent's z)."""
+    d, e = inputs.uniform(300, 12)
+    d, e = d * 1e150, e * 1e150
+    d[::7] = 1e-170
+    e[3::11] = -1e-170
+    s = _vals(bdc, d, e, leaf=16)
+    assert check.sigma_rel_err(s, oracle.sigma_only(d, e)) <= 1e-13 * 300
+
+
 def test_values_seeded_start(bdc):
     d, e = inputs.graded(2048, 3)
     s0 = _vals(bdc, d, e)
