@@ -42,7 +42,7 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
 # FP64 rates of this part measured by throughput probes (per SM per clock):
 # mma.sync.m8n8k4.f64 6.66 MAC; DFMA 1.99 lane operations (independent chains
-# on every SM: 626.7 G DFMA/s = 1.253 TFLOP/s at 2070 MHz)
+# on every SM: 626.7 G DFMA/s = 1.253 TFLOP/s at 2070 MHz; bench_fp64_peak.cu)
 FP64_DMMA_MAC_PER_CLK_SM = 6.66
 FP64_ALU_OPS_PER_CLK_SM = 1.99
 SMS = 152
