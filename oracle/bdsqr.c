@@ -299,16 +299,33 @@ double oracle_sturm_sigma(int n, const double *d, const double *e, int k)
 double oracle_residual(int n, const double *d, const double *e, const double *s,
                        const double *U, int ldu, const double *VT, int ldvt)
 {
+    /* The ratio does not change when B and S are scaled by the same power of
+     * two (exact), so both are taken as d 2^-k, e 2^-k, s 2^-k with 2^k <=
+     * max|d, e| < 2^(k+1): the sums of squares then stay inside the exponent
+     * range for entries near either end of it. */
+    double mx = 0.0;
+    for (int i = 0; i < n; ++i) mx = fmax(mx, fabs(d[i]));
+    for (int i = 0; i + 1 < n; ++i) mx = fmax(mx, fabs(e[i]));
+    const int k = (mx > 0.0 && isfinite(mx)) ? ilogb(mx) : 0;
+    double *ds = (double *)malloc(sizeof(double) * (size_t)(3 * n + 1));
+    if (!ds) return NAN;
+    double *es = ds + n, *ss = es + n;
+    for (int i = 0; i < n; ++i) {
+        ds[i] = ldexp(d[i], -k);
+        es[i] = (i + 1 < n) ? ldexp(e[i], -k) : 0.0;
+        ss[i] = ldexp(s[i], -k);
+    }
     double num = 0.0, den = 0.0;
-    for (int i = 0; i < n; ++i) den += d[i] * d[i];
-    for (int i = 0; i + 1 < n; ++i) den += e[i] * e[i];
+    for (int i = 0; i < n; ++i) den += ds[i] * ds[i];
+    for (int i = 0; i + 1 < n; ++i) den += es[i] * es[i];
     for (int c = 0; c < n; ++c) {                 /* column c: B v_c - s_c u_c */
         for (int r = 0; r < n; ++r) {
-            double bv = d[r] * VT[(size_t)r * ldvt + c];
-            if (r + 1 < n) bv += e[r] * VT[(size_t)(r + 1) * ldvt + c];
-            double t = bv - s[c] * U[(size_t)c * ldu + r];
+            double bv = ds[r] * VT[(size_t)r * ldvt + c];
+            if (r + 1 < n) bv += es[r] * VT[(size_t)(r + 1) * ldvt + c];
+            double t = bv - ss[c] * U[(size_t)c * ldu + r];
             num += t * t;
         }
     }
+    free(ds);
     return den > 0.0 ? sqrt(num / den) : sqrt(num);
 }
