@@ -1,0 +1,51 @@
+"""Property-based pins of the FP64 QR oracle against LAPACK (numpy's SVD of
+the dense bidiagonal), over random small bidiagonals whose entries mix
+zeros, values of order one, and tiny and huge magnitudes (1e-150 to 1e150,
+either sign), the inputs on which the QR's zero-diagonal chases, splits and
+scaling are taken.  Bar: singular values norm-wise within 8 n eps of
+LAPACK's, residual and orthogonality of the vectors within 8 n eps.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import check
+
+hypothesis = pytest.importorskip("hypothesis")
+from hypothesis import given, settings, strategies as st  # noqa: E402
+
+EPS = np.finfo(np.float64).eps
+
+_entry = st.one_of(
+    st.just(0.0),
+    st.floats(min_value=0.5, max_value=1.5),
+    st.floats(min_value=-1.5, max_value=-0.5),
+    st.sampled_from([1e-150, -1e-150, 1e-20, 3e-8, 1e8, 1e150, -1e150]),
+)
+
+
+@st.composite
+def bidiagonals(draw):
+    n = draw(st.integers(min_value=1, max_value=24))
+    d = np.array(draw(st.lists(_entry, min_size=n, max_size=n)), dtype=np.float64)
+    e = np.array(draw(st.lists(_entry, min_size=n - 1, max_size=n - 1)), dtype=np.float64)
+    scale = draw(st.sampled_from([1.0, 1e-100, 1e100]))
+    return d * scale, e * scale
+
+
+@settings(max_examples=300, deadline=None)
+@given(bidiagonals())
+def test_oracle_against_lapack_on_mixed_magnitudes(de):
+    d, e = de
+    n = d.shape[0]
+    B = oracle.dense(d, e)
+    ref = np.linalg.svd(B, compute_uv=False)
+    s, U, VT = oracle.bdsqr(d, e)
+    assert np.all(np.diff(s) <= 0) and np.all(s >= 0)
+    if ref[0] == 0.0:
+        assert np.all(s == 0.0)
+        return
+    assert np.max(np.abs(s - ref)) <= 8 * n * EPS * ref[0]
+    assert np.array_equal(oracle.sigma_only(d, e), s)
+    assert oracle.residual(d, e, s, U, VT) <= 8 * n * EPS
+    assert check.orth_err(U) <= 8 * n * EPS and check.orth_err(VT.T) <= 8 * n * EPS
