@@ -60,15 +60,16 @@ def secular_roots(d, z, max_iter: int = 400):
     lower = d.copy()
     # midpoint sign decides the origin
     mid = 0.5 * (lower + upper)
-    org_left = np.arange(N)
-    fmid = _f_shifted(d, z, org_left, mid - lower)
-    left = fmid >= 0.0                      # root in the left half -> origin d_i
-    left[-1] = True                         # last root measured from d_{N-1}
+    left = np.ones(N, dtype=bool)           # root in the left half -> origin d_i
+    if N > 1:                               # (the last root is measured from d_{N-1})
+        left[:-1] = _f_shifted(d, z, np.arange(N - 1), (mid - lower)[:-1]) >= 0.0
     org = np.where(left, np.arange(N), np.minimum(np.arange(N) + 1, N - 1))
     # bracket for tau around the origin
     lo = np.where(left, 0.0, -(upper - mid))
     hi = np.where(left, mid - lower, 0.0)
-    hi[-1] = upper[-1] - lower[-1]
+    # the last interval's length sqrt(d^2 + |z|^2) - d as |z|^2 / (sqrt(d^2 +
+    # |z|^2) + d): the difference cancels to 0 when |z|^2 is below d^2 eps
+    hi[-1] = zz / (upper[-1] + d[-1]) if zz > 0.0 else 0.0
     for _ in range(max_iter):
         m = 0.5 * (lo + hi)
         moving = (m > lo) & (m < hi)

@@ -73,6 +73,28 @@ def test_secular_roots_near_tiny_weight_poles_first_order():
     assert np.all(np.abs(f) <= 64 * N * EPS * scale)
 
 
+@pytest.mark.parametrize("z1", [1e-3, 1e-8, 1e-12])
+def test_last_root_with_tiny_weight_closed_form(z1):
+    """Two poles d = (0, 1), z = (z0, z1) with z1^2 below eps: the last root
+    omega = 1 + tau sits within an ulp of its pole.  Closed form: x = omega^2
+    - 1 solves x^2 + (1 - z0^2 - z1^2) x - z1^2 = 0 (the characteristic
+    polynomial of M^T M for M = [[z0, z1], [0, 1]]), whose positive root,
+    written without cancellation, is 2 z1^2 / (b + sqrt(b^2 + 4 z1^2)),
+    b = 1 - z0^2 - z1^2; tau = x / (1 + sqrt(1 + x))."""
+    z0 = 1e-20
+    d, z = np.array([0.0, 1.0]), np.array([z0, z1])
+    org, tau, omega = merge.secular_roots(d, z)
+    b = 1.0 - z0 * z0 - z1 * z1
+    x = 2.0 * z1 * z1 / (b + np.sqrt(b * b + 4.0 * z1 * z1))
+    t = x / (1.0 + np.sqrt(1.0 + x))
+    assert org[-1] == 1
+    assert abs(tau[-1] - t) <= 4 * EPS * t
+    # and the vectors of M built from it are orthonormal (no zero denominator)
+    zt = merge.lowner_ztilde(d, z, org, tau)
+    UM, VM = merge.m_vectors(d, zt, org, tau)
+    assert check.orth_err(UM) <= 8 * EPS and check.orth_err(VM) <= 8 * EPS
+
+
 def test_lowner_reproduces_z_when_separated():
     d, z = _random_M(60, 9, gap=1e-2)
     org, tau, _ = merge.secular_roots(d, z)
