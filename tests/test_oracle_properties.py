@@ -1,15 +1,20 @@
-"""Property-based pins of the FP64 QR oracle against LAPACK (numpy's SVD of
-the dense bidiagonal), over random small bidiagonals whose entries mix
-zeros, values of order one, and tiny and huge magnitudes (1e-150 to 1e150,
-either sign), the inputs on which the QR's zero-diagonal chases, splits and
-scaling are taken.  Bar: singular values norm-wise within 8 n eps of
-LAPACK's, residual and orthogonality of the vectors within 8 n eps.
+"""Property-based pins of the FP64 oracles over random small bidiagonals
+whose entries mix zeros, values of order one, and tiny and huge magnitudes
+(1e-150 to 1e150, either sign): the inputs on which the QR's zero-diagonal
+chases, splits and scaling, and the merge model's deflation cases, are taken.
+
+* the QR oracle against LAPACK (numpy's SVD of the dense bidiagonal);
+* the numpy model of Algorithm 2 (merge.bdc_svd, leaves of 4 and 8) against
+  the QR oracle.
+
+Bar: singular values norm-wise within 8 n eps, residual and orthogonality of
+the vectors within 8 n eps.
 """
 import numpy as np
 import pytest
 
 import oracle
-from oracle import check
+from oracle import check, merge
 
 hypothesis = pytest.importorskip("hypothesis")
 from hypothesis import given, settings, strategies as st  # noqa: E402
@@ -47,5 +52,23 @@ def test_oracle_against_lapack_on_mixed_magnitudes(de):
         return
     assert np.max(np.abs(s - ref)) <= 8 * n * EPS * ref[0]
     assert np.array_equal(oracle.sigma_only(d, e), s)
+    assert oracle.residual(d, e, s, U, VT) <= 8 * n * EPS
+    assert check.orth_err(U) <= 8 * n * EPS and check.orth_err(VT.T) <= 8 * n * EPS
+
+
+@settings(max_examples=150, deadline=None)
+@given(bidiagonals(), st.sampled_from([4, 8]))
+def test_merge_model_against_qr_on_mixed_magnitudes(de, leaf):
+    d, e = de
+    n = d.shape[0]
+    ref = oracle.sigma_only(d, e)
+    with np.errstate(all="ignore"):
+        s, U, VT = merge.bdc_svd(d, e, leaf=leaf)
+    s = np.asarray(s)
+    assert np.all(np.isfinite(s)) and np.all(s >= 0)
+    if ref[0] == 0.0:
+        assert np.all(s == 0.0)
+        return
+    assert np.max(np.abs(np.sort(s)[::-1] - ref)) <= 8 * n * EPS * ref[0]
     assert oracle.residual(d, e, s, U, VT) <= 8 * n * EPS
     assert check.orth_err(U) <= 8 * n * EPS and check.orth_err(VT.T) <= 8 * n * EPS
