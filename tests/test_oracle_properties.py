@@ -5,7 +5,10 @@ chases, splits and scaling, and the merge model's deflation cases, are taken.
 
 * the QR oracle against LAPACK (numpy's SVD of the dense bidiagonal);
 * the numpy model of Algorithm 2 (merge.bdc_svd, leaves of 4 and 8) against
-  the QR oracle.
+  the QR oracle;
+* the dense oracle (dense_svd.gesvd, with and without the QR first) against
+  LAPACK on small m x n matrices: Gaussian, with zero columns, with columns
+  graded down to 1e-12, of rank one, and scaled by 1e-150 or 1e150.
 
 Bar: singular values norm-wise within 8 n eps, residual and orthogonality of
 the vectors within 8 n eps.
@@ -14,7 +17,7 @@ import numpy as np
 import pytest
 
 import oracle
-from oracle import check, merge
+from oracle import check, dense_svd, merge
 
 hypothesis = pytest.importorskip("hypothesis")
 from hypothesis import given, settings, strategies as st  # noqa: E402
@@ -72,3 +75,39 @@ def test_merge_model_against_qr_on_mixed_magnitudes(de, leaf):
     assert np.max(np.abs(np.sort(s)[::-1] - ref)) <= 8 * n * EPS * ref[0]
     assert oracle.residual(d, e, s, U, VT) <= 8 * n * EPS
     assert check.orth_err(U) <= 8 * n * EPS and check.orth_err(VT.T) <= 8 * n * EPS
+
+
+@st.composite
+def dense_matrices(draw):
+    n = draw(st.integers(min_value=1, max_value=12))
+    m = draw(st.integers(min_value=n, max_value=20))
+    rng = np.random.default_rng(draw(st.integers(min_value=0, max_value=10 ** 6)))
+    A = rng.standard_normal((m, n))
+    kind = draw(st.sampled_from(["gauss", "zero_cols", "graded_cols", "rank1", "scaled"]))
+    if kind == "zero_cols":
+        A[:, rng.integers(0, n, max(1, n // 3))] = 0.0
+    elif kind == "graded_cols":
+        A = A * np.logspace(0, -12, n)[None, :]
+    elif kind == "rank1":
+        A = np.outer(rng.standard_normal(m), rng.standard_normal(n))
+    elif kind == "scaled":
+        A = A * draw(st.sampled_from([1e-150, 1e150]))
+    return A
+
+
+@settings(max_examples=200, deadline=None)
+@given(dense_matrices(), st.booleans())
+def test_dense_oracle_against_lapack(A, qr_first):
+    m, n = A.shape
+    ref = np.linalg.svd(A, compute_uv=False)
+    S, U, VT = dense_svd.gesvd(A, qr_first=qr_first)
+    S = np.asarray(S)
+    tol = 8 * max(m, n) * EPS
+    assert np.all(np.isfinite(S)) and np.all(np.diff(S) <= 0)
+    if ref[0] == 0.0:
+        assert np.all(S == 0.0)
+        return
+    assert np.max(np.abs(S - ref)) <= tol * ref[0]
+    U = U[:, :n]
+    assert np.linalg.norm(A - (U * S[None, :]) @ VT) <= tol * np.linalg.norm(A)
+    assert check.orth_err(U) <= tol and check.orth_err(VT.T) <= tol
